@@ -1,0 +1,243 @@
+"""FP64 CPU oracle of the Gaussian-mixture checkpoint-restart method
+(Chen, Chacon & Nguyen, arXiv 2007.12273), wrapped for numpy.
+
+TEST INFRASTRUCTURE.  Only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The arithmetic
+lives in ``gm_oracle.c`` (plain C, FP64, one cell at a time); this module
+only builds it with gcc and marshals numpy arrays.  It shares no code with
+the CUDA path.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gm_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# per-cell status bits (the library's documented values)
+ST_EM_MAXSWEEPS = 0x01
+ST_COV_NOT_PD = 0x02
+ST_TOO_FEW = 0x04
+ST_EMPTY = 0x08
+ST_DEGENERATE = 0x10
+ST_PROJ_SKIPPED = 0x100
+ST_NEG_WEIGHT = 0x200
+ST_MM_EMPTY_COL = 0x400
+ST_NO_MIXTURE = 0x800
+
+
+def build(force: bool = False) -> str:
+    """Compile gm_oracle.c into liboracle.so (gcc, OpenMP, no FP contraction
+    so that x86 and Arm hosts round identically)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+               "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Cfg(ct.Structure):
+    _fields_ = [("D", ct.c_int), ("Kmax", ct.c_int), ("shape_order", ct.c_int),
+                ("max_sweeps", ct.c_int), ("tol", ct.c_double), ("seed", ct.c_uint64),
+                ("L", ct.c_double), ("q", ct.c_double)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ct.CDLL(_LIB)
+            P = ct.c_void_p
+            lib.oracle_philox4x32_10.argtypes = [P, P, P]
+            lib.oracle_uniform52.argtypes = [ct.c_uint32, ct.c_uint32]
+            lib.oracle_uniform52.restype = ct.c_double
+            lib.oracle_compress.argtypes = [P, ct.c_int64] + [P] * 12 + [ct.c_int]
+            lib.oracle_em_cell.argtypes = [P, ct.c_int64, ct.c_int64, P, P, P, ct.c_int, ct.c_int,
+                                           P, P, P, P, P, P, P, P, ct.c_int, P]
+            lib.oracle_penalised_L.argtypes = [ct.c_int, ct.c_int, P, ct.c_int64, P, P]
+            lib.oracle_penalised_L.restype = ct.c_double
+            lib.oracle_cyclic_tridiag.argtypes = [ct.c_int64, P, P, P, P, P]
+            lib.oracle_reconstruct.argtypes = [P, ct.c_int64] + [P] * 11 + [ct.c_int]
+            lib.oracle_moments.argtypes = [P, ct.c_int64] + [P] * 9
+            lib.oracle_mixture_moments.argtypes = [P, ct.c_int64] + [P] * 7
+            lib.oracle_shape.argtypes = [ct.c_int, ct.c_double]
+            lib.oracle_shape.restype = ct.c_double
+            lib.oracle_max_threads.restype = ct.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ct.c_void_p) if a is not None else None
+
+
+def _cfg(params: dict, seed_key="seed") -> _Cfg:
+    return _Cfg(int(params["D"]), int(params["Kmax"]), int(params["shape_order"]),
+                int(params.get("max_sweeps", 1000)), float(params.get("tol", 1e-6)),
+                int(params.get(seed_key, 1)), float(params["L"]), float(params.get("q", 1.0)))
+
+
+def P_of(D: int) -> int:
+    return 1 + D + D * (D + 1) // 2
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def philox(ctr, key) -> np.ndarray:
+    lib = _load()
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib.oracle_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def uniform52(hi: int, lo: int) -> float:
+    return _load().oracle_uniform52(hi, lo)
+
+
+def shape(order: int, s: float) -> float:
+    return _load().oracle_shape(order, s)
+
+
+def max_threads() -> int:
+    return _load().oracle_max_threads()
+
+
+def compress(params: dict, cell_off, x, v, alpha, nthreads: int = 1) -> dict:
+    """Oracle compression of every cell (Sec. 2.2-2.3, final step of
+    Sec. 2.3.1, target charge density of Sec. 2.4.1)."""
+    lib = _load()
+    cfg = _cfg(params)
+    cell_off = np.ascontiguousarray(cell_off, dtype=np.int64)
+    C = cell_off.shape[0] - 1
+    D = cfg.D
+    x = _f64(x); v = _f64(v); alpha = _f64(alpha)
+    assert v.shape == (D, int(cell_off[-1]))
+    out = dict(K=np.zeros(C, np.int32), params=np.zeros((C, cfg.Kmax, P_of(D))),
+               W=np.zeros(C), rho_target=np.zeros(C), lnL=np.zeros(C),
+               sweeps=np.zeros(C, np.int32), kwork=np.zeros(C, np.int32),
+               status=np.zeros(C, np.uint32))
+    rc = lib.oracle_compress(ct.byref(cfg), C, _ptr(cell_off), _ptr(x), _ptr(v), _ptr(alpha),
+                             _ptr(out["K"]), _ptr(out["params"]), _ptr(out["W"]),
+                             _ptr(out["rho_target"]), _ptr(out["lnL"]), _ptr(out["sweeps"]),
+                             _ptr(out["kwork"]), _ptr(out["status"]), int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle_compress failed ({rc})")
+    return out
+
+
+def em_cell(params: dict, vv, alpha, cell: int = 0, init_params=None, init_K: int = 0,
+            only_sweeps: int = 0, trace_cap: int = 0) -> dict:
+    """One cell: ``vv`` is [N, D].  ``init_params`` [K, P] replaces the
+    random initialisation; ``only_sweeps`` > 0 runs that many penalised
+    sweeps and skips the final unpenalised step."""
+    lib = _load()
+    cfg = _cfg(params)
+    vv = _f64(vv).reshape(-1, cfg.D)
+    N = vv.shape[0]
+    alpha = _f64(alpha)
+    prm = np.zeros((cfg.Kmax, P_of(cfg.D)))
+    ip = None
+    if init_params is not None:
+        ip = _f64(init_params)
+        init_K = ip.shape[0]
+    K = np.zeros(1, np.int32); W = np.zeros(1); lnL = np.zeros(1)
+    sw = np.zeros(1, np.int32); st = np.zeros(1, np.uint32)
+    tr = np.zeros(max(trace_cap, 1)); kt = np.zeros(max(trace_cap, 1), np.int32)
+    nt = np.zeros(1, np.int32)
+    lib.oracle_em_cell(ct.byref(cfg), int(cell), N, _ptr(vv), _ptr(alpha), _ptr(ip), int(init_K),
+                       int(only_sweeps), _ptr(prm), _ptr(K), _ptr(W), _ptr(lnL), _ptr(sw),
+                       _ptr(st), _ptr(tr) if trace_cap else None, _ptr(kt) if trace_cap else None,
+                       int(trace_cap), _ptr(nt))
+    # Ktrace: K after initialisation / after each sweep, negative when the
+    # sweep removed a component
+    return dict(K=int(K[0]), params=prm, W=float(W[0]), lnL=float(lnL[0]), sweeps=int(sw[0]),
+                status=int(st[0]), Ltrace=tr[: int(nt[0])].copy(),
+                Ktrace=kt[: int(nt[0])].copy())
+
+
+def penalised_L(D: int, prm, vv, ah) -> float:
+    lib = _load()
+    prm = _f64(prm)
+    vv = _f64(vv).reshape(-1, D)
+    ah = _f64(ah)
+    return lib.oracle_penalised_L(D, prm.shape[0], _ptr(prm), vv.shape[0], _ptr(vv), _ptr(ah))
+
+
+def cyclic_tridiag(a, b, c, d) -> np.ndarray:
+    lib = _load()
+    a, b, c, d = (_f64(t) for t in (a, b, c, d))
+    x = np.zeros_like(d)
+    if lib.oracle_cyclic_tridiag(d.shape[0], _ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(x)) != 0:
+        raise ValueError("n < 3")
+    return x
+
+
+def reconstruct(params: dict, K, prm, W, rho_target, out_off, nthreads: int = 1,
+                want_raw: bool = False) -> dict:
+    """Oracle reconstruction (Sec. 2.4): sampling, Gauss'-law weight
+    correction, Lemons projection.  Uses ``params['recon_seed']``."""
+    lib = _load()
+    cfg = _cfg(params, "recon_seed")
+    out_off = np.ascontiguousarray(out_off, dtype=np.int64)
+    C = out_off.shape[0] - 1
+    D = cfg.D
+    Nout = int(out_off[-1])
+    K = np.ascontiguousarray(K, dtype=np.int32)
+    prm = _f64(prm); W = _f64(W); rho_target = _f64(rho_target)
+    assert prm.shape == (C, cfg.Kmax, P_of(D))
+    out = dict(x=np.zeros(Nout), v=np.zeros((D, Nout)), alpha=np.zeros(Nout),
+               status=np.zeros(C, np.uint32), dA=np.zeros(C))
+    raw = np.zeros((D, Nout)) if want_raw else None
+    rc = lib.oracle_reconstruct(ct.byref(cfg), C, _ptr(K), _ptr(prm), _ptr(W), _ptr(rho_target),
+                                _ptr(out_off), _ptr(out["x"]), _ptr(out["v"]), _ptr(out["alpha"]),
+                                _ptr(out["status"]), _ptr(out["dA"]), _ptr(raw), int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle_reconstruct failed ({rc})")
+    if want_raw:
+        out["v_raw"] = raw
+    return out
+
+
+def moments(params: dict, cell_off, x, v, alpha) -> dict:
+    lib = _load()
+    cfg = _cfg(params)
+    cell_off = np.ascontiguousarray(cell_off, dtype=np.int64)
+    C = cell_off.shape[0] - 1
+    D = cfg.D
+    nm = D * (D + 1) // 2
+    x = _f64(x); v = _f64(v); alpha = _f64(alpha)
+    out = dict(W=np.zeros(C), p=np.zeros((C, D)), M2=np.zeros((C, nm)), E=np.zeros(C),
+               rho=np.zeros(C))
+    lib.oracle_moments(ct.byref(cfg), C, _ptr(cell_off), _ptr(x), _ptr(v), _ptr(alpha),
+                       _ptr(out["W"]), _ptr(out["p"]), _ptr(out["M2"]), _ptr(out["E"]),
+                       _ptr(out["rho"]))
+    return out
+
+
+def mixture_moments(params: dict, K, prm, W) -> dict:
+    lib = _load()
+    cfg = _cfg(params)
+    K = np.ascontiguousarray(K, dtype=np.int32)
+    C = K.shape[0]
+    D = cfg.D
+    nm = D * (D + 1) // 2
+    prm = _f64(prm); W = _f64(W)
+    out = dict(W=np.zeros(C), p=np.zeros((C, D)), M2=np.zeros((C, nm)), E=np.zeros(C))
+    lib.oracle_mixture_moments(ct.byref(cfg), C, _ptr(K), _ptr(prm), _ptr(W), _ptr(out["W"]),
+                               _ptr(out["p"]), _ptr(out["M2"]), _ptr(out["E"]))
+    return out

@@ -1,0 +1,887 @@
+/*
+ * gm_oracle.c -- plain, slow FP64 CPU oracle of the Gaussian-mixture
+ * checkpoint-restart method of Chen, Chacon & Nguyen, "An unsupervised
+ * machine-learning checkpoint-restart algorithm using Gaussian mixtures for
+ * particle-in-cell simulations" (arXiv 2007.12273).
+ *
+ * TEST INFRASTRUCTURE.  Only the test-suite, the package smoke check and the
+ * benchmark's CPU-baseline leg load this library.  It shares no code, header,
+ * table or helper with the CUDA path, and the CUDA path never calls it.
+ *
+ * Every routine follows the paper's definitions in the paper's order, in
+ * FP64, one cell at a time, with no blocking, fusion or reordering beyond
+ * what the definition states.  Readings of points the paper leaves open are
+ * marked "Reading:" where they are applied.
+ *
+ * Parameter record of one component (the checkpoint payload, Sec. 1):
+ *   [ omega, mu_0..mu_{D-1}, Sigma upper triangle row-major ]
+ * i.e. P = 1 + D + D(D+1)/2 numbers (3 for 1V, 10 for 3V).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_MAXD 3
+#define OR_MAXK 16
+#define OR_PI 3.14159265358979323846
+
+/* per-cell status bits (same values as the library's documented ABI) */
+#define ST_EM_MAXSWEEPS   0x01u
+#define ST_COV_NOT_PD     0x02u
+#define ST_TOO_FEW        0x04u
+#define ST_EMPTY          0x08u
+#define ST_DEGENERATE     0x10u
+#define ST_PROJ_SKIPPED   0x100u
+#define ST_NEG_WEIGHT     0x200u
+#define ST_MM_EMPTY_COL   0x400u
+#define ST_NO_MIXTURE     0x800u
+
+typedef struct oracle_cfg {
+  int D;            /* velocity dimensions, 1 or 3 */
+  int Kmax;         /* initial number of components */
+  int shape_order;  /* 1 = CIC (S1), 2 = quadratic B-spline (S2) */
+  int max_sweeps;   /* cap on EM sweeps */
+  double tol;       /* relative change of L that ends EM */
+  uint64_t seed;    /* Philox key for the initial picks / the sampler */
+  double L;         /* periodic domain length; dx = L / C */
+  double q;         /* species charge */
+} oracle_cfg;
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 counter-based generator, written from its published        */
+/* definition (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy */
+/* as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplies, the key      */
+/* bumped by the two Weyl constants between rounds.                          */
+/* ------------------------------------------------------------------------ */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* uniform in (0,1) from two 32-bit words: 52 random bits m, u = (m + 1/2) 2^-52 */
+double oracle_uniform52(uint32_t hi, uint32_t lo) {
+  uint64_t m = ((uint64_t)hi << 20) | (uint64_t)(lo >> 12);
+  return ((double)m + 0.5) * (1.0 / 4503599627370496.0);
+}
+
+#define TAG_INIT 0x494E4954u   /* counter word 1 of the initial picks */
+#define TAG_SAMPLE 0x53000000u /* counter word 1 of the sampler (| block) */
+
+static void philox_draw(uint64_t seed, uint32_t c0, uint32_t c1, int64_t cell, uint32_t out[4]) {
+  uint32_t ctr[4] = {c0, c1, (uint32_t)((uint64_t)cell & 0xffffffffu), (uint32_t)((uint64_t)cell >> 32)};
+  uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  oracle_philox4x32_10(ctr, key, out);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gaussian component: eq. (mix-dist) and the density below it.             */
+/* ------------------------------------------------------------------------ */
+typedef struct comp {
+  double w;                    /* omega_k */
+  double mu[OR_MAXD];          /* mu_k */
+  double S[OR_MAXD][OR_MAXD];  /* Sigma_k (full symmetric) */
+  double Lc[OR_MAXD][OR_MAXD]; /* Cholesky factor, Sigma = Lc Lc^T */
+  double logdet;               /* ln |Sigma_k| */
+} comp;
+
+/* Cholesky of a symmetric DxD matrix.  Fails (returns 0) if a pivot is not
+ * positive or falls under the covariance floor 1e-13 * scale2, where scale2
+ * = sum_d (S_dd + mu_d^2) (Reading: the paper adds no regularisation; a
+ * numerically singular covariance is treated as not positive definite). */
+static int chol_floor(int D, double S[OR_MAXD][OR_MAXD], const double *mu,
+                      double Lc[OR_MAXD][OR_MAXD], double *logdet) {
+  double scale2 = 0.0;
+  for (int d = 0; d < D; ++d) scale2 += S[d][d] + mu[d] * mu[d];
+  double floor_ = 1e-13 * scale2;
+  double ld = 0.0;
+  memset(Lc, 0, sizeof(double) * OR_MAXD * OR_MAXD);
+  for (int i = 0; i < D; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      double s = S[i][j];
+      for (int m = 0; m < j; ++m) s -= Lc[i][m] * Lc[j][m];
+      if (i == j) {
+        if (!(s > floor_) || !isfinite(s)) return 0;
+        Lc[i][i] = sqrt(s);
+        ld += log(s);
+      } else {
+        Lc[i][j] = s / Lc[j][j];
+      }
+    }
+  }
+  *logdet = ld;
+  return 1;
+}
+
+/* ln f_k(v): f_k = (2 pi)^{-D/2} |Sigma|^{-1/2} exp(-(v-mu)^T Sigma^{-1} (v-mu)/2) */
+static double log_gauss(int D, const comp *c, const double *v) {
+  double d[OR_MAXD], y[OR_MAXD];
+  for (int i = 0; i < D; ++i) d[i] = v[i] - c->mu[i];
+  double maha = 0.0;
+  for (int i = 0; i < D; ++i) { /* solve Lc y = d */
+    double s = d[i];
+    for (int m = 0; m < i; ++m) s -= c->Lc[i][m] * y[m];
+    y[i] = s / c->Lc[i][i];
+    maha += y[i] * y[i];
+  }
+  return -0.5 * maha - 0.5 * c->logdet - 0.5 * D * log(2.0 * OR_PI);
+}
+
+static int T_of(int D) { return D * (D + 3) / 2; }        /* T = D(D+3)/2, App. A */
+static int P_of(int D) { return 1 + D + D * (D + 1) / 2; } /* numbers per component */
+
+/* ln sum_k omega_k f_k(v), by log-sum-exp; also returns every
+ * log(omega_k f_k(v)) in lf[] */
+static double log_mix(int D, int K, const comp *cs, const double *v, double *lf) {
+  double m = -INFINITY;
+  for (int k = 0; k < K; ++k) {
+    lf[k] = log(cs[k].w) + log_gauss(D, &cs[k], v);
+    if (lf[k] > m) m = lf[k];
+  }
+  double s = 0.0;
+  for (int k = 0; k < K; ++k) s += exp(lf[k] - m);
+  return m + log(s);
+}
+
+/* Penalised log-likelihood, eq. (lnL-GM):
+ *   L = sum_p alpha_p ln sum_k omega_k f_k(v_p) - (d/2) ln N - (T/2) sum_k ln omega_k
+ * with T = D(D+3)/2 and d = K(T+1) - 1 (App. A). */
+static double penalised_L(int D, int K, const comp *cs, int64_t N, const double *vv,
+                          const double *ah) {
+  double lf[OR_MAXK];
+  double s = 0.0;
+  for (int64_t p = 0; p < N; ++p) s += ah[p] * log_mix(D, K, cs, vv + p * D, lf);
+  int T = T_of(D);
+  double dpar = (double)K * (T + 1) - 1.0;
+  double pen = 0.0;
+  for (int k = 0; k < K; ++k) pen += log(cs[k].w);
+  return s - 0.5 * dpar * log((double)N) - 0.5 * T * pen;
+}
+
+static void renormalise(int K, comp *cs) {
+  double s = 0.0;
+  for (int k = 0; k < K; ++k) s += cs[k].w;
+  for (int k = 0; k < K; ++k) cs[k].w /= s;
+}
+
+static void remove_comp(int *K, comp *cs, int k) {
+  for (int m = k; m < *K - 1; ++m) cs[m] = cs[m + 1];
+  (*K)--;
+}
+
+static void store_params(int D, int Kmax, int K, const comp *cs, double *prm) {
+  int P = P_of(D);
+  memset(prm, 0, sizeof(double) * (size_t)Kmax * P);
+  for (int k = 0; k < K; ++k) {
+    double *r = prm + (size_t)k * P;
+    r[0] = cs[k].w;
+    for (int d = 0; d < D; ++d) r[1 + d] = cs[k].mu[d];
+    int t = 1 + D;
+    for (int i = 0; i < D; ++i)
+      for (int j = i; j < D; ++j) r[t++] = cs[k].S[i][j];
+  }
+}
+
+static void load_params(int D, int K, const double *prm, comp *cs) {
+  int P = P_of(D);
+  for (int k = 0; k < K; ++k) {
+    const double *r = prm + (size_t)k * P;
+    cs[k].w = r[0];
+    for (int d = 0; d < D; ++d) cs[k].mu[d] = r[1 + d];
+    int t = 1 + D;
+    for (int i = 0; i < D; ++i)
+      for (int j = i; j < D; ++j) { cs[k].S[i][j] = r[t]; cs[k].S[j][i] = r[t]; ++t; }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Compression of one cell (Sec. 2.2-2.3).                                  */
+/*   vv   : the cell's velocities, particle-major [N][D] (FP64)             */
+/*   alpha: the cell's weights [N]                                          */
+/* Optional: init_prm/init_K replace the random initialisation; Ltrace gets */
+/* L after initialisation and after every sweep (trace_cap entries).        */
+/* ------------------------------------------------------------------------ */
+typedef struct cell_out {
+  int32_t K;
+  double W, lnL;
+  int32_t sweeps, kwork;
+  uint32_t status;
+} cell_out;
+
+static void em_cell(const oracle_cfg *cfg, int64_t cell, int64_t N, const double *vv,
+                    const double *alpha, double *prm_out, cell_out *o,
+                    const double *init_prm, int init_K, int only_sweeps,
+                    double *Ltrace, int32_t *Ktrace, int trace_cap, int *ntrace) {
+  const int D = cfg->D, T = T_of(D);
+  const double halfT = 0.5 * T;
+  comp cs[OR_MAXK];
+  memset(o, 0, sizeof(*o));
+  memset(prm_out, 0, sizeof(double) * (size_t)cfg->Kmax * P_of(D));
+  if (ntrace) *ntrace = 0;
+  if (N == 0) { o->status = ST_EMPTY; return; }
+
+  /* Weights are normalised so that sum_p alpha_p = N (Sec. 2.2, below eq.
+   * lnL-GM); W = sum alpha is kept for reconstruction. */
+  double W = 0.0;
+  for (int64_t p = 0; p < N; ++p) W += alpha[p];
+  o->W = W;
+  if (!(W > 0.0)) { o->status = ST_EMPTY | ST_DEGENERATE; return; }
+  const double Nd = (double)N;
+  double *ah = (double *)malloc(sizeof(double) * (size_t)N);
+  double *gam = (double *)malloc(sizeof(double) * (size_t)N * OR_MAXK);
+  for (int64_t p = 0; p < N; ++p) ah[p] = alpha[p] * Nd / W;
+  if (N <= 10) o->status |= ST_TOO_FEW; /* Sec. 1: "more than 10" per cell */
+
+  /* total (sample) mean and covariance, alpha-weighted, divided by N */
+  double mean[OR_MAXD] = {0}, cov[OR_MAXD][OR_MAXD] = {{0}};
+  for (int64_t p = 0; p < N; ++p)
+    for (int d = 0; d < D; ++d) mean[d] += ah[p] * vv[p * D + d];
+  for (int d = 0; d < D; ++d) mean[d] /= Nd;
+  for (int64_t p = 0; p < N; ++p)
+    for (int i = 0; i < D; ++i)
+      for (int j = 0; j < D; ++j)
+        cov[i][j] += ah[p] * (vv[p * D + i] - mean[i]) * (vv[p * D + j] - mean[j]);
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < D; ++j) cov[i][j] /= Nd;
+
+  int K;
+  {
+    double Ltmp[OR_MAXD][OR_MAXD], ldtmp;
+    if (!chol_floor(D, cov, mean, Ltmp, &ldtmp)) {
+      /* every particle (numerically) at one velocity: a single degenerate
+       * component carrying the sample moments, no likelihood */
+      cs[0].w = 1.0;
+      for (int d = 0; d < D; ++d) cs[0].mu[d] = mean[d];
+      memcpy(cs[0].S, cov, sizeof(cov));
+      store_params(D, cfg->Kmax, 1, cs, prm_out);
+      o->K = 1; o->lnL = 0.0; o->sweeps = 0;
+      o->status |= ST_DEGENERATE | ST_COV_NOT_PD;
+      free(ah); free(gam);
+      return;
+    }
+  }
+
+  if (init_prm) {
+    K = init_K;
+    load_params(D, K, init_prm, cs);
+  } else {
+    /* Initialisation (Sec. 2.3): K ~ Kmax components, each mean a randomly
+     * chosen particle, each covariance the total covariance, equal weights.
+     * Reading: K0 = min(Kmax, N), lowered while N - T K/2 <= 0 so that the
+     * denominator of eq. (omegak) stays positive; picks are distinct
+     * indices drawn uniformly with a Philox stream keyed by (seed, cell). */
+    K = cfg->Kmax < N ? cfg->Kmax : (int)N;
+    while (K > 1 && Nd - halfT * K <= 0.0) --K;
+    int64_t picks[OR_MAXK];
+    int got = 0;
+    for (uint32_t t = 0; got < K; ++t) {
+      int64_t idx;
+      if (t < 100000u) {
+        uint32_t r[4];
+        philox_draw(cfg->seed, t, TAG_INIT, cell, r);
+        double u = oracle_uniform52(r[0], r[1]);
+        idx = (int64_t)floor(u * Nd);
+        if (idx >= N) idx = N - 1;
+      } else { /* give up drawing: smallest unused index */
+        idx = 0;
+        for (;;) {
+          int used = 0;
+          for (int m = 0; m < got; ++m) used |= (picks[m] == idx);
+          if (!used) break;
+          ++idx;
+        }
+      }
+      int dup = 0;
+      for (int m = 0; m < got; ++m) dup |= (picks[m] == idx);
+      if (!dup) picks[got++] = idx;
+    }
+    for (int k = 0; k < K; ++k) {
+      cs[k].w = 1.0 / K;
+      for (int d = 0; d < D; ++d) cs[k].mu[d] = vv[picks[k] * D + d];
+      memcpy(cs[k].S, cov, sizeof(cov));
+    }
+  }
+  for (int k = 0; k < K; ++k) {
+    if (!chol_floor(D, cs[k].S, cs[k].mu, cs[k].Lc, &cs[k].logdet)) {
+      /* cannot happen for the random init (the total covariance passed);
+       * for a supplied init, drop the component */
+      remove_comp(&K, cs, k); --k; o->status |= ST_COV_NOT_PD;
+    }
+  }
+  if (K == 0) { free(ah); free(gam); o->status |= ST_DEGENERATE; return; }
+  renormalise(K, cs);
+
+  double Lprev = penalised_L(D, K, cs, N, vv, ah);
+  if (Ltrace && *ntrace < trace_cap) { Ktrace[*ntrace] = K; Ltrace[(*ntrace)++] = Lprev; }
+  int converged = 0, sweep = 0, kwork = 0;
+  int max_sweeps = only_sweeps > 0 ? only_sweeps : cfg->max_sweeps;
+  double lf[OR_MAXK];
+
+  /* Component-wise EM (Sec. 2.3, after Celeux et al.): for each component
+   * in storage order, an E-step for that component with the current
+   * parameters of all components, then its M-step (eqs. muk, sigmak,
+   * omegak), removal if N_k - T/2 <= 0, and renormalisation of the weights;
+   * after the sweep, the convergence check on eq. (lnL-GM). */
+  for (sweep = 1; sweep <= max_sweeps; ++sweep) {
+    int annihilated = 0;
+    int k = 0;
+    while (k < K) {
+      ++kwork;
+      /* E-step, eq. (responsibility): gamma_pk = alpha_p w_k f_k / sum_j w_j f_j */
+      double Nk = 0.0;
+      for (int64_t p = 0; p < N; ++p) {
+        double lm = log_mix(D, K, cs, vv + p * D, lf);
+        gam[p] = ah[p] * exp(lf[k] - lm);
+        Nk += gam[p];
+      }
+      /* annihilation: omega_k <= 0  <=>  N_k - T/2 <= 0 (eq. omegak).
+       * Reading: the last component is never removed. */
+      if (K > 1 && Nk - halfT <= 0.0) {
+        remove_comp(&K, cs, k);
+        annihilated = 1;
+        renormalise(K, cs);
+        continue;
+      }
+      /* M-step: eq. (muk), then eq. (sigmak) about the new mean */
+      comp nc;
+      for (int d = 0; d < D; ++d) {
+        double s = 0.0;
+        for (int64_t p = 0; p < N; ++p) s += gam[p] * vv[p * D + d];
+        nc.mu[d] = s / Nk;
+      }
+      for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) {
+          double s = 0.0;
+          for (int64_t p = 0; p < N; ++p)
+            s += gam[p] * (vv[p * D + i] - nc.mu[i]) * (vv[p * D + j] - nc.mu[j]);
+          nc.S[i][j] = s / Nk;
+        }
+      if (!chol_floor(D, nc.S, nc.mu, nc.Lc, &nc.logdet)) {
+        o->status |= ST_COV_NOT_PD;
+        if (K > 1) {
+          remove_comp(&K, cs, k);
+          annihilated = 1;
+          renormalise(K, cs);
+          continue;
+        }
+        ++k; /* a lone component keeps its old parameters */
+        continue;
+      }
+      /* eq. (omegak): omega_k = (N_k - T/2) / (N - T K / 2) */
+      nc.w = (K == 1) ? 1.0 : (Nk - halfT) / (Nd - halfT * K);
+      cs[k] = nc;
+      renormalise(K, cs); /* step 3 */
+      ++k;
+    }
+    double L = penalised_L(D, K, cs, N, vv, ah);
+    if (Ltrace && *ntrace < trace_cap) { Ktrace[*ntrace] = annihilated ? -K : K; Ltrace[(*ntrace)++] = L; }
+    /* Reading: converged when the relative change of L over a sweep with no
+     * removal is at most tol. */
+    if (!annihilated && fabs(L - Lprev) <= cfg->tol * fabs(Lprev)) { converged = 1; break; }
+    Lprev = L;
+  }
+  if (!converged) {
+    sweep = max_sweeps;
+    if (only_sweeps <= 0) o->status |= ST_EM_MAXSWEEPS;
+  }
+
+  if (only_sweeps <= 0) {
+    /* Final unpenalised step (Sec. 2.3.1): one simultaneous E-step over all
+     * components, then eqs. (muk), (sigmak) and omega_k = N_k / N
+     * (eq. omegak-mle), which restores the sample mass, mean and
+     * covariance exactly. */
+    double NkA[OR_MAXK] = {0};
+    for (int64_t p = 0; p < N; ++p) {
+      double lm = log_mix(D, K, cs, vv + p * D, lf);
+      for (int k = 0; k < K; ++k) {
+        gam[p * OR_MAXK + k] = ah[p] * exp(lf[k] - lm);
+        NkA[k] += gam[p * OR_MAXK + k];
+      }
+    }
+    comp fc[OR_MAXK];
+    int Kf = 0, final_pd = 1;
+    for (int k = 0; k < K; ++k) {
+      if (!(NkA[k] > 0.0)) continue; /* a component that owns nothing */
+      comp nc;
+      for (int d = 0; d < D; ++d) {
+        double s = 0.0;
+        for (int64_t p = 0; p < N; ++p) s += gam[p * OR_MAXK + k] * vv[p * D + d];
+        nc.mu[d] = s / NkA[k];
+      }
+      for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) {
+          double s = 0.0;
+          for (int64_t p = 0; p < N; ++p)
+            s += gam[p * OR_MAXK + k] * (vv[p * D + i] - nc.mu[i]) * (vv[p * D + j] - nc.mu[j]);
+          nc.S[i][j] = s / NkA[k];
+        }
+      nc.w = NkA[k] / Nd;
+      if (!chol_floor(D, nc.S, nc.mu, nc.Lc, &nc.logdet)) { o->status |= ST_COV_NOT_PD; final_pd = 0; }
+      fc[Kf++] = nc;
+    }
+    K = Kf;
+    memcpy(cs, fc, sizeof(comp) * (size_t)K);
+    o->lnL = final_pd ? penalised_L(D, K, cs, N, vv, ah) : 0.0;
+  } else {
+    o->lnL = penalised_L(D, K, cs, N, vv, ah);
+  }
+  store_params(D, cfg->Kmax, K, cs, prm_out);
+  o->K = K;
+  o->sweeps = sweep;
+  o->kwork = kwork;
+  free(ah);
+  free(gam);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Shape functions (Sec. 2.4.1): B-splines of the distance in units of dx.  */
+/* ------------------------------------------------------------------------ */
+static double shape_S(int order, double s) {
+  double a = fabs(s);
+  if (order == 0) return a < 0.5 ? 1.0 : 0.0;
+  if (order == 1) return a < 1.0 ? 1.0 - a : 0.0;
+  /* order 2 */
+  if (a <= 0.5) return 0.75 - a * a;
+  if (a < 1.5) return 0.5 * (1.5 - a) * (1.5 - a);
+  return 0.0;
+}
+
+static int64_t wrap(int64_t i, int64_t C) { i %= C; return i < 0 ? i + C : i; }
+
+/* rho_i = (1/dx) sum_p q alpha_p S(x_i - x_p), node i at (i + 1/2) dx on the
+ * periodic mesh; a particle of cell j reaches nodes j-1, j, j+1. */
+static void deposit(const oracle_cfg *cfg, int64_t C, const int64_t *cell_off,
+                    const double *x, const double *alpha, double *rho) {
+  const double dx = cfg->L / (double)C;
+  for (int64_t i = 0; i < C; ++i) rho[i] = 0.0;
+  for (int64_t j = 0; j < C; ++j)
+    for (int64_t p = cell_off[j]; p < cell_off[j + 1]; ++p)
+      for (int64_t i = j - 1; i <= j + 1; ++i) {
+        double xi = ((double)i + 0.5) * dx;
+        rho[wrap(i, C)] += cfg->q * alpha[p] * shape_S(cfg->shape_order, (xi - x[p]) / dx) / dx;
+      }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exported: compression of all cells.                                      */
+/* ------------------------------------------------------------------------ */
+int oracle_compress(const oracle_cfg *cfg, int64_t C, const int64_t *cell_off,
+                    const double *x, const double *v /* [D][Ntot] */, const double *alpha,
+                    int32_t *K_out, double *params_out, double *W_out,
+                    double *rho_target_out, double *lnL_out, int32_t *sweeps_out,
+                    int32_t *kwork_out, uint32_t *status_out, int nthreads) {
+  const int D = cfg->D;
+  if (D != 1 && D != 3) return -1;
+  if (cfg->Kmax < 1 || cfg->Kmax > OR_MAXK) return -1;
+  const int64_t Ntot = cell_off[C];
+  const size_t P = (size_t)P_of(D);
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int64_t j = 0; j < C; ++j) {
+    int64_t n = cell_off[j + 1] - cell_off[j];
+    double *vv = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * D);
+    for (int64_t p = 0; p < n; ++p)
+      for (int d = 0; d < D; ++d) vv[p * D + d] = v[(int64_t)d * Ntot + cell_off[j] + p];
+    cell_out o;
+    em_cell(cfg, j, n, vv, alpha + cell_off[j], params_out + (size_t)j * cfg->Kmax * P, &o,
+            NULL, 0, 0, NULL, NULL, 0, NULL);
+    K_out[j] = o.K; W_out[j] = o.W; lnL_out[j] = o.lnL;
+    if (sweeps_out) sweeps_out[j] = o.sweeps;
+    if (kwork_out) kwork_out[j] = o.kwork;
+    status_out[j] = o.status;
+    free(vv);
+  }
+  /* stored charge density rho' from the original particles (Sec. 2.4.1) */
+  if (rho_target_out) deposit(cfg, C, cell_off, x, alpha, rho_target_out);
+  return 0;
+}
+
+/* Exported: one cell, for tests -- optional supplied initial parameters,
+ * an optional fixed number of penalised sweeps with no final step
+ * (only_sweeps > 0), and the trace of L. */
+int oracle_em_cell(const oracle_cfg *cfg, int64_t cell, int64_t N, const double *vv /*[N][D]*/,
+                   const double *alpha, const double *init_prm, int init_K, int only_sweeps,
+                   double *params_out, int32_t *K_out, double *W_out, double *lnL_out,
+                   int32_t *sweeps_out, uint32_t *status_out, double *Ltrace, int32_t *Ktrace,
+                   int trace_cap, int32_t *ntrace) {
+  cell_out o;
+  int nt = 0;
+  em_cell(cfg, cell, N, vv, alpha, params_out, &o, init_prm, init_K, only_sweeps, Ltrace,
+          Ktrace, trace_cap, &nt);
+  *K_out = o.K; *W_out = o.W; *lnL_out = o.lnL; *sweeps_out = o.sweeps; *status_out = o.status;
+  if (ntrace) *ntrace = nt;
+  return 0;
+}
+
+/* Exported: penalised L of given parameters on one cell (weights already
+ * normalised to sum N), eq. (lnL-GM). */
+double oracle_penalised_L(int D, int K, const double *prm, int64_t N, const double *vv,
+                          const double *ah) {
+  comp cs[OR_MAXK];
+  load_params(D, K, prm, cs);
+  for (int k = 0; k < K; ++k)
+    if (!chol_floor(D, cs[k].S, cs[k].mu, cs[k].Lc, &cs[k].logdet)) return NAN;
+  return penalised_L(D, K, cs, N, vv, ah);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exported: cyclic tridiagonal solve, row i:                               */
+/*   a_i x_{i-1} + b_i x_i + c_i x_{i+1} = d_i,  indices mod n, n >= 3.     */
+/* Thomas elimination on the tridiagonal part plus the Sherman-Morrison     */
+/* correction for the two corner entries (textbook direct solve).           */
+/* ------------------------------------------------------------------------ */
+static void thomas(int64_t n, const double *a, const double *b, const double *c,
+                   const double *d, double *x, double *cp, double *dp) {
+  cp[0] = c[0] / b[0];
+  dp[0] = d[0] / b[0];
+  for (int64_t i = 1; i < n; ++i) {
+    double m = b[i] - a[i] * cp[i - 1];
+    cp[i] = c[i] / m;
+    dp[i] = (d[i] - a[i] * dp[i - 1]) / m;
+  }
+  x[n - 1] = dp[n - 1];
+  for (int64_t i = n - 2; i >= 0; --i) x[i] = dp[i] - cp[i] * x[i + 1];
+}
+
+int oracle_cyclic_tridiag(int64_t n, const double *a, const double *b, const double *c,
+                          const double *d, double *x) {
+  if (n < 3) return -1;
+  double *bb = (double *)malloc(sizeof(double) * n);
+  double *u = (double *)malloc(sizeof(double) * n);
+  double *y = (double *)malloc(sizeof(double) * n);
+  double *z = (double *)malloc(sizeof(double) * n);
+  double *cp = (double *)malloc(sizeof(double) * n);
+  double *dp = (double *)malloc(sizeof(double) * n);
+  /* A = T + u v^T, u = (g, 0..0, c_{n-1}), v = (1, 0..0, a_0/g), g = -b_0 */
+  double g = -b[0];
+  for (int64_t i = 0; i < n; ++i) { bb[i] = b[i]; u[i] = 0.0; }
+  bb[0] = b[0] - g;
+  bb[n - 1] = b[n - 1] - c[n - 1] * a[0] / g;
+  u[0] = g;
+  u[n - 1] = c[n - 1];
+  thomas(n, a, bb, c, d, y, cp, dp);
+  thomas(n, a, bb, c, u, z, cp, dp);
+  double vy = y[0] + a[0] / g * y[n - 1];
+  double vz = z[0] + a[0] / g * z[n - 1];
+  double f = vy / (1.0 + vz);
+  for (int64_t i = 0; i < n; ++i) x[i] = y[i] - f * z[i];
+  free(bb); free(u); free(y); free(z); free(cp); free(dp);
+  return 0;
+}
+
+/* dense Gaussian elimination with partial pivoting, for meshes of 1-2 cells */
+static int dense_solve(int n, double *A, double *b, double *x) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabs(A[r * n + c]) > fabs(A[piv * n + c])) piv = r;
+    if (A[piv * n + c] == 0.0) return -1;
+    if (piv != c) {
+      for (int k = 0; k < n; ++k) { double t = A[c * n + k]; A[c * n + k] = A[piv * n + k]; A[piv * n + k] = t; }
+      double t = b[c]; b[c] = b[piv]; b[piv] = t;
+    }
+    for (int r = c + 1; r < n; ++r) {
+      double f = A[r * n + c] / A[c * n + c];
+      for (int k = c; k < n; ++k) A[r * n + k] -= f * A[c * n + k];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int r = n - 1; r >= 0; --r) {
+    double s = b[r];
+    for (int k = r + 1; k < n; ++k) s -= A[r * n + k] * x[k];
+    x[r] = s / A[r * n + r];
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exported: reconstruction of all cells (Sec. 2.4).                        */
+/* ------------------------------------------------------------------------ */
+int oracle_reconstruct(const oracle_cfg *cfg, int64_t C, const int32_t *K, const double *params,
+                       const double *W, const double *rho_target, const int64_t *out_off,
+                       double *x_out, double *v_out /* [D][Nout] */, double *alpha_out,
+                       uint32_t *status_out, double *dA_out /* [C] or NULL */,
+                       double *v_raw_out /* [D][Nout] or NULL: velocities before projection */,
+                       int nthreads) {
+  const int D = cfg->D;
+  const size_t P = (size_t)P_of(D);
+  const int64_t Nout = out_off[C];
+  const double dx = cfg->L / (double)C;
+  if (D != 1 && D != 3) return -1;
+  for (int64_t j = 0; j < C; ++j) status_out[j] = 0;
+
+  /* 1. Sampling (Sec. 2.4): uniform position in the cell; ancestral
+   *    sampling of the mixture, eq. (mix-dist-1): a component z with
+   *    probability omega_z, then v ~ N(mu_z, Sigma_z) as v = mu + Lc xi
+   *    with xi from Box-Muller; all particles of cell j get alpha = W_j/N'_j. */
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int64_t j = 0; j < C; ++j) {
+    int64_t n = out_off[j + 1] - out_off[j];
+    if (n == 0) continue;
+    comp cs[OR_MAXK];
+    int Kj = K[j];
+    load_params(D, Kj, params + (size_t)j * cfg->Kmax * P, cs);
+    for (int k = 0; k < Kj; ++k) {
+      /* sampling needs only the Cholesky factor, no floor */
+      double ld;
+      memset(cs[k].Lc, 0, sizeof(cs[k].Lc));
+      for (int a = 0; a < D; ++a)
+        for (int b = 0; b <= a; ++b) {
+          double s = cs[k].S[a][b];
+          for (int m = 0; m < b; ++m) s -= cs[k].Lc[a][m] * cs[k].Lc[b][m];
+          if (a == b) cs[k].Lc[a][a] = s > 0.0 ? sqrt(s) : 0.0;
+          else cs[k].Lc[a][b] = cs[k].Lc[b][b] > 0.0 ? s / cs[k].Lc[b][b] : 0.0;
+        }
+      (void)ld;
+    }
+    if (Kj == 0) status_out[j] |= ST_NO_MIXTURE;
+    for (int64_t i = 0; i < n; ++i) {
+      int64_t g = out_off[j] + i;
+      uint32_t r0[4], r1[4], r2[4];
+      philox_draw(cfg->seed, (uint32_t)i, TAG_SAMPLE | 0u, j, r0);
+      philox_draw(cfg->seed, (uint32_t)i, TAG_SAMPLE | 1u, j, r1);
+      double u0 = oracle_uniform52(r0[0], r0[1]);
+      double u1 = oracle_uniform52(r0[2], r0[3]);
+      x_out[g] = ((double)j + u0) * dx;
+      /* categorical draw by the cumulative weights */
+      int z = Kj - 1;
+      double cum = 0.0;
+      for (int k = 0; k < Kj; ++k) {
+        cum += cs[k].w;
+        if (u1 < cum) { z = k; break; }
+      }
+      /* Box-Muller (Box & Muller 1958) on pairs of uniforms */
+      double xi[4];
+      {
+        double ua = oracle_uniform52(r1[0], r1[1]), ub = oracle_uniform52(r1[2], r1[3]);
+        double rr = sqrt(-2.0 * log(ua));
+        xi[0] = rr * cos(2.0 * OR_PI * ub);
+        xi[1] = rr * sin(2.0 * OR_PI * ub);
+      }
+      if (D == 3) {
+        philox_draw(cfg->seed, (uint32_t)i, TAG_SAMPLE | 2u, j, r2);
+        double ua = oracle_uniform52(r2[0], r2[1]), ub = oracle_uniform52(r2[2], r2[3]);
+        double rr = sqrt(-2.0 * log(ua));
+        xi[2] = rr * cos(2.0 * OR_PI * ub);
+        xi[3] = rr * sin(2.0 * OR_PI * ub);
+      }
+      for (int a = 0; a < D; ++a) {
+        double s = 0.0;
+        if (Kj > 0) {
+          s = cs[z].mu[a];
+          for (int b = 0; b <= a; ++b) s += cs[z].Lc[a][b] * xi[b];
+        }
+        v_out[(int64_t)a * Nout + g] = s;
+      }
+      alpha_out[g] = W[j] / (double)n;
+    }
+  }
+  if (v_raw_out) memcpy(v_raw_out, v_out, sizeof(double) * (size_t)D * Nout);
+
+  /* 2. Gauss' law (Sec. 2.4.1): rho from the sampled particles, the mass
+   *    matrix M_ij = sum_p q S0(x_j - x_p) S(x_i - x_p) (column j collects
+   *    the particles of cell j), and the solve M dA = dx (rho' - rho). */
+  double *rho = (double *)malloc(sizeof(double) * C);
+  double *rhs = (double *)malloc(sizeof(double) * C);
+  double *dA = (double *)malloc(sizeof(double) * C);
+  deposit(cfg, C, out_off, x_out, alpha_out, rho);
+  for (int64_t i = 0; i < C; ++i) rhs[i] = dx * (rho_target[i] - rho[i]);
+  if (C >= 3) {
+    double *a = (double *)calloc(C, sizeof(double)); /* M(i, i-1) */
+    double *b = (double *)calloc(C, sizeof(double)); /* M(i, i)   */
+    double *c = (double *)calloc(C, sizeof(double)); /* M(i, i+1) */
+    for (int64_t j = 0; j < C; ++j)
+      for (int64_t p = out_off[j]; p < out_off[j + 1]; ++p)
+        for (int64_t i = j - 1; i <= j + 1; ++i) {
+          double xi = ((double)i + 0.5) * dx;
+          double m = cfg->q * shape_S(cfg->shape_order, (xi - x_out[p]) / dx);
+          int64_t iw = wrap(i, C);
+          if (i == j) b[iw] += m;
+          else if (i == j - 1) c[iw] += m; /* row j-1, column j */
+          else a[iw] += m;                 /* row j+1, column j */
+        }
+    /* Reading: a cell with no resampled particle has an empty column; it
+     * gets a unit diagonal so its (inert) dA_j is defined. */
+    for (int64_t j = 0; j < C; ++j)
+      if (out_off[j + 1] == out_off[j]) {
+        b[j] = 1.0; c[wrap(j - 1, C)] = 0.0; a[wrap(j + 1, C)] = 0.0;
+        status_out[j] |= ST_MM_EMPTY_COL;
+      }
+    oracle_cyclic_tridiag(C, a, b, c, rhs, dA);
+    free(a); free(b); free(c);
+  } else {
+    int n = (int)C;
+    double A[4] = {0, 0, 0, 0}, bb[2], xx[2];
+    for (int64_t j = 0; j < C; ++j)
+      for (int64_t p = out_off[j]; p < out_off[j + 1]; ++p)
+        for (int64_t i = j - 1; i <= j + 1; ++i) {
+          double xi = ((double)i + 0.5) * dx;
+          A[wrap(i, C) * n + j] += cfg->q * shape_S(cfg->shape_order, (xi - x_out[p]) / dx);
+        }
+    for (int64_t j = 0; j < C; ++j)
+      if (out_off[j + 1] == out_off[j]) {
+        for (int r = 0; r < n; ++r) A[r * n + j] = 0.0;
+        A[j * n + j] = 1.0;
+        status_out[j] |= ST_MM_EMPTY_COL;
+      }
+    for (int i = 0; i < n; ++i) bb[i] = rhs[i];
+    dense_solve(n, A, bb, xx);
+    for (int i = 0; i < n; ++i) dA[i] = xx[i];
+  }
+  /* eqs. (p-weight-correction), (new-p-weight): alpha'_p = alpha_p + dA_j */
+  for (int64_t j = 0; j < C; ++j)
+    for (int64_t p = out_off[j]; p < out_off[j + 1]; ++p) {
+      alpha_out[p] += dA[j];
+      if (!(alpha_out[p] > 0.0)) status_out[j] |= ST_NEG_WEIGHT;
+    }
+  if (dA_out) memcpy(dA_out, dA, sizeof(double) * C);
+  free(rho); free(rhs); free(dA);
+
+  /* 3. Lemons projection (Sec. 2.4.2), after the weight correction:
+   *    v' = a (v + beta), with targets p, E from the mixture and
+   *    N' = sum alpha', p' = sum alpha' v, E' = 1/2 sum alpha' |v|^2 (eq. beta),
+   *    a = sqrt((2 E N' - p^2) / (2 E' N' - p'^2)), beta = (p - a p')/(a N')
+   *    (eq. alpha).  A non-positive numerator skips the cell (Sec. 2.4.2:
+   *    "forgo the local moment-matching step"). */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int64_t j = 0; j < C; ++j) {
+    int64_t n = out_off[j + 1] - out_off[j];
+    if (n == 0 || K[j] == 0) continue;
+    comp cs[OR_MAXK];
+    load_params(D, K[j], params + (size_t)j * cfg->Kmax * P, cs);
+    double pt[OR_MAXD] = {0}, Et = 0.0;
+    for (int k = 0; k < K[j]; ++k) {
+      double tr = 0.0, mm = 0.0;
+      for (int a = 0; a < D; ++a) {
+        pt[a] += W[j] * cs[k].w * cs[k].mu[a];
+        tr += cs[k].S[a][a];
+        mm += cs[k].mu[a] * cs[k].mu[a];
+      }
+      Et += 0.5 * W[j] * cs[k].w * (tr + mm);
+    }
+    double Np = 0.0, pp[OR_MAXD] = {0}, Ep = 0.0;
+    for (int64_t p = out_off[j]; p < out_off[j + 1]; ++p) {
+      Np += alpha_out[p];
+      for (int a = 0; a < D; ++a) {
+        double va = v_out[(int64_t)a * Nout + p];
+        pp[a] += alpha_out[p] * va;
+        Ep += 0.5 * alpha_out[p] * va * va;
+      }
+    }
+    double pt2 = 0.0, pp2 = 0.0;
+    for (int a = 0; a < D; ++a) { pt2 += pt[a] * pt[a]; pp2 += pp[a] * pp[a]; }
+    double num = 2.0 * Et * Np - pt2;
+    double den = 2.0 * Ep * Np - pp2;
+    if (!(num > 0.0) || !(den > 0.0) || !(Np > 0.0)) { status_out[j] |= ST_PROJ_SKIPPED; continue; }
+    double aa = sqrt(num / den);
+    double beta[OR_MAXD];
+    for (int a = 0; a < D; ++a) beta[a] = (pt[a] - aa * pp[a]) / (aa * Np);
+    for (int64_t p = out_off[j]; p < out_off[j + 1]; ++p)
+      for (int a = 0; a < D; ++a) {
+        double *va = &v_out[(int64_t)a * Nout + p];
+        *va = aa * (*va + beta[a]);
+      }
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exported: per-cell moments of particles (Sec. 2.3.1 quantities) and the  */
+/* charge density.  W = sum alpha, p = sum alpha v, M2 = sum alpha v v^T    */
+/* (upper triangle row-major), E = 1/2 sum alpha |v|^2.                     */
+/* ------------------------------------------------------------------------ */
+int oracle_moments(const oracle_cfg *cfg, int64_t C, const int64_t *cell_off, const double *x,
+                   const double *v /*[D][Ntot]*/, const double *alpha, double *W, double *p,
+                   double *M2, double *E, double *rho) {
+  const int D = cfg->D;
+  const int64_t Ntot = cell_off[C];
+  const int nm = D * (D + 1) / 2;
+  for (int64_t j = 0; j < C; ++j) {
+    double w = 0.0, pm[OR_MAXD] = {0}, m2[6] = {0}, e = 0.0;
+    for (int64_t q = cell_off[j]; q < cell_off[j + 1]; ++q) {
+      w += alpha[q];
+      int t = 0;
+      for (int a = 0; a < D; ++a) {
+        double va = v[(int64_t)a * Ntot + q];
+        pm[a] += alpha[q] * va;
+        e += 0.5 * alpha[q] * va * va;
+        for (int b = a; b < D; ++b) m2[t++] += alpha[q] * va * v[(int64_t)b * Ntot + q];
+      }
+    }
+    W[j] = w;
+    for (int a = 0; a < D; ++a) p[j * D + a] = pm[a];
+    for (int t = 0; t < nm; ++t) M2[j * nm + t] = m2[t];
+    E[j] = e;
+  }
+  if (rho) deposit(cfg, C, cell_off, x, alpha, rho);
+  return 0;
+}
+
+/* Exported: the same moments of the mixtures: W_j, p = W sum_k w_k mu_k,
+ * M2 = W sum_k w_k (Sigma_k + mu_k mu_k^T), E = tr(M2)/2. */
+int oracle_mixture_moments(const oracle_cfg *cfg, int64_t C, const int32_t *K,
+                           const double *params, const double *Wc, double *W, double *p,
+                           double *M2, double *E) {
+  const int D = cfg->D;
+  const size_t P = (size_t)P_of(D);
+  const int nm = D * (D + 1) / 2;
+  for (int64_t j = 0; j < C; ++j) {
+    comp cs[OR_MAXK];
+    load_params(D, K[j], params + (size_t)j * cfg->Kmax * P, cs);
+    double pm[OR_MAXD] = {0}, m2[6] = {0};
+    for (int k = 0; k < K[j]; ++k) {
+      int t = 0;
+      for (int a = 0; a < D; ++a) {
+        pm[a] += Wc[j] * cs[k].w * cs[k].mu[a];
+        for (int b = a; b < D; ++b)
+          m2[t++] += Wc[j] * cs[k].w * (cs[k].S[a][b] + cs[k].mu[a] * cs[k].mu[b]);
+      }
+    }
+    W[j] = Wc[j];
+    double e = 0.0;
+    int t = 0;
+    for (int a = 0; a < D; ++a) {
+      p[j * D + a] = pm[a];
+      for (int b = a; b < D; ++b) {
+        if (a == b) e += 0.5 * m2[t];
+        M2[j * nm + t] = m2[t];
+        ++t;
+      }
+    }
+    E[j] = e;
+  }
+  return 0;
+}
+
+/* Exported: shape function value, for tests */
+double oracle_shape(int order, double s) { return shape_S(order, s); }
+
+/* Exported: number of OpenMP threads a parallel region would use */
+int oracle_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
