@@ -1,0 +1,418 @@
+#!/usr/bin/env python3
+"""Benchmark of the GM checkpoint-restart hot path on GB300.
+
+One step = compress (adaptive penalised EM + final unpenalised step + target
+charge deposit) and reconstruct (sampling, Gauss'-law weight correction,
+Lemons projection) of one batch of cells.  Metric: particles/s =
+N_in / (t_compress + t_reconstruct), with N' = N_in per cell.
+
+Default workload: 1D-1V batched cells -- 4096 cells with Poisson(2000)
+particles (clipped to 200-8000), each a random mixture of 1-4 drifting
+Maxwellians (drifts U[-0.5, 0.5], vth U[0.02, 0.1], Dirichlet(1) weights),
+FP32 velocities, FP64 weights and positions, Kmax = 8, quadratic B-spline
+shape functions.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gmcr|reference]
+
+Under torchrun every rank fits its own independent batch (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "GM CR particles/s (compress+reconstruct) on GB300, learned-init vs plain EM"
+UNIT = "particles/s"
+WORKLOAD_DESC = ("mixture_1d1v: 4096 cells x Poisson(2000) particles (clip 200-8000), "
+                 "1-4 drifting Maxwellians per cell, FP32 v, FP64 x/alpha, Kmax=8, S2 shape, "
+                 "tol=1e-6, max_sweeps=1000, N'=N per cell")
+L2_BYTES = 126 * 1024 * 1024
+
+
+def rank_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def rank_seed(rank: int) -> int:
+    """Each rank fits an independent batch: its own generator seed."""
+    return workloads.GEN_SEED_BASE + 1 + 1000 * rank
+
+
+def make_workload(name: str, rank: int):
+    if name == "mixture_1d1v":
+        return workloads.mixture_1d1v(seed=rank_seed(rank))
+    if name == "two_stream_1d1v":
+        return workloads.two_stream_1d1v(seed=rank_seed(rank))
+    if name == "bimaxwellian_1d3v":
+        return workloads.bimaxwellian_1d3v(seed=rank_seed(rank))
+    if name == "lognormal_1d3v":
+        return workloads.lognormal_1d3v(seed=rank_seed(rank))
+    raise SystemExit(f"unknown workload {name}")
+
+
+def reduce_max(value: float, dist, device=None) -> float:
+    """Max over ranks (the slowest rank sets the job time)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(value: float, dist, device=None) -> float:
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"gmcr_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work of the EM kernel ("Roofline")
+# ---------------------------------------------------------------------------
+FLOPS_PER_PK = {1: 30, 3: 90}  # FP32 flops per particle per component step
+
+
+def em_flops(counts: np.ndarray, kwork: np.ndarray, D: int) -> float:
+    return float(np.sum(counts.astype(np.float64) * kwork.astype(np.float64))) * FLOPS_PER_PK[D]
+
+
+def fp32_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p))
+    return {}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle, as it stands, on a bounded sample of cells
+# ---------------------------------------------------------------------------
+def sub_workload(wl, ncells: int):
+    ncells = min(ncells, wl.C)
+    n = int(wl.cell_off[ncells])
+    p = dict(wl.params)
+    p["L"] = wl.params["L"] * ncells / wl.C  # same dx
+    return workloads.Workload(wl.name + "_sample", wl.cell_off[: ncells + 1].copy(), wl.x[:n].copy(),
+                              np.ascontiguousarray(wl.v[:, :n]), wl.alpha[:n].copy(), p)
+
+
+def oracle_step(wl, nthreads: int) -> float:
+    import oracle
+    t0 = time.perf_counter()
+    out = oracle.compress(wl.params, wl.cell_off, wl.x, wl.v, wl.alpha, nthreads=nthreads)
+    oracle.reconstruct(wl.params, out["K"], out["params"], out["W"], out["rho_target"], wl.cell_off,
+                       nthreads=nthreads)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(wl, budget_s: float = 15.0) -> dict:
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    ncells = max(cores, 4)
+    sw = sub_workload(wl, ncells)
+    t = oracle_step(sw, cores)
+    # grow the sample toward the budget
+    if t < budget_s / 3:
+        scale = max(1, int(budget_s / max(t, 1e-3) / 1.5))
+        ncells = min(wl.C, ncells * scale)
+        sw = sub_workload(wl, ncells)
+        t = oracle_step(sw, cores)
+    return {"value": sw.ntot / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {sw.C} cells ({sw.ntot} particles) of the workload, "
+                      f"compress+reconstruct, OpenMP over cells, {t:.1f} s"}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank, world, _ = rank_info()
+    if rank != 0:
+        return 0
+    wl = make_workload(args.workload, 0)
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    ncells = max(2 * cores, 8)
+    sw = sub_workload(wl, ncells)
+    for _ in range(args.warmup):
+        oracle_step(sw, cores)
+    times = [oracle_step(sw, cores) for _ in range(args.steps)]
+    tot = sum(times)
+    value = sw.ntot * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC if args.workload == "mixture_1d1v" else args.workload,
+                       "sample_cells": sw.C, "sample_particles": sw.ntot},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"first {sw.C} cells ({sw.ntot} particles) per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def run_gmcr(args):
+    import torch
+    rank, world, local = rank_info()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_
+        dist = dist_
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    device = torch.device("cuda", torch.cuda.current_device())
+    from paper_2007_12273_gb300 import build as gbuild
+    from paper_2007_12273_gb300 import gm
+    gbuild.build()
+    gm.load()
+
+    wl = make_workload(args.workload, rank)
+    D = wl.D
+    cfg = gm.config(wl.params, precision=args.precision)
+    rcfg = gm.config(wl.params, seed_key="recon_seed", precision=args.precision)
+    counts = wl.counts()
+    n = wl.ntot
+    C = wl.C
+
+    # inputs resident in HBM
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+    cell_off, x, v, alpha = t(wl.cell_off), t(wl.x), t(wl.v), t(wl.alpha)
+    out_off = cell_off
+    cout = dict(K=torch.empty(C, dtype=torch.int32, device=device),
+                params=torch.empty((C, cfg.Kmax, gm.P_of(D)), dtype=torch.float64, device=device),
+                W=torch.empty(C, dtype=torch.float64, device=device),
+                rho_target=torch.empty(C, dtype=torch.float64, device=device),
+                lnL=torch.empty(C, dtype=torch.float64, device=device),
+                sweeps=torch.empty(C, dtype=torch.int32, device=device),
+                kwork=torch.empty(C, dtype=torch.int32, device=device),
+                status=torch.empty(C, dtype=torch.int32, device=device))
+    rout = dict(x=torch.empty(n, dtype=torch.float64, device=device),
+                v=torch.empty((D, n), dtype=torch.float64, device=device),
+                alpha=torch.empty(n, dtype=torch.float64, device=device),
+                status=torch.empty(C, dtype=torch.int32, device=device))
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=device)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        gm.gm_compress(cfg, cell_off, x, v, alpha, stream=stream, out=cout)
+        gm.gm_reconstruct(rcfg, cout["K"], cout["params"], cout["W"], cout["rho_target"], out_off,
+                          n_out=n, stream=stream, out=rout)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- device-resident timing: per-step events, L2 flushed between steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e0, e1, e2 = ev[i]
+        e0.record(stream)
+        gm.gm_compress(cfg, cell_off, x, v, alpha, stream=stream, out=cout)
+        e1.record(stream)
+        gm.gm_reconstruct(rcfg, cout["K"], cout["params"], cout["W"], cout["rho_target"], out_off,
+                          n_out=n, stream=stream, out=rout)
+        e2.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    t_comp = [a.elapsed_time(b) for a, b, _ in ev]
+    t_rec = [b.elapsed_time(c) for _, b, c in ev]
+    step_ms_local = sum(t_comp) / args.steps + sum(t_rec) / args.steps
+    step_ms = reduce_max(step_ms_local, dist, device)
+    total_particles = reduce_sum(float(n), dist, device)
+    value = total_particles / (step_ms * 1e-3)
+
+    # ---- end to end through the API with host buffers ----------------------
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_in = [pin(wl.cell_off), pin(wl.x), pin(wl.v), pin(wl.alpha)]
+    d_in = [torch.empty_like(h, device=device) for h in h_in]
+    h_out = {k: torch.empty(tuple(vv.shape), dtype=vv.dtype).pin_memory()
+             for k, vv in list(rout.items()) + [("params", cout["params"]), ("K", cout["K"]),
+                                                ("W", cout["W"]), ("rho_target", cout["rho_target"])]}
+    h2d = sum(h.numel() * h.element_size() for h in h_in)
+    d2h = sum(h.numel() * h.element_size() for h in h_out.values())
+    e2e_steps = max(2, min(args.steps, 5))
+
+    def e2e_step():
+        for h, d in zip(h_in, d_in):
+            d.copy_(h, non_blocking=True)
+        gm.gm_compress(cfg, d_in[0], d_in[1], d_in[2], d_in[3], stream=stream, out=cout)
+        gm.gm_reconstruct(rcfg, cout["K"], cout["params"], cout["W"], cout["rho_target"], d_in[0],
+                          n_out=n, stream=stream, out=rout)
+        for k, h in h_out.items():
+            src = rout[k] if k in rout else cout[k]
+            h.copy_(src, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = reduce_max(e0.elapsed_time(e1) / e2e_steps, dist, device)
+    e2e_value = total_particles / (e2e_ms * 1e-3)
+
+    # ---- statistics of the fit and the roofline of the EM kernel -----------
+    K = cout["K"].cpu().numpy()
+    kwork = cout["kwork"].cpu().numpy()
+    sweeps = cout["sweeps"].cpu().numpy()
+    st = cout["status"].cpu().numpy()
+    rst = rout["status"].cpu().numpy()
+    flops = em_flops(counts, kwork, D)
+    t_em = sum(t_comp) / args.steps * 1e-3
+    achieved = flops / t_em / 1e12
+    peaks = measured_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = fp32_peak_tflops(sm_mhz)
+    P = gm.P_of(D)
+    numbers_per_particle = 1 + D + 1  # x, v, alpha
+    cr = counts.sum() * numbers_per_particle / max(1.0, float(np.sum(K)) * P)
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC if args.workload == "mixture_1d1v" else args.workload,
+                   "cells": C, "particles": n, "D": D, "Kmax": cfg.Kmax, "init": "paper (random)",
+                   "precision": "fp64 m-step" if args.precision == 0 else "fp32 m-step",
+                   "l2": "inputs > L2 and a 252 MB flush between timed steps",
+                   "parallelism": f"replicas x{world} (independent batches)"},
+        "ms_compress": sum(t_comp) / args.steps, "ms_reconstruct": sum(t_rec) / args.steps,
+        "cells_per_s": C * world / (step_ms * 1e-3),
+        "fit": {"Kbar": float(K.mean()), "sweeps_mean": float(sweeps.mean()),
+                "maxsweeps_frac": float(np.mean((st & 1) != 0)),
+                "compression_ratio": cr,
+                "proj_skipped_frac": float(np.mean((rst & 0x100) != 0))},
+        "roofline": {"kernel": "em_kernel (gm_compress)", "bound": "alu", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "note": f"FP32 flops = sum_j N_j * kwork_j * {FLOPS_PER_PK[D]}; peak = 152 SMs "
+                             f"x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (of fallback nominal clock)"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": 7 * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(wl, args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gmcr", choices=["gmcr", "reference"])
+    ap.add_argument("--workload", default="mixture_1d1v")
+    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gmcr(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

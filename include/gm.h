@@ -1,0 +1,159 @@
+/*
+ * gm.h -- C ABI of the GB300 Gaussian-mixture checkpoint-restart library
+ * (method of Chen, Chacon & Nguyen, arXiv 2007.12273).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All array arguments are DEVICE pointers owned by the caller, unless a
+ *    comment says otherwise.  The library never frees or keeps them.
+ *  - Particles are sorted by spatial cell (CSR): the particles of cell j are
+ *    indices cell_off[j] .. cell_off[j+1]-1 (cell_off has C+1 int64 entries,
+ *    cell_off[0] = 0, non-decreasing).  Positions are absolute, in
+ *    [j*dx, (j+1)*dx) for a particle of cell j, with dx = L / C.
+ *  - Velocities are structure-of-arrays: v[d * n + i] is component d of
+ *    particle i, d < D, n the number of particles of that array.
+ *  - The mesh is 1D and periodic: node i sits at (i + 1/2) dx.
+ *  - A component's parameter record (the checkpoint payload, Sec. 1) is
+ *      [ omega, mu_0 .. mu_{D-1}, Sigma upper triangle row-major ]
+ *    P = 1 + D + D(D+1)/2 doubles (3 for D = 1, 10 for D = 3); a cell's
+ *    records are params[(j * Kmax + k) * P + t]; slots k >= K[j] are zero.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ *    default stream).  Return value: GM_OK or a negative GM_ERR_* code;
+ *    gm_last_error() then describes the failure (per host thread).
+ *    Per-cell outcomes that are not errors go in status bits (GM_ST_*).
+ *  - The library keeps one internal device workspace per process (grown on
+ *    demand, freed by gm_shutdown()).  Concurrent calls from several host
+ *    threads or on several streams must be serialised by the caller.
+ */
+#ifndef GMCR_GM_H
+#define GMCR_GM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define GM_OK 0
+#define GM_ERR_ARG (-1)         /* invalid argument; nothing was launched */
+#define GM_ERR_CUDA (-2)        /* a CUDA call or launch failed */
+#define GM_ERR_NOMEM (-3)       /* workspace allocation failed */
+#define GM_ERR_UNSUPPORTED (-4) /* e.g. no sm_103 device */
+
+/* per-cell status bits */
+#define GM_ST_EM_MAXSWEEPS 0x01u  /* EM stopped at max_sweeps, not converged */
+#define GM_ST_COV_NOT_PD 0x02u    /* a covariance failed its Cholesky factorisation */
+#define GM_ST_TOO_FEW 0x04u       /* cell has at most 10 particles (Sec. 1) */
+#define GM_ST_EMPTY 0x08u         /* no particles, or non-positive total weight */
+#define GM_ST_DEGENERATE 0x10u    /* all velocities (numerically) equal */
+#define GM_ST_PROJ_SKIPPED 0x100u /* Lemons numerator <= 0: projection skipped */
+#define GM_ST_NEG_WEIGHT 0x200u   /* a corrected weight alpha' <= 0 */
+#define GM_ST_MM_EMPTY_COL 0x400u /* no resampled particle: unit mass-matrix column */
+#define GM_ST_NO_MIXTURE 0x800u   /* K[j] = 0 but particles were requested */
+
+typedef struct gm_config {
+  int32_t D;           /* velocity dimensions: 1 or 3 */
+  int32_t Kmax;        /* initial components per cell, 1..16 */
+  int32_t shape_order; /* 1 = CIC (linear B-spline), 2 = quadratic B-spline */
+  int32_t max_sweeps;  /* cap on EM sweeps (e.g. 1000) */
+  double tol;          /* EM stops when |L - L_prev| <= tol |L_prev| (e.g. 1e-6) */
+  uint64_t seed;       /* Philox key: initial picks (compress) / sampler (reconstruct) */
+  double L;            /* periodic domain length; dx = L / C */
+  double q;            /* species charge q_p */
+  int32_t threads_per_cell; /* EM CTA size: 0 = library choice, else 128 or 256 */
+  int32_t smem_particles;   /* EM shared-memory tile in particles: 0 = library choice;
+                               cells with more particles use an L2-resident global tile */
+  int32_t precision;        /* 0: FP64 cross-warp statistics and M-step (default);
+                               1: FP32 M-step during the penalised sweeps (the final
+                               unpenalised step stays FP64) */
+  int32_t reserved;         /* must be 0 */
+} gm_config;
+
+/*
+ * gm_compress -- per-cell adaptive Gaussian-mixture fit (Sec. 2.2-2.3).
+ *
+ * For every cell: weights are normalised to sum N (Sec. 2.2); Kmax
+ * components start at randomly chosen particles (Philox key cfg->seed,
+ * counter (draw, 0x494E4954, cell)) with the total covariance; the
+ * component-wise penalised EM (eqs. responsibility, muk, sigmak, omegak)
+ * removes a component when N_k - T/2 <= 0 and stops when the penalised
+ * log-likelihood, eq. (lnL-GM), changes by at most tol (relative) over a
+ * sweep with no removal; a final unpenalised step (eq. omegak-mle,
+ * Sec. 2.3.1) then makes the mixture's mass, mean and covariance equal the
+ * cell's weighted sample moments.  Also deposits the target charge density
+ * rho'_i = (q/dx) sum_p alpha_p S(x_i - x_p) (Sec. 2.4.1).
+ *
+ * In:  cell_off [C+1] int64; x [n] f64; v [D][n] f32 (v_is_f64 = 0) or f64
+ *      (v_is_f64 = 1); alpha [n] f64.  n = n_particles = cell_off[C].
+ * Out: K_out [C] int32; params_out [C][Kmax][P] f64; W_out [C] f64 (sum of
+ *      weights); rho_target_out [C] f64; lnL_out [C] f64 (eq. lnL-GM at the
+ *      final parameters, with the normalised weights); sweeps_out [C] int32;
+ *      kwork_out [C] int32 (component E-steps performed, may be NULL);
+ *      status_out [C] uint32.
+ * E-step densities and responsibilities are FP32; sufficient statistics
+ * are promoted to FP64 at the warp reduction; parameters, Cholesky factors
+ * and the whole final step are FP64.
+ */
+int gm_compress(const gm_config* cfg, int64_t C, int64_t n_particles, const int64_t* cell_off,
+                const double* x, const void* v, int32_t v_is_f64, const double* alpha,
+                int32_t* K_out, double* params_out, double* W_out, double* rho_target_out,
+                double* lnL_out, int32_t* sweeps_out, int32_t* kwork_out, uint32_t* status_out,
+                void* stream);
+
+/*
+ * gm_reconstruct -- resample every cell from its mixture (Sec. 2.4).
+ *
+ * Cell j gets N'_j = out_off[j+1] - out_off[j] particles: position uniform
+ * in the cell; a component z with probability omega_z and v ~ N(mu_z,
+ * Sigma_z) (ancestral sampling, eq. mix-dist-1), Philox key cfg->seed,
+ * counter (i, 0x53000000 | block, cell); weight W_j / N'_j.  Then the
+ * Gauss'-law correction: alpha'_p = alpha_p + dA_j with M dA = dx (rho' -
+ * rho), M_ij = sum_p q S0(x_j - x_p) S(x_i - x_p) (eqs. p-weight-correction,
+ * new-p-weight; solved directly in FP64).  Then the Lemons projection
+ * v' = a (v + beta) restoring the mixture's momentum and energy per cell
+ * (eqs. alpha, beta); a cell whose numerator 2 E N' - p^2 is not positive
+ * keeps its samples and gets GM_ST_PROJ_SKIPPED.
+ *
+ * In:  K [C] int32; params [C][Kmax][P] f64; W [C] f64; rho_target [C] f64;
+ *      out_off [C+1] int64, n_out = out_off[C].
+ * Out: x_out [n_out] f64; v_out [D][n_out] f64; alpha_out [n_out] f64;
+ *      status_out [C] uint32; dA_out [C] f64 (may be NULL).
+ * Box-Muller normals are FP32; everything else is FP64.
+ */
+int gm_reconstruct(const gm_config* cfg, int64_t C, const int32_t* K, const double* params,
+                   const double* W, const double* rho_target, int64_t n_out,
+                   const int64_t* out_off, double* x_out, double* v_out, double* alpha_out,
+                   uint32_t* status_out, double* dA_out, void* stream);
+
+/*
+ * gm_moments -- per-cell particle moments (the quantities of Sec. 2.3.1 and
+ * 2.4.2): W = sum alpha, p = sum alpha v [C][D], M2 = sum alpha v v^T upper
+ * triangle row-major [C][D(D+1)/2], E = (1/2) sum alpha |v|^2, and the
+ * charge density rho [C] with the shape function of cfg (Sec. 2.4.1).
+ * Any output pointer may be NULL.  FP64 accumulation.
+ */
+int gm_moments(const gm_config* cfg, int64_t C, int64_t n_particles, const int64_t* cell_off,
+               const double* x, const void* v, int32_t v_is_f64, const double* alpha, double* W,
+               double* p, double* M2, double* E, double* rho, void* stream);
+
+/*
+ * gm_mixture_moments -- the same moments of each cell's mixture (W given):
+ * p = W sum_k w_k mu_k, M2 = W sum_k w_k (Sigma_k + mu_k mu_k^T),
+ * E = tr(M2)/2 (eq. equal-mean and the variance identity of Sec. 2.3.1).
+ */
+int gm_mixture_moments(const gm_config* cfg, int64_t C, const int32_t* K, const double* params,
+                       const double* Wc, double* W, double* p, double* M2, double* E,
+                       void* stream);
+
+/* Description of the last error on this host thread ("" if none). */
+const char* gm_last_error(void);
+
+/* Frees the internal workspace.  The library stays usable. */
+int gm_shutdown(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GMCR_GM_H */

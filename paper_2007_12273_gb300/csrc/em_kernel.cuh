@@ -1,0 +1,709 @@
+// em_kernel.cuh -- persistent per-cell adaptive EM (compression, Sec. 2.2-2.3)
+//
+// One CTA fits one cell at a time and pulls the next cell from an atomic
+// ticket.  A cell's particles are staged once (whitened FP32 velocities and
+// normalised weights) in shared memory -- or, when the cell is larger than
+// the shared tile, in an L2-resident global scratch with the same layout --
+// and reused by every sweep.
+//
+// Component-wise EM (Sec. 2.3, Celeux et al.): the E-step of component k
+// needs the normaliser s_p = sum_j omega_j f_j(v_p) with the *current*
+// parameters of every component.  s_p is kept per particle (FP32, relative
+// to a per-particle log2 shift m_p): a pass for component k first replaces
+// the previous component's old term by its updated one, then evaluates
+// f_k, the responsibility gamma_pk = alpha_p omega_k f_k / s_p and the
+// per-thread FP32 sufficient statistics of component k about its old mean.
+// Once per sweep an exact pass recomputes s_p and m_p and yields eq.
+// (lnL-GM).  Weights are kept unnormalised (omega_j = u_j / Z), which makes
+// the renormalisation after each component (step 3) implicit.
+//
+// Precision: E-step densities / responsibilities FP32; statistics FP32 per
+// thread and per warp, summed across warps in R (FP64 by default); M-step,
+// Cholesky factors and the annihilation / floor tests in R; the final
+// unpenalised step (Sec. 2.3.1) entirely in FP64 with FP64-normalised
+// responsibilities, which is what makes the moments exact.
+#pragma once
+
+#include "gm_common.cuh"
+
+namespace gmcr {
+
+struct EmParams {
+  int64_t C, n;
+  const int64_t* cell_off;
+  const void* v;
+  const double* alpha;
+  int32_t* K_out;
+  double* params_out;
+  double* W_out;
+  double* lnL_out;
+  int32_t* sweeps_out;
+  int32_t* kwork_out;
+  uint32_t* status_out;
+  float* scratch;  // [(D+4)][n] floats, used by cells larger than the tile
+  unsigned int* queue;
+  int Kmax, max_sweeps, cap;
+  double tol;
+  uint64_t seed;
+};
+
+constexpr float kHalfLog2e = 0.72134752044448170368f;  // log2(e) / 2
+constexpr double kLn2 = 0.69314718055994530942;
+
+template <int D, int NW>
+struct EmCtl {
+  static constexpr int NM = D * (D + 1) / 2;
+  static constexpr int NS = 1 + D + NM;
+  // master parameters in whitened coordinates y = (v - mean) / sc
+  double u[kMaxK];  // unnormalised weights, omega = u / Z
+  double mu[kMaxK][D];
+  double S[kMaxK][NM];  // upper triangle, row-major
+  // FP32 E-step constants: log2(u f) = b - |A (y - mu)|^2
+  float emu[kMaxK][D];
+  float eA[kMaxK][NM];  // lower triangle of sqrt(log2e/2) L^{-1}, row-major
+  float elc[kMaxK];     // -log2|L| - (D/2) log2(2 pi)
+  float eb[kMaxK];      // log2(u) + elc
+  float pmu[D], pA[NM], pb;  // updated constants of the previous component
+  double mean[D], sc[D], isc[D];
+  double Nd, W, Z, L, Lprev, logjac;
+  float redf[NW][NS + 1];
+  double redd[NW][NS + 1];
+  double res[NS + 1];
+  // final step (centered original coordinates)
+  double fw[kMaxK], fmu[kMaxK][D], fS[kMaxK][NM];
+  int64_t cell, off, N;
+  int K, Kf, k, sweep, kwork, annih, done, pstate, degenerate, final_pd;
+  unsigned int status;
+};
+
+// ---------------------------------------------------------------------------
+// small dense helpers (one thread)
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ int tri(int i, int j) {  // upper-triangle index, i <= j
+  return D == 1 ? 0 : (i == 0 ? j : (i == 1 ? 2 + j : 5));
+}
+
+// Cholesky of the upper-triangle S (precision R); returns false if a pivot
+// is not positive or, measured in the original coordinates (pivots scale by
+// sc_i^2), falls under 1e-13 * sum_d (Sigma_dd + mu_d^2).
+template <int D, typename R>
+__device__ bool chol_whitened(const R* S, const R* mu, const double* mean, const double* sc,
+                              R (&Lc)[3][3]) {
+  R scale2 = 0;
+  for (int d = 0; d < D; ++d) {
+    const R m = (R)mean[d] + (R)sc[d] * mu[d];
+    scale2 += (R)(sc[d] * sc[d]) * S[tri<D>(d, d)] + m * m;
+  }
+  const R fl = (R)1e-13 * scale2;
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j <= i; ++j) {
+      R s = S[tri<D>(j, i)];
+      for (int m = 0; m < j; ++m) s -= Lc[i][m] * Lc[j][m];
+      if (i == j) {
+        if (!(s * (R)(sc[i] * sc[i]) > fl) || !(s < (R)1e300)) return false;
+        Lc[i][i] = sqrt(s);
+      } else {
+        Lc[i][j] = s / Lc[j][j];
+      }
+    }
+  return true;
+}
+
+// E-step constants of a component from its Cholesky factor
+template <int D, typename R>
+__device__ void make_econst(const R (&Lc)[3][3], float* eA, float& elc) {
+  const float c = 0.84932180028801904272f;  // sqrt(log2(e) / 2)
+  if (D == 1) {
+    eA[0] = c / (float)Lc[0][0];
+    elc = -log2f((float)Lc[0][0]) - 0.5f * 2.6514961294723187f;  // log2(2 pi) / 2
+  } else {
+    const R i00 = (R)1 / Lc[0][0], i11 = (R)1 / Lc[1][1], i22 = (R)1 / Lc[2][2];
+    const R i10 = -Lc[1][0] * i00 * i11;
+    const R i21 = -Lc[2][1] * i11 * i22;
+    const R i20 = -(Lc[2][0] * i00 + Lc[2][1] * i10) * i22;
+    eA[0] = c * (float)i00;
+    eA[1] = c * (float)i10;
+    eA[2] = c * (float)i11;
+    eA[3] = c * (float)i20;
+    eA[4] = c * (float)i21;
+    eA[5] = c * (float)i22;
+    elc = -log2f((float)Lc[0][0]) - log2f((float)Lc[1][1]) - log2f((float)Lc[2][2]) -
+          1.5f * 2.6514961294723187f;
+  }
+}
+
+// log2(u_k f_k(y)) - shift, with d = y - mu returned
+template <int D>
+__device__ __forceinline__ float lg_eval(const float* mu, const float* A, float b, const float* y,
+                                         float* d) {
+  if (D == 1) {
+    d[0] = y[0] - mu[0];
+    const float t0 = A[0] * d[0];
+    return fmaf(-t0, t0, b);
+  } else {
+    d[0] = y[0] - mu[0];
+    d[1] = y[1] - mu[1];
+    d[2] = y[2] - mu[2];
+    const float t0 = A[0] * d[0];
+    const float t1 = fmaf(A[1], d[0], A[2] * d[1]);
+    const float t2 = fmaf(A[3], d[0], fmaf(A[4], d[1], A[5] * d[2]));
+    return b - fmaf(t0, t0, fmaf(t1, t1, t2 * t2));
+  }
+}
+
+// FP64 block reduction of NV values (NV <= NS + 1); result in c.res
+template <int D, int NT, int NV>
+__device__ __forceinline__ void block_sum_d(EmCtl<D, NT / 32>& c, double (&v)[NV]) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = warp_sum(v[i]);
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) c.redd[w][i] = v[i];
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    for (int q = 0; q < NT / 32; ++q) s += c.redd[q][threadIdx.x];
+    c.res[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// the kernel
+// ---------------------------------------------------------------------------
+template <int D, int NT, typename VT, typename R>
+__global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
+  constexpr int NW = NT / 32;
+  constexpr int NM = D * (D + 1) / 2;
+  constexpr int NS = 1 + D + NM;
+  constexpr int T = D * (D + 3) / 2;
+  constexpr int P = 1 + D + NM;
+  const double halfT = 0.5 * T;
+  __shared__ EmCtl<D, NW> c;
+  extern __shared__ float tile_smem[];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const VT* __restrict__ vin = static_cast<const VT*>(a.v);
+
+  for (;;) {
+    if (tid == 0) {
+      const unsigned int t = atomicAdd(a.queue, 1u);
+      c.cell = (int64_t)t;
+    }
+    __syncthreads();
+    const int64_t j = c.cell;
+    if (j >= a.C) break;
+    const int64_t off = a.cell_off[j];
+    const int64_t N = a.cell_off[j + 1] - off;
+    double* prm_out = a.params_out + (size_t)j * a.Kmax * P;
+
+    if (N == 0) {
+      for (int i = tid; i < a.Kmax * P; i += NT) prm_out[i] = 0.0;
+      if (tid == 0) {
+        a.K_out[j] = 0;
+        a.W_out[j] = 0.0;
+        a.lnL_out[j] = 0.0;
+        if (a.sweeps_out) a.sweeps_out[j] = 0;
+        if (a.kwork_out) a.kwork_out[j] = 0;
+        a.status_out[j] = GM_ST_EMPTY;
+      }
+      __syncthreads();
+      continue;
+    }
+
+    // ---- total weight and weighted mean (FP64) ---------------------------
+    {
+      double acc[1 + D];
+#pragma unroll
+      for (int i = 0; i <= D; ++i) acc[i] = 0.0;
+      for (int64_t p = tid; p < N; p += NT) {
+        const double al = a.alpha[off + p];
+        acc[0] += al;
+#pragma unroll
+        for (int d = 0; d < D; ++d) acc[1 + d] += al * (double)vin[(int64_t)d * a.n + off + p];
+      }
+      block_sum_d<D, NT, 1 + D>(c, acc);
+      if (tid == 0) {
+        c.W = c.res[0];
+        c.Nd = (double)N;
+        for (int d = 0; d < D; ++d) c.mean[d] = c.res[1 + d] / c.res[0];
+      }
+      __syncthreads();
+    }
+    if (!(c.W > 0.0)) {
+      for (int i = tid; i < a.Kmax * P; i += NT) prm_out[i] = 0.0;
+      if (tid == 0) {
+        a.K_out[j] = 0;
+        a.W_out[j] = c.W;
+        a.lnL_out[j] = 0.0;
+        if (a.sweeps_out) a.sweeps_out[j] = 0;
+        if (a.kwork_out) a.kwork_out[j] = 0;
+        a.status_out[j] = GM_ST_EMPTY | GM_ST_DEGENERATE;
+      }
+      __syncthreads();
+      continue;
+    }
+    // ---- total covariance (two-pass, FP64) --------------------------------
+    {
+      double acc[NM];
+#pragma unroll
+      for (int i = 0; i < NM; ++i) acc[i] = 0.0;
+      for (int64_t p = tid; p < N; p += NT) {
+        const double al = a.alpha[off + p];
+        double dv[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) dv[d] = (double)vin[(int64_t)d * a.n + off + p] - c.mean[d];
+        int t = 0;
+#pragma unroll
+        for (int x = 0; x < D; ++x)
+#pragma unroll
+          for (int y = x; y < D; ++y) acc[t++] += al * dv[x] * dv[y];
+      }
+      block_sum_d<D, NT, NM>(c, acc);
+      if (tid == 0) {
+        double cov[NM];
+        for (int i = 0; i < NM; ++i) cov[i] = c.res[i] / c.W;
+        c.status = (N <= 10) ? GM_ST_TOO_FEW : 0u;
+        // degenerate cell: the total covariance fails the Cholesky floor
+        // 1e-13 * sum_d (cov_dd + mean_d^2)
+        {
+          double scale2 = 0.0;
+          for (int d = 0; d < D; ++d) scale2 += cov[tri<D>(d, d)] + c.mean[d] * c.mean[d];
+          const double fl = 1e-13 * scale2;
+          bool ok = true;
+          double L2[3][3] = {{0}};
+          for (int x = 0; x < D && ok; ++x)
+            for (int y = 0; y <= x && ok; ++y) {
+              double s = cov[tri<D>(y, x)];
+              for (int m = 0; m < y; ++m) s -= L2[x][m] * L2[y][m];
+              if (x == y) {
+                if (!(s > fl) || !(s < 1e300)) ok = false;
+                else L2[x][x] = sqrt(s);
+              } else {
+                L2[x][y] = s / L2[y][y];
+              }
+            }
+          c.degenerate = ok ? 0 : 1;
+        }
+        if (c.degenerate) {
+          c.fw[0] = 1.0;
+          for (int d = 0; d < D; ++d) c.fmu[0][d] = 0.0;
+          for (int i = 0; i < NM; ++i) c.fS[0][i] = cov[i];
+        } else {
+          c.logjac = 0.0;
+          for (int d = 0; d < D; ++d) {
+            c.sc[d] = sqrt(cov[tri<D>(d, d)]);
+            c.isc[d] = 1.0 / c.sc[d];
+            c.logjac += log(c.sc[d]);
+          }
+          // whitened total covariance (correlation matrix) for the init
+          for (int x = 0; x < D; ++x)
+            for (int y = x; y < D; ++y)
+              c.S[0][tri<D>(x, y)] = (x == y) ? 1.0 : cov[tri<D>(x, y)] * c.isc[x] * c.isc[y];
+        }
+      }
+      __syncthreads();
+    }
+    if (c.degenerate) {
+      for (int i = tid; i < a.Kmax * P; i += NT) prm_out[i] = 0.0;
+      __syncthreads();
+      if (tid == 0) {
+        prm_out[0] = 1.0;
+        for (int d = 0; d < D; ++d) prm_out[1 + d] = c.mean[d];
+        for (int i = 0; i < NM; ++i) prm_out[1 + D + i] = c.fS[0][i];
+        a.K_out[j] = 1;
+        a.W_out[j] = c.W;
+        a.lnL_out[j] = 0.0;
+        if (a.sweeps_out) a.sweeps_out[j] = 0;
+        if (a.kwork_out) a.kwork_out[j] = 0;
+        a.status_out[j] = c.status | GM_ST_DEGENERATE | GM_ST_COV_NOT_PD;
+      }
+      __syncthreads();
+      continue;
+    }
+
+    // ---- stage whitened velocities and normalised weights ----------------
+    float* tb;
+    int64_t st;
+    if (N <= a.cap) {
+      tb = tile_smem;
+      st = a.cap;
+    } else {
+      tb = a.scratch + off;
+      st = a.n;
+    }
+    float* Y = tb;
+    float* AH = tb + D * st;
+    float* SS = tb + (D + 1) * st;
+    float* MM = tb + (D + 2) * st;
+    float* GG = tb + (D + 3) * st;
+    {
+      const double nw = c.Nd / c.W;
+      for (int64_t p = tid; p < N; p += NT) {
+#pragma unroll
+        for (int d = 0; d < D; ++d)
+          Y[d * st + p] = (float)(((double)vin[(int64_t)d * a.n + off + p] - c.mean[d]) * c.isc[d]);
+        AH[p] = (float)(a.alpha[off + p] * nw);
+      }
+    }
+    // ---- initialisation (Sec. 2.3): Kmax components at random particles --
+    if (tid == 0) {
+      int K = a.Kmax < N ? a.Kmax : (int)N;
+      while (K > 1 && c.Nd - halfT * K <= 0.0) --K;
+      int64_t picks[kMaxK];
+      int got = 0;
+      for (uint32_t t = 0; got < K; ++t) {
+        int64_t idx;
+        if (t < 100000u) {
+          const u32x4 r = philox_draw(a.seed, t, kTagInit, j);
+          const double uu = uniform52(r.x, r.y);
+          idx = (int64_t)floor(uu * c.Nd);
+          if (idx >= N) idx = N - 1;
+        } else {
+          idx = 0;
+          for (;;) {
+            bool used = false;
+            for (int m = 0; m < got; ++m) used |= (picks[m] == idx);
+            if (!used) break;
+            ++idx;
+          }
+        }
+        bool dup = false;
+        for (int m = 0; m < got; ++m) dup |= (picks[m] == idx);
+        if (!dup) picks[got++] = idx;
+      }
+      c.K = K;
+      c.Z = 1.0;
+      R Lc[3][3];
+      R S0[NM], m0[D];
+      for (int i = 0; i < NM; ++i) S0[i] = (R)c.S[0][i];
+      for (int d = 0; d < D; ++d) m0[d] = 0;
+      chol_whitened<D, R>(S0, m0, c.mean, c.sc, Lc);  // the total covariance passed above
+      float eA[NM], elc;
+      make_econst<D, R>(Lc, eA, elc);
+      double Stot[NM];
+      for (int i = 0; i < NM; ++i) Stot[i] = c.S[0][i];
+      for (int k = 0; k < K; ++k) {
+        c.u[k] = 1.0 / K;
+        for (int d = 0; d < D; ++d) {
+          c.mu[k][d] = ((double)vin[(int64_t)d * a.n + off + picks[k]] - c.mean[d]) * c.isc[d];
+          c.emu[k][d] = (float)c.mu[k][d];
+        }
+        for (int i = 0; i < NM; ++i) {
+          c.S[k][i] = Stot[i];
+          c.eA[k][i] = eA[i];
+        }
+        c.elc[k] = elc;
+        c.eb[k] = log2f((float)c.u[k]) + elc;
+      }
+      c.sweep = 0;
+      c.kwork = 0;
+      c.done = 0;
+    }
+    __syncthreads();
+
+    // ---- exact pass: s_p, m_p and eq. (lnL-GM) ----------------------------
+    auto resync = [&]() {
+      const int K = c.K;
+      float acc = 0.0f;
+      for (int64_t p = tid; p < N; p += NT) {
+        float y[D], d[D];
+#pragma unroll
+        for (int q = 0; q < D; ++q) y[q] = Y[q * st + p];
+        float m = -3.0e38f, s = 0.0f;
+        for (int k = 0; k < K; ++k) {
+          const float l = lg_eval<D>(c.emu[k], c.eA[k], c.eb[k], y, d);
+          const float t = ex2(-fabsf(l - m));
+          s = (l > m) ? fmaf(s, t, 1.0f) : s + t;
+          m = fmaxf(m, l);
+        }
+        SS[p] = s;
+        MM[p] = m;
+        acc = fmaf(AH[p], m + lg2(s), acc);
+      }
+      double v1[1] = {(double)acc};
+      block_sum_d<D, NT, 1>(c, v1);
+      if (tid == 0) {
+        double pen = 0.0;
+        for (int k = 0; k < K; ++k) pen += log(c.u[k] / c.Z);
+        const double dpar = (double)K * (T + 1) - 1.0;
+        c.L = c.res[0] * kLn2 - c.Nd * c.logjac - 0.5 * dpar * log(c.Nd) - 0.5 * T * pen;
+      }
+      __syncthreads();
+    };
+
+    resync();
+    if (tid == 0) c.Lprev = c.L;
+    __syncthreads();
+
+    // ---- sweeps -----------------------------------------------------------
+    for (int sweep = 1; sweep <= a.max_sweeps; ++sweep) {
+      if (tid == 0) {
+        c.k = 0;
+        c.annih = 0;
+        c.pstate = 0;
+      }
+      __syncthreads();
+      while (c.k < c.K) {
+        const int k = c.k;
+        // E constants of component k and of the previous component's update
+        float kmu[D], kA[NM], pmu[D], pA[NM];
+#pragma unroll
+        for (int q = 0; q < D; ++q) { kmu[q] = c.emu[k][q]; pmu[q] = c.pmu[q]; }
+#pragma unroll
+        for (int q = 0; q < NM; ++q) { kA[q] = c.eA[k][q]; pA[q] = c.pA[q]; }
+        const float kb = c.eb[k], pb = c.pb;
+        const int ps = c.pstate;
+        float acc[NS];
+#pragma unroll
+        for (int q = 0; q < NS; ++q) acc[q] = 0.0f;
+        for (int64_t p = tid; p < N; p += NT) {
+          float y[D], d[D];
+#pragma unroll
+          for (int q = 0; q < D; ++q) y[q] = Y[q * st + p];
+          const float m = MM[p];
+          float s = SS[p];
+          if (ps == 1) {  // previous component updated
+            const float gn = ex2(fminf(lg_eval<D>(pmu, pA, pb, y, d) - m, 100.0f));
+            s = fmaxf(s - GG[p] + gn, gn);
+          } else if (ps == 2) {  // previous component removed
+            s = s - GG[p];
+          }
+          const float g = ex2(fminf(lg_eval<D>(kmu, kA, kb, y, d) - m, 100.0f));
+          GG[p] = g;
+          SS[p] = s;
+          const float den = fmaxf(fmaxf(s, g), 1e-30f);
+          const float gam = AH[p] * __fdividef(g, den);
+          acc[0] += gam;
+          int t = 1 + D;
+#pragma unroll
+          for (int x = 0; x < D; ++x) {
+            const float gd = gam * d[x];
+            acc[1 + x] += gd;
+#pragma unroll
+            for (int yy = x; yy < D; ++yy, ++t) acc[t] = fmaf(gd, d[yy], acc[t]);
+          }
+        }
+        // warp (FP32) then cross-warp (precision R) reduction
+#pragma unroll
+        for (int q = 0; q < NS; ++q) acc[q] = warp_sum(acc[q]);
+        if (lane == 0)
+#pragma unroll
+          for (int q = 0; q < NS; ++q) c.redf[wid][q] = acc[q];
+        __syncthreads();
+        if (tid < 32) {
+          R stat = 0;
+          if (lane < NS)
+            for (int q = 0; q < NW; ++q) stat += (R)c.redf[q][lane];
+          // thread 0 gathers the NS sums of its warp
+          R sv[NS];
+#pragma unroll
+          for (int q = 0; q < NS; ++q) sv[q] = __shfl_sync(0xffffffffu, stat, q);
+          if (lane == 0) {
+            // ---- M-step for component k (eqs. muk, sigmak, omegak) --------
+            c.kwork++;
+            const int K = c.K;
+            const R Nk = sv[0];
+            bool removed = false;
+            if (K > 1 && (double)Nk - halfT <= 0.0) {
+              removed = true;
+            } else {
+              const R rN = (R)1 / Nk;
+              R dl[D], mun[D], Sn[NM];
+              for (int x = 0; x < D; ++x) {
+                dl[x] = sv[1 + x] * rN;
+                mun[x] = (R)c.mu[k][x] + dl[x];
+              }
+              int t = 0;
+              for (int x = 0; x < D; ++x)
+                for (int yy = x; yy < D; ++yy, ++t) Sn[t] = sv[1 + D + t] * rN - dl[x] * dl[yy];
+              R Lc[3][3];
+              if (!chol_whitened<D, R>(Sn, mun, c.mean, c.sc, Lc)) {
+                c.status |= GM_ST_COV_NOT_PD;
+                if (K > 1) {
+                  removed = true;
+                } else {
+                  c.pstate = 0;  // a lone component keeps its parameters
+                  c.k = k + 1;
+                }
+              } else {
+                const double wn = (K == 1) ? 1.0 : ((double)Nk - halfT) / (c.Nd - halfT * K);
+                const double un = wn * c.Z;
+                c.Z = c.Z - c.u[k] + un;
+                c.u[k] = un;
+                float eA[NM], elc;
+                make_econst<D, R>(Lc, eA, elc);
+                for (int x = 0; x < D; ++x) {
+                  c.mu[k][x] = (double)mun[x];
+                  c.emu[k][x] = (float)mun[x];
+                  c.pmu[x] = (float)mun[x];
+                }
+                for (int q = 0; q < NM; ++q) {
+                  c.S[k][q] = (double)Sn[q];
+                  c.eA[k][q] = eA[q];
+                  c.pA[q] = eA[q];
+                }
+                c.elc[k] = elc;
+                c.eb[k] = log2f((float)un) + elc;
+                c.pb = c.eb[k];
+                c.pstate = 1;
+                c.k = k + 1;
+              }
+            }
+            if (removed) {
+              c.Z -= c.u[k];
+              for (int m = k; m < K - 1; ++m) {
+                c.u[m] = c.u[m + 1];
+                for (int x = 0; x < D; ++x) { c.mu[m][x] = c.mu[m + 1][x]; c.emu[m][x] = c.emu[m + 1][x]; }
+                for (int q = 0; q < NM; ++q) { c.S[m][q] = c.S[m + 1][q]; c.eA[m][q] = c.eA[m + 1][q]; }
+                c.elc[m] = c.elc[m + 1];
+                c.eb[m] = c.eb[m + 1];
+              }
+              c.K = K - 1;
+              c.annih = 1;
+              c.pstate = 2;
+            }
+          }
+        }
+        __syncthreads();
+      }
+      // normalise the weights, then the exact pass and the convergence test
+      if (tid < c.K) {
+        const double un = c.u[tid] / c.Z;
+        c.eb[tid] = log2f((float)un) + c.elc[tid];
+      }
+      __syncthreads();
+      if (tid == 0) {
+        for (int k = 0; k < c.K; ++k) c.u[k] /= c.Z;
+        c.Z = 1.0;
+      }
+      __syncthreads();
+      resync();
+      if (tid == 0) {
+        c.sweep = sweep;
+        if (!c.annih && fabs(c.L - c.Lprev) <= a.tol * fabs(c.Lprev)) c.done = 1;
+        c.Lprev = c.L;
+      }
+      __syncthreads();
+      if (c.done) break;
+    }
+    if (tid == 0 && !c.done) c.status |= GM_ST_EM_MAXSWEEPS;
+
+    // ---- final unpenalised step (Sec. 2.3.1), FP64 -------------------------
+    if (tid == 0) c.Kf = 0;
+    __syncthreads();
+    {
+      const int K = c.K;
+      const double nw = c.Nd / c.W;
+      for (int k = 0; k < K; ++k) {
+        double ck[D];
+#pragma unroll
+        for (int q = 0; q < D; ++q) ck[q] = c.mu[k][q] * c.sc[q];
+        double acc[NS];
+#pragma unroll
+        for (int q = 0; q < NS; ++q) acc[q] = 0.0;
+        for (int64_t p = tid; p < N; p += NT) {
+          float y[D], d[D];
+#pragma unroll
+          for (int q = 0; q < D; ++q) y[q] = Y[q * st + p];
+          float m = -3.0e38f;
+          for (int jj = 0; jj < K; ++jj) m = fmaxf(m, lg_eval<D>(c.emu[jj], c.eA[jj], c.eb[jj], y, d));
+          double Ssum = 0.0, gk = 0.0;
+          for (int jj = 0; jj < K; ++jj) {
+            const double g = (double)ex2(lg_eval<D>(c.emu[jj], c.eA[jj], c.eb[jj], y, d) - m);
+            Ssum += g;
+            if (jj == k) gk = g;
+          }
+          const double gam = a.alpha[off + p] * nw * gk / Ssum;
+          double dv[D];
+#pragma unroll
+          for (int q = 0; q < D; ++q) dv[q] = ((double)vin[(int64_t)q * a.n + off + p] - c.mean[q]) - ck[q];
+          acc[0] += gam;
+          int t = 1 + D;
+#pragma unroll
+          for (int x = 0; x < D; ++x) {
+            const double gd = gam * dv[x];
+            acc[1 + x] += gd;
+#pragma unroll
+            for (int yy = x; yy < D; ++yy, ++t) acc[t] += gd * dv[yy];
+          }
+        }
+        block_sum_d<D, NT, NS>(c, acc);
+        if (tid == 0 && c.res[0] > 0.0) {
+          const int f = c.Kf;
+          const double n = c.res[0];
+          double dl[D];
+          for (int x = 0; x < D; ++x) {
+            dl[x] = c.res[1 + x] / n;
+            c.fmu[f][x] = ck[x] + dl[x];
+          }
+          int t = 0;
+          for (int x = 0; x < D; ++x)
+            for (int yy = x; yy < D; ++yy, ++t) c.fS[f][t] = c.res[1 + D + t] / n - dl[x] * dl[yy];
+          c.fw[f] = n / c.Nd;
+          c.Kf = f + 1;
+        }
+        __syncthreads();
+      }
+    }
+    // ---- final parameters: E constants, Cholesky floor, eq. (lnL-GM) -----
+    if (tid == 0) {
+      const int Kf = c.Kf;
+      int pd = 1;
+      double one[D];
+      for (int d = 0; d < D; ++d) one[d] = 1.0;
+      for (int k = 0; k < Kf; ++k) {
+        // floor test in the original coordinates
+        double So[NM], mo[D], Lo[3][3];
+        for (int q = 0; q < NM; ++q) So[q] = c.fS[k][q];
+        for (int d = 0; d < D; ++d) mo[d] = 0.0;
+        double meano[D];
+        for (int d = 0; d < D; ++d) meano[d] = c.mean[d] + c.fmu[k][d];
+        if (!chol_whitened<D, double>(So, mo, meano, one, Lo)) pd = 0;
+        // whitened copy for the likelihood pass
+        double Sw[NM], mw[D], Lw[3][3];
+        for (int x = 0; x < D; ++x) {
+          mw[x] = c.fmu[k][x] * c.isc[x];
+          for (int yy = x; yy < D; ++yy) Sw[tri<D>(x, yy)] = c.fS[k][tri<D>(x, yy)] * c.isc[x] * c.isc[yy];
+        }
+        if (chol_whitened<D, double>(Sw, mw, c.mean, c.sc, Lw)) {
+          float eA[NM], elc;
+          make_econst<D, double>(Lw, eA, elc);
+          for (int q = 0; q < NM; ++q) c.eA[k][q] = eA[q];
+          c.elc[k] = elc;
+        } else {
+          pd = 0;
+        }
+        for (int x = 0; x < D; ++x) c.emu[k][x] = (float)mw[x];
+        c.eb[k] = log2f((float)c.fw[k]) + c.elc[k];
+        c.u[k] = c.fw[k];
+      }
+      if (!pd) c.status |= GM_ST_COV_NOT_PD;
+      c.final_pd = pd;
+      c.K = Kf;
+      c.Z = 1.0;
+    }
+    __syncthreads();
+    if (c.final_pd) resync();
+    if (tid == 0) {
+      const int Kf = c.K;
+      for (int k = 0; k < Kf; ++k) {
+        double* r = prm_out + (size_t)k * P;
+        r[0] = c.fw[k];
+        for (int d = 0; d < D; ++d) r[1 + d] = c.mean[d] + c.fmu[k][d];
+        for (int q = 0; q < NM; ++q) r[1 + D + q] = c.fS[k][q];
+      }
+      for (int i = Kf * P; i < a.Kmax * P; ++i) prm_out[i] = 0.0;
+      a.K_out[j] = Kf;
+      a.W_out[j] = c.W;
+      a.lnL_out[j] = c.final_pd ? c.L : 0.0;
+      if (a.sweeps_out) a.sweeps_out[j] = c.sweep;
+      if (a.kwork_out) a.kwork_out[j] = c.kwork;
+      a.status_out[j] = c.status;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace gmcr

@@ -1,0 +1,256 @@
+// gm_api.cu -- the C ABI (include/gm.h): argument checks, the internal
+// workspace, launch configuration and error reporting.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "gm_kernels.cuh"
+
+namespace gmcr {
+int em_blocks_per_sm_d1(int nt, int fp64_mstep, int v_f64, size_t smem);
+int em_blocks_per_sm_d3(int nt, int fp64_mstep, int v_f64, size_t smem);
+}  // namespace gmcr
+
+namespace {
+
+thread_local std::string g_err;
+std::mutex g_ws_mu;
+void* g_ws = nullptr;
+size_t g_ws_bytes = 0;
+int g_ws_dev = -1;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(GM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// the kernels are built for sm_103a only
+int check_device(int* sm_count) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  int major = 0, minor = 0, sms = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (major != 10 || minor != 3)
+    return fail(GM_ERR_UNSUPPORTED, "device %d has compute capability %d.%d; this library is built for sm_103a",
+                dev, major, minor);
+  if (sm_count) *sm_count = sms;
+  return GM_OK;
+}
+
+// grows the single workspace; the old buffer is released with cudaFree,
+// which waits for work that may still use it
+int ws_get(size_t bytes, void** out) {
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (g_ws && (bytes > g_ws_bytes || dev != g_ws_dev)) {
+    int cur = dev;
+    cudaSetDevice(g_ws_dev);
+    cudaFree(g_ws);
+    cudaSetDevice(cur);
+    g_ws = nullptr;
+    g_ws_bytes = 0;
+  }
+  if (!g_ws) {
+    const size_t want = bytes + bytes / 4 + 4096;
+    cudaError_t e = cudaMalloc(&g_ws, want);
+    if (e != cudaSuccess) {
+      g_ws = nullptr;
+      return fail(GM_ERR_NOMEM, "workspace of %zu bytes: %s", want, cudaGetErrorString(e));
+    }
+    g_ws_bytes = want;
+    g_ws_dev = dev;
+  }
+  *out = g_ws;
+  return GM_OK;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+int check_cfg(const gm_config* cfg) {
+  if (!cfg) return fail(GM_ERR_ARG, "cfg is NULL");
+  if (cfg->D != 1 && cfg->D != 3) return fail(GM_ERR_ARG, "D must be 1 or 3 (got %d)", cfg->D);
+  if (cfg->Kmax < 1 || cfg->Kmax > gmcr::kMaxK)
+    return fail(GM_ERR_ARG, "Kmax must be in 1..%d (got %d)", gmcr::kMaxK, cfg->Kmax);
+  if (cfg->shape_order != 1 && cfg->shape_order != 2)
+    return fail(GM_ERR_ARG, "shape_order must be 1 or 2 (got %d)", cfg->shape_order);
+  if (!(cfg->L > 0.0)) return fail(GM_ERR_ARG, "L must be positive");
+  return GM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gm_last_error(void) { return g_err.c_str(); }
+
+int gm_shutdown(void) {
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  if (g_ws) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(g_ws_dev);
+    cudaFree(g_ws);
+    cudaSetDevice(cur);
+  }
+  g_ws = nullptr;
+  g_ws_bytes = 0;
+  g_ws_dev = -1;
+  return GM_OK;
+}
+
+int gm_compress(const gm_config* cfg, int64_t C, int64_t n_particles, const int64_t* cell_off,
+                const double* x, const void* v, int32_t v_is_f64, const double* alpha,
+                int32_t* K_out, double* params_out, double* W_out, double* rho_target_out,
+                double* lnL_out, int32_t* sweeps_out, int32_t* kwork_out, uint32_t* status_out,
+                void* stream) {
+  g_err.clear();
+  int rc = check_cfg(cfg);
+  if (rc) return rc;
+  if (C < 0 || C >= (int64_t)1 << 31) return fail(GM_ERR_ARG, "C out of range (%lld)", (long long)C);
+  if (n_particles < 0) return fail(GM_ERR_ARG, "n_particles < 0");
+  if (cfg->max_sweeps < 1) return fail(GM_ERR_ARG, "max_sweeps must be >= 1");
+  if (!(cfg->tol >= 0.0)) return fail(GM_ERR_ARG, "tol must be >= 0");
+  if (C == 0) return GM_OK;
+  if (!cell_off || !x || !v || !alpha || !K_out || !params_out || !W_out || !rho_target_out ||
+      !lnL_out || !status_out)
+    return fail(GM_ERR_ARG, "a required pointer is NULL");
+  int sms = 0;
+  if ((rc = check_device(&sms))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int D = cfg->D;
+  int nt = cfg->threads_per_cell > 0 ? cfg->threads_per_cell : 256;
+  if (nt != 128 && nt != 256) return fail(GM_ERR_ARG, "threads_per_cell must be 128 or 256");
+  int cap = cfg->smem_particles > 0 ? cfg->smem_particles : (D == 1 ? 2560 : 4096);
+  const size_t smem = (size_t)cap * (D + 4) * sizeof(float);
+  if (smem > 200 * 1024) return fail(GM_ERR_ARG, "smem_particles too large (%d)", cap);
+  const int fp64_mstep = (cfg->precision == 0) ? 1 : 0;
+
+  const size_t q_bytes = 256, part_bytes = align256((size_t)3 * C * sizeof(double));
+  const size_t scr_bytes = align256((size_t)n_particles * (D + 4) * sizeof(float));
+  void* ws = nullptr;
+  if ((rc = ws_get(q_bytes + part_bytes + scr_bytes, &ws))) return rc;
+  char* wb = (char*)ws;
+  unsigned int* queue = (unsigned int*)wb;
+  double* part = (double*)(wb + q_bytes);
+  float* scratch = (float*)(wb + q_bytes + part_bytes);
+
+  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  gmcr::EmParams p;
+  p.C = C;
+  p.n = n_particles;
+  p.cell_off = cell_off;
+  p.v = v;
+  p.alpha = alpha;
+  p.K_out = K_out;
+  p.params_out = params_out;
+  p.W_out = W_out;
+  p.lnL_out = lnL_out;
+  p.sweeps_out = sweeps_out;
+  p.kwork_out = kwork_out;
+  p.status_out = status_out;
+  p.scratch = scratch;
+  p.queue = queue;
+  p.Kmax = cfg->Kmax;
+  p.max_sweeps = cfg->max_sweeps;
+  p.cap = cap;
+  p.tol = cfg->tol;
+  p.seed = cfg->seed;
+  const int per_sm = D == 1 ? gmcr::em_blocks_per_sm_d1(nt, fp64_mstep, v_is_f64, smem)
+                            : gmcr::em_blocks_per_sm_d3(nt, fp64_mstep, v_is_f64, smem);
+  if (per_sm < 1) return fail(GM_ERR_CUDA, "EM kernel does not fit on an SM (smem %zu)", smem);
+  int64_t grid = (int64_t)per_sm * sms;
+  if (grid > C) grid = C;
+  e = D == 1 ? gmcr::launch_em1(p, nt, fp64_mstep, v_is_f64, smem, (int)grid, s)
+             : gmcr::launch_em3(p, nt, fp64_mstep, v_is_f64, smem, (int)grid, s);
+  if (e != cudaSuccess) return cuda_fail(e, "EM kernel launch");
+  e = gmcr::launch_deposit(C, cell_off, x, alpha, cfg->L / (double)C, cfg->q, cfg->shape_order,
+                           part, rho_target_out, s);
+  if (e != cudaSuccess) return cuda_fail(e, "deposit launch");
+  return GM_OK;
+}
+
+int gm_reconstruct(const gm_config* cfg, int64_t C, const int32_t* K, const double* params,
+                   const double* W, const double* rho_target, int64_t n_out,
+                   const int64_t* out_off, double* x_out, double* v_out, double* alpha_out,
+                   uint32_t* status_out, double* dA_out, void* stream) {
+  g_err.clear();
+  int rc = check_cfg(cfg);
+  if (rc) return rc;
+  if (C < 0) return fail(GM_ERR_ARG, "C < 0");
+  if (n_out < 0 || n_out >= (int64_t)1 << 40) return fail(GM_ERR_ARG, "n_out out of range");
+  if (C == 0) return GM_OK;
+  if (!K || !params || !W || !rho_target || !out_off || !status_out)
+    return fail(GM_ERR_ARG, "a required pointer is NULL");
+  if (n_out > 0 && (!x_out || !v_out || !alpha_out))
+    return fail(GM_ERR_ARG, "an output particle pointer is NULL");
+  if ((rc = check_device(nullptr))) return rc;
+  void* ws = nullptr;
+  if ((rc = ws_get(gmcr::reconstruct_ws_bytes(cfg->D, C), &ws))) return rc;
+  cudaError_t e = gmcr::launch_reconstruct(cfg->D, C, cfg->Kmax, K, params, W, rho_target, n_out,
+                                           out_off, cfg->seed, cfg->L / (double)C, cfg->q,
+                                           cfg->shape_order, x_out, v_out, alpha_out, status_out,
+                                           dA_out, ws, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "reconstruct launch");
+  return GM_OK;
+}
+
+int gm_moments(const gm_config* cfg, int64_t C, int64_t n_particles, const int64_t* cell_off,
+               const double* x, const void* v, int32_t v_is_f64, const double* alpha, double* W,
+               double* p, double* M2, double* E, double* rho, void* stream) {
+  g_err.clear();
+  int rc = check_cfg(cfg);
+  if (rc) return rc;
+  if (C < 0 || n_particles < 0) return fail(GM_ERR_ARG, "negative size");
+  if (C == 0) return GM_OK;
+  if (!cell_off || !alpha || (!v && (p || M2 || E)) || (!x && rho))
+    return fail(GM_ERR_ARG, "a required pointer is NULL");
+  if ((rc = check_device(nullptr))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (W || p || M2 || E) {
+    e = gmcr::launch_moments(cfg->D, C, n_particles, cell_off, v, v_is_f64, alpha, W, p, M2, E, s);
+    if (e != cudaSuccess) return cuda_fail(e, "moments launch");
+  }
+  if (rho) {
+    void* ws = nullptr;
+    if ((rc = ws_get(align256((size_t)3 * C * sizeof(double)), &ws))) return rc;
+    e = gmcr::launch_deposit(C, cell_off, x, alpha, cfg->L / (double)C, cfg->q, cfg->shape_order,
+                             (double*)ws, rho, s);
+    if (e != cudaSuccess) return cuda_fail(e, "deposit launch");
+  }
+  return GM_OK;
+}
+
+int gm_mixture_moments(const gm_config* cfg, int64_t C, const int32_t* K, const double* params,
+                       const double* Wc, double* W, double* p, double* M2, double* E,
+                       void* stream) {
+  g_err.clear();
+  int rc = check_cfg(cfg);
+  if (rc) return rc;
+  if (C < 0) return fail(GM_ERR_ARG, "C < 0");
+  if (C == 0) return GM_OK;
+  if (!K || !params || !Wc) return fail(GM_ERR_ARG, "a required pointer is NULL");
+  if ((rc = check_device(nullptr))) return rc;
+  cudaError_t e = gmcr::launch_mixture_moments(cfg->D, C, cfg->Kmax, K, params, Wc, W, p, M2, E,
+                                               (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "mixture moments launch");
+  return GM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,106 @@
+// gm_common.cuh -- shared device helpers of the GB300 GM checkpoint-restart
+// kernels: the Philox4x32-10 generator, the 52-bit uniform map, warp
+// reductions and the per-cell status bits.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gm.h"
+
+namespace gmcr {
+
+constexpr int kMaxK = 16;
+constexpr int kWarp = 32;
+
+__host__ __device__ constexpr int T_of(int D) { return D * (D + 3) / 2; }         // App. A
+__host__ __device__ constexpr int P_of(int D) { return 1 + D + D * (D + 1) / 2; }  // record size
+__host__ __device__ constexpr int NM_of(int D) { return D * (D + 1) / 2; }         // covariance entries
+
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds, each two
+// 32x32 -> 64-bit products of counter words with the round multipliers,
+// an xor/permute with the key, and the key advanced by the Weyl increments
+// between rounds.
+struct u32x4 {
+  uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = u32x4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// uniform in (0,1): the 52 leading bits m of (hi, lo), u = (m + 1/2) 2^-52
+__device__ __forceinline__ double uniform52(uint32_t hi, uint32_t lo) {
+  const uint64_t m = ((uint64_t)hi << 20) | (uint64_t)(lo >> 12);
+  return __dmul_rn(__dadd_rn((double)m, 0.5), 2.220446049250313080847263336181640625e-16);
+}
+
+constexpr uint32_t kTagInit = 0x494E4954u;
+constexpr uint32_t kTagSample = 0x53000000u;
+
+__device__ __forceinline__ u32x4 philox_draw(uint64_t seed, uint32_t c0, uint32_t c1, int64_t cell) {
+  return philox4x32_10(u32x4{c0, c1, (uint32_t)((uint64_t)cell), (uint32_t)((uint64_t)cell >> 32)},
+                       (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// hardware base-2 exponential / logarithm (PTX ex2.approx / lg2.approx,
+// relative error about 2^-22)
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float lg2(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Shape-function weights of a particle at fractional cell position
+// xi in [0,1) on the nodes j-1, j, j+1 (B-splines of order 1 or 2 centred
+// on the nodes at (i + 1/2) dx).
+__device__ __forceinline__ void shape3(int order, double xi, double& wm, double& w0, double& wp) {
+  const double s = xi - 0.5;
+  if (order == 1) {
+    wm = s < 0.0 ? -s : 0.0;
+    wp = s > 0.0 ? s : 0.0;
+    w0 = 1.0 - (s < 0.0 ? -s : s);
+  } else {
+    const double a = 0.5 - s, b = 0.5 + s;
+    wm = 0.5 * a * a;
+    wp = 0.5 * b * b;
+    w0 = 0.75 - s * s;
+  }
+}
+
+// fractional position of x inside cell j (clamped to [0,1))
+__device__ __forceinline__ double cell_frac(double x, int64_t j, double inv_dx) {
+  double xi = x * inv_dx - (double)j;
+  xi = xi < 0.0 ? 0.0 : xi;
+  return xi < 1.0 ? xi : 0.99999999999999989;
+}
+
+}  // namespace gmcr

@@ -1,0 +1,36 @@
+// gm_kernels.cuh -- launchers shared between the translation units of the
+// library (kernels live in gm_em*.cu, gm_moments.cu, gm_reconstruct.cu).
+#pragma once
+
+#include "gm_common.cuh"
+#include "em_kernel.cuh"
+
+namespace gmcr {
+
+// EM (compression); returns the launch error
+cudaError_t launch_em1(const EmParams& p, int nt, int fp64_mstep, int v_f64, size_t smem, int grid,
+                       cudaStream_t s);
+cudaError_t launch_em3(const EmParams& p, int nt, int fp64_mstep, int v_f64, size_t smem, int grid,
+                       cudaStream_t s);
+// CTAs of an EM kernel that fit on one SM with `smem` dynamic bytes
+int em_blocks_per_sm(int D, int nt, int fp64_mstep, int v_f64, size_t smem);
+
+cudaError_t launch_deposit(int64_t C, const int64_t* cell_off, const double* x,
+                           const double* alpha, double dx, double q, int order, double* part,
+                           double* rho, cudaStream_t s);
+cudaError_t launch_moments(int D, int64_t C, int64_t n, const int64_t* cell_off, const void* v,
+                           int v_f64, const double* alpha, double* W, double* p, double* M2,
+                           double* E, cudaStream_t s);
+cudaError_t launch_mixture_moments(int D, int64_t C, int Kmax, const int32_t* K, const double* prm,
+                                   const double* Wc, double* W, double* p, double* M2, double* E,
+                                   cudaStream_t s);
+
+int solve_blocks(int64_t C);
+size_t reconstruct_ws_bytes(int D, int64_t C);
+cudaError_t launch_reconstruct(int D, int64_t C, int Kmax, const int32_t* K, const double* prm,
+                               const double* W, const double* rho_target, int64_t n_out,
+                               const int64_t* out_off, uint64_t seed, double dx, double q,
+                               int order, double* x_out, double* v_out, double* alpha_out,
+                               uint32_t* status_out, double* dA_user, void* ws, cudaStream_t s);
+
+}  // namespace gmcr

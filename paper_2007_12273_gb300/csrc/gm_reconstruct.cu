@@ -1,0 +1,457 @@
+// gm_reconstruct.cu -- particle reconstruction (Sec. 2.4): ancestral
+// sampling, the Gauss'-law mass-matrix weight correction and the Lemons
+// moment-matching projection.
+//
+// The sampler is counter-based, so a particle can be regenerated
+// bit-identically from (seed, cell, index).  The pipeline therefore never
+// writes unprojected particles: pass 1 regenerates every particle to
+// accumulate the per-cell mass-matrix column and the velocity sums, a small
+// FP64 solve gives dA, and pass 2 regenerates the particles once more and
+// writes the final positions, projected velocities and corrected weights.
+// HBM traffic is the output alone: 8 (x) + 8 D (v) + 8 (alpha) bytes per
+// particle.
+#include "gm_kernels.cuh"
+
+namespace gmcr {
+
+template <int D>
+struct RecCell {
+  static constexpr int NM = D * (D + 1) / 2;
+  double cw[kMaxK];         // cumulative weights, summed in component order
+  double mu[kMaxK][D];
+  double Lc[kMaxK][NM];     // lower-triangular Cholesky factor, row-major
+  double u[D];              // mixture mean sum_k w_k mu_k
+  double theta;             // sum_k w_k (tr Sigma_k + |mu_k - u|^2)
+  double a, beta[D], alpha_new;
+  int K;
+  int skip;
+  unsigned int status;
+};
+
+// load cell j's mixture: Cholesky factors (no floor; a non-positive pivot
+// gives a zero column, as for a degenerate stored covariance)
+template <int D>
+__device__ void load_cell(RecCell<D>& rc, int64_t j, int Kmax, const int32_t* K,
+                          const double* prm) {
+  constexpr int NM = D * (D + 1) / 2;
+  constexpr int P = 1 + D + NM;
+  const int Kj = K[j];
+  const int k = threadIdx.x;
+  if (k < Kj) {
+    const double* r = prm + ((size_t)j * Kmax + k) * P;
+    for (int d = 0; d < D; ++d) rc.mu[k][d] = r[1 + d];
+    if (D == 1) {
+      const double s = r[2];
+      rc.Lc[k][0] = s > 0.0 ? sqrt(s) : 0.0;
+    } else {
+      // S upper: [s00 s01 s02 s11 s12 s22]
+      const double s00 = r[4], s01 = r[5], s02 = r[6], s11 = r[7], s12 = r[8], s22 = r[9];
+      const double l00 = s00 > 0.0 ? sqrt(s00) : 0.0;
+      const double l10 = l00 > 0.0 ? s01 / l00 : 0.0;
+      const double l20 = l00 > 0.0 ? s02 / l00 : 0.0;
+      const double t11 = s11 - l10 * l10;
+      const double l11 = t11 > 0.0 ? sqrt(t11) : 0.0;
+      const double l21 = l11 > 0.0 ? (s12 - l20 * l10) / l11 : 0.0;
+      const double t22 = s22 - l20 * l20 - l21 * l21;
+      const double l22 = t22 > 0.0 ? sqrt(t22) : 0.0;
+      rc.Lc[k][0] = l00; rc.Lc[k][1] = l10; rc.Lc[k][2] = l11;
+      rc.Lc[k][3] = l20; rc.Lc[k][4] = l21; rc.Lc[k][5] = l22;
+    }
+  }
+  if (threadIdx.x == 0) {
+    rc.K = Kj;
+    double cum = 0.0, u[D], th = 0.0;
+    for (int d = 0; d < D; ++d) u[d] = 0.0;
+    for (int q = 0; q < Kj; ++q) {
+      const double* r = prm + ((size_t)j * Kmax + q) * P;
+      cum += r[0];
+      rc.cw[q] = cum;
+      for (int d = 0; d < D; ++d) u[d] += r[0] * r[1 + d];
+    }
+    for (int q = 0; q < Kj; ++q) {
+      const double* r = prm + ((size_t)j * Kmax + q) * P;
+      double tr = 0.0, dd = 0.0;
+      int t = 1 + D;
+      for (int x = 0; x < D; ++x)
+        for (int y = x; y < D; ++y, ++t) {
+          if (x == y) tr += r[t];
+        }
+      for (int d = 0; d < D; ++d) dd += (r[1 + d] - u[d]) * (r[1 + d] - u[d]);
+      th += r[0] * (tr + dd);
+    }
+    for (int d = 0; d < D; ++d) rc.u[d] = u[d];
+    rc.theta = th;
+  }
+}
+
+// particle i of cell j: position and velocity (Sec. 2.4, eq. mix-dist-1)
+template <int D>
+__device__ __forceinline__ void sample_particle(const RecCell<D>& rc, int64_t j, int64_t i,
+                                                uint64_t seed, double dx, double& x,
+                                                double (&v)[D]) {
+  const u32x4 r0 = philox_draw(seed, (uint32_t)i, kTagSample | 0u, j);
+  const double u0 = uniform52(r0.x, r0.y);
+  const double u1 = uniform52(r0.z, r0.w);
+  x = __dmul_rn(__dadd_rn((double)j, u0), dx);
+  const int K = rc.K;
+  int z = K - 1;
+  for (int k = 0; k < K; ++k)
+    if (u1 < rc.cw[k]) { z = k; break; }
+  // Box-Muller (Box & Muller 1958) on (u2, u3) [and (u4, u5) for D = 3]
+  float xi[3];
+  {
+    const u32x4 r1 = philox_draw(seed, (uint32_t)i, kTagSample | 1u, j);
+    const float ua = (float)uniform52(r1.x, r1.y), ub = (float)uniform52(r1.z, r1.w);
+    const float rr = sqrtf(-2.0f * logf(ua));
+    float sn, cs;
+    sincospif(2.0f * ub, &sn, &cs);
+    xi[0] = rr * cs;
+    if (D == 3) xi[1] = rr * sn;
+  }
+  if (D == 3) {
+    const u32x4 r2 = philox_draw(seed, (uint32_t)i, kTagSample | 2u, j);
+    const float ua = (float)uniform52(r2.x, r2.y), ub = (float)uniform52(r2.z, r2.w);
+    const float rr = sqrtf(-2.0f * logf(ua));
+    xi[2] = rr * cospif(2.0f * ub);
+  }
+  if (K == 0) {
+    for (int d = 0; d < D; ++d) v[d] = 0.0;
+    return;
+  }
+  if (D == 1) {
+    v[0] = __fma_rn(rc.Lc[z][0], (double)xi[0], rc.mu[z][0]);
+  } else {
+    const double* L = rc.Lc[z];
+    const double x0 = xi[0], x1 = xi[1], x2 = xi[2];
+    v[0] = __fma_rn(L[0], x0, rc.mu[z][0]);
+    v[1] = __fma_rn(L[2], x1, __fma_rn(L[1], x0, rc.mu[z][1]));
+    v[2] = __fma_rn(L[5], x2, __fma_rn(L[4], x1, __fma_rn(L[3], x0, rc.mu[z][2])));
+  }
+}
+
+template <int NT, int NV>
+__device__ __forceinline__ void rblock_sum_to0(double (&v)[NV], double (*red)[NV]) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = warp_sum(v[i]);
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) red[w][i] = v[i];
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int q = 1; q < NT / 32; ++q)
+#pragma unroll
+      for (int i = 0; i < NV; ++i) v[i] += red[q][i];
+}
+
+// Pass 1: per cell, the unit-weight shape sums of the resampled particles
+// on nodes j-1, j, j+1 (column j of M / q) and sum w, sum |w|^2 with
+// w = v - u.  cstat[j] = [c-, c0, c+, sum w (D), sum |w|^2].
+template <int D, int NT>
+__global__ void __launch_bounds__(NT) recon_stats_kernel(int64_t C, int Kmax, const int32_t* K,
+                                                         const double* prm, const int64_t* out_off,
+                                                         uint64_t seed, double dx, int order,
+                                                         double* cstat) {
+  constexpr int NV = 3 + D + 1;
+  __shared__ RecCell<D> rc;
+  __shared__ double red[NT / 32][NV];
+  const double inv_dx = 1.0 / dx;
+  for (int64_t j = blockIdx.x; j < C; j += gridDim.x) {
+    load_cell<D>(rc, j, Kmax, K, prm);
+    __syncthreads();
+    const int64_t o = out_off[j], n = out_off[j + 1] - o;
+    double acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += NT) {
+      double x, v[D];
+      sample_particle<D>(rc, j, i, seed, dx, x, v);
+      double wm, w0, wp;
+      shape3(order, cell_frac(x, j, inv_dx), wm, w0, wp);
+      acc[0] += wm;
+      acc[1] += w0;
+      acc[2] += wp;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const double w = v[d] - rc.u[d];
+        acc[3 + d] += w;
+        acc[3 + D] += w * w;
+      }
+    }
+    rblock_sum_to0<NT, NV>(acc, red);
+    if (threadIdx.x == 0)
+      for (int i = 0; i < NV; ++i) cstat[(size_t)j * NV + i] = acc[i];
+    __syncthreads();
+  }
+}
+
+// Mass matrix rows (eq. below new-p-weight): row i couples dA_{i-1}, dA_i,
+// dA_{i+1}; M(i,j) = q * (shape sum of cell j's particles on node i).
+// rhs_i = dx (rho'_i - rho_i), rho_i dx = q sum_j alpha_j (shape sum).
+template <int D>
+__global__ void assemble_kernel(int64_t C, const double* cstat, const double* W,
+                                const int64_t* out_off, const double* rho_target, double dx,
+                                double q, double* A, double* B, double* Cc, double* Dd) {
+  constexpr int NV = 3 + D + 1;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < C;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t im = (i == 0) ? C - 1 : i - 1;
+    const int64_t ip = (i == C - 1) ? 0 : i + 1;
+    const int64_t nm = out_off[im + 1] - out_off[im];
+    const int64_t n0 = out_off[i + 1] - out_off[i];
+    const int64_t np = out_off[ip + 1] - out_off[ip];
+    const double am = nm > 0 ? W[im] / (double)nm : 0.0;
+    const double a0 = n0 > 0 ? W[i] / (double)n0 : 0.0;
+    const double ap = np > 0 ? W[ip] / (double)np : 0.0;
+    const double cm = cstat[(size_t)im * NV + 2];  // cell i-1 on node i
+    const double c0 = cstat[(size_t)i * NV + 1];
+    const double cp = cstat[(size_t)ip * NV + 0];  // cell i+1 on node i
+    A[i] = q * cm;
+    B[i] = n0 > 0 ? q * c0 : 1.0;  // empty column: unit diagonal
+    Cc[i] = q * cp;
+    Dd[i] = dx * rho_target[i] - q * (am * cm + a0 * c0 + ap * cp);
+  }
+}
+
+// Sequential cyclic tridiagonal solve (Thomas elimination and a rank-one
+// Sherman-Morrison correction for the corners), one thread, n >= 3.
+// Row r: a_r x_{r-1} + b_r x_r + c_r x_{r+1} = d_r (indices mod n).
+__device__ void cyclic_thomas_seq(int64_t n, const double* a, const double* b, const double* c,
+                                  const double* d, double* x, double* cp, double* y, double* z) {
+  const double g = -b[0];
+  const double corner = a[0] / g;
+  // forward elimination with two right-hand sides: d and u = (g, 0..0, c_{n-1})
+  double bb = b[0] - g;
+  double r = 1.0 / bb;
+  cp[0] = c[0] * r;
+  y[0] = d[0] * r;
+  z[0] = g * r;
+  for (int64_t i = 1; i < n; ++i) {
+    double bi = b[i];
+    if (i == n - 1) bi -= c[n - 1] * corner;
+    const double m = bi - a[i] * cp[i - 1];
+    r = 1.0 / m;
+    cp[i] = c[i] * r;
+    const double ui = (i == n - 1) ? c[n - 1] : 0.0;
+    y[i] = (d[i] - a[i] * y[i - 1]) * r;
+    z[i] = (ui - a[i] * z[i - 1]) * r;
+  }
+  for (int64_t i = n - 2; i >= 0; --i) {
+    y[i] -= cp[i] * y[i + 1];
+    z[i] -= cp[i] * z[i + 1];
+  }
+  const double vy = y[0] + corner * y[n - 1];
+  const double vz = z[0] + corner * z[n - 1];
+  const double f = vy / (1.0 + vz);
+  for (int64_t i = 0; i < n; ++i) x[i] = y[i] - f * z[i];
+}
+
+// Mass-matrix solve M dA = rhs on one CTA.
+// n <= 2: dense; n < 64: sequential; otherwise a partition method: P blocks
+// of contiguous rows, each thread eliminates its block with three
+// right-hand sides (rhs, the coupling to the previous block's last unknown,
+// the coupling to the next block's first unknown); the 2P interface
+// unknowns satisfy a cyclic tridiagonal system (after the row combinations
+// that eliminate the outer coupling of each block's first / last equation)
+// solved by one thread; the blocks then reconstruct their interiors.
+struct SolveWs {
+  double *y, *v, *w, *cp;      // [n]
+  double *ra, *rb, *rc, *rd;   // [2P]
+  double *rz, *rcp, *ry, *rzz; // [2P]
+};
+
+__global__ void __launch_bounds__(1024) mass_solve_kernel(int64_t n, const double* a,
+                                                          const double* b, const double* c,
+                                                          const double* d, double* x, SolveWs ws,
+                                                          int P) {
+  const int t = threadIdx.x;
+  if (n <= 2) {
+    if (t == 0) {
+      if (n == 1) {
+        x[0] = d[0] / (a[0] + b[0] + c[0]);
+      } else {
+        // rows: b0 x0 + (a0 + c0) x1 = d0 ; (a1 + c1) x0 + b1 x1 = d1
+        const double m00 = b[0], m01 = a[0] + c[0], m10 = a[1] + c[1], m11 = b[1];
+        const double det = m00 * m11 - m01 * m10;
+        x[0] = (d[0] * m11 - m01 * d[1]) / det;
+        x[1] = (m00 * d[1] - m10 * d[0]) / det;
+      }
+    }
+    return;
+  }
+  if (n < 64 || P < 2) {
+    if (t == 0) cyclic_thomas_seq(n, a, b, c, d, x, ws.cp, ws.y, ws.v);
+    return;
+  }
+  if (t < P) {
+    const int64_t r0 = (int64_t)t * n / P, r1 = (int64_t)(t + 1) * n / P;
+    // forward: local tridiagonal (no outer couplings), three rhs
+    double r = 1.0 / b[r0];
+    ws.cp[r0] = c[r0] * r;
+    ws.y[r0] = d[r0] * r;
+    ws.v[r0] = a[r0] * r;
+    ws.w[r0] = (r1 - 1 == r0) ? c[r0] * r : 0.0;
+    for (int64_t i = r0 + 1; i < r1; ++i) {
+      const double m = b[i] - a[i] * ws.cp[i - 1];
+      r = 1.0 / m;
+      ws.cp[i] = c[i] * r;
+      ws.y[i] = (d[i] - a[i] * ws.y[i - 1]) * r;
+      ws.v[i] = (-a[i] * ws.v[i - 1]) * r;
+      ws.w[i] = ((i == r1 - 1 ? c[i] : 0.0) - a[i] * ws.w[i - 1]) * r;
+    }
+    for (int64_t i = r1 - 2; i >= r0; --i) {
+      ws.y[i] -= ws.cp[i] * ws.y[i + 1];
+      ws.v[i] -= ws.cp[i] * ws.v[i + 1];
+      ws.w[i] -= ws.cp[i] * ws.w[i + 1];
+    }
+    const double yF = ws.y[r0], vF = ws.v[r0], wF = ws.w[r0];
+    const double yL = ws.y[r1 - 1], vL = ws.v[r1 - 1], wL = ws.w[r1 - 1];
+    // interface rows: 2t (eliminates X_{t+1}^F), 2t+1 (eliminates X_{t-1}^L)
+    ws.ra[2 * t] = wL * vF - wF * vL;
+    ws.rb[2 * t] = wL;
+    ws.rc[2 * t] = -wF;
+    ws.rd[2 * t] = wL * yF - wF * yL;
+    ws.ra[2 * t + 1] = vL;
+    ws.rb[2 * t + 1] = -vF;
+    ws.rc[2 * t + 1] = vL * wF - vF * wL;
+    ws.rd[2 * t + 1] = vL * yF - vF * yL;
+  }
+  __syncthreads();
+  if (t == 0) cyclic_thomas_seq(2 * P, ws.ra, ws.rb, ws.rc, ws.rd, ws.rz, ws.rcp, ws.ry, ws.rzz);
+  __syncthreads();
+  if (t < P) {
+    const int64_t r0 = (int64_t)t * n / P, r1 = (int64_t)(t + 1) * n / P;
+    const double Xl = ws.rz[(2 * t - 1 + 2 * P) % (2 * P)];  // last unknown of block t-1
+    const double Xf = ws.rz[(2 * t + 2) % (2 * P)];          // first unknown of block t+1
+    for (int64_t i = r0; i < r1; ++i) x[i] = ws.y[i] - ws.v[i] * Xl - ws.w[i] * Xf;
+  }
+}
+
+// Pass 2: Lemons projection coefficients and the final particles.
+template <int D, int NT>
+__global__ void __launch_bounds__(NT) recon_emit_kernel(
+    int64_t C, int Kmax, const int32_t* K, const double* prm, const double* W,
+    const int64_t* out_off, const double* cstat, const double* dA, uint64_t seed, double dx,
+    int64_t n_out, double* x_out, double* v_out, double* alpha_out, uint32_t* status_out) {
+  constexpr int NV = 3 + D + 1;
+  __shared__ RecCell<D> rc;
+  for (int64_t j = blockIdx.x; j < C; j += gridDim.x) {
+    load_cell<D>(rc, j, Kmax, K, prm);
+    __syncthreads();
+    const int64_t o = out_off[j], n = out_off[j + 1] - o;
+    if (threadIdx.x == 0) {
+      unsigned int st = 0;
+      if (n == 0) st |= GM_ST_MM_EMPTY_COL;
+      const double Wj = W[j];
+      const double an = (n > 0 ? Wj / (double)n : 0.0) + dA[j];
+      rc.alpha_new = an;
+      if (n > 0 && !(an > 0.0)) st |= GM_ST_NEG_WEIGHT;
+      rc.skip = 1;
+      rc.a = 1.0;
+      for (int d = 0; d < D; ++d) rc.beta[d] = 0.0;
+      if (n > 0 && rc.K == 0) st |= GM_ST_NO_MIXTURE;
+      if (n > 0 && rc.K > 0) {
+        // eqs. (alpha), (beta) in the frame of the mixture mean u:
+        // 2 E N' - p^2 = W (N' theta + (N' - W) |u|^2),
+        // 2 E' N' - p'^2 = alpha'^2 (n sum|w|^2 - |sum w|^2)
+        const double* cs = cstat + (size_t)j * NV;
+        const double Np = (double)n * an;
+        double u2 = 0.0, sw2 = 0.0;
+        for (int d = 0; d < D; ++d) {
+          u2 += rc.u[d] * rc.u[d];
+          sw2 += cs[3 + d] * cs[3 + d];
+        }
+        const double num = Wj * (Np * rc.theta + (Np - Wj) * u2);
+        const double den = an * an * ((double)n * cs[3 + D] - sw2);
+        if (num > 0.0 && den > 0.0 && Np > 0.0) {
+          const double aa = sqrt(num / den);
+          rc.a = aa;
+          for (int d = 0; d < D; ++d) rc.beta[d] = ((Wj - Np) * rc.u[d] - aa * an * cs[3 + d]) / (aa * Np);
+          rc.skip = 0;
+        } else {
+          st |= GM_ST_PROJ_SKIPPED;
+        }
+      }
+      rc.status = st;
+      status_out[j] = st;
+    }
+    __syncthreads();
+    const double aa = rc.a, an = rc.alpha_new;
+    const int skip = rc.skip;
+    for (int64_t i = threadIdx.x; i < n; i += NT) {
+      double x, v[D];
+      sample_particle<D>(rc, j, i, seed, dx, x, v);
+      x_out[o + i] = x;
+      alpha_out[o + i] = an;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const double vp = skip ? v[d] : rc.u[d] + aa * ((v[d] - rc.u[d]) + rc.beta[d]);
+        v_out[(int64_t)d * n_out + o + i] = vp;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+size_t reconstruct_ws_bytes(int D, int64_t C) {
+  const int P = solve_blocks(C);
+  const size_t per_cell = (size_t)(3 + D + 1) + 4 /*a b c d*/ + 1 /*dA*/ + 4 /*y v w cp*/;
+  return (per_cell * (size_t)C + 8 * (size_t)(2 * P + 2)) * sizeof(double) + 1024;
+}
+
+int solve_blocks(int64_t C) {
+  if (C < 64) return 1;
+  int P = (int)sqrt((double)C / 2.0);
+  if (P > 1024) P = 1024;
+  if (P < 2) P = 2;
+  return P;
+}
+
+cudaError_t launch_reconstruct(int D, int64_t C, int Kmax, const int32_t* K, const double* prm,
+                               const double* W, const double* rho_target, int64_t n_out,
+                               const int64_t* out_off, uint64_t seed, double dx, double q,
+                               int order, double* x_out, double* v_out, double* alpha_out,
+                               uint32_t* status_out, double* dA_user, void* ws, cudaStream_t s) {
+  if (C == 0) return cudaSuccess;
+  const int NVm = 3 + D + 1;
+  const int P = solve_blocks(C);
+  double* base = (double*)ws;
+  double* cstat = base;
+  double* A = cstat + (size_t)NVm * C;
+  double* B = A + C;
+  double* Cc = B + C;
+  double* Dd = Cc + C;
+  double* dA = Dd + C;
+  SolveWs sw;
+  sw.y = dA + C;
+  sw.v = sw.y + C;
+  sw.w = sw.v + C;
+  sw.cp = sw.w + C;
+  double* r = sw.cp + C;
+  const int64_t R2 = 2 * (int64_t)P + 2;
+  sw.ra = r; sw.rb = r + R2; sw.rc = r + 2 * R2; sw.rd = r + 3 * R2;
+  sw.rz = r + 4 * R2; sw.rcp = r + 5 * R2; sw.ry = r + 6 * R2; sw.rzz = r + 7 * R2;
+  if (dA_user) dA = dA_user;
+
+  const int g = (int)(C < 152 * 32 ? C : 152 * 32);
+  if (D == 1)
+    recon_stats_kernel<1, 128><<<g, 128, 0, s>>>(C, Kmax, K, prm, out_off, seed, dx, order, cstat);
+  else
+    recon_stats_kernel<3, 128><<<g, 128, 0, s>>>(C, Kmax, K, prm, out_off, seed, dx, order, cstat);
+  const int ga = (int)((C + 255) / 256 < 4096 ? (C + 255) / 256 : 4096);
+  if (D == 1)
+    assemble_kernel<1><<<ga, 256, 0, s>>>(C, cstat, W, out_off, rho_target, dx, q, A, B, Cc, Dd);
+  else
+    assemble_kernel<3><<<ga, 256, 0, s>>>(C, cstat, W, out_off, rho_target, dx, q, A, B, Cc, Dd);
+  mass_solve_kernel<<<1, P < 32 ? 32 : ((P + 31) / 32) * 32, 0, s>>>(C, A, B, Cc, Dd, dA, sw, P);
+  if (D == 1)
+    recon_emit_kernel<1, 128><<<g, 128, 0, s>>>(C, Kmax, K, prm, W, out_off, cstat, dA, seed, dx,
+                                                 n_out, x_out, v_out, alpha_out, status_out);
+  else
+    recon_emit_kernel<3, 128><<<g, 128, 0, s>>>(C, Kmax, K, prm, W, out_off, cstat, dA, seed, dx,
+                                                 n_out, x_out, v_out, alpha_out, status_out);
+  return cudaGetLastError();
+}
+
+}  // namespace gmcr

@@ -1,0 +1,218 @@
+"""Thin Python binding of the C ABI in ``include/gm.h`` (argument marshalling
+only).  Tensors are torch CUDA tensors; every computation runs in the
+library's CUDA kernels on the current (or given) torch stream.
+
+The library is loaded from the package's ``_lib/libgmcr.so``; a missing
+library or a missing GPU raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+GM_OK = 0
+ST_EM_MAXSWEEPS = 0x01
+ST_COV_NOT_PD = 0x02
+ST_TOO_FEW = 0x04
+ST_EMPTY = 0x08
+ST_DEGENERATE = 0x10
+ST_PROJ_SKIPPED = 0x100
+ST_NEG_WEIGHT = 0x200
+ST_MM_EMPTY_COL = 0x400
+ST_NO_MIXTURE = 0x800
+
+EXPORTED = ("gm_compress", "gm_reconstruct", "gm_moments", "gm_mixture_moments",
+            "gm_last_error", "gm_shutdown")
+
+
+class GMConfig(ct.Structure):
+    """Mirror of ``gm_config`` (include/gm.h)."""
+    _fields_ = [("D", ct.c_int32), ("Kmax", ct.c_int32), ("shape_order", ct.c_int32),
+                ("max_sweeps", ct.c_int32), ("tol", ct.c_double), ("seed", ct.c_uint64),
+                ("L", ct.c_double), ("q", ct.c_double), ("threads_per_cell", ct.c_int32),
+                ("smem_particles", ct.c_int32), ("precision", ct.c_int32),
+                ("reserved", ct.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libgmcr.so (ctypes).  Raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB):
+            if build_if_missing:
+                _build.build()
+            else:
+                raise RuntimeError(f"CUDA library {_build.LIB} is missing: run "
+                                   "__graft_entry__.build() (nvcc, sm_103a) first")
+        lib = ct.CDLL(_build.LIB)
+        P, I64, I32 = ct.c_void_p, ct.c_int64, ct.c_int32
+        lib.gm_compress.argtypes = [P, I64, I64, P, P, P, I32, P, P, P, P, P, P, P, P, P, P]
+        lib.gm_reconstruct.argtypes = [P, I64, P, P, P, P, I64, P, P, P, P, P, P, P]
+        lib.gm_moments.argtypes = [P, I64, I64, P, P, P, I32, P, P, P, P, P, P, P]
+        lib.gm_mixture_moments.argtypes = [P, I64, P, P, P, P, P, P, P, P]
+        for f in ("gm_compress", "gm_reconstruct", "gm_moments", "gm_mixture_moments", "gm_shutdown"):
+            getattr(lib, f).restype = ct.c_int
+        lib.gm_last_error.restype = ct.c_char_p
+        _lib = lib
+        return lib
+
+
+def config(params: dict, seed_key: str = "seed", **over) -> GMConfig:
+    """gm_config from a plain method-parameter dict (see workloads)."""
+    c = GMConfig()
+    c.D = int(params["D"])
+    c.Kmax = int(params["Kmax"])
+    c.shape_order = int(params["shape_order"])
+    c.max_sweeps = int(params.get("max_sweeps", 1000))
+    c.tol = float(params.get("tol", 1e-6))
+    c.seed = int(params.get(seed_key, 1))
+    c.L = float(params["L"])
+    c.q = float(params.get("q", 1.0))
+    c.threads_per_cell = int(over.get("threads_per_cell", params.get("threads_per_cell", 0)))
+    c.smem_particles = int(over.get("smem_particles", params.get("smem_particles", 0)))
+    c.precision = int(over.get("precision", params.get("precision", 0)))
+    c.reserved = 0
+    return c
+
+
+def P_of(D: int) -> int:
+    return 1 + D + D * (D + 1) // 2
+
+
+def _ptr(t):
+    return ct.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream_ptr(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ct.c_void_p(s.cuda_stream)
+
+
+def _check(t, dtype, name):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def _rc(lib, rc, what):
+    if rc != GM_OK:
+        raise RuntimeError(f"{what} failed ({rc}): {lib.gm_last_error().decode()}")
+
+
+def gm_compress(cfg: GMConfig, cell_off, x, v, alpha, stream=None, out=None) -> dict:
+    """Per-cell adaptive GM fit.  cell_off [C+1] int64, x [n] f64,
+    v [D, n] f32/f64, alpha [n] f64 (all CUDA).  Returns the outputs of
+    ``gm_compress`` as CUDA tensors (``out`` may supply them)."""
+    lib = load()
+    C = cell_off.shape[0] - 1
+    n = x.shape[0]
+    D = cfg.D
+    _check(cell_off, torch.int64, "cell_off")
+    _check(x, torch.float64, "x")
+    _check(alpha, torch.float64, "alpha")
+    if v.dtype not in (torch.float32, torch.float64) or tuple(v.shape) != (D, n):
+        raise ValueError("v must be [D, n] float32/float64")
+    _check(v, v.dtype, "v")
+    dev = x.device
+    if out is None:
+        out = dict(K=torch.empty(C, dtype=torch.int32, device=dev),
+                   params=torch.empty((C, cfg.Kmax, P_of(D)), dtype=torch.float64, device=dev),
+                   W=torch.empty(C, dtype=torch.float64, device=dev),
+                   rho_target=torch.empty(C, dtype=torch.float64, device=dev),
+                   lnL=torch.empty(C, dtype=torch.float64, device=dev),
+                   sweeps=torch.empty(C, dtype=torch.int32, device=dev),
+                   kwork=torch.empty(C, dtype=torch.int32, device=dev),
+                   status=torch.empty(C, dtype=torch.int32, device=dev))
+    rc = lib.gm_compress(ct.byref(cfg), C, n, _ptr(cell_off), _ptr(x), _ptr(v),
+                         1 if v.dtype == torch.float64 else 0, _ptr(alpha), _ptr(out["K"]),
+                         _ptr(out["params"]), _ptr(out["W"]), _ptr(out["rho_target"]),
+                         _ptr(out["lnL"]), _ptr(out["sweeps"]), _ptr(out["kwork"]),
+                         _ptr(out["status"]), _stream_ptr(stream))
+    _rc(lib, rc, "gm_compress")
+    return out
+
+
+def gm_reconstruct(cfg: GMConfig, K, params, W, rho_target, out_off, n_out: int | None = None,
+                   stream=None, want_dA: bool = False, out=None) -> dict:
+    """Resample every cell: returns x [n'], v [D, n'], alpha [n'], status [C]
+    (and dA [C] if asked).  ``n_out`` = out_off[-1] (read from the device if
+    not given)."""
+    lib = load()
+    C = out_off.shape[0] - 1
+    D = cfg.D
+    _check(K, torch.int32, "K")
+    _check(params, torch.float64, "params")
+    _check(W, torch.float64, "W")
+    _check(rho_target, torch.float64, "rho_target")
+    _check(out_off, torch.int64, "out_off")
+    if n_out is None:
+        n_out = int(out_off[-1].item())
+    dev = W.device
+    if out is None:
+        out = dict(x=torch.empty(n_out, dtype=torch.float64, device=dev),
+                   v=torch.empty((D, n_out), dtype=torch.float64, device=dev),
+                   alpha=torch.empty(n_out, dtype=torch.float64, device=dev),
+                   status=torch.empty(C, dtype=torch.int32, device=dev))
+        if want_dA:
+            out["dA"] = torch.empty(C, dtype=torch.float64, device=dev)
+    rc = lib.gm_reconstruct(ct.byref(cfg), C, _ptr(K), _ptr(params), _ptr(W), _ptr(rho_target),
+                            n_out, _ptr(out_off), _ptr(out["x"]), _ptr(out["v"]),
+                            _ptr(out["alpha"]), _ptr(out["status"]), _ptr(out.get("dA")),
+                            _stream_ptr(stream))
+    _rc(lib, rc, "gm_reconstruct")
+    return out
+
+
+def gm_moments(cfg: GMConfig, cell_off, x, v, alpha, stream=None) -> dict:
+    lib = load()
+    C = cell_off.shape[0] - 1
+    n = alpha.shape[0]
+    D = cfg.D
+    dev = alpha.device
+    nm = D * (D + 1) // 2
+    out = dict(W=torch.empty(C, dtype=torch.float64, device=dev),
+               p=torch.empty((C, D), dtype=torch.float64, device=dev),
+               M2=torch.empty((C, nm), dtype=torch.float64, device=dev),
+               E=torch.empty(C, dtype=torch.float64, device=dev),
+               rho=torch.empty(C, dtype=torch.float64, device=dev))
+    rc = lib.gm_moments(ct.byref(cfg), C, n, _ptr(cell_off), _ptr(x), _ptr(v),
+                        1 if v.dtype == torch.float64 else 0, _ptr(alpha), _ptr(out["W"]),
+                        _ptr(out["p"]), _ptr(out["M2"]), _ptr(out["E"]), _ptr(out["rho"]),
+                        _stream_ptr(stream))
+    _rc(lib, rc, "gm_moments")
+    return out
+
+
+def gm_mixture_moments(cfg: GMConfig, K, params, W, stream=None) -> dict:
+    lib = load()
+    C = K.shape[0]
+    D = cfg.D
+    dev = W.device
+    nm = D * (D + 1) // 2
+    out = dict(W=torch.empty(C, dtype=torch.float64, device=dev),
+               p=torch.empty((C, D), dtype=torch.float64, device=dev),
+               M2=torch.empty((C, nm), dtype=torch.float64, device=dev),
+               E=torch.empty(C, dtype=torch.float64, device=dev))
+    rc = lib.gm_mixture_moments(ct.byref(cfg), C, _ptr(K), _ptr(params), _ptr(W), _ptr(out["W"]),
+                                _ptr(out["p"]), _ptr(out["M2"]), _ptr(out["E"]),
+                                _stream_ptr(stream))
+    _rc(lib, rc, "gm_mixture_moments")
+    return out

@@ -1,0 +1,70 @@
+"""Host-side checks of the C ABI: the library builds for sm_103a, loads, and
+exports every entry point include/gm.h declares; the Python mirror of
+gm_config has the C layout; argument errors are reported without touching
+the GPU."""
+import ctypes as ct
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gm.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2007_12273_gb300 import build, gm
+    build.build()
+    return gm.load()
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^(?:int|const char\*)\s+(gm_\w+)\s*\(", txt, re.M)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert {"gm_compress", "gm_reconstruct", "gm_moments"} <= set(names)
+    out = subprocess.run(["nm", "-D", "--defined-only", lib._name], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r" T (gm_\w+)", out))
+    for n in names:
+        assert n in exported, n
+        assert hasattr(lib, n)
+
+
+def test_config_layout_matches_header(tmp_path):
+    from paper_2007_12273_gb300.gm import GMConfig
+    src = tmp_path / "lay.c"
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "gm.h"\n'
+        "int main(void){printf(\"%zu\", sizeof(gm_config));"
+        + "".join(f'printf(" %zu", offsetof(gm_config, {f}));' for f, _ in GMConfig._fields_)
+        + "return 0;}\n")
+    exe = tmp_path / "lay"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    vals = [int(t) for t in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    assert vals[0] == ct.sizeof(GMConfig)
+    assert vals[1:] == [getattr(GMConfig, f).offset for f, _ in GMConfig._fields_]
+
+
+def test_argument_errors_without_gpu(lib):
+    from paper_2007_12273_gb300 import gm
+    cfg = gm.config(dict(D=2, Kmax=4, shape_order=2, L=1.0))
+    rc = lib.gm_compress(ct.byref(cfg), 1, 1, None, None, None, 0, None, None, None, None, None,
+                         None, None, None, None, None)
+    assert rc == -1 and b"D must be 1 or 3" in lib.gm_last_error()
+    cfg = gm.config(dict(D=1, Kmax=40, shape_order=2, L=1.0))
+    rc = lib.gm_reconstruct(ct.byref(cfg), 1, None, None, None, None, 0, None, None, None, None,
+                            None, None, None)
+    assert rc == -1 and b"Kmax" in lib.gm_last_error()
+    cfg = gm.config(dict(D=1, Kmax=4, shape_order=3, L=1.0))
+    assert lib.gm_moments(ct.byref(cfg), 1, 1, None, None, None, 0, None, None, None, None,
+                          None, None, None) == -1
+    # empty problems are valid no-ops
+    cfg = gm.config(dict(D=1, Kmax=4, shape_order=2, L=1.0))
+    assert lib.gm_mixture_moments(ct.byref(cfg), 0, None, None, None, None, None, None, None,
+                                  None) == 0
