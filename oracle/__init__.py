@@ -62,7 +62,7 @@ def _load():
             lib.oracle_philox4x32_10.argtypes = [P, P, P]
             lib.oracle_uniform52.argtypes = [ct.c_uint32, ct.c_uint32]
             lib.oracle_uniform52.restype = ct.c_double
-            lib.oracle_compress.argtypes = [P, ct.c_int64] + [P] * 12 + [ct.c_int]
+            lib.oracle_compress.argtypes = [P, ct.c_int64] + [P] * 13 + [ct.c_int]
             lib.oracle_em_cell.argtypes = [P, ct.c_int64, ct.c_int64, P, P, P, ct.c_int, ct.c_int,
                                            P, P, P, P, P, P, P, P, ct.c_int, P]
             lib.oracle_penalised_L.argtypes = [ct.c_int, ct.c_int, P, ct.c_int64, P, P]
@@ -117,9 +117,11 @@ def max_threads() -> int:
     return _load().oracle_max_threads()
 
 
-def compress(params: dict, cell_off, x, v, alpha, nthreads: int = 1) -> dict:
+def compress(params: dict, cell_off, x, v, alpha, nthreads: int = 1, cell_ids=None) -> dict:
     """Oracle compression of every cell (Sec. 2.2-2.3, final step of
-    Sec. 2.3.1, target charge density of Sec. 2.4.1)."""
+    Sec. 2.3.1, target charge density of Sec. 2.4.1).  ``cell_ids`` gives
+    each cell's index in a larger batch (it keys the initial picks); the
+    charge density then refers to the sub-mesh given."""
     lib = _load()
     cfg = _cfg(params)
     cell_off = np.ascontiguousarray(cell_off, dtype=np.int64)
@@ -134,7 +136,9 @@ def compress(params: dict, cell_off, x, v, alpha, nthreads: int = 1) -> dict:
     rc = lib.oracle_compress(ct.byref(cfg), C, _ptr(cell_off), _ptr(x), _ptr(v), _ptr(alpha),
                              _ptr(out["K"]), _ptr(out["params"]), _ptr(out["W"]),
                              _ptr(out["rho_target"]), _ptr(out["lnL"]), _ptr(out["sweeps"]),
-                             _ptr(out["kwork"]), _ptr(out["status"]), int(nthreads))
+                             _ptr(out["kwork"]), _ptr(out["status"]),
+                             _ptr(None if cell_ids is None else np.ascontiguousarray(cell_ids, dtype=np.int64)),
+                             int(nthreads))
     if rc != 0:
         raise ValueError(f"oracle_compress failed ({rc})")
     return out

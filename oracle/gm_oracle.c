@@ -483,7 +483,8 @@ int oracle_compress(const oracle_cfg *cfg, int64_t C, const int64_t *cell_off,
                     const double *x, const double *v /* [D][Ntot] */, const double *alpha,
                     int32_t *K_out, double *params_out, double *W_out,
                     double *rho_target_out, double *lnL_out, int32_t *sweeps_out,
-                    int32_t *kwork_out, uint32_t *status_out, int nthreads) {
+                    int32_t *kwork_out, uint32_t *status_out, const int64_t *cell_ids,
+                    int nthreads) {
   const int D = cfg->D;
   if (D != 1 && D != 3) return -1;
   if (cfg->Kmax < 1 || cfg->Kmax > OR_MAXK) return -1;
@@ -499,7 +500,10 @@ int oracle_compress(const oracle_cfg *cfg, int64_t C, const int64_t *cell_off,
     for (int64_t p = 0; p < n; ++p)
       for (int d = 0; d < D; ++d) vv[p * D + d] = v[(int64_t)d * Ntot + cell_off[j] + p];
     cell_out o;
-    em_cell(cfg, j, n, vv, alpha + cell_off[j], params_out + (size_t)j * cfg->Kmax * P, &o,
+    /* cell_ids (optional) gives each cell's index in a larger batch, which
+     * keys its Philox stream */
+    em_cell(cfg, cell_ids ? cell_ids[j] : j, n, vv, alpha + cell_off[j],
+            params_out + (size_t)j * cfg->Kmax * P, &o,
             NULL, 0, 0, NULL, NULL, 0, NULL);
     K_out[j] = o.K; W_out[j] = o.W; lnL_out[j] = o.lnL;
     if (sweeps_out) sweeps_out[j] = o.sweeps;

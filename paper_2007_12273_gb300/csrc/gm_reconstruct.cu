@@ -84,6 +84,14 @@ __device__ void load_cell(RecCell<D>& rc, int64_t j, int Kmax, const int32_t* K,
   }
 }
 
+// Box-Muller radius sqrt(-2 ln u) in FP32; near u = 1 the logarithm is
+// taken as log1p(u - 1) with u - 1 formed exactly in FP64, so the radius
+// keeps FP32 relative accuracy where its derivative is unbounded
+__device__ __forceinline__ float bm_radius(double u) {
+  const float lnu = u < 0.5 ? logf((float)u) : log1pf((float)(u - 1.0));
+  return sqrtf(-2.0f * lnu);
+}
+
 // particle i of cell j: position and velocity (Sec. 2.4, eq. mix-dist-1)
 template <int D>
 __device__ __forceinline__ void sample_particle(const RecCell<D>& rc, int64_t j, int64_t i,
@@ -101,18 +109,16 @@ __device__ __forceinline__ void sample_particle(const RecCell<D>& rc, int64_t j,
   float xi[3];
   {
     const u32x4 r1 = philox_draw(seed, (uint32_t)i, kTagSample | 1u, j);
-    const float ua = (float)uniform52(r1.x, r1.y), ub = (float)uniform52(r1.z, r1.w);
-    const float rr = sqrtf(-2.0f * logf(ua));
+    const float rr = bm_radius(uniform52(r1.x, r1.y));
     float sn, cs;
-    sincospif(2.0f * ub, &sn, &cs);
+    sincospif(2.0f * (float)uniform52(r1.z, r1.w), &sn, &cs);
     xi[0] = rr * cs;
     if (D == 3) xi[1] = rr * sn;
   }
   if (D == 3) {
     const u32x4 r2 = philox_draw(seed, (uint32_t)i, kTagSample | 2u, j);
-    const float ua = (float)uniform52(r2.x, r2.y), ub = (float)uniform52(r2.z, r2.w);
-    const float rr = sqrtf(-2.0f * logf(ua));
-    xi[2] = rr * cospif(2.0f * ub);
+    const float rr = bm_radius(uniform52(r2.x, r2.y));
+    xi[2] = rr * cospif(2.0f * (float)uniform52(r2.z, r2.w));
   }
   if (K == 0) {
     for (int d = 0; d < D; ++d) v[d] = 0.0;
