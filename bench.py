@@ -251,6 +251,8 @@ def run_gmcr(args):
     gm.load()
 
     wl = make_workload(args.workload, rank)
+    if args.cells:
+        wl = sub_workload(wl, args.cells)
     D = wl.D
     cfg = gm.config(wl.params, precision=args.precision)
     rcfg = gm.config(wl.params, seed_key="recon_seed", precision=args.precision)
@@ -408,6 +410,7 @@ def main(argv=None):
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--cells", type=int, default=0, help="use only the first N cells (profiling)")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

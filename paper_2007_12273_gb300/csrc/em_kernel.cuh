@@ -511,10 +511,14 @@ __global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
             } else {
               const R rN = (R)1 / Nk;
               R dl[D], mun[D], Sn[NM];
-              // the statistics are about the FP32 mean the E-step used
+              // The statistics are about the FP32 copy of the mean that the
+              // E-step used; the shift is added to the FP64 mean, which
+              // thereby keeps the sub-ulp part of every update (the FP32
+              // copy then follows the FP64 trajectory instead of stalling
+              // when an update is below its resolution).
               for (int x = 0; x < D; ++x) {
                 dl[x] = sv[1 + x] * rN;
-                mun[x] = (R)c.emu[k][x] + dl[x];
+                mun[x] = (R)c.mu[k][x] + dl[x];
               }
               int t = 0;
               for (int x = 0; x < D; ++x)
