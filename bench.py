@@ -254,8 +254,10 @@ def run_gmcr(args):
     if args.cells:
         wl = sub_workload(wl, args.cells)
     D = wl.D
-    cfg = gm.config(wl.params, precision=args.precision)
-    rcfg = gm.config(wl.params, seed_key="recon_seed", precision=args.precision)
+    over = dict(precision=args.precision, threads_per_cell=args.threads_per_cell,
+                smem_particles=args.smem_particles)
+    cfg = gm.config(wl.params, **over)
+    rcfg = gm.config(wl.params, seed_key="recon_seed", **over)
     counts = wl.counts()
     n = wl.ntot
     C = wl.C
@@ -411,6 +413,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--cells", type=int, default=0, help="use only the first N cells (profiling)")
+    ap.add_argument("--threads-per-cell", type=int, default=0)
+    ap.add_argument("--smem-particles", type=int, default=0)
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

@@ -50,14 +50,15 @@ struct EmParams {
 constexpr float kHalfLog2e = 0.72134752044448170368f;  // log2(e) / 2
 constexpr double kLn2 = 0.69314718055994530942;
 
-template <int D, int NW>
+template <int D, int NW, typename R>
 struct EmCtl {
   static constexpr int NM = D * (D + 1) / 2;
   static constexpr int NS = 1 + D + NM;
   // master parameters in whitened coordinates y = (v - mean) / sc
-  double u[kMaxK];  // unnormalised weights, omega = u / Z
+  R u[kMaxK];  // unnormalised weights, omega = u / Z (precision of the M-step)
+  R Z;
   double mu[kMaxK][D];
-  double S[kMaxK][NM];  // upper triangle, row-major
+  double S[1][NM];      // whitened total covariance (initial covariance of every component)
   // FP32 E-step constants: log2(u f) = b - |A (y - mu)|^2
   float emu[kMaxK][D];
   float eA[kMaxK][NM];  // lower triangle of sqrt(log2e/2) L^{-1}, row-major
@@ -65,7 +66,8 @@ struct EmCtl {
   float eb[kMaxK];      // log2(u) + elc
   float pmu[D], pA[NM], pb;  // updated constants of the previous component
   double mean[D], sc[D], isc[D];
-  double Nd, W, Z, L, Lprev, logjac;
+  float meanf[D], scf[D];
+  double Nd, W, L, Lprev, logjac, logN;
   float redf[NW][NS + 1];
   double redd[NW][NS + 1];
   double res[NS + 1];
@@ -87,8 +89,8 @@ __device__ __forceinline__ int tri(int i, int j) {  // upper-triangle index, i <
 // Cholesky of the upper-triangle S (precision R); returns false if a pivot
 // is not positive or, measured in the original coordinates (pivots scale by
 // sc_i^2), falls under 1e-13 * sum_d (Sigma_dd + mu_d^2).
-template <int D, typename R>
-__device__ bool chol_whitened(const R* S, const R* mu, const double* mean, const double* sc,
+template <int D, typename R, typename M>
+__device__ bool chol_whitened(const R* S, const R* mu, const M* mean, const M* sc,
                               R (&Lc)[3][3]) {
   R scale2 = 0;
   for (int d = 0; d < D; ++d) {
@@ -153,8 +155,8 @@ __device__ __forceinline__ float lg_eval(const float* mu, const float* A, float 
 }
 
 // FP64 block reduction of NV values (NV <= NS + 1); result in c.res
-template <int D, int NT, int NV>
-__device__ __forceinline__ void block_sum_d(EmCtl<D, NT / 32>& c, double (&v)[NV]) {
+template <int D, int NT, int NV, typename R>
+__device__ __forceinline__ void block_sum_d(EmCtl<D, NT / 32, R>& c, double (&v)[NV]) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < NV; ++i) v[i] = warp_sum(v[i]);
@@ -181,7 +183,7 @@ __global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
   constexpr int T = D * (D + 3) / 2;
   constexpr int P = 1 + D + NM;
   const double halfT = 0.5 * T;
-  __shared__ EmCtl<D, NW> c;
+  __shared__ EmCtl<D, NW, R> c;
   extern __shared__ float tile_smem[];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const VT* __restrict__ vin = static_cast<const VT*>(a.v);
@@ -223,7 +225,7 @@ __global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
 #pragma unroll
         for (int d = 0; d < D; ++d) acc[1 + d] += al * (double)vin[(int64_t)d * a.n + off + p];
       }
-      block_sum_d<D, NT, 1 + D>(c, acc);
+      block_sum_d<D, NT, 1 + D, R>(c, acc);
       if (tid == 0) {
         c.W = c.res[0];
         c.Nd = (double)N;
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
 #pragma unroll
           for (int y = x; y < D; ++y) acc[t++] += al * dv[x] * dv[y];
       }
-      block_sum_d<D, NT, NM>(c, acc);
+      block_sum_d<D, NT, NM, R>(c, acc);
       if (tid == 0) {
         double cov[NM];
         for (int i = 0; i < NM; ++i) cov[i] = c.res[i] / c.W;
@@ -292,10 +294,13 @@ __global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
           for (int i = 0; i < NM; ++i) c.fS[0][i] = cov[i];
         } else {
           c.logjac = 0.0;
+          c.logN = log(c.Nd);
           for (int d = 0; d < D; ++d) {
             c.sc[d] = sqrt(cov[tri<D>(d, d)]);
             c.isc[d] = 1.0 / c.sc[d];
             c.logjac += log(c.sc[d]);
+            c.meanf[d] = (float)c.mean[d];
+            c.scf[d] = (float)c.sc[d];
           }
           // whitened total covariance (correlation matrix) for the init
           for (int x = 0; x < D; ++x)
@@ -374,26 +379,23 @@ __global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
         if (!dup) picks[got++] = idx;
       }
       c.K = K;
-      c.Z = 1.0;
+      c.Z = (R)1;
       R Lc[3][3];
       R S0[NM], m0[D];
       for (int i = 0; i < NM; ++i) S0[i] = (R)c.S[0][i];
       for (int d = 0; d < D; ++d) m0[d] = 0;
-      chol_whitened<D, R>(S0, m0, c.mean, c.sc, Lc);  // the total covariance passed above
+      chol_whitened<D, R, double>(S0, m0, c.mean, c.sc, Lc);  // the total covariance passed above
       float eA[NM], elc;
       make_econst<D, R>(Lc, eA, elc);
       double Stot[NM];
       for (int i = 0; i < NM; ++i) Stot[i] = c.S[0][i];
       for (int k = 0; k < K; ++k) {
-        c.u[k] = 1.0 / K;
+        c.u[k] = (R)1 / (R)K;
         for (int d = 0; d < D; ++d) {
           c.mu[k][d] = ((double)vin[(int64_t)d * a.n + off + picks[k]] - c.mean[d]) * c.isc[d];
           c.emu[k][d] = (float)c.mu[k][d];
         }
-        for (int i = 0; i < NM; ++i) {
-          c.S[k][i] = Stot[i];
-          c.eA[k][i] = eA[i];
-        }
+        for (int i = 0; i < NM; ++i) c.eA[k][i] = eA[i];
         c.elc[k] = elc;
         c.eb[k] = log2f((float)c.u[k]) + elc;
       }
@@ -423,12 +425,14 @@ __global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
         acc = fmaf(AH[p], m + lg2(s), acc);
       }
       double v1[1] = {(double)acc};
-      block_sum_d<D, NT, 1>(c, v1);
-      if (tid == 0) {
-        double pen = 0.0;
-        for (int k = 0; k < K; ++k) pen += log(c.u[k] / c.Z);
-        const double dpar = (double)K * (T + 1) - 1.0;
-        c.L = c.res[0] * kLn2 - c.Nd * c.logjac - 0.5 * dpar * log(c.Nd) - 0.5 * T * pen;
+      block_sum_d<D, NT, 1, R>(c, v1);
+      if (tid < 32) {
+        float pen = lane < K ? logf((float)(c.u[lane] / c.Z)) : 0.0f;
+        pen = warp_sum(pen);
+        if (lane == 0) {
+          const double dpar = (double)K * (T + 1) - 1.0;
+          c.L = c.res[0] * kLn2 - c.Nd * c.logjac - 0.5 * dpar * c.logN - 0.5 * T * (double)pen;
+        }
       }
       __syncthreads();
     };
@@ -506,7 +510,7 @@ __global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
             const int K = c.K;
             const R Nk = sv[0];
             bool removed = false;
-            if (K > 1 && (double)Nk - halfT <= 0.0) {
+            if (K > 1 && Nk - (R)halfT <= (R)0) {
               removed = true;
             } else {
               const R rN = (R)1 / Nk;
@@ -516,15 +520,22 @@ __global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
               // thereby keeps the sub-ulp part of every update (the FP32
               // copy then follows the FP64 trajectory instead of stalling
               // when an update is below its resolution).
+              double mu64[D];
               for (int x = 0; x < D; ++x) {
                 dl[x] = sv[1 + x] * rN;
-                mun[x] = (R)c.mu[k][x] + dl[x];
+                mu64[x] = c.mu[k][x] + (double)dl[x];
+                mun[x] = (R)mu64[x];
               }
               int t = 0;
               for (int x = 0; x < D; ++x)
                 for (int yy = x; yy < D; ++yy, ++t) Sn[t] = sv[1 + D + t] * rN - dl[x] * dl[yy];
               R Lc[3][3];
-              if (!chol_whitened<D, R>(Sn, mun, c.mean, c.sc, Lc)) {
+              bool pd;
+              if constexpr (sizeof(R) == 4)
+                pd = chol_whitened<D, R, float>(Sn, mun, c.meanf, c.scf, Lc);
+              else
+                pd = chol_whitened<D, R, double>(Sn, mun, c.mean, c.sc, Lc);
+              if (!pd) {
                 c.status |= GM_ST_COV_NOT_PD;
                 if (K > 1) {
                   removed = true;
@@ -533,19 +544,19 @@ __global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
                   c.k = k + 1;
                 }
               } else {
-                const double wn = (K == 1) ? 1.0 : ((double)Nk - halfT) / (c.Nd - halfT * K);
-                const double un = wn * c.Z;
+                // eq. (omegak), then the renormalisation of step 3 through Z
+                const R wn = (K == 1) ? (R)1 : (Nk - (R)halfT) / ((R)c.Nd - (R)halfT * (R)K);
+                const R un = wn * c.Z;
                 c.Z = c.Z - c.u[k] + un;
                 c.u[k] = un;
                 float eA[NM], elc;
                 make_econst<D, R>(Lc, eA, elc);
                 for (int x = 0; x < D; ++x) {
-                  c.mu[k][x] = (double)mun[x];
+                  c.mu[k][x] = mu64[x];
                   c.emu[k][x] = (float)mun[x];
                   c.pmu[x] = (float)mun[x];
                 }
                 for (int q = 0; q < NM; ++q) {
-                  c.S[k][q] = (double)Sn[q];
                   c.eA[k][q] = eA[q];
                   c.pA[q] = eA[q];
                 }
@@ -561,7 +572,7 @@ __global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
               for (int m = k; m < K - 1; ++m) {
                 c.u[m] = c.u[m + 1];
                 for (int x = 0; x < D; ++x) { c.mu[m][x] = c.mu[m + 1][x]; c.emu[m][x] = c.emu[m + 1][x]; }
-                for (int q = 0; q < NM; ++q) { c.S[m][q] = c.S[m + 1][q]; c.eA[m][q] = c.eA[m + 1][q]; }
+                for (int q = 0; q < NM; ++q) c.eA[m][q] = c.eA[m + 1][q];
                 c.elc[m] = c.elc[m + 1];
                 c.eb[m] = c.eb[m + 1];
               }
@@ -575,14 +586,13 @@ __global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
       }
       // normalise the weights, then the exact pass and the convergence test
       if (tid < c.K) {
-        const double un = c.u[tid] / c.Z;
+        const R un = c.u[tid] / c.Z;
         c.eb[tid] = log2f((float)un) + c.elc[tid];
       }
       __syncthreads();
-      if (tid == 0) {
-        for (int k = 0; k < c.K; ++k) c.u[k] /= c.Z;
-        c.Z = 1.0;
-      }
+      if (tid < c.K) c.u[tid] = c.u[tid] / c.Z;
+      __syncthreads();
+      if (tid == 0) c.Z = (R)1;
       __syncthreads();
       resync();
       if (tid == 0) {
@@ -634,7 +644,7 @@ __global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
             for (int yy = x; yy < D; ++yy, ++t) acc[t] += gd * dv[yy];
           }
         }
-        block_sum_d<D, NT, NS>(c, acc);
+        block_sum_d<D, NT, NS, R>(c, acc);
         if (tid == 0 && c.res[0] > 0.0) {
           const int f = c.Kf;
           const double n = c.res[0];
@@ -665,14 +675,14 @@ __global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
         for (int d = 0; d < D; ++d) mo[d] = 0.0;
         double meano[D];
         for (int d = 0; d < D; ++d) meano[d] = c.mean[d] + c.fmu[k][d];
-        if (!chol_whitened<D, double>(So, mo, meano, one, Lo)) pd = 0;
+        if (!chol_whitened<D, double, double>(So, mo, meano, one, Lo)) pd = 0;
         // whitened copy for the likelihood pass
         double Sw[NM], mw[D], Lw[3][3];
         for (int x = 0; x < D; ++x) {
           mw[x] = c.fmu[k][x] * c.isc[x];
           for (int yy = x; yy < D; ++yy) Sw[tri<D>(x, yy)] = c.fS[k][tri<D>(x, yy)] * c.isc[x] * c.isc[yy];
         }
-        if (chol_whitened<D, double>(Sw, mw, c.mean, c.sc, Lw)) {
+        if (chol_whitened<D, double, double>(Sw, mw, c.mean, c.sc, Lw)) {
           float eA[NM], elc;
           make_econst<D, double>(Lw, eA, elc);
           for (int q = 0; q < NM; ++q) c.eA[k][q] = eA[q];
@@ -682,12 +692,12 @@ __global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
         }
         for (int x = 0; x < D; ++x) c.emu[k][x] = (float)mw[x];
         c.eb[k] = log2f((float)c.fw[k]) + c.elc[k];
-        c.u[k] = c.fw[k];
+        c.u[k] = (R)c.fw[k];
       }
       if (!pd) c.status |= GM_ST_COV_NOT_PD;
       c.final_pd = pd;
       c.K = Kf;
-      c.Z = 1.0;
+      c.Z = (R)1;
     }
     __syncthreads();
     if (c.final_pd) resync();
