@@ -4,7 +4,8 @@
 // ticket.  A cell's particles are staged once (whitened FP32 velocities and
 // normalised weights) in shared memory -- or, when the cell is larger than
 // the shared tile, in an L2-resident global scratch with the same layout --
-// and reused by every sweep.
+// and reused by every sweep.  Each thread works on pairs of particles with
+// Blackwell's packed FP32 (f32x2) arithmetic.
 //
 // Component-wise EM (Sec. 2.3, Celeux et al.): the E-step of component k
 // needs the normaliser s_p = sum_j omega_j f_j(v_p) with the *current*
@@ -18,10 +19,11 @@
 // the renormalisation after each component (step 3) implicit.
 //
 // Precision: E-step densities / responsibilities FP32; statistics FP32 per
-// thread and per warp, summed across warps in R (FP64 by default); M-step,
-// Cholesky factors and the annihilation / floor tests in R; the final
-// unpenalised step (Sec. 2.3.1) entirely in FP64 with FP64-normalised
-// responsibilities, which is what makes the moments exact.
+// thread and per warp, summed across warps in R; the M-step in R (FP64:
+// precision 0, FP32: precision 1) with the component means accumulated in
+// FP64 either way; the final unpenalised step (Sec. 2.3.1) entirely in FP64
+// with FP64-normalised responsibilities, which is what makes the moments
+// exact.
 #pragma once
 
 #include "gm_common.cuh"
@@ -40,15 +42,28 @@ struct EmParams {
   int32_t* sweeps_out;
   int32_t* kwork_out;
   uint32_t* status_out;
-  float* scratch;  // [(D+4)][n] floats, used by cells larger than the tile
+  float* scratch;          // global tile for cells larger than the shared one
+  int64_t scratch_stride;  // floats per array of the global tile (even)
   unsigned int* queue;
   int Kmax, max_sweeps, cap;
   double tol;
   uint64_t seed;
 };
 
-constexpr float kHalfLog2e = 0.72134752044448170368f;  // log2(e) / 2
+// float offset of cell j's global tile: even, and disjoint from its
+// neighbours' tiles of N_j rounded up to even length
+__host__ __device__ inline int64_t scratch_offset(int64_t off, int64_t j) {
+  return off + 2 * j + (off & 1);
+}
+__host__ inline int64_t scratch_stride(int64_t n, int64_t C) { return n + 2 * C + 2; }
+
 constexpr double kLn2 = 0.69314718055994530942;
+
+template <int D>
+struct NConst {  // packed E constants of one component
+  static constexpr int NM = D * (D + 1) / 2;
+  static constexpr int N = D + NM + 1;  // -mu (D), A (D = 3) or -A^2 (D = 1), b
+};
 
 template <int D, int NW, typename R>
 struct EmCtl {
@@ -58,13 +73,15 @@ struct EmCtl {
   R u[kMaxK];  // unnormalised weights, omega = u / Z (precision of the M-step)
   R Z;
   double mu[kMaxK][D];
-  double S[1][NM];      // whitened total covariance (initial covariance of every component)
+  double S0[NM];  // whitened total covariance (initial covariance of every component)
   // FP32 E-step constants: log2(u f) = b - |A (y - mu)|^2
   float emu[kMaxK][D];
   float eA[kMaxK][NM];  // lower triangle of sqrt(log2e/2) L^{-1}, row-major
   float elc[kMaxK];     // -log2|L| - (D/2) log2(2 pi)
   float eb[kMaxK];      // log2(u) + elc
-  float pmu[D], pA[NM], pb;  // updated constants of the previous component
+  // the same, packed for the pair loop; slot kMaxK holds the previous
+  // component's updated constants
+  f32x2 ec[kMaxK + 1][NConst<D>::N];
   double mean[D], sc[D], isc[D];
   float meanf[D], scf[D];
   double Nd, W, L, Lprev, logjac, logN;
@@ -73,7 +90,7 @@ struct EmCtl {
   double res[NS + 1];
   // final step (centered original coordinates)
   double fw[kMaxK], fmu[kMaxK][D], fS[kMaxK][NM];
-  int64_t cell, off, N;
+  int64_t cell;
   int K, Kf, k, sweep, kwork, annih, done, pstate, degenerate, final_pd;
   unsigned int status;
 };
@@ -135,7 +152,19 @@ __device__ void make_econst(const R (&Lc)[3][3], float* eA, float& elc) {
   }
 }
 
-// log2(u_k f_k(y)) - shift, with d = y - mu returned
+// packed copy of scalar E constants
+template <int D>
+__device__ __forceinline__ void pack_econst(const float* mu, const float* A, float b, f32x2* out) {
+  constexpr int NM = D * (D + 1) / 2;
+  for (int x = 0; x < D; ++x) out[x] = bc2(-mu[x]);
+  if (D == 1)
+    out[1] = bc2(-A[0] * A[0]);
+  else
+    for (int q = 0; q < NM; ++q) out[D + q] = bc2(A[q]);
+  out[D + NM] = bc2(b);
+}
+
+// log2(u_k f_k(y)) (scalar), with d = y - mu returned
 template <int D>
 __device__ __forceinline__ float lg_eval(const float* mu, const float* A, float b, const float* y,
                                          float* d) {
@@ -151,6 +180,25 @@ __device__ __forceinline__ float lg_eval(const float* mu, const float* A, float 
     const float t1 = fmaf(A[1], d[0], A[2] * d[1]);
     const float t2 = fmaf(A[3], d[0], fmaf(A[4], d[1], A[5] * d[2]));
     return b - fmaf(t0, t0, fmaf(t1, t1, t2 * t2));
+  }
+}
+
+// the same for a pair of particles (packed constants)
+template <int D>
+__device__ __forceinline__ f32x2 lg_eval2(const f32x2* e, const f32x2* y, f32x2* d) {
+  constexpr int NM = D * (D + 1) / 2;
+  if (D == 1) {
+    d[0] = add2(y[0], e[0]);
+    return fma2(e[1], mul2(d[0], d[0]), e[2]);
+  } else {
+    d[0] = add2(y[0], e[0]);
+    d[1] = add2(y[1], e[1]);
+    d[2] = add2(y[2], e[2]);
+    const f32x2 t0 = mul2(e[3], d[0]);
+    const f32x2 t1 = fma2(e[4], d[0], mul2(e[5], d[1]));
+    const f32x2 t2 = fma2(e[6], d[0], fma2(e[7], d[1], mul2(e[8], d[2])));
+    const f32x2 q = fma2(t0, t0, fma2(t1, t1, mul2(t2, t2)));
+    return fma2(q, bc2(-1.0f), e[D + NM]);
   }
 }
 
@@ -173,53 +221,469 @@ __device__ __forceinline__ void block_sum_d(EmCtl<D, NT / 32, R>& c, double (&v)
 }
 
 // ---------------------------------------------------------------------------
-// the kernel
+// one cell, after its moments are known and it is not degenerate.
+// base: the particle tile (shared or global), st: floats per array (even).
+// Arrays: Y[d] (whitened v), AH (normalised alpha), SS (s_p), MM (-m_p),
+// GG (the current component's term); N rounded up to even with a
+// zero-weight pad particle.
 // ---------------------------------------------------------------------------
 template <int D, int NT, typename VT, typename R>
-__global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
+__device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32, R>& c,
+                                             int64_t j, int64_t off, int N, float* base,
+                                             int st) {
   constexpr int NW = NT / 32;
   constexpr int NM = D * (D + 1) / 2;
   constexpr int NS = 1 + D + NM;
   constexpr int T = D * (D + 3) / 2;
   constexpr int P = 1 + D + NM;
+  constexpr int NC = NConst<D>::N;
   const double halfT = 0.5 * T;
-  __shared__ EmCtl<D, NW, R> c;
-  extern __shared__ float tile_smem[];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const VT* __restrict__ vin = static_cast<const VT*>(a.v);
+  double* prm_out = a.params_out + (size_t)j * a.Kmax * P;
+  float* Y = base;
+  float* AH = base + D * st;
+  float* SS = base + (D + 1) * st;
+  float* MM = base + (D + 2) * st;
+  float* GG = base + (D + 3) * st;
+  const int P2 = (N + 1) >> 1;  // particle pairs
+  const int st2 = st >> 1;
+
+  // ---- stage whitened velocities and normalised weights ------------------
+  {
+    const double nw = c.Nd / c.W;
+    for (int p = tid; p < 2 * P2; p += NT) {
+      if (p < N) {
+#pragma unroll
+        for (int d = 0; d < D; ++d)
+          Y[d * st + p] = (float)(((double)vin[(int64_t)d * a.n + off + p] - c.mean[d]) * c.isc[d]);
+        AH[p] = (float)(a.alpha[off + p] * nw);
+      } else {  // zero-weight pad particle
+#pragma unroll
+        for (int d = 0; d < D; ++d) Y[d * st + p] = 0.0f;
+        AH[p] = 0.0f;
+      }
+    }
+  }
+  // ---- initialisation (Sec. 2.3): Kmax components at random particles ----
+  if (tid == 0) {
+    int K = a.Kmax < N ? a.Kmax : N;
+    while (K > 1 && c.Nd - halfT * K <= 0.0) --K;
+    int picks[kMaxK];
+    int got = 0;
+    for (uint32_t t = 0; got < K; ++t) {
+      int idx;
+      if (t < 100000u) {
+        const u32x4 r = philox_draw(a.seed, t, kTagInit, j);
+        const double uu = uniform52(r.x, r.y);
+        idx = (int)floor(uu * c.Nd);
+        if (idx >= N) idx = N - 1;
+      } else {
+        idx = 0;
+        for (;;) {
+          bool used = false;
+          for (int m = 0; m < got; ++m) used |= (picks[m] == idx);
+          if (!used) break;
+          ++idx;
+        }
+      }
+      bool dup = false;
+      for (int m = 0; m < got; ++m) dup |= (picks[m] == idx);
+      if (!dup) picks[got++] = idx;
+    }
+    c.K = K;
+    c.Z = (R)1;
+    R Lc[3][3];
+    R S0[NM], m0[D];
+    for (int i = 0; i < NM; ++i) S0[i] = (R)c.S0[i];
+    for (int d = 0; d < D; ++d) m0[d] = 0;
+    chol_whitened<D, R, double>(S0, m0, c.mean, c.sc, Lc);  // the total covariance passed
+    float eA[NM], elc;
+    make_econst<D, R>(Lc, eA, elc);
+    for (int k = 0; k < K; ++k) {
+      c.u[k] = (R)1 / (R)K;
+      for (int d = 0; d < D; ++d) {
+        c.mu[k][d] = ((double)vin[(int64_t)d * a.n + off + picks[k]] - c.mean[d]) * c.isc[d];
+        c.emu[k][d] = (float)c.mu[k][d];
+      }
+      for (int i = 0; i < NM; ++i) c.eA[k][i] = eA[i];
+      c.elc[k] = elc;
+      c.eb[k] = log2f((float)c.u[k]) + elc;
+      pack_econst<D>(c.emu[k], c.eA[k], c.eb[k], c.ec[k]);
+    }
+    c.sweep = 0;
+    c.kwork = 0;
+    c.done = 0;
+  }
+  __syncthreads();
+
+  const f32x2* Y2 = reinterpret_cast<const f32x2*>(Y);
+  const f32x2* AH2 = reinterpret_cast<const f32x2*>(AH);
+  f32x2* SS2 = reinterpret_cast<f32x2*>(SS);
+  f32x2* MM2 = reinterpret_cast<f32x2*>(MM);
+  f32x2* GG2 = reinterpret_cast<f32x2*>(GG);
+
+  // ---- exact pass: s_p, m_p and eq. (lnL-GM) ------------------------------
+  auto resync = [&]() {
+    const int K = c.K;
+    float acc = 0.0f;
+    for (int pp = tid; pp < P2; pp += NT) {
+      f32x2 y[D], d[D];
+#pragma unroll
+      for (int q = 0; q < D; ++q) y[q] = Y2[q * st2 + pp];
+      float m0 = -3.0e38f, s0 = 0.0f, m1 = -3.0e38f, s1 = 0.0f;
+      for (int k = 0; k < K; ++k) {
+        float l0, l1;
+        upk2(lg_eval2<D>(c.ec[k], y, d), l0, l1);
+        const float t0 = ex2(-fabsf(l0 - m0)), t1 = ex2(-fabsf(l1 - m1));
+        s0 = (l0 > m0) ? fmaf(s0, t0, 1.0f) : s0 + t0;
+        s1 = (l1 > m1) ? fmaf(s1, t1, 1.0f) : s1 + t1;
+        m0 = fmaxf(m0, l0);
+        m1 = fmaxf(m1, l1);
+      }
+      SS2[pp] = pk2(s0, s1);
+      MM2[pp] = pk2(-m0, -m1);
+      float a0, a1;
+      upk2(AH2[pp], a0, a1);
+      acc = fmaf(a0, m0 + lg2(s0), acc);
+      acc = fmaf(a1, m1 + lg2(s1), acc);
+    }
+    double v1[1] = {(double)acc};
+    block_sum_d<D, NT, 1, R>(c, v1);
+    if (tid < 32) {
+      float pen = lane < K ? logf((float)(c.u[lane] / c.Z)) : 0.0f;
+      pen = warp_sum(pen);
+      if (lane == 0) {
+        const double dpar = (double)K * (T + 1) - 1.0;
+        c.L = c.res[0] * kLn2 - c.Nd * c.logjac - 0.5 * dpar * c.logN - 0.5 * T * (double)pen;
+      }
+    }
+    __syncthreads();
+  };
+
+  resync();
+  if (tid == 0) c.Lprev = c.L;
+  __syncthreads();
+
+  // ---- sweeps -------------------------------------------------------------
+  for (int sweep = 1; sweep <= a.max_sweeps; ++sweep) {
+    if (tid == 0) {
+      c.k = 0;
+      c.annih = 0;
+      c.pstate = 0;
+    }
+    __syncthreads();
+    while (c.k < c.K) {
+      const int k = c.k;
+      const int ps = c.pstate;
+      const f32x2* ek = c.ec[k];
+      const f32x2* ep = c.ec[kMaxK];
+      f32x2 acc[NS];
+#pragma unroll
+      for (int q = 0; q < NS; ++q) acc[q] = 0ull;
+      for (int pp = tid; pp < P2; pp += NT) {
+        f32x2 y[D], d[D];
+#pragma unroll
+        for (int q = 0; q < D; ++q) y[q] = Y2[q * st2 + pp];
+        const f32x2 nm = MM2[pp];  // -m
+        f32x2 s = SS2[pp];
+        if (ps == 1) {  // previous component updated: replace its term
+          float x0, x1;
+          upk2(add2(lg_eval2<D>(ep, y, d), nm), x0, x1);
+          const float gn0 = ex2(fminf(x0, 100.0f)), gn1 = ex2(fminf(x1, 100.0f));
+          float sn0, sn1;
+          upk2(add2(fma2(GG2[pp], bc2(-1.0f), s), pk2(gn0, gn1)), sn0, sn1);
+          s = pk2(fmaxf(sn0, gn0), fmaxf(sn1, gn1));
+        } else if (ps == 2) {  // previous component removed
+          s = fma2(GG2[pp], bc2(-1.0f), s);
+        }
+        float x0, x1;
+        upk2(add2(lg_eval2<D>(ek, y, d), nm), x0, x1);
+        const float g0 = ex2(fminf(x0, 100.0f)), g1 = ex2(fminf(x1, 100.0f));
+        GG2[pp] = pk2(g0, g1);
+        SS2[pp] = s;
+        float s0, s1;
+        upk2(s, s0, s1);
+        const float r0 = rcp_approx(fmaxf(fmaxf(s0, g0), 1e-30f));
+        const float r1 = rcp_approx(fmaxf(fmaxf(s1, g1), 1e-30f));
+        const f32x2 gam = mul2(AH2[pp], pk2(g0 * r0, g1 * r1));
+        acc[0] = add2(acc[0], gam);
+        int t = 1 + D;
+#pragma unroll
+        for (int x = 0; x < D; ++x) {
+          const f32x2 gd = mul2(gam, d[x]);
+          acc[1 + x] = add2(acc[1 + x], gd);
+#pragma unroll
+          for (int yy = x; yy < D; ++yy, ++t) acc[t] = fma2(gd, d[yy], acc[t]);
+        }
+      }
+      // warp (FP32) then cross-warp (precision R) reduction
+      float accs[NS];
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        float lo, hi;
+        upk2(acc[q], lo, hi);
+        accs[q] = warp_sum(lo + hi);
+      }
+      if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NS; ++q) c.redf[wid][q] = accs[q];
+      __syncthreads();
+      if (tid < 32) {
+        R stat = 0;
+        if (lane < NS)
+          for (int q = 0; q < NW; ++q) stat += (R)c.redf[q][lane];
+        R sv[NS];
+#pragma unroll
+        for (int q = 0; q < NS; ++q) sv[q] = __shfl_sync(0xffffffffu, stat, q);
+        if (lane == 0) {
+          // ---- M-step for component k (eqs. muk, sigmak, omegak) ----------
+          c.kwork++;
+          const int K = c.K;
+          const R Nk = sv[0];
+          bool removed = false;
+          if (K > 1 && Nk - (R)halfT <= (R)0) {
+            removed = true;
+          } else {
+            const R rN = (R)1 / Nk;
+            R dl[D], mun[D], Sn[NM];
+            // The statistics are about the FP32 copy of the mean that the
+            // E-step used; the shift is added to the FP64 mean, which
+            // thereby keeps the sub-ulp part of every update (the FP32 copy
+            // then follows the FP64 trajectory instead of stalling when an
+            // update is below its resolution).
+            double mu64[D];
+            for (int x = 0; x < D; ++x) {
+              dl[x] = sv[1 + x] * rN;
+              mu64[x] = c.mu[k][x] + (double)dl[x];
+              mun[x] = (R)mu64[x];
+            }
+            int t = 0;
+            for (int x = 0; x < D; ++x)
+              for (int yy = x; yy < D; ++yy, ++t) Sn[t] = sv[1 + D + t] * rN - dl[x] * dl[yy];
+            R Lc[3][3];
+            bool pd;
+            if constexpr (sizeof(R) == 4)
+              pd = chol_whitened<D, R, float>(Sn, mun, c.meanf, c.scf, Lc);
+            else
+              pd = chol_whitened<D, R, double>(Sn, mun, c.mean, c.sc, Lc);
+            if (!pd) {
+              c.status |= GM_ST_COV_NOT_PD;
+              if (K > 1) {
+                removed = true;
+              } else {
+                c.pstate = 0;  // a lone component keeps its parameters
+                c.k = k + 1;
+              }
+            } else {
+              // eq. (omegak), then the renormalisation of step 3 through Z
+              const R wn = (K == 1) ? (R)1 : (Nk - (R)halfT) / ((R)c.Nd - (R)halfT * (R)K);
+              const R un = wn * c.Z;
+              c.Z = c.Z - c.u[k] + un;
+              c.u[k] = un;
+              float eA[NM], elc;
+              make_econst<D, R>(Lc, eA, elc);
+              for (int x = 0; x < D; ++x) {
+                c.mu[k][x] = mu64[x];
+                c.emu[k][x] = (float)mun[x];
+              }
+              for (int q = 0; q < NM; ++q) c.eA[k][q] = eA[q];
+              c.elc[k] = elc;
+              c.eb[k] = log2f((float)un) + elc;
+              pack_econst<D>(c.emu[k], c.eA[k], c.eb[k], c.ec[k]);
+              for (int q = 0; q < NC; ++q) c.ec[kMaxK][q] = c.ec[k][q];
+              c.pstate = 1;
+              c.k = k + 1;
+            }
+          }
+          if (removed) {
+            c.Z -= c.u[k];
+            for (int m = k; m < K - 1; ++m) {
+              c.u[m] = c.u[m + 1];
+              for (int x = 0; x < D; ++x) {
+                c.mu[m][x] = c.mu[m + 1][x];
+                c.emu[m][x] = c.emu[m + 1][x];
+              }
+              for (int q = 0; q < NM; ++q) c.eA[m][q] = c.eA[m + 1][q];
+              for (int q = 0; q < NC; ++q) c.ec[m][q] = c.ec[m + 1][q];
+              c.elc[m] = c.elc[m + 1];
+              c.eb[m] = c.eb[m + 1];
+            }
+            c.K = K - 1;
+            c.annih = 1;
+            c.pstate = 2;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    // normalise the weights, then the exact pass and the convergence test
+    if (tid < c.K) {
+      const R un = c.u[tid] / c.Z;
+      c.u[tid] = un;
+      c.eb[tid] = log2f((float)un) + c.elc[tid];
+      pack_econst<D>(c.emu[tid], c.eA[tid], c.eb[tid], c.ec[tid]);
+    }
+    __syncthreads();
+    if (tid == 0) c.Z = (R)1;
+    __syncthreads();
+    resync();
+    if (tid == 0) {
+      c.sweep = sweep;
+      if (!c.annih && fabs(c.L - c.Lprev) <= a.tol * fabs(c.Lprev)) c.done = 1;
+      c.Lprev = c.L;
+    }
+    __syncthreads();
+    if (c.done) break;
+  }
+  if (tid == 0 && !c.done) c.status |= GM_ST_EM_MAXSWEEPS;
+
+  // ---- final unpenalised step (Sec. 2.3.1), FP64 ---------------------------
+  if (tid == 0) c.Kf = 0;
+  __syncthreads();
+  {
+    const int K = c.K;
+    const double nw = c.Nd / c.W;
+    for (int k = 0; k < K; ++k) {
+      double ck[D];
+#pragma unroll
+      for (int q = 0; q < D; ++q) ck[q] = c.mu[k][q] * c.sc[q];
+      double acc[NS];
+#pragma unroll
+      for (int q = 0; q < NS; ++q) acc[q] = 0.0;
+      for (int p = tid; p < N; p += NT) {
+        float y[D], d[D];
+#pragma unroll
+        for (int q = 0; q < D; ++q) y[q] = Y[q * st + p];
+        float m = -3.0e38f;
+        for (int jj = 0; jj < K; ++jj) m = fmaxf(m, lg_eval<D>(c.emu[jj], c.eA[jj], c.eb[jj], y, d));
+        double Ssum = 0.0, gk = 0.0;
+        for (int jj = 0; jj < K; ++jj) {
+          const double g = (double)ex2(lg_eval<D>(c.emu[jj], c.eA[jj], c.eb[jj], y, d) - m);
+          Ssum += g;
+          if (jj == k) gk = g;
+        }
+        const double gam = a.alpha[off + p] * nw * gk / Ssum;
+        double dv[D];
+#pragma unroll
+        for (int q = 0; q < D; ++q) dv[q] = ((double)vin[(int64_t)q * a.n + off + p] - c.mean[q]) - ck[q];
+        acc[0] += gam;
+        int t = 1 + D;
+#pragma unroll
+        for (int x = 0; x < D; ++x) {
+          const double gd = gam * dv[x];
+          acc[1 + x] += gd;
+#pragma unroll
+          for (int yy = x; yy < D; ++yy, ++t) acc[t] += gd * dv[yy];
+        }
+      }
+      block_sum_d<D, NT, NS, R>(c, acc);
+      if (tid == 0 && c.res[0] > 0.0) {
+        const int f = c.Kf;
+        const double n = c.res[0];
+        double dl[D];
+        for (int x = 0; x < D; ++x) {
+          dl[x] = c.res[1 + x] / n;
+          c.fmu[f][x] = ck[x] + dl[x];
+        }
+        int t = 0;
+        for (int x = 0; x < D; ++x)
+          for (int yy = x; yy < D; ++yy, ++t) c.fS[f][t] = c.res[1 + D + t] / n - dl[x] * dl[yy];
+        c.fw[f] = n / c.Nd;
+        c.Kf = f + 1;
+      }
+      __syncthreads();
+    }
+  }
+  // ---- final parameters: E constants, Cholesky floor, eq. (lnL-GM) -------
+  if (tid == 0) {
+    const int Kf = c.Kf;
+    int pd = 1;
+    double one[D];
+    for (int d = 0; d < D; ++d) one[d] = 1.0;
+    for (int k = 0; k < Kf; ++k) {
+      // floor test in the original coordinates
+      double So[NM], mo[D], Lo[3][3];
+      for (int q = 0; q < NM; ++q) So[q] = c.fS[k][q];
+      for (int d = 0; d < D; ++d) mo[d] = 0.0;
+      double meano[D];
+      for (int d = 0; d < D; ++d) meano[d] = c.mean[d] + c.fmu[k][d];
+      if (!chol_whitened<D, double, double>(So, mo, meano, one, Lo)) pd = 0;
+      // whitened copy for the likelihood pass
+      double Sw[NM], mw[D], Lw[3][3];
+      for (int x = 0; x < D; ++x) {
+        mw[x] = c.fmu[k][x] * c.isc[x];
+        for (int yy = x; yy < D; ++yy) Sw[tri<D>(x, yy)] = c.fS[k][tri<D>(x, yy)] * c.isc[x] * c.isc[yy];
+      }
+      if (chol_whitened<D, double, double>(Sw, mw, c.mean, c.sc, Lw)) {
+        float eA[NM], elc;
+        make_econst<D, double>(Lw, eA, elc);
+        for (int q = 0; q < NM; ++q) c.eA[k][q] = eA[q];
+        c.elc[k] = elc;
+      } else {
+        pd = 0;
+      }
+      for (int x = 0; x < D; ++x) c.emu[k][x] = (float)mw[x];
+      c.eb[k] = log2f((float)c.fw[k]) + c.elc[k];
+      c.u[k] = (R)c.fw[k];
+      pack_econst<D>(c.emu[k], c.eA[k], c.eb[k], c.ec[k]);
+    }
+    if (!pd) c.status |= GM_ST_COV_NOT_PD;
+    c.final_pd = pd;
+    c.K = Kf;
+    c.Z = (R)1;
+  }
+  __syncthreads();
+  if (c.final_pd) resync();
+  if (tid == 0) {
+    const int Kf = c.K;
+    for (int k = 0; k < Kf; ++k) {
+      double* r = prm_out + (size_t)k * P;
+      r[0] = c.fw[k];
+      for (int d = 0; d < D; ++d) r[1 + d] = c.mean[d] + c.fmu[k][d];
+      for (int q = 0; q < NM; ++q) r[1 + D + q] = c.fS[k][q];
+    }
+    for (int i = Kf * P; i < a.Kmax * P; ++i) prm_out[i] = 0.0;
+    a.K_out[j] = Kf;
+    a.W_out[j] = c.W;
+    a.lnL_out[j] = c.final_pd ? c.L : 0.0;
+    if (a.sweeps_out) a.sweeps_out[j] = c.sweep;
+    if (a.kwork_out) a.kwork_out[j] = c.kwork;
+    a.status_out[j] = c.status;
+  }
+  __syncthreads();
+  (void)NW;
+}
+
+// ---------------------------------------------------------------------------
+// the kernel: work queue, per-cell moments, degenerate cells, dispatch of
+// the cell body on the shared or the global tile
+// ---------------------------------------------------------------------------
+template <int D, int NT, typename VT, typename R>
+__global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
+  constexpr int NW = NT / 32;
+  constexpr int NM = D * (D + 1) / 2;
+  constexpr int P = 1 + D + NM;
+  __shared__ EmCtl<D, NW, R> c;
+  extern __shared__ __align__(16) float tile_smem[];
+  const int tid = threadIdx.x;
   const VT* __restrict__ vin = static_cast<const VT*>(a.v);
 
   for (;;) {
-    if (tid == 0) {
-      const unsigned int t = atomicAdd(a.queue, 1u);
-      c.cell = (int64_t)t;
-    }
+    if (tid == 0) c.cell = (int64_t)atomicAdd(a.queue, 1u);
     __syncthreads();
     const int64_t j = c.cell;
     if (j >= a.C) break;
     const int64_t off = a.cell_off[j];
-    const int64_t N = a.cell_off[j + 1] - off;
+    const int N = (int)(a.cell_off[j + 1] - off);
     double* prm_out = a.params_out + (size_t)j * a.Kmax * P;
-
-    if (N == 0) {
-      for (int i = tid; i < a.Kmax * P; i += NT) prm_out[i] = 0.0;
-      if (tid == 0) {
-        a.K_out[j] = 0;
-        a.W_out[j] = 0.0;
-        a.lnL_out[j] = 0.0;
-        if (a.sweeps_out) a.sweeps_out[j] = 0;
-        if (a.kwork_out) a.kwork_out[j] = 0;
-        a.status_out[j] = GM_ST_EMPTY;
-      }
-      __syncthreads();
-      continue;
-    }
 
     // ---- total weight and weighted mean (FP64) ---------------------------
     {
       double acc[1 + D];
 #pragma unroll
       for (int i = 0; i <= D; ++i) acc[i] = 0.0;
-      for (int64_t p = tid; p < N; p += NT) {
+      for (int p = tid; p < N; p += NT) {
         const double al = a.alpha[off + p];
         acc[0] += al;
 #pragma unroll
@@ -233,15 +697,15 @@ __global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
       }
       __syncthreads();
     }
-    if (!(c.W > 0.0)) {
+    if (N == 0 || !(c.W > 0.0)) {
       for (int i = tid; i < a.Kmax * P; i += NT) prm_out[i] = 0.0;
       if (tid == 0) {
         a.K_out[j] = 0;
-        a.W_out[j] = c.W;
+        a.W_out[j] = N == 0 ? 0.0 : c.W;
         a.lnL_out[j] = 0.0;
         if (a.sweeps_out) a.sweeps_out[j] = 0;
         if (a.kwork_out) a.kwork_out[j] = 0;
-        a.status_out[j] = GM_ST_EMPTY | GM_ST_DEGENERATE;
+        a.status_out[j] = N == 0 ? GM_ST_EMPTY : (GM_ST_EMPTY | GM_ST_DEGENERATE);
       }
       __syncthreads();
       continue;
@@ -251,7 +715,7 @@ __global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
       double acc[NM];
 #pragma unroll
       for (int i = 0; i < NM; ++i) acc[i] = 0.0;
-      for (int64_t p = tid; p < N; p += NT) {
+      for (int p = tid; p < N; p += NT) {
         const double al = a.alpha[off + p];
         double dv[D];
 #pragma unroll
@@ -260,7 +724,7 @@ __global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
 #pragma unroll
         for (int x = 0; x < D; ++x)
 #pragma unroll
-          for (int y = x; y < D; ++y) acc[t++] += al * dv[x] * dv[y];
+          for (int y = x; y < D; ++y, ++t) acc[t] += al * dv[x] * dv[y];
       }
       block_sum_d<D, NT, NM, R>(c, acc);
       if (tid == 0) {
@@ -289,8 +753,6 @@ __global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
           c.degenerate = ok ? 0 : 1;
         }
         if (c.degenerate) {
-          c.fw[0] = 1.0;
-          for (int d = 0; d < D; ++d) c.fmu[0][d] = 0.0;
           for (int i = 0; i < NM; ++i) c.fS[0][i] = cov[i];
         } else {
           c.logjac = 0.0;
@@ -305,7 +767,7 @@ __global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
           // whitened total covariance (correlation matrix) for the init
           for (int x = 0; x < D; ++x)
             for (int y = x; y < D; ++y)
-              c.S[0][tri<D>(x, y)] = (x == y) ? 1.0 : cov[tri<D>(x, y)] * c.isc[x] * c.isc[y];
+              c.S0[tri<D>(x, y)] = (x == y) ? 1.0 : cov[tri<D>(x, y)] * c.isc[x] * c.isc[y];
         }
       }
       __syncthreads();
@@ -327,397 +789,11 @@ __global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
       __syncthreads();
       continue;
     }
-
-    // ---- stage whitened velocities and normalised weights ----------------
-    float* tb;
-    int64_t st;
-    if (N <= a.cap) {
-      tb = tile_smem;
-      st = a.cap;
-    } else {
-      tb = a.scratch + off;
-      st = a.n;
-    }
-    float* Y = tb;
-    float* AH = tb + D * st;
-    float* SS = tb + (D + 1) * st;
-    float* MM = tb + (D + 2) * st;
-    float* GG = tb + (D + 3) * st;
-    {
-      const double nw = c.Nd / c.W;
-      for (int64_t p = tid; p < N; p += NT) {
-#pragma unroll
-        for (int d = 0; d < D; ++d)
-          Y[d * st + p] = (float)(((double)vin[(int64_t)d * a.n + off + p] - c.mean[d]) * c.isc[d]);
-        AH[p] = (float)(a.alpha[off + p] * nw);
-      }
-    }
-    // ---- initialisation (Sec. 2.3): Kmax components at random particles --
-    if (tid == 0) {
-      int K = a.Kmax < N ? a.Kmax : (int)N;
-      while (K > 1 && c.Nd - halfT * K <= 0.0) --K;
-      int64_t picks[kMaxK];
-      int got = 0;
-      for (uint32_t t = 0; got < K; ++t) {
-        int64_t idx;
-        if (t < 100000u) {
-          const u32x4 r = philox_draw(a.seed, t, kTagInit, j);
-          const double uu = uniform52(r.x, r.y);
-          idx = (int64_t)floor(uu * c.Nd);
-          if (idx >= N) idx = N - 1;
-        } else {
-          idx = 0;
-          for (;;) {
-            bool used = false;
-            for (int m = 0; m < got; ++m) used |= (picks[m] == idx);
-            if (!used) break;
-            ++idx;
-          }
-        }
-        bool dup = false;
-        for (int m = 0; m < got; ++m) dup |= (picks[m] == idx);
-        if (!dup) picks[got++] = idx;
-      }
-      c.K = K;
-      c.Z = (R)1;
-      R Lc[3][3];
-      R S0[NM], m0[D];
-      for (int i = 0; i < NM; ++i) S0[i] = (R)c.S[0][i];
-      for (int d = 0; d < D; ++d) m0[d] = 0;
-      chol_whitened<D, R, double>(S0, m0, c.mean, c.sc, Lc);  // the total covariance passed above
-      float eA[NM], elc;
-      make_econst<D, R>(Lc, eA, elc);
-      double Stot[NM];
-      for (int i = 0; i < NM; ++i) Stot[i] = c.S[0][i];
-      for (int k = 0; k < K; ++k) {
-        c.u[k] = (R)1 / (R)K;
-        for (int d = 0; d < D; ++d) {
-          c.mu[k][d] = ((double)vin[(int64_t)d * a.n + off + picks[k]] - c.mean[d]) * c.isc[d];
-          c.emu[k][d] = (float)c.mu[k][d];
-        }
-        for (int i = 0; i < NM; ++i) c.eA[k][i] = eA[i];
-        c.elc[k] = elc;
-        c.eb[k] = log2f((float)c.u[k]) + elc;
-      }
-      c.sweep = 0;
-      c.kwork = 0;
-      c.done = 0;
-    }
-    __syncthreads();
-
-    // ---- exact pass: s_p, m_p and eq. (lnL-GM) ----------------------------
-    auto resync = [&]() {
-      const int K = c.K;
-      float acc = 0.0f;
-      for (int64_t p = tid; p < N; p += NT) {
-        float y[D], d[D];
-#pragma unroll
-        for (int q = 0; q < D; ++q) y[q] = Y[q * st + p];
-        float m = -3.0e38f, s = 0.0f;
-        for (int k = 0; k < K; ++k) {
-          const float l = lg_eval<D>(c.emu[k], c.eA[k], c.eb[k], y, d);
-          const float t = ex2(-fabsf(l - m));
-          s = (l > m) ? fmaf(s, t, 1.0f) : s + t;
-          m = fmaxf(m, l);
-        }
-        SS[p] = s;
-        MM[p] = m;
-        acc = fmaf(AH[p], m + lg2(s), acc);
-      }
-      double v1[1] = {(double)acc};
-      block_sum_d<D, NT, 1, R>(c, v1);
-      if (tid < 32) {
-        float pen = lane < K ? logf((float)(c.u[lane] / c.Z)) : 0.0f;
-        pen = warp_sum(pen);
-        if (lane == 0) {
-          const double dpar = (double)K * (T + 1) - 1.0;
-          c.L = c.res[0] * kLn2 - c.Nd * c.logjac - 0.5 * dpar * c.logN - 0.5 * T * (double)pen;
-        }
-      }
-      __syncthreads();
-    };
-
-    resync();
-    if (tid == 0) c.Lprev = c.L;
-    __syncthreads();
-
-    // ---- sweeps -----------------------------------------------------------
-    for (int sweep = 1; sweep <= a.max_sweeps; ++sweep) {
-      if (tid == 0) {
-        c.k = 0;
-        c.annih = 0;
-        c.pstate = 0;
-      }
-      __syncthreads();
-      while (c.k < c.K) {
-        const int k = c.k;
-        // E constants of component k and of the previous component's update
-        float kmu[D], kA[NM], pmu[D], pA[NM];
-#pragma unroll
-        for (int q = 0; q < D; ++q) { kmu[q] = c.emu[k][q]; pmu[q] = c.pmu[q]; }
-#pragma unroll
-        for (int q = 0; q < NM; ++q) { kA[q] = c.eA[k][q]; pA[q] = c.pA[q]; }
-        const float kb = c.eb[k], pb = c.pb;
-        const int ps = c.pstate;
-        float acc[NS];
-#pragma unroll
-        for (int q = 0; q < NS; ++q) acc[q] = 0.0f;
-        for (int64_t p = tid; p < N; p += NT) {
-          float y[D], d[D];
-#pragma unroll
-          for (int q = 0; q < D; ++q) y[q] = Y[q * st + p];
-          const float m = MM[p];
-          float s = SS[p];
-          if (ps == 1) {  // previous component updated
-            const float gn = ex2(fminf(lg_eval<D>(pmu, pA, pb, y, d) - m, 100.0f));
-            s = fmaxf(s - GG[p] + gn, gn);
-          } else if (ps == 2) {  // previous component removed
-            s = s - GG[p];
-          }
-          const float g = ex2(fminf(lg_eval<D>(kmu, kA, kb, y, d) - m, 100.0f));
-          GG[p] = g;
-          SS[p] = s;
-          const float den = fmaxf(fmaxf(s, g), 1e-30f);
-          const float gam = AH[p] * __fdividef(g, den);
-          acc[0] += gam;
-          int t = 1 + D;
-#pragma unroll
-          for (int x = 0; x < D; ++x) {
-            const float gd = gam * d[x];
-            acc[1 + x] += gd;
-#pragma unroll
-            for (int yy = x; yy < D; ++yy, ++t) acc[t] = fmaf(gd, d[yy], acc[t]);
-          }
-        }
-        // warp (FP32) then cross-warp (precision R) reduction
-#pragma unroll
-        for (int q = 0; q < NS; ++q) acc[q] = warp_sum(acc[q]);
-        if (lane == 0)
-#pragma unroll
-          for (int q = 0; q < NS; ++q) c.redf[wid][q] = acc[q];
-        __syncthreads();
-        if (tid < 32) {
-          R stat = 0;
-          if (lane < NS)
-            for (int q = 0; q < NW; ++q) stat += (R)c.redf[q][lane];
-          // thread 0 gathers the NS sums of its warp
-          R sv[NS];
-#pragma unroll
-          for (int q = 0; q < NS; ++q) sv[q] = __shfl_sync(0xffffffffu, stat, q);
-          if (lane == 0) {
-            // ---- M-step for component k (eqs. muk, sigmak, omegak) --------
-            c.kwork++;
-            const int K = c.K;
-            const R Nk = sv[0];
-            bool removed = false;
-            if (K > 1 && Nk - (R)halfT <= (R)0) {
-              removed = true;
-            } else {
-              const R rN = (R)1 / Nk;
-              R dl[D], mun[D], Sn[NM];
-              // The statistics are about the FP32 copy of the mean that the
-              // E-step used; the shift is added to the FP64 mean, which
-              // thereby keeps the sub-ulp part of every update (the FP32
-              // copy then follows the FP64 trajectory instead of stalling
-              // when an update is below its resolution).
-              double mu64[D];
-              for (int x = 0; x < D; ++x) {
-                dl[x] = sv[1 + x] * rN;
-                mu64[x] = c.mu[k][x] + (double)dl[x];
-                mun[x] = (R)mu64[x];
-              }
-              int t = 0;
-              for (int x = 0; x < D; ++x)
-                for (int yy = x; yy < D; ++yy, ++t) Sn[t] = sv[1 + D + t] * rN - dl[x] * dl[yy];
-              R Lc[3][3];
-              bool pd;
-              if constexpr (sizeof(R) == 4)
-                pd = chol_whitened<D, R, float>(Sn, mun, c.meanf, c.scf, Lc);
-              else
-                pd = chol_whitened<D, R, double>(Sn, mun, c.mean, c.sc, Lc);
-              if (!pd) {
-                c.status |= GM_ST_COV_NOT_PD;
-                if (K > 1) {
-                  removed = true;
-                } else {
-                  c.pstate = 0;  // a lone component keeps its parameters
-                  c.k = k + 1;
-                }
-              } else {
-                // eq. (omegak), then the renormalisation of step 3 through Z
-                const R wn = (K == 1) ? (R)1 : (Nk - (R)halfT) / ((R)c.Nd - (R)halfT * (R)K);
-                const R un = wn * c.Z;
-                c.Z = c.Z - c.u[k] + un;
-                c.u[k] = un;
-                float eA[NM], elc;
-                make_econst<D, R>(Lc, eA, elc);
-                for (int x = 0; x < D; ++x) {
-                  c.mu[k][x] = mu64[x];
-                  c.emu[k][x] = (float)mun[x];
-                  c.pmu[x] = (float)mun[x];
-                }
-                for (int q = 0; q < NM; ++q) {
-                  c.eA[k][q] = eA[q];
-                  c.pA[q] = eA[q];
-                }
-                c.elc[k] = elc;
-                c.eb[k] = log2f((float)un) + elc;
-                c.pb = c.eb[k];
-                c.pstate = 1;
-                c.k = k + 1;
-              }
-            }
-            if (removed) {
-              c.Z -= c.u[k];
-              for (int m = k; m < K - 1; ++m) {
-                c.u[m] = c.u[m + 1];
-                for (int x = 0; x < D; ++x) { c.mu[m][x] = c.mu[m + 1][x]; c.emu[m][x] = c.emu[m + 1][x]; }
-                for (int q = 0; q < NM; ++q) c.eA[m][q] = c.eA[m + 1][q];
-                c.elc[m] = c.elc[m + 1];
-                c.eb[m] = c.eb[m + 1];
-              }
-              c.K = K - 1;
-              c.annih = 1;
-              c.pstate = 2;
-            }
-          }
-        }
-        __syncthreads();
-      }
-      // normalise the weights, then the exact pass and the convergence test
-      if (tid < c.K) {
-        const R un = c.u[tid] / c.Z;
-        c.eb[tid] = log2f((float)un) + c.elc[tid];
-      }
-      __syncthreads();
-      if (tid < c.K) c.u[tid] = c.u[tid] / c.Z;
-      __syncthreads();
-      if (tid == 0) c.Z = (R)1;
-      __syncthreads();
-      resync();
-      if (tid == 0) {
-        c.sweep = sweep;
-        if (!c.annih && fabs(c.L - c.Lprev) <= a.tol * fabs(c.Lprev)) c.done = 1;
-        c.Lprev = c.L;
-      }
-      __syncthreads();
-      if (c.done) break;
-    }
-    if (tid == 0 && !c.done) c.status |= GM_ST_EM_MAXSWEEPS;
-
-    // ---- final unpenalised step (Sec. 2.3.1), FP64 -------------------------
-    if (tid == 0) c.Kf = 0;
-    __syncthreads();
-    {
-      const int K = c.K;
-      const double nw = c.Nd / c.W;
-      for (int k = 0; k < K; ++k) {
-        double ck[D];
-#pragma unroll
-        for (int q = 0; q < D; ++q) ck[q] = c.mu[k][q] * c.sc[q];
-        double acc[NS];
-#pragma unroll
-        for (int q = 0; q < NS; ++q) acc[q] = 0.0;
-        for (int64_t p = tid; p < N; p += NT) {
-          float y[D], d[D];
-#pragma unroll
-          for (int q = 0; q < D; ++q) y[q] = Y[q * st + p];
-          float m = -3.0e38f;
-          for (int jj = 0; jj < K; ++jj) m = fmaxf(m, lg_eval<D>(c.emu[jj], c.eA[jj], c.eb[jj], y, d));
-          double Ssum = 0.0, gk = 0.0;
-          for (int jj = 0; jj < K; ++jj) {
-            const double g = (double)ex2(lg_eval<D>(c.emu[jj], c.eA[jj], c.eb[jj], y, d) - m);
-            Ssum += g;
-            if (jj == k) gk = g;
-          }
-          const double gam = a.alpha[off + p] * nw * gk / Ssum;
-          double dv[D];
-#pragma unroll
-          for (int q = 0; q < D; ++q) dv[q] = ((double)vin[(int64_t)q * a.n + off + p] - c.mean[q]) - ck[q];
-          acc[0] += gam;
-          int t = 1 + D;
-#pragma unroll
-          for (int x = 0; x < D; ++x) {
-            const double gd = gam * dv[x];
-            acc[1 + x] += gd;
-#pragma unroll
-            for (int yy = x; yy < D; ++yy, ++t) acc[t] += gd * dv[yy];
-          }
-        }
-        block_sum_d<D, NT, NS, R>(c, acc);
-        if (tid == 0 && c.res[0] > 0.0) {
-          const int f = c.Kf;
-          const double n = c.res[0];
-          double dl[D];
-          for (int x = 0; x < D; ++x) {
-            dl[x] = c.res[1 + x] / n;
-            c.fmu[f][x] = ck[x] + dl[x];
-          }
-          int t = 0;
-          for (int x = 0; x < D; ++x)
-            for (int yy = x; yy < D; ++yy, ++t) c.fS[f][t] = c.res[1 + D + t] / n - dl[x] * dl[yy];
-          c.fw[f] = n / c.Nd;
-          c.Kf = f + 1;
-        }
-        __syncthreads();
-      }
-    }
-    // ---- final parameters: E constants, Cholesky floor, eq. (lnL-GM) -----
-    if (tid == 0) {
-      const int Kf = c.Kf;
-      int pd = 1;
-      double one[D];
-      for (int d = 0; d < D; ++d) one[d] = 1.0;
-      for (int k = 0; k < Kf; ++k) {
-        // floor test in the original coordinates
-        double So[NM], mo[D], Lo[3][3];
-        for (int q = 0; q < NM; ++q) So[q] = c.fS[k][q];
-        for (int d = 0; d < D; ++d) mo[d] = 0.0;
-        double meano[D];
-        for (int d = 0; d < D; ++d) meano[d] = c.mean[d] + c.fmu[k][d];
-        if (!chol_whitened<D, double, double>(So, mo, meano, one, Lo)) pd = 0;
-        // whitened copy for the likelihood pass
-        double Sw[NM], mw[D], Lw[3][3];
-        for (int x = 0; x < D; ++x) {
-          mw[x] = c.fmu[k][x] * c.isc[x];
-          for (int yy = x; yy < D; ++yy) Sw[tri<D>(x, yy)] = c.fS[k][tri<D>(x, yy)] * c.isc[x] * c.isc[yy];
-        }
-        if (chol_whitened<D, double, double>(Sw, mw, c.mean, c.sc, Lw)) {
-          float eA[NM], elc;
-          make_econst<D, double>(Lw, eA, elc);
-          for (int q = 0; q < NM; ++q) c.eA[k][q] = eA[q];
-          c.elc[k] = elc;
-        } else {
-          pd = 0;
-        }
-        for (int x = 0; x < D; ++x) c.emu[k][x] = (float)mw[x];
-        c.eb[k] = log2f((float)c.fw[k]) + c.elc[k];
-        c.u[k] = (R)c.fw[k];
-      }
-      if (!pd) c.status |= GM_ST_COV_NOT_PD;
-      c.final_pd = pd;
-      c.K = Kf;
-      c.Z = (R)1;
-    }
-    __syncthreads();
-    if (c.final_pd) resync();
-    if (tid == 0) {
-      const int Kf = c.K;
-      for (int k = 0; k < Kf; ++k) {
-        double* r = prm_out + (size_t)k * P;
-        r[0] = c.fw[k];
-        for (int d = 0; d < D; ++d) r[1 + d] = c.mean[d] + c.fmu[k][d];
-        for (int q = 0; q < NM; ++q) r[1 + D + q] = c.fS[k][q];
-      }
-      for (int i = Kf * P; i < a.Kmax * P; ++i) prm_out[i] = 0.0;
-      a.K_out[j] = Kf;
-      a.W_out[j] = c.W;
-      a.lnL_out[j] = c.final_pd ? c.L : 0.0;
-      if (a.sweeps_out) a.sweeps_out[j] = c.sweep;
-      if (a.kwork_out) a.kwork_out[j] = c.kwork;
-      a.status_out[j] = c.status;
-    }
-    __syncthreads();
+    if (N + (N & 1) <= a.cap)
+      em_cell_body<D, NT, VT, R>(a, c, j, off, N, tile_smem, a.cap);
+    else
+      em_cell_body<D, NT, VT, R>(a, c, j, off, N, a.scratch + scratch_offset(off, j),
+                                 (int)a.scratch_stride);
   }
 }
 

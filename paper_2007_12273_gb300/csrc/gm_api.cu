@@ -136,12 +136,17 @@ int gm_compress(const gm_config* cfg, int64_t C, int64_t n_particles, const int6
   int nt = cfg->threads_per_cell > 0 ? cfg->threads_per_cell : 256;
   if (nt != 128 && nt != 256) return fail(GM_ERR_ARG, "threads_per_cell must be 128 or 256");
   int cap = cfg->smem_particles > 0 ? cfg->smem_particles : (D == 1 ? 2560 : 4096);
+  cap &= ~1;  // the tile holds particle pairs
+  if (cap < 2) cap = 2;
   const size_t smem = (size_t)cap * (D + 4) * sizeof(float);
   if (smem > 200 * 1024) return fail(GM_ERR_ARG, "smem_particles too large (%d)", cap);
   const int fp64_mstep = (cfg->precision == 0) ? 1 : 0;
 
   const size_t q_bytes = 256, part_bytes = align256((size_t)3 * C * sizeof(double));
-  const size_t scr_bytes = align256((size_t)n_particles * (D + 4) * sizeof(float));
+  const int64_t sstride = gmcr::scratch_stride(n_particles, C);
+  if ((int64_t)(D + 4) * sstride >= ((int64_t)1 << 31))
+    return fail(GM_ERR_ARG, "too many particles for one call (%lld)", (long long)n_particles);
+  const size_t scr_bytes = align256((size_t)sstride * (D + 4) * sizeof(float));
   void* ws = nullptr;
   if ((rc = ws_get(q_bytes + part_bytes + scr_bytes, &ws))) return rc;
   char* wb = (char*)ws;
@@ -165,6 +170,7 @@ int gm_compress(const gm_config* cfg, int64_t C, int64_t n_particles, const int6
   p.kwork_out = kwork_out;
   p.status_out = status_out;
   p.scratch = scratch;
+  p.scratch_stride = sstride;
   p.queue = queue;
   p.Kmax = cfg->Kmax;
   p.max_sweeps = cfg->max_sweeps;
