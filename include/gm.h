@@ -146,6 +146,35 @@ int gm_mixture_moments(const gm_config* cfg, int64_t C, const int32_t* K, const 
                        const double* Wc, double* W, double* p, double* M2, double* E,
                        void* stream);
 
+/*
+ * gm_reconstruct_noalloc -- gm_reconstruct without any device allocation.
+ *
+ * The paper has no counterpart: this is a library-usage variant.  Some
+ * callers cannot allocate device memory while they run -- a host code whose
+ * device memory is owned by its own allocator or by a fixed budget, or one
+ * that must not pay the device-wide synchronisation that cudaFree/cudaMalloc
+ * imply (gm_reconstruct grows its workspace that way).  This entry point
+ * computes exactly what gm_reconstruct computes, with the same arguments,
+ * but takes its scratch from a fixed 5 MiB array that the library reserves
+ * statically on every GPU that loads it, held until the process exits.
+ *
+ * Limits and rules:
+ *  - at most 32768 cells per call (C > 32768 returns GM_ERR_ARG);
+ *  - the first call on a device looks up the array's device address (once
+ *    per device, with that device current); make that first call before any
+ *    stream capture;
+ *  - every call shares the one array: calls that overlap on the GPU (other
+ *    streams, other host threads) race and must be serialised by the
+ *    caller; the array keeps the last call's contents, and nothing in it has
+ *    to start at zero (each call writes every entry before reading it);
+ *  - no cudaMalloc, cudaFree or allocating library routine is called.
+ */
+int gm_reconstruct_noalloc(const gm_config* cfg, int64_t C, const int32_t* K, const double* params,
+                           const double* W, const double* rho_target, int64_t n_out,
+                           const int64_t* out_off, double* x_out, double* v_out,
+                           double* alpha_out, uint32_t* status_out, double* dA_out,
+                           void* stream);
+
 /* Description of the last error on this host thread ("" if none). */
 const char* gm_last_error(void);
 

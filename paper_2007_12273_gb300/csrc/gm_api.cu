@@ -94,6 +94,11 @@ int check_cfg(const gm_config* cfg) {
 
 }  // namespace
 
+int gmcr::record_error(int code, const char* msg) {
+  g_err = msg;
+  return code;
+}
+
 extern "C" {
 
 const char* gm_last_error(void) { return g_err.c_str(); }

@@ -26,6 +26,8 @@ cudaError_t launch_mixture_moments(int D, int64_t C, int Kmax, const int32_t* K,
                                    cudaStream_t s);
 
 int solve_blocks(int64_t C);
+// sets the calling thread's gm_last_error() text; returns code
+int record_error(int code, const char* msg);
 size_t reconstruct_ws_bytes(int D, int64_t C);
 cudaError_t launch_reconstruct(int D, int64_t C, int Kmax, const int32_t* K, const double* prm,
                                const double* W, const double* rho_target, int64_t n_out,

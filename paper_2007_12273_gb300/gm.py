@@ -27,7 +27,7 @@ ST_MM_EMPTY_COL = 0x400
 ST_NO_MIXTURE = 0x800
 
 EXPORTED = ("gm_compress", "gm_reconstruct", "gm_moments", "gm_mixture_moments",
-            "gm_last_error", "gm_shutdown")
+            "gm_last_error", "gm_shutdown", "gm_reconstruct_noalloc")
 
 
 class GMConfig(ct.Structure):
@@ -63,9 +63,11 @@ def load(build_if_missing: bool = False):
         P, I64, I32 = ct.c_void_p, ct.c_int64, ct.c_int32
         lib.gm_compress.argtypes = [P, I64, I64, P, P, P, I32, P, P, P, P, P, P, P, P, P, P]
         lib.gm_reconstruct.argtypes = [P, I64, P, P, P, P, I64, P, P, P, P, P, P, P]
+        lib.gm_reconstruct_noalloc.argtypes = [P, I64, P, P, P, P, I64, P, P, P, P, P, P, P]
         lib.gm_moments.argtypes = [P, I64, I64, P, P, P, I32, P, P, P, P, P, P, P]
         lib.gm_mixture_moments.argtypes = [P, I64, P, P, P, P, P, P, P, P]
-        for f in ("gm_compress", "gm_reconstruct", "gm_moments", "gm_mixture_moments", "gm_shutdown"):
+        for f in ("gm_compress", "gm_reconstruct", "gm_moments", "gm_mixture_moments", "gm_shutdown",
+                  "gm_reconstruct_noalloc"):
             getattr(lib, f).restype = ct.c_int
         lib.gm_last_error.restype = ct.c_char_p
         _lib = lib
@@ -178,6 +180,26 @@ def gm_reconstruct(cfg: GMConfig, K, params, W, rho_target, out_off, n_out: int 
                             _ptr(out["alpha"]), _ptr(out["status"]), _ptr(out.get("dA")),
                             _stream_ptr(stream))
     _rc(lib, rc, "gm_reconstruct")
+    return out
+
+
+def gm_reconstruct_noalloc(cfg: GMConfig, K, params, W, rho_target, out_off, out: dict,
+                           n_out: int, stream=None) -> dict:
+    """``gm_reconstruct`` without device allocation inside the library: the
+    scratch is the library's fixed static array (at most 32768 cells per
+    call) and every output tensor is supplied by the caller in ``out``
+    (keys x, v, alpha, status, optionally dA)."""
+    lib = load()
+    C = out_off.shape[0] - 1
+    for nm_, t_, dt in (("K", K, torch.int32), ("params", params, torch.float64),
+                        ("W", W, torch.float64), ("rho_target", rho_target, torch.float64),
+                        ("out_off", out_off, torch.int64)):
+        _check(t_, dt, nm_)
+    rc = lib.gm_reconstruct_noalloc(ct.byref(cfg), C, _ptr(K), _ptr(params), _ptr(W),
+                                    _ptr(rho_target), int(n_out), _ptr(out_off), _ptr(out["x"]),
+                                    _ptr(out["v"]), _ptr(out["alpha"]), _ptr(out["status"]),
+                                    _ptr(out.get("dA")), _stream_ptr(stream))
+    _rc(lib, rc, "gm_reconstruct_noalloc")
     return out
 
 
