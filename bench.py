@@ -374,7 +374,8 @@ def run_gmcr(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC if args.workload == "mixture_1d1v" else args.workload,
                    "cells": C, "particles": n, "D": D, "Kmax": cfg.Kmax, "init": "paper (random)",
-                   "precision": "fp64 m-step" if args.precision == 0 else "fp32 m-step",
+                   "precision": ("fp32 m-step, fp64 means and final step" if args.precision == 0
+                                 else "fp64 m-step"),
                    "l2": "inputs > L2 and a 252 MB flush between timed steps",
                    "parallelism": f"replicas x{world} (independent batches)"},
         "ms_compress": sum(t_comp) / args.steps, "ms_reconstruct": sum(t_rec) / args.steps,

@@ -64,9 +64,10 @@ typedef struct gm_config {
   int32_t threads_per_cell; /* EM CTA size: 0 = library choice, else 128 or 256 */
   int32_t smem_particles;   /* EM shared-memory tile in particles: 0 = library choice;
                                cells with more particles use an L2-resident global tile */
-  int32_t precision;        /* 0: FP64 cross-warp statistics and M-step (default);
-                               1: FP32 M-step during the penalised sweeps (the final
-                               unpenalised step stays FP64) */
+  int32_t precision;        /* penalised sweeps' M-step (covariance, Cholesky factor,
+                               inverse, weight): 0 = FP32 (default), 1 = FP64.  Either
+                               way the component means are accumulated in FP64 and the
+                               final unpenalised step is entirely FP64 */
   int32_t reserved;         /* must be 0 */
 } gm_config;
 
@@ -91,9 +92,10 @@ typedef struct gm_config {
  *      final parameters, with the normalised weights); sweeps_out [C] int32;
  *      kwork_out [C] int32 (component E-steps performed, may be NULL);
  *      status_out [C] uint32.
- * E-step densities and responsibilities are FP32; sufficient statistics
- * are promoted to FP64 at the warp reduction; parameters, Cholesky factors
- * and the whole final step are FP64.
+ * E-step densities and responsibilities are FP32; the per-component
+ * statistics are FP32 per thread and warp and summed across warps in the
+ * M-step's precision (cfg->precision); component means are accumulated in
+ * FP64; the whole final step (which makes the moments exact) is FP64.
  */
 int gm_compress(const gm_config* cfg, int64_t C, int64_t n_particles, const int64_t* cell_off,
                 const double* x, const void* v, int32_t v_is_f64, const double* alpha,

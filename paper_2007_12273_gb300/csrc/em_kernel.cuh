@@ -103,12 +103,43 @@ __device__ __forceinline__ int tri(int i, int j) {  // upper-triangle index, i <
   return D == 1 ? 0 : (i == 0 ? j : (i == 1 ? 2 + j : 5));
 }
 
+// Reciprocal and reciprocal square root for the one-thread M-step: an FP32
+// hardware seed refined by Newton steps (two in FP64: relative error about
+// 1e-16; one in FP32).  They avoid the long division / square-root
+// sequences on the M-step's critical path.
+__device__ __forceinline__ double rcp_nr(double x) {
+  if (!(fabs(x) > 1e-30 && fabs(x) < 1e30)) return 1.0 / x;  // outside the FP32 seed's range
+  double r = (double)rcp_approx((float)x);
+  r = r * (2.0 - x * r);
+  return r * (2.0 - x * r);
+}
+__device__ __forceinline__ float rcp_nr(float x) {
+  const float r = rcp_approx(x);
+  return r * (2.0f - x * r);
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);  // outside the FP32 seed's range
+  double y = (double)rsqrt_approx((float)x);
+  y = y * (1.5 - 0.5 * x * y * y);
+  return y * (1.5 - 0.5 * x * y * y);
+}
+__device__ __forceinline__ float rsqrt_nr(float x) {
+  const float y = rsqrt_approx(x);
+  return y * (1.5f - 0.5f * x * y * y);
+}
+
 // Cholesky of the upper-triangle S (precision R); returns false if a pivot
 // is not positive or, measured in the original coordinates (pivots scale by
-// sc_i^2), falls under 1e-13 * sum_d (Sigma_dd + mu_d^2).
+// sc_i^2), falls under 1e-13 * sum_d (Sigma_dd + mu_d^2).  Lc[i][i] holds the
+// pivot's square root and ri[i] its reciprocal.
 template <int D, typename R, typename M>
 __device__ bool chol_whitened(const R* S, const R* mu, const M* mean, const M* sc,
-                              R (&Lc)[3][3]) {
+                              R (&Lc)[3][3], R (&ri)[3]) {
   R scale2 = 0;
   for (int d = 0; d < D; ++d) {
     const R m = (R)mean[d] + (R)sc[d] * mu[d];
@@ -120,24 +151,32 @@ __device__ bool chol_whitened(const R* S, const R* mu, const M* mean, const M* s
       R s = S[tri<D>(j, i)];
       for (int m = 0; m < j; ++m) s -= Lc[i][m] * Lc[j][m];
       if (i == j) {
-        if (!(s * (R)(sc[i] * sc[i]) > fl) || !(s < (R)1e300)) return false;
-        Lc[i][i] = sqrt(s);
+        if (!(s * (R)(sc[i] * sc[i]) > fl) || !(s < (R)(sizeof(R) == 8 ? 1e300 : 1e30))) return false;
+        ri[i] = rsqrt_nr(s);
+        Lc[i][i] = s * ri[i];
       } else {
-        Lc[i][j] = s / Lc[j][j];
+        Lc[i][j] = s * ri[j];
       }
     }
   return true;
 }
+template <int D, typename R, typename M>
+__device__ bool chol_whitened(const R* S, const R* mu, const M* mean, const M* sc,
+                              R (&Lc)[3][3]) {
+  R ri[3];
+  return chol_whitened<D, R, M>(S, mu, mean, sc, Lc, ri);
+}
 
-// E-step constants of a component from its Cholesky factor
+// E-step constants of a component from its Cholesky factor (ri: reciprocal
+// diagonal)
 template <int D, typename R>
-__device__ void make_econst(const R (&Lc)[3][3], float* eA, float& elc) {
+__device__ void make_econst(const R (&Lc)[3][3], const R (&ri)[3], float* eA, float& elc) {
   const float c = 0.84932180028801904272f;  // sqrt(log2(e) / 2)
   if (D == 1) {
-    eA[0] = c / (float)Lc[0][0];
+    eA[0] = c * (float)ri[0];
     elc = -log2f((float)Lc[0][0]) - 0.5f * 2.6514961294723187f;  // log2(2 pi) / 2
   } else {
-    const R i00 = (R)1 / Lc[0][0], i11 = (R)1 / Lc[1][1], i22 = (R)1 / Lc[2][2];
+    const R i00 = ri[0], i11 = ri[1], i22 = ri[2];
     const R i10 = -Lc[1][0] * i00 * i11;
     const R i21 = -Lc[2][1] * i11 * i22;
     const R i20 = -(Lc[2][0] * i00 + Lc[2][1] * i10) * i22;
@@ -293,13 +332,13 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
     }
     c.K = K;
     c.Z = (R)1;
-    R Lc[3][3];
+    R Lc[3][3], ri[3];
     R S0[NM], m0[D];
     for (int i = 0; i < NM; ++i) S0[i] = (R)c.S0[i];
     for (int d = 0; d < D; ++d) m0[d] = 0;
-    chol_whitened<D, R, double>(S0, m0, c.mean, c.sc, Lc);  // the total covariance passed
+    chol_whitened<D, R, double>(S0, m0, c.mean, c.sc, Lc, ri);  // the total covariance passed
     float eA[NM], elc;
-    make_econst<D, R>(Lc, eA, elc);
+    make_econst<D, R>(Lc, ri, eA, elc);
     for (int k = 0; k < K; ++k) {
       c.u[k] = (R)1 / (R)K;
       for (int d = 0; d < D; ++d) {
@@ -445,7 +484,7 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
           if (K > 1 && Nk - (R)halfT <= (R)0) {
             removed = true;
           } else {
-            const R rN = (R)1 / Nk;
+            const R rN = rcp_nr(Nk);
             R dl[D], mun[D], Sn[NM];
             // The statistics are about the FP32 copy of the mean that the
             // E-step used; the shift is added to the FP64 mean, which
@@ -461,12 +500,12 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
             int t = 0;
             for (int x = 0; x < D; ++x)
               for (int yy = x; yy < D; ++yy, ++t) Sn[t] = sv[1 + D + t] * rN - dl[x] * dl[yy];
-            R Lc[3][3];
+            R Lc[3][3], ri[3];
             bool pd;
             if constexpr (sizeof(R) == 4)
-              pd = chol_whitened<D, R, float>(Sn, mun, c.meanf, c.scf, Lc);
+              pd = chol_whitened<D, R, float>(Sn, mun, c.meanf, c.scf, Lc, ri);
             else
-              pd = chol_whitened<D, R, double>(Sn, mun, c.mean, c.sc, Lc);
+              pd = chol_whitened<D, R, double>(Sn, mun, c.mean, c.sc, Lc, ri);
             if (!pd) {
               c.status |= GM_ST_COV_NOT_PD;
               if (K > 1) {
@@ -477,12 +516,13 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
               }
             } else {
               // eq. (omegak), then the renormalisation of step 3 through Z
-              const R wn = (K == 1) ? (R)1 : (Nk - (R)halfT) / ((R)c.Nd - (R)halfT * (R)K);
+              const R wn =
+                  (K == 1) ? (R)1 : (Nk - (R)halfT) * rcp_nr((R)c.Nd - (R)halfT * (R)K);
               const R un = wn * c.Z;
               c.Z = c.Z - c.u[k] + un;
               c.u[k] = un;
               float eA[NM], elc;
-              make_econst<D, R>(Lc, eA, elc);
+              make_econst<D, R>(Lc, ri, eA, elc);
               for (int x = 0; x < D; ++x) {
                 c.mu[k][x] = mu64[x];
                 c.emu[k][x] = (float)mun[x];
@@ -615,9 +655,10 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
         mw[x] = c.fmu[k][x] * c.isc[x];
         for (int yy = x; yy < D; ++yy) Sw[tri<D>(x, yy)] = c.fS[k][tri<D>(x, yy)] * c.isc[x] * c.isc[yy];
       }
-      if (chol_whitened<D, double, double>(Sw, mw, c.mean, c.sc, Lw)) {
+      double rw[3];
+      if (chol_whitened<D, double, double>(Sw, mw, c.mean, c.sc, Lw, rw)) {
         float eA[NM], elc;
-        make_econst<D, double>(Lw, eA, elc);
+        make_econst<D, double>(Lw, rw, eA, elc);
         for (int q = 0; q < NM; ++q) c.eA[k][q] = eA[q];
         c.elc[k] = elc;
       } else {
