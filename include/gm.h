@@ -177,6 +177,22 @@ int gm_reconstruct_noalloc(const gm_config* cfg, int64_t C, const int32_t* K, co
                            double* alpha_out, uint32_t* status_out, double* dA_out,
                            void* stream);
 
+/*
+ * gm_gemm_bf16 -- C[M,N] = A[M,K] B[N,K]^T (+ bias[N]) (ReLU if relu != 0)
+ * (entries set to 0 where mask[row * ldm + col] <= 0, if mask != NULL), on
+ * the tcgen05 tensor cores with FP32 accumulation.  Used by the learned
+ * initialisation network (not part of the paper's method).
+ *
+ * A, B: BF16, row-major with K contiguous, leading dimensions lda, ldb
+ * (multiples of 8, >= K), 16-byte aligned; bias: FP32 [N] or NULL; mask:
+ * BF16 [M][ldm] or NULL; outputs C_f32 (FP32) and/or C_bf16 (BF16), row
+ * stride ldc.  err (device, may be NULL) gets bit 0 set if a tensor-core
+ * completion wait timed out (results then undefined).
+ */
+int gm_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, int32_t lda, const void* B,
+                 int32_t ldb, const float* bias, int32_t relu, const void* mask, int32_t ldm,
+                 float* C_f32, void* C_bf16, int32_t ldc, uint32_t* err, void* stream);
+
 /* Description of the last error on this host thread ("" if none). */
 const char* gm_last_error(void);
 

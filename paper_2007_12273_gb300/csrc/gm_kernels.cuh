@@ -35,4 +35,10 @@ cudaError_t launch_reconstruct(int D, int64_t C, int Kmax, const int32_t* K, con
                                int order, double* x_out, double* v_out, double* alpha_out,
                                uint32_t* status_out, double* dA_user, void* ws, cudaStream_t s);
 
+// BF16 tcgen05 GEMM: C = A B^T (+bias, ReLU, mask), see tc_gemm.cu
+size_t tc_gemm_smem(int bn);
+cudaError_t launch_tc_gemm(const void* A, const void* B, int M, int N, int K, int lda, int ldb,
+                           const float* bias, int relu, const void* mask, int ldm, float* Cf,
+                           void* Cb, int ldc, unsigned int* err, cudaStream_t s);
+
 }  // namespace gmcr

@@ -27,7 +27,7 @@ ST_MM_EMPTY_COL = 0x400
 ST_NO_MIXTURE = 0x800
 
 EXPORTED = ("gm_compress", "gm_reconstruct", "gm_moments", "gm_mixture_moments",
-            "gm_last_error", "gm_shutdown", "gm_reconstruct_noalloc")
+            "gm_last_error", "gm_shutdown", "gm_reconstruct_noalloc", "gm_gemm_bf16")
 
 
 class GMConfig(ct.Structure):
@@ -66,8 +66,9 @@ def load(build_if_missing: bool = False):
         lib.gm_reconstruct_noalloc.argtypes = [P, I64, P, P, P, P, I64, P, P, P, P, P, P, P]
         lib.gm_moments.argtypes = [P, I64, I64, P, P, P, I32, P, P, P, P, P, P, P]
         lib.gm_mixture_moments.argtypes = [P, I64, P, P, P, P, P, P, P, P]
+        lib.gm_gemm_bf16.argtypes = [I32, I32, I32, P, I32, P, I32, P, I32, P, I32, P, P, I32, P, P]
         for f in ("gm_compress", "gm_reconstruct", "gm_moments", "gm_mixture_moments", "gm_shutdown",
-                  "gm_reconstruct_noalloc"):
+                  "gm_reconstruct_noalloc", "gm_gemm_bf16"):
             getattr(lib, f).restype = ct.c_int
         lib.gm_last_error.restype = ct.c_char_p
         _lib = lib
@@ -238,3 +239,23 @@ def gm_mixture_moments(cfg: GMConfig, K, params, W, stream=None) -> dict:
                                 _stream_ptr(stream))
     _rc(lib, rc, "gm_mixture_moments")
     return out
+
+
+def gm_gemm_bf16(A, B, bias=None, relu=False, mask=None, out_f32=None, out_bf16=None,
+                 err=None, stream=None):
+    """C = A B^T (+bias) (ReLU) (mask) on the tcgen05 tensor cores.  A [M,K],
+    B [N,K] bf16 (row-major, K contiguous); returns the FP32 output (or the
+    BF16 one if only that is requested)."""
+    lib = load()
+    M, K = A.shape
+    N = B.shape[0]
+    _check(A, torch.bfloat16, "A")
+    _check(B, torch.bfloat16, "B")
+    if out_f32 is None and out_bf16 is None:
+        out_f32 = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    ldc = (out_f32 if out_f32 is not None else out_bf16).stride(0)
+    rc = lib.gm_gemm_bf16(M, N, K, _ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(bias),
+                          1 if relu else 0, _ptr(mask), mask.stride(0) if mask is not None else 0,
+                          _ptr(out_f32), _ptr(out_bf16), ldc, _ptr(err), _stream_ptr(stream))
+    _rc(lib, rc, "gm_gemm_bf16")
+    return out_f32 if out_f32 is not None else out_bf16

@@ -1,0 +1,44 @@
+"""The tcgen05 BF16 GEMM (C = A B^T + bias, ReLU, mask) against a plain FP32
+matmul of the same BF16 inputs (CPU)."""
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gm():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    from paper_2007_12273_gb300 import build, gm as gm_
+    build.build()
+    gm_.load()
+    return gm_
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 32, 64), (128, 256, 64), (256, 256, 576), (300, 112, 130),
+                                   (1000, 300, 256), (64, 16, 8)])
+def test_gemm_matches_fp32_reference(gm, M, N, K):
+    g = torch.Generator().manual_seed(M * 7 + N * 3 + K)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16)
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16)
+    bias = torch.randn(N, generator=g)
+    ref = A.float() @ B.float().T + bias
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    C = gm.gm_gemm_bf16(A.cuda(), B.cuda(), bias=bias.cuda(), err=err)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    torch.testing.assert_close(C.cpu(), ref, rtol=1e-4, atol=1e-3 * K ** 0.5)
+
+
+def test_gemm_relu_mask_and_bf16_output(gm):
+    g = torch.Generator().manual_seed(1)
+    M, N, K = 256, 128, 192
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16)
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16)
+    mask = (torch.rand(M, N, generator=g) > 0.5).to(torch.bfloat16)
+    ref = torch.relu(A.float() @ B.float().T) * (mask.float() > 0)
+    outb = torch.empty(M, N, dtype=torch.bfloat16, device="cuda")
+    C = gm.gm_gemm_bf16(A.cuda(), B.cuda(), relu=True, mask=mask.cuda(), out_bf16=outb)
+    torch.cuda.synchronize()
+    torch.testing.assert_close(C.float().cpu(), ref.to(torch.bfloat16).float(), rtol=1e-2, atol=1e-2)
