@@ -249,8 +249,9 @@ def gm_gemm_bf16(A, B, bias=None, relu=False, mask=None, out_f32=None, out_bf16=
     lib = load()
     M, K = A.shape
     N = B.shape[0]
-    _check(A, torch.bfloat16, "A")
-    _check(B, torch.bfloat16, "B")
+    for t_, nm_ in ((A, "A"), (B, "B")):
+        if not t_.is_cuda or t_.dtype != torch.bfloat16 or t_.stride(1) != 1:
+            raise ValueError(f"{nm_} must be a CUDA bf16 matrix with unit column stride")
     if out_f32 is None and out_bf16 is None:
         out_f32 = torch.empty((M, N), dtype=torch.float32, device=A.device)
     ldc = (out_f32 if out_f32 is not None else out_bf16).stride(0)

@@ -25,7 +25,13 @@ def test_gemm_matches_fp32_reference(gm, M, N, K):
     bias = torch.randn(N, generator=g)
     ref = A.float() @ B.float().T + bias
     err = torch.zeros(1, dtype=torch.int32, device="cuda")
-    C = gm.gm_gemm_bf16(A.cuda(), B.cuda(), bias=bias.cuda(), err=err)
+    # operands in row-padded storage (leading dimension a multiple of 8)
+    Kp = (K + 7) // 8 * 8
+    Ad = torch.zeros(M, Kp, dtype=torch.bfloat16, device="cuda")
+    Bd = torch.zeros(N, Kp, dtype=torch.bfloat16, device="cuda")
+    Ad[:, :K] = A.cuda()
+    Bd[:, :K] = B.cuda()
+    C = gm.gm_gemm_bf16(Ad[:, :K], Bd[:, :K], bias=bias.cuda(), err=err)
     torch.cuda.synchronize()
     assert int(err.item()) == 0
     torch.testing.assert_close(C.cpu(), ref, rtol=1e-4, atol=1e-3 * K ** 0.5)
