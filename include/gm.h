@@ -193,6 +193,104 @@ int gm_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, int32_t lda, co
                  int32_t ldb, const float* bias, int32_t relu, const void* mask, int32_t ldm,
                  float* C_f32, void* C_bf16, int32_t ldc, uint32_t* err, void* stream);
 
+/*
+ * gm_compress_from -- gm_compress started from given initial mixtures
+ * instead of the paper's random initialisation (Sec. 2.3); used by the
+ * learned initialisation.  init_K [C] int32 and init_params [C][Kmax][P]
+ * f64 (original coordinates, gm_compress's record layout).  Components
+ * whose covariance fails the Cholesky floor are dropped, the count is
+ * capped so that N - T K / 2 > 0, and a cell left with none falls back to
+ * the random initialisation.  Everything after the initialisation is the
+ * paper's method, as in gm_compress.
+ */
+int gm_compress_from(const gm_config* cfg, int64_t C, int64_t n_particles,
+                     const int64_t* cell_off, const double* x, const void* v, int32_t v_is_f64,
+                     const double* alpha, const int32_t* init_K, const double* init_params,
+                     int32_t* K_out, double* params_out, double* W_out, double* rho_target_out,
+                     double* lnL_out, int32_t* sweeps_out, int32_t* kwork_out,
+                     uint32_t* status_out, void* stream);
+
+/*
+ * Learned initialisation (not in the paper).  A small network maps per-cell
+ * features to an initial mixture from which gm_compress_from runs the
+ * paper's EM.
+ *
+ * Features of a cell (gm_features): with W = sum alpha, the alpha-weighted
+ * mean and per-dimension standard deviation sd (written to wstat [C][2D]:
+ * mean, then sd), y = (v - mean)/sd and alpha-weighted expectations E[.]:
+ *   D = 1: [E y^3, E y^4 - 3, ln(N)/10, 64-bin histogram of y on [-4, 4)]
+ *   D = 3: [E y_d^3 (3), E y_d^4 - 3 (3), E y0y1, E y0y2, E y1y2, ln(N)/10,
+ *           8x8x8 histogram of y on [-2.5, 2.5)^3, index b0*64 + b1*8 + b2]
+ * (histogram entry = alpha mass in the bin / W * number of bins; values
+ * outside the range go to the edge bins), zero-padded to F = 128 (D = 1) or
+ * 576 (D = 3), BF16 [C][F].
+ *
+ * Network: h1 = relu(x W1^T + b1), h2 = relu(h1 W2^T + b2),
+ * h3 = relu(h2 W3^T + b3), out = h3 W4^T + b4 (FP32 [M][O]); hidden width
+ * H = 256.  out holds Kmax slots of SP = 2 + 2D + D(D-1)/2 values
+ * [presence logit, log weight, mu (D), log diag of L (D), L10, L20, L21] in
+ * the whitened coordinates y (Sigma = L L^T), O = Kmax SP rounded up to a
+ * multiple of 16.
+ */
+typedef struct gm_mlp {
+  int32_t D, Kmax;  /* velocity dimensions, slots */
+  int32_t F, H, O;  /* widths: features, hidden, output */
+  float* W[4];      /* FP32 master weights, row-major [out][in]: HxF, HxH, HxH, OxH */
+  float* b[4];      /* FP32 biases [out] */
+  void* W16[4];     /* BF16 copies [out][in] */
+  void* WT16[4];    /* BF16 transposes [in][out] */
+  float* gW[4];     /* gradients (written by gm_mlp_train_step) */
+  float* gb[4];
+  float* mW[4];     /* Adam first / second moments */
+  float* vW[4];
+  float* mb[4];
+  float* vb[4];
+} gm_mlp;
+
+/* Features (see above) of every cell; wstat [C][2D] gets mean and sd. */
+int gm_features(const gm_config* cfg, int64_t C, int64_t n_particles, const int64_t* cell_off,
+                const void* v, int32_t v_is_f64, const double* alpha, void* feat, double* wstat,
+                void* stream);
+
+/* Training targets from fits (K, params: gm_compress outputs) and the
+ * cells' wstat: components sorted by whitened mu_0; slot s < K gets
+ * presence 1 and [ln w, mu, ln diag L, L10, L20, L21] of the whitened
+ * component, slots s >= K presence 0.  T, Mk: FP32 [C][O]; Mk marks the
+ * entries that enter the loss. */
+int gm_mlp_targets(const gm_config* cfg, int64_t C, const int32_t* K, const double* params,
+                   const double* wstat, int32_t O, float* T, float* Mk, void* stream);
+
+/* BF16 copies and transposes of the FP32 master weights (after the caller
+ * sets or loads W). */
+int gm_mlp_sync(const gm_mlp* net, void* stream);
+
+/* Device scratch that gm_mlp_forward / gm_mlp_train_step need for M rows. */
+size_t gm_mlp_scratch_bytes(const gm_mlp* net, int32_t M);
+
+/* out [M][O] = network(X [M][F] BF16).  M any. */
+int gm_mlp_forward(const gm_mlp* net, int32_t M, const void* X, void* scratch,
+                   size_t scratch_bytes, float* out, uint32_t* err, void* stream);
+
+/* One training step on a batch of M rows (M a multiple of 64): forward,
+ * loss (mean over rows: sum over slots of softplus(p) - t p on presence
+ * logits plus squared errors on the entries Mk marks) added to *loss
+ * (device FP64), backward into net->gW / net->gb, and, if lr > 0, an Adam
+ * update (beta1 0.9, beta2 0.999, eps 1e-8, bias correction with step
+ * number `step` >= 1) that also refreshes the BF16 copies. */
+int gm_mlp_train_step(const gm_mlp* net, int32_t M, const void* X, const float* T,
+                      const float* Mk, float lr, int32_t step, void* scratch,
+                      size_t scratch_bytes, float* out, double* loss, uint32_t* err,
+                      void* stream);
+
+/* Initial mixtures from the network's output: slots with a positive
+ * presence logit (at least the most likely one), capped so that
+ * N - T K0 / 2 > 0 by dropping the smallest log weights; weights by softmax
+ * of the log weights; mu = mean + sd * mu_w, Sigma = diag(sd) L L^T diag(sd)
+ * with ln diag L clamped to [-10, 5].  K0 [C], init_params [C][Kmax][P]. */
+int gm_mlp_decode(const gm_config* cfg, int64_t C, const float* out, int32_t O,
+                  const double* wstat, const int64_t* cell_off, int32_t* K0, double* init_params,
+                  void* stream);
+
 /* Description of the last error on this host thread ("" if none). */
 const char* gm_last_error(void);
 

@@ -62,7 +62,7 @@ def _load():
             lib.oracle_philox4x32_10.argtypes = [P, P, P]
             lib.oracle_uniform52.argtypes = [ct.c_uint32, ct.c_uint32]
             lib.oracle_uniform52.restype = ct.c_double
-            lib.oracle_compress.argtypes = [P, ct.c_int64] + [P] * 13 + [ct.c_int]
+            lib.oracle_compress.argtypes = [P, ct.c_int64] + [P] * 15 + [ct.c_int]
             lib.oracle_em_cell.argtypes = [P, ct.c_int64, ct.c_int64, P, P, P, ct.c_int, ct.c_int,
                                            P, P, P, P, P, P, P, P, ct.c_int, P]
             lib.oracle_penalised_L.argtypes = [ct.c_int, ct.c_int, P, ct.c_int64, P, P]
@@ -117,7 +117,8 @@ def max_threads() -> int:
     return _load().oracle_max_threads()
 
 
-def compress(params: dict, cell_off, x, v, alpha, nthreads: int = 1, cell_ids=None) -> dict:
+def compress(params: dict, cell_off, x, v, alpha, nthreads: int = 1, cell_ids=None,
+             init_K=None, init_params=None) -> dict:
     """Oracle compression of every cell (Sec. 2.2-2.3, final step of
     Sec. 2.3.1, target charge density of Sec. 2.4.1).  ``cell_ids`` gives
     each cell's index in a larger batch (it keys the initial picks); the
@@ -138,6 +139,8 @@ def compress(params: dict, cell_off, x, v, alpha, nthreads: int = 1, cell_ids=No
                              _ptr(out["rho_target"]), _ptr(out["lnL"]), _ptr(out["sweeps"]),
                              _ptr(out["kwork"]), _ptr(out["status"]),
                              _ptr(None if cell_ids is None else np.ascontiguousarray(cell_ids, dtype=np.int64)),
+                             _ptr(None if init_K is None else np.ascontiguousarray(init_K, dtype=np.int32)),
+                             _ptr(None if init_params is None else _f64(init_params)),
                              int(nthreads))
     if rc != 0:
         raise ValueError(f"oracle_compress failed ({rc})")

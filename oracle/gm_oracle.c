@@ -275,10 +275,22 @@ static void em_cell(const oracle_cfg *cfg, int64_t cell, int64_t N, const double
     }
   }
 
-  if (init_prm) {
-    K = init_K;
+  K = 0;
+  if (init_prm && init_K > 0) {
+    /* a supplied initial mixture (learned initialisation): components whose
+     * covariance fails the Cholesky floor are dropped, the count is capped
+     * so that N - T K / 2 > 0 (last components dropped), and an empty
+     * result falls back to the random initialisation below */
+    K = init_K < cfg->Kmax ? init_K : cfg->Kmax;
     load_params(D, K, init_prm, cs);
-  } else {
+    for (int k = 0; k < K; ++k)
+      if (!chol_floor(D, cs[k].S, cs[k].mu, cs[k].Lc, &cs[k].logdet) || !(cs[k].w > 0.0)) {
+        remove_comp(&K, cs, k);
+        --k;
+      }
+    while (K > 1 && Nd - halfT * K <= 0.0) --K;
+  }
+  if (K == 0) {
     /* Initialisation (Sec. 2.3): K ~ Kmax components, each mean a randomly
      * chosen particle, each covariance the total covariance, equal weights.
      * Reading: K0 = min(Kmax, N), lowered while N - T K/2 <= 0 so that the
@@ -315,14 +327,8 @@ static void em_cell(const oracle_cfg *cfg, int64_t cell, int64_t N, const double
       memcpy(cs[k].S, cov, sizeof(cov));
     }
   }
-  for (int k = 0; k < K; ++k) {
-    if (!chol_floor(D, cs[k].S, cs[k].mu, cs[k].Lc, &cs[k].logdet)) {
-      /* cannot happen for the random init (the total covariance passed);
-       * for a supplied init, drop the component */
-      remove_comp(&K, cs, k); --k; o->status |= ST_COV_NOT_PD;
-    }
-  }
-  if (K == 0) { free(ah); free(gam); o->status |= ST_DEGENERATE; return; }
+  for (int k = 0; k < K; ++k) /* Cholesky factors of the initial covariances */
+    chol_floor(D, cs[k].S, cs[k].mu, cs[k].Lc, &cs[k].logdet);
   renormalise(K, cs);
 
   double Lprev = penalised_L(D, K, cs, N, vv, ah);
@@ -484,7 +490,8 @@ int oracle_compress(const oracle_cfg *cfg, int64_t C, const int64_t *cell_off,
                     int32_t *K_out, double *params_out, double *W_out,
                     double *rho_target_out, double *lnL_out, int32_t *sweeps_out,
                     int32_t *kwork_out, uint32_t *status_out, const int64_t *cell_ids,
-                    int nthreads) {
+                    const int32_t *init_K /* [C] or NULL */,
+                    const double *init_params /* [C][Kmax][P] or NULL */, int nthreads) {
   const int D = cfg->D;
   if (D != 1 && D != 3) return -1;
   if (cfg->Kmax < 1 || cfg->Kmax > OR_MAXK) return -1;
@@ -504,7 +511,8 @@ int oracle_compress(const oracle_cfg *cfg, int64_t C, const int64_t *cell_off,
      * keys its Philox stream */
     em_cell(cfg, cell_ids ? cell_ids[j] : j, n, vv, alpha + cell_off[j],
             params_out + (size_t)j * cfg->Kmax * P, &o,
-            NULL, 0, 0, NULL, NULL, 0, NULL);
+            init_K ? init_params + (size_t)j * cfg->Kmax * P : NULL, init_K ? init_K[j] : 0, 0,
+            NULL, NULL, 0, NULL);
     K_out[j] = o.K; W_out[j] = o.W; lnL_out[j] = o.lnL;
     if (sweeps_out) sweeps_out[j] = o.sweeps;
     if (kwork_out) kwork_out[j] = o.kwork;

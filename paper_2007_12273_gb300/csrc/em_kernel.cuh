@@ -42,6 +42,8 @@ struct EmParams {
   int32_t* sweeps_out;
   int32_t* kwork_out;
   uint32_t* status_out;
+  const int32_t* init_K;   // optional initial mixtures (original coordinates)
+  const double* init_prm;  // [C][Kmax][P]
   float* scratch;          // global tile for cells larger than the shared one
   int64_t scratch_stride;  // floats per array of the global tile (even)
   unsigned int* queue;
@@ -304,8 +306,52 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
       }
     }
   }
-  // ---- initialisation (Sec. 2.3): Kmax components at random particles ----
+  // ---- initialisation --------------------------------------------------
+  // A supplied initial mixture (learned initialisation) is used when given:
+  // components failing the Cholesky floor are dropped, the count is capped
+  // so that N - T K / 2 > 0, and an empty result falls back to the paper's
+  // initialisation (Sec. 2.3): Kmax components at random particles.
   if (tid == 0) {
+    int K = 0;
+    if (a.init_K) {
+      const int K0 = a.init_K[j] < a.Kmax ? a.init_K[j] : a.Kmax;
+      double wsum = 0.0;
+      for (int k = 0; k < K0; ++k) {
+        const double* r = a.init_prm + ((size_t)j * a.Kmax + k) * P;
+        double mw[D], Sw[NM], Lw[3][3], rw[3];
+        for (int d = 0; d < D; ++d) mw[d] = (r[1 + d] - c.mean[d]) * c.isc[d];
+        int q = 0;
+        for (int x = 0; x < D; ++x)
+          for (int yy = x; yy < D; ++yy, ++q) Sw[q] = r[1 + D + q] * c.isc[x] * c.isc[yy];
+        if (!(r[0] > 0.0) || !chol_whitened<D, double, double>(Sw, mw, c.mean, c.sc, Lw, rw))
+          continue;
+        float eA[NM], elc;
+        make_econst<D, double>(Lw, rw, eA, elc);
+        for (int d = 0; d < D; ++d) {
+          c.mu[K][d] = mw[d];
+          c.emu[K][d] = (float)mw[d];
+        }
+        for (int i = 0; i < NM; ++i) c.eA[K][i] = eA[i];
+        c.elc[K] = elc;
+        c.u[K] = (R)r[0];
+        wsum += r[0];
+        ++K;
+      }
+      while (K > 1 && c.Nd - halfT * K <= 0.0) {
+        --K;
+        wsum -= (double)c.u[K];
+      }
+      for (int k = 0; k < K; ++k) {
+        c.u[k] = (R)((double)c.u[k] / wsum);
+        c.eb[k] = log2f((float)c.u[k]) + c.elc[k];
+        pack_econst<D>(c.emu[k], c.eA[k], c.eb[k], c.ec[k]);
+      }
+      c.K = K;
+      c.Z = (R)1;
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && c.K == 0) {
     int K = a.Kmax < N ? a.Kmax : N;
     while (K > 1 && c.Nd - halfT * K <= 0.0) --K;
     int picks[kMaxK];
@@ -350,6 +396,8 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
       c.eb[k] = log2f((float)c.u[k]) + elc;
       pack_econst<D>(c.emu[k], c.eA[k], c.eb[k], c.ec[k]);
     }
+  }
+  if (tid == 0) {
     c.sweep = 0;
     c.kwork = 0;
     c.done = 0;
@@ -830,6 +878,8 @@ __global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
       __syncthreads();
       continue;
     }
+    if (tid == 0) c.K = 0;
+    __syncthreads();
     if (N + (N & 1) <= a.cap)
       em_cell_body<D, NT, VT, R>(a, c, j, off, N, tile_smem, a.cap);
     else

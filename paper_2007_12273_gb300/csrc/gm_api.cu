@@ -118,11 +118,12 @@ int gm_shutdown(void) {
   return GM_OK;
 }
 
-int gm_compress(const gm_config* cfg, int64_t C, int64_t n_particles, const int64_t* cell_off,
-                const double* x, const void* v, int32_t v_is_f64, const double* alpha,
-                int32_t* K_out, double* params_out, double* W_out, double* rho_target_out,
-                double* lnL_out, int32_t* sweeps_out, int32_t* kwork_out, uint32_t* status_out,
-                void* stream) {
+static int compress_impl(const gm_config* cfg, int64_t C, int64_t n_particles,
+                         const int64_t* cell_off, const double* x, const void* v, int32_t v_is_f64,
+                         const double* alpha, const int32_t* init_K, const double* init_params,
+                         int32_t* K_out, double* params_out, double* W_out,
+                         double* rho_target_out, double* lnL_out, int32_t* sweeps_out,
+                         int32_t* kwork_out, uint32_t* status_out, void* stream) {
   g_err.clear();
   int rc = check_cfg(cfg);
   if (rc) return rc;
@@ -174,6 +175,8 @@ int gm_compress(const gm_config* cfg, int64_t C, int64_t n_particles, const int6
   p.sweeps_out = sweeps_out;
   p.kwork_out = kwork_out;
   p.status_out = status_out;
+  p.init_K = init_K;
+  p.init_prm = init_params;
   p.scratch = scratch;
   p.scratch_stride = sstride;
   p.queue = queue;
@@ -194,6 +197,28 @@ int gm_compress(const gm_config* cfg, int64_t C, int64_t n_particles, const int6
                            part, rho_target_out, s);
   if (e != cudaSuccess) return cuda_fail(e, "deposit launch");
   return GM_OK;
+}
+
+int gm_compress(const gm_config* cfg, int64_t C, int64_t n_particles, const int64_t* cell_off,
+                const double* x, const void* v, int32_t v_is_f64, const double* alpha,
+                int32_t* K_out, double* params_out, double* W_out, double* rho_target_out,
+                double* lnL_out, int32_t* sweeps_out, int32_t* kwork_out, uint32_t* status_out,
+                void* stream) {
+  return compress_impl(cfg, C, n_particles, cell_off, x, v, v_is_f64, alpha, nullptr, nullptr,
+                       K_out, params_out, W_out, rho_target_out, lnL_out, sweeps_out, kwork_out,
+                       status_out, stream);
+}
+
+int gm_compress_from(const gm_config* cfg, int64_t C, int64_t n_particles,
+                     const int64_t* cell_off, const double* x, const void* v, int32_t v_is_f64,
+                     const double* alpha, const int32_t* init_K, const double* init_params,
+                     int32_t* K_out, double* params_out, double* W_out, double* rho_target_out,
+                     double* lnL_out, int32_t* sweeps_out, int32_t* kwork_out,
+                     uint32_t* status_out, void* stream) {
+  if (!init_K || !init_params) return fail(GM_ERR_ARG, "init_K and init_params are required");
+  return compress_impl(cfg, C, n_particles, cell_off, x, v, v_is_f64, alpha, init_K, init_params,
+                       K_out, params_out, W_out, rho_target_out, lnL_out, sweeps_out, kwork_out,
+                       status_out, stream);
 }
 
 int gm_reconstruct(const gm_config* cfg, int64_t C, const int32_t* K, const double* params,

@@ -42,3 +42,24 @@ cudaError_t launch_tc_gemm(const void* A, const void* B, int M, int N, int K, in
                            void* Cb, int ldc, unsigned int* err, cudaStream_t s);
 
 }  // namespace gmcr
+
+namespace gmcr {
+// learned-initialisation network helpers (mlp_kernels.cu)
+cudaError_t launch_features(int D, int64_t C, int64_t n, const int64_t* cell_off, const void* v,
+                            int v_f64, const double* alpha, void* feat, double* wstat,
+                            cudaStream_t s);
+cudaError_t launch_targets(int D, int64_t C, int Kmax, int O, const int32_t* K, const double* prm,
+                           const double* wstat, float* T, float* Mk, cudaStream_t s);
+cudaError_t launch_decode(int D, int64_t C, int Kmax, int O, const float* out, const double* wstat,
+                          const int64_t* cell_off, int32_t* K0, double* prm, cudaStream_t s);
+cudaError_t launch_loss_grad(int B, int O, int D, int Kmax, const float* out, const float* T,
+                             const float* Mk, float* G32, void* G16, double* loss, cudaStream_t s);
+cudaError_t launch_transpose_bf16(int R, int Cc, const void* in, int ldi, void* out, int ldo,
+                                  cudaStream_t s);
+cudaError_t launch_colsum(int R, int Cc, const void* G, int ld, int g_is_bf16, float* db,
+                          cudaStream_t s);
+cudaError_t launch_adam(int n_out, int n_in, float* w, const float* g, float* m, float* v, float lr,
+                        int step, void* w16, void* wt16, cudaStream_t s);
+cudaError_t launch_cast_weights(int n_out, int n_in, const float* w, void* w16, void* wt16,
+                                cudaStream_t s);
+}  // namespace gmcr

@@ -27,7 +27,16 @@ ST_MM_EMPTY_COL = 0x400
 ST_NO_MIXTURE = 0x800
 
 EXPORTED = ("gm_compress", "gm_reconstruct", "gm_moments", "gm_mixture_moments",
-            "gm_last_error", "gm_shutdown", "gm_reconstruct_noalloc", "gm_gemm_bf16")
+            "gm_last_error", "gm_shutdown", "gm_reconstruct_noalloc", "gm_gemm_bf16",
+            "gm_compress_from", "gm_features", "gm_mlp_targets", "gm_mlp_sync",
+            "gm_mlp_scratch_bytes", "gm_mlp_forward", "gm_mlp_train_step", "gm_mlp_decode")
+
+
+class GMMlp(ct.Structure):
+    """Mirror of ``gm_mlp`` (include/gm.h)."""
+    _fields_ = [("D", ct.c_int32), ("Kmax", ct.c_int32), ("F", ct.c_int32), ("H", ct.c_int32),
+                ("O", ct.c_int32)] + [(nm, ct.c_void_p * 4) for nm in
+                                     ("W", "b", "W16", "WT16", "gW", "gb", "mW", "vW", "mb", "vb")]
 
 
 class GMConfig(ct.Structure):
@@ -67,8 +76,19 @@ def load(build_if_missing: bool = False):
         lib.gm_moments.argtypes = [P, I64, I64, P, P, P, I32, P, P, P, P, P, P, P]
         lib.gm_mixture_moments.argtypes = [P, I64, P, P, P, P, P, P, P, P]
         lib.gm_gemm_bf16.argtypes = [I32, I32, I32, P, I32, P, I32, P, I32, P, I32, P, P, I32, P, P]
+        lib.gm_compress_from.argtypes = [P, I64, I64, P, P, P, I32, P, P, P, P, P, P, P, P, P, P, P, P]
+        lib.gm_features.argtypes = [P, I64, I64, P, P, I32, P, P, P, P]
+        lib.gm_mlp_targets.argtypes = [P, I64, P, P, P, I32, P, P, P]
+        lib.gm_mlp_sync.argtypes = [P, P]
+        lib.gm_mlp_scratch_bytes.argtypes = [P, I32]
+        lib.gm_mlp_scratch_bytes.restype = ct.c_size_t
+        lib.gm_mlp_forward.argtypes = [P, I32, P, P, ct.c_size_t, P, P, P]
+        lib.gm_mlp_train_step.argtypes = [P, I32, P, P, P, ct.c_float, I32, P, ct.c_size_t, P, P, P, P]
+        lib.gm_mlp_decode.argtypes = [P, I64, P, I32, P, P, P, P, P]
         for f in ("gm_compress", "gm_reconstruct", "gm_moments", "gm_mixture_moments", "gm_shutdown",
-                  "gm_reconstruct_noalloc", "gm_gemm_bf16"):
+                  "gm_reconstruct_noalloc", "gm_gemm_bf16", "gm_compress_from", "gm_features",
+                  "gm_mlp_targets", "gm_mlp_sync", "gm_mlp_forward", "gm_mlp_train_step",
+                  "gm_mlp_decode"):
             getattr(lib, f).restype = ct.c_int
         lib.gm_last_error.restype = ct.c_char_p
         _lib = lib
@@ -120,10 +140,13 @@ def _rc(lib, rc, what):
         raise RuntimeError(f"{what} failed ({rc}): {lib.gm_last_error().decode()}")
 
 
-def gm_compress(cfg: GMConfig, cell_off, x, v, alpha, stream=None, out=None) -> dict:
+def gm_compress(cfg: GMConfig, cell_off, x, v, alpha, stream=None, out=None, init_K=None,
+                init_params=None) -> dict:
     """Per-cell adaptive GM fit.  cell_off [C+1] int64, x [n] f64,
     v [D, n] f32/f64, alpha [n] f64 (all CUDA).  Returns the outputs of
-    ``gm_compress`` as CUDA tensors (``out`` may supply them)."""
+    ``gm_compress`` as CUDA tensors (``out`` may supply them).  With
+    ``init_K`` / ``init_params`` the fit starts from those mixtures
+    (``gm_compress_from``)."""
     lib = load()
     C = cell_off.shape[0] - 1
     n = x.shape[0]
@@ -144,12 +167,20 @@ def gm_compress(cfg: GMConfig, cell_off, x, v, alpha, stream=None, out=None) -> 
                    sweeps=torch.empty(C, dtype=torch.int32, device=dev),
                    kwork=torch.empty(C, dtype=torch.int32, device=dev),
                    status=torch.empty(C, dtype=torch.int32, device=dev))
-    rc = lib.gm_compress(ct.byref(cfg), C, n, _ptr(cell_off), _ptr(x), _ptr(v),
-                         1 if v.dtype == torch.float64 else 0, _ptr(alpha), _ptr(out["K"]),
-                         _ptr(out["params"]), _ptr(out["W"]), _ptr(out["rho_target"]),
-                         _ptr(out["lnL"]), _ptr(out["sweeps"]), _ptr(out["kwork"]),
-                         _ptr(out["status"]), _stream_ptr(stream))
-    _rc(lib, rc, "gm_compress")
+    vf = 1 if v.dtype == torch.float64 else 0
+    tail = (_ptr(out["K"]), _ptr(out["params"]), _ptr(out["W"]), _ptr(out["rho_target"]),
+            _ptr(out["lnL"]), _ptr(out["sweeps"]), _ptr(out["kwork"]), _ptr(out["status"]),
+            _stream_ptr(stream))
+    if init_K is None:
+        rc = lib.gm_compress(ct.byref(cfg), C, n, _ptr(cell_off), _ptr(x), _ptr(v), vf,
+                             _ptr(alpha), *tail)
+        _rc(lib, rc, "gm_compress")
+    else:
+        _check(init_K, torch.int32, "init_K")
+        _check(init_params, torch.float64, "init_params")
+        rc = lib.gm_compress_from(ct.byref(cfg), C, n, _ptr(cell_off), _ptr(x), _ptr(v), vf,
+                                  _ptr(alpha), _ptr(init_K), _ptr(init_params), *tail)
+        _rc(lib, rc, "gm_compress_from")
     return out
 
 
@@ -260,3 +291,146 @@ def gm_gemm_bf16(A, B, bias=None, relu=False, mask=None, out_f32=None, out_bf16=
                           _ptr(out_f32), _ptr(out_bf16), ldc, _ptr(err), _stream_ptr(stream))
     _rc(lib, rc, "gm_gemm_bf16")
     return out_f32 if out_f32 is not None else out_bf16
+
+
+# ---------------------------------------------------------------------------
+# learned initialisation
+# ---------------------------------------------------------------------------
+def feat_width(D: int) -> int:
+    return 128 if D == 1 else 576
+
+
+def slot_size(D: int) -> int:
+    return 2 + 2 * D + D * (D - 1) // 2
+
+
+def out_width(D: int, Kmax: int) -> int:
+    return (Kmax * slot_size(D) + 15) // 16 * 16
+
+
+def gm_features(cfg: GMConfig, cell_off, v, alpha, stream=None):
+    """Per-cell features (BF16 [C][F]) and whitening statistics
+    (FP64 [C][2D]: mean, sd)."""
+    lib = load()
+    C = cell_off.shape[0] - 1
+    n = alpha.shape[0]
+    D = cfg.D
+    feat = torch.empty((C, feat_width(D)), dtype=torch.bfloat16, device=alpha.device)
+    wstat = torch.empty((C, 2 * D), dtype=torch.float64, device=alpha.device)
+    rc = lib.gm_features(ct.byref(cfg), C, n, _ptr(cell_off), _ptr(v),
+                         1 if v.dtype == torch.float64 else 0, _ptr(alpha), _ptr(feat),
+                         _ptr(wstat), _stream_ptr(stream))
+    _rc(lib, rc, "gm_features")
+    return feat, wstat
+
+
+def gm_mlp_targets(cfg: GMConfig, K, params, wstat, stream=None):
+    lib = load()
+    C = K.shape[0]
+    O = out_width(cfg.D, cfg.Kmax)
+    T = torch.empty((C, O), dtype=torch.float32, device=K.device)
+    Mk = torch.empty((C, O), dtype=torch.float32, device=K.device)
+    rc = lib.gm_mlp_targets(ct.byref(cfg), C, _ptr(K), _ptr(params), _ptr(wstat), O, _ptr(T),
+                            _ptr(Mk), _stream_ptr(stream))
+    _rc(lib, rc, "gm_mlp_targets")
+    return T, Mk
+
+
+def gm_mlp_decode(cfg: GMConfig, out, wstat, cell_off, stream=None):
+    lib = load()
+    C = cell_off.shape[0] - 1
+    K0 = torch.empty(C, dtype=torch.int32, device=out.device)
+    prm = torch.empty((C, cfg.Kmax, P_of(cfg.D)), dtype=torch.float64, device=out.device)
+    rc = lib.gm_mlp_decode(ct.byref(cfg), C, _ptr(out), out.shape[1], _ptr(wstat), _ptr(cell_off),
+                           _ptr(K0), _ptr(prm), _stream_ptr(stream))
+    _rc(lib, rc, "gm_mlp_decode")
+    return K0, prm
+
+
+class Net:
+    """Device buffers of the learned-initialisation network (FP32 masters,
+    BF16 copies and transposes, gradients, Adam moments) and the gm_mlp
+    struct that points at them."""
+
+    def __init__(self, D: int, Kmax: int, device="cuda"):
+        self.D, self.Kmax = D, Kmax
+        self.F, self.H, self.O = feat_width(D), 256, out_width(D, Kmax)
+        self.device = torch.device(device)
+        shapes = [(self.H, self.F), (self.H, self.H), (self.H, self.H), (self.O, self.H)]
+        z = lambda *sh, dt=torch.float32: torch.zeros(sh, dtype=dt, device=self.device)
+        self.W = [z(*sh) for sh in shapes]
+        self.b = [z(sh[0]) for sh in shapes]
+        self.W16 = [z(*sh, dt=torch.bfloat16) for sh in shapes]
+        self.WT16 = [z(sh[1], sh[0], dt=torch.bfloat16) for sh in shapes]
+        self.gW = [z(*sh) for sh in shapes]
+        self.gb = [z(sh[0]) for sh in shapes]
+        self.mW = [z(*sh) for sh in shapes]
+        self.vW = [z(*sh) for sh in shapes]
+        self.mb = [z(sh[0]) for sh in shapes]
+        self.vb = [z(sh[0]) for sh in shapes]
+        self.step = 0
+        self._scratch = None
+        self.err = torch.zeros(1, dtype=torch.int32, device=self.device)
+        self.s = GMMlp()
+        self.s.D, self.s.Kmax, self.s.F, self.s.H, self.s.O = D, Kmax, self.F, self.H, self.O
+        for nm in ("W", "b", "W16", "WT16", "gW", "gb", "mW", "vW", "mb", "vb"):
+            arr = getattr(self.s, nm)
+            for i, t in enumerate(getattr(self, nm)):
+                arr[i] = t.data_ptr()
+
+    def init_weights(self, seed: int = 0):
+        """He-normal weights, zero biases (seeded on the host)."""
+        g = torch.Generator().manual_seed(seed)
+        for W in self.W:
+            n, k = W.shape
+            W.copy_(torch.randn((n, k), generator=g, dtype=torch.float64).mul_((2.0 / k) ** 0.5))
+        for b in self.b:
+            b.zero_()
+        self.sync()
+
+    def load(self, Ws, bs):
+        for W, w in zip(self.W, Ws):
+            W.copy_(torch.as_tensor(w, dtype=torch.float32))
+        for b, bb in zip(self.b, bs):
+            b.copy_(torch.as_tensor(bb, dtype=torch.float32))
+        self.sync()
+
+    def sync(self, stream=None):
+        lib = load()
+        _rc(lib, lib.gm_mlp_sync(ct.byref(self.s), _stream_ptr(stream)), "gm_mlp_sync")
+
+    def scratch(self, M: int):
+        lib = load()
+        need = lib.gm_mlp_scratch_bytes(ct.byref(self.s), M)
+        if self._scratch is None or self._scratch.numel() < need:
+            self._scratch = torch.empty(need, dtype=torch.uint8, device=self.device)
+        return self._scratch
+
+    def forward(self, X, out=None, stream=None):
+        lib = load()
+        M = X.shape[0]
+        if out is None:
+            out = torch.empty((M, self.O), dtype=torch.float32, device=self.device)
+        sc = self.scratch(M)
+        rc = lib.gm_mlp_forward(ct.byref(self.s), M, _ptr(X), _ptr(sc), sc.numel(), _ptr(out),
+                                _ptr(self.err), _stream_ptr(stream))
+        _rc(lib, rc, "gm_mlp_forward")
+        return out
+
+    def train_step(self, X, T, Mk, lr: float, loss=None, out=None, stream=None):
+        """One step; returns the device loss accumulator.  lr <= 0 computes
+        gradients only."""
+        lib = load()
+        M = X.shape[0]
+        if out is None:
+            out = torch.empty((M, self.O), dtype=torch.float32, device=self.device)
+        if loss is None:
+            loss = torch.zeros(1, dtype=torch.float64, device=self.device)
+        if lr > 0:
+            self.step += 1
+        sc = self.scratch(M)
+        rc = lib.gm_mlp_train_step(ct.byref(self.s), M, _ptr(X), _ptr(T), _ptr(Mk), float(lr),
+                                   self.step, _ptr(sc), sc.numel(), _ptr(out), _ptr(loss),
+                                   _ptr(self.err), _stream_ptr(stream))
+        _rc(lib, rc, "gm_mlp_train_step")
+        return loss

@@ -22,7 +22,7 @@ def lib():
 
 def declared_functions():
     txt = open(HEADER).read()
-    return sorted(set(re.findall(r"^(?:int|const char\*)\s+(gm_\w+)\s*\(", txt, re.M)))
+    return sorted(set(re.findall(r"^(?:int|size_t|const char\*)\s+(gm_\w+)\s*\(", txt, re.M)))
 
 
 def test_exports_every_declared_symbol(lib):
@@ -68,3 +68,19 @@ def test_argument_errors_without_gpu(lib):
     cfg = gm.config(dict(D=1, Kmax=4, shape_order=2, L=1.0))
     assert lib.gm_mixture_moments(ct.byref(cfg), 0, None, None, None, None, None, None, None,
                                   None) == 0
+
+
+def test_mlp_struct_layout_matches_header(tmp_path):
+    from paper_2007_12273_gb300.gm import GMMlp
+    src = tmp_path / "lay2.c"
+    fields = [f for f, _ in GMMlp._fields_]
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "gm.h"\n'
+        "int main(void){printf(\"%zu\", sizeof(gm_mlp));"
+        + "".join(f'printf(" %zu", offsetof(gm_mlp, {f}));' for f in fields)
+        + "return 0;}\n")
+    exe = tmp_path / "lay2"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    vals = [int(t) for t in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    assert vals[0] == ct.sizeof(GMMlp)
+    assert vals[1:] == [getattr(GMMlp, f).offset for f in fields]
