@@ -17,7 +17,10 @@ Interface shared with the CUDA path (each side implements it separately):
   outside the range go to the edge bins; the vector is zero-padded to
   F = 128 (D = 1) or 576 (D = 3).
 * network: h1 = relu(x W1^T + b1), h2 = relu(h1 W2^T + b2),
-  h3 = relu(h2 W3^T + b3), out = h3 W4^T + b4; hidden width 256;
+  h3 = relu(h2 W3^T + b3), out = h3 W4^T + b4; hidden width 256; the
+  hidden activations are stored in BF16 (round to nearest even), as the
+  tensor-core network stores them; backward treats that rounding as the
+  identity;
   out has Kmax slots of SP = 2 + 2D + D(D-1)/2 values, zero-padded to a
   multiple of 16:
     [presence logit, log weight, mu (D), log diag of L (D), L10, L20, L21]
@@ -146,13 +149,21 @@ def init_params(D: int, Kmax: int, seed: int = 0) -> dict:
     return p
 
 
-def forward(p: dict, X: np.ndarray) -> dict:
+def bf16(a: np.ndarray) -> np.ndarray:
+    """Round to BF16 (via FP32, round to nearest even), returned as FP64."""
+    u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward(p: dict, X: np.ndarray, round_bf16: bool = True) -> dict:
+    rnd = bf16 if round_bf16 else (lambda a: a)
     Z1 = X @ p["W1"].T + p["b1"]
-    H1 = np.maximum(Z1, 0.0)
+    H1 = rnd(np.maximum(Z1, 0.0))
     Z2 = H1 @ p["W2"].T + p["b2"]
-    H2 = np.maximum(Z2, 0.0)
+    H2 = rnd(np.maximum(Z2, 0.0))
     Z3 = H2 @ p["W3"].T + p["b3"]
-    H3 = np.maximum(Z3, 0.0)
+    H3 = rnd(np.maximum(Z3, 0.0))
     out = H3 @ p["W4"].T + p["b4"]
     return dict(X=X, H1=H1, H2=H2, H3=H3, out=out)
 

@@ -39,7 +39,8 @@ cudaError_t launch_reconstruct(int D, int64_t C, int Kmax, const int32_t* K, con
 size_t tc_gemm_smem(int bn);
 cudaError_t launch_tc_gemm(const void* A, const void* B, int M, int N, int K, int lda, int ldb,
                            const float* bias, int relu, const void* mask, int ldm, float* Cf,
-                           void* Cb, int ldc, unsigned int* err, cudaStream_t s);
+                           void* Cb, int ldc, unsigned int* err, cudaStream_t s,
+                           int accumulate = 0);
 
 }  // namespace gmcr
 
@@ -62,4 +63,6 @@ cudaError_t launch_adam(int n_out, int n_in, float* w, const float* g, float* m,
                         int step, void* w16, void* wt16, cudaStream_t s);
 cudaError_t launch_cast_weights(int n_out, int n_in, const float* w, void* w16, void* wt16,
                                 cudaStream_t s);
+cudaError_t launch_split_bf16(int64_t total, int cols, float* x, const void* mask, int ldm,
+                              void* hi, void* lo, cudaStream_t s);
 }  // namespace gmcr

@@ -67,8 +67,8 @@ int check_net(const gm_mlp* net) {
 
 // scratch layout for M rows
 struct MlpScratch {
-  void *H[3], *G16, *dZa, *dZb, *TL, *TR;
-  float* G32;
+  void *H[3], *Ghi, *Glo, *dZhi, *dZlo, *TLhi, *TLlo, *TR;
+  float *G32, *dZ32;
 };
 size_t scratch_layout(const gm_mlp* net, int M, char* base, MlpScratch* sc) {
   const size_t H = net->H, O = net->O, F = net->F;
@@ -81,20 +81,32 @@ size_t scratch_layout(const gm_mlp* net, int M, char* base, MlpScratch* sc) {
   };
   for (int l = 0; l < 3; ++l) sc->H[l] = take((size_t)M * H * 2);
   sc->G32 = (float*)take((size_t)M * O * 4);
-  sc->G16 = take((size_t)M * O * 2);
-  sc->dZa = take((size_t)M * H * 2);
-  sc->dZb = take((size_t)M * H * 2);
-  sc->TL = take(big * (size_t)M * 2);
+  sc->Ghi = take((size_t)M * O * 2);
+  sc->Glo = take((size_t)M * O * 2);
+  sc->dZ32 = (float*)take((size_t)M * H * 4);
+  sc->dZhi = take((size_t)M * H * 2);
+  sc->dZlo = take((size_t)M * H * 2);
+  sc->TLhi = take(big * (size_t)M * 2);
+  sc->TLlo = take(big * (size_t)M * 2);
   sc->TR = take(big * (size_t)M * 2);
   return off;
 }
 
 int gemm(const void* A, const void* B, int M, int N, int K, int lda, int ldb, const float* bias,
          int relu, const void* mask, int ldm, float* Cf, void* Cb, int ldc, uint32_t* err,
-         cudaStream_t s) {
+         cudaStream_t s, int accumulate = 0) {
   cudaError_t e = gmcr::launch_tc_gemm(A, B, M, N, K, lda, ldb, bias, relu, mask, ldm, Cf, Cb, ldc,
-                                       err, s);
+                                       err, s, accumulate);
   return e == cudaSuccess ? GM_OK : cuda_err(e, "GEMM launch");
+}
+
+// C (FP32) = (Ahi + Alo) B^T: a gradient carried as two BF16 parts keeps
+// FP32-level accuracy through the tensor-core products
+int gemm_split(const void* Ahi, const void* Alo, const void* B, int M, int N, int K, int lda,
+               int ldb, float* Cf, int ldc, uint32_t* err, cudaStream_t s) {
+  int rc = gemm(Ahi, B, M, N, K, lda, ldb, nullptr, 0, nullptr, 0, Cf, nullptr, ldc, err, s, 0);
+  if (rc) return rc;
+  return gemm(Alo, B, M, N, K, lda, ldb, nullptr, 0, nullptr, 0, Cf, nullptr, ldc, err, s, 1);
 }
 
 int forward_impl(const gm_mlp* net, int M, const void* X, const MlpScratch& sc, float* out,
@@ -207,32 +219,38 @@ int gm_mlp_train_step(const gm_mlp* net, int32_t M, const void* X, const float* 
   scratch_layout(net, M, (char*)scratch, &sc);
   const int F = net->F, H = net->H, O = net->O;
   if ((rc = forward_impl(net, M, X, sc, out, err, s))) return rc;
-  cudaError_t e = gmcr::launch_loss_grad(M, O, net->D, net->Kmax, out, T, Mk, sc.G32, sc.G16, loss, s);
+  cudaError_t e = gmcr::launch_loss_grad(M, O, net->D, net->Kmax, out, T, Mk, sc.G32, sc.Ghi, loss, s);
   if (e != cudaSuccess) return cuda_err(e, "loss launch");
-  // layer 4: gW4 = G^T H3, gb4 = colsum(G), dZ3 = (G W4) * (H3 > 0)
+  // Backward pass.  Each layer's gradient dZ is kept in FP32 and fed to the
+  // tensor cores as hi + lo BF16 parts (two products each).
+  //   layer 4: gW4 = G^T H3, gb4 = colsum(G), dZ3 = (G W4) * (H3 > 0)
+  if ((e = gmcr::launch_split_bf16((int64_t)M * O, O, sc.G32, nullptr, 0, sc.Ghi, sc.Glo, s)) != cudaSuccess)
+    return cuda_err(e, "split");
   if ((e = gmcr::launch_colsum(M, O, sc.G32, O, 0, net->gb[3], s)) != cudaSuccess) return cuda_err(e, "colsum");
-  if ((e = gmcr::launch_transpose_bf16(M, O, sc.G16, O, sc.TL, M, s)) != cudaSuccess) return cuda_err(e, "transpose");
+  if ((e = gmcr::launch_transpose_bf16(M, O, sc.Ghi, O, sc.TLhi, M, s)) != cudaSuccess) return cuda_err(e, "transpose");
+  if ((e = gmcr::launch_transpose_bf16(M, O, sc.Glo, O, sc.TLlo, M, s)) != cudaSuccess) return cuda_err(e, "transpose");
   if ((e = gmcr::launch_transpose_bf16(M, H, sc.H[2], H, sc.TR, M, s)) != cudaSuccess) return cuda_err(e, "transpose");
-  if ((rc = gemm(sc.TL, sc.TR, O, H, M, M, M, nullptr, 0, nullptr, 0, net->gW[3], nullptr, H, err, s))) return rc;
-  if ((rc = gemm(sc.G16, net->WT16[3], M, H, O, O, O, nullptr, 0, sc.H[2], H, nullptr, sc.dZa, H, err, s))) return rc;
-  // layers 3, 2: gW = dZ^T H_prev, gb = colsum(dZ), dZ_prev = (dZ W) * (H_prev > 0)
-  void* dz = sc.dZa;
-  void* dzn = sc.dZb;
+  if ((rc = gemm_split(sc.TLhi, sc.TLlo, sc.TR, O, H, M, M, M, net->gW[3], H, err, s))) return rc;
+  if ((rc = gemm_split(sc.Ghi, sc.Glo, net->WT16[3], M, H, O, O, O, sc.dZ32, H, err, s))) return rc;
+  if ((e = gmcr::launch_split_bf16((int64_t)M * H, H, sc.dZ32, sc.H[2], H, sc.dZhi, sc.dZlo, s)) != cudaSuccess)
+    return cuda_err(e, "split");
+  //   layers 3, 2: gW = dZ^T H_prev, gb = colsum(dZ), dZ_prev = (dZ W) * (H_prev > 0)
   for (int l = 2; l >= 1; --l) {
-    if ((e = gmcr::launch_colsum(M, H, dz, H, 1, net->gb[l], s)) != cudaSuccess) return cuda_err(e, "colsum");
-    if ((e = gmcr::launch_transpose_bf16(M, H, dz, H, sc.TL, M, s)) != cudaSuccess) return cuda_err(e, "transpose");
+    if ((e = gmcr::launch_colsum(M, H, sc.dZ32, H, 0, net->gb[l], s)) != cudaSuccess) return cuda_err(e, "colsum");
+    if ((e = gmcr::launch_transpose_bf16(M, H, sc.dZhi, H, sc.TLhi, M, s)) != cudaSuccess) return cuda_err(e, "transpose");
+    if ((e = gmcr::launch_transpose_bf16(M, H, sc.dZlo, H, sc.TLlo, M, s)) != cudaSuccess) return cuda_err(e, "transpose");
     if ((e = gmcr::launch_transpose_bf16(M, H, sc.H[l - 1], H, sc.TR, M, s)) != cudaSuccess) return cuda_err(e, "transpose");
-    if ((rc = gemm(sc.TL, sc.TR, H, H, M, M, M, nullptr, 0, nullptr, 0, net->gW[l], nullptr, H, err, s))) return rc;
-    if ((rc = gemm(dz, net->WT16[l], M, H, H, H, H, nullptr, 0, sc.H[l - 1], H, nullptr, dzn, H, err, s))) return rc;
-    void* t = dz;
-    dz = dzn;
-    dzn = t;
+    if ((rc = gemm_split(sc.TLhi, sc.TLlo, sc.TR, H, H, M, M, M, net->gW[l], H, err, s))) return rc;
+    if ((rc = gemm_split(sc.dZhi, sc.dZlo, net->WT16[l], M, H, H, H, H, sc.dZ32, H, err, s))) return rc;
+    if ((e = gmcr::launch_split_bf16((int64_t)M * H, H, sc.dZ32, sc.H[l - 1], H, sc.dZhi, sc.dZlo, s)) != cudaSuccess)
+      return cuda_err(e, "split");
   }
-  // layer 1: gW1 = dZ1^T X, gb1 = colsum(dZ1)
-  if ((e = gmcr::launch_colsum(M, H, dz, H, 1, net->gb[0], s)) != cudaSuccess) return cuda_err(e, "colsum");
-  if ((e = gmcr::launch_transpose_bf16(M, H, dz, H, sc.TL, M, s)) != cudaSuccess) return cuda_err(e, "transpose");
+  //   layer 1: gW1 = dZ1^T X, gb1 = colsum(dZ1)
+  if ((e = gmcr::launch_colsum(M, H, sc.dZ32, H, 0, net->gb[0], s)) != cudaSuccess) return cuda_err(e, "colsum");
+  if ((e = gmcr::launch_transpose_bf16(M, H, sc.dZhi, H, sc.TLhi, M, s)) != cudaSuccess) return cuda_err(e, "transpose");
+  if ((e = gmcr::launch_transpose_bf16(M, H, sc.dZlo, H, sc.TLlo, M, s)) != cudaSuccess) return cuda_err(e, "transpose");
   if ((e = gmcr::launch_transpose_bf16(M, F, X, F, sc.TR, M, s)) != cudaSuccess) return cuda_err(e, "transpose");
-  if ((rc = gemm(sc.TL, sc.TR, H, F, M, M, M, nullptr, 0, nullptr, 0, net->gW[0], nullptr, F, err, s))) return rc;
+  if ((rc = gemm_split(sc.TLhi, sc.TLlo, sc.TR, H, F, M, M, M, net->gW[0], F, err, s))) return rc;
   if (lr > 0.0f) {
     const int rows[4] = {H, H, H, O};
     const int cols[4] = {F, H, H, H};

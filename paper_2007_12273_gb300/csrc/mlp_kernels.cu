@@ -300,6 +300,23 @@ __global__ void adam_kernel(int n_out, int n_in, float* w, const float* g, float
   }
 }
 
+// x (FP32, zeroed where mask <= 0 if a mask is given) as hi + lo BF16
+// parts: hi = bf16(x), lo = bf16(x - hi)
+__global__ void split_bf16_kernel(int64_t total, int cols, float* x, const __nv_bfloat16* mask,
+                                  int ldm, __nv_bfloat16* hi, __nv_bfloat16* lo) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float v = x[i];
+    if (mask && !(__bfloat162float(mask[(i / cols) * ldm + i % cols]) > 0.0f)) {
+      v = 0.0f;
+      x[i] = 0.0f;
+    }
+    const __nv_bfloat16 h = __float2bfloat16(v);
+    hi[i] = h;
+    lo[i] = __float2bfloat16(v - __bfloat162float(h));
+  }
+}
+
 // BF16 copy and transpose of FP32 weights
 __global__ void cast_weights_kernel(int n_out, int n_in, const float* w, __nv_bfloat16* w16,
                                     __nv_bfloat16* wt16) {
@@ -466,6 +483,14 @@ cudaError_t launch_cast_weights(int n_out, int n_in, const float* w, void* w16, 
   const int64_t total = (int64_t)n_out * n_in;
   const int g = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
   cast_weights_kernel<<<g, 256, 0, s>>>(n_out, n_in, w, (__nv_bfloat16*)w16, (__nv_bfloat16*)wt16);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_bf16(int64_t total, int cols, float* x, const void* mask, int ldm,
+                              void* hi, void* lo, cudaStream_t s) {
+  const int g = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+  split_bf16_kernel<<<g, 256, 0, s>>>(total, cols, x, (const __nv_bfloat16*)mask, ldm,
+                                      (__nv_bfloat16*)hi, (__nv_bfloat16*)lo);
   return cudaGetLastError();
 }
 

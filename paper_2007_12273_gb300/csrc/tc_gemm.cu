@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __nv_bfloat16* __res
                                                       const __nv_bfloat16* __restrict__ mask,
                                                       int ldm, float* __restrict__ Cf,
                                                       __nv_bfloat16* __restrict__ Cb, int ldc,
-                                                      unsigned int* err) {
+                                                      int accumulate, unsigned int* err) {
   constexpr int TCOLS = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
   constexpr uint32_t IDESC = idesc_bf16(kBM, BN);
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -193,7 +193,10 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __nv_bfloat16* __res
           if (bias) x += bias[col];
           if (relu) x = fmaxf(x, 0.0f);
           if (mask && !(__bfloat162float(mask[(size_t)row * ldm + col]) > 0.0f)) x = 0.0f;
-          if (Cf) Cf[(size_t)row * ldc + col] = x;
+          if (Cf) {
+            float* cp = Cf + (size_t)row * ldc + col;
+            *cp = accumulate ? *cp + x : x;
+          }
           if (Cb) Cb[(size_t)row * ldc + col] = __float2bfloat16(x);
         }
       }
@@ -209,7 +212,7 @@ size_t tc_gemm_smem(int bn) { return (size_t)(kBM + bn) * kBK * 2 + 1024; }
 
 cudaError_t launch_tc_gemm(const void* A, const void* B, int M, int N, int K, int lda, int ldb,
                            const float* bias, int relu, const void* mask, int ldm, float* Cf,
-                           void* Cb, int ldc, unsigned int* err, cudaStream_t s) {
+                           void* Cb, int ldc, unsigned int* err, cudaStream_t s, int accumulate) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
   int bn = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
   // at least 80 KB of shared memory per CTA keeps two CTAs (2 x 256 TMEM
@@ -225,7 +228,7 @@ cudaError_t launch_tc_gemm(const void* A, const void* B, int M, int N, int K, in
     if (e != cudaSuccess) return e;                                                              \
     k<<<grid, 128, smem, s>>>((const __nv_bfloat16*)A, (const __nv_bfloat16*)B, M, N, K, lda,    \
                               ldb, bias, relu, (const __nv_bfloat16*)mask, ldm, Cf,              \
-                              (__nv_bfloat16*)Cb, ldc, err);                                     \
+                              (__nv_bfloat16*)Cb, ldc, accumulate, err);                         \
   }
   if (bn == 32) GM_TC_LAUNCH(32)
   else if (bn == 64) GM_TC_LAUNCH(64)

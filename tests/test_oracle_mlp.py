@@ -31,10 +31,10 @@ def test_backward_matches_finite_differences(D, Kmax):
                 Mk[b, s * SP + 1:(s + 1) * SP] = 1
 
     def loss(pp):
-        f = mlp.forward(pp, X)
+        f = mlp.forward(pp, X, round_bf16=False)
         return mlp.loss_and_grad_out(f["out"], T, Mk, D, Kmax)[0]
 
-    f = mlp.forward(p, X)
+    f = mlp.forward(p, X, round_bf16=False)
     L, G = mlp.loss_and_grad_out(f["out"], T, Mk, D, Kmax)
     g = mlp.backward(p, f, G)
     h = 1e-6
@@ -128,3 +128,10 @@ def test_decode_of_targets_reproduces_the_fit(D, Kmax):
     assert K0 == K
     order = np.argsort(prm[:, 1])  # decode returns components sorted by whitened mu_0
     np.testing.assert_allclose(dec, prm[order], rtol=1e-10, atol=1e-12)
+
+
+def test_bf16_rounding():
+    torch = pytest.importorskip("torch")
+    x = np.random.default_rng(0).standard_normal(10000) * 10.0 ** np.random.default_rng(1).uniform(-5, 5, 10000)
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).double().numpy()
+    np.testing.assert_array_equal(mlp.bf16(x), ref)
