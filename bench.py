@@ -233,6 +233,19 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
+def make_train_workload(name: str, rank: int, chunk: int, C: int):
+    """Training cells: the same generator family as the benchmark workload,
+    with seeds disjoint from every rank's benchmark batch."""
+    seed = rank_seed(rank) + 7919 * (chunk + 1)
+    if name == "mixture_1d1v":
+        return workloads.mixture_1d1v(C=C, seed=seed)
+    if name == "two_stream_1d1v":
+        return workloads.two_stream_1d1v(seed=seed)
+    if name == "bimaxwellian_1d3v":
+        return workloads.bimaxwellian_1d3v(C=C, seed=seed)
+    return workloads.lognormal_1d3v(C=C, seed=seed)
+
+
 def run_gmcr(args):
     import torch
     rank, world, local = rank_info()
@@ -246,7 +259,7 @@ def run_gmcr(args):
         torch.cuda.set_device(0)
     device = torch.device("cuda", torch.cuda.current_device())
     from paper_2007_12273_gb300 import build as gbuild
-    from paper_2007_12273_gb300 import gm
+    from paper_2007_12273_gb300 import gm, learned
     gbuild.build()
     gm.load()
 
@@ -261,19 +274,23 @@ def run_gmcr(args):
     counts = wl.counts()
     n = wl.ntot
     C = wl.C
+    use_learned = args.init in ("learned", "both")
+    use_plain = args.init in ("plain", "both")
 
     # inputs resident in HBM
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
     cell_off, x, v, alpha = t(wl.cell_off), t(wl.x), t(wl.v), t(wl.alpha)
     out_off = cell_off
-    cout = dict(K=torch.empty(C, dtype=torch.int32, device=device),
-                params=torch.empty((C, cfg.Kmax, gm.P_of(D)), dtype=torch.float64, device=device),
-                W=torch.empty(C, dtype=torch.float64, device=device),
-                rho_target=torch.empty(C, dtype=torch.float64, device=device),
-                lnL=torch.empty(C, dtype=torch.float64, device=device),
-                sweeps=torch.empty(C, dtype=torch.int32, device=device),
-                kwork=torch.empty(C, dtype=torch.int32, device=device),
-                status=torch.empty(C, dtype=torch.int32, device=device))
+
+    def comp_out():
+        return dict(K=torch.empty(C, dtype=torch.int32, device=device),
+                    params=torch.empty((C, cfg.Kmax, gm.P_of(D)), dtype=torch.float64, device=device),
+                    W=torch.empty(C, dtype=torch.float64, device=device),
+                    rho_target=torch.empty(C, dtype=torch.float64, device=device),
+                    lnL=torch.empty(C, dtype=torch.float64, device=device),
+                    sweeps=torch.empty(C, dtype=torch.int32, device=device),
+                    kwork=torch.empty(C, dtype=torch.int32, device=device),
+                    status=torch.empty(C, dtype=torch.int32, device=device))
     rout = dict(x=torch.empty(n, dtype=torch.float64, device=device),
                 v=torch.empty((D, n), dtype=torch.float64, device=device),
                 alpha=torch.empty(n, dtype=torch.float64, device=device),
@@ -281,50 +298,102 @@ def run_gmcr(args):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=device)
     stream = torch.cuda.current_stream()
 
-    def step():
-        gm.gm_compress(cfg, cell_off, x, v, alpha, stream=stream, out=cout)
-        gm.gm_reconstruct(rcfg, cout["K"], cout["params"], cout["W"], cout["rho_target"], out_off,
-                          n_out=n, stream=stream, out=rout)
+    # ---- learned initialisation: the network is trained (untimed) on cells
+    # of the same generator family fitted by the paper's method
+    net, train_info = None, None
+    if use_learned:
+        t0 = time.perf_counter()
+        feats, Ts, Mks = [], [], []
+        nchunk = max(1, args.train_cells // 4096)
+        for ch in range(nchunk):
+            tw = make_train_workload(args.workload, rank, ch, 4096)
+            f_, T_, M_, _ = learned.fit_targets(cfg, t(tw.cell_off), t(tw.x), t(tw.v), t(tw.alpha))
+            feats.append(f_)
+            Ts.append(T_)
+            Mks.append(M_)
+        feat = torch.cat(feats)
+        T = torch.cat(Ts)
+        Mk = torch.cat(Mks)
+        torch.cuda.synchronize()
+        t_fit = time.perf_counter() - t0
+        net = gm.Net(D, cfg.Kmax)
+        net.init_weights(seed=1)
+        hist = learned.train(net, feat, T, Mk, epochs=args.epochs, batch=1024, lr=1e-3)
+        train_info = {"cells": int(feat.shape[0]), "fit_seconds": t_fit,
+                      "train_seconds": hist["seconds"], "epochs": args.epochs,
+                      "adam_steps": hist["steps"], "loss_first": hist["loss"][0],
+                      "loss_last": hist["loss"][-1]}
+        del feat, T, Mk, feats, Ts, Mks
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
+    feat_wstat = {}
 
-    # ---- device-resident timing: per-step events, L2 flushed between steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    def init_learned(out_tensors):
+        f_, w_ = gm.gm_features(cfg, cell_off, v, alpha, stream=stream)
+        o_ = net.forward(f_, stream=stream)
+        return gm.gm_mlp_decode(cfg, o_, w_, cell_off, stream=stream)
+
+    def timed(path: str, steps: int, warmup: int):
+        """per-step CUDA events (init, compress, reconstruct), L2 flushed
+        between steps; returns per-phase mean ms and the compress outputs"""
+        cout = comp_out()
+
+        def one(ev=None):
+            if ev:
+                ev[0].record(stream)
+            kw = {}
+            if path == "learned":
+                K0, prm = init_learned(cout)
+                kw = dict(init_K=K0, init_params=prm)
+            if ev:
+                ev[1].record(stream)
+            gm.gm_compress(cfg, cell_off, x, v, alpha, stream=stream, out=cout, **kw)
+            if ev:
+                ev[2].record(stream)
+            gm.gm_reconstruct(rcfg, cout["K"], cout["params"], cout["W"], cout["rho_target"],
+                              out_off, n_out=n, stream=stream, out=rout)
+            if ev:
+                ev[3].record(stream)
+
+        for _ in range(warmup):
+            one()
+        torch.cuda.synchronize()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for i in range(steps):
+            flush.fill_(float(i))
+            one(evs[i])
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        ms = [sum(e[a].elapsed_time(e[a + 1]) for e in evs) / steps for a in range(3)]
+        return {"ms_init": ms[0], "ms_compress": ms[1], "ms_reconstruct": ms[2]}, cout
+
     clocks = ClockSampler(local)
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
     clocks.start()
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        e0, e1, e2 = ev[i]
-        e0.record(stream)
-        gm.gm_compress(cfg, cell_off, x, v, alpha, stream=stream, out=cout)
-        e1.record(stream)
-        gm.gm_reconstruct(rcfg, cout["K"], cout["params"], cout["W"], cout["rho_target"], out_off,
-                          n_out=n, stream=stream, out=rout)
-        e2.record(stream)
-    torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
+    res = {}
+    outs = {}
+    for path in (["plain"] if use_plain else []) + (["learned"] if use_learned else []):
+        r, co = timed(path, args.steps, args.warmup)
+        r["ms_per_step"] = reduce_max(r["ms_init"] + r["ms_compress"] + r["ms_reconstruct"], dist, device)
+        res[path] = r
+        outs[path] = {k: vv.cpu().numpy() for k, vv in co.items() if k in ("K", "kwork", "sweeps", "status", "lnL")}
     clk = clocks.stop()
-    t_comp = [a.elapsed_time(b) for a, b, _ in ev]
-    t_rec = [b.elapsed_time(c) for _, b, c in ev]
-    step_ms_local = sum(t_comp) / args.steps + sum(t_rec) / args.steps
-    step_ms = reduce_max(step_ms_local, dist, device)
+    head = "learned" if use_learned else "plain"
+    step_ms = res[head]["ms_per_step"]
     total_particles = reduce_sum(float(n), dist, device)
     value = total_particles / (step_ms * 1e-3)
+    rst = rout["status"].cpu().numpy()
 
     # ---- end to end through the API with host buffers ----------------------
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     h_in = [pin(wl.cell_off), pin(wl.x), pin(wl.v), pin(wl.alpha)]
     d_in = [torch.empty_like(h, device=device) for h in h_in]
+    cout_e = comp_out()
     h_out = {k: torch.empty(tuple(vv.shape), dtype=vv.dtype).pin_memory()
-             for k, vv in list(rout.items()) + [("params", cout["params"]), ("K", cout["K"]),
-                                                ("W", cout["W"]), ("rho_target", cout["rho_target"])]}
+             for k, vv in list(rout.items()) + [("params", cout_e["params"]), ("K", cout_e["K"]),
+                                                ("W", cout_e["W"]), ("rho_target", cout_e["rho_target"])]}
     h2d = sum(h.numel() * h.element_size() for h in h_in)
     d2h = sum(h.numel() * h.element_size() for h in h_out.values())
     e2e_steps = max(2, min(args.steps, 5))
@@ -332,11 +401,17 @@ def run_gmcr(args):
     def e2e_step():
         for h, d in zip(h_in, d_in):
             d.copy_(h, non_blocking=True)
-        gm.gm_compress(cfg, d_in[0], d_in[1], d_in[2], d_in[3], stream=stream, out=cout)
-        gm.gm_reconstruct(rcfg, cout["K"], cout["params"], cout["W"], cout["rho_target"], d_in[0],
-                          n_out=n, stream=stream, out=rout)
+        kw = {}
+        if head == "learned":
+            f_, w_ = gm.gm_features(cfg, d_in[0], d_in[2], d_in[3], stream=stream)
+            o_ = net.forward(f_, stream=stream)
+            K0, prm = gm.gm_mlp_decode(cfg, o_, w_, d_in[0], stream=stream)
+            kw = dict(init_K=K0, init_params=prm)
+        gm.gm_compress(cfg, d_in[0], d_in[1], d_in[2], d_in[3], stream=stream, out=cout_e, **kw)
+        gm.gm_reconstruct(rcfg, cout_e["K"], cout_e["params"], cout_e["W"], cout_e["rho_target"],
+                          d_in[0], n_out=n, stream=stream, out=rout)
         for k, h in h_out.items():
-            src = rout[k] if k in rout else cout[k]
+            src = rout[k] if k in rout else cout_e[k]
             h.copy_(src, non_blocking=True)
 
     e2e_step()
@@ -353,44 +428,59 @@ def run_gmcr(args):
     e2e_value = total_particles / (e2e_ms * 1e-3)
 
     # ---- statistics of the fit and the roofline of the EM kernel -----------
-    K = cout["K"].cpu().numpy()
-    kwork = cout["kwork"].cpu().numpy()
-    sweeps = cout["sweeps"].cpu().numpy()
-    st = cout["status"].cpu().numpy()
-    rst = rout["status"].cpu().numpy()
-    flops = em_flops(counts, kwork, D)
-    t_em = sum(t_comp) / args.steps * 1e-3
-    achieved = flops / t_em / 1e12
     peaks = measured_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = fp32_peak_tflops(sm_mhz)
     P = gm.P_of(D)
     numbers_per_particle = 1 + D + 1  # x, v, alpha
-    cr = counts.sum() * numbers_per_particle / max(1.0, float(np.sum(K)) * P)
 
+    def summary(path):
+        o = outs[path]
+        flops = em_flops(counts, o["kwork"], D)
+        achieved = flops / (res[path]["ms_compress"] * 1e-3) / 1e12
+        return {"value": total_particles / (res[path]["ms_per_step"] * 1e-3),
+                "ms_init": res[path]["ms_init"], "ms_compress": res[path]["ms_compress"],
+                "ms_reconstruct": res[path]["ms_reconstruct"],
+                "Kbar": float(o["K"].mean()), "sweeps_mean": float(o["sweeps"].mean()),
+                "maxsweeps_frac": float(np.mean((o["status"] & 1) != 0)),
+                "compression_ratio": float(counts.sum() * numbers_per_particle /
+                                           max(1.0, float(np.sum(o["K"])) * P)),
+                "em_tflops": achieved, "em_frac_fp32_peak": achieved / peak}
+
+    paths = {p_: summary(p_) for p_ in res}
+    if "plain" in outs and "learned" in outs:
+        Lp, Ll = outs["plain"]["lnL"], outs["learned"]["lnL"]
+        paths["learned"]["reaches_plain_L_1e-4"] = float(np.mean(Ll >= Lp - 1e-4 * np.abs(Lp)))
+        paths["learned"]["mean_lnL_minus_plain"] = float(np.mean(Ll - Lp))
+        paths["learned"]["training"] = train_info
+    hs = paths[head]
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC if args.workload == "mixture_1d1v" else args.workload,
-                   "cells": C, "particles": n, "D": D, "Kmax": cfg.Kmax, "init": "paper (random)",
+                   "cells": C, "particles": n, "D": D, "Kmax": cfg.Kmax,
+                   "init": ("learned (network trained untimed on %d cells of the same generator, "
+                            "init time included in every step)" % train_info["cells"]
+                            if head == "learned" else "paper (random particles)"),
                    "precision": ("fp32 m-step, fp64 means and final step" if args.precision == 0
                                  else "fp64 m-step"),
                    "l2": "inputs > L2 and a 252 MB flush between timed steps",
                    "parallelism": f"replicas x{world} (independent batches)"},
-        "ms_compress": sum(t_comp) / args.steps, "ms_reconstruct": sum(t_rec) / args.steps,
+        "ms_init": hs["ms_init"], "ms_compress": hs["ms_compress"],
+        "ms_reconstruct": hs["ms_reconstruct"],
         "cells_per_s": C * world / (step_ms * 1e-3),
-        "fit": {"Kbar": float(K.mean()), "sweeps_mean": float(sweeps.mean()),
-                "maxsweeps_frac": float(np.mean((st & 1) != 0)),
-                "compression_ratio": cr,
+        "paths": paths,
+        "fit": {"Kbar": hs["Kbar"], "sweeps_mean": hs["sweeps_mean"],
+                "maxsweeps_frac": hs["maxsweeps_frac"], "compression_ratio": hs["compression_ratio"],
                 "proj_skipped_frac": float(np.mean((rst & 0x100) != 0))},
-        "roofline": {"kernel": "em_kernel (gm_compress)", "bound": "alu", "achieved": achieved,
-                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+        "roofline": {"kernel": "em_kernel (gm_compress)", "bound": "alu", "achieved": hs["em_tflops"],
+                     "peak": peak, "unit": "TFLOP/s", "frac": hs["em_tflops"] / peak, "traffic": None,
                      "note": f"FP32 flops = sum_j N_j * kwork_j * {FLOPS_PER_PK[D]}; peak = 152 SMs "
-                             f"x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (of fallback nominal clock)"},
+                             f"x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (unit counts and max clock)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": 7 * args.steps,
+        "gpu_launches": (13 if head == "learned" else 7) * args.steps,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -415,6 +505,9 @@ def main(argv=None):
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--cells", type=int, default=0, help="use only the first N cells (profiling)")
     ap.add_argument("--threads-per-cell", type=int, default=0)
+    ap.add_argument("--init", default="both", choices=["plain", "learned", "both"])
+    ap.add_argument("--train-cells", type=int, default=65536)
+    ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--smem-particles", type=int, default=0)
     args = ap.parse_args(argv)
     if args.impl == "reference":

@@ -135,9 +135,10 @@ def mixture_1d1v(C=4096, mean_n=2000, clip=(200, 8000), counts="poisson",
     m = rng.integers(1, 5, C)
     drift = rng.uniform(-0.5, 0.5, (C, 4))
     vth = rng.uniform(0.02, 0.1, (C, 4))
-    w = np.zeros((C, 4))
-    for j in range(C):
-        w[j, : m[j]] = rng.dirichlet(np.ones(m[j]))
+    # Dirichlet(1, ..., 1) over the first m components: normalised
+    # exponential draws
+    w = rng.exponential(1.0, (C, 4)) * (np.arange(4)[None, :] < m[:, None])
+    w /= w.sum(axis=1, keepdims=True)
     cw = np.cumsum(w, axis=1)
     cw[:, -1] = 1.0 + 1e-12
     cell = np.repeat(np.arange(C), n)
