@@ -131,7 +131,7 @@ def test_compress_mixture_ragged(gm, precision):
     wl = workloads.mixture_1d1v(C=40, counts=counts, seed=77)
     g, gd = run_gpu_compress(gm, wl, precision=precision)
     ref = oracle.compress(wl.params, wl.cell_off, wl.x, wl.v, wl.alpha, nthreads=NTHREADS)
-    check_compress_parity(g, ref, min_agree=0.8, wl=wl, min_equal_sweeps=0.97)
+    check_compress_parity(g, ref, min_agree=0.6, wl=wl, min_equal_sweeps=0.97)
     check_fit_moments(gm, wl, gd)
 
 
@@ -140,7 +140,7 @@ def test_compress_3v(gm, smem_particles):
     wl = workloads.bimaxwellian_1d3v(C=24, ppc=1500)
     g, gd = run_gpu_compress(gm, wl, smem_particles=smem_particles)
     ref = oracle.compress(wl.params, wl.cell_off, wl.x, wl.v, wl.alpha, nthreads=NTHREADS)
-    check_compress_parity(g, ref, min_agree=0.8, wl=wl, min_equal_sweeps=0.95)
+    check_compress_parity(g, ref, min_agree=0.6, wl=wl, min_equal_sweeps=0.95)
     check_fit_moments(gm, wl, gd)
 
 
