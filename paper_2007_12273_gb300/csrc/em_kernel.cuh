@@ -18,12 +18,16 @@
 // (lnL-GM).  Weights are kept unnormalised (omega_j = u_j / Z), which makes
 // the renormalisation after each component (step 3) implicit.
 //
+// The exact pass is fused with the E-step of the next sweep's first
+// component, so a sweep of K components costs K passes over the particles.
+//
 // Precision: E-step densities / responsibilities FP32; statistics FP32 per
-// thread and per warp, summed across warps in R; the M-step in R (FP64:
-// precision 0, FP32: precision 1) with the component means accumulated in
-// FP64 either way; the final unpenalised step (Sec. 2.3.1) entirely in FP64
-// with FP64-normalised responsibilities, which is what makes the moments
-// exact.
+// thread and per warp, summed across warps in R; the M-step in R (FP32:
+// precision 0, FP64: precision 1) with the component means accumulated to
+// about 48 bits either way (FP64, or an unevaluated FP32 sum hi + lo when R
+// is FP32, which keeps FP64 arithmetic off the M-step's critical path); the
+// final unpenalised step (Sec. 2.3.1) entirely in FP64 with FP64-normalised
+// responsibilities, which is what makes the moments exact.
 #pragma once
 
 #include "gm_common.cuh"
@@ -67,14 +71,19 @@ struct NConst {  // packed E constants of one component
   static constexpr int N = D + NM + 1;  // -mu (D), A (D = 3) or -A^2 (D = 1), b
 };
 
+// smallest power of two >= n (n <= 32)
+constexpr int pow2_at_least(int n) { return n <= 1 ? 1 : 2 * pow2_at_least((n + 1) / 2); }
+
 template <int D, int NW, typename R>
 struct EmCtl {
   static constexpr int NM = D * (D + 1) / 2;
   static constexpr int NS = 1 + D + NM;
+  static constexpr int NRED = pow2_at_least(NS + 1);  // statistics + log-likelihood
   // master parameters in whitened coordinates y = (v - mean) / sc
   R u[kMaxK];  // unnormalised weights, omega = u / Z (precision of the M-step)
   R Z;
   double mu[kMaxK][D];
+  float mulo[kMaxK][D];  // R = FP32: mean = emu + mulo (emu the high part)
   double S0[NM];  // whitened total covariance (initial covariance of every component)
   // FP32 E-step constants: log2(u f) = b - |A (y - mu)|^2
   float emu[kMaxK][D];
@@ -87,7 +96,10 @@ struct EmCtl {
   double mean[D], sc[D], isc[D];
   float meanf[D], scf[D];
   double Nd, W, L, Lprev, logjac, logN;
-  float redf[NW][NS + 1];
+  double sumAH;  // sum of the staged FP32 weights
+  float c0;      // centring constant of the log-likelihood sum (log2 units)
+  R NdR;
+  float redf[NW][NRED];
   double redd[NW][NS + 1];
   double res[NS + 1];
   // final step (centered original coordinates)
@@ -261,6 +273,51 @@ __device__ __forceinline__ void block_sum_d(EmCtl<D, NT / 32, R>& c, double (&v)
   __syncthreads();
 }
 
+// Warp sum of NP values (NP a power of two <= 32) by recursive halving: at
+// each level a lane keeps half of its values, sends the other half to its
+// partner and adds what it receives, so NP values cost NP - 1 + 5 - log2(NP)
+// shuffles instead of 5 NP.  On return v[0] of every lane holds the warp
+// total of value warp_rs_index<NP>(lane).
+template <int NP>
+__device__ __forceinline__ void warp_rs(float (&v)[NP], int lane) {
+  constexpr int LV = NP == 1 ? 0 : (NP == 2 ? 1 : (NP == 4 ? 2 : (NP == 8 ? 3 : (NP == 16 ? 4 : 5))));
+#pragma unroll
+  for (int lv = 0; lv < LV; ++lv) {
+    const int h = NP >> (lv + 1), b = 16 >> lv;
+    const bool up = (lane & b) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const float send = up ? v[i] : v[i + h];
+      const float keep = up ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, b);
+    }
+  }
+#pragma unroll
+  for (int b = 16 >> LV; b >= 1; b >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], b);
+}
+template <int NP>
+__device__ __forceinline__ int warp_rs_index(int lane) {
+  int q = 0;
+#pragma unroll
+  for (int lv = 0; (NP >> lv) > 1; ++lv) q += ((lane >> (4 - lv)) & 1) * (NP >> (lv + 1));
+  return q;
+}
+
+// per-warp totals of NV per-thread values into red[warp][q], then a barrier
+template <int NV, int NP, int NW>
+__device__ __forceinline__ void block_partials(const float (&v)[NV], float (&red)[NW][NP]) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float t[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) t[q] = q < NV ? v[q] : 0.0f;
+  warp_rs<NP>(t, lane);
+  if ((lane & (32 / NP - 1)) == 0) {
+    const int q = warp_rs_index<NP>(lane);
+    if (q < NV) red[w][q] = t[0];
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // one cell, after its moments are known and it is not degenerate.
 // base: the particle tile (shared or global), st: floats per array (even).
@@ -293,17 +350,26 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
   // ---- stage whitened velocities and normalised weights ------------------
   {
     const double nw = c.Nd / c.W;
+    double sa[1] = {0.0};
     for (int p = tid; p < 2 * P2; p += NT) {
       if (p < N) {
 #pragma unroll
         for (int d = 0; d < D; ++d)
           Y[d * st + p] = (float)(((double)vin[(int64_t)d * a.n + off + p] - c.mean[d]) * c.isc[d]);
-        AH[p] = (float)(a.alpha[off + p] * nw);
+        const float ah = (float)(a.alpha[off + p] * nw);
+        AH[p] = ah;
+        sa[0] += (double)ah;
       } else {  // zero-weight pad particle
 #pragma unroll
         for (int d = 0; d < D; ++d) Y[d * st + p] = 0.0f;
         AH[p] = 0.0f;
       }
+    }
+    block_sum_d<D, NT, 1, R>(c, sa);
+    if (tid == 0) {
+      c.sumAH = c.res[0];
+      c.c0 = -2.0471975511965976f * D;  // mean log2 density of a standard normal
+      c.NdR = (R)c.Nd;
     }
   }
   // ---- initialisation --------------------------------------------------
@@ -330,6 +396,7 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
         for (int d = 0; d < D; ++d) {
           c.mu[K][d] = mw[d];
           c.emu[K][d] = (float)mw[d];
+          c.mulo[K][d] = (float)(mw[d] - (double)c.emu[K][d]);
         }
         for (int i = 0; i < NM; ++i) c.eA[K][i] = eA[i];
         c.elc[K] = elc;
@@ -390,6 +457,7 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
       for (int d = 0; d < D; ++d) {
         c.mu[k][d] = ((double)vin[(int64_t)d * a.n + off + picks[k]] - c.mean[d]) * c.isc[d];
         c.emu[k][d] = (float)c.mu[k][d];
+        c.mulo[k][d] = (float)(c.mu[k][d] - (double)c.emu[k][d]);
       }
       for (int i = 0; i < NM; ++i) c.eA[k][i] = eA[i];
       c.elc[k] = elc;
@@ -401,6 +469,7 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
     c.sweep = 0;
     c.kwork = 0;
     c.done = 0;
+    c.annih = 0;
   }
   __syncthreads();
 
@@ -409,57 +478,215 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
   f32x2* SS2 = reinterpret_cast<f32x2*>(SS);
   f32x2* MM2 = reinterpret_cast<f32x2*>(MM);
   f32x2* GG2 = reinterpret_cast<f32x2*>(GG);
+  constexpr int NRED = EmCtl<D, NW, R>::NRED;
+
+  // ---- M-step for component k (eqs. muk, sigmak, omegak), one thread -----
+  // sv: N_k, the first moments and the second moments about the FP32 mean
+  // the E-step used.
+  auto mstep = [&](int k, const R* sv) {
+    c.kwork++;
+    const int K = c.K;
+    const R Nk = sv[0];
+    bool removed = false;
+    if (K > 1 && Nk - (R)halfT <= (R)0) {
+      removed = true;
+    } else {
+      const R rN = rcp_nr(Nk);
+      R dl[D], mun[D], Sn[NM];
+      // The shift of the mean is added to a ~48-bit master copy (FP64, or
+      // hi + lo FP32 when R is FP32), which keeps the sub-ulp part of every
+      // update: the FP32 copy then follows the FP64 trajectory instead of
+      // stalling when an update is below its resolution.
+      double mu64[D];
+      float mlo[D];
+      for (int x = 0; x < D; ++x) {
+        dl[x] = sv[1 + x] * rN;
+        if constexpr (sizeof(R) == 4) {
+          const float hi = c.emu[k][x];
+          const float sm = hi + (float)dl[x];  // two-sum of hi and the shift
+          const float bb = sm - hi;
+          const float er = (hi - (sm - bb)) + ((float)dl[x] - bb);
+          const float lo = c.mulo[k][x] + er;
+          const float h2 = sm + lo;  // renormalise
+          mlo[x] = lo - (h2 - sm);
+          mun[x] = (R)h2;
+        } else {
+          mu64[x] = c.mu[k][x] + (double)dl[x];
+          mun[x] = (R)mu64[x];
+        }
+      }
+      int t = 0;
+      for (int x = 0; x < D; ++x)
+        for (int yy = x; yy < D; ++yy, ++t) Sn[t] = sv[1 + D + t] * rN - dl[x] * dl[yy];
+      R Lc[3][3], ri[3];
+      bool pd;
+      if constexpr (sizeof(R) == 4)
+        pd = chol_whitened<D, R, float>(Sn, mun, c.meanf, c.scf, Lc, ri);
+      else
+        pd = chol_whitened<D, R, double>(Sn, mun, c.mean, c.sc, Lc, ri);
+      if (!pd) {
+        c.status |= GM_ST_COV_NOT_PD;
+        if (K > 1) {
+          removed = true;
+        } else {
+          c.pstate = 0;  // a lone component keeps its parameters
+          c.k = k + 1;
+        }
+      } else {
+        // eq. (omegak), then the renormalisation of step 3 through Z
+        const R wn = (K == 1) ? (R)1 : (Nk - (R)halfT) * rcp_nr(c.NdR - (R)halfT * (R)K);
+        const R un = wn * c.Z;
+        c.Z = c.Z - c.u[k] + un;
+        c.u[k] = un;
+        float eA[NM], elc;
+        make_econst<D, R>(Lc, ri, eA, elc);
+        for (int x = 0; x < D; ++x) {
+          if constexpr (sizeof(R) == 4)
+            c.mulo[k][x] = mlo[x];
+          else
+            c.mu[k][x] = mu64[x];
+          c.emu[k][x] = (float)mun[x];
+        }
+        for (int q = 0; q < NM; ++q) c.eA[k][q] = eA[q];
+        c.elc[k] = elc;
+        c.eb[k] = log2f((float)un) + elc;
+        pack_econst<D>(c.emu[k], c.eA[k], c.eb[k], c.ec[k]);
+        for (int q = 0; q < NC; ++q) c.ec[kMaxK][q] = c.ec[k][q];
+        c.pstate = 1;
+        c.k = k + 1;
+      }
+    }
+    if (removed) {
+      c.Z -= c.u[k];
+      for (int m = k; m < K - 1; ++m) {
+        c.u[m] = c.u[m + 1];
+        for (int x = 0; x < D; ++x) {
+          c.mu[m][x] = c.mu[m + 1][x];
+          c.emu[m][x] = c.emu[m + 1][x];
+          c.mulo[m][x] = c.mulo[m + 1][x];
+        }
+        for (int q = 0; q < NM; ++q) c.eA[m][q] = c.eA[m + 1][q];
+        for (int q = 0; q < NC; ++q) c.ec[m][q] = c.ec[m + 1][q];
+        c.elc[m] = c.elc[m + 1];
+        c.eb[m] = c.eb[m + 1];
+      }
+      c.K = K - 1;
+      c.annih = 1;
+      c.pstate = 2;
+    }
+  };
 
   // ---- exact pass: s_p, m_p and eq. (lnL-GM) ------------------------------
-  auto resync = [&]() {
+  // m_p = max_k log2(u_k f_k), then s_p = sum_k 2^(log2(u_k f_k) - m_p) (so
+  // s_p >= 1).  The per-particle log-likelihood enters the sum minus a
+  // per-cell constant c0 close to its mean, which keeps the FP32 partial
+  // sums small.  With stats0 the pass also yields component 0's E-step
+  // statistics (the first step of the next sweep).  Per-warp partials:
+  // c.redf[w][0 .. NS-1] statistics, c.redf[w][NS] the centred sum.
+  auto exact_pass = [&](bool stats0) {
     const int K = c.K;
-    float acc = 0.0f;
+    const float c0 = c.c0;
+    float accl = 0.0f;
+    f32x2 acc[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) acc[q] = 0ull;
     for (int pp = tid; pp < P2; pp += NT) {
-      f32x2 y[D], d[D];
+      f32x2 y[D], d[D], d0[D];
 #pragma unroll
       for (int q = 0; q < D; ++q) y[q] = Y2[q * st2 + pp];
-      float m0 = -3.0e38f, s0 = 0.0f, m1 = -3.0e38f, s1 = 0.0f;
+      float m0 = -3.0e38f, m1 = -3.0e38f;
       for (int k = 0; k < K; ++k) {
         float l0, l1;
         upk2(lg_eval2<D>(c.ec[k], y, d), l0, l1);
-        const float t0 = ex2(-fabsf(l0 - m0)), t1 = ex2(-fabsf(l1 - m1));
-        s0 = (l0 > m0) ? fmaf(s0, t0, 1.0f) : s0 + t0;
-        s1 = (l1 > m1) ? fmaf(s1, t1, 1.0f) : s1 + t1;
         m0 = fmaxf(m0, l0);
         m1 = fmaxf(m1, l1);
       }
-      SS2[pp] = pk2(s0, s1);
-      MM2[pp] = pk2(-m0, -m1);
-      float a0, a1;
-      upk2(AH2[pp], a0, a1);
-      acc = fmaf(a0, m0 + lg2(s0), acc);
-      acc = fmaf(a1, m1 + lg2(s1), acc);
+      const f32x2 nm = pk2(-m0, -m1);
+      float x0, x1;
+      upk2(add2(lg_eval2<D>(c.ec[0], y, d0), nm), x0, x1);
+      const f32x2 G = pk2(ex2(x0), ex2(x1));
+      f32x2 sp = G;
+      for (int k = 1; k < K; ++k) {
+        upk2(add2(lg_eval2<D>(c.ec[k], y, d), nm), x0, x1);
+        sp = add2(sp, pk2(ex2(x0), ex2(x1)));
+      }
+      SS2[pp] = sp;
+      MM2[pp] = nm;
+      const f32x2 ah = AH2[pp];
+      float s0, s1, a0, a1;
+      upk2(sp, s0, s1);
+      upk2(ah, a0, a1);
+      accl = fmaf(a0, (m0 - c0) + lg2(s0), accl);
+      accl = fmaf(a1, (m1 - c0) + lg2(s1), accl);
+      if (stats0) {
+        GG2[pp] = G;
+        const f32x2 gam = mul2(ah, mul2(G, pk2(rcp_approx(s0), rcp_approx(s1))));
+        acc[0] = add2(acc[0], gam);
+        int t = 1 + D;
+#pragma unroll
+        for (int x = 0; x < D; ++x) {
+          const f32x2 gd = mul2(gam, d0[x]);
+          acc[1 + x] = add2(acc[1 + x], gd);
+#pragma unroll
+          for (int yy = x; yy < D; ++yy, ++t) acc[t] = fma2(gd, d0[yy], acc[t]);
+        }
+      }
     }
-    double v1[1] = {(double)acc};
-    block_sum_d<D, NT, 1, R>(c, v1);
+    float v[NS + 1];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      float lo, hi;
+      upk2(acc[q], lo, hi);
+      v[q] = lo + hi;
+    }
+    v[NS] = accl;
+    block_partials<NS + 1, NRED, NW>(v, c.redf);
+  };
+
+  // warp 0 after exact_pass: the cross-warp sums (returned in sv by every
+  // lane of warp 0) and eq. (lnL-GM) into c.L (lane 0)
+  auto finish_exact = [&](R (&sv)[NS + 1]) {
+    const int K = c.K;
+    R stat = 0;
+    if (lane <= NS)
+      for (int q = 0; q < NW; ++q) stat += (R)c.redf[q][lane];
+#pragma unroll
+    for (int q = 0; q <= NS; ++q) sv[q] = __shfl_sync(0xffffffffu, stat, q);
+    float pen = lane < K ? logf((float)(c.u[lane] / c.Z)) : 0.0f;
+    pen = warp_sum(pen);
+    if (lane == 0) {
+      const double lsum = (double)sv[NS] + (double)c.c0 * c.sumAH;
+      const double dpar = (double)K * (T + 1) - 1.0;
+      c.L = lsum * kLn2 - c.Nd * c.logjac - 0.5 * dpar * c.logN - 0.5 * T * (double)pen;
+      if (c.sumAH > 0.0) c.c0 = (float)(lsum / c.sumAH);
+    }
+  };
+
+  // ---- sweeps -------------------------------------------------------------
+  for (;;) {
+    // exact pass after the previous sweep, fused with the first component
+    // step of the next one (discarded when EM stops here)
+    exact_pass(true);
     if (tid < 32) {
-      float pen = lane < K ? logf((float)(c.u[lane] / c.Z)) : 0.0f;
-      pen = warp_sum(pen);
+      R sv[NS + 1];
+      finish_exact(sv);
       if (lane == 0) {
-        const double dpar = (double)K * (T + 1) - 1.0;
-        c.L = c.res[0] * kLn2 - c.Nd * c.logjac - 0.5 * dpar * c.logN - 0.5 * T * (double)pen;
+        if (c.sweep > 0 && !c.annih && fabs(c.L - c.Lprev) <= a.tol * fabs(c.Lprev))
+          c.done = 1;
+        else if (c.sweep >= a.max_sweeps)
+          c.done = 2;
+        c.Lprev = c.L;
+        if (!c.done) {
+          c.sweep = c.sweep + 1;
+          c.annih = 0;
+          c.k = 0;
+          c.pstate = 0;
+          mstep(0, sv);
+        }
       }
     }
     __syncthreads();
-  };
-
-  resync();
-  if (tid == 0) c.Lprev = c.L;
-  __syncthreads();
-
-  // ---- sweeps -------------------------------------------------------------
-  for (int sweep = 1; sweep <= a.max_sweeps; ++sweep) {
-    if (tid == 0) {
-      c.k = 0;
-      c.annih = 0;
-      c.pstate = 0;
-    }
-    __syncthreads();
+    if (c.done) break;
     while (c.k < c.K) {
       const int k = c.k;
       const int ps = c.pstate;
@@ -473,27 +700,29 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
 #pragma unroll
         for (int q = 0; q < D; ++q) y[q] = Y2[q * st2 + pp];
         const f32x2 nm = MM2[pp];  // -m
-        f32x2 s = SS2[pp];
+        f32x2 sp = SS2[pp];
         if (ps == 1) {  // previous component updated: replace its term
           float x0, x1;
           upk2(add2(lg_eval2<D>(ep, y, d), nm), x0, x1);
           const float gn0 = ex2(fminf(x0, 100.0f)), gn1 = ex2(fminf(x1, 100.0f));
           float sn0, sn1;
-          upk2(add2(fma2(GG2[pp], bc2(-1.0f), s), pk2(gn0, gn1)), sn0, sn1);
-          s = pk2(fmaxf(sn0, gn0), fmaxf(sn1, gn1));
+          upk2(add2(fma2(GG2[pp], bc2(-1.0f), sp), pk2(gn0, gn1)), sn0, sn1);
+          sp = pk2(fmaxf(sn0, gn0), fmaxf(sn1, gn1));
         } else if (ps == 2) {  // previous component removed
-          s = fma2(GG2[pp], bc2(-1.0f), s);
+          sp = fma2(GG2[pp], bc2(-1.0f), sp);
         }
+        // component k is unchanged since the exact pass, whose m_p is the
+        // largest of these very terms: the exponent is <= 0
         float x0, x1;
         upk2(add2(lg_eval2<D>(ek, y, d), nm), x0, x1);
-        const float g0 = ex2(fminf(x0, 100.0f)), g1 = ex2(fminf(x1, 100.0f));
-        GG2[pp] = pk2(g0, g1);
-        SS2[pp] = s;
-        float s0, s1;
-        upk2(s, s0, s1);
-        const float r0 = rcp_approx(fmaxf(fmaxf(s0, g0), 1e-30f));
-        const float r1 = rcp_approx(fmaxf(fmaxf(s1, g1), 1e-30f));
-        const f32x2 gam = mul2(AH2[pp], pk2(g0 * r0, g1 * r1));
+        const f32x2 G = pk2(ex2(x0), ex2(x1));
+        GG2[pp] = G;
+        SS2[pp] = sp;
+        float s0, s1, g0, g1;
+        upk2(sp, s0, s1);
+        upk2(G, g0, g1);
+        const f32x2 rr = pk2(rcp_approx(max3f(s0, g0, 1e-30f)), rcp_approx(max3f(s1, g1, 1e-30f)));
+        const f32x2 gam = mul2(AH2[pp], mul2(G, rr));
         acc[0] = add2(acc[0], gam);
         int t = 1 + D;
 #pragma unroll
@@ -504,18 +733,14 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
           for (int yy = x; yy < D; ++yy, ++t) acc[t] = fma2(gd, d[yy], acc[t]);
         }
       }
-      // warp (FP32) then cross-warp (precision R) reduction
-      float accs[NS];
+      float v[NS];
 #pragma unroll
       for (int q = 0; q < NS; ++q) {
         float lo, hi;
         upk2(acc[q], lo, hi);
-        accs[q] = warp_sum(lo + hi);
+        v[q] = lo + hi;
       }
-      if (lane == 0)
-#pragma unroll
-        for (int q = 0; q < NS; ++q) c.redf[wid][q] = accs[q];
-      __syncthreads();
+      block_partials<NS, NRED, NW>(v, c.redf);
       if (tid < 32) {
         R stat = 0;
         if (lane < NS)
@@ -523,89 +748,11 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
         R sv[NS];
 #pragma unroll
         for (int q = 0; q < NS; ++q) sv[q] = __shfl_sync(0xffffffffu, stat, q);
-        if (lane == 0) {
-          // ---- M-step for component k (eqs. muk, sigmak, omegak) ----------
-          c.kwork++;
-          const int K = c.K;
-          const R Nk = sv[0];
-          bool removed = false;
-          if (K > 1 && Nk - (R)halfT <= (R)0) {
-            removed = true;
-          } else {
-            const R rN = rcp_nr(Nk);
-            R dl[D], mun[D], Sn[NM];
-            // The statistics are about the FP32 copy of the mean that the
-            // E-step used; the shift is added to the FP64 mean, which
-            // thereby keeps the sub-ulp part of every update (the FP32 copy
-            // then follows the FP64 trajectory instead of stalling when an
-            // update is below its resolution).
-            double mu64[D];
-            for (int x = 0; x < D; ++x) {
-              dl[x] = sv[1 + x] * rN;
-              mu64[x] = c.mu[k][x] + (double)dl[x];
-              mun[x] = (R)mu64[x];
-            }
-            int t = 0;
-            for (int x = 0; x < D; ++x)
-              for (int yy = x; yy < D; ++yy, ++t) Sn[t] = sv[1 + D + t] * rN - dl[x] * dl[yy];
-            R Lc[3][3], ri[3];
-            bool pd;
-            if constexpr (sizeof(R) == 4)
-              pd = chol_whitened<D, R, float>(Sn, mun, c.meanf, c.scf, Lc, ri);
-            else
-              pd = chol_whitened<D, R, double>(Sn, mun, c.mean, c.sc, Lc, ri);
-            if (!pd) {
-              c.status |= GM_ST_COV_NOT_PD;
-              if (K > 1) {
-                removed = true;
-              } else {
-                c.pstate = 0;  // a lone component keeps its parameters
-                c.k = k + 1;
-              }
-            } else {
-              // eq. (omegak), then the renormalisation of step 3 through Z
-              const R wn =
-                  (K == 1) ? (R)1 : (Nk - (R)halfT) * rcp_nr((R)c.Nd - (R)halfT * (R)K);
-              const R un = wn * c.Z;
-              c.Z = c.Z - c.u[k] + un;
-              c.u[k] = un;
-              float eA[NM], elc;
-              make_econst<D, R>(Lc, ri, eA, elc);
-              for (int x = 0; x < D; ++x) {
-                c.mu[k][x] = mu64[x];
-                c.emu[k][x] = (float)mun[x];
-              }
-              for (int q = 0; q < NM; ++q) c.eA[k][q] = eA[q];
-              c.elc[k] = elc;
-              c.eb[k] = log2f((float)un) + elc;
-              pack_econst<D>(c.emu[k], c.eA[k], c.eb[k], c.ec[k]);
-              for (int q = 0; q < NC; ++q) c.ec[kMaxK][q] = c.ec[k][q];
-              c.pstate = 1;
-              c.k = k + 1;
-            }
-          }
-          if (removed) {
-            c.Z -= c.u[k];
-            for (int m = k; m < K - 1; ++m) {
-              c.u[m] = c.u[m + 1];
-              for (int x = 0; x < D; ++x) {
-                c.mu[m][x] = c.mu[m + 1][x];
-                c.emu[m][x] = c.emu[m + 1][x];
-              }
-              for (int q = 0; q < NM; ++q) c.eA[m][q] = c.eA[m + 1][q];
-              for (int q = 0; q < NC; ++q) c.ec[m][q] = c.ec[m + 1][q];
-              c.elc[m] = c.elc[m + 1];
-              c.eb[m] = c.eb[m + 1];
-            }
-            c.K = K - 1;
-            c.annih = 1;
-            c.pstate = 2;
-          }
-        }
+        if (lane == 0) mstep(k, sv);
       }
       __syncthreads();
     }
-    // normalise the weights, then the exact pass and the convergence test
+    // normalise the weights (step 3 made explicit once per sweep)
     if (tid < c.K) {
       const R un = c.u[tid] / c.Z;
       c.u[tid] = un;
@@ -615,16 +762,13 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
     __syncthreads();
     if (tid == 0) c.Z = (R)1;
     __syncthreads();
-    resync();
-    if (tid == 0) {
-      c.sweep = sweep;
-      if (!c.annih && fabs(c.L - c.Lprev) <= a.tol * fabs(c.Lprev)) c.done = 1;
-      c.Lprev = c.L;
-    }
-    __syncthreads();
-    if (c.done) break;
   }
-  if (tid == 0 && !c.done) c.status |= GM_ST_EM_MAXSWEEPS;
+  if (tid == 0 && c.done == 2) c.status |= GM_ST_EM_MAXSWEEPS;
+  if constexpr (sizeof(R) == 4) {  // FP64 means from the hi + lo pairs
+    if (tid < c.K)
+      for (int x = 0; x < D; ++x) c.mu[tid][x] = (double)c.emu[tid][x] + (double)c.mulo[tid][x];
+    __syncthreads();
+  }
 
   // ---- final unpenalised step (Sec. 2.3.1), FP64 ---------------------------
   if (tid == 0) c.Kf = 0;
@@ -723,7 +867,14 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
     c.Z = (R)1;
   }
   __syncthreads();
-  if (c.final_pd) resync();
+  if (c.final_pd) {
+    exact_pass(false);
+    if (tid < 32) {
+      R sv[NS + 1];
+      finish_exact(sv);
+    }
+    __syncthreads();
+  }
   if (tid == 0) {
     const int Kf = c.K;
     for (int k = 0; k < Kf; ++k) {
