@@ -95,7 +95,10 @@ struct EmCtl {
   f32x2 ec[kMaxK + 1][NConst<D>::N];
   double mean[D], sc[D], isc[D];
   float meanf[D], scf[D];
-  double Nd, W, L, Lprev, logjac, logN;
+  double Nd, W, L, logjac, logN;
+  // FP32 convergence test on the centred log-likelihood (natural log, up to
+  // the constant Lbase that c0 removes)
+  float Lf, Lfprev, Lbase, halfLogNf;
   double sumAH;  // sum of the staged FP32 weights
   float c0;      // centring constant of the log-likelihood sum (log2 units)
   R NdR;
@@ -188,7 +191,7 @@ __device__ void make_econst(const R (&Lc)[3][3], const R (&ri)[3], float* eA, fl
   const float c = 0.84932180028801904272f;  // sqrt(log2(e) / 2)
   if (D == 1) {
     eA[0] = c * (float)ri[0];
-    elc = -log2f((float)Lc[0][0]) - 0.5f * 2.6514961294723187f;  // log2(2 pi) / 2
+    elc = -lg2((float)Lc[0][0]) - 0.5f * 2.6514961294723187f;  // log2(2 pi) / 2
   } else {
     const R i00 = ri[0], i11 = ri[1], i22 = ri[2];
     const R i10 = -Lc[1][0] * i00 * i11;
@@ -200,7 +203,7 @@ __device__ void make_econst(const R (&Lc)[3][3], const R (&ri)[3], float* eA, fl
     eA[3] = c * (float)i20;
     eA[4] = c * (float)i21;
     eA[5] = c * (float)i22;
-    elc = -log2f((float)Lc[0][0]) - log2f((float)Lc[1][1]) - log2f((float)Lc[2][2]) -
+    elc = -lg2((float)Lc[0][0]) - lg2((float)Lc[1][1]) - lg2((float)Lc[2][2]) -
           1.5f * 2.6514961294723187f;
   }
 }
@@ -370,6 +373,7 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
       c.sumAH = c.res[0];
       c.c0 = -2.0471975511965976f * D;  // mean log2 density of a standard normal
       c.NdR = (R)c.Nd;
+      c.halfLogNf = (float)(0.5 * c.logN);
     }
   }
   // ---- initialisation --------------------------------------------------
@@ -410,7 +414,7 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
       }
       for (int k = 0; k < K; ++k) {
         c.u[k] = (R)((double)c.u[k] / wsum);
-        c.eb[k] = log2f((float)c.u[k]) + c.elc[k];
+        c.eb[k] = lg2((float)c.u[k]) + c.elc[k];
         pack_econst<D>(c.emu[k], c.eA[k], c.eb[k], c.ec[k]);
       }
       c.K = K;
@@ -461,7 +465,7 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
       }
       for (int i = 0; i < NM; ++i) c.eA[k][i] = eA[i];
       c.elc[k] = elc;
-      c.eb[k] = log2f((float)c.u[k]) + elc;
+      c.eb[k] = lg2((float)c.u[k]) + elc;
       pack_econst<D>(c.emu[k], c.eA[k], c.eb[k], c.ec[k]);
     }
   }
@@ -483,7 +487,7 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
   // ---- M-step for component k (eqs. muk, sigmak, omegak), one thread -----
   // sv: N_k, the first moments and the second moments about the FP32 mean
   // the E-step used.
-  auto mstep = [&](int k, const R* sv) {
+  auto mstep = [&](int k, const R (&sv)[NS + 1]) {
     c.kwork++;
     const int K = c.K;
     const R Nk = sv[0];
@@ -549,9 +553,16 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
         }
         for (int q = 0; q < NM; ++q) c.eA[k][q] = eA[q];
         c.elc[k] = elc;
-        c.eb[k] = log2f((float)un) + elc;
-        pack_econst<D>(c.emu[k], c.eA[k], c.eb[k], c.ec[k]);
-        for (int q = 0; q < NC; ++q) c.ec[kMaxK][q] = c.ec[k][q];
+        const float eb = lg2((float)un) + elc;
+        c.eb[k] = eb;
+        float emu[D];
+        for (int x = 0; x < D; ++x) emu[x] = (float)mun[x];
+        f32x2 ec[NC];
+        pack_econst<D>(emu, eA, eb, ec);
+        for (int q = 0; q < NC; ++q) {
+          c.ec[k][q] = ec[q];
+          c.ec[kMaxK][q] = ec[q];
+        }
         c.pstate = 1;
         c.k = k + 1;
       }
@@ -644,21 +655,38 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
   };
 
   // warp 0 after exact_pass: the cross-warp sums (returned in sv by every
-  // lane of warp 0) and eq. (lnL-GM) into c.L (lane 0)
-  auto finish_exact = [&](R (&sv)[NS + 1]) {
+  // lane of warp 0) and eq. (lnL-GM) (lane 0): the FP32 centred value c.Lf
+  // for the convergence test, and with full the FP64 value c.L.  The first
+  // pass of a cell fixes c0 at the mean per-particle term, so that later
+  // passes sum small deviations.  The weights are normalised here (Z = 1).
+  auto finish_exact = [&](R (&sv)[NS + 1], bool full) {
     const int K = c.K;
-    R stat = 0;
-    if (lane <= NS)
-      for (int q = 0; q < NW; ++q) stat += (R)c.redf[q][lane];
+    R st[NW];
 #pragma unroll
-    for (int q = 0; q <= NS; ++q) sv[q] = __shfl_sync(0xffffffffu, stat, q);
-    float pen = lane < K ? logf((float)(c.u[lane] / c.Z)) : 0.0f;
-    pen = warp_sum(pen);
+    for (int q = 0; q < NW; ++q) st[q] = lane <= NS ? (R)c.redf[q][lane] : (R)0;
+#pragma unroll
+    for (int h = NW / 2; h >= 1; h >>= 1)
+#pragma unroll
+      for (int q = 0; q < h; ++q) st[q] += st[q + h];
+#pragma unroll
+    for (int q = 0; q <= NS; ++q) sv[q] = __shfl_sync(0xffffffffu, st[0], q);
+    float pen = lane < K ? lg2((float)c.u[lane]) : 0.0f;  // log2 units
+    pen = warp_sum(pen) * (float)kLn2;
     if (lane == 0) {
-      const double lsum = (double)sv[NS] + (double)c.c0 * c.sumAH;
-      const double dpar = (double)K * (T + 1) - 1.0;
-      c.L = lsum * kLn2 - c.Nd * c.logjac - 0.5 * dpar * c.logN - 0.5 * T * (double)pen;
-      if (c.sumAH > 0.0) c.c0 = (float)(lsum / c.sumAH);
+      const int dpar = K * (T + 1) - 1;
+      if (full || c.sweep == 0) {
+        const double lsum = (double)sv[NS] + (double)c.c0 * c.sumAH;
+        const double pc = -0.5 * dpar * c.logN - 0.5 * T * (double)pen;
+        c.L = lsum * kLn2 - c.Nd * c.logjac + pc;
+        if (!full) {
+          const float c0n = c.sumAH > 0.0 ? (float)(lsum / c.sumAH) : c.c0;
+          c.c0 = c0n;
+          c.Lf = (float)((lsum - (double)c0n * c.sumAH) * kLn2 + pc);
+          c.Lbase = (float)((double)c0n * c.sumAH * kLn2 - c.Nd * c.logjac);
+        }
+      } else {
+        c.Lf = (float)kLn2 * (float)sv[NS] - c.halfLogNf * (float)dpar - 0.5f * T * pen;
+      }
     }
   };
 
@@ -669,13 +697,14 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
     exact_pass(true);
     if (tid < 32) {
       R sv[NS + 1];
-      finish_exact(sv);
+      finish_exact(sv, false);
       if (lane == 0) {
-        if (c.sweep > 0 && !c.annih && fabs(c.L - c.Lprev) <= a.tol * fabs(c.Lprev))
+        if (c.sweep > 0 && !c.annih &&
+            fabsf(c.Lf - c.Lfprev) <= (float)a.tol * fabsf(c.Lfprev + c.Lbase))
           c.done = 1;
         else if (c.sweep >= a.max_sweeps)
           c.done = 2;
-        c.Lprev = c.L;
+        c.Lfprev = c.Lf;
         if (!c.done) {
           c.sweep = c.sweep + 1;
           c.annih = 0;
@@ -742,12 +771,17 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
       }
       block_partials<NS, NRED, NW>(v, c.redf);
       if (tid < 32) {
-        R stat = 0;
-        if (lane < NS)
-          for (int q = 0; q < NW; ++q) stat += (R)c.redf[q][lane];
-        R sv[NS];
+        R st[NW];
 #pragma unroll
-        for (int q = 0; q < NS; ++q) sv[q] = __shfl_sync(0xffffffffu, stat, q);
+        for (int q = 0; q < NW; ++q) st[q] = lane < NS ? (R)c.redf[q][lane] : (R)0;
+#pragma unroll
+        for (int h = NW / 2; h >= 1; h >>= 1)
+#pragma unroll
+          for (int q = 0; q < h; ++q) st[q] += st[q + h];
+        R sv[NS + 1];
+#pragma unroll
+        for (int q = 0; q < NS; ++q) sv[q] = __shfl_sync(0xffffffffu, st[0], q);
+        sv[NS] = (R)0;
         if (lane == 0) mstep(k, sv);
       }
       __syncthreads();
@@ -756,7 +790,7 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
     if (tid < c.K) {
       const R un = c.u[tid] / c.Z;
       c.u[tid] = un;
-      c.eb[tid] = log2f((float)un) + c.elc[tid];
+      c.eb[tid] = lg2((float)un) + c.elc[tid];
       pack_econst<D>(c.emu[tid], c.eA[tid], c.eb[tid], c.ec[tid]);
     }
     __syncthreads();
@@ -857,7 +891,7 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
         pd = 0;
       }
       for (int x = 0; x < D; ++x) c.emu[k][x] = (float)mw[x];
-      c.eb[k] = log2f((float)c.fw[k]) + c.elc[k];
+      c.eb[k] = lg2((float)c.fw[k]) + c.elc[k];
       c.u[k] = (R)c.fw[k];
       pack_econst<D>(c.emu[k], c.eA[k], c.eb[k], c.ec[k]);
     }
@@ -871,7 +905,7 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
     exact_pass(false);
     if (tid < 32) {
       R sv[NS + 1];
-      finish_exact(sv);
+      finish_exact(sv, true);
     }
     __syncthreads();
   }
