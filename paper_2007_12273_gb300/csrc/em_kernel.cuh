@@ -56,12 +56,16 @@ struct EmParams {
   uint64_t seed;
 };
 
-// float offset of cell j's global tile: even, and disjoint from its
-// neighbours' tiles of N_j rounded up to even length
+// float offset o of cell j's global tile: even, and disjoint from its
+// neighbours' tiles of N_j rounded up to even length.  Its velocity arrays
+// start at o (stride: scratch_stride floats), its two pair records at
+// D * stride + 2 o and (D + 2) * stride + 2 o.
 __host__ __device__ inline int64_t scratch_offset(int64_t off, int64_t j) {
   return off + 2 * j + (off & 1);
 }
-__host__ inline int64_t scratch_stride(int64_t n, int64_t C) { return n + 2 * C + 2; }
+// floats per array of the global tile; a multiple of 4, so that the pair
+// records are 16-byte aligned
+__host__ inline int64_t scratch_stride(int64_t n, int64_t C) { return (n + 2 * C + 2 + 3) & ~(int64_t)3; }
 
 constexpr double kLn2 = 0.69314718055994530942;
 
@@ -322,16 +326,19 @@ __device__ __forceinline__ void block_partials(const float (&v)[NV], float (&red
 }
 
 // ---------------------------------------------------------------------------
-// one cell, after its moments are known and it is not degenerate.
-// base: the particle tile (shared or global), st: floats per array (even).
-// Arrays: Y[d] (whitened v), AH (normalised alpha), SS (s_p), MM (-m_p),
-// GG (the current component's term); N rounded up to even with a
-// zero-weight pad particle.
+// one cell, after its moments are known and it is not degenerate.  The
+// particle tile (shared or global) holds N rounded up to even particles (a
+// zero-weight pad particle) as pairs:
+//   Y[d][p]  whitened velocity, array d at Y + d * ys
+//   SMT[pp]  16 bytes per pair: {s_p (2), -m_p (2)}
+//   GAT[pp]  16 bytes per pair: {the current component's term (2), the
+//            normalised weights (2)}
+// so a pair's state is read with one 16-byte load per record.
 // ---------------------------------------------------------------------------
 template <int D, int NT, typename VT, typename R>
 __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32, R>& c,
-                                             int64_t j, int64_t off, int N, float* base,
-                                             int st) {
+                                             int64_t j, int64_t off, int N, float* Y, int ys,
+                                             float* SMT, float* GAT) {
   constexpr int NW = NT / 32;
   constexpr int NM = D * (D + 1) / 2;
   constexpr int NS = 1 + D + NM;
@@ -342,13 +349,8 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const VT* __restrict__ vin = static_cast<const VT*>(a.v);
   double* prm_out = a.params_out + (size_t)j * a.Kmax * P;
-  float* Y = base;
-  float* AH = base + D * st;
-  float* SS = base + (D + 1) * st;
-  float* MM = base + (D + 2) * st;
-  float* GG = base + (D + 3) * st;
   const int P2 = (N + 1) >> 1;  // particle pairs
-  const int st2 = st >> 1;
+  const int ys2 = ys >> 1;
 
   // ---- stage whitened velocities and normalised weights ------------------
   {
@@ -358,14 +360,14 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
       if (p < N) {
 #pragma unroll
         for (int d = 0; d < D; ++d)
-          Y[d * st + p] = (float)(((double)vin[(int64_t)d * a.n + off + p] - c.mean[d]) * c.isc[d]);
+          Y[d * ys + p] = (float)(((double)vin[(int64_t)d * a.n + off + p] - c.mean[d]) * c.isc[d]);
         const float ah = (float)(a.alpha[off + p] * nw);
-        AH[p] = ah;
+        GAT[4 * (p >> 1) + 2 + (p & 1)] = ah;
         sa[0] += (double)ah;
       } else {  // zero-weight pad particle
 #pragma unroll
-        for (int d = 0; d < D; ++d) Y[d * st + p] = 0.0f;
-        AH[p] = 0.0f;
+        for (int d = 0; d < D; ++d) Y[d * ys + p] = 0.0f;
+        GAT[4 * (p >> 1) + 2 + (p & 1)] = 0.0f;
       }
     }
     block_sum_d<D, NT, 1, R>(c, sa);
@@ -478,10 +480,9 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
   __syncthreads();
 
   const f32x2* Y2 = reinterpret_cast<const f32x2*>(Y);
-  const f32x2* AH2 = reinterpret_cast<const f32x2*>(AH);
-  f32x2* SS2 = reinterpret_cast<f32x2*>(SS);
-  f32x2* MM2 = reinterpret_cast<f32x2*>(MM);
-  f32x2* GG2 = reinterpret_cast<f32x2*>(GG);
+  ulonglong2* SM4 = reinterpret_cast<ulonglong2*>(SMT);
+  ulonglong2* GA4 = reinterpret_cast<ulonglong2*>(GAT);
+  f32x2* GG2 = reinterpret_cast<f32x2*>(GAT);  // term of pair pp at GG2[2 * pp]
   constexpr int NRED = EmCtl<D, NW, R>::NRED;
 
   // ---- M-step for component k (eqs. muk, sigmak, omegak), one thread -----
@@ -588,13 +589,17 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
   };
 
   // ---- exact pass: s_p, m_p and eq. (lnL-GM) ------------------------------
-  // m_p = max_k log2(u_k f_k), then s_p = sum_k 2^(log2(u_k f_k) - m_p) (so
-  // s_p >= 1).  The per-particle log-likelihood enters the sum minus a
-  // per-cell constant c0 close to its mean, which keeps the FP32 partial
-  // sums small.  With stats0 the pass also yields component 0's E-step
-  // statistics (the first step of the next sweep).  Per-warp partials:
-  // c.redf[w][0 .. NS-1] statistics, c.redf[w][NS] the centred sum.
-  auto exact_pass = [&](bool stats0) {
+  // s_p = sum_k 2^(log2(u_k f_k) - m_p).  A fresh pass (the first of a cell,
+  // or a pair whose sum left [1e-30, 1e30]) takes m_p = max_k log2(u_k f_k),
+  // so s_p >= 1; otherwise the pair keeps its previous shift m_p, which saves
+  // the pass for the maximum.  Either way every unchanged component's term
+  // stays below 1e30 until the next exact pass.  The per-particle
+  // log-likelihood enters the sum minus a per-cell constant c0 close to its
+  // mean, which keeps the FP32 partial sums small.  With stats0 the pass also
+  // yields component 0's E-step statistics (the first step of the next
+  // sweep).  Per-warp partials: c.redf[w][0 .. NS-1] statistics,
+  // c.redf[w][NS] the centred sum.
+  auto exact_pass = [&](bool stats0, bool fresh) {
     const int K = c.K;
     const float c0 = c.c0;
     float accl = 0.0f;
@@ -604,33 +609,49 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
     for (int pp = tid; pp < P2; pp += NT) {
       f32x2 y[D], d[D], d0[D];
 #pragma unroll
-      for (int q = 0; q < D; ++q) y[q] = Y2[q * st2 + pp];
-      float m0 = -3.0e38f, m1 = -3.0e38f;
-      for (int k = 0; k < K; ++k) {
-        float l0, l1;
-        upk2(lg_eval2<D>(c.ec[k], y, d), l0, l1);
-        m0 = fmaxf(m0, l0);
-        m1 = fmaxf(m1, l1);
+      for (int q = 0; q < D; ++q) y[q] = Y2[q * ys2 + pp];
+      f32x2 nm, sp, G;
+      float x0, x1, s0 = 0.0f, s1 = 0.0f;
+      bool slow = fresh;
+      if (!fresh) {
+        nm = SM4[pp].y;
+        upk2(add2(lg_eval2<D>(c.ec[0], y, d0), nm), x0, x1);
+        G = pk2(ex2(x0), ex2(x1));
+        sp = G;
+        for (int k = 1; k < K; ++k) {
+          upk2(add2(lg_eval2<D>(c.ec[k], y, d), nm), x0, x1);
+          sp = add2(sp, pk2(ex2(x0), ex2(x1)));
+        }
+        upk2(sp, s0, s1);
+        slow = !(s0 > 1e-30f && s0 < 1e30f && s1 > 1e-30f && s1 < 1e30f);
       }
-      const f32x2 nm = pk2(-m0, -m1);
-      float x0, x1;
-      upk2(add2(lg_eval2<D>(c.ec[0], y, d0), nm), x0, x1);
-      const f32x2 G = pk2(ex2(x0), ex2(x1));
-      f32x2 sp = G;
-      for (int k = 1; k < K; ++k) {
-        upk2(add2(lg_eval2<D>(c.ec[k], y, d), nm), x0, x1);
-        sp = add2(sp, pk2(ex2(x0), ex2(x1)));
+      if (slow) {
+        float m0 = -3.0e38f, m1 = -3.0e38f;
+        for (int k = 0; k < K; ++k) {
+          float l0, l1;
+          upk2(lg_eval2<D>(c.ec[k], y, d), l0, l1);
+          m0 = fmaxf(m0, l0);
+          m1 = fmaxf(m1, l1);
+        }
+        nm = pk2(-m0, -m1);
+        upk2(add2(lg_eval2<D>(c.ec[0], y, d0), nm), x0, x1);
+        G = pk2(ex2(x0), ex2(x1));
+        sp = G;
+        for (int k = 1; k < K; ++k) {
+          upk2(add2(lg_eval2<D>(c.ec[k], y, d), nm), x0, x1);
+          sp = add2(sp, pk2(ex2(x0), ex2(x1)));
+        }
+        upk2(sp, s0, s1);
       }
-      SS2[pp] = sp;
-      MM2[pp] = nm;
-      const f32x2 ah = AH2[pp];
-      float s0, s1, a0, a1;
-      upk2(sp, s0, s1);
+      SM4[pp] = make_ulonglong2(sp, nm);
+      const f32x2 ah = GA4[pp].y;
+      float a0, a1, n0, n1;
       upk2(ah, a0, a1);
-      accl = fmaf(a0, (m0 - c0) + lg2(s0), accl);
-      accl = fmaf(a1, (m1 - c0) + lg2(s1), accl);
+      upk2(nm, n0, n1);
+      accl = fmaf(a0, (-n0 - c0) + lg2(s0), accl);
+      accl = fmaf(a1, (-n1 - c0) + lg2(s1), accl);
       if (stats0) {
-        GG2[pp] = G;
+        GG2[2 * pp] = G;
         const f32x2 gam = mul2(ah, mul2(G, pk2(rcp_approx(s0), rcp_approx(s1))));
         acc[0] = add2(acc[0], gam);
         int t = 1 + D;
@@ -694,7 +715,7 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
   for (;;) {
     // exact pass after the previous sweep, fused with the first component
     // step of the next one (discarded when EM stops here)
-    exact_pass(true);
+    exact_pass(true, c.sweep == 0);
     if (tid < 32) {
       R sv[NS + 1];
       finish_exact(sv, false);
@@ -727,31 +748,33 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
       for (int pp = tid; pp < P2; pp += NT) {
         f32x2 y[D], d[D];
 #pragma unroll
-        for (int q = 0; q < D; ++q) y[q] = Y2[q * st2 + pp];
-        const f32x2 nm = MM2[pp];  // -m
-        f32x2 sp = SS2[pp];
+        for (int q = 0; q < D; ++q) y[q] = Y2[q * ys2 + pp];
+        const ulonglong2 sm = SM4[pp];
+        const ulonglong2 ga = GA4[pp];
+        const f32x2 nm = sm.y;  // -m
+        f32x2 sp = sm.x;
         if (ps == 1) {  // previous component updated: replace its term
           float x0, x1;
           upk2(add2(lg_eval2<D>(ep, y, d), nm), x0, x1);
           const float gn0 = ex2(fminf(x0, 100.0f)), gn1 = ex2(fminf(x1, 100.0f));
           float sn0, sn1;
-          upk2(add2(fma2(GG2[pp], bc2(-1.0f), sp), pk2(gn0, gn1)), sn0, sn1);
+          upk2(add2(fma2(ga.x, bc2(-1.0f), sp), pk2(gn0, gn1)), sn0, sn1);
           sp = pk2(fmaxf(sn0, gn0), fmaxf(sn1, gn1));
         } else if (ps == 2) {  // previous component removed
-          sp = fma2(GG2[pp], bc2(-1.0f), sp);
+          sp = fma2(ga.x, bc2(-1.0f), sp);
         }
-        // component k is unchanged since the exact pass, whose m_p is the
-        // largest of these very terms: the exponent is <= 0
+        // component k is unchanged since the exact pass, which kept its
+        // term below 1e30: no clamp needed
         float x0, x1;
         upk2(add2(lg_eval2<D>(ek, y, d), nm), x0, x1);
         const f32x2 G = pk2(ex2(x0), ex2(x1));
-        GG2[pp] = G;
-        SS2[pp] = sp;
+        GG2[2 * pp] = G;
+        SM4[pp] = make_ulonglong2(sp, nm);
         float s0, s1, g0, g1;
         upk2(sp, s0, s1);
         upk2(G, g0, g1);
         const f32x2 rr = pk2(rcp_approx(max3f(s0, g0, 1e-30f)), rcp_approx(max3f(s1, g1, 1e-30f)));
-        const f32x2 gam = mul2(AH2[pp], mul2(G, rr));
+        const f32x2 gam = mul2(ga.y, mul2(G, rr));
         acc[0] = add2(acc[0], gam);
         int t = 1 + D;
 #pragma unroll
@@ -820,7 +843,7 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
       for (int p = tid; p < N; p += NT) {
         float y[D], d[D];
 #pragma unroll
-        for (int q = 0; q < D; ++q) y[q] = Y[q * st + p];
+        for (int q = 0; q < D; ++q) y[q] = Y[q * ys + p];
         float m = -3.0e38f;
         for (int jj = 0; jj < K; ++jj) m = fmaxf(m, lg_eval<D>(c.emu[jj], c.eA[jj], c.eb[jj], y, d));
         double Ssum = 0.0, gk = 0.0;
@@ -902,7 +925,7 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
   }
   __syncthreads();
   if (c.final_pd) {
-    exact_pass(false);
+    exact_pass(false, true);
     if (tid < 32) {
       R sv[NS + 1];
       finish_exact(sv, true);
@@ -934,7 +957,7 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
 // the cell body on the shared or the global tile
 // ---------------------------------------------------------------------------
 template <int D, int NT, typename VT, typename R>
-__global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
+__global__ void __launch_bounds__(NT, (D == 1 ? 1024 : 512) / NT) em_kernel(EmParams a) {
   constexpr int NW = NT / 32;
   constexpr int NM = D * (D + 1) / 2;
   constexpr int P = 1 + D + NM;
@@ -1065,11 +1088,14 @@ __global__ void __launch_bounds__(NT) em_kernel(EmParams a) {
     }
     if (tid == 0) c.K = 0;
     __syncthreads();
-    if (N + (N & 1) <= a.cap)
-      em_cell_body<D, NT, VT, R>(a, c, j, off, N, tile_smem, a.cap);
-    else
-      em_cell_body<D, NT, VT, R>(a, c, j, off, N, a.scratch + scratch_offset(off, j),
-                                 (int)a.scratch_stride);
+    if (N + (N & 1) <= a.cap) {
+      em_cell_body<D, NT, VT, R>(a, c, j, off, N, tile_smem, a.cap, tile_smem + D * a.cap,
+                                 tile_smem + (D + 2) * a.cap);
+    } else {
+      const int64_t o = scratch_offset(off, j), ss = a.scratch_stride;
+      em_cell_body<D, NT, VT, R>(a, c, j, off, N, a.scratch + o, (int)ss,
+                                 a.scratch + D * ss + 2 * o, a.scratch + (D + 2) * ss + 2 * o);
+    }
   }
 }
 

@@ -142,8 +142,8 @@ static int compress_impl(const gm_config* cfg, int64_t C, int64_t n_particles,
   int nt = cfg->threads_per_cell > 0 ? cfg->threads_per_cell : 256;
   if (nt != 128 && nt != 256) return fail(GM_ERR_ARG, "threads_per_cell must be 128 or 256");
   int cap = cfg->smem_particles > 0 ? cfg->smem_particles : (D == 1 ? 2560 : 3072);
-  cap &= ~1;  // the tile holds particle pairs
-  if (cap < 2) cap = 2;
+  cap &= ~3;  // pair records of 16 bytes behind D arrays of cap floats
+  if (cap < 4) cap = 4;
   const size_t smem = (size_t)cap * (D + 4) * sizeof(float);
   if (smem > 200 * 1024) return fail(GM_ERR_ARG, "smem_particles too large (%d)", cap);
   const int fp64_mstep = (cfg->precision == 1) ? 1 : 0;
