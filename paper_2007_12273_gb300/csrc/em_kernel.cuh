@@ -104,6 +104,7 @@ struct EmCtl {
   // the constant Lbase that c0 removes)
   float Lf, Lfprev, Lbase, halfLogNf;
   double sumAH;  // sum of the staged FP32 weights
+  float sumAHf;
   float c0;      // centring constant of the log-likelihood sum (log2 units)
   R NdR;
   float redf[NW][NRED];
@@ -373,6 +374,7 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
     block_sum_d<D, NT, 1, R>(c, sa);
     if (tid == 0) {
       c.sumAH = c.res[0];
+      c.sumAHf = (float)c.res[0];
       c.c0 = -2.0471975511965976f * D;  // mean log2 density of a standard normal
       c.NdR = (R)c.Nd;
       c.halfLogNf = (float)(0.5 * c.logN);
@@ -675,11 +677,12 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
     block_partials<NS + 1, NRED, NW>(v, c.redf);
   };
 
-  // warp 0 after exact_pass: the cross-warp sums (returned in sv by every
-  // lane of warp 0) and eq. (lnL-GM) (lane 0): the FP32 centred value c.Lf
-  // for the convergence test, and with full the FP64 value c.L.  The first
-  // pass of a cell fixes c0 at the mean per-particle term, so that later
-  // passes sum small deviations.  The weights are normalised here (Z = 1).
+  // warp 0 after a pass that summed the log-likelihood: the cross-warp sums
+  // (returned in sv by every lane of warp 0) and eq. (lnL-GM) (lane 0): the
+  // FP32 centred value c.Lf for the convergence test, and with full the FP64
+  // value c.L.  The first pass of a cell fixes c0 at the mean per-particle
+  // term, so that later passes sum small deviations.  The weights enter as
+  // omega_k = u_k / Z (Z = 1 after an exact pass).
   auto finish_exact = [&](R (&sv)[NS + 1], bool full) {
     const int K = c.K;
     R st[NW];
@@ -691,10 +694,12 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
       for (int q = 0; q < h; ++q) st[q] += st[q + h];
 #pragma unroll
     for (int q = 0; q <= NS; ++q) sv[q] = __shfl_sync(0xffffffffu, st[0], q);
-    float pen = lane < K ? lg2((float)c.u[lane]) : 0.0f;  // log2 units
+    const float lz = lg2((float)c.Z);
+    float pen = lane < K ? lg2((float)c.u[lane]) - lz : 0.0f;  // log2 units
     pen = warp_sum(pen) * (float)kLn2;
     if (lane == 0) {
       const int dpar = K * (T + 1) - 1;
+      sv[NS] -= (R)(c.sumAHf * lz);
       if (full || c.sweep == 0) {
         const double lsum = (double)sv[NS] + (double)c.c0 * c.sumAH;
         const double pc = -0.5 * dpar * c.logN - 0.5 * T * (double)pen;
@@ -711,11 +716,133 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
     }
   };
 
+  // ---- one component step's pass ----------------------------------------
+  // Replaces the previous component's term in s_p (ps = 1: updated, 2:
+  // removed), evaluates component k and accumulates its statistics; with
+  // withL it also sums the centred log-likelihood of s_p after the
+  // replacement (the first step of a sweep without an exact pass: s_p then
+  // holds every component's current term).  A pair whose s_p dropped more
+  // than 64-fold in the replacement (cancellation), or with withL left
+  // [1e-30, 1e30], is recomputed exactly from all components with a fresh
+  // shift.  Terms are clamped at 2^100 relative to the shift.
+  auto comp_pass = [&](int k, int ps, bool withL) {
+    const f32x2* ek = c.ec[k];
+    const f32x2* ep = c.ec[kMaxK];
+    const int K = c.K;
+    const float c0 = c.c0;
+    float accl = 0.0f;
+    f32x2 acc[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) acc[q] = 0ull;
+    for (int pp = tid; pp < P2; pp += NT) {
+      f32x2 y[D], d[D];
+#pragma unroll
+      for (int q = 0; q < D; ++q) y[q] = Y2[q * ys2 + pp];
+      const ulonglong2 sm = SM4[pp];
+      const ulonglong2 ga = GA4[pp];
+      f32x2 nm = sm.y;  // -m
+      f32x2 sp = sm.x;
+      bool fix = false;
+      if (ps != 0) {
+        float so0, so1;
+        upk2(sp, so0, so1);
+        float sn0, sn1;
+        if (ps == 1) {  // previous component updated: replace its term
+          float x0, x1;
+          upk2(add2(lg_eval2<D>(ep, y, d), nm), x0, x1);
+          const float gn0 = ex2(fminf(x0, 100.0f)), gn1 = ex2(fminf(x1, 100.0f));
+          upk2(add2(fma2(ga.x, bc2(-1.0f), sp), pk2(gn0, gn1)), sn0, sn1);
+          sn0 = fmaxf(sn0, gn0);
+          sn1 = fmaxf(sn1, gn1);
+        } else {  // previous component removed
+          upk2(fma2(ga.x, bc2(-1.0f), sp), sn0, sn1);
+        }
+        fix = !(sn0 * 64.0f >= so0 && sn1 * 64.0f >= so1);
+        sp = pk2(sn0, sn1);
+      }
+      if (withL) {
+        float s0, s1;
+        upk2(sp, s0, s1);
+        fix |= !(s0 > 1e-30f && s0 < 1e30f && s1 > 1e-30f && s1 < 1e30f);
+      }
+      float x0, x1;
+      upk2(add2(lg_eval2<D>(ek, y, d), nm), x0, x1);
+      f32x2 G = pk2(ex2(fminf(x0, 100.0f)), ex2(fminf(x1, 100.0f)));
+      if (fix) {  // exact s_p with the largest term as the shift
+        f32x2 dd[D];
+        float m0 = -3.0e38f, m1 = -3.0e38f;
+        for (int j2 = 0; j2 < K; ++j2) {
+          float l0, l1;
+          upk2(lg_eval2<D>(c.ec[j2], y, dd), l0, l1);
+          m0 = fmaxf(m0, l0);
+          m1 = fmaxf(m1, l1);
+        }
+        nm = pk2(-m0, -m1);
+        sp = 0ull;
+        for (int j2 = 0; j2 < K; ++j2) {
+          upk2(add2(lg_eval2<D>(c.ec[j2], y, dd), nm), x0, x1);
+          const f32x2 t = pk2(ex2(x0), ex2(x1));
+          sp = add2(sp, t);
+          if (j2 == k) G = t;
+        }
+      }
+      GG2[2 * pp] = G;
+      SM4[pp] = make_ulonglong2(sp, nm);
+      float s0, s1, g0, g1;
+      upk2(sp, s0, s1);
+      upk2(G, g0, g1);
+      if (withL) {
+        float a0, a1, n0, n1;
+        upk2(ga.y, a0, a1);
+        upk2(nm, n0, n1);
+        accl = fmaf(a0, (-n0 - c0) + lg2(s0), accl);
+        accl = fmaf(a1, (-n1 - c0) + lg2(s1), accl);
+      }
+      const f32x2 rr = pk2(rcp_approx(max3f(s0, g0, 1e-30f)), rcp_approx(max3f(s1, g1, 1e-30f)));
+      const f32x2 gam = mul2(ga.y, mul2(G, rr));
+      acc[0] = add2(acc[0], gam);
+      int t = 1 + D;
+#pragma unroll
+      for (int x = 0; x < D; ++x) {
+        const f32x2 gd = mul2(gam, d[x]);
+        acc[1 + x] = add2(acc[1 + x], gd);
+#pragma unroll
+        for (int yy = x; yy < D; ++yy, ++t) acc[t] = fma2(gd, d[yy], acc[t]);
+      }
+    }
+    float v[NS + 1];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      float lo, hi;
+      upk2(acc[q], lo, hi);
+      v[q] = lo + hi;
+    }
+    v[NS] = accl;
+    block_partials<NS + 1, NRED, NW>(v, c.redf);
+  };
+
   // ---- sweeps -------------------------------------------------------------
+  // Every kExactEvery-th sweep starts with the exact pass (after the weights
+  // are normalised); the others start with the first component step, which
+  // also yields the log-likelihood of the previous sweep's parameters.
+  constexpr int kExactEvery = 8;
   for (;;) {
-    // exact pass after the previous sweep, fused with the first component
-    // step of the next one (discarded when EM stops here)
-    exact_pass(true, c.sweep == 0);
+    if (c.sweep % kExactEvery == 0) {
+      if (c.sweep > 0) {
+        if (tid < c.K) {
+          const R un = c.u[tid] / c.Z;
+          c.u[tid] = un;
+          c.eb[tid] = lg2((float)un) + c.elc[tid];
+          pack_econst<D>(c.emu[tid], c.eA[tid], c.eb[tid], c.ec[tid]);
+        }
+        __syncthreads();
+        if (tid == 0) c.Z = (R)1;
+        __syncthreads();
+      }
+      exact_pass(true, c.sweep == 0);
+    } else {
+      comp_pass(0, c.pstate, true);
+    }
     if (tid < 32) {
       R sv[NS + 1];
       finish_exact(sv, false);
@@ -739,60 +866,7 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
     if (c.done) break;
     while (c.k < c.K) {
       const int k = c.k;
-      const int ps = c.pstate;
-      const f32x2* ek = c.ec[k];
-      const f32x2* ep = c.ec[kMaxK];
-      f32x2 acc[NS];
-#pragma unroll
-      for (int q = 0; q < NS; ++q) acc[q] = 0ull;
-      for (int pp = tid; pp < P2; pp += NT) {
-        f32x2 y[D], d[D];
-#pragma unroll
-        for (int q = 0; q < D; ++q) y[q] = Y2[q * ys2 + pp];
-        const ulonglong2 sm = SM4[pp];
-        const ulonglong2 ga = GA4[pp];
-        const f32x2 nm = sm.y;  // -m
-        f32x2 sp = sm.x;
-        if (ps == 1) {  // previous component updated: replace its term
-          float x0, x1;
-          upk2(add2(lg_eval2<D>(ep, y, d), nm), x0, x1);
-          const float gn0 = ex2(fminf(x0, 100.0f)), gn1 = ex2(fminf(x1, 100.0f));
-          float sn0, sn1;
-          upk2(add2(fma2(ga.x, bc2(-1.0f), sp), pk2(gn0, gn1)), sn0, sn1);
-          sp = pk2(fmaxf(sn0, gn0), fmaxf(sn1, gn1));
-        } else if (ps == 2) {  // previous component removed
-          sp = fma2(ga.x, bc2(-1.0f), sp);
-        }
-        // component k is unchanged since the exact pass, which kept its
-        // term below 1e30: no clamp needed
-        float x0, x1;
-        upk2(add2(lg_eval2<D>(ek, y, d), nm), x0, x1);
-        const f32x2 G = pk2(ex2(x0), ex2(x1));
-        GG2[2 * pp] = G;
-        SM4[pp] = make_ulonglong2(sp, nm);
-        float s0, s1, g0, g1;
-        upk2(sp, s0, s1);
-        upk2(G, g0, g1);
-        const f32x2 rr = pk2(rcp_approx(max3f(s0, g0, 1e-30f)), rcp_approx(max3f(s1, g1, 1e-30f)));
-        const f32x2 gam = mul2(ga.y, mul2(G, rr));
-        acc[0] = add2(acc[0], gam);
-        int t = 1 + D;
-#pragma unroll
-        for (int x = 0; x < D; ++x) {
-          const f32x2 gd = mul2(gam, d[x]);
-          acc[1 + x] = add2(acc[1 + x], gd);
-#pragma unroll
-          for (int yy = x; yy < D; ++yy, ++t) acc[t] = fma2(gd, d[yy], acc[t]);
-        }
-      }
-      float v[NS];
-#pragma unroll
-      for (int q = 0; q < NS; ++q) {
-        float lo, hi;
-        upk2(acc[q], lo, hi);
-        v[q] = lo + hi;
-      }
-      block_partials<NS, NRED, NW>(v, c.redf);
+      comp_pass(k, c.pstate, false);
       if (tid < 32) {
         R st[NW];
 #pragma unroll
@@ -809,16 +883,6 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
       }
       __syncthreads();
     }
-    // normalise the weights (step 3 made explicit once per sweep)
-    if (tid < c.K) {
-      const R un = c.u[tid] / c.Z;
-      c.u[tid] = un;
-      c.eb[tid] = lg2((float)un) + c.elc[tid];
-      pack_econst<D>(c.emu[tid], c.eA[tid], c.eb[tid], c.ec[tid]);
-    }
-    __syncthreads();
-    if (tid == 0) c.Z = (R)1;
-    __syncthreads();
   }
   if (tid == 0 && c.done == 2) c.status |= GM_ST_EM_MAXSWEEPS;
   if constexpr (sizeof(R) == 4) {  // FP64 means from the hi + lo pairs
