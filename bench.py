@@ -296,7 +296,16 @@ def run_gmcr(args):
                 alpha=torch.empty(n, dtype=torch.float64, device=device),
                 status=torch.empty(C, dtype=torch.int32, device=device))
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=device)
-    stream = torch.cuda.current_stream()
+    # a side stream: CUDA graphs cannot capture the legacy default stream
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+
+    # ---- launch shape of the EM kernel: the library's autotuner (untimed)
+    tune = None
+    if not args.threads_per_cell and not args.smem_particles:
+        trial_ms = gm.gm_autotune(cfg, cell_off, x, v, alpha, stream=stream)
+        tune = {"threads_per_cell": cfg.threads_per_cell, "smem_particles": cfg.smem_particles,
+                "trial_ms": [round(z, 4) for z in trial_ms]}
 
     # ---- learned initialisation: the network is trained (untimed) on cells
     # of the same generator family fitted by the paper's method
@@ -334,7 +343,9 @@ def run_gmcr(args):
 
     def timed(path: str, steps: int, warmup: int):
         """per-step CUDA events (init, compress, reconstruct), L2 flushed
-        between steps; returns per-phase mean ms and the compress outputs"""
+        between steps; the phases are replayed from CUDA graphs captured
+        after the warm-up (unless --no-graph); returns per-phase mean ms and
+        the compress outputs"""
         cout = comp_out()
 
         def one(ev=None):
@@ -357,6 +368,46 @@ def run_gmcr(args):
         for _ in range(warmup):
             one()
         torch.cuda.synchronize()
+        graphs = None
+        if not args.no_graph:
+            graphs = []
+            if path == "learned":
+                f_, w_ = gm.gm_features(cfg, cell_off, v, alpha, stream=stream)
+                o_ = net.forward(f_, stream=stream)
+                K0, prm = gm.gm_mlp_decode(cfg, o_, w_, cell_off, stream=stream)
+                gi = gm.Graph(stream)
+                with gi:
+                    gm.gm_features(cfg, cell_off, v, alpha, stream=stream, out=(f_, w_))
+                    net.forward(f_, out=o_, stream=stream)
+                    gm.gm_mlp_decode(cfg, o_, w_, cell_off, stream=stream, dest=(K0, prm))
+                gi.keep(f_, w_, o_, K0, prm)
+                graphs.append(gi)
+                kw = dict(init_K=K0, init_params=prm)
+            else:
+                graphs.append(None)
+                kw = {}
+            gc = gm.Graph(stream)
+            with gc:
+                gm.gm_compress(cfg, cell_off, x, v, alpha, stream=stream, out=cout, **kw)
+            graphs.append(gc)
+            gr = gm.Graph(stream)
+            with gr:
+                gm.gm_reconstruct(rcfg, cout["K"], cout["params"], cout["W"], cout["rho_target"],
+                                  out_off, n_out=n, stream=stream, out=rout)
+            graphs.append(gr)
+
+            def one(ev=None):  # noqa: F811  (graph replay of the same step)
+                for a, g_ in enumerate(graphs):
+                    if ev:
+                        ev[a].record(stream)
+                    if g_ is not None:
+                        g_.launch(stream)
+                if ev:
+                    ev[3].record(stream)
+
+            for _ in range(warmup):
+                one()
+            torch.cuda.synchronize()
         evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
         if dist is not None:
             dist.barrier()
@@ -368,6 +419,10 @@ def run_gmcr(args):
         if dist is not None:
             dist.barrier()
         ms = [sum(e[a].elapsed_time(e[a + 1]) for e in evs) / steps for a in range(3)]
+        if graphs:
+            for g_ in graphs:
+                if g_ is not None:
+                    g_.close()
         return {"ms_init": ms[0], "ms_compress": ms[1], "ms_reconstruct": ms[2]}, cout
 
     clocks = ClockSampler(local)
@@ -466,6 +521,10 @@ def run_gmcr(args):
                    "precision": ("fp32 m-step, fp64 means and final step" if args.precision == 0
                                  else "fp64 m-step"),
                    "l2": "inputs > L2 and a 252 MB flush between timed steps",
+                   "launch": ("CUDA-graph replay of init / compress / reconstruct" if not args.no_graph
+                              else "direct calls"),
+                   "em_shape": ({"threads_per_cell": cfg.threads_per_cell,
+                                 "smem_particles": cfg.smem_particles, "autotune": tune}),
                    "parallelism": f"replicas x{world} (independent batches)"},
         "ms_init": hs["ms_init"], "ms_compress": hs["ms_compress"],
         "ms_reconstruct": hs["ms_reconstruct"],
@@ -509,6 +568,7 @@ def main(argv=None):
     ap.add_argument("--train-cells", type=int, default=65536)
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--smem-particles", type=int, default=0)
+    ap.add_argument("--no-graph", action="store_true", help="time direct calls instead of graph replay")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

@@ -66,8 +66,9 @@ typedef struct gm_config {
                                cells with more particles use an L2-resident global tile */
   int32_t precision;        /* penalised sweeps' M-step (covariance, Cholesky factor,
                                inverse, weight): 0 = FP32 (default), 1 = FP64.  Either
-                               way the component means are accumulated in FP64 and the
-                               final unpenalised step is entirely FP64 */
+                               way the component means are accumulated to about 48
+                               bits (FP64, or a pair of FP32 numbers) and the final
+                               unpenalised step is entirely FP64 */
   int32_t reserved;         /* must be 0 */
 } gm_config;
 
@@ -290,6 +291,58 @@ int gm_mlp_train_step(const gm_mlp* net, int32_t M, const void* X, const float* 
 int gm_mlp_decode(const gm_config* cfg, int64_t C, const float* out, int32_t O,
                   const double* wstat, const int64_t* cell_off, int32_t* K0, double* init_params,
                   void* stream);
+
+/*
+ * Pipeline capture into a CUDA graph.  The paper has no counterpart: this
+ * is how a caller replays a fixed compress / reconstruct (and learned
+ * initialisation) pipeline with one launch.
+ *
+ * gm_graph_begin starts capturing `stream` (relaxed capture mode).  Every
+ * library call this host thread issues until gm_graph_end must go to that
+ * stream; each one that needs device workspace gets a buffer of its own,
+ * allocated at capture time and owned by the graph (so graphs and direct
+ * calls never share workspace).  gm_graph_end ends the capture and
+ * instantiates the graph into *out.  gm_graph_launch replays it on any
+ * stream: the captured calls run again with the same pointers, sizes and
+ * configuration, so the caller keeps every captured buffer alive (and its
+ * inputs in place) for the graph's lifetime.  gm_graph_destroy frees the
+ * graph and its workspace; it waits for the device to finish first.
+ * Errors: GM_ERR_ARG (no capture in progress on this thread, a capture
+ * already in progress, NULL arguments), GM_ERR_CUDA (capture, instantiation
+ * or launch failed -- a library call that failed during capture also
+ * invalidates it).  The capture is always ended by gm_graph_end.
+ */
+typedef struct gm_graph gm_graph;
+int gm_graph_begin(void* stream);
+int gm_graph_end(void* stream, gm_graph** out);
+int gm_graph_launch(const gm_graph* g, void* stream);
+int gm_graph_destroy(gm_graph* g);
+
+/*
+ * gm_autotune -- picks the EM launch shape for a batch of cells.  The paper
+ * has no counterpart (it runs one cell per process on CPUs).
+ *
+ * Times gm_compress on a sample of the batch (the first cells, about two
+ * waves of CTAs) for every candidate shape: threads_per_cell in {128, 256}
+ * and shared-tile capacities smem_particles covering the library default
+ * and the 90th, 99th and 100th percentiles of the cell sizes (only those
+ * that fit in shared memory; larger cells use the L2-resident global
+ * tile).  Each trial runs a fixed number of sweeps (tol = 0, max_sweeps =
+ * sweeps_per_trial, 0 = 24) so that every candidate does the same work,
+ * and the fastest of two repetitions counts; the library default (256
+ * threads, default tile) is kept unless another candidate is more than 3 %
+ * faster.  Writes the winner into
+ * cfg->threads_per_cell and cfg->smem_particles and, if timings_ms is not
+ * NULL, the trial times (host array of at least 8 floats, -1 for skipped
+ * candidates, candidate i = (threads 128 : 256 for i even : odd, tile i/2)).
+ * Arguments as gm_compress (device arrays); cell_off is copied to the host,
+ * so the call synchronises `stream`.  Results of later gm_compress calls do
+ * not depend on the tile; the CTA size changes the order of FP32 partial
+ * sums only.  Returns GM_OK or an error code; cfg is unchanged on error.
+ */
+int gm_autotune(gm_config* cfg, int64_t C, int64_t n_particles, const int64_t* cell_off,
+                const double* x, const void* v, int32_t v_is_f64, const double* alpha,
+                int32_t sweeps_per_trial, float* timings_ms, void* stream);
 
 /* Description of the last error on this host thread ("" if none). */
 const char* gm_last_error(void);

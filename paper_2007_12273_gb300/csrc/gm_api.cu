@@ -5,6 +5,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "gm_kernels.cuh"
 
@@ -16,6 +17,16 @@ int em_blocks_per_sm_d3(int nt, int fp64_mstep, int v_f64, size_t smem);
 namespace {
 
 thread_local std::string g_err;
+
+// a capture in progress on this host thread (gm_graph_begin .. gm_graph_end):
+// workspace requests get buffers of their own, handed to the graph
+struct Capture {
+  bool active = false;
+  cudaStream_t stream = nullptr;
+  std::vector<void*> bufs;
+};
+thread_local Capture g_cap;
+
 std::mutex g_ws_mu;
 void* g_ws = nullptr;
 size_t g_ws_bytes = 0;
@@ -54,6 +65,15 @@ int check_device(int* sm_count) {
 // grows the single workspace; the old buffer is released with cudaFree,
 // which waits for work that may still use it
 int ws_get(size_t bytes, void** out) {
+  if (g_cap.active) {  // owned by the graph being captured
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes > 0 ? bytes : 256);
+    if (e != cudaSuccess) return fail(GM_ERR_NOMEM, "graph workspace of %zu bytes: %s", bytes,
+                                      cudaGetErrorString(e));
+    g_cap.bufs.push_back(p);
+    *out = p;
+    return GM_OK;
+  }
   std::lock_guard<std::mutex> lk(g_ws_mu);
   int dev = 0;
   cudaGetDevice(&dev);
@@ -99,9 +119,84 @@ int gmcr::record_error(int code, const char* msg) {
   return code;
 }
 
+struct gm_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<void*> bufs;
+};
+
 extern "C" {
 
 const char* gm_last_error(void) { return g_err.c_str(); }
+
+int gm_graph_begin(void* stream) {
+  g_err.clear();
+  if (g_cap.active) return fail(GM_ERR_ARG, "a capture is already in progress on this thread");
+  int rc = check_device(nullptr);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+  g_cap.active = true;
+  g_cap.stream = s;
+  g_cap.bufs.clear();
+  return GM_OK;
+}
+
+int gm_graph_end(void* stream, gm_graph** out) {
+  g_err.clear();
+  if (!g_cap.active) return fail(GM_ERR_ARG, "no capture in progress on this thread");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (s != g_cap.stream) return fail(GM_ERR_ARG, "gm_graph_end on another stream than gm_graph_begin");
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &graph);
+  g_cap.active = false;
+  std::vector<void*> bufs;
+  bufs.swap(g_cap.bufs);
+  auto release = [&]() {
+    if (graph) cudaGraphDestroy(graph);
+    for (void* p : bufs) cudaFree(p);
+  };
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(e, "cudaStreamEndCapture");
+  }
+  if (!out) {
+    release();
+    return fail(GM_ERR_ARG, "out is NULL");
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  gm_graph* g = new gm_graph;
+  g->graph = graph;
+  g->exec = exec;
+  g->bufs.swap(bufs);
+  *out = g;
+  return GM_OK;
+}
+
+int gm_graph_launch(const gm_graph* g, void* stream) {
+  g_err.clear();
+  if (!g) return fail(GM_ERR_ARG, "graph is NULL");
+  cudaError_t e = cudaGraphLaunch(g->exec, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+  return GM_OK;
+}
+
+int gm_graph_destroy(gm_graph* g) {
+  g_err.clear();
+  if (!g) return GM_OK;
+  cudaDeviceSynchronize();
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  for (void* p : g->bufs) cudaFree(p);
+  delete g;
+  return GM_OK;
+}
 
 int gm_shutdown(void) {
   std::lock_guard<std::mutex> lk(g_ws_mu);

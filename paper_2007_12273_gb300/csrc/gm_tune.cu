@@ -1,0 +1,152 @@
+// gm_tune.cu -- launch-shape autotuner of the EM kernel (gm_autotune, C ABI
+// in include/gm.h).  Trials run gm_compress itself on a sample of the
+// batch, with a fixed number of sweeps so that every candidate does the
+// same work.
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
+#include "gm_kernels.cuh"
+
+namespace {
+
+int tune_fail(int code, const char* what, cudaError_t e = cudaSuccess) {
+  char buf[256];
+  if (e != cudaSuccess)
+    snprintf(buf, sizeof buf, "gm_autotune: %s: %s", what, cudaGetErrorString(e));
+  else
+    snprintf(buf, sizeof buf, "gm_autotune: %s", what);
+  return gmcr::record_error(code, buf);
+}
+
+// device buffers of one trial's outputs
+struct TrialOut {
+  void* base = nullptr;
+  int32_t *K = nullptr, *sweeps = nullptr, *kwork = nullptr;
+  double *params = nullptr, *W = nullptr, *rho = nullptr, *lnL = nullptr;
+  uint32_t* status = nullptr;
+};
+
+size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" int gm_autotune(gm_config* cfg, int64_t C, int64_t n_particles, const int64_t* cell_off,
+                           const double* x, const void* v, int32_t v_is_f64, const double* alpha,
+                           int32_t sweeps_per_trial, float* timings_ms, void* stream) {
+  if (!cfg || !cell_off || !x || !v || !alpha) return tune_fail(GM_ERR_ARG, "a required pointer is NULL");
+  if (C < 1) return tune_fail(GM_ERR_ARG, "C must be >= 1");
+  if (cfg->D != 1 && cfg->D != 3) return tune_fail(GM_ERR_ARG, "D must be 1 or 3");
+  if (cfg->Kmax < 1 || cfg->Kmax > gmcr::kMaxK) return tune_fail(GM_ERR_ARG, "Kmax out of range");
+  if (sweeps_per_trial < 0) return tune_fail(GM_ERR_ARG, "sweeps_per_trial < 0");
+  const int spt = sweeps_per_trial > 0 ? sweeps_per_trial : 24;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int D = cfg->D;
+  const int P = 1 + D + D * (D + 1) / 2;
+
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return tune_fail(GM_ERR_CUDA, "cudaGetDevice", e);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms < 1) sms = 1;
+
+  // cell sizes of the sample: the first cells, about two waves of CTAs
+  const int64_t S = std::min<int64_t>(C, (int64_t)8 * sms);
+  std::vector<int64_t> off((size_t)S + 1);
+  e = cudaMemcpyAsync(off.data(), cell_off, sizeof(int64_t) * (size_t)(S + 1), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return tune_fail(GM_ERR_CUDA, "reading cell_off", e);
+  std::vector<int64_t> sizes((size_t)S);
+  for (int64_t j = 0; j < S; ++j) sizes[(size_t)j] = off[(size_t)j + 1] - off[(size_t)j];
+  std::sort(sizes.begin(), sizes.end());
+  auto quant = [&](double q) {
+    const size_t i = std::min(sizes.size() - 1, (size_t)(q * (double)(sizes.size() - 1) + 0.5));
+    return sizes[i];
+  };
+
+  // candidate shared tiles (particles, multiple of 4, within 200 KB)
+  const int64_t max_cap = (int64_t)(200 * 1024) / ((int64_t)(D + 4) * 4) & ~(int64_t)3;
+  std::vector<int> caps;
+  auto add_cap = [&](int64_t c) {
+    c = (c + 1 + 3) & ~(int64_t)3;  // pad particle, multiple of 4
+    if (c < 4) c = 4;
+    if (c > max_cap) return;
+    if (std::find(caps.begin(), caps.end(), (int)c) == caps.end()) caps.push_back((int)c);
+  };
+  add_cap(D == 1 ? 2559 : 3071);  // the library default
+  add_cap(quant(0.90));
+  add_cap(quant(0.99));
+  add_cap(sizes.back());
+  if (caps.size() > 4) caps.resize(4);
+
+  // trial outputs
+  TrialOut o;
+  const size_t bK = up256(sizeof(int32_t) * (size_t)S), bP = up256(sizeof(double) * (size_t)S * cfg->Kmax * P),
+               bD = up256(sizeof(double) * (size_t)S);
+  e = cudaMalloc(&o.base, 4 * bK + bP + 3 * bD);
+  if (e != cudaSuccess) return tune_fail(GM_ERR_NOMEM, "trial outputs", e);
+  char* b = (char*)o.base;
+  o.K = (int32_t*)b;
+  o.sweeps = (int32_t*)(b + bK);
+  o.kwork = (int32_t*)(b + 2 * bK);
+  o.status = (uint32_t*)(b + 3 * bK);
+  o.params = (double*)(b + 4 * bK);
+  o.W = (double*)(b + 4 * bK + bP);
+  o.rho = (double*)(b + 4 * bK + bP + bD);
+  o.lnL = (double*)(b + 4 * bK + bP + 2 * bD);
+
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  float times[8];
+  for (int i = 0; i < 8; ++i) times[i] = -1.0f;
+  int best = -1;
+  int rc = GM_OK;
+  for (size_t ci = 0; ci < caps.size() && rc == GM_OK; ++ci) {
+    for (int ti = 0; ti < 2; ++ti) {
+      gm_config tr = *cfg;
+      tr.tol = 0.0;
+      tr.max_sweeps = spt;
+      tr.threads_per_cell = ti == 0 ? 128 : 256;
+      tr.smem_particles = caps[ci];
+      tr.L = cfg->L * (double)S / (double)C;  // the sample keeps the cell width
+      float tmin = -1.0f;
+      for (int rep = 0; rep < 3; ++rep) {  // one warm-up, two timed
+        cudaEventRecord(t0, s);
+        const int r = gm_compress(&tr, S, n_particles, cell_off, x, v, v_is_f64, alpha, o.K, o.params,
+                                  o.W, o.rho, o.lnL, o.sweeps, o.kwork, o.status, stream);
+        if (r != GM_OK) {
+          tmin = -1.0f;
+          break;
+        }
+        cudaEventRecord(t1, s);
+        e = cudaEventSynchronize(t1);
+        if (e != cudaSuccess) {
+          rc = tune_fail(GM_ERR_CUDA, "trial", e);
+          break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, t0, t1);
+        if (rep > 0 && (tmin < 0.0f || ms < tmin)) tmin = ms;
+      }
+      times[(int)ci * 2 + ti] = tmin;
+    }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  cudaFree(o.base);
+  if (rc != GM_OK) return rc;
+  // the library default (256 threads, default tile: candidate 1) stays
+  // unless another shape is faster by more than 3 %: trials closer than
+  // that are within the run-to-run spread
+  for (int i = 0; i < 8; ++i)
+    if (times[i] >= 0.0f && (best < 0 || times[i] < times[best])) best = i;
+  if (best >= 0 && times[1] >= 0.0f && times[best] > 0.97f * times[1]) best = 1;
+  if (best < 0) return tune_fail(GM_ERR_CUDA, "no candidate ran");
+  if (timings_ms)
+    for (int i = 0; i < 8; ++i) timings_ms[i] = times[i];
+  cfg->threads_per_cell = (best % 2 == 0) ? 128 : 256;
+  cfg->smem_particles = caps[(size_t)(best / 2)];
+  gmcr::record_error(GM_OK, "");
+  return GM_OK;
+}

@@ -16,6 +16,10 @@ import torch
 from . import build as _build
 
 GM_OK = 0
+GM_ERR_ARG = -1
+GM_ERR_CUDA = -2
+GM_ERR_NOMEM = -3
+GM_ERR_UNSUPPORTED = -4
 ST_EM_MAXSWEEPS = 0x01
 ST_COV_NOT_PD = 0x02
 ST_TOO_FEW = 0x04
@@ -85,10 +89,16 @@ def load(build_if_missing: bool = False):
         lib.gm_mlp_forward.argtypes = [P, I32, P, P, ct.c_size_t, P, P, P]
         lib.gm_mlp_train_step.argtypes = [P, I32, P, P, P, ct.c_float, I32, P, ct.c_size_t, P, P, P, P]
         lib.gm_mlp_decode.argtypes = [P, I64, P, I32, P, P, P, P, P]
+        lib.gm_graph_begin.argtypes = [P]
+        lib.gm_graph_end.argtypes = [P, ct.POINTER(ct.c_void_p)]
+        lib.gm_graph_launch.argtypes = [P, P]
+        lib.gm_graph_destroy.argtypes = [P]
+        lib.gm_autotune.argtypes = [P, I64, I64, P, P, P, I32, P, I32, ct.POINTER(ct.c_float), P]
         for f in ("gm_compress", "gm_reconstruct", "gm_moments", "gm_mixture_moments", "gm_shutdown",
                   "gm_reconstruct_noalloc", "gm_gemm_bf16", "gm_compress_from", "gm_features",
                   "gm_mlp_targets", "gm_mlp_sync", "gm_mlp_forward", "gm_mlp_train_step",
-                  "gm_mlp_decode"):
+                  "gm_mlp_decode", "gm_graph_begin", "gm_graph_end", "gm_graph_launch",
+                  "gm_graph_destroy", "gm_autotune"):
             getattr(lib, f).restype = ct.c_int
         lib.gm_last_error.restype = ct.c_char_p
         _lib = lib
@@ -308,15 +318,18 @@ def out_width(D: int, Kmax: int) -> int:
     return (Kmax * slot_size(D) + 15) // 16 * 16
 
 
-def gm_features(cfg: GMConfig, cell_off, v, alpha, stream=None):
+def gm_features(cfg: GMConfig, cell_off, v, alpha, stream=None, out=None):
     """Per-cell features (BF16 [C][F]) and whitening statistics
-    (FP64 [C][2D]: mean, sd)."""
+    (FP64 [C][2D]: mean, sd); ``out`` = (feat, wstat) may supply them."""
     lib = load()
     C = cell_off.shape[0] - 1
     n = alpha.shape[0]
     D = cfg.D
-    feat = torch.empty((C, feat_width(D)), dtype=torch.bfloat16, device=alpha.device)
-    wstat = torch.empty((C, 2 * D), dtype=torch.float64, device=alpha.device)
+    if out is None:
+        feat = torch.empty((C, feat_width(D)), dtype=torch.bfloat16, device=alpha.device)
+        wstat = torch.empty((C, 2 * D), dtype=torch.float64, device=alpha.device)
+    else:
+        feat, wstat = out
     rc = lib.gm_features(ct.byref(cfg), C, n, _ptr(cell_off), _ptr(v),
                          1 if v.dtype == torch.float64 else 0, _ptr(alpha), _ptr(feat),
                          _ptr(wstat), _stream_ptr(stream))
@@ -336,11 +349,16 @@ def gm_mlp_targets(cfg: GMConfig, K, params, wstat, stream=None):
     return T, Mk
 
 
-def gm_mlp_decode(cfg: GMConfig, out, wstat, cell_off, stream=None):
+def gm_mlp_decode(cfg: GMConfig, out, wstat, cell_off, stream=None, dest=None):
+    """Initial mixtures (K0 [C] int32, params [C][Kmax][P] f64) from the
+    network output; ``dest`` = (K0, params) may supply them."""
     lib = load()
     C = cell_off.shape[0] - 1
-    K0 = torch.empty(C, dtype=torch.int32, device=out.device)
-    prm = torch.empty((C, cfg.Kmax, P_of(cfg.D)), dtype=torch.float64, device=out.device)
+    if dest is None:
+        K0 = torch.empty(C, dtype=torch.int32, device=out.device)
+        prm = torch.empty((C, cfg.Kmax, P_of(cfg.D)), dtype=torch.float64, device=out.device)
+    else:
+        K0, prm = dest
     rc = lib.gm_mlp_decode(ct.byref(cfg), C, _ptr(out), out.shape[1], _ptr(wstat), _ptr(cell_off),
                            _ptr(K0), _ptr(prm), _stream_ptr(stream))
     _rc(lib, rc, "gm_mlp_decode")
@@ -434,3 +452,70 @@ class Net:
                                    _ptr(self.err), _stream_ptr(stream))
         _rc(lib, rc, "gm_mlp_train_step")
         return loss
+
+
+def gm_autotune(cfg: GMConfig, cell_off, x, v, alpha, sweeps_per_trial: int = 0, stream=None):
+    """Times the EM launch shapes on a sample of the batch and writes the
+    fastest into ``cfg`` (threads_per_cell, smem_particles).  Returns the
+    trial times in ms (8 entries, -1 = not run)."""
+    lib = load()
+    C = cell_off.shape[0] - 1
+    n = x.shape[0]
+    t = (ct.c_float * 8)()
+    rc = lib.gm_autotune(ct.byref(cfg), C, n, _ptr(cell_off), _ptr(x), _ptr(v),
+                         1 if v.dtype == torch.float64 else 0, _ptr(alpha), int(sweeps_per_trial), t,
+                         _stream_ptr(stream))
+    _rc(lib, rc, "gm_autotune")
+    return list(t)
+
+
+class Graph:
+    """A CUDA graph of library calls, captured natively (gm_graph_begin /
+    gm_graph_end).  Use as a context manager on a non-default stream; every
+    library call inside must target that stream and write into buffers that
+    exist before the capture (``keep`` holds references to them for the
+    graph's lifetime).  ``launch`` replays the calls."""
+
+    def __init__(self, stream=None):
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = None
+        self._keep = []
+
+    def keep(self, *objs):
+        self._keep.extend(objs)
+        return objs[0] if len(objs) == 1 else objs
+
+    def __enter__(self):
+        lib = load()
+        _rc(lib, lib.gm_graph_begin(_stream_ptr(self.stream)), "gm_graph_begin")
+        return self
+
+    def __exit__(self, exc_type, exc, tb):
+        lib = load()
+        h = ct.c_void_p()
+        rc = lib.gm_graph_end(_stream_ptr(self.stream), ct.byref(h))
+        if exc_type is not None:
+            if rc == GM_OK:
+                lib.gm_graph_destroy(h)
+            return False
+        _rc(lib, rc, "gm_graph_end")
+        self.handle = h
+        return False
+
+    def launch(self, stream=None):
+        lib = load()
+        _rc(lib, lib.gm_graph_launch(self.handle, _stream_ptr(stream if stream is not None else self.stream)),
+            "gm_graph_launch")
+
+    def close(self):
+        if self.handle is not None:
+            lib = load()
+            lib.gm_graph_destroy(self.handle)
+            self.handle = None
+        self._keep = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
