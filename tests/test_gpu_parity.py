@@ -2,8 +2,11 @@
 C ABI, on seeded inputs.
 
 Tolerances:
-  * selected component count K: equal in at least 99% of cells;
-  * per-cell penalised log-likelihood: 1e-5 relative where K agrees;
+  * selected component count K and per-cell penalised log-likelihood
+    (1e-5 relative): naturally equal in most cells; the rest must agree
+    under the equal-sweep rule of parity_helpers (the FP32 E-step moves the
+    knife-edge stopping sweep; unconverged cells drift along flat
+    directions); each test states both rates it requires;
   * moments of the fit vs the particles': 1e-12 relative (exact, Sec. 2.3.1);
   * reconstruction: positions bit-identical; corrected weights and dA
     1e-12 relative; velocities 2e-6 relative to the cell's spread (FP32
@@ -18,6 +21,7 @@ import pytest
 
 import oracle
 import workloads
+from parity_helpers import agreement
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -51,30 +55,18 @@ def run_gpu_compress(gm, wl, **over):
 
 
 def check_compress_parity(g, ref, min_agree=0.99, wl=None, cells=None, min_equal_sweeps=0.99):
-    """A cell agrees when it selects the same K and its penalised
-    log-likelihood is within 1e-5 (relative) of the oracle's.
-
-    The stopping rule (relative change of L at most tol over a sweep) is
-    knife-edge for cells whose EM creeps at a rate close to tol: rounding
-    differences of order 1e-8 in L then decide whether a sweep stops, and
-    the two sides can end many sweeps apart in different states.  For every
-    cell that disagrees, the oracle is rerun for exactly the GPU's number of
-    sweeps (tol = 0); the states must then agree (same K, lnL within 1e-5):
-    this checks the kernel's arithmetic along the same trajectory.
-    Returns (natural agreement, agreement at equal sweeps)."""
-    rel = np.abs(g["lnL"] - ref["lnL"]) / np.maximum(np.abs(ref["lnL"]), 1e-300)
-    agree = (g["K"] == ref["K"]) & (rel <= 1e-5)
-    bad = np.flatnonzero(~agree)
-    eq = agree.copy()
+    """Natural agreement (same K, lnL within 1e-5) and agreement after the
+    equal-sweep rule of parity_helpers (knife-edge stopping, unconverged
+    cells); both rates are asserted.  Returns (natural, equal-sweep)."""
     if wl is not None:
-        for i in bad:
-            j = int(cells[i]) if cells is not None else int(i)
-            sl = slice(wl.cell_off[j], wl.cell_off[j + 1])
-            p = dict(wl.params, tol=0.0, max_sweeps=max(int(g["sweeps"][i]), 1))
-            r = oracle.em_cell(p, wl.v[:, sl].T, wl.alpha[sl], cell=j)
-            eq[i] = (r["K"] == g["K"][i]) and abs(g["lnL"][i] - r["lnL"]) <= 1e-5 * abs(r["lnL"])
-    assert eq.mean() >= min_equal_sweeps, (np.flatnonzero(~eq), g["K"][~eq], ref["K"][~eq], rel[~eq])
-    assert agree.mean() >= min_agree, (bad, g["K"][bad], ref["K"][bad], rel[bad])
+        agree, eq = agreement(g, ref, wl, cells)
+    else:
+        rel = np.abs(g["lnL"] - ref["lnL"]) / np.maximum(np.abs(ref["lnL"]), 1e-300)
+        agree = (g["K"] == ref["K"]) & (rel <= 1e-5)
+        eq = agree.copy()
+    bad = np.flatnonzero(~agree)
+    assert eq.mean() >= min_equal_sweeps, (np.flatnonzero(~eq), g["K"][~eq], ref["K"][~eq])
+    assert agree.mean() >= min_agree, (bad, g["K"][bad], ref["K"][bad])
     np.testing.assert_allclose(g["W"], ref["W"], rtol=1e-13)
     if cells is None:
         np.testing.assert_allclose(g["rho_target"], ref["rho_target"], rtol=1e-12,
