@@ -283,14 +283,16 @@ int gm_mlp_train_step(const gm_mlp* net, int32_t M, const void* X, const float* 
                       size_t scratch_bytes, float* out, double* loss, uint32_t* err,
                       void* stream);
 
-/* Initial mixtures from the network's output: slots with a positive
- * presence logit (at least the most likely one), capped so that
- * N - T K0 / 2 > 0 by dropping the smallest log weights; weights by softmax
- * of the log weights; mu = mean + sd * mu_w, Sigma = diag(sd) L L^T diag(sd)
- * with ln diag L clamped to [-10, 5].  K0 [C], init_params [C][Kmax][P]. */
+/* Initial mixtures from the network's output: slots whose presence logit
+ * exceeds presence_logit (at least the most likely one; 0 = presence
+ * probability above 1/2, negative values start EM with more components,
+ * which the annihilation may remove again), capped so that N - T K0 / 2 > 0
+ * by dropping the smallest log weights; weights by softmax of the log
+ * weights; mu = mean + sd * mu_w, Sigma = diag(sd) L L^T diag(sd) with
+ * ln diag L clamped to [-10, 5].  K0 [C], init_params [C][Kmax][P]. */
 int gm_mlp_decode(const gm_config* cfg, int64_t C, const float* out, int32_t O,
-                  const double* wstat, const int64_t* cell_off, int32_t* K0, double* init_params,
-                  void* stream);
+                  const double* wstat, const int64_t* cell_off, float presence_logit, int32_t* K0,
+                  double* init_params, void* stream);
 
 /*
  * Pipeline capture into a CUDA graph.  The paper has no counterpart: this

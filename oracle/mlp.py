@@ -215,14 +215,16 @@ def adam_step(p: dict, g: dict, state: dict, lr: float, t: int, b1=0.9, b2=0.999
         p[k] = p[k] - lr * mh / (np.sqrt(vh) + eps)
 
 
-def decode(out: np.ndarray, mean: np.ndarray, sd: np.ndarray, N: int, D: int, Kmax: int):
+def decode(out: np.ndarray, mean: np.ndarray, sd: np.ndarray, N: int, D: int, Kmax: int,
+           presence_logit: float = 0.0):
     """Initial mixture (original coordinates) from one cell's network output:
-    slots with a positive presence logit (at least the most likely one),
-    capped so that N - T K0 / 2 > 0; weights by softmax of the log weights."""
+    slots whose presence logit exceeds ``presence_logit`` (at least the most
+    likely one), capped so that N - T K0 / 2 > 0; weights by softmax of the
+    log weights."""
     SP = slot_size(D)
     T_ = D * (D + 3) / 2
     pres = out[0:Kmax * SP:SP]
-    order = [s for s in range(Kmax) if pres[s] > 0]
+    order = [s for s in range(Kmax) if pres[s] > presence_logit]
     if not order:
         order = [int(np.argmax(pres))]
     lw = np.array([out[s * SP + 1] for s in order])

@@ -52,7 +52,8 @@ cudaError_t launch_features(int D, int64_t C, int64_t n, const int64_t* cell_off
 cudaError_t launch_targets(int D, int64_t C, int Kmax, int O, const int32_t* K, const double* prm,
                            const double* wstat, float* T, float* Mk, cudaStream_t s);
 cudaError_t launch_decode(int D, int64_t C, int Kmax, int O, const float* out, const double* wstat,
-                          const int64_t* cell_off, int32_t* K0, double* prm, cudaStream_t s);
+                          const int64_t* cell_off, float presence_logit, int32_t* K0, double* prm,
+                          cudaStream_t s);
 cudaError_t launch_loss_grad(int B, int O, int D, int Kmax, const float* out, const float* T,
                              const float* Mk, float* G32, void* G16, double* loss, cudaStream_t s);
 cudaError_t launch_transpose_bf16(int R, int Cc, const void* in, int ldi, void* out, int ldo,

@@ -267,8 +267,8 @@ int gm_mlp_train_step(const gm_mlp* net, int32_t M, const void* X, const float* 
 }
 
 int gm_mlp_decode(const gm_config* cfg, int64_t C, const float* out, int32_t O,
-                  const double* wstat, const int64_t* cell_off, int32_t* K0, double* init_params,
-                  void* stream) {
+                  const double* wstat, const int64_t* cell_off, float presence_logit, int32_t* K0,
+                  double* init_params, void* stream) {
   gmcr::record_error(GM_OK, "");
   if (!cfg || (cfg->D != 1 && cfg->D != 3) || cfg->Kmax < 1 || cfg->Kmax > gmcr::kMaxK)
     return gmcr::record_error(GM_ERR_ARG, "bad cfg");
@@ -279,8 +279,9 @@ int gm_mlp_decode(const gm_config* cfg, int64_t C, const float* out, int32_t O,
     return gmcr::record_error(GM_ERR_ARG, "a required pointer is NULL");
   int rc = check_sm103();
   if (rc) return rc;
-  cudaError_t e = gmcr::launch_decode(cfg->D, C, cfg->Kmax, O, out, wstat, cell_off, K0,
-                                      init_params, (cudaStream_t)stream);
+  if (!(presence_logit == presence_logit)) return gmcr::record_error(GM_ERR_ARG, "presence_logit is NaN");
+  cudaError_t e = gmcr::launch_decode(cfg->D, C, cfg->Kmax, O, out, wstat, cell_off, presence_logit,
+                                      K0, init_params, (cudaStream_t)stream);
   return e == cudaSuccess ? GM_OK : cuda_err(e, "decode launch");
 }
 

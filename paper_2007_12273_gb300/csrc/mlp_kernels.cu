@@ -337,7 +337,8 @@ __global__ void cast_weights_kernel(int n_out, int n_in, const float* w, __nv_bf
 // ---------------------------------------------------------------------------
 template <int D>
 __global__ void decode_kernel(int64_t C, int Kmax, int O, const float* out, const double* wstat,
-                              const int64_t* cell_off, int32_t* K0, double* prm) {
+                              const int64_t* cell_off, float presence_logit, int32_t* K0,
+                              double* prm) {
   constexpr int NM = D * (D + 1) / 2;
   constexpr int P = 1 + D + NM;
   constexpr int SP = mlp_SP(D);
@@ -353,7 +354,7 @@ __global__ void decode_kernel(int64_t C, int Kmax, int O, const float* out, cons
     int sel[kMaxK], ns = 0, best = 0;
     for (int s = 0; s < Kmax; ++s) {
       if (o[s * SP] > o[best * SP]) best = s;
-      if (o[s * SP] > 0.0f) sel[ns++] = s;
+      if (o[s * SP] > presence_logit) sel[ns++] = s;
     }
     if (ns == 0) sel[ns++] = best;
     while (ns > 1 && (double)N - halfT * ns <= 0.0) {
@@ -431,11 +432,12 @@ cudaError_t launch_targets(int D, int64_t C, int Kmax, int O, const int32_t* K, 
 }
 
 cudaError_t launch_decode(int D, int64_t C, int Kmax, int O, const float* out, const double* wstat,
-                          const int64_t* cell_off, int32_t* K0, double* prm, cudaStream_t s) {
+                          const int64_t* cell_off, float presence_logit, int32_t* K0, double* prm,
+                          cudaStream_t s) {
   if (C == 0) return cudaSuccess;
   const int g = (int)((C + 127) / 128 < 4096 ? (C + 127) / 128 : 4096);
-  if (D == 1) decode_kernel<1><<<g, 128, 0, s>>>(C, Kmax, O, out, wstat, cell_off, K0, prm);
-  else decode_kernel<3><<<g, 128, 0, s>>>(C, Kmax, O, out, wstat, cell_off, K0, prm);
+  if (D == 1) decode_kernel<1><<<g, 128, 0, s>>>(C, Kmax, O, out, wstat, cell_off, presence_logit, K0, prm);
+  else decode_kernel<3><<<g, 128, 0, s>>>(C, Kmax, O, out, wstat, cell_off, presence_logit, K0, prm);
   return cudaGetLastError();
 }
 

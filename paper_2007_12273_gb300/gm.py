@@ -88,7 +88,7 @@ def load(build_if_missing: bool = False):
         lib.gm_mlp_scratch_bytes.restype = ct.c_size_t
         lib.gm_mlp_forward.argtypes = [P, I32, P, P, ct.c_size_t, P, P, P]
         lib.gm_mlp_train_step.argtypes = [P, I32, P, P, P, ct.c_float, I32, P, ct.c_size_t, P, P, P, P]
-        lib.gm_mlp_decode.argtypes = [P, I64, P, I32, P, P, P, P, P]
+        lib.gm_mlp_decode.argtypes = [P, I64, P, I32, P, P, ct.c_float, P, P, P]
         lib.gm_graph_begin.argtypes = [P]
         lib.gm_graph_end.argtypes = [P, ct.POINTER(ct.c_void_p)]
         lib.gm_graph_launch.argtypes = [P, P]
@@ -349,9 +349,11 @@ def gm_mlp_targets(cfg: GMConfig, K, params, wstat, stream=None):
     return T, Mk
 
 
-def gm_mlp_decode(cfg: GMConfig, out, wstat, cell_off, stream=None, dest=None):
+def gm_mlp_decode(cfg: GMConfig, out, wstat, cell_off, stream=None, dest=None,
+                  presence_logit: float = 0.0):
     """Initial mixtures (K0 [C] int32, params [C][Kmax][P] f64) from the
-    network output; ``dest`` = (K0, params) may supply them."""
+    network output (slots with presence logit above ``presence_logit``);
+    ``dest`` = (K0, params) may supply them."""
     lib = load()
     C = cell_off.shape[0] - 1
     if dest is None:
@@ -360,7 +362,7 @@ def gm_mlp_decode(cfg: GMConfig, out, wstat, cell_off, stream=None, dest=None):
     else:
         K0, prm = dest
     rc = lib.gm_mlp_decode(ct.byref(cfg), C, _ptr(out), out.shape[1], _ptr(wstat), _ptr(cell_off),
-                           _ptr(K0), _ptr(prm), _stream_ptr(stream))
+                           float(presence_logit), _ptr(K0), _ptr(prm), _stream_ptr(stream))
     _rc(lib, rc, "gm_mlp_decode")
     return K0, prm
 

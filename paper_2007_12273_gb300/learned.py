@@ -43,14 +43,14 @@ def train(net: gm.Net, feat, T, Mk, epochs: int = 10, batch: int = 1024, lr: flo
     return {"loss": losses, "seconds": time.perf_counter() - t0, "steps": nb * epochs}
 
 
-def init_from_net(net: gm.Net, cfg, cell_off, v, alpha):
+def init_from_net(net: gm.Net, cfg, cell_off, v, alpha, presence_logit: float = 0.0):
     """Features -> network -> initial mixtures (K0, params)."""
     feat, wstat = gm.gm_features(cfg, cell_off, v, alpha)
     out = net.forward(feat)
-    return gm.gm_mlp_decode(cfg, out, wstat, cell_off)
+    return gm.gm_mlp_decode(cfg, out, wstat, cell_off, presence_logit=presence_logit)
 
 
-def compress_learned(net: gm.Net, cfg, cell_off, x, v, alpha, out=None):
+def compress_learned(net: gm.Net, cfg, cell_off, x, v, alpha, out=None, presence_logit: float = 0.0):
     """gm_compress started from the network's mixtures."""
-    K0, prm = init_from_net(net, cfg, cell_off, v, alpha)
+    K0, prm = init_from_net(net, cfg, cell_off, v, alpha, presence_logit)
     return gm.gm_compress(cfg, cell_off, x, v, alpha, out=out, init_K=K0, init_params=prm)

@@ -72,14 +72,16 @@ def test_targets_and_decode_match_oracle(gm, which):
         np.testing.assert_array_equal(Mk[j], m)
         np.testing.assert_allclose(T[j], t, rtol=1e-5, atol=1e-6)
         outs[j] = (t + 0.3 * rng.standard_normal(t.shape)).astype(np.float32)
-    K0, prm = gm.gm_mlp_decode(cfg, dev(outs), wstat, dev(wl.cell_off))
-    K0, prm = K0.cpu().numpy(), prm.cpu().numpy()
-    for j in range(wl.C):
-        sl = slice(wl.cell_off[j], wl.cell_off[j + 1])
-        _, mean, sd = mlp.cell_features(wl.v[:, sl].T, wl.alpha[sl])
-        k0, dec = mlp.decode(outs[j].astype(np.float64), mean, sd, sl.stop - sl.start, D, Kmax)
-        assert K0[j] == k0
-        np.testing.assert_allclose(prm[j, :k0], dec, rtol=1e-6, atol=1e-9)
+    for thr in (0.0, -0.75, -2.5):  # presence-logit thresholds (exact in FP32)
+        K0, prm = gm.gm_mlp_decode(cfg, dev(outs), wstat, dev(wl.cell_off), presence_logit=thr)
+        K0, prm = K0.cpu().numpy(), prm.cpu().numpy()
+        for j in range(wl.C):
+            sl = slice(wl.cell_off[j], wl.cell_off[j + 1])
+            _, mean, sd = mlp.cell_features(wl.v[:, sl].T, wl.alpha[sl])
+            k0, dec = mlp.decode(outs[j].astype(np.float64), mean, sd, sl.stop - sl.start, D, Kmax,
+                                 presence_logit=thr)
+            assert K0[j] == k0
+            np.testing.assert_allclose(prm[j, :k0], dec, rtol=1e-6, atol=1e-9)
 
 
 def _net_and_batch(gm, D, Kmax, B, seed):
