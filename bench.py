@@ -145,6 +145,13 @@ class ClockSampler:
 FLOPS_PER_PK = {1: 30, 3: 90}  # FP32 flops per particle per component step
 
 
+# DRAM bytes (read + write) of one em_kernel launch per particle, from an
+# ncu capture of 1216 cells of the 1D-1V batch (FP32 v): 30.29 MB for
+# 2434617 particles, i.e. the inputs read once (4 B v + 8 B alpha).  The
+# traffic grows with the particles, so a full launch is this times n.
+EM_DRAM_BYTES_PER_PARTICLE = 30.290432e6 / 2434617
+
+
 def em_flops(counts: np.ndarray, kwork: np.ndarray, D: int) -> float:
     return float(np.sum(counts.astype(np.float64) * kwork.astype(np.float64))) * FLOPS_PER_PK[D]
 
@@ -543,7 +550,9 @@ def run_gmcr(args):
                 "maxsweeps_frac": hs["maxsweeps_frac"], "compression_ratio": hs["compression_ratio"],
                 "proj_skipped_frac": float(np.mean((rst & 0x100) != 0))},
         "roofline": {"kernel": "em_kernel (gm_compress)", "bound": "alu", "achieved": hs["em_tflops"],
-                     "peak": peak, "unit": "TFLOP/s", "frac": hs["em_tflops"] / peak, "traffic": None,
+                     "peak": peak, "unit": "TFLOP/s", "frac": hs["em_tflops"] / peak,
+                     "traffic": (EM_DRAM_BYTES_PER_PARTICLE * n
+                                 if D == 1 and wl.v.dtype == np.float32 else None),
                      "note": f"FP32 flops = sum_j N_j * kwork_j * {FLOPS_PER_PK[D]}; peak = 152 SMs "
                              f"x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (unit counts and max clock)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
