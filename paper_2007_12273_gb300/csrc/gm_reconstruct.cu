@@ -3,7 +3,11 @@
 // moment-matching projection.
 //
 // The sampler is counter-based, so a particle can be regenerated
-// bit-identically from (seed, cell, index).  The pipeline therefore never
+// bit-identically from (seed, cell, index).  It keeps FP64 to the position
+// and to the velocity's offset from the mixture mean (so that both passes
+// see the same w = v - u, which is what makes the projected moments exact);
+// the categorical choice is decided on integers and the Gaussian draw is
+// FP32 (GB300 runs FP64 at 1/64 of the FP32 rate).  The pipeline therefore never
 // writes unprojected particles: pass 1 regenerates every particle to
 // accumulate the per-cell mass-matrix column and the velocity sums, a small
 // FP64 solve gives dA, and pass 2 regenerates the particles once more and
@@ -17,9 +21,13 @@ namespace gmcr {
 template <int D>
 struct RecCell {
   static constexpr int NM = D * (D + 1) / 2;
-  double cw[kMaxK];         // cumulative weights, summed in component order
-  double mu[kMaxK][D];
-  double Lc[kMaxK][NM];     // lower-triangular Cholesky factor, row-major
+  // categorical thresholds: u < cw_k  <=>  2 m + 1 < thr_k, where
+  // u = (m + 1/2) 2^-52 and thr_k = ceil(cw_k 2^53) (cw_k the cumulative
+  // weights summed in component order): the FP64 comparison, decided on
+  // integers
+  long long thr[kMaxK];
+  double dz[kMaxK][D];      // mu_k - u
+  float Lf[kMaxK][NM];      // lower-triangular Cholesky factor (FP32), row-major
   double u[D];              // mixture mean sum_k w_k mu_k
   double theta;             // sum_k w_k (tr Sigma_k + |mu_k - u|^2)
   double a, beta[D], alpha_new;
@@ -39,10 +47,9 @@ __device__ void load_cell(RecCell<D>& rc, int64_t j, int Kmax, const int32_t* K,
   const int k = threadIdx.x;
   if (k < Kj) {
     const double* r = prm + ((size_t)j * Kmax + k) * P;
-    for (int d = 0; d < D; ++d) rc.mu[k][d] = r[1 + d];
     if (D == 1) {
       const double s = r[2];
-      rc.Lc[k][0] = s > 0.0 ? sqrt(s) : 0.0;
+      rc.Lf[k][0] = (float)(s > 0.0 ? sqrt(s) : 0.0);
     } else {
       // S upper: [s00 s01 s02 s11 s12 s22]
       const double s00 = r[4], s01 = r[5], s02 = r[6], s11 = r[7], s12 = r[8], s22 = r[9];
@@ -54,8 +61,8 @@ __device__ void load_cell(RecCell<D>& rc, int64_t j, int Kmax, const int32_t* K,
       const double l21 = l11 > 0.0 ? (s12 - l20 * l10) / l11 : 0.0;
       const double t22 = s22 - l20 * l20 - l21 * l21;
       const double l22 = t22 > 0.0 ? sqrt(t22) : 0.0;
-      rc.Lc[k][0] = l00; rc.Lc[k][1] = l10; rc.Lc[k][2] = l11;
-      rc.Lc[k][3] = l20; rc.Lc[k][4] = l21; rc.Lc[k][5] = l22;
+      rc.Lf[k][0] = (float)l00; rc.Lf[k][1] = (float)l10; rc.Lf[k][2] = (float)l11;
+      rc.Lf[k][3] = (float)l20; rc.Lf[k][4] = (float)l21; rc.Lf[k][5] = (float)l22;
     }
   }
   if (threadIdx.x == 0) {
@@ -65,7 +72,8 @@ __device__ void load_cell(RecCell<D>& rc, int64_t j, int Kmax, const int32_t* K,
     for (int q = 0; q < Kj; ++q) {
       const double* r = prm + ((size_t)j * Kmax + q) * P;
       cum += r[0];
-      rc.cw[q] = cum;
+      const double t = ceil(cum * 9007199254740992.0);  // 2^53
+      rc.thr[q] = t < 4.0e18 ? (long long)t : 4000000000000000000ll;
       for (int d = 0; d < D; ++d) u[d] += r[0] * r[1 + d];
     }
     for (int q = 0; q < Kj; ++q) {
@@ -76,7 +84,10 @@ __device__ void load_cell(RecCell<D>& rc, int64_t j, int Kmax, const int32_t* K,
         for (int y = x; y < D; ++y, ++t) {
           if (x == y) tr += r[t];
         }
-      for (int d = 0; d < D; ++d) dd += (r[1 + d] - u[d]) * (r[1 + d] - u[d]);
+      for (int d = 0; d < D; ++d) {
+        rc.dz[q][d] = r[1 + d] - u[d];
+        dd += (r[1 + d] - u[d]) * (r[1 + d] - u[d]);
+      }
       th += r[0] * (tr + dd);
     }
     for (int d = 0; d < D; ++d) rc.u[d] = u[d];
@@ -84,54 +95,65 @@ __device__ void load_cell(RecCell<D>& rc, int64_t j, int Kmax, const int32_t* K,
   }
 }
 
-// Box-Muller radius sqrt(-2 ln u) in FP32; near u = 1 the logarithm is
-// taken as log1p(u - 1) with u - 1 formed exactly in FP64, so the radius
+// the 52 leading bits of (hi, lo), as uniform52 uses them
+__device__ __forceinline__ uint64_t bits52(uint32_t hi, uint32_t lo) {
+  return ((uint64_t)hi << 20) | (uint64_t)(lo >> 12);
+}
+// (t + 1/2) 2^-52 in FP32 (relative error ~2^-24) for a 52-bit t, without
+// FP64 arithmetic: t = hi26 2^26 + lo26
+__device__ __forceinline__ float half_ulp52_f(uint64_t t) {
+  const float hi = (float)(uint32_t)(t >> 26), lo = (float)(uint32_t)(t & 0x3FFFFFFull);
+  return fmaf(hi, 1.4901161193847656e-08f /* 2^-26 */, (lo + 0.5f) * 2.220446049250313e-16f);
+}
+// Box-Muller radius sqrt(-2 ln u) for u = (m + 1/2) 2^-52, in FP32 from the
+// integer: below 1/2, ln u; above, log1p(-(1 - u)) with 1 - u =
+// (2^52 - 1 - m + 1/2) 2^-52 formed exactly on integers, so the radius
 // keeps FP32 relative accuracy where its derivative is unbounded
-__device__ __forceinline__ float bm_radius(double u) {
-  const float lnu = u < 0.5 ? logf((float)u) : log1pf((float)(u - 1.0));
+__device__ __forceinline__ float bm_radius(uint64_t m) {
+  const float lnu = m < (1ull << 51) ? logf(half_ulp52_f(m))
+                                     : log1pf(-half_ulp52_f((1ull << 52) - 1ull - m));
   return sqrtf(-2.0f * lnu);
 }
 
-// particle i of cell j: position and velocity (Sec. 2.4, eq. mix-dist-1)
+// particle i of cell j (Sec. 2.4, eq. mix-dist-1): position x and w = v - u
+// (u the mixture mean), w = (mu_z - u) + L_z xi with L_z xi in FP32
 template <int D>
 __device__ __forceinline__ void sample_particle(const RecCell<D>& rc, int64_t j, int64_t i,
                                                 uint64_t seed, double dx, double& x,
-                                                double (&v)[D]) {
+                                                double (&w)[D]) {
   const u32x4 r0 = philox_draw(seed, (uint32_t)i, kTagSample | 0u, j);
-  const double u0 = uniform52(r0.x, r0.y);
-  const double u1 = uniform52(r0.z, r0.w);
-  x = __dmul_rn(__dadd_rn((double)j, u0), dx);
+  x = __dmul_rn(__dadd_rn((double)j, uniform52(r0.x, r0.y)), dx);
+  const long long m1x2 = 2 * (long long)bits52(r0.z, r0.w) + 1;
   const int K = rc.K;
   int z = K - 1;
   for (int k = 0; k < K; ++k)
-    if (u1 < rc.cw[k]) { z = k; break; }
+    if (m1x2 < rc.thr[k]) { z = k; break; }
   // Box-Muller (Box & Muller 1958) on (u2, u3) [and (u4, u5) for D = 3]
   float xi[3];
   {
     const u32x4 r1 = philox_draw(seed, (uint32_t)i, kTagSample | 1u, j);
-    const float rr = bm_radius(uniform52(r1.x, r1.y));
+    const float rr = bm_radius(bits52(r1.x, r1.y));
     float sn, cs;
-    sincospif(2.0f * (float)uniform52(r1.z, r1.w), &sn, &cs);
+    sincospif(2.0f * half_ulp52_f(bits52(r1.z, r1.w)), &sn, &cs);
     xi[0] = rr * cs;
     if (D == 3) xi[1] = rr * sn;
   }
   if (D == 3) {
     const u32x4 r2 = philox_draw(seed, (uint32_t)i, kTagSample | 2u, j);
-    const float rr = bm_radius(uniform52(r2.x, r2.y));
-    xi[2] = rr * cospif(2.0f * (float)uniform52(r2.z, r2.w));
+    const float rr = bm_radius(bits52(r2.x, r2.y));
+    xi[2] = rr * cospif(2.0f * half_ulp52_f(bits52(r2.z, r2.w)));
   }
   if (K == 0) {
-    for (int d = 0; d < D; ++d) v[d] = 0.0;
+    for (int d = 0; d < D; ++d) w[d] = -rc.u[d];
     return;
   }
+  const float* L = rc.Lf[z];
   if (D == 1) {
-    v[0] = __fma_rn(rc.Lc[z][0], (double)xi[0], rc.mu[z][0]);
+    w[0] = rc.dz[z][0] + (double)(L[0] * xi[0]);
   } else {
-    const double* L = rc.Lc[z];
-    const double x0 = xi[0], x1 = xi[1], x2 = xi[2];
-    v[0] = __fma_rn(L[0], x0, rc.mu[z][0]);
-    v[1] = __fma_rn(L[2], x1, __fma_rn(L[1], x0, rc.mu[z][1]));
-    v[2] = __fma_rn(L[5], x2, __fma_rn(L[4], x1, __fma_rn(L[3], x0, rc.mu[z][2])));
+    w[0] = rc.dz[z][0] + (double)(L[0] * xi[0]);
+    w[1] = rc.dz[z][1] + (double)fmaf(L[2], xi[1], L[1] * xi[0]);
+    w[2] = rc.dz[z][2] + (double)fmaf(L[5], xi[2], fmaf(L[4], xi[1], L[3] * xi[0]));
   }
 }
 
@@ -170,8 +192,8 @@ __global__ void __launch_bounds__(NT) recon_stats_kernel(int64_t C, int Kmax, co
 #pragma unroll
     for (int i = 0; i < NV; ++i) acc[i] = 0.0;
     for (int64_t i = threadIdx.x; i < n; i += NT) {
-      double x, v[D];
-      sample_particle<D>(rc, j, i, seed, dx, x, v);
+      double x, w[D];
+      sample_particle<D>(rc, j, i, seed, dx, x, w);
       double wm, w0, wp;
       shape3(order, cell_frac(x, j, inv_dx), wm, w0, wp);
       acc[0] += wm;
@@ -179,9 +201,8 @@ __global__ void __launch_bounds__(NT) recon_stats_kernel(int64_t C, int Kmax, co
       acc[2] += wp;
 #pragma unroll
       for (int d = 0; d < D; ++d) {
-        const double w = v[d] - rc.u[d];
-        acc[3 + d] += w;
-        acc[3 + D] += w * w;
+        acc[3 + d] += w[d];
+        acc[3 + D] = fma(w[d], w[d], acc[3 + D]);
       }
     }
     rblock_sum_to0<NT, NV>(acc, red);
@@ -385,13 +406,14 @@ __global__ void __launch_bounds__(NT) recon_emit_kernel(
     const double aa = rc.a, an = rc.alpha_new;
     const int skip = rc.skip;
     for (int64_t i = threadIdx.x; i < n; i += NT) {
-      double x, v[D];
-      sample_particle<D>(rc, j, i, seed, dx, x, v);
+      double x, w[D];
+      sample_particle<D>(rc, j, i, seed, dx, x, w);
       x_out[o + i] = x;
       alpha_out[o + i] = an;
 #pragma unroll
       for (int d = 0; d < D; ++d) {
-        const double vp = skip ? v[d] : rc.u[d] + aa * ((v[d] - rc.u[d]) + rc.beta[d]);
+        // v = u + w; projected: u + a (w + beta) (eqs. alpha, beta)
+        const double vp = skip ? rc.u[d] + w[d] : fma(aa, w[d] + rc.beta[d], rc.u[d]);
         v_out[(int64_t)d * n_out + o + i] = vp;
       }
     }

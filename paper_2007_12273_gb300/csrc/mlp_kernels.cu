@@ -96,37 +96,46 @@ __global__ void __launch_bounds__(128) features_kernel(int64_t C, int64_t n, con
       __syncthreads();
       continue;
     }
-    // higher moments and the histogram
-    double s3[NC];
-    for (int i = 0; i < NC; ++i) s3[i] = 0.0;
+    // higher moments and the histogram: FP32 (the features are stored in
+    // BF16; GB300 runs FP64 at 1/64 of the FP32 rate)
+    float mf[D], isf[D];
+    for (int d = 0; d < D; ++d) {
+      mf[d] = (float)mean[d];
+      isf[d] = (float)(1.0 / sd[d]);
+    }
+    const float iW = (float)(1.0 / W);
+    float s3f[NC];
+    for (int i = 0; i < NC; ++i) s3f[i] = 0.0f;
     for (int p = threadIdx.x; p < N; p += NT) {
-      const double w = alpha[o + p] / W;
-      double y[D];
-      for (int d = 0; d < D; ++d) y[d] = ((double)v[(int64_t)d * n + o + p] - mean[d]) / sd[d];
+      const float w = (float)alpha[o + p] * iW;
+      float y[D];
+      for (int d = 0; d < D; ++d) y[d] = ((float)v[(int64_t)d * n + o + p] - mf[d]) * isf[d];
       if (D == 1) {
-        const double y2 = y[0] * y[0];
-        s3[0] += w * y2 * y[0];
-        s3[1] += w * y2 * y2;
-        int b = (int)floor((y[0] + 4.0) * 8.0);
+        const float wy2 = w * y[0] * y[0];
+        s3f[0] = fmaf(wy2, y[0], s3f[0]);
+        s3f[1] = fmaf(wy2, y[0] * y[0], s3f[1]);
+        int b = (int)floorf((y[0] + 4.0f) * 8.0f);
         b = b < 0 ? 0 : (b > 63 ? 63 : b);
-        atomicAdd(&hist[b], (float)w);
+        atomicAdd(&hist[b], w);
       } else {
         for (int d = 0; d < D; ++d) {
-          const double y2 = y[d] * y[d];
-          s3[d] += w * y2 * y[d];
-          s3[3 + d] += w * y2 * y2;
+          const float wy2 = w * y[d] * y[d];
+          s3f[d] = fmaf(wy2, y[d], s3f[d]);
+          s3f[3 + d] = fmaf(wy2, y[d] * y[d], s3f[3 + d]);
         }
-        s3[6] += w * y[0] * y[1];
-        s3[7] += w * y[0] * y[2];
-        s3[8] += w * y[1] * y[2];
+        s3f[6] = fmaf(w * y[0], y[1], s3f[6]);
+        s3f[7] = fmaf(w * y[0], y[2], s3f[7]);
+        s3f[8] = fmaf(w * y[1], y[2], s3f[8]);
         int b[3];
         for (int d = 0; d < 3; ++d) {
-          b[d] = (int)floor((y[d] + 2.5) * 1.6);
+          b[d] = (int)floorf((y[d] + 2.5f) * 1.6f);
           b[d] = b[d] < 0 ? 0 : (b[d] > 7 ? 7 : b[d]);
         }
-        atomicAdd(&hist[b[0] * 64 + b[1] * 8 + b[2]], (float)w);
+        atomicAdd(&hist[b[0] * 64 + b[1] * 8 + b[2]], w);
       }
     }
+    double s3[NC];
+    for (int i = 0; i < NC; ++i) s3[i] = (double)s3f[i];
     bsum<NT>(s3, NC, red);
     // assemble
     for (int i = threadIdx.x; i < F; i += NT) {
