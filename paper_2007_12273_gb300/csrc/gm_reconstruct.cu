@@ -40,11 +40,11 @@ struct RecCell {
 // gives a zero column, as for a degenerate stored covariance)
 template <int D>
 __device__ void load_cell(RecCell<D>& rc, int64_t j, int Kmax, const int32_t* K,
-                          const double* prm) {
+                          const double* prm, int lane) {
   constexpr int NM = D * (D + 1) / 2;
   constexpr int P = 1 + D + NM;
   const int Kj = K[j];
-  const int k = threadIdx.x;
+  const int k = lane;
   if (k < Kj) {
     const double* r = prm + ((size_t)j * Kmax + k) * P;
     if (D == 1) {
@@ -65,7 +65,7 @@ __device__ void load_cell(RecCell<D>& rc, int64_t j, int Kmax, const int32_t* K,
       rc.Lf[k][3] = (float)l20; rc.Lf[k][4] = (float)l21; rc.Lf[k][5] = (float)l22;
     }
   }
-  if (threadIdx.x == 0) {
+  if (lane == 0) {
     rc.K = Kj;
     double cum = 0.0, u[D], th = 0.0;
     for (int d = 0; d < D; ++d) u[d] = 0.0;
@@ -115,14 +115,14 @@ __device__ __forceinline__ float bm_radius(uint64_t m) {
   return sqrtf(-2.0f * lnu);
 }
 
-// particle i of cell j (Sec. 2.4, eq. mix-dist-1): position x and w = v - u
-// (u the mixture mean), w = (mu_z - u) + L_z xi with L_z xi in FP32
+// particle i of cell j (Sec. 2.4, eq. mix-dist-1): the 52-bit integer m0
+// of its position's uniform u0 = (m0 + 1/2) 2^-52 (x = (j + u0) dx) and
+// w = v - u (u the mixture mean), w = (mu_z - u) + L_z xi with L_z xi in FP32
 template <int D>
 __device__ __forceinline__ void sample_particle(const RecCell<D>& rc, int64_t j, int64_t i,
-                                                uint64_t seed, double dx, double& x,
-                                                double (&w)[D]) {
+                                                uint64_t seed, uint64_t& m0, double (&w)[D]) {
   const u32x4 r0 = philox_draw(seed, (uint32_t)i, kTagSample | 0u, j);
-  x = __dmul_rn(__dadd_rn((double)j, uniform52(r0.x, r0.y)), dx);
+  m0 = bits52(r0.x, r0.y);
   const long long m1x2 = 2 * (long long)bits52(r0.z, r0.w) + 1;
   const int K = rc.K;
   int z = K - 1;
@@ -157,58 +157,66 @@ __device__ __forceinline__ void sample_particle(const RecCell<D>& rc, int64_t j,
   }
 }
 
-template <int NT, int NV>
-__device__ __forceinline__ void rblock_sum_to0(double (&v)[NV], double (*red)[NV]) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int i = 0; i < NV; ++i) v[i] = warp_sum(v[i]);
-  if (lane == 0)
-#pragma unroll
-    for (int i = 0; i < NV; ++i) red[w][i] = v[i];
-  __syncthreads();
-  if (threadIdx.x == 0)
-    for (int q = 1; q < NT / 32; ++q)
-#pragma unroll
-      for (int i = 0; i < NV; ++i) v[i] += red[q][i];
-}
-
-// Pass 1: per cell, the unit-weight shape sums of the resampled particles
-// on nodes j-1, j, j+1 (column j of M / q) and sum w, sum |w|^2 with
-// w = v - u.  cstat[j] = [c-, c0, c+, sum w (D), sum |w|^2].
-template <int D, int NT>
-__global__ void __launch_bounds__(NT) recon_stats_kernel(int64_t C, int Kmax, const int32_t* K,
-                                                         const double* prm, const int64_t* out_off,
-                                                         uint64_t seed, double dx, int order,
-                                                         double* cstat) {
+// Pass 1, one warp per cell: per cell, the unit-weight shape sums of the
+// resampled particles on nodes j-1, j, j+1 (column j of M / q) and sum w,
+// sum |w|^2 with w = v - u.  cstat[j] = [c-, c0, c+, sum w (D), sum |w|^2].
+// The shape sums come from the moments of s = xi - 1/2 (xi = u0, the
+// particle's position inside its cell): for the quadratic B-spline
+// c- = (n/4 - S1 + S2) / 2, c+ = (n/4 + S1 + S2) / 2, c0 = 3n/4 - S2 with
+// S1 = sum s, S2 = sum s^2; for CIC c- = sum max(-s, 0), c+ = sum max(s, 0),
+// c0 = n - c- - c+.
+template <int D, int NW>
+__global__ void __launch_bounds__(NW * 32) recon_stats_kernel(int64_t C, int Kmax, const int32_t* K,
+                                                              const double* prm,
+                                                              const int64_t* out_off, uint64_t seed,
+                                                              int order, double* cstat) {
   constexpr int NV = 3 + D + 1;
-  __shared__ RecCell<D> rc;
-  __shared__ double red[NT / 32][NV];
-  const double inv_dx = 1.0 / dx;
-  for (int64_t j = blockIdx.x; j < C; j += gridDim.x) {
-    load_cell<D>(rc, j, Kmax, K, prm);
-    __syncthreads();
+  constexpr int NA = 2 + D + 1;
+  __shared__ RecCell<D> rcs[NW];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  RecCell<D>& rc = rcs[wid];
+  for (int64_t j = (int64_t)blockIdx.x * NW + wid; j < C; j += (int64_t)gridDim.x * NW) {
+    load_cell<D>(rc, j, Kmax, K, prm, lane);
+    __syncwarp();
     const int64_t o = out_off[j], n = out_off[j + 1] - o;
-    double acc[NV];
+    double acc[NA];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += NT) {
-      double x, w[D];
-      sample_particle<D>(rc, j, i, seed, dx, x, w);
-      double wm, w0, wp;
-      shape3(order, cell_frac(x, j, inv_dx), wm, w0, wp);
-      acc[0] += wm;
-      acc[1] += w0;
-      acc[2] += wp;
+    for (int i = 0; i < NA; ++i) acc[i] = 0.0;
+    for (int64_t i = lane; i < n; i += 32) {
+      uint64_t m0;
+      double w[D];
+      sample_particle<D>(rc, j, i, seed, m0, w);
+      const double sx = ((double)((long long)m0 - (1ll << 51)) + 0.5) * 2.220446049250313080847263336181640625e-16;
+      if (order == 1) {
+        acc[0] += sx < 0.0 ? -sx : 0.0;
+        acc[1] += sx > 0.0 ? sx : 0.0;
+      } else {
+        acc[0] += sx;
+        acc[1] = fma(sx, sx, acc[1]);
+      }
 #pragma unroll
       for (int d = 0; d < D; ++d) {
-        acc[3 + d] += w[d];
-        acc[3 + D] = fma(w[d], w[d], acc[3 + D]);
+        acc[2 + d] += w[d];
+        acc[2 + D] = fma(w[d], w[d], acc[2 + D]);
       }
     }
-    rblock_sum_to0<NT, NV>(acc, red);
-    if (threadIdx.x == 0)
-      for (int i = 0; i < NV; ++i) cstat[(size_t)j * NV + i] = acc[i];
-    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NA; ++i) acc[i] = warp_sum(acc[i]);
+    if (lane == 0) {
+      double* cs = cstat + (size_t)j * NV;
+      const double nd = (double)n;
+      if (order == 1) {
+        cs[0] = acc[0];
+        cs[2] = acc[1];
+        cs[1] = nd - acc[0] - acc[1];
+      } else {
+        cs[0] = 0.5 * (0.25 * nd - acc[0] + acc[1]);
+        cs[2] = 0.5 * (0.25 * nd + acc[0] + acc[1]);
+        cs[1] = 0.75 * nd - acc[1];
+      }
+      for (int d = 0; d <= D; ++d) cs[3 + d] = acc[2 + d];
+    }
+    __syncwarp();
   }
 }
 
@@ -354,19 +362,22 @@ __global__ void __launch_bounds__(1024) mass_solve_kernel(int64_t n, const doubl
   }
 }
 
-// Pass 2: Lemons projection coefficients and the final particles.
-template <int D, int NT>
-__global__ void __launch_bounds__(NT) recon_emit_kernel(
+// Pass 2, one warp per cell: Lemons projection coefficients and the final
+// particles.
+template <int D, int NW>
+__global__ void __launch_bounds__(NW * 32) recon_emit_kernel(
     int64_t C, int Kmax, const int32_t* K, const double* prm, const double* W,
     const int64_t* out_off, const double* cstat, const double* dA, uint64_t seed, double dx,
     int64_t n_out, double* x_out, double* v_out, double* alpha_out, uint32_t* status_out) {
   constexpr int NV = 3 + D + 1;
-  __shared__ RecCell<D> rc;
-  for (int64_t j = blockIdx.x; j < C; j += gridDim.x) {
-    load_cell<D>(rc, j, Kmax, K, prm);
-    __syncthreads();
+  __shared__ RecCell<D> rcs[NW];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  RecCell<D>& rc = rcs[wid];
+  for (int64_t j = (int64_t)blockIdx.x * NW + wid; j < C; j += (int64_t)gridDim.x * NW) {
+    load_cell<D>(rc, j, Kmax, K, prm, lane);
+    __syncwarp();
     const int64_t o = out_off[j], n = out_off[j + 1] - o;
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
       unsigned int st = 0;
       if (n == 0) st |= GM_ST_MM_EMPTY_COL;
       const double Wj = W[j];
@@ -402,13 +413,15 @@ __global__ void __launch_bounds__(NT) recon_emit_kernel(
       rc.status = st;
       status_out[j] = st;
     }
-    __syncthreads();
+    __syncwarp();
     const double aa = rc.a, an = rc.alpha_new;
     const int skip = rc.skip;
-    for (int64_t i = threadIdx.x; i < n; i += NT) {
-      double x, w[D];
-      sample_particle<D>(rc, j, i, seed, dx, x, w);
-      x_out[o + i] = x;
+    for (int64_t i = lane; i < n; i += 32) {
+      uint64_t m0;
+      double w[D];
+      sample_particle<D>(rc, j, i, seed, m0, w);
+      const double u0 = __dmul_rn(__dadd_rn((double)m0, 0.5), 2.220446049250313080847263336181640625e-16);
+      x_out[o + i] = __dmul_rn(__dadd_rn((double)j, u0), dx);
       alpha_out[o + i] = an;
 #pragma unroll
       for (int d = 0; d < D; ++d) {
@@ -417,7 +430,7 @@ __global__ void __launch_bounds__(NT) recon_emit_kernel(
         v_out[(int64_t)d * n_out + o + i] = vp;
       }
     }
-    __syncthreads();
+    __syncwarp();
   }
 }
 
@@ -462,11 +475,14 @@ cudaError_t launch_reconstruct(int D, int64_t C, int Kmax, const int32_t* K, con
   sw.rz = r + 4 * R2; sw.rcp = r + 5 * R2; sw.ry = r + 6 * R2; sw.rzz = r + 7 * R2;
   if (dA_user) dA = dA_user;
 
-  const int g = (int)(C < 152 * 32 ? C : 152 * 32);
+  // one warp per cell, 4 cells per CTA, at most 16 CTAs per SM resident
+  constexpr int NW = 4;
+  const int64_t ncta = (C + NW - 1) / NW;
+  const int g = (int)(ncta < 152 * 16 ? ncta : 152 * 16);
   if (D == 1)
-    recon_stats_kernel<1, 128><<<g, 128, 0, s>>>(C, Kmax, K, prm, out_off, seed, dx, order, cstat);
+    recon_stats_kernel<1, NW><<<g, NW * 32, 0, s>>>(C, Kmax, K, prm, out_off, seed, order, cstat);
   else
-    recon_stats_kernel<3, 128><<<g, 128, 0, s>>>(C, Kmax, K, prm, out_off, seed, dx, order, cstat);
+    recon_stats_kernel<3, NW><<<g, NW * 32, 0, s>>>(C, Kmax, K, prm, out_off, seed, order, cstat);
   const int ga = (int)((C + 255) / 256 < 4096 ? (C + 255) / 256 : 4096);
   if (D == 1)
     assemble_kernel<1><<<ga, 256, 0, s>>>(C, cstat, W, out_off, rho_target, dx, q, A, B, Cc, Dd);
@@ -474,11 +490,11 @@ cudaError_t launch_reconstruct(int D, int64_t C, int Kmax, const int32_t* K, con
     assemble_kernel<3><<<ga, 256, 0, s>>>(C, cstat, W, out_off, rho_target, dx, q, A, B, Cc, Dd);
   mass_solve_kernel<<<1, P < 32 ? 32 : ((P + 31) / 32) * 32, 0, s>>>(C, A, B, Cc, Dd, dA, sw, P);
   if (D == 1)
-    recon_emit_kernel<1, 128><<<g, 128, 0, s>>>(C, Kmax, K, prm, W, out_off, cstat, dA, seed, dx,
-                                                 n_out, x_out, v_out, alpha_out, status_out);
+    recon_emit_kernel<1, NW><<<g, NW * 32, 0, s>>>(C, Kmax, K, prm, W, out_off, cstat, dA, seed, dx,
+                                                    n_out, x_out, v_out, alpha_out, status_out);
   else
-    recon_emit_kernel<3, 128><<<g, 128, 0, s>>>(C, Kmax, K, prm, W, out_off, cstat, dA, seed, dx,
-                                                 n_out, x_out, v_out, alpha_out, status_out);
+    recon_emit_kernel<3, NW><<<g, NW * 32, 0, s>>>(C, Kmax, K, prm, W, out_off, cstat, dA, seed, dx,
+                                                    n_out, x_out, v_out, alpha_out, status_out);
   return cudaGetLastError();
 }
 
