@@ -20,32 +20,49 @@ __device__ __forceinline__ void block_sum_to0(double (&v)[NV], double (*red)[NV]
 }
 
 // Per-cell partial deposits: part[j] = sum_{p in j} alpha_p S(x_i - x_p)
-// for i = j-1, j, j+1 (alpha = NULL means unit weights).  One CTA per cell
-// (grid-stride over cells).
-template <int NT>
-__global__ void __launch_bounds__(NT) deposit_partials_kernel(int64_t C, const int64_t* cell_off,
-                                                              const double* x, const double* alpha,
-                                                              double inv_dx, int order,
-                                                              double* part /*[C][3]*/) {
-  __shared__ double red[NT / 32][3];
-  for (int64_t j = blockIdx.x; j < C; j += gridDim.x) {
+// for i = j-1, j, j+1 (alpha = NULL means unit weights).  One warp per
+// cell.  With s = xi - 1/2 (xi the position inside the cell) the quadratic
+// B-spline weights are (1/2 - s)^2 / 2, 3/4 - s^2, (1/2 + s)^2 / 2, so the
+// three sums follow from A0 = sum alpha, A1 = sum alpha s, A2 = sum alpha
+// s^2; for CIC they are sum alpha max(-s, 0), A0 - (the other two),
+// sum alpha max(s, 0).
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) deposit_partials_kernel(int64_t C, const int64_t* cell_off,
+                                                                   const double* x, const double* alpha,
+                                                                   double inv_dx, int order,
+                                                                   double* part /*[C][3]*/) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int64_t j = (int64_t)blockIdx.x * NW + wid; j < C; j += (int64_t)gridDim.x * NW) {
     const int64_t o = cell_off[j], n = cell_off[j + 1] - o;
-    double acc[3] = {0.0, 0.0, 0.0};
-    for (int64_t p = threadIdx.x; p < n; p += NT) {
-      double wm, w0, wp;
-      shape3(order, cell_frac(x[o + p], j, inv_dx), wm, w0, wp);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int64_t p = lane; p < n; p += 32) {
+      const double sx = cell_frac(x[o + p], j, inv_dx) - 0.5;
       const double al = alpha ? alpha[o + p] : 1.0;
-      acc[0] += al * wm;
-      acc[1] += al * w0;
-      acc[2] += al * wp;
+      if (order == 1) {
+        a0 += al;
+        a1 = sx < 0.0 ? fma(-al, sx, a1) : a1;
+        a2 = sx > 0.0 ? fma(al, sx, a2) : a2;
+      } else {
+        const double as = al * sx;
+        a0 += al;
+        a1 += as;
+        a2 = fma(as, sx, a2);
+      }
     }
-    block_sum_to0<NT, 3>(acc, red);
-    if (threadIdx.x == 0) {
-      part[3 * j + 0] = acc[0];
-      part[3 * j + 1] = acc[1];
-      part[3 * j + 2] = acc[2];
+    a0 = warp_sum(a0);
+    a1 = warp_sum(a1);
+    a2 = warp_sum(a2);
+    if (lane == 0) {
+      if (order == 1) {
+        part[3 * j + 0] = a1;
+        part[3 * j + 1] = a0 - a1 - a2;
+        part[3 * j + 2] = a2;
+      } else {
+        part[3 * j + 0] = 0.5 * (0.25 * a0 - a1 + a2);
+        part[3 * j + 1] = 0.75 * a0 - a2;
+        part[3 * j + 2] = 0.5 * (0.25 * a0 + a1 + a2);
+      }
     }
-    __syncthreads();
   }
 }
 
@@ -145,8 +162,8 @@ cudaError_t launch_deposit(int64_t C, const int64_t* cell_off, const double* x,
                            const double* alpha, double dx, double q, int order, double* part,
                            double* rho, cudaStream_t s) {
   if (C == 0) return cudaSuccess;
-  deposit_partials_kernel<128><<<grid_for(C, 152 * 16), 128, 0, s>>>(C, cell_off, x, alpha,
-                                                                     1.0 / dx, order, part);
+  deposit_partials_kernel<4><<<grid_for((C + 3) / 4, 152 * 16), 128, 0, s>>>(C, cell_off, x, alpha,
+                                                                              1.0 / dx, order, part);
   deposit_combine_kernel<<<grid_for((C + 255) / 256, 1024), 256, 0, s>>>(C, part, q / dx, rho);
   return cudaGetLastError();
 }

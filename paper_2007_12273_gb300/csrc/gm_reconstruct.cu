@@ -295,6 +295,53 @@ struct SolveWs {
   double *rz, *rcp, *ry, *rzz; // [2P]
 };
 
+// block t of P (rows r0 .. r1-1): forward elimination of the local
+// tridiagonal system (no outer couplings) with three right-hand sides, back
+// substitution, and the block's two interface rows
+__device__ __forceinline__ void block_eliminate(int64_t n, const double* a, const double* b,
+                                                const double* c, const double* d, const SolveWs& ws,
+                                                int P, int t) {
+  const int64_t r0 = (int64_t)t * n / P, r1 = (int64_t)(t + 1) * n / P;
+  double r = 1.0 / b[r0];
+  ws.cp[r0] = c[r0] * r;
+  ws.y[r0] = d[r0] * r;
+  ws.v[r0] = a[r0] * r;
+  ws.w[r0] = (r1 - 1 == r0) ? c[r0] * r : 0.0;
+  for (int64_t i = r0 + 1; i < r1; ++i) {
+    const double m = b[i] - a[i] * ws.cp[i - 1];
+    r = 1.0 / m;
+    ws.cp[i] = c[i] * r;
+    ws.y[i] = (d[i] - a[i] * ws.y[i - 1]) * r;
+    ws.v[i] = (-a[i] * ws.v[i - 1]) * r;
+    ws.w[i] = ((i == r1 - 1 ? c[i] : 0.0) - a[i] * ws.w[i - 1]) * r;
+  }
+  for (int64_t i = r1 - 2; i >= r0; --i) {
+    ws.y[i] -= ws.cp[i] * ws.y[i + 1];
+    ws.v[i] -= ws.cp[i] * ws.v[i + 1];
+    ws.w[i] -= ws.cp[i] * ws.w[i + 1];
+  }
+  const double yF = ws.y[r0], vF = ws.v[r0], wF = ws.w[r0];
+  const double yL = ws.y[r1 - 1], vL = ws.v[r1 - 1], wL = ws.w[r1 - 1];
+  // interface rows: 2t (eliminates X_{t+1}^F), 2t+1 (eliminates X_{t-1}^L)
+  ws.ra[2 * t] = wL * vF - wF * vL;
+  ws.rb[2 * t] = wL;
+  ws.rc[2 * t] = -wF;
+  ws.rd[2 * t] = wL * yF - wF * yL;
+  ws.ra[2 * t + 1] = vL;
+  ws.rb[2 * t + 1] = -vF;
+  ws.rc[2 * t + 1] = vL * wF - vF * wL;
+  ws.rd[2 * t + 1] = vL * yF - vF * yL;
+}
+
+// block t's interior from the interface solution ws.rz
+__device__ __forceinline__ void block_reconstruct(int64_t n, const SolveWs& ws, int P, int t,
+                                                  double* x) {
+  const int64_t r0 = (int64_t)t * n / P, r1 = (int64_t)(t + 1) * n / P;
+  const double Xl = ws.rz[(2 * t - 1 + 2 * P) % (2 * P)];  // last unknown of block t-1
+  const double Xf = ws.rz[(2 * t + 2) % (2 * P)];          // first unknown of block t+1
+  for (int64_t i = r0; i < r1; ++i) x[i] = ws.y[i] - ws.v[i] * Xl - ws.w[i] * Xf;
+}
+
 __global__ void __launch_bounds__(1024) mass_solve_kernel(int64_t n, const double* a,
                                                           const double* b, const double* c,
                                                           const double* d, double* x, SolveWs ws,
@@ -318,48 +365,25 @@ __global__ void __launch_bounds__(1024) mass_solve_kernel(int64_t n, const doubl
     if (t == 0) cyclic_thomas_seq(n, a, b, c, d, x, ws.cp, ws.y, ws.v);
     return;
   }
-  if (t < P) {
-    const int64_t r0 = (int64_t)t * n / P, r1 = (int64_t)(t + 1) * n / P;
-    // forward: local tridiagonal (no outer couplings), three rhs
-    double r = 1.0 / b[r0];
-    ws.cp[r0] = c[r0] * r;
-    ws.y[r0] = d[r0] * r;
-    ws.v[r0] = a[r0] * r;
-    ws.w[r0] = (r1 - 1 == r0) ? c[r0] * r : 0.0;
-    for (int64_t i = r0 + 1; i < r1; ++i) {
-      const double m = b[i] - a[i] * ws.cp[i - 1];
-      r = 1.0 / m;
-      ws.cp[i] = c[i] * r;
-      ws.y[i] = (d[i] - a[i] * ws.y[i - 1]) * r;
-      ws.v[i] = (-a[i] * ws.v[i - 1]) * r;
-      ws.w[i] = ((i == r1 - 1 ? c[i] : 0.0) - a[i] * ws.w[i - 1]) * r;
-    }
-    for (int64_t i = r1 - 2; i >= r0; --i) {
-      ws.y[i] -= ws.cp[i] * ws.y[i + 1];
-      ws.v[i] -= ws.cp[i] * ws.v[i + 1];
-      ws.w[i] -= ws.cp[i] * ws.w[i + 1];
-    }
-    const double yF = ws.y[r0], vF = ws.v[r0], wF = ws.w[r0];
-    const double yL = ws.y[r1 - 1], vL = ws.v[r1 - 1], wL = ws.w[r1 - 1];
-    // interface rows: 2t (eliminates X_{t+1}^F), 2t+1 (eliminates X_{t-1}^L)
-    ws.ra[2 * t] = wL * vF - wF * vL;
-    ws.rb[2 * t] = wL;
-    ws.rc[2 * t] = -wF;
-    ws.rd[2 * t] = wL * yF - wF * yL;
-    ws.ra[2 * t + 1] = vL;
-    ws.rb[2 * t + 1] = -vF;
-    ws.rc[2 * t + 1] = vL * wF - vF * wL;
-    ws.rd[2 * t + 1] = vL * yF - vF * yL;
-  }
+  if (t < P) block_eliminate(n, a, b, c, d, ws, P, t);
   __syncthreads();
   if (t == 0) cyclic_thomas_seq(2 * P, ws.ra, ws.rb, ws.rc, ws.rd, ws.rz, ws.rcp, ws.ry, ws.rzz);
   __syncthreads();
-  if (t < P) {
-    const int64_t r0 = (int64_t)t * n / P, r1 = (int64_t)(t + 1) * n / P;
-    const double Xl = ws.rz[(2 * t - 1 + 2 * P) % (2 * P)];  // last unknown of block t-1
-    const double Xf = ws.rz[(2 * t + 2) % (2 * P)];          // first unknown of block t+1
-    for (int64_t i = r0; i < r1; ++i) x[i] = ws.y[i] - ws.v[i] * Xl - ws.w[i] * Xf;
-  }
+  if (t < P) block_reconstruct(n, ws, P, t, x);
+}
+
+// The same partition method across the GPU for large meshes: the blocks
+// are eliminated by one thread each over many CTAs (the FP64 work of a
+// large mesh would otherwise run at one SM's FP64 rate), the 2P interface
+// unknowns are solved by mass_solve_kernel, and the blocks reconstructed.
+__global__ void mm_eliminate_kernel(int64_t n, const double* a, const double* b, const double* c,
+                                    const double* d, SolveWs ws, int P) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < P) block_eliminate(n, a, b, c, d, ws, P, t);
+}
+__global__ void mm_reconstruct_kernel(int64_t n, SolveWs ws, int P, double* x) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < P) block_reconstruct(n, ws, P, t, x);
 }
 
 // Pass 2, one warp per cell: Lemons projection coefficients and the final
@@ -435,18 +459,37 @@ __global__ void __launch_bounds__(NW * 32) recon_emit_kernel(
 }
 
 // ---------------------------------------------------------------------------
-size_t reconstruct_ws_bytes(int D, int64_t C) {
-  const int P = solve_blocks(C);
-  const size_t per_cell = (size_t)(3 + D + 1) + 4 /*a b c d*/ + 1 /*dA*/ + 4 /*y v w cp*/;
-  return (per_cell * (size_t)C + 8 * (size_t)(2 * P + 2)) * sizeof(double) + 1024;
-}
-
 int solve_blocks(int64_t C) {
   if (C < 64) return 1;
   int P = (int)sqrt((double)C / 2.0);
   if (P > 1024) P = 1024;
   if (P < 2) P = 2;
   return P;
+}
+
+// mass-matrix solve plan: meshes of at least kMultiRows cells are
+// eliminated in blocks of ~64 rows across the GPU (P blocks; interface
+// system of 2P rows solved on one CTA with P2 blocks); smaller ones on one
+// CTA (P = solve_blocks(C))
+constexpr int64_t kMultiRows = 2048;
+struct SolvePlan {
+  bool multi;
+  int P, P2;
+};
+static SolvePlan plan_solve(int64_t C) {
+  SolvePlan pl;
+  pl.multi = C >= kMultiRows;
+  pl.P = pl.multi ? (int)(C / 64) : solve_blocks(C);
+  pl.P2 = pl.multi ? solve_blocks(2 * (int64_t)pl.P) : 1;
+  return pl;
+}
+
+size_t reconstruct_ws_bytes(int D, int64_t C) {
+  const SolvePlan pl = plan_solve(C);
+  const size_t per_cell = (size_t)(3 + D + 1) + 4 /*a b c d*/ + 1 /*dA*/ + 4 /*y v w cp*/;
+  size_t dbl = per_cell * (size_t)C + 8 * (size_t)(2 * pl.P + 2);
+  if (pl.multi) dbl += 4 * (size_t)(2 * pl.P) + 8 * (size_t)(2 * pl.P2 + 2);
+  return dbl * sizeof(double) + 1024;
 }
 
 cudaError_t launch_reconstruct(int D, int64_t C, int Kmax, const int32_t* K, const double* prm,
@@ -456,7 +499,8 @@ cudaError_t launch_reconstruct(int D, int64_t C, int Kmax, const int32_t* K, con
                                uint32_t* status_out, double* dA_user, void* ws, cudaStream_t s) {
   if (C == 0) return cudaSuccess;
   const int NVm = 3 + D + 1;
-  const int P = solve_blocks(C);
+  const SolvePlan pl = plan_solve(C);
+  const int P = pl.P;
   double* base = (double*)ws;
   double* cstat = base;
   double* A = cstat + (size_t)NVm * C;
@@ -473,6 +517,15 @@ cudaError_t launch_reconstruct(int D, int64_t C, int Kmax, const int32_t* K, con
   const int64_t R2 = 2 * (int64_t)P + 2;
   sw.ra = r; sw.rb = r + R2; sw.rc = r + 2 * R2; sw.rd = r + 3 * R2;
   sw.rz = r + 4 * R2; sw.rcp = r + 5 * R2; sw.ry = r + 6 * R2; sw.rzz = r + 7 * R2;
+  SolveWs sw2;  // the interface system's own workspace (multi-CTA plan)
+  if (pl.multi) {
+    const int64_t n2 = 2 * (int64_t)P, R22 = 2 * (int64_t)pl.P2 + 2;
+    double* r2 = r + 8 * R2;
+    sw2.y = r2; sw2.v = r2 + n2; sw2.w = r2 + 2 * n2; sw2.cp = r2 + 3 * n2;
+    double* q2 = r2 + 4 * n2;
+    sw2.ra = q2; sw2.rb = q2 + R22; sw2.rc = q2 + 2 * R22; sw2.rd = q2 + 3 * R22;
+    sw2.rz = q2 + 4 * R22; sw2.rcp = q2 + 5 * R22; sw2.ry = q2 + 6 * R22; sw2.rzz = q2 + 7 * R22;
+  }
   if (dA_user) dA = dA_user;
 
   // one warp per cell, 4 cells per CTA, at most 16 CTAs per SM resident
@@ -488,7 +541,15 @@ cudaError_t launch_reconstruct(int D, int64_t C, int Kmax, const int32_t* K, con
     assemble_kernel<1><<<ga, 256, 0, s>>>(C, cstat, W, out_off, rho_target, dx, q, A, B, Cc, Dd);
   else
     assemble_kernel<3><<<ga, 256, 0, s>>>(C, cstat, W, out_off, rho_target, dx, q, A, B, Cc, Dd);
-  mass_solve_kernel<<<1, P < 32 ? 32 : ((P + 31) / 32) * 32, 0, s>>>(C, A, B, Cc, Dd, dA, sw, P);
+  if (pl.multi) {
+    mm_eliminate_kernel<<<(P + 127) / 128, 128, 0, s>>>(C, A, B, Cc, Dd, sw, P);
+    const int P2 = pl.P2;
+    mass_solve_kernel<<<1, P2 < 32 ? 32 : ((P2 + 31) / 32) * 32, 0, s>>>(
+        2 * (int64_t)P, sw.ra, sw.rb, sw.rc, sw.rd, sw.rz, sw2, P2);
+    mm_reconstruct_kernel<<<(P + 127) / 128, 128, 0, s>>>(C, sw, P, dA);
+  } else {
+    mass_solve_kernel<<<1, P < 32 ? 32 : ((P + 31) / 32) * 32, 0, s>>>(C, A, B, Cc, Dd, dA, sw, P);
+  }
   if (D == 1)
     recon_emit_kernel<1, NW><<<g, NW * 32, 0, s>>>(C, Kmax, K, prm, W, out_off, cstat, dA, seed, dx,
                                                     n_out, x_out, v_out, alpha_out, status_out);

@@ -19,114 +19,111 @@ namespace {
 __host__ __device__ constexpr int mlp_F(int D) { return D == 1 ? 128 : 576; }
 __host__ __device__ constexpr int mlp_SP(int D) { return 2 + 2 * D + D * (D - 1) / 2; }
 
-// block sum of nv <= 16 doubles held by every thread (result in every thread)
-template <int NT>
-__device__ __forceinline__ void bsum(double* v, int nv, double (*red)[16]) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int i = 0; i < nv; ++i) v[i] = warp_sum(v[i]);
-  if (lane == 0)
-    for (int i = 0; i < nv; ++i) red[w][i] = v[i];
-  __syncthreads();
-  for (int i = 0; i < nv; ++i) {
-    double s = 0.0;
-    for (int q = 0; q < NT / 32; ++q) s += red[q][i];
-    v[i] = s;
-  }
-  __syncthreads();
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// features: one CTA per cell
+// features: one warp per cell (NW cells per CTA).  The weighted mean and
+// standard deviation (which whiten the cell and map the network's output
+// back) are FP64 two-pass sums; the whitened moments and the histogram are
+// FP32 (the features are stored in BF16; GB300 runs FP64 at 1/64 of the
+// FP32 rate).
 // ---------------------------------------------------------------------------
-template <int D, typename VT>
-__global__ void __launch_bounds__(128) features_kernel(int64_t C, int64_t n, const int64_t* cell_off,
-                                                       const VT* v, const double* alpha,
-                                                       __nv_bfloat16* feat, double* wstat) {
-  constexpr int NT = 128;
+template <int D, typename VT, int NW>
+__global__ void __launch_bounds__(NW * 32) features_kernel(int64_t C, int64_t n, const int64_t* cell_off,
+                                                           const VT* v, const double* alpha,
+                                                           __nv_bfloat16* feat, double* wstat) {
   constexpr int F = mlp_F(D);
   constexpr int NB = D == 1 ? 64 : 512;
   constexpr int NMOM = D == 1 ? 3 : 10;
-  constexpr int NA = 1 + D;
   constexpr int NC = D == 1 ? 2 : 9;  // higher moments accumulated
-  __shared__ double red[NT / 32][16];
-  __shared__ float hist[NB];
-  for (int64_t j = blockIdx.x; j < C; j += gridDim.x) {
+  __shared__ float hists[NW][NB];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float* hist = hists[wid];
+  for (int64_t j = (int64_t)blockIdx.x * NW + wid; j < C; j += (int64_t)gridDim.x * NW) {
     const int64_t o = cell_off[j];
     const int N = (int)(cell_off[j + 1] - o);
-    for (int b = threadIdx.x; b < NB; b += NT) hist[b] = 0.0f;
+    for (int b = lane; b < NB; b += 32) hist[b] = 0.0f;
     // W and the weighted mean
-    double s1[NA];
-    for (int i = 0; i < NA; ++i) s1[i] = 0.0;
-    for (int p = threadIdx.x; p < N; p += NT) {
+    double W = 0.0, s1[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) s1[d] = 0.0;
+    for (int p = lane; p < N; p += 32) {
       const double a = alpha[o + p];
-      s1[0] += a;
-      for (int d = 0; d < D; ++d) s1[1 + d] += a * (double)v[(int64_t)d * n + o + p];
+      W += a;
+#pragma unroll
+      for (int d = 0; d < D; ++d) s1[d] = fma(a, (double)v[(int64_t)d * n + o + p], s1[d]);
     }
-    bsum<NT>(s1, NA, red);
-    const double W = s1[0];
+    W = warp_sum(W);
     double mean[D];
-    for (int d = 0; d < D; ++d) mean[d] = W > 0.0 ? s1[1 + d] / W : 0.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) mean[d] = W > 0.0 ? warp_sum(s1[d]) / W : 0.0;
     // variances
     double s2[D];
+#pragma unroll
     for (int d = 0; d < D; ++d) s2[d] = 0.0;
-    for (int p = threadIdx.x; p < N; p += NT) {
+    for (int p = lane; p < N; p += 32) {
       const double a = alpha[o + p];
+#pragma unroll
       for (int d = 0; d < D; ++d) {
         const double dv = (double)v[(int64_t)d * n + o + p] - mean[d];
-        s2[d] += a * dv * dv;
+        s2[d] = fma(a * dv, dv, s2[d]);
       }
     }
-    bsum<NT>(s2, D, red);
     double sd[D];
     bool ok = W > 0.0;
+#pragma unroll
     for (int d = 0; d < D; ++d) {
-      sd[d] = ok ? sqrt(s2[d] / W) : 0.0;
+      const double var = warp_sum(s2[d]);
+      sd[d] = ok ? sqrt(var / W) : 0.0;
       ok = ok && sd[d] > 0.0;
     }
-    if (threadIdx.x == 0)
+    if (lane == 0)
       for (int d = 0; d < D; ++d) {
         wstat[j * 2 * D + d] = mean[d];
         wstat[j * 2 * D + D + d] = sd[d];
       }
     __nv_bfloat16* fj = feat + (size_t)j * F;
     if (!ok) {
-      for (int i = threadIdx.x; i < F; i += NT) fj[i] = __float2bfloat16(0.0f);
-      __syncthreads();
+      for (int i = lane; i < F; i += 32) fj[i] = __float2bfloat16(0.0f);
+      __syncwarp();
       continue;
     }
-    // higher moments and the histogram: FP32 (the features are stored in
-    // BF16; GB300 runs FP64 at 1/64 of the FP32 rate)
+    __syncwarp();  // histogram zeroed
+    // higher moments and the histogram (FP32)
     float mf[D], isf[D];
+#pragma unroll
     for (int d = 0; d < D; ++d) {
       mf[d] = (float)mean[d];
       isf[d] = (float)(1.0 / sd[d]);
     }
     const float iW = (float)(1.0 / W);
-    float s3f[NC];
-    for (int i = 0; i < NC; ++i) s3f[i] = 0.0f;
-    for (int p = threadIdx.x; p < N; p += NT) {
+    float s3[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) s3[i] = 0.0f;
+    for (int p = lane; p < N; p += 32) {
       const float w = (float)alpha[o + p] * iW;
       float y[D];
+#pragma unroll
       for (int d = 0; d < D; ++d) y[d] = ((float)v[(int64_t)d * n + o + p] - mf[d]) * isf[d];
       if (D == 1) {
         const float wy2 = w * y[0] * y[0];
-        s3f[0] = fmaf(wy2, y[0], s3f[0]);
-        s3f[1] = fmaf(wy2, y[0] * y[0], s3f[1]);
+        s3[0] = fmaf(wy2, y[0], s3[0]);
+        s3[1] = fmaf(wy2, y[0] * y[0], s3[1]);
         int b = (int)floorf((y[0] + 4.0f) * 8.0f);
         b = b < 0 ? 0 : (b > 63 ? 63 : b);
         atomicAdd(&hist[b], w);
       } else {
+#pragma unroll
         for (int d = 0; d < D; ++d) {
           const float wy2 = w * y[d] * y[d];
-          s3f[d] = fmaf(wy2, y[d], s3f[d]);
-          s3f[3 + d] = fmaf(wy2, y[d] * y[d], s3f[3 + d]);
+          s3[d] = fmaf(wy2, y[d], s3[d]);
+          s3[3 + d] = fmaf(wy2, y[d] * y[d], s3[3 + d]);
         }
-        s3f[6] = fmaf(w * y[0], y[1], s3f[6]);
-        s3f[7] = fmaf(w * y[0], y[2], s3f[7]);
-        s3f[8] = fmaf(w * y[1], y[2], s3f[8]);
+        s3[6] = fmaf(w * y[0], y[1], s3[6]);
+        s3[7] = fmaf(w * y[0], y[2], s3[7]);
+        s3[8] = fmaf(w * y[1], y[2], s3[8]);
         int b[3];
+#pragma unroll
         for (int d = 0; d < 3; ++d) {
           b[d] = (int)floorf((y[d] + 2.5f) * 1.6f);
           b[d] = b[d] < 0 ? 0 : (b[d] > 7 ? 7 : b[d]);
@@ -134,19 +131,19 @@ __global__ void __launch_bounds__(128) features_kernel(int64_t C, int64_t n, con
         atomicAdd(&hist[b[0] * 64 + b[1] * 8 + b[2]], w);
       }
     }
-    double s3[NC];
-    for (int i = 0; i < NC; ++i) s3[i] = (double)s3f[i];
-    bsum<NT>(s3, NC, red);
+#pragma unroll
+    for (int i = 0; i < NC; ++i) s3[i] = warp_sum(s3[i]);
+    __syncwarp();  // histogram complete
     // assemble
-    for (int i = threadIdx.x; i < F; i += NT) {
+    for (int i = lane; i < F; i += 32) {
       float val = 0.0f;
       if (i < NMOM) {
         if (D == 1) {
-          val = i == 0 ? (float)s3[0] : (i == 1 ? (float)(s3[1] - 3.0) : (float)(log((double)N) / 10.0));
+          val = i == 0 ? s3[0] : (i == 1 ? s3[1] - 3.0f : (float)(log((double)N) / 10.0));
         } else {
-          if (i < 3) val = (float)s3[i];
-          else if (i < 6) val = (float)(s3[i] - 3.0);
-          else if (i < 9) val = (float)s3[i];
+          if (i < 3) val = s3[i];
+          else if (i < 6) val = s3[i] - 3.0f;
+          else if (i < 9) val = s3[i];
           else val = (float)(log((double)N) / 10.0);
         }
       } else if (i < NMOM + NB) {
@@ -154,7 +151,7 @@ __global__ void __launch_bounds__(128) features_kernel(int64_t C, int64_t n, con
       }
       fj[i] = __float2bfloat16(val);
     }
-    __syncthreads();
+    __syncwarp();  // before the next cell clears the histogram
   }
 }
 
@@ -419,14 +416,16 @@ cudaError_t launch_features(int D, int64_t C, int64_t n, const int64_t* cell_off
                             int v_f64, const double* alpha, void* feat, double* wstat,
                             cudaStream_t s) {
   if (C == 0) return cudaSuccess;
-  const int g = (int)(C < 152 * 16 ? C : 152 * 16);
+  constexpr int NW = 4;
+  const int64_t ncta = (C + NW - 1) / NW;
+  const int g = (int)(ncta < 152 * 16 ? ncta : 152 * 16);
   __nv_bfloat16* f = (__nv_bfloat16*)feat;
   if (D == 1) {
-    if (v_f64) features_kernel<1, double><<<g, 128, 0, s>>>(C, n, cell_off, (const double*)v, alpha, f, wstat);
-    else features_kernel<1, float><<<g, 128, 0, s>>>(C, n, cell_off, (const float*)v, alpha, f, wstat);
+    if (v_f64) features_kernel<1, double, NW><<<g, NW * 32, 0, s>>>(C, n, cell_off, (const double*)v, alpha, f, wstat);
+    else features_kernel<1, float, NW><<<g, NW * 32, 0, s>>>(C, n, cell_off, (const float*)v, alpha, f, wstat);
   } else {
-    if (v_f64) features_kernel<3, double><<<g, 128, 0, s>>>(C, n, cell_off, (const double*)v, alpha, f, wstat);
-    else features_kernel<3, float><<<g, 128, 0, s>>>(C, n, cell_off, (const float*)v, alpha, f, wstat);
+    if (v_f64) features_kernel<3, double, NW><<<g, NW * 32, 0, s>>>(C, n, cell_off, (const double*)v, alpha, f, wstat);
+    else features_kernel<3, float, NW><<<g, NW * 32, 0, s>>>(C, n, cell_off, (const float*)v, alpha, f, wstat);
   }
   return cudaGetLastError();
 }

@@ -213,6 +213,25 @@ def test_reconstruct_parity_and_conservation(gm, which):
         assert abs(m1["E"][j] - m0["E"][j]) <= 1e-12 * m0["E"][j]
 
 
+@pytest.mark.parametrize("C", [2048, 9001])
+def test_reconstruct_large_mesh_block_solve(gm, C):
+    """Meshes of 2048 cells and more take the multi-CTA mass-matrix solve
+    (blocks of ~64 rows eliminated across the GPU, the interface system on
+    one CTA): dA against the oracle's direct cyclic solve, and the charge
+    on every node."""
+    wl = workloads.mixture_1d1v(C=C, mean_n=40, clip=(12, 90), seed=41)
+    ref = oracle.compress(wl.params, wl.cell_off, wl.x, wl.v, wl.alpha, nthreads=NTHREADS)
+    g, o = recon_both(gm, wl, ref)
+    np.testing.assert_array_equal(g["x"], o["x"])
+    np.testing.assert_allclose(g["dA"], o["dA"], rtol=0, atol=1e-12 * np.abs(o["alpha"]).max())
+    np.testing.assert_allclose(g["alpha"], o["alpha"], rtol=1e-12)
+    cfg = gm.config(wl.params)
+    m1 = {k: host(v) for k, v in gm.gm_moments(cfg, dev(wl.cell_off), dev(g["x"]), dev(g["v"]),
+                                                 dev(g["alpha"])).items()}
+    rt = ref["rho_target"]
+    np.testing.assert_allclose(m1["rho"], rt, rtol=0, atol=1e-12 * np.abs(rt).max())
+
+
 def test_reconstruct_small_meshes_and_empty_cells(gm):
     for C in (1, 2, 3, 5, 70):
         rng = np.random.default_rng(C)
