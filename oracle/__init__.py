@@ -74,6 +74,12 @@ def _load():
             lib.oracle_shape.argtypes = [ct.c_int, ct.c_double]
             lib.oracle_shape.restype = ct.c_double
             lib.oracle_max_threads.restype = ct.c_int
+            lib.oracle_standard.argtypes = ([P, ct.c_int64] + [P] * 4 + [ct.c_int] * 3 + [P] * 11
+                                            + [ct.c_int])
+            lib.oracle_std_cell.argtypes = ([P, ct.c_int64, ct.c_int64, P, P] + [ct.c_int] * 3
+                                            + [P] * 9 + [ct.c_int, P])
+            lib.oracle_aa_affine.argtypes = [ct.c_int, P, P, P, ct.c_int, ct.c_int, P, P]
+            lib.oracle_kmeans.argtypes = [ct.c_int, ct.c_int, ct.c_int64, P, P, P, ct.c_int, P, P, P]
             _lib = lib
     return _lib
 
@@ -175,6 +181,89 @@ def em_cell(params: dict, vv, alpha, cell: int = 0, init_params=None, init_K: in
     return dict(K=int(K[0]), params=prm, W=float(W[0]), lnL=float(lnL[0]), sweeps=int(sw[0]),
                 status=int(st[0]), Ltrace=tr[: int(nt[0])].copy(),
                 Ktrace=kt[: int(nt[0])].copy())
+
+
+def standard(params: dict, cell_off, x, v, alpha, init: int = 0, aa_memory: int = 0,
+             kmeans_iters: int = 0, nthreads: int = 1, cell_ids=None) -> dict:
+    """Oracle of the standard (non-adaptive) EM of Sec. 4 for every cell:
+    ``init`` 0 = random particles, 1 = K-means; ``aa_memory`` > 0 turns on
+    Anderson acceleration.  Outputs as ``compress`` plus iterations, AA
+    steps, AA resets and K-means passes per cell."""
+    lib = _load()
+    cfg = _cfg(params)
+    cell_off = np.ascontiguousarray(cell_off, dtype=np.int64)
+    C = cell_off.shape[0] - 1
+    D = cfg.D
+    x = _f64(x); v = _f64(v); alpha = _f64(alpha)
+    assert v.shape == (D, int(cell_off[-1]))
+    out = dict(K=np.zeros(C, np.int32), params=np.zeros((C, cfg.Kmax, P_of(D))),
+               W=np.zeros(C), rho_target=np.zeros(C), lnL=np.zeros(C),
+               iters=np.zeros(C, np.int32), aa_steps=np.zeros(C, np.int32),
+               aa_resets=np.zeros(C, np.int32), km_passes=np.zeros(C, np.int32),
+               status=np.zeros(C, np.uint32))
+    rc = lib.oracle_standard(ct.byref(cfg), C, _ptr(cell_off), _ptr(x), _ptr(v), _ptr(alpha),
+                             int(init), int(aa_memory), int(kmeans_iters), _ptr(out["K"]),
+                             _ptr(out["params"]), _ptr(out["W"]), _ptr(out["rho_target"]),
+                             _ptr(out["lnL"]), _ptr(out["iters"]), _ptr(out["aa_steps"]),
+                             _ptr(out["aa_resets"]), _ptr(out["km_passes"]), _ptr(out["status"]),
+                             _ptr(None if cell_ids is None else np.ascontiguousarray(cell_ids, dtype=np.int64)),
+                             int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle_standard failed ({rc})")
+    return out
+
+
+def std_cell(params: dict, vv, alpha, cell: int = 0, init: int = 0, aa_memory: int = 0,
+             kmeans_iters: int = 0, trace_cap: int = 0) -> dict:
+    """Standard EM of one cell (``vv`` [N, D]) with the trace of L(theta_i)."""
+    lib = _load()
+    cfg = _cfg(params)
+    vv = _f64(vv).reshape(-1, cfg.D)
+    N = vv.shape[0]
+    alpha = _f64(alpha)
+    prm = np.zeros((cfg.Kmax, P_of(cfg.D)))
+    i32 = lambda: np.zeros(1, np.int32)
+    K, it, na, nr, km = i32(), i32(), i32(), i32(), i32()
+    lnL = np.zeros(1); st = np.zeros(1, np.uint32)
+    tr = np.zeros(max(trace_cap, 1)); nt = np.zeros(1, np.int32)
+    lib.oracle_std_cell(ct.byref(cfg), int(cell), N, _ptr(vv), _ptr(alpha), int(init),
+                        int(aa_memory), int(kmeans_iters), _ptr(prm), _ptr(K), _ptr(lnL), _ptr(it),
+                        _ptr(na), _ptr(nr), _ptr(km), _ptr(st), _ptr(tr) if trace_cap else None,
+                        int(trace_cap), _ptr(nt))
+    return dict(K=int(K[0]), params=prm, lnL=float(lnL[0]), iters=int(it[0]), aa_steps=int(na[0]),
+                aa_resets=int(nr[0]), km_passes=int(km[0]), status=int(st[0]),
+                Ltrace=tr[: int(nt[0])].copy())
+
+
+def kmeans(vv, ah, picks, iters: int = 100):
+    """The oracle's K-means initialisation of one cell (``vv`` [N, D],
+    normalised weights ``ah``) from the given centre indices: (K, params
+    [K][P], passes)."""
+    lib = _load()
+    vv = _f64(vv)
+    N, D = vv.shape
+    ah = _f64(ah)
+    picks = np.ascontiguousarray(picks, dtype=np.int64)
+    K = picks.shape[0]
+    prm = np.zeros((K, P_of(D)))
+    Ko = np.zeros(1, np.int32); ps = np.zeros(1, np.int32)
+    rc = lib.oracle_kmeans(D, K, N, _ptr(vv), _ptr(ah), _ptr(picks), int(iters), _ptr(prm), _ptr(Ko), _ptr(ps))
+    if rc != 0:
+        raise ValueError("oracle_kmeans failed")
+    return int(Ko[0]), prm[: int(Ko[0])], int(ps[0])
+
+
+def aa_affine(A, b, x0, memory: int, iters: int):
+    """The oracle's Anderson iteration on G(x) = A x + b: (final iterate,
+    residual norm ||G(x_i) - x_i|| per step)."""
+    lib = _load()
+    A = _f64(A); b = _f64(b); x0 = _f64(x0)
+    n = b.shape[0]
+    x = np.zeros(n); res = np.zeros(iters)
+    rc = lib.oracle_aa_affine(n, _ptr(A), _ptr(b), _ptr(x0), int(memory), int(iters), _ptr(x), _ptr(res))
+    if rc != 0:
+        raise ValueError("oracle_aa_affine failed")
+    return x, res
 
 
 def penalised_L(D: int, prm, vv, ah) -> float:

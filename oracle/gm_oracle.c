@@ -897,3 +897,523 @@ int oracle_max_threads(void) {
   return 1;
 #endif
 }
+
+/* ======================================================================== */
+/* Standard (non-adaptive) EM, K-means initialisation and Anderson          */
+/* acceleration: the acceleration study of Sec. 4 ("On the acceleration of   */
+/* convergence of the EM-GM nonlinear algorithm"), where the paper applies   */
+/* both to the non-adaptive EM-GM algorithm.                                 */
+/* ======================================================================== */
+
+#define AA_MAXM 8
+#define AA_MAXN (OR_MAXK * 10)
+/* Reading: AA starts once the relative change of L over an EM iteration is
+ * at most this (the paper does not say when; extrapolating the first,
+ * large EM moves from a random start led to poorer stationary points) */
+#define AA_START 1e-4
+
+/* Anderson acceleration of a fixed-point map G (Walker & Ni 2011, the
+ * "type II" form): with f_i = G(x_i) - x_i and the differences of the last
+ * m pairs (f, G), gamma minimises || f_i - dF gamma ||_2 and
+ * x_{i+1} = G(x_i) - dG gamma. */
+typedef struct aa_state {
+  int n, m, h, have_prev;
+  double dF[AA_MAXM][AA_MAXN], dG[AA_MAXM][AA_MAXN];
+  double f_prev[AA_MAXN], g_prev[AA_MAXN];
+} aa_state;
+
+static void aa_init(aa_state *s, int n, int m) {
+  s->n = n; s->m = m < AA_MAXM ? m : AA_MAXM; s->h = 0; s->have_prev = 0;
+}
+
+/* forgets the stored differences; the last (f, G) pair stays the previous one */
+static void aa_clear(aa_state *s) { s->h = 0; }
+
+/* One step: the new difference joins the history (oldest dropped beyond m);
+ * gamma from the normal equations (dF^T dF + 1e-12 max_a (dF^T dF)_aa I)
+ * gamma = dF^T f by Cholesky (Reading: the paper does not say how the
+ * least-squares problem is solved).  Returns 1 and out = G - dG gamma, or 0
+ * and out = G when there is no history or a pivot is not positive. */
+static int aa_step(aa_state *s, const double *x, const double *g, double *out) {
+  const int n = s->n;
+  double f[AA_MAXN];
+  for (int i = 0; i < n; ++i) f[i] = g[i] - x[i];
+  if (s->m > 0 && s->have_prev) {
+    if (s->h == s->m) {
+      for (int c = 1; c < s->m; ++c) {
+        memcpy(s->dF[c - 1], s->dF[c], sizeof(double) * (size_t)n);
+        memcpy(s->dG[c - 1], s->dG[c], sizeof(double) * (size_t)n);
+      }
+      s->h--;
+    }
+    for (int i = 0; i < n; ++i) {
+      s->dF[s->h][i] = f[i] - s->f_prev[i];
+      s->dG[s->h][i] = g[i] - s->g_prev[i];
+    }
+    s->h++;
+  }
+  memcpy(s->f_prev, f, sizeof(double) * (size_t)n);
+  memcpy(s->g_prev, g, sizeof(double) * (size_t)n);
+  s->have_prev = 1;
+  const int h = s->h;
+  memcpy(out, g, sizeof(double) * (size_t)n);
+  if (h == 0) return 0;
+  double A[AA_MAXM][AA_MAXM], b[AA_MAXM], Lm[AA_MAXM][AA_MAXM], z[AA_MAXM], gam[AA_MAXM];
+  double dmax = 0.0;
+  for (int a = 0; a < h; ++a) {
+    for (int c = 0; c <= a; ++c) {
+      double t = 0.0;
+      for (int i = 0; i < n; ++i) t += s->dF[a][i] * s->dF[c][i];
+      A[a][c] = A[c][a] = t;
+    }
+    double t = 0.0;
+    for (int i = 0; i < n; ++i) t += s->dF[a][i] * f[i];
+    b[a] = t;
+    if (A[a][a] > dmax) dmax = A[a][a];
+  }
+  if (!(dmax > 0.0)) return 0;
+  for (int a = 0; a < h; ++a) A[a][a] += 1e-12 * dmax;
+  for (int a = 0; a < h; ++a)
+    for (int c = 0; c <= a; ++c) {
+      double t = A[a][c];
+      for (int e = 0; e < c; ++e) t -= Lm[a][e] * Lm[c][e];
+      if (a == c) {
+        if (!(t > 0.0)) return 0;
+        Lm[a][a] = sqrt(t);
+      } else {
+        Lm[a][c] = t / Lm[c][c];
+      }
+    }
+  for (int a = 0; a < h; ++a) {
+    double t = b[a];
+    for (int e = 0; e < a; ++e) t -= Lm[a][e] * z[e];
+    z[a] = t / Lm[a][a];
+  }
+  for (int a = h - 1; a >= 0; --a) {
+    double t = z[a];
+    for (int e = a + 1; e < h; ++e) t -= Lm[e][a] * gam[e];
+    gam[a] = t / Lm[a][a];
+  }
+  for (int i = 0; i < n; ++i) {
+    double t = g[i];
+    for (int c = 0; c < h; ++c) t -= s->dG[c][i] * gam[c];
+    out[i] = t;
+  }
+  return 1;
+}
+
+/* The accelerated unknowns (Sec. 4): per component omega_k, mu_k and the
+ * second-moment matrix M2_k = Sigma_k + mu_k mu_k^T (upper triangle), which
+ * is linear in the mixture; Reading: in the cell's whitened coordinates
+ * (v - mean) / sd per dimension, so that all unknowns have unit scale. */
+static void theta_pack(int D, int K, const comp *cs, const double *mean, const double *sd,
+                       double *th) {
+  int t = 0;
+  for (int k = 0; k < K; ++k) {
+    double mw[OR_MAXD];
+    th[t++] = cs[k].w;
+    for (int d = 0; d < D; ++d) th[t++] = mw[d] = (cs[k].mu[d] - mean[d]) / sd[d];
+    for (int i = 0; i < D; ++i)
+      for (int j = i; j < D; ++j) th[t++] = cs[k].S[i][j] / (sd[i] * sd[j]) + mw[i] * mw[j];
+  }
+}
+
+/* back to a mixture (original coordinates); 0 if a weight is not positive
+ * or a covariance M2 - mu mu^T fails the Cholesky floor (in the whitened and
+ * in the original coordinates) */
+static int theta_unpack(int D, int K, const double *th, const double *mean, const double *sd,
+                        comp *cs) {
+  int t = 0;
+  for (int k = 0; k < K; ++k) {
+    double mw[OR_MAXD], Sw[OR_MAXD][OR_MAXD], Lw[OR_MAXD][OR_MAXD], ldw;
+    cs[k].w = th[t++];
+    for (int d = 0; d < D; ++d) mw[d] = th[t++];
+    for (int i = 0; i < D; ++i)
+      for (int j = i; j < D; ++j) { Sw[i][j] = Sw[j][i] = th[t++] - mw[i] * mw[j]; }
+    if (!(cs[k].w > 0.0)) return 0;
+    if (!chol_floor(D, Sw, mw, Lw, &ldw)) return 0;
+    for (int d = 0; d < D; ++d) cs[k].mu[d] = mean[d] + sd[d] * mw[d];
+    for (int i = 0; i < D; ++i)
+      for (int j = 0; j < D; ++j) cs[k].S[i][j] = Sw[i][j] * sd[i] * sd[j];
+    if (!chol_floor(D, cs[k].S, cs[k].mu, cs[k].Lc, &cs[k].logdet)) return 0;
+  }
+  return 1;
+}
+
+/* Unpenalised log-likelihood sum_p alpha_p ln sum_k omega_k f_k(v_p) */
+static double plain_L(int D, int K, const comp *cs, int64_t N, const double *vv, const double *ah) {
+  double lf[OR_MAXK], s = 0.0;
+  for (int64_t p = 0; p < N; ++p) s += ah[p] * log_mix(D, K, cs, vv + p * D, lf);
+  return s;
+}
+
+/* One standard EM step: the E-step (eq. responsibility) for all components
+ * with the same parameters, then eqs. (muk), (sigmak) and omega_k = N_k / N
+ * (eq. omegak-mle).  Returns L at the input parameters; out receives the
+ * update.  Reading: a component that owns nothing or whose covariance fails
+ * the floor is dropped (the count only shrinks; status COV_NOT_PD for the
+ * floor). */
+static double std_em_step(int D, int K, const comp *cs, int64_t N, const double *vv,
+                          const double *ah, double *gam, comp *out, int *Kout, uint32_t *status) {
+  double lf[OR_MAXK], Nk[OR_MAXK] = {0}, L = 0.0;
+  const double Nd = (double)N;
+  for (int64_t p = 0; p < N; ++p) {
+    double lm = log_mix(D, K, cs, vv + p * D, lf);
+    L += ah[p] * lm;
+    for (int k = 0; k < K; ++k) {
+      gam[p * OR_MAXK + k] = ah[p] * exp(lf[k] - lm);
+      Nk[k] += gam[p * OR_MAXK + k];
+    }
+  }
+  int Ko = 0;
+  for (int k = 0; k < K; ++k) {
+    if (!(Nk[k] > 0.0)) continue;
+    comp nc;
+    for (int d = 0; d < D; ++d) {
+      double s = 0.0;
+      for (int64_t p = 0; p < N; ++p) s += gam[p * OR_MAXK + k] * vv[p * D + d];
+      nc.mu[d] = s / Nk[k];
+    }
+    for (int i = 0; i < D; ++i)
+      for (int j = 0; j < D; ++j) {
+        double s = 0.0;
+        for (int64_t p = 0; p < N; ++p)
+          s += gam[p * OR_MAXK + k] * (vv[p * D + i] - nc.mu[i]) * (vv[p * D + j] - nc.mu[j]);
+        nc.S[i][j] = s / Nk[k];
+      }
+    nc.w = Nk[k] / Nd;
+    if (!chol_floor(D, nc.S, nc.mu, nc.Lc, &nc.logdet)) { *status |= ST_COV_NOT_PD; continue; }
+    out[Ko++] = nc;
+  }
+  *Kout = Ko;
+  return L;
+}
+
+/* K-means (Lloyd) initialisation in the whitened coordinates
+ * y = (v - mean) * (1 / sd), stored in FP32; the centres start at the picked
+ * particles.  Each pass assigns every particle to the nearest centre
+ * (squared distance in FP32, fmaf in dimension order, the lowest index on
+ * ties -- Reading: the decision is taken in the precision the GPU kernel
+ * uses), stops when no assignment changed, else moves every centre to the
+ * alpha-weighted mean of its particles (an empty cluster keeps its centre);
+ * at most iters passes.  The mixture: one component per non-empty cluster,
+ * weight = its share of the normalised weights, mean and biased covariance
+ * of its particles (the total covariance if that fails the floor).
+ * Returns the number of components. */
+static int kmeans_init(int D, int K, int64_t N, const double *vv, const double *ah,
+                       const double *mean, const double *sd, const double cov[OR_MAXD][OR_MAXD],
+                       const int64_t *picks, int iters, comp *cs, int *passes) {
+  double isd[OR_MAXD];
+  for (int d = 0; d < D; ++d) isd[d] = 1.0 / sd[d];
+  float *y = (float *)malloc(sizeof(float) * (size_t)N * D);
+  int *as = (int *)malloc(sizeof(int) * (size_t)N);
+  for (int64_t p = 0; p < N; ++p)
+    for (int d = 0; d < D; ++d) y[p * D + d] = (float)((vv[p * D + d] - mean[d]) * isd[d]);
+  float c[OR_MAXK][OR_MAXD];
+  for (int k = 0; k < K; ++k)
+    for (int d = 0; d < D; ++d) c[k][d] = y[picks[k] * D + d];
+  int it;
+  for (it = 0; it < iters; ++it) {
+    int64_t changed = 0;
+    for (int64_t p = 0; p < N; ++p) {
+      int best = 0;
+      float bd = 0.0f;
+      for (int k = 0; k < K; ++k) {
+        const float d0 = y[p * D] - c[k][0];
+        float dist = d0 * d0;
+        if (D == 3) {
+          const float d1 = y[p * D + 1] - c[k][1], d2 = y[p * D + 2] - c[k][2];
+          dist = fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
+        }
+        if (k == 0 || dist < bd) { bd = dist; best = k; }
+      }
+      if (it == 0 || as[p] != best) ++changed;
+      as[p] = best;
+    }
+    if (it > 0 && changed == 0) break;
+    double A[OR_MAXK] = {0}, S[OR_MAXK][OR_MAXD] = {{0}};
+    for (int64_t p = 0; p < N; ++p) {
+      A[as[p]] += ah[p];
+      for (int d = 0; d < D; ++d) S[as[p]][d] += ah[p] * (double)y[p * D + d];
+    }
+    for (int k = 0; k < K; ++k)
+      if (A[k] > 0.0)
+        for (int d = 0; d < D; ++d) c[k][d] = (float)(S[k][d] / A[k]);
+  }
+  *passes = it < iters ? it + 1 : iters;
+  int Ko = 0;
+  for (int k = 0; k < K; ++k) {
+    double A = 0.0;
+    comp nc;
+    memset(&nc, 0, sizeof(nc));
+    for (int64_t p = 0; p < N; ++p)
+      if (as[p] == k) {
+        A += ah[p];
+        for (int d = 0; d < D; ++d) nc.mu[d] += ah[p] * vv[p * D + d];
+      }
+    if (!(A > 0.0)) continue;
+    for (int d = 0; d < D; ++d) nc.mu[d] /= A;
+    for (int64_t p = 0; p < N; ++p)
+      if (as[p] == k)
+        for (int i = 0; i < D; ++i)
+          for (int j = 0; j < D; ++j)
+            nc.S[i][j] += ah[p] * (vv[p * D + i] - nc.mu[i]) * (vv[p * D + j] - nc.mu[j]);
+    for (int i = 0; i < D; ++i)
+      for (int j = 0; j < D; ++j) nc.S[i][j] /= A;
+    nc.w = A / (double)N;
+    if (!chol_floor(D, nc.S, nc.mu, nc.Lc, &nc.logdet)) {
+      memcpy(nc.S, cov, sizeof(double) * OR_MAXD * OR_MAXD);
+      chol_floor(D, nc.S, nc.mu, nc.Lc, &nc.logdet);
+    }
+    cs[Ko++] = nc;
+  }
+  free(y);
+  free(as);
+  return Ko;
+}
+
+typedef struct std_out {
+  int32_t K, iters, aa_steps, aa_resets, km_passes;
+  double W, lnL;
+  uint32_t status;
+} std_out;
+
+/* Standard EM of one cell.  init: 0 = the paper's random particles (the
+ * same Philox picks as the adaptive EM, K = min(Kmax, N), total
+ * covariance, equal weights), 1 = K-means from those picks.  aa_m: Anderson
+ * memory (0 = plain EM).  Iteration i evaluates g_i = G(theta_i), one
+ * standard EM step, whose E-step also gives L(theta_i); EM stops when
+ * |L_i - L_{i-1}| <= tol |L_{i-1}| (or after max_sweeps evaluations), and
+ * the output is that last g: a standard EM step after the accelerated
+ * iteration, which makes the moments exact (Sec. 4, as for the penalised
+ * EM's final step).  With AA, from the first i with |L_i - L_{i-1}| <=
+ * AA_START |L_{i-1}| on, theta_{i+1} is the Anderson extrapolation, unless it has a non-positive
+ * weight or an indefinite covariance: then the history is cleared and
+ * theta_{i+1} = g_i (Sec. 4); a dropped component restarts AA.  Ltrace:
+ * L(theta_i) per evaluation. */
+static void std_cell(const oracle_cfg *cfg, int64_t cell, int64_t N, const double *vv,
+                     const double *alpha, int init, int aa_m, int km_iters, double *prm_out,
+                     std_out *o, double *Ltrace, int trace_cap, int *ntrace) {
+  const int D = cfg->D, P = P_of(D);
+  memset(o, 0, sizeof(*o));
+  memset(prm_out, 0, sizeof(double) * (size_t)cfg->Kmax * P);
+  if (ntrace) *ntrace = 0;
+  if (N == 0) { o->status = ST_EMPTY; return; }
+  double W = 0.0;
+  for (int64_t p = 0; p < N; ++p) W += alpha[p];
+  o->W = W;
+  if (!(W > 0.0)) { o->status = ST_EMPTY | ST_DEGENERATE; return; }
+  const double Nd = (double)N;
+  double *ah = (double *)malloc(sizeof(double) * (size_t)N);
+  double *gam = (double *)malloc(sizeof(double) * (size_t)N * OR_MAXK);
+  for (int64_t p = 0; p < N; ++p) ah[p] = alpha[p] * Nd / W;
+  if (N <= 10) o->status |= ST_TOO_FEW;
+  double mean[OR_MAXD] = {0}, cov[OR_MAXD][OR_MAXD] = {{0}}, sd[OR_MAXD];
+  for (int64_t p = 0; p < N; ++p)
+    for (int d = 0; d < D; ++d) mean[d] += ah[p] * vv[p * D + d];
+  for (int d = 0; d < D; ++d) mean[d] /= Nd;
+  for (int64_t p = 0; p < N; ++p)
+    for (int i = 0; i < D; ++i)
+      for (int j = 0; j < D; ++j)
+        cov[i][j] += ah[p] * (vv[p * D + i] - mean[i]) * (vv[p * D + j] - mean[j]);
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < D; ++j) cov[i][j] /= Nd;
+  comp cs[OR_MAXK], g[OR_MAXK];
+  {
+    double Ltmp[OR_MAXD][OR_MAXD], ldtmp;
+    if (!chol_floor(D, cov, mean, Ltmp, &ldtmp)) {
+      cs[0].w = 1.0;
+      for (int d = 0; d < D; ++d) cs[0].mu[d] = mean[d];
+      memcpy(cs[0].S, cov, sizeof(cov));
+      store_params(D, cfg->Kmax, 1, cs, prm_out);
+      o->K = 1; o->status |= ST_DEGENERATE | ST_COV_NOT_PD;
+      free(ah); free(gam);
+      return;
+    }
+  }
+  for (int d = 0; d < D; ++d) sd[d] = sqrt(cov[d][d]);
+  /* the initial picks: the adaptive EM's procedure with K = min(Kmax, N) */
+  int K = cfg->Kmax < N ? cfg->Kmax : (int)N;
+  int64_t picks[OR_MAXK];
+  {
+    int got = 0;
+    for (uint32_t t = 0; got < K; ++t) {
+      int64_t idx;
+      if (t < 100000u) {
+        uint32_t r[4];
+        philox_draw(cfg->seed, t, TAG_INIT, cell, r);
+        double u = oracle_uniform52(r[0], r[1]);
+        idx = (int64_t)floor(u * Nd);
+        if (idx >= N) idx = N - 1;
+      } else {
+        idx = 0;
+        for (;;) {
+          int used = 0;
+          for (int m = 0; m < got; ++m) used |= (picks[m] == idx);
+          if (!used) break;
+          ++idx;
+        }
+      }
+      int dup = 0;
+      for (int m = 0; m < got; ++m) dup |= (picks[m] == idx);
+      if (!dup) picks[got++] = idx;
+    }
+  }
+  if (init == 1) {
+    int passes = 0;
+    K = kmeans_init(D, K, N, vv, ah, mean, sd, cov, picks, km_iters > 0 ? km_iters : 100, cs, &passes);
+    o->km_passes = passes;
+  } else {
+    for (int k = 0; k < K; ++k) {
+      cs[k].w = 1.0 / K;
+      for (int d = 0; d < D; ++d) cs[k].mu[d] = vv[picks[k] * D + d];
+      memcpy(cs[k].S, cov, sizeof(cov));
+      chol_floor(D, cs[k].S, cs[k].mu, cs[k].Lc, &cs[k].logdet);
+    }
+  }
+  aa_state *aa = (aa_state *)malloc(sizeof(aa_state));
+  aa_init(aa, K * P, aa_m);
+  double th[AA_MAXN], tg[AA_MAXN], tn[AA_MAXN];
+  double Lprev = 0.0;
+  int converged = 0, it, Kg = K, aa_on = 0;
+  for (it = 0; it < cfg->max_sweeps; ++it) {
+    const double L = std_em_step(D, K, cs, N, vv, ah, gam, g, &Kg, &o->status);
+    if (Ltrace && *ntrace < trace_cap) Ltrace[(*ntrace)++] = L;
+    if (it > 0 && fabs(L - Lprev) <= cfg->tol * fabs(Lprev)) { converged = 1; break; }
+    if (!aa_on && it > 0 && fabs(L - Lprev) <= AA_START * fabs(Lprev)) aa_on = 1;
+    Lprev = L;
+    if (Kg < K || aa_m == 0 || !aa_on) { /* a dropped component restarts AA */
+      if (Kg < K) aa_init(aa, Kg * P, aa_m);
+      K = Kg;
+      memcpy(cs, g, sizeof(comp) * (size_t)K);
+      continue;
+    }
+    theta_pack(D, K, cs, mean, sd, th);
+    theta_pack(D, K, g, mean, sd, tg);
+    comp cand[OR_MAXK];
+    if (aa_step(aa, th, tg, tn) && theta_unpack(D, K, tn, mean, sd, cand)) {
+      renormalise(K, cand);
+      memcpy(cs, cand, sizeof(comp) * (size_t)K);
+      o->aa_steps++;
+    } else {
+      if (aa->h > 0) { aa_clear(aa); o->aa_resets++; }
+      memcpy(cs, g, sizeof(comp) * (size_t)K);
+    }
+  }
+  if (!converged) { it = cfg->max_sweeps - 1; o->status |= ST_EM_MAXSWEEPS; }
+  K = Kg;
+  o->iters = it + 1;
+  o->K = K;
+  o->lnL = plain_L(D, K, g, N, vv, ah);
+  store_params(D, cfg->Kmax, K, g, prm_out);
+  free(aa);
+  free(ah);
+  free(gam);
+}
+
+/* Exported: standard EM of a batch of cells (layout as oracle_compress);
+ * iters/aa_steps/aa_resets/km_passes per cell (each may be NULL). */
+int oracle_standard(const oracle_cfg *cfg, int64_t C, const int64_t *cell_off, const double *x,
+                    const double *v, const double *alpha, int init, int aa_m, int km_iters,
+                    int32_t *K_out, double *params_out, double *W_out, double *rho_target_out,
+                    double *lnL_out, int32_t *iters_out, int32_t *aa_steps_out,
+                    int32_t *aa_resets_out, int32_t *km_out, uint32_t *status_out,
+                    const int64_t *cell_ids, int nthreads) {
+  const int D = cfg->D;
+  if (D != 1 && D != 3) return -1;
+  if (cfg->Kmax < 1 || cfg->Kmax > OR_MAXK || aa_m < 0) return -1;
+  const int64_t Ntot = cell_off[C];
+  const size_t P = (size_t)P_of(D);
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int64_t j = 0; j < C; ++j) {
+    int64_t n = cell_off[j + 1] - cell_off[j];
+    double *vv = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * D);
+    for (int64_t p = 0; p < n; ++p)
+      for (int d = 0; d < D; ++d) vv[p * D + d] = v[(int64_t)d * Ntot + cell_off[j] + p];
+    std_out o;
+    std_cell(cfg, cell_ids ? cell_ids[j] : j, n, vv, alpha + cell_off[j], init, aa_m, km_iters,
+             params_out + (size_t)j * cfg->Kmax * P, &o, NULL, 0, NULL);
+    K_out[j] = o.K; W_out[j] = o.W; lnL_out[j] = o.lnL; status_out[j] = o.status;
+    if (iters_out) iters_out[j] = o.iters;
+    if (aa_steps_out) aa_steps_out[j] = o.aa_steps;
+    if (aa_resets_out) aa_resets_out[j] = o.aa_resets;
+    if (km_out) km_out[j] = o.km_passes;
+    free(vv);
+  }
+  if (rho_target_out) deposit(cfg, C, cell_off, x, alpha, rho_target_out);
+  return 0;
+}
+
+/* Exported: standard EM of one cell with the trace of L(theta_i) */
+int oracle_std_cell(const oracle_cfg *cfg, int64_t cell, int64_t N, const double *vv /*[N][D]*/,
+                    const double *alpha, int init, int aa_m, int km_iters, double *params_out,
+                    int32_t *K_out, double *lnL_out, int32_t *iters_out, int32_t *aa_steps_out,
+                    int32_t *aa_resets_out, int32_t *km_out, uint32_t *status_out, double *Ltrace,
+                    int trace_cap, int32_t *ntrace) {
+  std_out o;
+  int nt = 0;
+  std_cell(cfg, cell, N, vv, alpha, init, aa_m, km_iters, params_out, &o, Ltrace, trace_cap, &nt);
+  *K_out = o.K; *lnL_out = o.lnL; *iters_out = o.iters; *aa_steps_out = o.aa_steps;
+  *aa_resets_out = o.aa_resets; *km_out = o.km_passes; *status_out = o.status;
+  if (ntrace) *ntrace = nt;
+  return 0;
+}
+
+/* Exported: the Anderson iteration above on the affine map G(x) = A x + b
+ * (n <= AA_MAXN, row-major A), from x0 for iters steps; writes the iterate
+ * and the residual norm ||G(x_i) - x_i|| per step.  For a test of the
+ * extrapolation itself. */
+int oracle_aa_affine(int n, const double *A, const double *b, const double *x0, int m, int iters,
+                     double *x_out, double *res_trace) {
+  if (n < 1 || n > AA_MAXN) return -1;
+  aa_state *s = (aa_state *)malloc(sizeof(aa_state));
+  aa_init(s, n, m);
+  double x[AA_MAXN], g[AA_MAXN], xn[AA_MAXN];
+  memcpy(x, x0, sizeof(double) * (size_t)n);
+  for (int it = 0; it < iters; ++it) {
+    double r = 0.0;
+    for (int i = 0; i < n; ++i) {
+      double t = b[i];
+      for (int j = 0; j < n; ++j) t += A[i * n + j] * x[j];
+      g[i] = t;
+      r += (t - x[i]) * (t - x[i]);
+    }
+    res_trace[it] = sqrt(r);
+    aa_step(s, x, g, xn);
+    memcpy(x, xn, sizeof(double) * (size_t)n);
+  }
+  memcpy(x_out, x, sizeof(double) * (size_t)n);
+  free(s);
+  return 0;
+}
+
+/* Exported: the K-means initialisation alone on one cell ([N][D]), from the
+ * given initial centre indices; normalised weights ah (sum N) */
+int oracle_kmeans(int D, int K, int64_t N, const double *vv, const double *ah,
+                  const int64_t *picks, int iters, double *params_out, int32_t *K_out,
+                  int32_t *passes_out) {
+  if (D != 1 && D != 3) return -1;
+  if (K < 1 || K > OR_MAXK || N < 1) return -1;
+  const double Nd = (double)N;
+  double mean[OR_MAXD] = {0}, cov[OR_MAXD][OR_MAXD] = {{0}}, sd[OR_MAXD];
+  for (int64_t p = 0; p < N; ++p)
+    for (int d = 0; d < D; ++d) mean[d] += ah[p] * vv[p * D + d];
+  for (int d = 0; d < D; ++d) mean[d] /= Nd;
+  for (int64_t p = 0; p < N; ++p)
+    for (int i = 0; i < D; ++i)
+      for (int j = 0; j < D; ++j)
+        cov[i][j] += ah[p] * (vv[p * D + i] - mean[i]) * (vv[p * D + j] - mean[j]);
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < D; ++j) cov[i][j] /= Nd;
+  for (int d = 0; d < D; ++d) sd[d] = sqrt(cov[d][d]);
+  comp cs[OR_MAXK];
+  int passes = 0;
+  const int Ko = kmeans_init(D, K, N, vv, ah, mean, sd, cov, picks, iters, cs, &passes);
+  store_params(D, K, Ko, cs, params_out);
+  *K_out = Ko;
+  *passes_out = passes;
+  return 0;
+}
