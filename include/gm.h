@@ -295,6 +295,67 @@ int gm_mlp_decode(const gm_config* cfg, int64_t C, const float* out, int32_t O,
                   double* init_params, void* stream);
 
 /*
+ * gm_compress_standard -- standard (non-adaptive) EM with optional K-means
+ * initialisation and Anderson acceleration: the acceleration study of
+ * Sec. 4, where the paper applies both to the non-adaptive EM-GM algorithm
+ * (the adaptive, penalised EM of gm_compress is the paper's main method).
+ *
+ * K = min(Kmax, N) components start at the paper's random particles (the
+ * same Philox picks as gm_compress) with the total covariance and equal
+ * weights, or (opts->init = 1) at a K-means partition grown from those
+ * picks: Lloyd passes in the cell's whitened coordinates until no
+ * assignment changes (at most opts->kmeans_iters, 0 = 100), one component
+ * per non-empty cluster with its weight share, mean and covariance (the
+ * total covariance if that fails the Cholesky floor).  Each iteration is
+ * one standard EM step -- the E-step of all components with the same
+ * parameters, then eqs. (muk), (sigmak) and omega_k = N_k / N (eq.
+ * omegak-mle); it stops when the unpenalised log-likelihood
+ * sum_p alpha_p ln sum_k omega_k f_k(v_p) changes by at most cfg->tol
+ * (relative), or after cfg->max_sweeps steps (GM_ST_EM_MAXSWEEPS).  With
+ * opts->aa_memory = m > 0 (at most 8), once that relative change is at
+ * most 1e-4 the next iterate is the Anderson extrapolation of the last m
+ * steps on (omega_k, mu_k, M2_k = Sigma_k + mu_k mu_k^T) in whitened
+ * coordinates, unless it has a non-positive weight or an indefinite
+ * covariance, in which case the history is cleared and the plain EM step
+ * is taken.  A component that owns nothing or whose covariance fails the
+ * floor is dropped.  The output is one more standard EM step, in FP64,
+ * which makes the mixture's mass, mean and covariance the cell's weighted
+ * sample moments; lnL_out is the unpenalised log-likelihood of the output.
+ *
+ * Arguments as gm_compress (cfg->threads_per_cell and cfg->precision are
+ * not used; cfg->smem_particles sets the shared tile); iters_out [C]: EM
+ * steps evaluated; aa_steps_out, aa_resets_out: extrapolations taken and
+ * history resets; km_passes_out: Lloyd passes (each of these may be NULL).
+ */
+typedef struct gm_std_opts {
+  int32_t init;         /* 0 = random particles (Sec. 2.3), 1 = K-means */
+  int32_t aa_memory;    /* Anderson memory m, 0 = plain EM, at most 8 */
+  int32_t kmeans_iters; /* cap on Lloyd passes, 0 = 100 */
+  int32_t reserved;     /* must be 0 */
+} gm_std_opts;
+int gm_compress_standard(const gm_config* cfg, const gm_std_opts* opts, int64_t C,
+                         int64_t n_particles, const int64_t* cell_off, const double* x,
+                         const void* v, int32_t v_is_f64, const double* alpha, int32_t* K_out,
+                         double* params_out, double* W_out, double* rho_target_out,
+                         double* lnL_out, int32_t* iters_out, int32_t* aa_steps_out,
+                         int32_t* aa_resets_out, int32_t* km_passes_out, uint32_t* status_out,
+                         void* stream);
+
+/*
+ * gm_anderson_affine -- the Anderson extrapolation of gm_compress_standard
+ * (Sec. 4), run by itself on the affine map G(x) = A x + b: iters steps
+ * from x0 with memory m (0..8), n <= 160 unknowns.  A [n][n] row-major, b,
+ * x0 [n] in; x_out [n] the last iterate, res_out [iters] the residual norm
+ * ||G(x_i) - x_i|| of every step (device arrays, FP64).  It exists to check
+ * the extrapolation's arithmetic apart from the EM map (on a linear map
+ * Anderson acceleration with m >= n reaches the fixed point in about n + 1
+ * steps).  GM_ERR_ARG for sizes out of range or NULL pointers.
+ */
+int gm_anderson_affine(int32_t n, const double* A, const double* b, const double* x0,
+                       int32_t memory, int32_t iters, double* x_out, double* res_out,
+                       void* stream);
+
+/*
  * Pipeline capture into a CUDA graph.  The paper has no counterpart: this
  * is how a caller replays a fixed compress / reconstruct (and learned
  * initialisation) pipeline with one launch.

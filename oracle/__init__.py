@@ -77,7 +77,7 @@ def _load():
             lib.oracle_standard.argtypes = ([P, ct.c_int64] + [P] * 4 + [ct.c_int] * 3 + [P] * 11
                                             + [ct.c_int])
             lib.oracle_std_cell.argtypes = ([P, ct.c_int64, ct.c_int64, P, P] + [ct.c_int] * 3
-                                            + [P] * 9 + [ct.c_int, P])
+                                            + [P] * 9 + [ct.c_int, P, P, ct.c_int])
             lib.oracle_aa_affine.argtypes = [ct.c_int, P, P, P, ct.c_int, ct.c_int, P, P]
             lib.oracle_kmeans.argtypes = [ct.c_int, ct.c_int, ct.c_int64, P, P, P, ct.c_int, P, P, P]
             _lib = lib
@@ -214,8 +214,9 @@ def standard(params: dict, cell_off, x, v, alpha, init: int = 0, aa_memory: int 
 
 
 def std_cell(params: dict, vv, alpha, cell: int = 0, init: int = 0, aa_memory: int = 0,
-             kmeans_iters: int = 0, trace_cap: int = 0) -> dict:
-    """Standard EM of one cell (``vv`` [N, D]) with the trace of L(theta_i)."""
+             kmeans_iters: int = 0, trace_cap: int = 0, init_params=None) -> dict:
+    """Standard EM of one cell (``vv`` [N, D]) with the trace of L(theta_i);
+    ``init_params`` [K][P] (with ``init`` = 2) continues from a given fit."""
     lib = _load()
     cfg = _cfg(params)
     vv = _f64(vv).reshape(-1, cfg.D)
@@ -229,7 +230,9 @@ def std_cell(params: dict, vv, alpha, cell: int = 0, init: int = 0, aa_memory: i
     lib.oracle_std_cell(ct.byref(cfg), int(cell), N, _ptr(vv), _ptr(alpha), int(init),
                         int(aa_memory), int(kmeans_iters), _ptr(prm), _ptr(K), _ptr(lnL), _ptr(it),
                         _ptr(na), _ptr(nr), _ptr(km), _ptr(st), _ptr(tr) if trace_cap else None,
-                        int(trace_cap), _ptr(nt))
+                        int(trace_cap), _ptr(nt),
+                        _ptr(None if init_params is None else _f64(init_params)),
+                        0 if init_params is None else int(np.asarray(init_params).shape[0]))
     return dict(K=int(K[0]), params=prm, lnL=float(lnL[0]), iters=int(it[0]), aa_steps=int(na[0]),
                 aa_resets=int(nr[0]), km_passes=int(km[0]), status=int(st[0]),
                 Ltrace=tr[: int(nt[0])].copy())

@@ -1093,10 +1093,11 @@ static double std_em_step(int D, int K, const comp *cs, int64_t N, const double 
  * y = (v - mean) * (1 / sd), stored in FP32; the centres start at the picked
  * particles.  Each pass assigns every particle to the nearest centre
  * (squared distance in FP32, fmaf in dimension order, the lowest index on
- * ties -- Reading: the decision is taken in the precision the GPU kernel
- * uses), stops when no assignment changed, else moves every centre to the
- * alpha-weighted mean of its particles (an empty cluster keeps its centre);
- * at most iters passes.  The mixture: one component per non-empty cluster,
+ * ties), stops when no assignment changed, else moves every centre to the
+ * weighted mean of its particles with the weights rounded to FP32 (sums in
+ * FP64, the centre rounded to FP32; an empty cluster keeps its centre); at
+ * most iters passes.  Reading: the assignment decisions are taken on the
+ * FP32 coordinates and weights the GPU kernel stages.  The mixture: one component per non-empty cluster,
  * weight = its share of the normalised weights, mean and biased covariance
  * of its particles (the total covariance if that fails the floor).
  * Returns the number of components. */
@@ -1133,8 +1134,9 @@ static int kmeans_init(int D, int K, int64_t N, const double *vv, const double *
     if (it > 0 && changed == 0) break;
     double A[OR_MAXK] = {0}, S[OR_MAXK][OR_MAXD] = {{0}};
     for (int64_t p = 0; p < N; ++p) {
-      A[as[p]] += ah[p];
-      for (int d = 0; d < D; ++d) S[as[p]][d] += ah[p] * (double)y[p * D + d];
+      const double af = (double)(float)ah[p];
+      A[as[p]] += af;
+      for (int d = 0; d < D; ++d) S[as[p]][d] += af * (double)y[p * D + d];
     }
     for (int k = 0; k < K; ++k)
       if (A[k] > 0.0)
@@ -1193,7 +1195,8 @@ typedef struct std_out {
  * L(theta_i) per evaluation. */
 static void std_cell(const oracle_cfg *cfg, int64_t cell, int64_t N, const double *vv,
                      const double *alpha, int init, int aa_m, int km_iters, double *prm_out,
-                     std_out *o, double *Ltrace, int trace_cap, int *ntrace) {
+                     std_out *o, double *Ltrace, int trace_cap, int *ntrace,
+                     const double *init_prm, int init_K) {
   const int D = cfg->D, P = P_of(D);
   memset(o, 0, sizeof(*o));
   memset(prm_out, 0, sizeof(double) * (size_t)cfg->Kmax * P);
@@ -1259,7 +1262,12 @@ static void std_cell(const oracle_cfg *cfg, int64_t cell, int64_t N, const doubl
       if (!dup) picks[got++] = idx;
     }
   }
-  if (init == 1) {
+  if (init == 2 && init_prm && init_K > 0) {
+    /* a supplied mixture (for tests: continue EM from a given fit) */
+    K = init_K < cfg->Kmax ? init_K : cfg->Kmax;
+    load_params(D, K, init_prm, cs);
+    for (int k = 0; k < K; ++k) chol_floor(D, cs[k].S, cs[k].mu, cs[k].Lc, &cs[k].logdet);
+  } else if (init == 1) {
     int passes = 0;
     K = kmeans_init(D, K, N, vv, ah, mean, sd, cov, picks, km_iters > 0 ? km_iters : 100, cs, &passes);
     o->km_passes = passes;
@@ -1335,7 +1343,7 @@ int oracle_standard(const oracle_cfg *cfg, int64_t C, const int64_t *cell_off, c
       for (int d = 0; d < D; ++d) vv[p * D + d] = v[(int64_t)d * Ntot + cell_off[j] + p];
     std_out o;
     std_cell(cfg, cell_ids ? cell_ids[j] : j, n, vv, alpha + cell_off[j], init, aa_m, km_iters,
-             params_out + (size_t)j * cfg->Kmax * P, &o, NULL, 0, NULL);
+             params_out + (size_t)j * cfg->Kmax * P, &o, NULL, 0, NULL, NULL, 0);
     K_out[j] = o.K; W_out[j] = o.W; lnL_out[j] = o.lnL; status_out[j] = o.status;
     if (iters_out) iters_out[j] = o.iters;
     if (aa_steps_out) aa_steps_out[j] = o.aa_steps;
@@ -1347,15 +1355,17 @@ int oracle_standard(const oracle_cfg *cfg, int64_t C, const int64_t *cell_off, c
   return 0;
 }
 
-/* Exported: standard EM of one cell with the trace of L(theta_i) */
+/* Exported: standard EM of one cell with the trace of L(theta_i); init = 2
+ * starts from the supplied mixture init_prm [init_K][P] */
 int oracle_std_cell(const oracle_cfg *cfg, int64_t cell, int64_t N, const double *vv /*[N][D]*/,
                     const double *alpha, int init, int aa_m, int km_iters, double *params_out,
                     int32_t *K_out, double *lnL_out, int32_t *iters_out, int32_t *aa_steps_out,
                     int32_t *aa_resets_out, int32_t *km_out, uint32_t *status_out, double *Ltrace,
-                    int trace_cap, int32_t *ntrace) {
+                    int trace_cap, int32_t *ntrace, const double *init_prm, int init_K) {
   std_out o;
   int nt = 0;
-  std_cell(cfg, cell, N, vv, alpha, init, aa_m, km_iters, params_out, &o, Ltrace, trace_cap, &nt);
+  std_cell(cfg, cell, N, vv, alpha, init, aa_m, km_iters, params_out, &o, Ltrace, trace_cap, &nt,
+           init_prm, init_K);
   *K_out = o.K; *lnL_out = o.lnL; *iters_out = o.iters; *aa_steps_out = o.aa_steps;
   *aa_resets_out = o.aa_resets; *km_out = o.km_passes; *status_out = o.status;
   if (ntrace) *ntrace = nt;

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "gm_kernels.cuh"
+#include "std_kernel.cuh"
 
 namespace gmcr {
 int em_blocks_per_sm_d1(int nt, int fp64_mstep, int v_f64, size_t smem);
@@ -302,6 +303,100 @@ int gm_compress(const gm_config* cfg, int64_t C, int64_t n_particles, const int6
   return compress_impl(cfg, C, n_particles, cell_off, x, v, v_is_f64, alpha, nullptr, nullptr,
                        K_out, params_out, W_out, rho_target_out, lnL_out, sweeps_out, kwork_out,
                        status_out, stream);
+}
+
+int gm_compress_standard(const gm_config* cfg, const gm_std_opts* opts, int64_t C,
+                         int64_t n_particles, const int64_t* cell_off, const double* x,
+                         const void* v, int32_t v_is_f64, const double* alpha, int32_t* K_out,
+                         double* params_out, double* W_out, double* rho_target_out,
+                         double* lnL_out, int32_t* iters_out, int32_t* aa_steps_out,
+                         int32_t* aa_resets_out, int32_t* km_passes_out, uint32_t* status_out,
+                         void* stream) {
+  g_err.clear();
+  int rc = check_cfg(cfg);
+  if (rc) return rc;
+  if (!opts) return fail(GM_ERR_ARG, "opts is NULL");
+  if (opts->init != 0 && opts->init != 1) return fail(GM_ERR_ARG, "opts->init must be 0 or 1");
+  if (opts->aa_memory < 0 || opts->aa_memory > gmcr::kStdMaxM)
+    return fail(GM_ERR_ARG, "opts->aa_memory must be in 0..%d", gmcr::kStdMaxM);
+  if (opts->kmeans_iters < 0) return fail(GM_ERR_ARG, "opts->kmeans_iters < 0");
+  if (C < 0 || C >= (int64_t)1 << 31) return fail(GM_ERR_ARG, "C out of range (%lld)", (long long)C);
+  if (n_particles < 0) return fail(GM_ERR_ARG, "n_particles < 0");
+  if (cfg->max_sweeps < 1) return fail(GM_ERR_ARG, "max_sweeps must be >= 1");
+  if (!(cfg->tol >= 0.0)) return fail(GM_ERR_ARG, "tol must be >= 0");
+  if (C == 0) return GM_OK;
+  if (!cell_off || !x || !v || !alpha || !K_out || !params_out || !W_out || !rho_target_out ||
+      !lnL_out || !status_out)
+    return fail(GM_ERR_ARG, "a required pointer is NULL");
+  int sms = 0;
+  if ((rc = check_device(&sms))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int D = cfg->D;
+  int cap = cfg->smem_particles > 0 ? cfg->smem_particles : (D == 1 ? 2560 : 3072);
+  cap &= ~3;
+  if (cap < 4) cap = 4;
+  const size_t smem = (size_t)cap * (D + 3) * sizeof(float);
+  if (smem > 160 * 1024) return fail(GM_ERR_ARG, "smem_particles too large (%d)", cap);
+
+  const size_t q_bytes = 256, part_bytes = align256((size_t)3 * C * sizeof(double));
+  const int64_t sstride = gmcr::scratch_stride(n_particles, C);
+  if ((int64_t)(D + 3) * sstride >= ((int64_t)1 << 31))
+    return fail(GM_ERR_ARG, "too many particles for one call (%lld)", (long long)n_particles);
+  const size_t scr_bytes = align256((size_t)sstride * (D + 3) * sizeof(float));
+  void* ws = nullptr;
+  if ((rc = ws_get(q_bytes + part_bytes + scr_bytes, &ws))) return rc;
+  char* wb = (char*)ws;
+  unsigned int* queue = (unsigned int*)wb;
+  double* part = (double*)(wb + q_bytes);
+  float* scratch = (float*)(wb + q_bytes + part_bytes);
+  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  gmcr::StdParams p;
+  p.C = C;
+  p.n = n_particles;
+  p.cell_off = cell_off;
+  p.v = v;
+  p.alpha = alpha;
+  p.K_out = K_out;
+  p.params_out = params_out;
+  p.W_out = W_out;
+  p.lnL_out = lnL_out;
+  p.iters_out = iters_out;
+  p.aa_steps_out = aa_steps_out;
+  p.aa_resets_out = aa_resets_out;
+  p.km_out = km_passes_out;
+  p.status_out = status_out;
+  p.scratch = scratch;
+  p.scratch_stride = sstride;
+  p.queue = queue;
+  p.Kmax = cfg->Kmax;
+  p.max_sweeps = cfg->max_sweeps;
+  p.cap = cap;
+  p.init = opts->init;
+  p.aa_m = opts->aa_memory;
+  p.km_iters = opts->kmeans_iters;
+  p.tol = cfg->tol;
+  p.seed = cfg->seed;
+  e = gmcr::launch_std(D, p, v_is_f64, smem, sms, s);
+  if (e != cudaSuccess) return cuda_fail(e, "standard EM kernel launch");
+  e = gmcr::launch_deposit(C, cell_off, x, alpha, cfg->L / (double)C, cfg->q, cfg->shape_order,
+                           part, rho_target_out, s);
+  if (e != cudaSuccess) return cuda_fail(e, "deposit launch");
+  return GM_OK;
+}
+
+int gm_anderson_affine(int32_t n, const double* A, const double* b, const double* x0,
+                       int32_t memory, int32_t iters, double* x_out, double* res_out,
+                       void* stream) {
+  g_err.clear();
+  if (n < 1 || n > gmcr::kMaxK * 10) return fail(GM_ERR_ARG, "n must be in 1..%d", gmcr::kMaxK * 10);
+  if (memory < 0 || memory > gmcr::kStdMaxM) return fail(GM_ERR_ARG, "memory must be in 0..%d", gmcr::kStdMaxM);
+  if (iters < 0) return fail(GM_ERR_ARG, "iters < 0");
+  if (!A || !b || !x0 || !x_out || (iters > 0 && !res_out)) return fail(GM_ERR_ARG, "a required pointer is NULL");
+  int rc = check_device(nullptr);
+  if (rc) return rc;
+  cudaError_t e = gmcr::launch_aa_affine(n, A, b, x0, memory, iters, x_out, res_out, (cudaStream_t)stream);
+  return e == cudaSuccess ? GM_OK : cuda_fail(e, "Anderson kernel launch");
 }
 
 int gm_compress_from(const gm_config* cfg, int64_t C, int64_t n_particles,

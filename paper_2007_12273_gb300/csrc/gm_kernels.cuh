@@ -26,6 +26,13 @@ cudaError_t launch_mixture_moments(int D, int64_t C, int Kmax, const int32_t* K,
                                    cudaStream_t s);
 
 int solve_blocks(int64_t C);
+
+// standard EM (gm_compress_standard); the parameter block is declared in
+// std_kernel.cuh
+struct StdParams;
+cudaError_t launch_std(int D, const StdParams& p, int v_f64, size_t smem, int sms, cudaStream_t s);
+cudaError_t launch_aa_affine(int n, const double* A, const double* b, const double* x0, int m,
+                             int iters, double* x_out, double* res_out, cudaStream_t s);
 // sets the calling thread's gm_last_error() text; returns code
 int record_error(int code, const char* msg);
 size_t reconstruct_ws_bytes(int D, int64_t C);

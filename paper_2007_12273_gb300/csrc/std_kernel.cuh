@@ -1,0 +1,837 @@
+// std_kernel.cuh -- standard (non-adaptive) EM with K-means initialisation
+// and Anderson acceleration: the acceleration study of Sec. 4, where the
+// paper applies both to the non-adaptive EM-GM algorithm.
+//
+// One CTA fits one cell at a time (persistent, atomic cell ticket).  The
+// cell is staged once as whitened FP32 velocities and normalised weights
+// (shared tile, or an L2-resident global tile for cells over the tile).
+//
+//   * K-means (Lloyd) from the paper's random particles: assignment on the
+//     FP32 coordinates (squared distance with fmaf in dimension order, the
+//     lowest index on ties), centre sums in 64-bit fixed point (2^-40:
+//     exact, so the result does not depend on the order of the sums).
+//   * Standard EM iteration: an exact pass gives each particle's normaliser
+//     and the log-likelihood L(theta_i); one pass per component gives its
+//     E-step statistics (no barrier between components); the M-step of all
+//     components runs on one lane each (FP64 masters, eq. omegak-mle).
+//   * Anderson acceleration (FP64, warp 0) on theta = (omega_k, mu_k,
+//     M2_k = Sigma_k + mu_k mu_k^T) in the cell's whitened coordinates,
+//     started once the relative change of L is at most 1e-4, reset when an
+//     extrapolation has a non-positive weight or an indefinite covariance.
+//   * Output: one standard EM step from the last iterate, entirely in FP64
+//     (FP64-normalised responsibilities), which makes the moments exact.
+#pragma once
+
+#include "em_kernel.cuh"
+
+namespace gmcr {
+
+struct StdParams {
+  int64_t C, n;
+  const int64_t* cell_off;
+  const void* v;
+  const double* alpha;
+  int32_t* K_out;
+  double* params_out;
+  double* W_out;
+  double* lnL_out;
+  int32_t* iters_out;
+  int32_t* aa_steps_out;
+  int32_t* aa_resets_out;
+  int32_t* km_out;
+  uint32_t* status_out;
+  float* scratch;
+  int64_t scratch_stride;
+  unsigned int* queue;
+  int Kmax, max_sweeps, cap, init, aa_m, km_iters;
+  double tol;
+  uint64_t seed;
+};
+
+constexpr int kStdMaxM = 8;            // Anderson memory, at most
+constexpr double kAAStart = 1e-4;      // AA starts when |dL| <= kAAStart |L|
+constexpr double kFix = 1099511627776.0;  // 2^40: fixed point of the K-means sums
+
+// Anderson state (Walker & Ni 2011, type II): the iterate x, G(x), the
+// extrapolation, the previous (f, G) pair and the last h <= m differences
+template <int MAXN>
+struct AAState {
+  double th[MAXN], tg[MAXN], tn[MAXN], fprev[MAXN], gprev[MAXN];
+  double dF[kStdMaxM][MAXN], dG[kStdMaxM][MAXN];
+  double gram[kStdMaxM][kStdMaxM], rhs[kStdMaxM], gam[kStdMaxM];
+  int h, have;
+};
+
+// One Anderson step by a whole warp (FP64): f = G(x) - x; the difference
+// with the previous pair joins the history (the oldest dropped beyond m);
+// gamma from (dF^T dF + 1e-12 max diag I) gamma = dF^T f by Cholesky on
+// lane 0; tn = G(x) - dG gamma.  Returns true if the extrapolation was
+// made (tn valid); false with no history or a pivot that is not positive.
+// Reads s.th, s.tg (n values); the caller syncs the warp before and after.
+template <int MAXN>
+__device__ bool aa_warp_step(AAState<MAXN>& s, int n, int m) {
+  const int lane = threadIdx.x & 31;
+  int h = s.h;
+  if (m > 0 && s.have) {
+    if (h == m) {
+      for (int col = 1; col < m; ++col)
+        for (int i = lane; i < n; i += 32) {
+          s.dF[col - 1][i] = s.dF[col][i];
+          s.dG[col - 1][i] = s.dG[col][i];
+        }
+      --h;
+    }
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+      s.dF[h][i] = (s.tg[i] - s.th[i]) - s.fprev[i];
+      s.dG[h][i] = s.tg[i] - s.gprev[i];
+    }
+    ++h;
+  }
+  for (int i = lane; i < n; i += 32) {
+    s.fprev[i] = s.tg[i] - s.th[i];
+    s.gprev[i] = s.tg[i];
+  }
+  __syncwarp();
+  if (lane == 0) {
+    s.h = h;
+    s.have = 1;
+  }
+  __syncwarp();
+  if (h == 0) return false;
+  for (int a0 = 0; a0 < h; ++a0) {
+    for (int c1 = 0; c1 <= a0; ++c1) {
+      double t = 0.0;
+      for (int i = lane; i < n; i += 32) t += s.dF[a0][i] * s.dF[c1][i];
+      t = warp_sum(t);
+      if (lane == 0) s.gram[a0][c1] = s.gram[c1][a0] = t;
+    }
+    double t = 0.0;
+    for (int i = lane; i < n; i += 32) t += s.dF[a0][i] * s.fprev[i];
+    t = warp_sum(t);
+    if (lane == 0) s.rhs[a0] = t;
+  }
+  __syncwarp();
+  int solved = 0;
+  if (lane == 0) {
+    double dmax = 0.0;
+    for (int a0 = 0; a0 < h; ++a0) dmax = fmax(dmax, s.gram[a0][a0]);
+    if (dmax > 0.0) {
+      double Lm[kStdMaxM][kStdMaxM], z[kStdMaxM];
+      solved = 1;
+      for (int a0 = 0; a0 < h; ++a0) s.gram[a0][a0] += 1e-12 * dmax;
+      for (int a0 = 0; a0 < h && solved; ++a0)
+        for (int c1 = 0; c1 <= a0 && solved; ++c1) {
+          double t = s.gram[a0][c1];
+          for (int e = 0; e < c1; ++e) t -= Lm[a0][e] * Lm[c1][e];
+          if (a0 == c1) {
+            if (!(t > 0.0)) solved = 0;
+            else Lm[a0][a0] = sqrt(t);
+          } else {
+            Lm[a0][c1] = t / Lm[c1][c1];
+          }
+        }
+      if (solved) {
+        for (int a0 = 0; a0 < h; ++a0) {
+          double t = s.rhs[a0];
+          for (int e = 0; e < a0; ++e) t -= Lm[a0][e] * z[e];
+          z[a0] = t / Lm[a0][a0];
+        }
+        for (int a0 = h - 1; a0 >= 0; --a0) {
+          double t = z[a0];
+          for (int e = a0 + 1; e < h; ++e) t -= Lm[e][a0] * s.gam[e];
+          s.gam[a0] = t / Lm[a0][a0];
+        }
+      }
+    }
+  }
+  solved = __shfl_sync(0xffffffffu, solved, 0);
+  __syncwarp();
+  if (!solved) return false;
+  for (int i = lane; i < n; i += 32) {
+    double t = s.tg[i];
+    for (int col = 0; col < h; ++col) t -= s.dG[col][i] * s.gam[col];
+    s.tn[i] = t;
+  }
+  __syncwarp();
+  return true;
+}
+
+template <int D, int NW>
+struct StdCtl {
+  static constexpr int NM = D * (D + 1) / 2;
+  static constexpr int NS = 1 + D + NM;
+  static constexpr int P = 1 + D + NM;
+  static constexpr int NTH = kMaxK * P;
+  static constexpr int NRED = pow2_at_least(NS);
+  // the cell
+  double mean[D], sc[D], isc[D], S0[NM];
+  double W, Nd, sumAH, logjac, L, Lprev;
+  float c0;
+  int64_t cell;
+  unsigned int status;
+  int K, degenerate, it, done, aa_on, naa, nreset, kmp, Kg;
+  int picks[kMaxK];
+  // mixture in whitened coordinates (FP64 masters) and its M-step update
+  double w[kMaxK], mu[kMaxK][D], S[kMaxK][NM];
+  double gw[kMaxK], gmu[kMaxK][D], gS[kMaxK][NM];
+  int gok[kMaxK];
+  // FP32 E-step constants: log2(omega f) = eb - |eA (y - emu)|^2
+  float emu[kMaxK][D], eA[kMaxK][NM], eb[kMaxK];
+  // reductions
+  float redk[kMaxK][NW][NRED];
+  float redl[NW];
+  double redd[NW][NS + 1];
+  double res[NS + 1];
+  // K-means
+  float kc[kMaxK][D];
+  unsigned long long kacc[kMaxK][1 + D + NM];
+  // Anderson
+  AAState<NTH> aa;
+  // final step
+  double fw[kMaxK], fmu[kMaxK][D], fS[kMaxK][NM];
+  int Kf;
+};
+
+// FP64 block sum of NV values (result in c.res)
+template <int D, int NW, int NV>
+__device__ __forceinline__ void std_bsum(StdCtl<D, NW>& c, double (&v)[NV]) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = warp_sum(v[i]);
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) c.redd[w][i] = v[i];
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    for (int q = 0; q < NW; ++q) s += c.redd[q][threadIdx.x];
+    c.res[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// E-step constants of component k from its FP64 whitened (w, mu, S);
+// false if the covariance fails the Cholesky floor (original coordinates)
+template <int D, int NW>
+__device__ bool std_econst(StdCtl<D, NW>& c, int k) {
+  constexpr int NM = D * (D + 1) / 2;
+  double Lc[3][3], ri[3];
+  if (!chol_whitened<D, double, double>(c.S[k], c.mu[k], c.mean, c.sc, Lc, ri)) return false;
+  float eA[NM], elc;
+  make_econst<D, double>(Lc, ri, eA, elc);
+  for (int q = 0; q < NM; ++q) c.eA[k][q] = eA[q];
+  for (int d = 0; d < D; ++d) c.emu[k][d] = (float)c.mu[k][d];
+  c.eb[k] = lg2((float)c.w[k]) + elc;
+  return true;
+}
+
+// component k of theta (whitened) -> (w, mu, M2 upper triangle)
+template <int D, int NW>
+__device__ __forceinline__ void std_pack(const double* w, const double (*mu)[D],
+                                         const double (*S)[D * (D + 1) / 2], int k, double* th) {
+  constexpr int P = 1 + D + D * (D + 1) / 2;
+  double* t = th + k * P;
+  t[0] = w[k];
+  for (int d = 0; d < D; ++d) t[1 + d] = mu[k][d];
+  int q = 0;
+  for (int x = 0; x < D; ++x)
+    for (int y = x; y < D; ++y, ++q) t[1 + D + q] = S[k][q] + mu[k][x] * mu[k][y];
+}
+
+template <int D, int NT, typename VT>
+__global__ void __launch_bounds__(NT, (D == 1 ? 1024 : 512) / NT) std_kernel(StdParams a) {
+  constexpr int NW = NT / 32;
+  using Ctl = StdCtl<D, NW>;
+  constexpr int NM = Ctl::NM, NS = Ctl::NS, P = Ctl::P, NRED = Ctl::NRED;
+  constexpr int T = D * (D + 3) / 2;
+  __shared__ Ctl c;
+  extern __shared__ __align__(16) float tile_smem[];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const VT* __restrict__ vin = static_cast<const VT*>(a.v);
+  (void)T;
+
+  for (;;) {
+    if (tid == 0) c.cell = (int64_t)atomicAdd(a.queue, 1u);
+    __syncthreads();
+    const int64_t j = c.cell;
+    if (j >= a.C) break;
+    const int64_t off = a.cell_off[j];
+    const int N = (int)(a.cell_off[j + 1] - off);
+    double* prm_out = a.params_out + (size_t)j * a.Kmax * P;
+
+    // ---- total weight and weighted mean (FP64) ----------------------------
+    {
+      double acc[1 + D];
+#pragma unroll
+      for (int i = 0; i <= D; ++i) acc[i] = 0.0;
+      for (int p = tid; p < N; p += NT) {
+        const double al = a.alpha[off + p];
+        acc[0] += al;
+#pragma unroll
+        for (int d = 0; d < D; ++d) acc[1 + d] += al * (double)vin[(int64_t)d * a.n + off + p];
+      }
+      std_bsum<D, NW, 1 + D>(c, acc);
+      if (tid == 0) {
+        c.W = c.res[0];
+        c.Nd = (double)N;
+        for (int d = 0; d < D; ++d) c.mean[d] = c.res[1 + d] / c.res[0];
+      }
+      __syncthreads();
+    }
+    if (N == 0 || !(c.W > 0.0)) {
+      for (int i = tid; i < a.Kmax * P; i += NT) prm_out[i] = 0.0;
+      if (tid == 0) {
+        a.K_out[j] = 0;
+        a.W_out[j] = N == 0 ? 0.0 : c.W;
+        a.lnL_out[j] = 0.0;
+        if (a.iters_out) a.iters_out[j] = 0;
+        if (a.aa_steps_out) a.aa_steps_out[j] = 0;
+        if (a.aa_resets_out) a.aa_resets_out[j] = 0;
+        if (a.km_out) a.km_out[j] = 0;
+        a.status_out[j] = N == 0 ? GM_ST_EMPTY : (GM_ST_EMPTY | GM_ST_DEGENERATE);
+      }
+      __syncthreads();
+      continue;
+    }
+    // ---- total covariance (two-pass, FP64) --------------------------------
+    {
+      double acc[NM];
+#pragma unroll
+      for (int i = 0; i < NM; ++i) acc[i] = 0.0;
+      for (int p = tid; p < N; p += NT) {
+        const double al = a.alpha[off + p];
+        double dv[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) dv[d] = (double)vin[(int64_t)d * a.n + off + p] - c.mean[d];
+        int t = 0;
+#pragma unroll
+        for (int x = 0; x < D; ++x)
+#pragma unroll
+          for (int y = x; y < D; ++y, ++t) acc[t] += al * dv[x] * dv[y];
+      }
+      std_bsum<D, NW, NM>(c, acc);
+      if (tid == 0) {
+        double cov[NM];
+        for (int i = 0; i < NM; ++i) cov[i] = c.res[i] / c.W;
+        c.status = (N <= 10) ? GM_ST_TOO_FEW : 0u;
+        double scale2 = 0.0;
+        for (int d = 0; d < D; ++d) scale2 += cov[tri<D>(d, d)] + c.mean[d] * c.mean[d];
+        const double fl = 1e-13 * scale2;
+        bool ok = true;
+        double L2[3][3] = {{0}};
+        for (int x = 0; x < D && ok; ++x)
+          for (int y = 0; y <= x && ok; ++y) {
+            double s = cov[tri<D>(y, x)];
+            for (int m = 0; m < y; ++m) s -= L2[x][m] * L2[y][m];
+            if (x == y) {
+              if (!(s > fl) || !(s < 1e300)) ok = false;
+              else L2[x][x] = sqrt(s);
+            } else {
+              L2[x][y] = s / L2[y][y];
+            }
+          }
+        c.degenerate = ok ? 0 : 1;
+        if (c.degenerate) {
+          for (int i = 0; i < NM; ++i) c.S0[i] = cov[i];
+        } else {
+          c.logjac = 0.0;
+          for (int d = 0; d < D; ++d) {
+            c.sc[d] = sqrt(cov[tri<D>(d, d)]);
+            c.isc[d] = 1.0 / c.sc[d];
+            c.logjac += log(c.sc[d]);
+          }
+          for (int x = 0; x < D; ++x)
+            for (int y = x; y < D; ++y)
+              c.S0[tri<D>(x, y)] = (x == y) ? 1.0 : cov[tri<D>(x, y)] * c.isc[x] * c.isc[y];
+        }
+      }
+      __syncthreads();
+    }
+    if (c.degenerate) {
+      for (int i = tid; i < a.Kmax * P; i += NT) prm_out[i] = 0.0;
+      __syncthreads();
+      if (tid == 0) {
+        prm_out[0] = 1.0;
+        for (int d = 0; d < D; ++d) prm_out[1 + d] = c.mean[d];
+        for (int i = 0; i < NM; ++i) prm_out[1 + D + i] = c.S0[i];
+        a.K_out[j] = 1;
+        a.W_out[j] = c.W;
+        a.lnL_out[j] = 0.0;
+        if (a.iters_out) a.iters_out[j] = 0;
+        if (a.aa_steps_out) a.aa_steps_out[j] = 0;
+        if (a.aa_resets_out) a.aa_resets_out[j] = 0;
+        if (a.km_out) a.km_out[j] = 0;
+        a.status_out[j] = c.status | GM_ST_DEGENERATE | GM_ST_COV_NOT_PD;
+      }
+      __syncthreads();
+      continue;
+    }
+
+    // ---- staging: whitened FP32 velocities and normalised weights ---------
+    float *Y, *AH, *SS, *MM;
+    int ys;
+    if (N <= a.cap) {
+      Y = tile_smem;
+      ys = a.cap;
+    } else {
+      Y = a.scratch + scratch_offset(off, j);
+      ys = (int)a.scratch_stride;
+    }
+    AH = Y + D * ys;
+    SS = Y + (D + 1) * ys;
+    MM = Y + (D + 2) * ys;
+    {
+      const double nw = c.Nd / c.W;
+      double sa[1] = {0.0};
+      for (int p = tid; p < N; p += NT) {
+#pragma unroll
+        for (int d = 0; d < D; ++d)
+          Y[d * ys + p] = (float)(((double)vin[(int64_t)d * a.n + off + p] - c.mean[d]) * c.isc[d]);
+        const float ah = (float)(a.alpha[off + p] * nw);
+        AH[p] = ah;
+        sa[0] += (double)ah;
+      }
+      std_bsum<D, NW, 1>(c, sa);
+      if (tid == 0) {
+        c.sumAH = c.res[0];
+        c.c0 = -2.0471975511965976f * D;
+      }
+    }
+    // ---- the paper's random picks (Sec. 2.3), K = min(Kmax, N) -------------
+    if (tid == 0) {
+      const int K = a.Kmax < N ? a.Kmax : N;
+      int got = 0;
+      for (uint32_t t = 0; got < K; ++t) {
+        int idx;
+        if (t < 100000u) {
+          const u32x4 r = philox_draw(a.seed, t, kTagInit, j);
+          idx = (int)floor(uniform52(r.x, r.y) * c.Nd);
+          if (idx >= N) idx = N - 1;
+        } else {
+          idx = 0;
+          for (;;) {
+            bool used = false;
+            for (int m = 0; m < got; ++m) used |= (c.picks[m] == idx);
+            if (!used) break;
+            ++idx;
+          }
+        }
+        bool dup = false;
+        for (int m = 0; m < got; ++m) dup |= (c.picks[m] == idx);
+        if (!dup) c.picks[got++] = idx;
+      }
+      c.K = K;
+      c.kmp = 0;
+      c.naa = 0;
+      c.nreset = 0;
+      c.aa_on = 0;
+      c.aa.h = 0;
+      c.aa.have = 0;
+    }
+    __syncthreads();
+
+    if (a.init == 1) {
+      // ---- K-means (Lloyd) on the staged coordinates ------------------------
+      const int K = c.K;
+      int* AS = reinterpret_cast<int*>(SS);
+      if (tid < K * D) c.kc[tid / D][tid % D] = Y[(tid % D) * ys + c.picks[tid / D]];
+      const int iters = a.km_iters > 0 ? a.km_iters : 100;
+      int it;
+      for (it = 0; it < iters; ++it) {
+        for (int i = tid; i < K * (1 + D); i += NT) c.kacc[i / (1 + D)][i % (1 + D)] = 0ull;
+        __syncthreads();
+        int changed = 0;
+        for (int p = tid; p < N; p += NT) {
+          float y[D];
+#pragma unroll
+          for (int d = 0; d < D; ++d) y[d] = Y[d * ys + p];
+          int best = 0;
+          float bd = 0.0f;
+          for (int k = 0; k < K; ++k) {
+            const float d0 = y[0] - c.kc[k][0];
+            float dist = d0 * d0;
+            if (D == 3) {
+              const float d1 = y[1] - c.kc[k][1], d2 = y[2] - c.kc[k][2];
+              dist = fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
+            }
+            if (k == 0 || dist < bd) {
+              bd = dist;
+              best = k;
+            }
+          }
+          if (it == 0 || AS[p] != best) changed = 1;
+          AS[p] = best;
+          const double af = (double)AH[p];
+          atomicAdd(&c.kacc[best][0], (unsigned long long)llrint(af * kFix));
+#pragma unroll
+          for (int d = 0; d < D; ++d)
+            atomicAdd(&c.kacc[best][1 + d], (unsigned long long)llrint(af * (double)y[d] * kFix));
+        }
+        const int any = __syncthreads_or(changed);
+        if (it > 0 && !any) break;
+        if (tid < K) {
+          const double A = (double)(long long)c.kacc[tid][0];
+          if (A > 0.0)
+            for (int d = 0; d < D; ++d)
+              c.kc[tid][d] = (float)((double)(long long)c.kacc[tid][1 + d] / A);
+        }
+        __syncthreads();
+      }
+      if (tid == 0) c.kmp = it < iters ? it + 1 : iters;
+      // cluster means (from the last pass's sums) and covariances
+      for (int i = tid; i < K * NM; i += NT) c.kacc[i / NM][1 + D + i % NM] = 0ull;
+      __syncthreads();
+      if (tid < K) {
+        const double A = (double)(long long)c.kacc[tid][0];
+        for (int d = 0; d < D; ++d)
+          c.mu[tid][d] = A > 0.0 ? (double)(long long)c.kacc[tid][1 + d] / A : 0.0;
+      }
+      __syncthreads();
+      for (int p = tid; p < N; p += NT) {
+        const int k = AS[p];
+        const double af = (double)AH[p];
+        double dy[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) dy[d] = (double)Y[d * ys + p] - c.mu[k][d];
+        int q = 0;
+#pragma unroll
+        for (int x = 0; x < D; ++x)
+#pragma unroll
+          for (int y = x; y < D; ++y, ++q)
+            atomicAdd(&c.kacc[k][1 + D + q], (unsigned long long)llrint(af * dy[x] * dy[y] * kFix));
+      }
+      __syncthreads();
+      if (tid == 0) {
+        int Ko = 0;
+        for (int k = 0; k < K; ++k) {
+          const double A = (double)(long long)c.kacc[k][0];
+          if (!(A > 0.0)) continue;
+          c.w[Ko] = A / kFix / c.Nd;
+          for (int d = 0; d < D; ++d) c.mu[Ko][d] = c.mu[k][d];
+          for (int q = 0; q < NM; ++q) c.S[Ko][q] = (double)(long long)c.kacc[k][1 + D + q] / A;
+          double Lc[3][3], ri[3];
+          if (!chol_whitened<D, double, double>(c.S[Ko], c.mu[Ko], c.mean, c.sc, Lc, ri))
+            for (int q = 0; q < NM; ++q) c.S[Ko][q] = c.S0[q];
+          ++Ko;
+        }
+        c.K = Ko;
+      }
+      __syncthreads();
+    } else {
+      if (tid < c.K) {
+        const int k = tid;
+        c.w[k] = 1.0 / (double)c.K;
+        for (int d = 0; d < D; ++d)
+          c.mu[k][d] = ((double)vin[(int64_t)d * a.n + off + c.picks[k]] - c.mean[d]) * c.isc[d];
+        for (int q = 0; q < NM; ++q) c.S[k][q] = c.S0[q];
+      }
+      __syncthreads();
+    }
+    if (tid < c.K) std_econst<D, NW>(c, tid);
+    if (tid == 0) {
+      c.done = 0;
+      c.it = 0;
+    }
+    __syncthreads();
+
+    // ---- standard EM iterations (with Anderson acceleration) ---------------
+    for (;;) {
+      const int K = c.K;
+      const float c0 = c.c0;
+      // exact pass: m_p = max_k log2(omega_k f_k), s_p, and the log-likelihood
+      {
+        float accl = 0.0f;
+        for (int p = tid; p < N; p += NT) {
+          float y[D], dd[D];
+#pragma unroll
+          for (int d = 0; d < D; ++d) y[d] = Y[d * ys + p];
+          float m = -3.0e38f;
+          for (int k = 0; k < K; ++k) m = fmaxf(m, lg_eval<D>(c.emu[k], c.eA[k], c.eb[k], y, dd));
+          float s = 0.0f;
+          for (int k = 0; k < K; ++k) s += ex2(lg_eval<D>(c.emu[k], c.eA[k], c.eb[k], y, dd) - m);
+          SS[p] = s;
+          MM[p] = m;
+          accl = fmaf(AH[p], (m - c0) + lg2(s), accl);
+        }
+        accl = warp_sum(accl);
+        if (lane == 0) c.redl[wid] = accl;
+      }
+      __syncthreads();
+      // one pass per component: its E-step statistics about its FP32 mean
+      for (int k = 0; k < K; ++k) {
+        float acc[NRED];
+#pragma unroll
+        for (int q = 0; q < NRED; ++q) acc[q] = 0.0f;
+        for (int p = tid; p < N; p += NT) {
+          float y[D], dd[D];
+#pragma unroll
+          for (int d = 0; d < D; ++d) y[d] = Y[d * ys + p];
+          const float g = ex2(lg_eval<D>(c.emu[k], c.eA[k], c.eb[k], y, dd) - MM[p]);
+          const float gam = AH[p] * g * rcp_approx(SS[p]);
+          acc[0] += gam;
+          int t = 1 + D;
+#pragma unroll
+          for (int x = 0; x < D; ++x) {
+            const float gd = gam * dd[x];
+            acc[1 + x] += gd;
+#pragma unroll
+            for (int yy = x; yy < D; ++yy, ++t) acc[t] = fmaf(gd, dd[yy], acc[t]);
+          }
+        }
+        warp_rs<NRED>(acc, lane);
+        if ((lane & (32 / NRED - 1)) == 0) {
+          const int q = warp_rs_index<NRED>(lane);
+          if (q < NS) c.redk[k][wid][q] = acc[0];
+        }
+      }
+      __syncthreads();
+      // M-step of every component (one lane each), L, convergence, AA start
+      if (tid < 32) {
+        if (lane < K) {
+          const int k = lane;
+          double st[NS];
+          for (int q = 0; q < NS; ++q) {
+            double s = 0.0;
+            for (int w = 0; w < NW; ++w) s += (double)c.redk[k][w][q];
+            st[q] = s;
+          }
+          const double Nk = st[0];
+          bool ok = Nk > 0.0;
+          if (ok) {
+            double dl[D];
+            for (int x = 0; x < D; ++x) {
+              dl[x] = st[1 + x] / Nk;
+              c.gmu[k][x] = (double)c.emu[k][x] + dl[x];
+            }
+            int t = 0;
+            for (int x = 0; x < D; ++x)
+              for (int yy = x; yy < D; ++yy, ++t) c.gS[k][t] = st[1 + D + t] / Nk - dl[x] * dl[yy];
+            c.gw[k] = Nk / c.sumAH;
+            double Lc[3][3], ri[3];
+            ok = chol_whitened<D, double, double>(c.gS[k], c.gmu[k], c.mean, c.sc, Lc, ri);
+            if (!ok) atomicOr(&c.status, GM_ST_COV_NOT_PD);
+          }
+          c.gok[k] = ok ? 1 : 0;
+        }
+        double ls = lane < NW ? (double)c.redl[lane] : 0.0;
+        ls = warp_sum(ls);
+        __syncwarp();
+        if (lane == 0) {
+          const double L = (ls + (double)c.c0 * c.sumAH) * kLn2 - c.Nd * c.logjac;
+          const int it = c.it;
+          if (it > 0 && fabs(L - c.Lprev) <= a.tol * fabs(c.Lprev))
+            c.done = 1;
+          else if (it + 1 >= a.max_sweeps)
+            c.done = 2;
+          if (!c.aa_on && it > 0 && fabs(L - c.Lprev) <= kAAStart * fabs(c.Lprev)) c.aa_on = 1;
+          if (it == 0 && c.sumAH > 0.0) {
+            // centre the FP32 log-likelihood sums on the first mean term
+            c.c0 = (float)((ls + (double)c.c0 * c.sumAH) / c.sumAH);
+          }
+          c.Lprev = L;
+          int Kg = 0;
+          for (int k = 0; k < K; ++k) Kg += c.gok[k];
+          c.Kg = Kg;
+        }
+      }
+      __syncthreads();
+      if (c.done) break;
+      // ---- the next iterate --------------------------------------------------
+      const bool plain = (c.Kg < K) || a.aa_m == 0 || !c.aa_on;
+      if (plain) {
+        if (tid == 0) {
+          int Ko = 0;
+          for (int k = 0; k < K; ++k) {
+            if (!c.gok[k]) continue;
+            c.w[Ko] = c.gw[k];
+            for (int d = 0; d < D; ++d) c.mu[Ko][d] = c.gmu[k][d];
+            for (int q = 0; q < NM; ++q) c.S[Ko][q] = c.gS[k][q];
+            ++Ko;
+          }
+          if (Ko < K) {  // a dropped component restarts AA
+            c.aa.h = 0;
+            c.aa.have = 0;
+          }
+          c.K = Ko;
+        }
+      } else if (tid < 32) {
+        // Anderson step (warp 0, FP64) on theta = (w, mu, M2) per component
+        const int n = K * P;
+        if (lane < K) {
+          std_pack<D, NW>(c.w, c.mu, c.S, lane, c.aa.th);
+          std_pack<D, NW>(c.gw, c.gmu, c.gS, lane, c.aa.tg);
+        }
+        __syncwarp();
+        const int m = a.aa_m < kStdMaxM ? a.aa_m : kStdMaxM;
+        bool applied = aa_warp_step<Ctl::NTH>(c.aa, n, m);
+        const int h = c.aa.h;
+        if (applied) {
+          // validity of the extrapolation: positive weights, covariances
+          // M2 - mu mu^T passing the floor (whitened and original)
+          bool valid = true;
+          if (lane < K) {
+            const double* t = c.aa.tn + lane * P;
+            double mw[D], Sw[NM], Lc[3][3], ri[3];
+            const double zero[3] = {0.0, 0.0, 0.0}, one[3] = {1.0, 1.0, 1.0};
+            for (int d = 0; d < D; ++d) mw[d] = t[1 + d];
+            int q = 0;
+            for (int x = 0; x < D; ++x)
+              for (int yy = x; yy < D; ++yy, ++q) Sw[q] = t[1 + D + q] - mw[x] * mw[yy];
+            valid = t[0] > 0.0 && chol_whitened<D, double, double>(Sw, mw, zero, one, Lc, ri) &&
+                    chol_whitened<D, double, double>(Sw, mw, c.mean, c.sc, Lc, ri);
+          }
+          applied = __all_sync(0xffffffffu, valid);
+          if (applied) {
+            double ws = lane < K ? c.aa.tn[lane * P] : 0.0;
+            ws = warp_sum(ws);
+            if (lane < K) {
+              const double* t = c.aa.tn + lane * P;
+              c.w[lane] = t[0] / ws;
+              for (int d = 0; d < D; ++d) c.mu[lane][d] = t[1 + d];
+              int q = 0;
+              for (int x = 0; x < D; ++x)
+                for (int yy = x; yy < D; ++yy, ++q) c.S[lane][q] = t[1 + D + q] - t[1 + x] * t[1 + yy];
+            }
+          }
+        }
+        if (!applied) {
+          if (lane < K) {
+            c.w[lane] = c.gw[lane];
+            for (int d = 0; d < D; ++d) c.mu[lane][d] = c.gmu[lane][d];
+            for (int q = 0; q < NM; ++q) c.S[lane][q] = c.gS[lane][q];
+          }
+          if (lane == 0 && h > 0) {  // a failed extrapolation clears the history
+            c.aa.h = 0;
+            c.nreset++;
+          }
+        } else if (lane == 0) {
+          c.naa++;
+        }
+      }
+      __syncthreads();
+      if (tid < c.K) std_econst<D, NW>(c, tid);
+      if (tid == 0) c.it++;
+      __syncthreads();
+    }
+    if (tid == 0 && c.done == 2) c.status |= GM_ST_EM_MAXSWEEPS;
+
+    // ---- output: one standard EM step in FP64 (Sec. 4; eq. omegak-mle) ------
+    if (tid == 0) c.Kf = 0;
+    __syncthreads();
+    {
+      const int K = c.K;
+      const double nw = c.Nd / c.W;
+      for (int k = 0; k < K; ++k) {
+        double ck[D];
+#pragma unroll
+        for (int q = 0; q < D; ++q) ck[q] = c.mu[k][q] * c.sc[q];
+        double acc[NS];
+#pragma unroll
+        for (int q = 0; q < NS; ++q) acc[q] = 0.0;
+        for (int p = tid; p < N; p += NT) {
+          float y[D], d[D];
+#pragma unroll
+          for (int q = 0; q < D; ++q) y[q] = Y[q * ys + p];
+          float m = -3.0e38f;
+          for (int jj = 0; jj < K; ++jj) m = fmaxf(m, lg_eval<D>(c.emu[jj], c.eA[jj], c.eb[jj], y, d));
+          double Ssum = 0.0, gk = 0.0;
+          for (int jj = 0; jj < K; ++jj) {
+            const double g = (double)ex2(lg_eval<D>(c.emu[jj], c.eA[jj], c.eb[jj], y, d) - m);
+            Ssum += g;
+            if (jj == k) gk = g;
+          }
+          const double gam = a.alpha[off + p] * nw * gk / Ssum;
+          double dv[D];
+#pragma unroll
+          for (int q = 0; q < D; ++q) dv[q] = ((double)vin[(int64_t)q * a.n + off + p] - c.mean[q]) - ck[q];
+          acc[0] += gam;
+          int t = 1 + D;
+#pragma unroll
+          for (int x = 0; x < D; ++x) {
+            const double gd = gam * dv[x];
+            acc[1 + x] += gd;
+#pragma unroll
+            for (int yy = x; yy < D; ++yy, ++t) acc[t] += gd * dv[yy];
+          }
+        }
+        std_bsum<D, NW, NS>(c, acc);
+        if (tid == 0 && c.res[0] > 0.0) {
+          const int f = c.Kf;
+          const double nn = c.res[0];
+          double dl[D];
+          for (int x = 0; x < D; ++x) {
+            dl[x] = c.res[1 + x] / nn;
+            c.fmu[f][x] = ck[x] + dl[x];
+          }
+          int t = 0;
+          for (int x = 0; x < D; ++x)
+            for (int yy = x; yy < D; ++yy, ++t) c.fS[f][t] = c.res[1 + D + t] / nn - dl[x] * dl[yy];
+          c.fw[f] = nn / c.Nd;
+          // a covariance failing the floor is dropped, as in every EM step
+          double So[NM], mo[D], meano[D], one[D], Lo[3][3];
+          for (int q = 0; q < NM; ++q) So[q] = c.fS[f][q];
+          for (int d2 = 0; d2 < D; ++d2) {
+            mo[d2] = 0.0;
+            one[d2] = 1.0;
+            meano[d2] = c.mean[d2] + c.fmu[f][d2];
+          }
+          if (chol_whitened<D, double, double>(So, mo, meano, one, Lo))
+            c.Kf = f + 1;
+          else
+            c.status |= GM_ST_COV_NOT_PD;
+        }
+        __syncthreads();
+      }
+    }
+    // ---- the log-likelihood of the output (unpenalised) ---------------------
+    if (tid < c.Kf) {
+      const int k = tid;
+      c.w[k] = c.fw[k];
+      for (int x = 0; x < D; ++x) c.mu[k][x] = c.fmu[k][x] * c.isc[x];
+      int q = 0;
+      for (int x = 0; x < D; ++x)
+        for (int yy = x; yy < D; ++yy, ++q) c.S[k][q] = c.fS[k][q] * c.isc[x] * c.isc[yy];
+      std_econst<D, NW>(c, k);
+    }
+    __syncthreads();
+    {
+      const int K = c.Kf;
+      const float c0 = c.c0;
+      float accl = 0.0f;
+      for (int p = tid; p < N; p += NT) {
+        float y[D], dd[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) y[d] = Y[d * ys + p];
+        float m = -3.0e38f;
+        for (int k = 0; k < K; ++k) m = fmaxf(m, lg_eval<D>(c.emu[k], c.eA[k], c.eb[k], y, dd));
+        float s = 0.0f;
+        for (int k = 0; k < K; ++k) s += ex2(lg_eval<D>(c.emu[k], c.eA[k], c.eb[k], y, dd) - m);
+        accl = fmaf(AH[p], (m - c0) + lg2(s), accl);
+      }
+      double v1[1] = {(double)accl};
+      std_bsum<D, NW, 1>(c, v1);
+    }
+    if (tid == 0) {
+      const int Kf = c.Kf;
+      for (int k = 0; k < Kf; ++k) {
+        double* r = prm_out + (size_t)k * P;
+        r[0] = c.fw[k];
+        for (int d = 0; d < D; ++d) r[1 + d] = c.mean[d] + c.fmu[k][d];
+        for (int q = 0; q < NM; ++q) r[1 + D + q] = c.fS[k][q];
+      }
+      for (int i = Kf * P; i < a.Kmax * P; ++i) prm_out[i] = 0.0;
+      a.K_out[j] = Kf;
+      a.W_out[j] = c.W;
+      a.lnL_out[j] = Kf > 0 ? (c.res[0] + (double)c.c0 * c.sumAH) * kLn2 - c.Nd * c.logjac : 0.0;
+      if (a.iters_out) a.iters_out[j] = c.it + 1;
+      if (a.aa_steps_out) a.aa_steps_out[j] = c.naa;
+      if (a.aa_resets_out) a.aa_resets_out[j] = c.nreset;
+      if (a.km_out) a.km_out[j] = c.kmp;
+      a.status_out[j] = c.status;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace gmcr

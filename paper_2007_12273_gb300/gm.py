@@ -52,6 +52,12 @@ class GMConfig(ct.Structure):
                 ("reserved", ct.c_int32)]
 
 
+class GMStdOpts(ct.Structure):
+    """Mirror of ``gm_std_opts`` (include/gm.h)."""
+    _fields_ = [("init", ct.c_int32), ("aa_memory", ct.c_int32), ("kmeans_iters", ct.c_int32),
+                ("reserved", ct.c_int32)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -94,11 +100,13 @@ def load(build_if_missing: bool = False):
         lib.gm_graph_launch.argtypes = [P, P]
         lib.gm_graph_destroy.argtypes = [P]
         lib.gm_autotune.argtypes = [P, I64, I64, P, P, P, I32, P, I32, ct.POINTER(ct.c_float), P]
+        lib.gm_compress_standard.argtypes = [P, P, I64, I64, P, P, P, I32, P] + [P] * 10 + [P]
+        lib.gm_anderson_affine.argtypes = [I32, P, P, P, I32, I32, P, P, P]
         for f in ("gm_compress", "gm_reconstruct", "gm_moments", "gm_mixture_moments", "gm_shutdown",
                   "gm_reconstruct_noalloc", "gm_gemm_bf16", "gm_compress_from", "gm_features",
                   "gm_mlp_targets", "gm_mlp_sync", "gm_mlp_forward", "gm_mlp_train_step",
                   "gm_mlp_decode", "gm_graph_begin", "gm_graph_end", "gm_graph_launch",
-                  "gm_graph_destroy", "gm_autotune"):
+                  "gm_graph_destroy", "gm_autotune", "gm_compress_standard", "gm_anderson_affine"):
             getattr(lib, f).restype = ct.c_int
         lib.gm_last_error.restype = ct.c_char_p
         _lib = lib
@@ -521,3 +529,53 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+def gm_compress_standard(cfg: GMConfig, cell_off, x, v, alpha, init: int = 0, aa_memory: int = 0,
+                         kmeans_iters: int = 0, stream=None, out=None) -> dict:
+    """Standard (non-adaptive) EM with optional K-means initialisation
+    (``init`` = 1) and Anderson acceleration (``aa_memory`` > 0): the
+    acceleration study of Sec. 4.  Returns the outputs of
+    ``gm_compress_standard`` as CUDA tensors (``out`` may supply them)."""
+    lib = load()
+    C = cell_off.shape[0] - 1
+    n = x.shape[0]
+    D = cfg.D
+    _check(cell_off, torch.int64, "cell_off")
+    _check(x, torch.float64, "x")
+    _check(alpha, torch.float64, "alpha")
+    if v.dtype not in (torch.float32, torch.float64) or tuple(v.shape) != (D, n):
+        raise ValueError("v must be [D, n] float32/float64")
+    _check(v, v.dtype, "v")
+    dev = x.device
+    if out is None:
+        i32 = lambda: torch.empty(C, dtype=torch.int32, device=dev)
+        out = dict(K=i32(), params=torch.empty((C, cfg.Kmax, P_of(D)), dtype=torch.float64, device=dev),
+                   W=torch.empty(C, dtype=torch.float64, device=dev),
+                   rho_target=torch.empty(C, dtype=torch.float64, device=dev),
+                   lnL=torch.empty(C, dtype=torch.float64, device=dev),
+                   iters=i32(), aa_steps=i32(), aa_resets=i32(), km_passes=i32(), status=i32())
+    opts = GMStdOpts(int(init), int(aa_memory), int(kmeans_iters), 0)
+    rc = lib.gm_compress_standard(ct.byref(cfg), ct.byref(opts), C, n, _ptr(cell_off), _ptr(x), _ptr(v),
+                                  1 if v.dtype == torch.float64 else 0, _ptr(alpha), _ptr(out["K"]),
+                                  _ptr(out["params"]), _ptr(out["W"]), _ptr(out["rho_target"]),
+                                  _ptr(out["lnL"]), _ptr(out["iters"]), _ptr(out["aa_steps"]),
+                                  _ptr(out["aa_resets"]), _ptr(out["km_passes"]), _ptr(out["status"]),
+                                  _stream_ptr(stream))
+    _rc(lib, rc, "gm_compress_standard")
+    return out
+
+
+def gm_anderson_affine(A, b, x0, memory: int, iters: int, stream=None):
+    """The standard-EM kernel's Anderson step on G(x) = A x + b (FP64 CUDA
+    tensors): (last iterate, residual norm per step)."""
+    lib = load()
+    n = b.shape[0]
+    for t, nm in ((A, "A"), (b, "b"), (x0, "x0")):
+        _check(t, torch.float64, nm)
+    x = torch.empty(n, dtype=torch.float64, device=b.device)
+    res = torch.empty(max(iters, 1), dtype=torch.float64, device=b.device)
+    rc = lib.gm_anderson_affine(n, _ptr(A), _ptr(b), _ptr(x0), int(memory), int(iters), _ptr(x), _ptr(res),
+                                _stream_ptr(stream))
+    _rc(lib, rc, "gm_anderson_affine")
+    return x, res[:iters]

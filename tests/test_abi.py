@@ -84,3 +84,19 @@ def test_mlp_struct_layout_matches_header(tmp_path):
     vals = [int(t) for t in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     assert vals[0] == ct.sizeof(GMMlp)
     assert vals[1:] == [getattr(GMMlp, f).offset for f in fields]
+
+
+def test_binding_argument_counts_match_header(lib):
+    """Every entry point the Python binding declares to ctypes takes as
+    many arguments as include/gm.h gives it."""
+    txt = open(HEADER).read()
+    decls = re.findall(r"^(?:int|size_t|const char\*)\s+(gm_\w+)\s*\((.*?)\);", txt, re.M | re.S)
+    checked = 0
+    for name, args in decls:
+        at = getattr(lib, name).argtypes
+        if at is None:
+            continue
+        n = 0 if args.strip() in ("", "void") else len(args.split(","))
+        assert len(at) == n, (name, len(at), n)
+        checked += 1
+    assert checked >= 20
