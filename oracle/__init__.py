@@ -74,9 +74,9 @@ def _load():
             lib.oracle_shape.argtypes = [ct.c_int, ct.c_double]
             lib.oracle_shape.restype = ct.c_double
             lib.oracle_max_threads.restype = ct.c_int
-            lib.oracle_standard.argtypes = ([P, ct.c_int64] + [P] * 4 + [ct.c_int] * 3 + [P] * 11
+            lib.oracle_standard.argtypes = ([P, ct.c_int64] + [P] * 4 + [ct.c_int] * 4 + [P] * 11
                                             + [ct.c_int])
-            lib.oracle_std_cell.argtypes = ([P, ct.c_int64, ct.c_int64, P, P] + [ct.c_int] * 3
+            lib.oracle_std_cell.argtypes = ([P, ct.c_int64, ct.c_int64, P, P] + [ct.c_int] * 4
                                             + [P] * 9 + [ct.c_int, P, P, ct.c_int])
             lib.oracle_aa_affine.argtypes = [ct.c_int, P, P, P, ct.c_int, ct.c_int, P, P]
             lib.oracle_kmeans.argtypes = [ct.c_int, ct.c_int, ct.c_int64, P, P, P, ct.c_int, P, P, P]
@@ -184,11 +184,13 @@ def em_cell(params: dict, vv, alpha, cell: int = 0, init_params=None, init_K: in
 
 
 def standard(params: dict, cell_off, x, v, alpha, init: int = 0, aa_memory: int = 0,
-             kmeans_iters: int = 0, nthreads: int = 1, cell_ids=None) -> dict:
+             kmeans_iters: int = 0, nthreads: int = 1, cell_ids=None, penalised: bool = False) -> dict:
     """Oracle of the standard (non-adaptive) EM of Sec. 4 for every cell:
     ``init`` 0 = random particles, 1 = K-means; ``aa_memory`` > 0 turns on
-    Anderson acceleration.  Outputs as ``compress`` plus iterations, AA
-    steps, AA resets and K-means passes per cell."""
+    Anderson acceleration; ``penalised`` runs the simultaneous EM with the
+    penalised weights and annihilation instead (no AA).  Outputs as
+    ``compress`` plus iterations, AA steps, AA resets and K-means passes per
+    cell."""
     lib = _load()
     cfg = _cfg(params)
     cell_off = np.ascontiguousarray(cell_off, dtype=np.int64)
@@ -202,7 +204,7 @@ def standard(params: dict, cell_off, x, v, alpha, init: int = 0, aa_memory: int 
                aa_resets=np.zeros(C, np.int32), km_passes=np.zeros(C, np.int32),
                status=np.zeros(C, np.uint32))
     rc = lib.oracle_standard(ct.byref(cfg), C, _ptr(cell_off), _ptr(x), _ptr(v), _ptr(alpha),
-                             int(init), int(aa_memory), int(kmeans_iters), _ptr(out["K"]),
+                             int(init), int(aa_memory), int(kmeans_iters), int(bool(penalised)), _ptr(out["K"]),
                              _ptr(out["params"]), _ptr(out["W"]), _ptr(out["rho_target"]),
                              _ptr(out["lnL"]), _ptr(out["iters"]), _ptr(out["aa_steps"]),
                              _ptr(out["aa_resets"]), _ptr(out["km_passes"]), _ptr(out["status"]),
@@ -214,9 +216,10 @@ def standard(params: dict, cell_off, x, v, alpha, init: int = 0, aa_memory: int 
 
 
 def std_cell(params: dict, vv, alpha, cell: int = 0, init: int = 0, aa_memory: int = 0,
-             kmeans_iters: int = 0, trace_cap: int = 0, init_params=None) -> dict:
-    """Standard EM of one cell (``vv`` [N, D]) with the trace of L(theta_i);
-    ``init_params`` [K][P] (with ``init`` = 2) continues from a given fit."""
+             kmeans_iters: int = 0, trace_cap: int = 0, init_params=None, penalised: bool = False) -> dict:
+    """Standard EM of one cell (``vv`` [N, D]) with the trace of L(theta_i)
+    (penalised L with ``penalised``); ``init_params`` [K][P] (with ``init``
+    = 2) continues from a given fit."""
     lib = _load()
     cfg = _cfg(params)
     vv = _f64(vv).reshape(-1, cfg.D)
@@ -228,7 +231,8 @@ def std_cell(params: dict, vv, alpha, cell: int = 0, init: int = 0, aa_memory: i
     lnL = np.zeros(1); st = np.zeros(1, np.uint32)
     tr = np.zeros(max(trace_cap, 1)); nt = np.zeros(1, np.int32)
     lib.oracle_std_cell(ct.byref(cfg), int(cell), N, _ptr(vv), _ptr(alpha), int(init),
-                        int(aa_memory), int(kmeans_iters), _ptr(prm), _ptr(K), _ptr(lnL), _ptr(it),
+                        int(aa_memory), int(kmeans_iters), int(bool(penalised)), _ptr(prm), _ptr(K),
+                        _ptr(lnL), _ptr(it),
                         _ptr(na), _ptr(nr), _ptr(km), _ptr(st), _ptr(tr) if trace_cap else None,
                         int(trace_cap), _ptr(nt),
                         _ptr(None if init_params is None else _f64(init_params)),

@@ -1089,6 +1089,79 @@ static double std_em_step(int D, int K, const comp *cs, int64_t N, const double 
   return L;
 }
 
+/* One simultaneous penalised EM step (NEXT variant of Sec. 2.3: the E-step
+ * of every component with the same parameters theta_i, then every M-step):
+ * gamma from eq. (responsibility); a component with N_k - T/2 <= 0 is
+ * annihilated (eq. omegak, a tie annihilated), as is one whose new
+ * covariance (eqs. muk, sigmak) fails the floor (status COV_NOT_PD); the
+ * survivors get omega_k = (N_k - T/2) / sum_survivors (N_j - T/2), which is
+ * eq. (omegak) renormalised (step 3).  Reading: the last component is never
+ * removed: if nothing survives, the component with the largest N_k (lowest
+ * index on ties) stays with omega = 1, updated if its covariance passes the
+ * floor, else with its old parameters.  Returns the penalised L (eq.
+ * lnL-GM) at the input parameters; *annihilated is set if the count fell. */
+static double mml_em_step(int D, int K, const comp *cs, int64_t N, const double *vv,
+                          const double *ah, double *gam, comp *out, int *Kout,
+                          int *annihilated, uint32_t *status) {
+  const int T = T_of(D);
+  const double halfT = 0.5 * T;
+  double lf[OR_MAXK], Nk[OR_MAXK] = {0}, L = 0.0;
+  for (int64_t p = 0; p < N; ++p) {
+    double lm = log_mix(D, K, cs, vv + p * D, lf);
+    L += ah[p] * lm;
+    for (int k = 0; k < K; ++k) {
+      gam[p * OR_MAXK + k] = ah[p] * exp(lf[k] - lm);
+      Nk[k] += gam[p * OR_MAXK + k];
+    }
+  }
+  double pen = 0.0;
+  for (int k = 0; k < K; ++k) pen += log(cs[k].w);
+  const double dpar = (double)K * (T + 1) - 1.0;
+  L = L - 0.5 * dpar * log((double)N) - 0.5 * T * pen;
+
+  comp nc[OR_MAXK];
+  int ok[OR_MAXK];
+  for (int k = 0; k < K; ++k) {
+    ok[k] = 0;
+    if (!(Nk[k] > 0.0)) continue;
+    for (int d = 0; d < D; ++d) {
+      double s = 0.0;
+      for (int64_t p = 0; p < N; ++p) s += gam[p * OR_MAXK + k] * vv[p * D + d];
+      nc[k].mu[d] = s / Nk[k];
+    }
+    for (int i = 0; i < D; ++i)
+      for (int j = 0; j < D; ++j) {
+        double s = 0.0;
+        for (int64_t p = 0; p < N; ++p)
+          s += gam[p * OR_MAXK + k] * (vv[p * D + i] - nc[k].mu[i]) * (vv[p * D + j] - nc[k].mu[j]);
+        nc[k].S[i][j] = s / Nk[k];
+      }
+    ok[k] = chol_floor(D, nc[k].S, nc[k].mu, nc[k].Lc, &nc[k].logdet);
+    if (!ok[k]) *status |= ST_COV_NOT_PD;
+  }
+  double den = 0.0;
+  int Ko = 0;
+  for (int k = 0; k < K; ++k)
+    if (Nk[k] - halfT > 0.0 && ok[k]) den += Nk[k] - halfT;
+  for (int k = 0; k < K; ++k) {
+    if (!(Nk[k] - halfT > 0.0 && ok[k])) continue;
+    out[Ko] = nc[k];
+    out[Ko].w = (Nk[k] - halfT) / den;
+    ++Ko;
+  }
+  if (Ko == 0) {
+    int kb = 0;
+    for (int k = 1; k < K; ++k)
+      if (Nk[k] > Nk[kb]) kb = k;
+    out[0] = ok[kb] ? nc[kb] : cs[kb];
+    out[0].w = 1.0;
+    Ko = 1;
+  }
+  *annihilated = Ko < K;
+  *Kout = Ko;
+  return L;
+}
+
 /* K-means (Lloyd) initialisation in the whitened coordinates
  * y = (v - mean) * (1 / sd), stored in FP32; the centres start at the picked
  * particles.  Each pass assigns every particle to the nearest centre
@@ -1192,9 +1265,14 @@ typedef struct std_out {
  * AA_START |L_{i-1}| on, theta_{i+1} is the Anderson extrapolation, unless it has a non-positive
  * weight or an indefinite covariance: then the history is cleared and
  * theta_{i+1} = g_i (Sec. 4); a dropped component restarts AA.  Ltrace:
- * L(theta_i) per evaluation. */
+ * L(theta_i) per evaluation.  mml = 1 replaces the EM map by the
+ * simultaneous penalised step (mml_em_step; no AA): K0 lowered while
+ * N - T K0 / 2 <= 0, convergence when the relative change of the penalised
+ * L over an iteration without annihilation is at most tol, Ltrace the
+ * penalised L, and the output one standard EM step from the last iterate
+ * (the final unpenalised step of Sec. 2.3.1). */
 static void std_cell(const oracle_cfg *cfg, int64_t cell, int64_t N, const double *vv,
-                     const double *alpha, int init, int aa_m, int km_iters, double *prm_out,
+                     const double *alpha, int init, int aa_m, int km_iters, int mml, double *prm_out,
                      std_out *o, double *Ltrace, int trace_cap, int *ntrace,
                      const double *init_prm, int init_K) {
   const int D = cfg->D, P = P_of(D);
@@ -1235,8 +1313,11 @@ static void std_cell(const oracle_cfg *cfg, int64_t cell, int64_t N, const doubl
     }
   }
   for (int d = 0; d < D; ++d) sd[d] = sqrt(cov[d][d]);
-  /* the initial picks: the adaptive EM's procedure with K = min(Kmax, N) */
+  /* the initial picks: the adaptive EM's procedure with K = min(Kmax, N)
+   * (penalised: lowered while N - T K / 2 <= 0, as in the adaptive EM) */
   int K = cfg->Kmax < N ? cfg->Kmax : (int)N;
+  if (mml)
+    while (K > 1 && Nd - 0.5 * T_of(D) * K <= 0.0) --K;
   int64_t picks[OR_MAXK];
   {
     int got = 0;
@@ -1283,7 +1364,32 @@ static void std_cell(const oracle_cfg *cfg, int64_t cell, int64_t N, const doubl
   aa_init(aa, K * P, aa_m);
   double th[AA_MAXN], tg[AA_MAXN], tn[AA_MAXN];
   double Lprev = 0.0;
-  int converged = 0, it, Kg = K, aa_on = 0;
+  int converged = 0, it, Kg = K, aa_on = 0, ann = 0, ann_prev = 0;
+  if (mml) {
+    /* simultaneous penalised EM (eq. omegak, annihilation) to convergence of
+     * eq. (lnL-GM) over an iteration without annihilation, then the final
+     * unpenalised step of Sec. 2.3.1 from the converged parameters */
+    for (it = 0; it < cfg->max_sweeps; ++it) {
+      const double L = mml_em_step(D, K, cs, N, vv, ah, gam, g, &Kg, &ann, &o->status);
+      if (Ltrace && *ntrace < trace_cap) Ltrace[(*ntrace)++] = L;
+      if (it > 0 && !ann_prev && fabs(L - Lprev) <= cfg->tol * fabs(Lprev)) { converged = 1; break; }
+      if (it + 1 >= cfg->max_sweeps) break;
+      Lprev = L;
+      ann_prev = ann;
+      K = Kg;
+      memcpy(cs, g, sizeof(comp) * (size_t)K);
+    }
+    if (!converged) { o->status |= ST_EM_MAXSWEEPS; it = cfg->max_sweeps - 1; }
+    /* the final step is from the last iterate whose L was evaluated */
+    std_em_step(D, K, cs, N, vv, ah, gam, g, &Kg, &o->status);
+    o->iters = it + 1;
+    o->K = Kg;
+    o->lnL = plain_L(D, Kg, g, N, vv, ah);
+    store_params(D, cfg->Kmax, Kg, g, prm_out);
+    free(ah);
+    free(gam);
+    return;
+  }
   for (it = 0; it < cfg->max_sweeps; ++it) {
     const double L = std_em_step(D, K, cs, N, vv, ah, gam, g, &Kg, &o->status);
     if (Ltrace && *ntrace < trace_cap) Ltrace[(*ntrace)++] = L;
@@ -1320,16 +1426,17 @@ static void std_cell(const oracle_cfg *cfg, int64_t cell, int64_t N, const doubl
 }
 
 /* Exported: standard EM of a batch of cells (layout as oracle_compress);
- * iters/aa_steps/aa_resets/km_passes per cell (each may be NULL). */
+ * iters/aa_steps/aa_resets/km_passes per cell (each may be NULL); mml = 1
+ * runs the simultaneous penalised EM with annihilation (aa_m must be 0). */
 int oracle_standard(const oracle_cfg *cfg, int64_t C, const int64_t *cell_off, const double *x,
                     const double *v, const double *alpha, int init, int aa_m, int km_iters,
-                    int32_t *K_out, double *params_out, double *W_out, double *rho_target_out,
+                    int mml, int32_t *K_out, double *params_out, double *W_out, double *rho_target_out,
                     double *lnL_out, int32_t *iters_out, int32_t *aa_steps_out,
                     int32_t *aa_resets_out, int32_t *km_out, uint32_t *status_out,
                     const int64_t *cell_ids, int nthreads) {
   const int D = cfg->D;
   if (D != 1 && D != 3) return -1;
-  if (cfg->Kmax < 1 || cfg->Kmax > OR_MAXK || aa_m < 0) return -1;
+  if (cfg->Kmax < 1 || cfg->Kmax > OR_MAXK || aa_m < 0 || (mml && aa_m > 0)) return -1;
   const int64_t Ntot = cell_off[C];
   const size_t P = (size_t)P_of(D);
 #ifdef _OPENMP
@@ -1342,7 +1449,7 @@ int oracle_standard(const oracle_cfg *cfg, int64_t C, const int64_t *cell_off, c
     for (int64_t p = 0; p < n; ++p)
       for (int d = 0; d < D; ++d) vv[p * D + d] = v[(int64_t)d * Ntot + cell_off[j] + p];
     std_out o;
-    std_cell(cfg, cell_ids ? cell_ids[j] : j, n, vv, alpha + cell_off[j], init, aa_m, km_iters,
+    std_cell(cfg, cell_ids ? cell_ids[j] : j, n, vv, alpha + cell_off[j], init, aa_m, km_iters, mml,
              params_out + (size_t)j * cfg->Kmax * P, &o, NULL, 0, NULL, NULL, 0);
     K_out[j] = o.K; W_out[j] = o.W; lnL_out[j] = o.lnL; status_out[j] = o.status;
     if (iters_out) iters_out[j] = o.iters;
@@ -1358,13 +1465,13 @@ int oracle_standard(const oracle_cfg *cfg, int64_t C, const int64_t *cell_off, c
 /* Exported: standard EM of one cell with the trace of L(theta_i); init = 2
  * starts from the supplied mixture init_prm [init_K][P] */
 int oracle_std_cell(const oracle_cfg *cfg, int64_t cell, int64_t N, const double *vv /*[N][D]*/,
-                    const double *alpha, int init, int aa_m, int km_iters, double *params_out,
-                    int32_t *K_out, double *lnL_out, int32_t *iters_out, int32_t *aa_steps_out,
+                    const double *alpha, int init, int aa_m, int km_iters, int mml,
+                    double *params_out, int32_t *K_out, double *lnL_out, int32_t *iters_out, int32_t *aa_steps_out,
                     int32_t *aa_resets_out, int32_t *km_out, uint32_t *status_out, double *Ltrace,
                     int trace_cap, int32_t *ntrace, const double *init_prm, int init_K) {
   std_out o;
   int nt = 0;
-  std_cell(cfg, cell, N, vv, alpha, init, aa_m, km_iters, params_out, &o, Ltrace, trace_cap, &nt,
+  std_cell(cfg, cell, N, vv, alpha, init, aa_m, km_iters, mml, params_out, &o, Ltrace, trace_cap, &nt,
            init_prm, init_K);
   *K_out = o.K; *lnL_out = o.lnL; *iters_out = o.iters; *aa_steps_out = o.aa_steps;
   *aa_resets_out = o.aa_resets; *km_out = o.km_passes; *status_out = o.status;
