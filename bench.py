@@ -579,13 +579,27 @@ def run_gmcr(args):
 # whitening, sum of squares), the normaliser and the responsibility, and the
 # moment sums (1 + D + D(D+1)/2 fused multiply-adds).
 STD_FLOPS_PER_PKI = {1: 14, 3: 46}
-STD_MODES = (("random", 0, 0), ("kmeans", 1, 0), ("random+aa5", 0, 5), ("kmeans+aa5", 1, 5))
+STD_MODES = (("random", 0, 0, False), ("kmeans", 1, 0, False), ("random+aa5", 0, 5, False),
+             ("kmeans+aa5", 1, 5, False), ("penalised", 0, 0, True))
+
+
+def mml_objective(K, params, lnL, counts, D):
+    """eq. (lnL-GM) of each cell's output mixture: lnL - (d/2) ln N -
+    (T/2) sum_k ln omega_k, d = K (T + 1) - 1 (cells with K > 0)"""
+    T = D * (D + 3) / 2
+    ok = K > 0
+    w = np.where(np.arange(params.shape[1])[None, :] < K[:, None], params[:, :, 0], 1.0)
+    pen = np.sum(np.log(np.maximum(w, 1e-300)), axis=1)
+    d = K * (T + 1) - 1
+    return np.where(ok, lnL - 0.5 * d * np.log(np.maximum(counts, 1)) - 0.5 * T * pen, 0.0)
 
 
 def run_standard(args):
     """One step = gm_compress_standard (standard EM to tol, final FP64 EM
     step, charge deposit) of the whole batch, for each initialisation and
-    acceleration of Sec. 4; the headline is K-means + Anderson (memory 5)."""
+    acceleration of Sec. 4, and the simultaneous penalised EM beside the
+    component-wise gm_compress; the headline is K-means + Anderson
+    (memory 5)."""
     import torch
     import oracle
     rank, world, local = rank_info()
@@ -614,23 +628,26 @@ def run_standard(args):
     clocks.start()
     modes = {}
     outs = {}
-    for name, init, aa in STD_MODES:
-        out = gm.gm_compress_standard(cfg, cell_off, x, v, alpha, init=init, aa_memory=aa, stream=stream)
+    def time_calls(call):
+        out = call(None)
         for _ in range(args.warmup):
-            gm.gm_compress_standard(cfg, cell_off, x, v, alpha, init=init, aa_memory=aa, stream=stream,
-                                    out=out)
+            call(out)
         torch.cuda.synchronize()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(args.steps)]
         for i in range(args.steps):
             flush.fill_(float(i))
             evs[i][0].record(stream)
-            gm.gm_compress_standard(cfg, cell_off, x, v, alpha, init=init, aa_memory=aa, stream=stream,
-                                    out=out)
+            call(out)
             evs[i][1].record(stream)
         torch.cuda.synchronize()
-        ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
-        o = {k: out[k].cpu().numpy() for k in ("K", "iters", "status", "lnL", "aa_steps", "km_passes")}
+        return out, sum(a.elapsed_time(b) for a, b in evs) / args.steps
+
+    for name, init, aa, pen in STD_MODES:
+        out, ms = time_calls(lambda o_: gm.gm_compress_standard(
+            cfg, cell_off, x, v, alpha, init=init, aa_memory=aa, penalised=pen, stream=stream, out=o_))
+        o = {k: out[k].cpu().numpy() for k in ("K", "iters", "status", "lnL", "aa_steps", "km_passes",
+                                                "params")}
         outs[name] = o
         flops = float(np.sum(counts * o["K"] * o["iters"])) * STD_FLOPS_PER_PKI[D]
         tf = flops / (ms * 1e-3) / 1e12
@@ -638,14 +655,25 @@ def run_standard(args):
                        "iters_p90": float(np.percentile(o["iters"], 90)),
                        "converged_frac": float(np.mean((o["status"] & 1) == 0)),
                        "Kbar": float(o["K"].mean()), "lnL_mean": float(o["lnL"].mean()),
+                       "mml_objective_mean": float(np.mean(mml_objective(o["K"], o["params"], o["lnL"],
+                                                                         counts, D))),
                        "aa_steps_mean": float(o["aa_steps"].mean()),
                        "kmeans_passes_mean": float(o["km_passes"].mean()),
                        "tflops": tf, "frac_fp32_peak": tf / peak}
+    # the component-wise adaptive EM (gm_compress, default launch shape) on
+    # the same batch, beside its simultaneous variant
+    out, ms = time_calls(lambda o_: gm.gm_compress(cfg, cell_off, x, v, alpha, stream=stream, out=o_))
+    o = {k: out[k].cpu().numpy() for k in ("K", "sweeps", "status", "lnL", "params")}
+    modes["component-wise (gm_compress)"] = {
+        "ms": ms, "value": n / (ms * 1e-3), "sweeps_mean": float(o["sweeps"].mean()),
+        "converged_frac": float(np.mean((o["status"] & 1) == 0)), "Kbar": float(o["K"].mean()),
+        "lnL_mean": float(o["lnL"].mean()),
+        "mml_objective_mean": float(np.mean(mml_objective(o["K"], o["params"], o["lnL"], counts, D)))}
     clk = clocks.stop()
     head = "kmeans+aa5"
     hm = modes[head]
     Lp = outs["random"]["lnL"]
-    for name in modes:
+    for name in outs:
         Ln = outs[name]["lnL"]
         modes[name]["reaches_random_plain_L_1e-4"] = float(np.mean(Ln >= Lp - 1e-4 * np.abs(Lp)))
 

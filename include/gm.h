@@ -322,6 +322,19 @@ int gm_mlp_decode(const gm_config* cfg, int64_t C, const float* out, int32_t O,
  * which makes the mixture's mass, mean and covariance the cell's weighted
  * sample moments; lnL_out is the unpenalised log-likelihood of the output.
  *
+ * opts->penalised = 1 runs the simultaneous variant of the paper's
+ * adaptive EM instead (Sec. 2.2-2.3 with all components updated at once;
+ * opts->aa_memory must be 0): K0 = min(Kmax, N) lowered while
+ * N - T K0 / 2 <= 0 (T = D(D+3)/2); each iteration the E-step of all
+ * components with the same parameters, then every M-step, with
+ * omega_k = (N_k - T/2) / sum over survivors (N_j - T/2) (eq. omegak,
+ * renormalised); a component with N_k - T/2 <= 0 or a covariance failing
+ * the floor is annihilated, the last one never (the one with the largest
+ * N_k stays).  It stops when the penalised log-likelihood (eq. lnL-GM)
+ * changes by at most cfg->tol (relative) over an iteration with no
+ * annihilation; the output is the final unpenalised FP64 step of
+ * Sec. 2.3.1 from the last iterate, as above.
+ *
  * Arguments as gm_compress (cfg->threads_per_cell and cfg->precision are
  * not used; cfg->smem_particles sets the shared tile); iters_out [C]: EM
  * steps evaluated; aa_steps_out, aa_resets_out: extrapolations taken and
@@ -331,7 +344,7 @@ typedef struct gm_std_opts {
   int32_t init;         /* 0 = random particles (Sec. 2.3), 1 = K-means */
   int32_t aa_memory;    /* Anderson memory m, 0 = plain EM, at most 8 */
   int32_t kmeans_iters; /* cap on Lloyd passes, 0 = 100 */
-  int32_t reserved;     /* must be 0 */
+  int32_t penalised;    /* 1 = simultaneous penalised EM with annihilation, else 0 */
 } gm_std_opts;
 int gm_compress_standard(const gm_config* cfg, const gm_std_opts* opts, int64_t C,
                          int64_t n_particles, const int64_t* cell_off, const double* x,

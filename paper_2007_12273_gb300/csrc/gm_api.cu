@@ -320,6 +320,9 @@ int gm_compress_standard(const gm_config* cfg, const gm_std_opts* opts, int64_t 
   if (opts->aa_memory < 0 || opts->aa_memory > gmcr::kStdMaxM)
     return fail(GM_ERR_ARG, "opts->aa_memory must be in 0..%d", gmcr::kStdMaxM);
   if (opts->kmeans_iters < 0) return fail(GM_ERR_ARG, "opts->kmeans_iters < 0");
+  if (opts->penalised != 0 && opts->penalised != 1) return fail(GM_ERR_ARG, "opts->penalised must be 0 or 1");
+  if (opts->penalised && opts->aa_memory)
+    return fail(GM_ERR_ARG, "opts->aa_memory must be 0 with opts->penalised");
   if (C < 0 || C >= (int64_t)1 << 31) return fail(GM_ERR_ARG, "C out of range (%lld)", (long long)C);
   if (n_particles < 0) return fail(GM_ERR_ARG, "n_particles < 0");
   if (cfg->max_sweeps < 1) return fail(GM_ERR_ARG, "max_sweeps must be >= 1");
@@ -375,6 +378,7 @@ int gm_compress_standard(const gm_config* cfg, const gm_std_opts* opts, int64_t 
   p.init = opts->init;
   p.aa_m = opts->aa_memory;
   p.km_iters = opts->kmeans_iters;
+  p.mml = opts->penalised;
   p.tol = cfg->tol;
   p.seed = cfg->seed;
   e = gmcr::launch_std(D, p, v_is_f64, smem, sms, s);

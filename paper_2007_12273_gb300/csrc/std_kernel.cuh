@@ -18,6 +18,10 @@
 //     M2_k = Sigma_k + mu_k mu_k^T) in the cell's whitened coordinates,
 //     started once the relative change of L is at most 1e-4, reset when an
 //     extrapolation has a non-positive weight or an indefinite covariance.
+//   * Penalised variant (mml): the same simultaneous iteration with the
+//     weights of eq. (omegak) from every component's N_k, annihilation of
+//     components with N_k - T/2 <= 0 (never the last), convergence of the
+//     penalised L (eq. lnL-GM) over an iteration without annihilation.
 //   * Output: one standard EM step from the last iterate, entirely in FP64
 //     (FP64-normalised responsibilities), which makes the moments exact.
 #pragma once
@@ -44,6 +48,7 @@ struct StdParams {
   int64_t scratch_stride;
   unsigned int* queue;
   int Kmax, max_sweeps, cap, init, aa_m, km_iters;
+  int mml;  // 1: simultaneous penalised EM with annihilation (eq. omegak)
   double tol;
   uint64_t seed;
 };
@@ -170,7 +175,7 @@ struct StdCtl {
   float c0;
   int64_t cell;
   unsigned int status;
-  int K, degenerate, it, done, aa_on, naa, nreset, kmp, Kg;
+  int K, degenerate, it, done, aa_on, naa, nreset, kmp, Kg, ann;
   int picks[kMaxK];
   // mixture in whitened coordinates (FP64 masters) and its M-step update
   double w[kMaxK], mu[kMaxK][D], S[kMaxK][NM];
@@ -249,7 +254,6 @@ __global__ void __launch_bounds__(NT, (D == 1 ? 1024 : 512) / NT) std_kernel(Std
   extern __shared__ __align__(16) float tile_smem[];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const VT* __restrict__ vin = static_cast<const VT*>(a.v);
-  (void)T;
 
   for (;;) {
     if (tid == 0) c.cell = (int64_t)atomicAdd(a.queue, 1u);
@@ -400,7 +404,9 @@ __global__ void __launch_bounds__(NT, (D == 1 ? 1024 : 512) / NT) std_kernel(Std
     }
     // ---- the paper's random picks (Sec. 2.3), K = min(Kmax, N) -------------
     if (tid == 0) {
-      const int K = a.Kmax < N ? a.Kmax : N;
+      int K = a.Kmax < N ? a.Kmax : N;
+      if (a.mml)
+        while (K > 1 && c.Nd - 0.5 * (double)T * K <= 0.0) --K;
       int got = 0;
       for (uint32_t t = 0; got < K; ++t) {
         int idx;
@@ -426,6 +432,7 @@ __global__ void __launch_bounds__(NT, (D == 1 ? 1024 : 512) / NT) std_kernel(Std
       c.naa = 0;
       c.nreset = 0;
       c.aa_on = 0;
+      c.ann = 0;
       c.aa.h = 0;
       c.aa.have = 0;
     }
@@ -588,6 +595,7 @@ __global__ void __launch_bounds__(NT, (D == 1 ? 1024 : 512) / NT) std_kernel(Std
       __syncthreads();
       // M-step of every component (one lane each), L, convergence, AA start
       if (tid < 32) {
+        double Nk = 0.0;
         if (lane < K) {
           const int k = lane;
           double st[NS];
@@ -596,7 +604,7 @@ __global__ void __launch_bounds__(NT, (D == 1 ? 1024 : 512) / NT) std_kernel(Std
             for (int w = 0; w < NW; ++w) s += (double)c.redk[k][w][q];
             st[q] = s;
           }
-          const double Nk = st[0];
+          Nk = st[0];
           bool ok = Nk > 0.0;
           if (ok) {
             double dl[D];
@@ -614,13 +622,57 @@ __global__ void __launch_bounds__(NT, (D == 1 ? 1024 : 512) / NT) std_kernel(Std
           }
           c.gok[k] = ok ? 1 : 0;
         }
+        __syncwarp();
+        if (a.mml) {
+          // eq. (omegak) over the survivors; annihilation of N_k - T/2 <= 0
+          const double hT = 0.5 * (double)T;
+          const bool okk = lane < K && c.gok[lane];
+          const bool alive = okk && Nk - hT > 0.0;
+          const double den = warp_sum(alive ? Nk - hT : 0.0);
+          if (__ballot_sync(0xffffffffu, alive) == 0u) {
+            // nothing survives: the component with the largest N_k stays
+            // (lowest index on ties), with its old parameters if its new
+            // covariance failed the floor
+            double bv = lane < K ? Nk : -1.0;
+            int bi = lane;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+              const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+              if (ov > bv || (ov == bv && oi < bi)) {
+                bv = ov;
+                bi = oi;
+              }
+            }
+            if (lane < K) {
+              c.gok[lane] = lane == bi ? 1 : 0;
+              if (lane == bi) {
+                c.gw[lane] = 1.0;
+                if (!okk) {
+                  for (int d = 0; d < D; ++d) c.gmu[lane][d] = c.mu[lane][d];
+                  for (int q = 0; q < NM; ++q) c.gS[lane][q] = c.S[lane][q];
+                }
+              }
+            }
+          } else if (lane < K) {
+            c.gok[lane] = alive ? 1 : 0;
+            c.gw[lane] = alive ? (Nk - hT) / den : 0.0;
+          }
+          __syncwarp();
+        }
         double ls = lane < NW ? (double)c.redl[lane] : 0.0;
         ls = warp_sum(ls);
         __syncwarp();
         if (lane == 0) {
-          const double L = (ls + (double)c.c0 * c.sumAH) * kLn2 - c.Nd * c.logjac;
+          double L = (ls + (double)c.c0 * c.sumAH) * kLn2 - c.Nd * c.logjac;
+          if (a.mml) {  // eq. (lnL-GM) at the current parameters
+            double pen = 0.0;
+            for (int k = 0; k < K; ++k) pen += log(c.w[k]);
+            const double dpar = (double)K * (T + 1) - 1.0;
+            L -= 0.5 * dpar * log(c.Nd) + 0.5 * (double)T * pen;
+          }
           const int it = c.it;
-          if (it > 0 && fabs(L - c.Lprev) <= a.tol * fabs(c.Lprev))
+          if (it > 0 && !c.ann && fabs(L - c.Lprev) <= a.tol * fabs(c.Lprev))
             c.done = 1;
           else if (it + 1 >= a.max_sweeps)
             c.done = 2;
@@ -653,6 +705,7 @@ __global__ void __launch_bounds__(NT, (D == 1 ? 1024 : 512) / NT) std_kernel(Std
             c.aa.h = 0;
             c.aa.have = 0;
           }
+          c.ann = a.mml && Ko < K;
           c.K = Ko;
         }
       } else if (tid < 32) {

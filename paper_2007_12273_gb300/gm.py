@@ -55,7 +55,7 @@ class GMConfig(ct.Structure):
 class GMStdOpts(ct.Structure):
     """Mirror of ``gm_std_opts`` (include/gm.h)."""
     _fields_ = [("init", ct.c_int32), ("aa_memory", ct.c_int32), ("kmeans_iters", ct.c_int32),
-                ("reserved", ct.c_int32)]
+                ("penalised", ct.c_int32)]
 
 
 _lock = threading.Lock()
@@ -532,11 +532,13 @@ class Graph:
 
 
 def gm_compress_standard(cfg: GMConfig, cell_off, x, v, alpha, init: int = 0, aa_memory: int = 0,
-                         kmeans_iters: int = 0, stream=None, out=None) -> dict:
+                         kmeans_iters: int = 0, stream=None, out=None, penalised: bool = False) -> dict:
     """Standard (non-adaptive) EM with optional K-means initialisation
     (``init`` = 1) and Anderson acceleration (``aa_memory`` > 0): the
-    acceleration study of Sec. 4.  Returns the outputs of
-    ``gm_compress_standard`` as CUDA tensors (``out`` may supply them)."""
+    acceleration study of Sec. 4; ``penalised`` runs the simultaneous EM
+    with the penalised weights and annihilation instead.  Returns the
+    outputs of ``gm_compress_standard`` as CUDA tensors (``out`` may supply
+    them)."""
     lib = load()
     C = cell_off.shape[0] - 1
     n = x.shape[0]
@@ -555,7 +557,7 @@ def gm_compress_standard(cfg: GMConfig, cell_off, x, v, alpha, init: int = 0, aa
                    rho_target=torch.empty(C, dtype=torch.float64, device=dev),
                    lnL=torch.empty(C, dtype=torch.float64, device=dev),
                    iters=i32(), aa_steps=i32(), aa_resets=i32(), km_passes=i32(), status=i32())
-    opts = GMStdOpts(int(init), int(aa_memory), int(kmeans_iters), 0)
+    opts = GMStdOpts(int(init), int(aa_memory), int(kmeans_iters), int(bool(penalised)))
     rc = lib.gm_compress_standard(ct.byref(cfg), ct.byref(opts), C, n, _ptr(cell_off), _ptr(x), _ptr(v),
                                   1 if v.dtype == torch.float64 else 0, _ptr(alpha), _ptr(out["K"]),
                                   _ptr(out["params"]), _ptr(out["W"]), _ptr(out["rho_target"]),

@@ -48,19 +48,19 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def run_both(gm, wl, init, aa, **cfg_over):
+def run_both(gm, wl, init, aa, penalised=False, **cfg_over):
     p = dict(wl.params, **cfg_over)
     cfg = gm.config(p)
     out = gm.gm_compress_standard(cfg, dev(wl.cell_off), dev(wl.x), dev(wl.v), dev(wl.alpha),
-                                  init=init, aa_memory=aa)
+                                  init=init, aa_memory=aa, penalised=penalised)
     torch.cuda.synchronize()
     g = {k: t.cpu().numpy() for k, t in out.items()}
     ref = oracle.standard(p, wl.cell_off, wl.x, wl.v, wl.alpha, init=init, aa_memory=aa,
-                          nthreads=NTHREADS)
+                          nthreads=NTHREADS, penalised=penalised)
     return p, g, ref, out
 
 
-def agreement(p, g, ref, wl, init, aa):
+def agreement(p, g, ref, wl, init, aa, penalised=False):
     rel = np.abs(g["lnL"] - ref["lnL"]) / np.maximum(np.abs(ref["lnL"]), 1e-300)
     nat = (g["K"] == ref["K"]) & (rel <= 1e-5)
     eq = nat.copy()
@@ -68,7 +68,7 @@ def agreement(p, g, ref, wl, init, aa):
         sl = slice(wl.cell_off[j], wl.cell_off[j + 1])
         it = max(int(g["iters"][j]), 1)
         r = oracle.std_cell(dict(p, tol=0.0, max_sweeps=it), wl.v[:, sl].T, wl.alpha[sl], cell=j,
-                            init=init, aa_memory=aa, trace_cap=it + 2)
+                            init=init, aa_memory=aa, trace_cap=it + 2, penalised=penalised)
         diff = abs(g["lnL"][j] - r["lnL"])
         if r["K"] != g["K"][j]:
             continue
@@ -151,6 +151,49 @@ def test_standard_3v_matches_oracle(gm, init, aa):
     if init == 1:
         assert np.mean(g["km_passes"] == ref["km_passes"]) >= 0.9
     check_moments(gm, wl, out)
+
+
+PENALISED_CASES = [("mixture_1d1v", 0), ("bimaxwellian_1d3v", 0), ("bimaxwellian_1d3v", 1),
+                   ("two_stream_1d1v", 0)]
+
+
+@pytest.mark.parametrize("which,init", PENALISED_CASES)
+def test_penalised_simultaneous_em_matches_oracle(gm, which, init):
+    """The simultaneous penalised EM with annihilation (penalised = 1): K
+    and lnL cell by cell, with the equal-iteration rule for the cells that
+    stop at another iteration (penalised L in the trace); exact moments."""
+    if which == "mixture_1d1v":
+        wl = workloads.mixture_1d1v(C=64, mean_n=900, clip=(100, 3000), seed=51)
+    elif which == "bimaxwellian_1d3v":
+        wl = workloads.with_weights(workloads.bimaxwellian_1d3v(C=32, ppc=800, seed=52))
+    else:
+        wl = workloads.two_stream_1d1v()
+    p, g, ref, out = run_both(gm, wl, init, 0, penalised=True)
+    nat, eq = agreement(p, g, ref, wl, init, 0, penalised=True)
+    print(f"penalised {which} init {init}: natural {nat:.3f}, equal iterations {eq:.3f}; K GPU "
+          f"{g['K'].mean():.2f} oracle {ref['K'].mean():.2f}; iterations GPU {g['iters'].mean():.1f} "
+          f"oracle {ref['iters'].mean():.1f}")
+    assert eq >= 0.95 and nat >= 0.4, (nat, eq)
+    assert abs(g["K"].mean() - ref["K"].mean()) <= 0.1 * ref["K"].mean()
+    np.testing.assert_allclose(g["W"], ref["W"], rtol=1e-13)
+    check_moments(gm, wl, out)
+
+
+def test_penalised_keeps_one_component_and_rejects_anderson(gm):
+    """A 12-particle cell with Kmax = 8 (1V: T/2 = 1): K0 is lowered to keep
+    N - T K0 / 2 > 0 and annihilation leaves at least one component; AA is
+    not defined for the penalised variant."""
+    counts = np.array([12, 3, 40, 0])
+    wl = workloads.mixture_1d1v(C=4, counts=counts, seed=56)
+    p, g, ref, out = run_both(gm, wl, 0, 0, penalised=True)
+    assert np.all(g["K"][counts > 0] >= 1)
+    np.testing.assert_array_equal(g["K"], ref["K"])
+    rel = np.abs(g["lnL"] - ref["lnL"]) / np.maximum(np.abs(ref["lnL"]), 1e-300)
+    assert np.all(rel[counts > 3] <= 1e-5)
+    cfg = gm.config(wl.params)
+    with pytest.raises(RuntimeError):
+        gm.gm_compress_standard(cfg, dev(wl.cell_off), dev(wl.x), dev(wl.v), dev(wl.alpha),
+                                aa_memory=3, penalised=True)
 
 
 @pytest.mark.parametrize("n,memory", [(6, 6), (24, 3), (160, 8), (40, 0)])
