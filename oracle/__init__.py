@@ -52,6 +52,14 @@ class _Cfg(ct.Structure):
                 ("L", ct.c_double), ("q", ct.c_double)]
 
 
+class _Mesh2d(ct.Structure):
+    _fields_ = [("Cx", ct.c_int64), ("Cy", ct.c_int64), ("Lx", ct.c_double), ("Ly", ct.c_double)]
+
+
+def _mesh(params: dict) -> _Mesh2d:
+    return _Mesh2d(int(params["Cx"]), int(params["Cy"]), float(params["Lx"]), float(params["Ly"]))
+
+
 def _load():
     global _lib
     with _lock:
@@ -80,6 +88,8 @@ def _load():
                                             + [P] * 9 + [ct.c_int, P, P, ct.c_int])
             lib.oracle_aa_affine.argtypes = [ct.c_int, P, P, P, ct.c_int, ct.c_int, P, P]
             lib.oracle_kmeans.argtypes = [ct.c_int, ct.c_int, ct.c_int64, P, P, P, ct.c_int, P, P, P]
+            lib.oracle_deposit2d.argtypes = [P] * 7
+            lib.oracle_reconstruct2d.argtypes = [P] * 12 + [ct.c_int]
             _lib = lib
     return _lib
 
@@ -313,6 +323,48 @@ def reconstruct(params: dict, K, prm, W, rho_target, out_off, nthreads: int = 1,
         raise ValueError(f"oracle_reconstruct failed ({rc})")
     if want_raw:
         out["v_raw"] = raw
+    return out
+
+
+def deposit2d(params: dict, cell_off, x, y, alpha) -> np.ndarray:
+    """Charge density [Cy * Cx] (node j = jy Cx + jx) of particles sorted by
+    cell on the 2D periodic mesh of ``params`` (Cx, Cy, Lx, Ly), tensor
+    product B-spline of ``shape_order``."""
+    lib = _load()
+    cfg = _cfg(params)
+    m = _mesh(params)
+    cell_off = np.ascontiguousarray(cell_off, dtype=np.int64)
+    rho = np.zeros(m.Cx * m.Cy)
+    rc = lib.oracle_deposit2d(ct.byref(cfg), ct.byref(m), _ptr(cell_off), _ptr(_f64(x)), _ptr(_f64(y)),
+                              _ptr(_f64(alpha)), _ptr(rho))
+    if rc != 0:
+        raise ValueError(f"oracle_deposit2d failed ({rc})")
+    return rho
+
+
+def reconstruct2d(params: dict, K, prm, W, rho_target, out_off, nthreads: int = 1) -> dict:
+    """Oracle reconstruction on the 2D periodic mesh (Sec. 2.4 with the
+    tensor-product shape function; dense direct solve, at most 2048
+    cells).  Uses ``params['recon_seed']``."""
+    lib = _load()
+    cfg = _cfg(params, "recon_seed")
+    m = _mesh(params)
+    out_off = np.ascontiguousarray(out_off, dtype=np.int64)
+    C = out_off.shape[0] - 1
+    assert C == m.Cx * m.Cy
+    D = cfg.D
+    Nout = int(out_off[-1])
+    K = np.ascontiguousarray(K, dtype=np.int32)
+    prm = _f64(prm); W = _f64(W); rho_target = _f64(rho_target)
+    assert prm.shape == (C, cfg.Kmax, P_of(D))
+    xy = np.zeros((2, Nout))
+    out = dict(v=np.zeros((D, Nout)), alpha=np.zeros(Nout), status=np.zeros(C, np.uint32), dA=np.zeros(C))
+    rc = lib.oracle_reconstruct2d(ct.byref(cfg), ct.byref(m), _ptr(K), _ptr(prm), _ptr(W),
+                                  _ptr(rho_target), _ptr(out_off), _ptr(xy), _ptr(out["v"]),
+                                  _ptr(out["alpha"]), _ptr(out["status"]), _ptr(out["dA"]), int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle_reconstruct2d failed ({rc})")
+    out["x"], out["y"] = xy[0], xy[1]
     return out
 
 

@@ -623,6 +623,124 @@ static int dense_solve(int n, double *A, double *b, double *x) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Reconstruction helpers shared by the 1D and 2D meshes (Sec. 2.4)          */
+/* ------------------------------------------------------------------------ */
+
+/* cell j's mixture with the Cholesky factors sampling needs (no floor: a
+ * non-positive pivot gives a zero column) */
+static void load_sampling_cell(int D, int Kj, const double *prm, comp *cs) {
+  load_params(D, Kj, prm, cs);
+  for (int k = 0; k < Kj; ++k) {
+    memset(cs[k].Lc, 0, sizeof(cs[k].Lc));
+    for (int a = 0; a < D; ++a)
+      for (int b = 0; b <= a; ++b) {
+        double s = cs[k].S[a][b];
+        for (int m = 0; m < b; ++m) s -= cs[k].Lc[a][m] * cs[k].Lc[b][m];
+        if (a == b) cs[k].Lc[a][a] = s > 0.0 ? sqrt(s) : 0.0;
+        else cs[k].Lc[a][b] = cs[k].Lc[b][b] > 0.0 ? s / cs[k].Lc[b][b] : 0.0;
+      }
+  }
+}
+
+/* particle i of cell j (Sec. 2.4, eq. mix-dist-1): the uniform u0 of its
+ * position inside the cell and its velocity: a component z with
+ * probability omega_z (the smallest k with u1 < sum_{m <= k} omega_m), then
+ * v = mu_z + Lc_z xi with xi from Box-Muller (Box & Muller 1958) on pairs
+ * of uniforms.  Philox counter (i, TAG_SAMPLE | block, j). */
+static double sample_one(const oracle_cfg *cfg, int D, const comp *cs, int Kj, int64_t j,
+                         int64_t i, double *v) {
+  uint32_t r0[4], r1[4], r2[4];
+  philox_draw(cfg->seed, (uint32_t)i, TAG_SAMPLE | 0u, j, r0);
+  philox_draw(cfg->seed, (uint32_t)i, TAG_SAMPLE | 1u, j, r1);
+  const double u0 = oracle_uniform52(r0[0], r0[1]);
+  const double u1 = oracle_uniform52(r0[2], r0[3]);
+  int z = Kj - 1;
+  double cum = 0.0;
+  for (int k = 0; k < Kj; ++k) {
+    cum += cs[k].w;
+    if (u1 < cum) { z = k; break; }
+  }
+  double xi[4];
+  {
+    double ua = oracle_uniform52(r1[0], r1[1]), ub = oracle_uniform52(r1[2], r1[3]);
+    double rr = sqrt(-2.0 * log(ua));
+    xi[0] = rr * cos(2.0 * OR_PI * ub);
+    xi[1] = rr * sin(2.0 * OR_PI * ub);
+  }
+  if (D == 3) {
+    philox_draw(cfg->seed, (uint32_t)i, TAG_SAMPLE | 2u, j, r2);
+    double ua = oracle_uniform52(r2[0], r2[1]), ub = oracle_uniform52(r2[2], r2[3]);
+    double rr = sqrt(-2.0 * log(ua));
+    xi[2] = rr * cos(2.0 * OR_PI * ub);
+    xi[3] = rr * sin(2.0 * OR_PI * ub);
+  }
+  for (int a = 0; a < D; ++a) {
+    double sv = 0.0;
+    if (Kj > 0) {
+      sv = cs[z].mu[a];
+      for (int b = 0; b <= a; ++b) sv += cs[z].Lc[a][b] * xi[b];
+    }
+    v[a] = sv;
+  }
+  return u0;
+}
+
+/* Lemons projection (Sec. 2.4.2), after the weight correction:
+ * v' = a (v + beta), with targets p, E from the mixture and
+ * N' = sum alpha', p' = sum alpha' v, E' = 1/2 sum alpha' |v|^2 (eq. beta),
+ * a = sqrt((2 E N' - p^2) / (2 E' N' - p'^2)), beta = (p - a p')/(a N')
+ * (eq. alpha).  A non-positive numerator skips the cell (Sec. 2.4.2:
+ * "forgo the local moment-matching step"). */
+static void lemons_project(const oracle_cfg *cfg, int64_t C, const int32_t *K, const double *params,
+                           const double *W, const int64_t *out_off, const double *alpha_out,
+                           double *v_out, uint32_t *status_out) {
+  const int D = cfg->D;
+  const size_t P = (size_t)P_of(D);
+  const int64_t Nout = out_off[C];
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int64_t j = 0; j < C; ++j) {
+    int64_t n = out_off[j + 1] - out_off[j];
+    if (n == 0 || K[j] == 0) continue;
+    comp cs[OR_MAXK];
+    load_params(D, K[j], params + (size_t)j * cfg->Kmax * P, cs);
+    double pt[OR_MAXD] = {0}, Et = 0.0;
+    for (int k = 0; k < K[j]; ++k) {
+      double tr = 0.0, mm = 0.0;
+      for (int a = 0; a < D; ++a) {
+        pt[a] += W[j] * cs[k].w * cs[k].mu[a];
+        tr += cs[k].S[a][a];
+        mm += cs[k].mu[a] * cs[k].mu[a];
+      }
+      Et += 0.5 * W[j] * cs[k].w * (tr + mm);
+    }
+    double Np = 0.0, pp[OR_MAXD] = {0}, Ep = 0.0;
+    for (int64_t p = out_off[j]; p < out_off[j + 1]; ++p) {
+      Np += alpha_out[p];
+      for (int a = 0; a < D; ++a) {
+        double va = v_out[(int64_t)a * Nout + p];
+        pp[a] += alpha_out[p] * va;
+        Ep += 0.5 * alpha_out[p] * va * va;
+      }
+    }
+    double pt2 = 0.0, pp2 = 0.0;
+    for (int a = 0; a < D; ++a) { pt2 += pt[a] * pt[a]; pp2 += pp[a] * pp[a]; }
+    double num = 2.0 * Et * Np - pt2;
+    double den = 2.0 * Ep * Np - pp2;
+    if (!(num > 0.0) || !(den > 0.0) || !(Np > 0.0)) { status_out[j] |= ST_PROJ_SKIPPED; continue; }
+    double aa = sqrt(num / den);
+    double beta[OR_MAXD];
+    for (int a = 0; a < D; ++a) beta[a] = (pt[a] - aa * pp[a]) / (aa * Np);
+    for (int64_t p = out_off[j]; p < out_off[j + 1]; ++p)
+      for (int a = 0; a < D; ++a) {
+        double *va = &v_out[(int64_t)a * Nout + p];
+        *va = aa * (*va + beta[a]);
+      }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Exported: reconstruction of all cells (Sec. 2.4).                        */
 /* ------------------------------------------------------------------------ */
 int oracle_reconstruct(const oracle_cfg *cfg, int64_t C, const int32_t *K, const double *params,
@@ -651,59 +769,14 @@ int oracle_reconstruct(const oracle_cfg *cfg, int64_t C, const int32_t *K, const
     if (n == 0) continue;
     comp cs[OR_MAXK];
     int Kj = K[j];
-    load_params(D, Kj, params + (size_t)j * cfg->Kmax * P, cs);
-    for (int k = 0; k < Kj; ++k) {
-      /* sampling needs only the Cholesky factor, no floor */
-      double ld;
-      memset(cs[k].Lc, 0, sizeof(cs[k].Lc));
-      for (int a = 0; a < D; ++a)
-        for (int b = 0; b <= a; ++b) {
-          double s = cs[k].S[a][b];
-          for (int m = 0; m < b; ++m) s -= cs[k].Lc[a][m] * cs[k].Lc[b][m];
-          if (a == b) cs[k].Lc[a][a] = s > 0.0 ? sqrt(s) : 0.0;
-          else cs[k].Lc[a][b] = cs[k].Lc[b][b] > 0.0 ? s / cs[k].Lc[b][b] : 0.0;
-        }
-      (void)ld;
-    }
+    load_sampling_cell(D, Kj, params + (size_t)j * cfg->Kmax * P, cs);
     if (Kj == 0) status_out[j] |= ST_NO_MIXTURE;
     for (int64_t i = 0; i < n; ++i) {
       int64_t g = out_off[j] + i;
-      uint32_t r0[4], r1[4], r2[4];
-      philox_draw(cfg->seed, (uint32_t)i, TAG_SAMPLE | 0u, j, r0);
-      philox_draw(cfg->seed, (uint32_t)i, TAG_SAMPLE | 1u, j, r1);
-      double u0 = oracle_uniform52(r0[0], r0[1]);
-      double u1 = oracle_uniform52(r0[2], r0[3]);
+      double vv[OR_MAXD];
+      const double u0 = sample_one(cfg, D, cs, Kj, j, i, vv);
       x_out[g] = ((double)j + u0) * dx;
-      /* categorical draw by the cumulative weights */
-      int z = Kj - 1;
-      double cum = 0.0;
-      for (int k = 0; k < Kj; ++k) {
-        cum += cs[k].w;
-        if (u1 < cum) { z = k; break; }
-      }
-      /* Box-Muller (Box & Muller 1958) on pairs of uniforms */
-      double xi[4];
-      {
-        double ua = oracle_uniform52(r1[0], r1[1]), ub = oracle_uniform52(r1[2], r1[3]);
-        double rr = sqrt(-2.0 * log(ua));
-        xi[0] = rr * cos(2.0 * OR_PI * ub);
-        xi[1] = rr * sin(2.0 * OR_PI * ub);
-      }
-      if (D == 3) {
-        philox_draw(cfg->seed, (uint32_t)i, TAG_SAMPLE | 2u, j, r2);
-        double ua = oracle_uniform52(r2[0], r2[1]), ub = oracle_uniform52(r2[2], r2[3]);
-        double rr = sqrt(-2.0 * log(ua));
-        xi[2] = rr * cos(2.0 * OR_PI * ub);
-        xi[3] = rr * sin(2.0 * OR_PI * ub);
-      }
-      for (int a = 0; a < D; ++a) {
-        double s = 0.0;
-        if (Kj > 0) {
-          s = cs[z].mu[a];
-          for (int b = 0; b <= a; ++b) s += cs[z].Lc[a][b] * xi[b];
-        }
-        v_out[(int64_t)a * Nout + g] = s;
-      }
+      for (int a = 0; a < D; ++a) v_out[(int64_t)a * Nout + g] = vv[a];
       alpha_out[g] = W[j] / (double)n;
     }
   }
@@ -768,53 +841,138 @@ int oracle_reconstruct(const oracle_cfg *cfg, int64_t C, const int32_t *K, const
   if (dA_out) memcpy(dA_out, dA, sizeof(double) * C);
   free(rho); free(rhs); free(dA);
 
-  /* 3. Lemons projection (Sec. 2.4.2), after the weight correction:
-   *    v' = a (v + beta), with targets p, E from the mixture and
-   *    N' = sum alpha', p' = sum alpha' v, E' = 1/2 sum alpha' |v|^2 (eq. beta),
-   *    a = sqrt((2 E N' - p^2) / (2 E' N' - p'^2)), beta = (p - a p')/(a N')
-   *    (eq. alpha).  A non-positive numerator skips the cell (Sec. 2.4.2:
-   *    "forgo the local moment-matching step"). */
+  /* 3. Lemons projection (Sec. 2.4.2), after the weight correction */
+  lemons_project(cfg, C, K, params, W, out_off, alpha_out, v_out, status_out);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The 2D periodic mesh (Sec. 2.4.1 in two dimensions, the geometry of the  */
+/* 2D-3V Weibel runs of Sec. 3.2).  Cells and nodes are numbered            */
+/* j = jy Cx + jx; node (ix, iy) sits at the cell centre                    */
+/* ((ix + 1/2) dx, (iy + 1/2) dy); the shape function is the tensor product */
+/* S(x) S(y) of the 1D B-spline of the chosen order, so a particle of cell  */
+/* (jx, jy) reaches the 3 x 3 nodes around its cell.                        */
+/* ------------------------------------------------------------------------ */
+typedef struct oracle_mesh2d {
+  int64_t Cx, Cy;
+  double Lx, Ly;
+} oracle_mesh2d;
+
+#define OR_MAX_DENSE2D 2048 /* the direct solve below is dense: C <= this */
+
+/* rho_i = (1 / (dx dy)) sum_p q alpha_p S(x_i - x_p) S(y_i - y_p) */
+static void deposit2d(const oracle_cfg *cfg, const oracle_mesh2d *m, const int64_t *cell_off,
+                      const double *x, const double *y, const double *alpha, double *rho) {
+  const int64_t Cx = m->Cx, Cy = m->Cy, C = Cx * Cy;
+  const double dx = m->Lx / (double)Cx, dy = m->Ly / (double)Cy;
+  for (int64_t i = 0; i < C; ++i) rho[i] = 0.0;
+  for (int64_t j = 0; j < C; ++j) {
+    const int64_t jx = j % Cx, jy = j / Cx;
+    for (int64_t p = cell_off[j]; p < cell_off[j + 1]; ++p)
+      for (int64_t iy = jy - 1; iy <= jy + 1; ++iy)
+        for (int64_t ix = jx - 1; ix <= jx + 1; ++ix) {
+          const double xi = ((double)ix + 0.5) * dx, yi = ((double)iy + 0.5) * dy;
+          const double w = shape_S(cfg->shape_order, (xi - x[p]) / dx) *
+                           shape_S(cfg->shape_order, (yi - y[p]) / dy);
+          rho[wrap(iy, Cy) * Cx + wrap(ix, Cx)] += cfg->q * alpha[p] * w / (dx * dy);
+        }
+  }
+}
+
+/* Exported: the 2D charge density of particles sorted by cell */
+int oracle_deposit2d(const oracle_cfg *cfg, const oracle_mesh2d *m, const int64_t *cell_off,
+                     const double *x, const double *y, const double *alpha, double *rho) {
+  if (m->Cx < 1 || m->Cy < 1) return -1;
+  deposit2d(cfg, m, cell_off, x, y, alpha, rho);
+  return 0;
+}
+
+/* Exported: reconstruction on the 2D mesh (Sec. 2.4): positions uniform in
+ * the cell (x from the 1D sampler's u0, y from Philox block 3:
+ * counter (i, TAG_SAMPLE | 3, j), words 0-1), velocities and weights as in
+ * 1D; Gauss' law with M_ij = sum_{p in j} q S(x_i - x_p) S(y_i - y_p) (a
+ * 9-point column per cell) and M dA = dx dy (rho' - rho), solved directly
+ * (dense Gaussian elimination with partial pivoting, C <= OR_MAX_DENSE2D;
+ * a cell with no resampled particle gets a unit diagonal); then the weight
+ * update and the Lemons projection, as in 1D.  xy_out [2][Nout]. */
+int oracle_reconstruct2d(const oracle_cfg *cfg, const oracle_mesh2d *m, const int32_t *K,
+                         const double *params, const double *W, const double *rho_target,
+                         const int64_t *out_off, double *xy_out, double *v_out, double *alpha_out,
+                         uint32_t *status_out, double *dA_out, int nthreads) {
+  const int D = cfg->D;
+  const size_t P = (size_t)P_of(D);
+  const int64_t Cx = m->Cx, Cy = m->Cy, C = Cx * Cy;
+  if (D != 1 && D != 3) return -1;
+  if (Cx < 1 || Cy < 1) return -1;
+  if (C > OR_MAX_DENSE2D) return -2;
+  const int64_t Nout = out_off[C];
+  const double dx = m->Lx / (double)Cx, dy = m->Ly / (double)Cy;
+  double *x_out = xy_out, *y_out = xy_out + Nout;
+  for (int64_t j = 0; j < C; ++j) status_out[j] = 0;
+
+  /* 1. sampling */
 #ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 1)
 #endif
   for (int64_t j = 0; j < C; ++j) {
     int64_t n = out_off[j + 1] - out_off[j];
-    if (n == 0 || K[j] == 0) continue;
+    if (n == 0) continue;
+    const int64_t jx = j % Cx, jy = j / Cx;
     comp cs[OR_MAXK];
-    load_params(D, K[j], params + (size_t)j * cfg->Kmax * P, cs);
-    double pt[OR_MAXD] = {0}, Et = 0.0;
-    for (int k = 0; k < K[j]; ++k) {
-      double tr = 0.0, mm = 0.0;
-      for (int a = 0; a < D; ++a) {
-        pt[a] += W[j] * cs[k].w * cs[k].mu[a];
-        tr += cs[k].S[a][a];
-        mm += cs[k].mu[a] * cs[k].mu[a];
-      }
-      Et += 0.5 * W[j] * cs[k].w * (tr + mm);
+    int Kj = K[j];
+    load_sampling_cell(D, Kj, params + (size_t)j * cfg->Kmax * P, cs);
+    if (Kj == 0) status_out[j] |= ST_NO_MIXTURE;
+    for (int64_t i = 0; i < n; ++i) {
+      int64_t g = out_off[j] + i;
+      double vv[OR_MAXD];
+      uint32_t r3[4];
+      const double u0 = sample_one(cfg, D, cs, Kj, j, i, vv);
+      philox_draw(cfg->seed, (uint32_t)i, TAG_SAMPLE | 3u, j, r3);
+      const double uy = oracle_uniform52(r3[0], r3[1]);
+      x_out[g] = ((double)jx + u0) * dx;
+      y_out[g] = ((double)jy + uy) * dy;
+      for (int a = 0; a < D; ++a) v_out[(int64_t)a * Nout + g] = vv[a];
+      alpha_out[g] = W[j] / (double)n;
     }
-    double Np = 0.0, pp[OR_MAXD] = {0}, Ep = 0.0;
-    for (int64_t p = out_off[j]; p < out_off[j + 1]; ++p) {
-      Np += alpha_out[p];
-      for (int a = 0; a < D; ++a) {
-        double va = v_out[(int64_t)a * Nout + p];
-        pp[a] += alpha_out[p] * va;
-        Ep += 0.5 * alpha_out[p] * va * va;
-      }
-    }
-    double pt2 = 0.0, pp2 = 0.0;
-    for (int a = 0; a < D; ++a) { pt2 += pt[a] * pt[a]; pp2 += pp[a] * pp[a]; }
-    double num = 2.0 * Et * Np - pt2;
-    double den = 2.0 * Ep * Np - pp2;
-    if (!(num > 0.0) || !(den > 0.0) || !(Np > 0.0)) { status_out[j] |= ST_PROJ_SKIPPED; continue; }
-    double aa = sqrt(num / den);
-    double beta[OR_MAXD];
-    for (int a = 0; a < D; ++a) beta[a] = (pt[a] - aa * pp[a]) / (aa * Np);
-    for (int64_t p = out_off[j]; p < out_off[j + 1]; ++p)
-      for (int a = 0; a < D; ++a) {
-        double *va = &v_out[(int64_t)a * Nout + p];
-        *va = aa * (*va + beta[a]);
-      }
   }
+
+  /* 2. Gauss' law */
+  double *rho = (double *)malloc(sizeof(double) * C);
+  double *rhs = (double *)malloc(sizeof(double) * C);
+  double *dA = (double *)malloc(sizeof(double) * C);
+  double *A = (double *)calloc((size_t)C * C, sizeof(double));
+  deposit2d(cfg, m, out_off, x_out, y_out, alpha_out, rho);
+  for (int64_t i = 0; i < C; ++i) rhs[i] = dx * dy * (rho_target[i] - rho[i]);
+  for (int64_t j = 0; j < C; ++j) {
+    const int64_t jx = j % Cx, jy = j / Cx;
+    for (int64_t p = out_off[j]; p < out_off[j + 1]; ++p)
+      for (int64_t iy = jy - 1; iy <= jy + 1; ++iy)
+        for (int64_t ix = jx - 1; ix <= jx + 1; ++ix) {
+          const double xi = ((double)ix + 0.5) * dx, yi = ((double)iy + 0.5) * dy;
+          const double w = shape_S(cfg->shape_order, (xi - x_out[p]) / dx) *
+                           shape_S(cfg->shape_order, (yi - y_out[p]) / dy);
+          A[(wrap(iy, Cy) * Cx + wrap(ix, Cx)) * C + j] += cfg->q * w;
+        }
+    if (out_off[j + 1] == out_off[j]) {
+      A[j * C + j] = 1.0;
+      status_out[j] |= ST_MM_EMPTY_COL;
+    }
+  }
+  int rc = dense_solve((int)C, A, rhs, dA);
+  free(A);
+  if (rc != 0) { free(rho); free(rhs); free(dA); return -3; }
+  for (int64_t j = 0; j < C; ++j)
+    for (int64_t p = out_off[j]; p < out_off[j + 1]; ++p) {
+      alpha_out[p] += dA[j];
+      if (!(alpha_out[p] > 0.0)) status_out[j] |= ST_NEG_WEIGHT;
+    }
+  if (dA_out) memcpy(dA_out, dA, sizeof(double) * C);
+  free(rho); free(rhs); free(dA);
+
+  /* 3. Lemons projection */
+  lemons_project(cfg, C, K, params, W, out_off, alpha_out, v_out, status_out);
   return 0;
 }
 

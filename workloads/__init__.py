@@ -18,6 +18,8 @@ Layout of every workload (all numpy arrays):
   x        [Ntot] f64    absolute positions, x in [j*dx, (j+1)*dx)
   v        [D, Ntot]     velocities, SoA, float32 or float64
   alpha    [Ntot] f64    particle weights
+  y        [Ntot] f64    (2D meshes only) second coordinate; cells are
+                         numbered j = jy * Cx + jx
 """
 from __future__ import annotations
 
@@ -37,6 +39,7 @@ class Workload:
     v: np.ndarray
     alpha: np.ndarray
     params: dict = field(default_factory=dict)
+    y: np.ndarray | None = None
 
     @property
     def C(self) -> int:
@@ -199,12 +202,54 @@ def lognormal_1d3v(C=262144, median=512, sigma=0.47, clip=(16, 8192),
                     method_params(3, Kmax, 2, float(C)))
 
 
+def weibel_2d3v(Cx=16, Cy=16, ppc=512, counts=None, Lx=10.0, Ly=10.0, eps=0.05,
+                seed=GEN_SEED_BASE + 5, v_dtype=np.float32, Kmax=8, shape_order=2):
+    """2D-3V cells of the Weibel set-up of Sec. 3.2: a doubly periodic
+    Lx x Ly = 10 x 10 domain (skin depths) of Cx x Cy cells (16 x 16 and
+    128-1024 particles per cell in the paper), v_th,x = 0.1 and
+    v_th,y = v_th,z = 0.3 (T_perp/T_par = 9), here relaxed per cell by a
+    factor U[0.8, 1] on the perpendicular speed with a drift N(0, 0.01^2)^3
+    (a state late in the linear phase).  Positions: uniform in each cell,
+    accepted with probability (1 + eps cos(2 pi x/Lx) cos(2 pi y/Ly)) /
+    (1 + eps) so that every cell keeps its count.  Cells are numbered
+    j = jy * Cx + jx; params carries Cx, Cy, Lx, Ly."""
+    rng = np.random.default_rng(seed)
+    C = Cx * Cy
+    n = np.full(C, ppc, dtype=np.int64) if counts is None else np.asarray(counts, dtype=np.int64)
+    dx, dy = Lx / Cx, Ly / Cy
+    cell = np.repeat(np.arange(C, dtype=np.int64), n)
+    jx, jy = cell % Cx, cell // Cx
+    x = np.empty(cell.shape[0])
+    y = np.empty(cell.shape[0])
+    todo = np.arange(cell.shape[0])
+    while todo.size:
+        ux, uy = rng.random(todo.size), rng.random(todo.size)
+        xt = (jx[todo] + ux) * dx
+        yt = (jy[todo] + uy) * dy
+        acc = rng.random(todo.size) * (1 + eps) < 1 + eps * np.cos(2 * math.pi * xt / Lx) * np.cos(
+            2 * math.pi * yt / Ly)
+        x[todo[acc]] = np.minimum(xt[acc], np.nextafter((jx[todo[acc]] + 1) * dx, -np.inf))
+        y[todo[acc]] = np.minimum(yt[acc], np.nextafter((jy[todo[acc]] + 1) * dy, -np.inf))
+        todo = todo[~acc]
+    vperp = 0.3 * rng.uniform(0.8, 1.0, C)
+    drift = 0.01 * rng.standard_normal((C, 3))
+    z = rng.standard_normal((3, cell.shape[0]))
+    v = np.empty((3, cell.shape[0]))
+    v[0] = drift[cell, 0] + 0.1 * z[0]
+    v[1] = drift[cell, 1] + vperp[cell] * z[1]
+    v[2] = drift[cell, 2] + vperp[cell] * z[2]
+    params = method_params(3, Kmax, shape_order, Lx)
+    params.update(Cx=int(Cx), Cy=int(Cy), Lx=float(Lx), Ly=float(Ly))
+    return Workload("weibel_2d3v", _offsets(n), x, np.ascontiguousarray(v.astype(v_dtype)),
+                    np.ones(x.shape[0]), params, y)
+
+
 def with_weights(wl: Workload, seed=7, lo=0.5, hi=1.5) -> Workload:
     """Copy of ``wl`` with non-identical weights alpha ~ U[lo, hi] (the
     variable-weight case of Sec. 3.2)."""
     rng = np.random.default_rng(seed)
     a = rng.uniform(lo, hi, wl.ntot)
-    return Workload(wl.name + "_varw", wl.cell_off, wl.x, wl.v, a, dict(wl.params))
+    return Workload(wl.name + "_varw", wl.cell_off, wl.x, wl.v, a, dict(wl.params), wl.y)
 
 
 # Named workloads: the first is small enough for the oracle to fit in
@@ -220,6 +265,8 @@ def get(name: str, **kw) -> Workload:
         return bimaxwellian_1d3v(**kw)
     if name == "lognormal_1d3v":
         return lognormal_1d3v(**kw)
+    if name == "weibel_2d3v":
+        return weibel_2d3v(**kw)
     raise KeyError(name)
 
 
