@@ -51,6 +51,7 @@ extern "C" {
 #define GM_ST_NEG_WEIGHT 0x200u   /* a corrected weight alpha' <= 0 */
 #define GM_ST_MM_EMPTY_COL 0x400u /* no resampled particle: unit mass-matrix column */
 #define GM_ST_NO_MIXTURE 0x800u   /* K[j] = 0 but particles were requested */
+#define GM_ST_MM_NOT_CONVERGED 0x1000u /* 2D mass-matrix solve stopped at its iteration cap */
 
 typedef struct gm_config {
   int32_t D;           /* velocity dimensions: 1 or 3 */
@@ -93,6 +94,8 @@ typedef struct gm_config {
  *      final parameters, with the normalised weights); sweeps_out [C] int32;
  *      kwork_out [C] int32 (component E-steps performed, may be NULL);
  *      status_out [C] uint32.
+ *      x and rho_target_out may both be NULL: no 1D deposit (a 2D mesh
+ *      takes its target charge from gm_deposit_2d).
  * E-step densities and responsibilities are FP32; the per-component
  * statistics are FP32 per thread and warp and summed across warps in the
  * M-step's precision (cfg->precision); component means are accumulated in
@@ -128,6 +131,58 @@ int gm_reconstruct(const gm_config* cfg, int64_t C, const int32_t* K, const doub
                    const double* W, const double* rho_target, int64_t n_out,
                    const int64_t* out_off, double* x_out, double* v_out, double* alpha_out,
                    uint32_t* status_out, double* dA_out, void* stream);
+
+/*
+ * The 2D doubly periodic mesh (the geometry of the paper's 2D-3V Weibel
+ * runs, Sec. 3.2): Cx x Cy cells of dx = Lx / Cx, dy = Ly / Cy, numbered
+ * j = jy * Cx + jx (particles sorted by that index, CSR as everywhere);
+ * node (ix, iy) at the cell centre ((ix + 1/2) dx, (iy + 1/2) dy); the
+ * shape function is the tensor product S(x) S(y) of cfg->shape_order.
+ * cfg->L is not used by these calls.
+ */
+typedef struct gm_mesh2d {
+  int64_t Cx, Cy; /* cells along x and y (1 .. 2^24 each, Cx * Cy < 2^31) */
+  double Lx, Ly;  /* domain lengths */
+} gm_mesh2d;
+
+/*
+ * gm_deposit_2d -- charge density on the 2D mesh (Sec. 2.4.1):
+ * rho_i = (q / (dx dy)) sum_p alpha_p S(x_i - x_p) S(y_i - y_p).
+ * In: cell_off [Cx Cy + 1] int64; x, y [n] f64 (each particle inside its
+ * cell); alpha [n] f64 or NULL (unit weights).  Out: rho_out [Cy][Cx] f64
+ * (node jy * Cx + jx).  This is the target rho' of the 2D reconstruction
+ * when called on the particles before compression.
+ */
+int gm_deposit_2d(const gm_config* cfg, const gm_mesh2d* mesh, const int64_t* cell_off,
+                  const double* x, const double* y, const double* alpha, double* rho_out,
+                  void* stream);
+
+/*
+ * gm_reconstruct_2d -- gm_reconstruct on the 2D mesh (Sec. 2.4).
+ *
+ * Positions uniform in the cell: x from the same uniform as in 1D, y from
+ * Philox block 3 (counter (i, 0x53000003, cell), words 0-1); velocities and
+ * weights W_j / N'_j as in gm_reconstruct.  Gauss' law: alpha'_p = alpha_p +
+ * dA_j with M dA = dx dy (rho' - rho), M_ij = q sum_{p in j} S(x_i - x_p)
+ * S(y_i - y_p) (eqs. p-weight-correction, new-p-weight; a 3 x 3 column per
+ * cell).  In 2D with the quadratic B-spline M is not diagonally dominant; it
+ * is solved by defect correction preconditioned with the matrix of
+ * uniformly filled cells (cyclic tridiagonal solves along x and along y),
+ * until max |residual| <= 1e-14 max |dx dy rho'| or 64 iterations
+ * (GM_ST_MM_NOT_CONVERGED on every cell).  A cell without resampled
+ * particles gets a unit column (GM_ST_MM_EMPTY_COL), as in 1D.  Then the
+ * Lemons projection per cell, as in gm_reconstruct.
+ *
+ * In: as gm_reconstruct with rho_target [Cy][Cx] and out_off [Cx Cy + 1]
+ * (cfg->q must be nonzero).  Out: x_out, y_out [n_out] f64, v_out
+ * [D][n_out] f64, alpha_out [n_out] f64, status_out [Cx Cy] uint32, dA_out
+ * [Cx Cy] f64 (may be NULL).
+ */
+int gm_reconstruct_2d(const gm_config* cfg, const gm_mesh2d* mesh, const int32_t* K,
+                      const double* params, const double* W, const double* rho_target,
+                      int64_t n_out, const int64_t* out_off, double* x_out, double* y_out,
+                      double* v_out, double* alpha_out, uint32_t* status_out, double* dA_out,
+                      void* stream);
 
 /*
  * gm_moments -- per-cell particle moments (the quantities of Sec. 2.3.1 and

@@ -228,9 +228,9 @@ static int compress_impl(const gm_config* cfg, int64_t C, int64_t n_particles,
   if (cfg->max_sweeps < 1) return fail(GM_ERR_ARG, "max_sweeps must be >= 1");
   if (!(cfg->tol >= 0.0)) return fail(GM_ERR_ARG, "tol must be >= 0");
   if (C == 0) return GM_OK;
-  if (!cell_off || !x || !v || !alpha || !K_out || !params_out || !W_out || !rho_target_out ||
-      !lnL_out || !status_out)
+  if (!cell_off || !v || !alpha || !K_out || !params_out || !W_out || !lnL_out || !status_out)
     return fail(GM_ERR_ARG, "a required pointer is NULL");
+  if (!x != !rho_target_out) return fail(GM_ERR_ARG, "x and rho_target_out must be both set or both NULL");
   int sms = 0;
   if ((rc = check_device(&sms))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
@@ -289,9 +289,11 @@ static int compress_impl(const gm_config* cfg, int64_t C, int64_t n_particles,
   e = D == 1 ? gmcr::launch_em1(p, nt, fp64_mstep, v_is_f64, smem, (int)grid, s)
              : gmcr::launch_em3(p, nt, fp64_mstep, v_is_f64, smem, (int)grid, s);
   if (e != cudaSuccess) return cuda_fail(e, "EM kernel launch");
-  e = gmcr::launch_deposit(C, cell_off, x, alpha, cfg->L / (double)C, cfg->q, cfg->shape_order,
-                           part, rho_target_out, s);
-  if (e != cudaSuccess) return cuda_fail(e, "deposit launch");
+  if (x) {
+    e = gmcr::launch_deposit(C, cell_off, x, alpha, cfg->L / (double)C, cfg->q, cfg->shape_order,
+                             part, rho_target_out, s);
+    if (e != cudaSuccess) return cuda_fail(e, "deposit launch");
+  }
   return GM_OK;
 }
 
@@ -328,9 +330,9 @@ int gm_compress_standard(const gm_config* cfg, const gm_std_opts* opts, int64_t 
   if (cfg->max_sweeps < 1) return fail(GM_ERR_ARG, "max_sweeps must be >= 1");
   if (!(cfg->tol >= 0.0)) return fail(GM_ERR_ARG, "tol must be >= 0");
   if (C == 0) return GM_OK;
-  if (!cell_off || !x || !v || !alpha || !K_out || !params_out || !W_out || !rho_target_out ||
-      !lnL_out || !status_out)
+  if (!cell_off || !v || !alpha || !K_out || !params_out || !W_out || !lnL_out || !status_out)
     return fail(GM_ERR_ARG, "a required pointer is NULL");
+  if (!x != !rho_target_out) return fail(GM_ERR_ARG, "x and rho_target_out must be both set or both NULL");
   int sms = 0;
   if ((rc = check_device(&sms))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
@@ -383,9 +385,11 @@ int gm_compress_standard(const gm_config* cfg, const gm_std_opts* opts, int64_t 
   p.seed = cfg->seed;
   e = gmcr::launch_std(D, p, v_is_f64, smem, sms, s);
   if (e != cudaSuccess) return cuda_fail(e, "standard EM kernel launch");
-  e = gmcr::launch_deposit(C, cell_off, x, alpha, cfg->L / (double)C, cfg->q, cfg->shape_order,
-                           part, rho_target_out, s);
-  if (e != cudaSuccess) return cuda_fail(e, "deposit launch");
+  if (x) {
+    e = gmcr::launch_deposit(C, cell_off, x, alpha, cfg->L / (double)C, cfg->q, cfg->shape_order,
+                             part, rho_target_out, s);
+    if (e != cudaSuccess) return cuda_fail(e, "deposit launch");
+  }
   return GM_OK;
 }
 
@@ -437,6 +441,62 @@ int gm_reconstruct(const gm_config* cfg, int64_t C, const int32_t* K, const doub
                                            cfg->shape_order, x_out, v_out, alpha_out, status_out,
                                            dA_out, ws, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "reconstruct launch");
+  return GM_OK;
+}
+
+static int check_mesh2d(const gm_mesh2d* mesh) {
+  if (!mesh) return fail(GM_ERR_ARG, "mesh is NULL");
+  if (mesh->Cx < 1 || mesh->Cy < 1 || mesh->Cx > ((int64_t)1 << 24) || mesh->Cy > ((int64_t)1 << 24) ||
+      mesh->Cx * mesh->Cy >= ((int64_t)1 << 31))
+    return fail(GM_ERR_ARG, "mesh size out of range (%lld x %lld)", (long long)mesh->Cx,
+                (long long)mesh->Cy);
+  if (!(mesh->Lx > 0.0) || !(mesh->Ly > 0.0)) return fail(GM_ERR_ARG, "Lx and Ly must be positive");
+  return GM_OK;
+}
+
+int gm_deposit_2d(const gm_config* cfg, const gm_mesh2d* mesh, const int64_t* cell_off,
+                  const double* x, const double* y, const double* alpha, double* rho_out,
+                  void* stream) {
+  g_err.clear();
+  int rc = check_cfg(cfg);
+  if (rc) return rc;
+  if ((rc = check_mesh2d(mesh))) return rc;
+  if (!cell_off || !x || !y || !rho_out) return fail(GM_ERR_ARG, "a required pointer is NULL");
+  if ((rc = check_device(nullptr))) return rc;
+  const int64_t C = mesh->Cx * mesh->Cy;
+  void* ws = nullptr;
+  if ((rc = ws_get(align256((size_t)9 * C * sizeof(double)), &ws))) return rc;
+  cudaError_t e = gmcr::launch_deposit2d(mesh->Cx, mesh->Cy, cell_off, x, y, alpha,
+                                         mesh->Lx / (double)mesh->Cx, mesh->Ly / (double)mesh->Cy,
+                                         cfg->q, cfg->shape_order, (double*)ws, rho_out,
+                                         (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "2D deposit launch");
+  return GM_OK;
+}
+
+int gm_reconstruct_2d(const gm_config* cfg, const gm_mesh2d* mesh, const int32_t* K,
+                      const double* params, const double* W, const double* rho_target,
+                      int64_t n_out, const int64_t* out_off, double* x_out, double* y_out,
+                      double* v_out, double* alpha_out, uint32_t* status_out, double* dA_out,
+                      void* stream) {
+  g_err.clear();
+  int rc = check_cfg(cfg);
+  if (rc) return rc;
+  if ((rc = check_mesh2d(mesh))) return rc;
+  if (!(cfg->q != 0.0)) return fail(GM_ERR_ARG, "q must be nonzero");
+  if (n_out < 0 || n_out >= (int64_t)1 << 40) return fail(GM_ERR_ARG, "n_out out of range");
+  if (!K || !params || !W || !rho_target || !out_off || !status_out)
+    return fail(GM_ERR_ARG, "a required pointer is NULL");
+  if (n_out > 0 && (!x_out || !y_out || !v_out || !alpha_out))
+    return fail(GM_ERR_ARG, "an output particle pointer is NULL");
+  if ((rc = check_device(nullptr))) return rc;
+  void* ws = nullptr;
+  if ((rc = ws_get(gmcr::reconstruct2d_ws_bytes(cfg->D, mesh->Cx, mesh->Cy), &ws))) return rc;
+  cudaError_t e = gmcr::launch_reconstruct2d(
+      cfg->D, mesh->Cx, mesh->Cy, cfg->Kmax, K, params, W, rho_target, n_out, out_off, cfg->seed,
+      mesh->Lx / (double)mesh->Cx, mesh->Ly / (double)mesh->Cy, cfg->q, cfg->shape_order, x_out,
+      y_out, v_out, alpha_out, status_out, dA_out, ws, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "2D reconstruct launch");
   return GM_OK;
 }
 

@@ -42,6 +42,20 @@ cudaError_t launch_reconstruct(int D, int64_t C, int Kmax, const int32_t* K, con
                                int order, double* x_out, double* v_out, double* alpha_out,
                                uint32_t* status_out, double* dA_user, void* ws, cudaStream_t s);
 
+// the 2D periodic mesh (gm_mesh2d.cu)
+constexpr int kMesh2dMaxIter = 64;    // defect-correction iterations, at most
+constexpr double kMesh2dTol = 1e-14;  // max |residual| / max |dx dy rho'| to stop
+cudaError_t launch_deposit2d(int64_t Cx, int64_t Cy, const int64_t* cell_off, const double* x,
+                             const double* y, const double* alpha, double dx, double dy, double q,
+                             int order, double* part, double* rho, cudaStream_t s);
+size_t reconstruct2d_ws_bytes(int D, int64_t Cx, int64_t Cy);
+cudaError_t launch_reconstruct2d(int D, int64_t Cx, int64_t Cy, int Kmax, const int32_t* K,
+                                 const double* prm, const double* W, const double* rho_target,
+                                 int64_t n_out, const int64_t* out_off, uint64_t seed, double dx,
+                                 double dy, double q, int order, double* x_out, double* y_out,
+                                 double* v_out, double* alpha_out, uint32_t* status_out,
+                                 double* dA_user, void* ws, cudaStream_t s);
+
 // BF16 tcgen05 GEMM: C = A B^T (+bias, ReLU, mask), see tc_gemm.cu
 size_t tc_gemm_smem(int bn);
 cudaError_t launch_tc_gemm(const void* A, const void* B, int M, int N, int K, int lda, int ldb,

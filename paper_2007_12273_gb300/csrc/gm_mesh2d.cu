@@ -1,0 +1,475 @@
+// gm_mesh2d.cu -- the reconstruction on a 2D doubly periodic mesh (Sec. 2.4
+// with the tensor-product shape function S(x) S(y), the geometry of the
+// 2D-3V Weibel runs of Sec. 3.2).  Cells and nodes are numbered
+// j = jy Cx + jx; node (ix, iy) sits at the cell centre.
+//
+// Sampling, the per-cell velocity sums and the Lemons projection are those
+// of the 1D path (recon_sampler.cuh), with one more uniform per particle for
+// y.  The mass matrix M_ij = q sum_{p in j} S(x_i - x_p) S(y_i - y_p) has a
+// 3 x 3 column per cell.  With the quadratic B-spline it is not diagonally
+// dominant in 2D (a uniformly filled cell keeps (2/3)^2 of its weight on
+// its own node), so M dA = dx dy (rho' - rho) is solved by defect
+// correction with the operator of uniformly filled cells as preconditioner:
+// P = (Tx (x) Ty) diag(q N'_j), T the circulant tridiagonal matrix of the
+// mean shape weights (1/6, 2/3, 1/6; CIC 1/8, 3/4, 1/8), so that P^-1 is a
+// cyclic tridiagonal solve along every row and then along every column.
+// Each iteration is a residual pass, an x sweep and a y sweep (three
+// launches, each a no-op once the residual is below the tolerance).  A cell
+// without resampled particles has a unit column: its unknown appears in its
+// own row only, so it is left out of the iteration and found afterwards
+// from its row.
+#include "recon_sampler.cuh"
+
+namespace gmcr {
+
+// shape weights of an in-cell offset s = u - 1/2 on the nodes -1, 0, +1 of
+// its cell (the B-spline S(a - s)): quadratic (1/2 - s)^2 / 2, 3/4 - s^2,
+// (1/2 + s)^2 / 2; CIC max(-s, 0), 1 - |s|, max(s, 0)
+__device__ __forceinline__ void shape3(int order, double s, double (&w)[3]) {
+  if (order == 1) {
+    w[0] = s < 0.0 ? -s : 0.0;
+    w[2] = s > 0.0 ? s : 0.0;
+    w[1] = 1.0 - (w[0] + w[2]);
+  } else {
+    const double a = 0.5 - s, b = 0.5 + s;
+    w[0] = 0.5 * a * a;
+    w[1] = 0.75 - s * s;
+    w[2] = 0.5 * b * b;
+  }
+}
+
+// part[j][3 (b + 1) + (a + 1)] = sum_{p in j} alpha_p S(x-weight a) S(y-weight b):
+// what cell j's particles put on node (jx + a, jy + b).  One warp per cell;
+// alpha = NULL means unit weights.
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) deposit2d_partials_kernel(
+    int64_t Cx, int64_t C, const int64_t* cell_off, const double* x, const double* y,
+    const double* alpha, double inv_dx, double inv_dy, int order, double* part) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int64_t j = (int64_t)blockIdx.x * NW + wid; j < C; j += (int64_t)gridDim.x * NW) {
+    const int64_t jx = j % Cx, jy = j / Cx;
+    const int64_t o = cell_off[j], n = cell_off[j + 1] - o;
+    double acc[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) acc[t] = 0.0;
+    for (int64_t p = lane; p < n; p += 32) {
+      double wx[3], wy[3];
+      shape3(order, cell_frac(x[o + p], jx, inv_dx) - 0.5, wx);
+      shape3(order, cell_frac(y[o + p], jy, inv_dy) - 0.5, wy);
+      const double al = alpha ? alpha[o + p] : 1.0;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const double ab = al * wy[b];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc[3 * b + a] = fma(ab, wx[a], acc[3 * b + a]);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 9; ++t) acc[t] = warp_sum(acc[t]);
+    if (lane == 0)
+#pragma unroll
+      for (int t = 0; t < 9; ++t) part[9 * j + t] = acc[t];
+  }
+}
+
+// the cell whose entry (a, b) lands on node (ix, iy): (ix - a, iy - b), periodic
+__device__ __forceinline__ int64_t src_cell(int64_t ix, int64_t iy, int a, int b, int64_t Cx,
+                                            int64_t Cy) {
+  int64_t sx = ix - a, sy = iy - b;
+  sx = sx < 0 ? sx + Cx : (sx >= Cx ? sx - Cx : sx);
+  sy = sy < 0 ? sy + Cy : (sy >= Cy ? sy - Cy : sy);
+  return sy * Cx + sx;
+}
+
+// rho_i = q / (dx dy) sum over the 3 x 3 cells around node i of their entry on it
+__global__ void deposit2d_combine_kernel(int64_t Cx, int64_t Cy, const double* part,
+                                         double q_over_dv, double* rho) {
+  const int64_t C = Cx * Cy;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < C;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ix = i % Cx, iy = i / Cx;
+    double s = 0.0;
+    for (int b = -1; b <= 1; ++b)
+      for (int a = -1; a <= 1; ++a) s += part[9 * src_cell(ix, iy, a, b, Cx, Cy) + 3 * (b + 1) + (a + 1)];
+    rho[i] = q_over_dv * s;
+  }
+}
+
+// Pass 1, one warp per cell: cstat[j] = [9 unit-weight shape sums (layout of
+// part above), sum w (D), sum |w|^2] of the resampled particles
+template <int D, int NW>
+__global__ void __launch_bounds__(NW * 32) recon2d_stats_kernel(
+    int64_t Cx, int64_t C, int Kmax, const int32_t* K, const double* prm, const int64_t* out_off,
+    uint64_t seed, int order, double* cstat) {
+  constexpr int NV = 9 + D + 1;
+  __shared__ RecCell<D> rcs[NW];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  RecCell<D>& rc = rcs[wid];
+  for (int64_t j = (int64_t)blockIdx.x * NW + wid; j < C; j += (int64_t)gridDim.x * NW) {
+    load_cell<D>(rc, j, Kmax, K, prm, lane);
+    __syncwarp();
+    const int64_t o = out_off[j], n = out_off[j + 1] - o;
+    double acc[NV];
+#pragma unroll
+    for (int t = 0; t < NV; ++t) acc[t] = 0.0;
+    for (int64_t i = lane; i < n; i += 32) {
+      uint64_t m0;
+      double w[D], wx[3], wy[3];
+      sample_particle<D>(rc, j, i, seed, m0, w);
+      shape3(order, centred52(m0), wx);
+      shape3(order, centred52(sample_y_bits(j, i, seed)), wy);
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc[3 * b + a] = fma(wy[b], wx[a], acc[3 * b + a]);
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        acc[9 + d] += w[d];
+        acc[9 + D] = fma(w[d], w[d], acc[9 + D]);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < NV; ++t) acc[t] = warp_sum(acc[t]);
+    if (lane == 0)
+#pragma unroll
+      for (int t = 0; t < NV; ++t) cstat[(size_t)j * NV + t] = acc[t];
+    __syncwarp();
+  }
+}
+
+// order-preserving bits of a non-negative double (for atomicMax)
+__device__ __forceinline__ unsigned long long pos_bits(double v) {
+  return (unsigned long long)__double_as_longlong(v);
+}
+
+struct Mesh2dSolve {
+  int64_t Cx, Cy;
+  const double* cstat;   // [C][NV]
+  int nv;                // 9 + D + 1
+  const int64_t* out_off;
+  double q;
+  double* b;             // [C] right-hand side dx dy (rho' - rho)
+  double* dA;            // [C]
+  double* r;             // [C] residual
+  double* t;             // [C] after the x sweep
+  unsigned long long* norm;  // [max_iter + 1] max |r| per iteration (as bits)
+  unsigned long long* scale; // [1] max |dx dy rho'| (as bits)
+  const double* tx;      // x-direction factors: [4][Cx] inv_m, cp, z and [2] (fact, vlast)
+  const double* ty;
+  double tol;
+};
+
+// rows of the right-hand side, the iteration's norms cleared, dA = 0
+__global__ void assemble2d_kernel(Mesh2dSolve m, const double* W, const double* rho_target,
+                                  double dv, int max_iter) {
+  const int64_t C = m.Cx * m.Cy;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < C;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ix = i % m.Cx, iy = i / m.Cx;
+    double s = 0.0;
+    for (int b = -1; b <= 1; ++b)
+      for (int a = -1; a <= 1; ++a) {
+        const int64_t src = src_cell(ix, iy, a, b, m.Cx, m.Cy);
+        const int64_t ns = m.out_off[src + 1] - m.out_off[src];
+        if (ns > 0) s += (W[src] / (double)ns) * m.cstat[(size_t)src * m.nv + 3 * (b + 1) + (a + 1)];
+      }
+    const double tgt = dv * rho_target[i];
+    m.b[i] = tgt - m.q * s;
+    m.dA[i] = 0.0;
+    atomicMax(m.scale, pos_bits(fabs(tgt)));
+    if (i <= max_iter) m.norm[i] = 0ull;
+  }
+}
+
+// r_i = b_i - (M dA)_i on the rows of cells with particles (empty rows 0);
+// block maximum of |r| into norm[it].  A no-op once iteration it - 1 has
+// converged.
+__global__ void __launch_bounds__(256) mm2d_residual_kernel(Mesh2dSolve m, int it) {
+  __shared__ double red[8];
+  const double thr = m.tol * __longlong_as_double((long long)*m.scale);
+  if (it > 0 && __longlong_as_double((long long)m.norm[it - 1]) <= thr) return;
+  const int64_t C = m.Cx * m.Cy;
+  double mx = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < C;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ix = i % m.Cx, iy = i / m.Cx;
+    double ri = 0.0;
+    if (m.out_off[i + 1] > m.out_off[i]) {
+      double s = 0.0;
+      for (int b = -1; b <= 1; ++b)
+        for (int a = -1; a <= 1; ++a) {
+          const int64_t src = src_cell(ix, iy, a, b, m.Cx, m.Cy);
+          if (m.out_off[src + 1] > m.out_off[src])
+            s = fma(m.cstat[(size_t)src * m.nv + 3 * (b + 1) + (a + 1)], m.dA[src], s);
+        }
+      ri = m.b[i] - m.q * s;
+    }
+    m.r[i] = ri;
+    mx = fmax(mx, fabs(ri));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) red[w] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) mx = fmax(mx, red[q]);
+    atomicMax(m.norm + it, pos_bits(mx));
+  }
+}
+
+// x = T^-1 r for the circulant tridiagonal T = (e, d0, e) of length n along
+// a line with stride st: Sherman-Morrison on the Thomas factors of f
+// (inv_m, cp, z: 3 n values, then fact, vlast); n = 1 and 2 in closed form
+__device__ __forceinline__ void circ_solve(int64_t n, const double* f, const double* r, double* x,
+                                           int64_t st, double e, double d0) {
+  if (n == 1) {
+    x[0] = r[0] / (d0 + 2.0 * e);
+    return;
+  }
+  if (n == 2) {
+    const double a = d0, c = 2.0 * e, det = a * a - c * c;
+    const double r0 = r[0], r1 = r[st];
+    x[0] = (a * r0 - c * r1) / det;
+    x[st] = (a * r1 - c * r0) / det;
+    return;
+  }
+  const double* inv_m = f;
+  const double* cp = f + n;
+  const double* z = f + 2 * n;
+  const double fact = f[3 * n], vlast = f[3 * n + 1];
+  double yp = r[0] * inv_m[0];
+  x[0] = yp;
+  for (int64_t i = 1; i < n; ++i) {
+    yp = (r[i * st] - e * yp) * inv_m[i];
+    x[i * st] = yp;
+  }
+  double yn = yp;
+  for (int64_t i = n - 2; i >= 0; --i) {
+    yn = x[i * st] - cp[i] * yn;
+    x[i * st] = yn;
+  }
+  const double g = (x[0] + vlast * x[(n - 1) * st]) * fact;
+  for (int64_t i = 0; i < n; ++i) x[i * st] = fma(-g, z[i], x[i * st]);
+}
+
+// the Thomas factors of T for both directions (thread 0: x, thread 1: y):
+// B = T with B_00 = d0 - gamma, B_nn = d0 - e^2 / gamma (gamma = -d0),
+// u = (gamma, 0, .., 0, e), v = (1, 0, .., 0, e / gamma); z = B^-1 u,
+// fact = 1 / (1 + v.z)
+__global__ void circ_factor_kernel(int64_t nx, int64_t ny, double e, double d0, double* fx,
+                                   double* fy) {
+  const int64_t n = threadIdx.x == 0 ? nx : ny;
+  double* f = threadIdx.x == 0 ? fx : fy;
+  if (threadIdx.x > 1 || n < 3) return;
+  const double gam = -d0;
+  double* inv_m = f;
+  double* cp = f + n;
+  double* z = f + 2 * n;
+  for (int64_t i = 0; i < n; ++i) {
+    double bi = d0;
+    if (i == 0) bi = d0 - gam;
+    if (i == n - 1) bi = d0 - e * e / gam;
+    const double mi = i == 0 ? bi : bi - e * cp[i - 1];
+    inv_m[i] = 1.0 / mi;
+    cp[i] = e * inv_m[i];
+  }
+  double yp = gam * inv_m[0];
+  z[0] = yp;
+  for (int64_t i = 1; i < n; ++i) {
+    yp = ((i == n - 1 ? e : 0.0) - e * yp) * inv_m[i];
+    z[i] = yp;
+  }
+  for (int64_t i = n - 2; i >= 0; --i) z[i] -= cp[i] * z[i + 1];
+  const double vlast = e / gam;
+  f[3 * n] = 1.0 / (1.0 + z[0] + vlast * z[n - 1]);
+  f[3 * n + 1] = vlast;
+}
+
+// x sweep: t = Tx^-1 r along every row (one thread per row)
+__global__ void mm2d_xsweep_kernel(Mesh2dSolve m, int it, double e, double d0) {
+  const double thr = m.tol * __longlong_as_double((long long)*m.scale);
+  if (__longlong_as_double((long long)m.norm[it]) <= thr) return;
+  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < m.Cy;
+       row += (int64_t)gridDim.x * blockDim.x)
+    circ_solve(m.Cx, m.tx, m.r + row * m.Cx, m.t + row * m.Cx, 1, e, d0);
+}
+
+// y sweep: s = Ty^-1 t along every column (in place), dA_j += s_j / (q N'_j)
+// on cells with particles
+__global__ void mm2d_ysweep_kernel(Mesh2dSolve m, int it, double e, double d0) {
+  const double thr = m.tol * __longlong_as_double((long long)*m.scale);
+  if (__longlong_as_double((long long)m.norm[it]) <= thr) return;
+  for (int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; col < m.Cx;
+       col += (int64_t)gridDim.x * blockDim.x) {
+    circ_solve(m.Cy, m.ty, m.t + col, m.t + col, m.Cx, e, d0);
+    for (int64_t iy = 0; iy < m.Cy; ++iy) {
+      const int64_t j = iy * m.Cx + col;
+      const int64_t n = m.out_off[j + 1] - m.out_off[j];
+      if (n > 0) m.dA[j] += m.t[j] / (m.q * (double)n);
+    }
+  }
+}
+
+// after the iterations: the unknowns of empty cells from their own rows
+// (unit diagonal), and the convergence status of the solve
+__global__ void mm2d_finish_kernel(Mesh2dSolve m, int max_iter, int* converged) {
+  const double thr = m.tol * __longlong_as_double((long long)*m.scale);
+  const int64_t C = m.Cx * m.Cy;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < C;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i == 0) {
+      int conv = 0;
+      for (int k = 0; k <= max_iter; ++k)
+        if (__longlong_as_double((long long)m.norm[k]) <= thr) conv = 1;
+      *converged = conv;
+    }
+    if (m.out_off[i + 1] > m.out_off[i]) continue;
+    const int64_t ix = i % m.Cx, iy = i / m.Cx;
+    double s = 0.0;
+    for (int b = -1; b <= 1; ++b)
+      for (int a = -1; a <= 1; ++a) {
+        const int64_t src = src_cell(ix, iy, a, b, m.Cx, m.Cy);
+        if (m.out_off[src + 1] > m.out_off[src])
+          s = fma(m.cstat[(size_t)src * m.nv + 3 * (b + 1) + (a + 1)], m.dA[src], s);
+      }
+    m.dA[i] = m.b[i] - m.q * s;
+  }
+}
+
+// Pass 2, one warp per cell: projection coefficients and the final particles
+template <int D, int NW>
+__global__ void __launch_bounds__(NW * 32) recon2d_emit_kernel(
+    int64_t Cx, int64_t C, int Kmax, const int32_t* K, const double* prm, const double* W,
+    const int64_t* out_off, const double* cstat, const double* dA, const int* converged,
+    uint64_t seed, double dx, double dy, int64_t n_out, double* x_out, double* y_out, double* v_out,
+    double* alpha_out, uint32_t* status_out) {
+  constexpr int NV = 9 + D + 1;
+  __shared__ RecCell<D> rcs[NW];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  RecCell<D>& rc = rcs[wid];
+  for (int64_t j = (int64_t)blockIdx.x * NW + wid; j < C; j += (int64_t)gridDim.x * NW) {
+    const int64_t jx = j % Cx, jy = j / Cx;
+    load_cell<D>(rc, j, Kmax, K, prm, lane);
+    __syncwarp();
+    const int64_t o = out_off[j], n = out_off[j + 1] - o;
+    if (lane == 0)
+      status_out[j] = projection_coeffs<D>(rc, n, W[j], dA[j], cstat + (size_t)j * NV + 9) |
+                      (*converged ? 0u : GM_ST_MM_NOT_CONVERGED);
+    __syncwarp();
+    const double aa = rc.a, an = rc.alpha_new;
+    const int skip = rc.skip;
+    for (int64_t i = lane; i < n; i += 32) {
+      uint64_t m0;
+      double w[D];
+      sample_particle<D>(rc, j, i, seed, m0, w);
+      const double u0 = __dmul_rn(__dadd_rn((double)m0, 0.5), 2.220446049250313080847263336181640625e-16);
+      const double uy =
+          __dmul_rn(__dadd_rn((double)sample_y_bits(j, i, seed), 0.5), 2.220446049250313080847263336181640625e-16);
+      x_out[o + i] = __dmul_rn(__dadd_rn((double)jx, u0), dx);
+      y_out[o + i] = __dmul_rn(__dadd_rn((double)jy, uy), dy);
+      alpha_out[o + i] = an;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const double vp = skip ? rc.u[d] + w[d] : fma(aa, w[d] + rc.beta[d], rc.u[d]);
+        v_out[(int64_t)d * n_out + o + i] = vp;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+static int grid_cap(int64_t units, int per, int cap) {
+  const int64_t g = (units + per - 1) / per;
+  return (int)(g < 1 ? 1 : (g < cap ? g : cap));
+}
+
+cudaError_t launch_deposit2d(int64_t Cx, int64_t Cy, const int64_t* cell_off, const double* x,
+                             const double* y, const double* alpha, double dx, double dy, double q,
+                             int order, double* part, double* rho, cudaStream_t s) {
+  const int64_t C = Cx * Cy;
+  if (C == 0) return cudaSuccess;
+  deposit2d_partials_kernel<4><<<grid_cap(C, 4, 152 * 16), 128, 0, s>>>(
+      Cx, C, cell_off, x, y, alpha, 1.0 / dx, 1.0 / dy, order, part);
+  deposit2d_combine_kernel<<<grid_cap(C, 256, 1024), 256, 0, s>>>(Cx, Cy, part, q / (dx * dy), rho);
+  return cudaGetLastError();
+}
+
+size_t reconstruct2d_ws_bytes(int D, int64_t Cx, int64_t Cy) {
+  const int64_t C = Cx * Cy;
+  const size_t dbl = (size_t)(9 + D + 1) * C + 4 * (size_t)C + (3 * (size_t)Cx + 2) +
+                     (3 * (size_t)Cy + 2) + (kMesh2dMaxIter + 1) + 1;
+  return dbl * sizeof(double) + 1024;
+}
+
+cudaError_t launch_reconstruct2d(int D, int64_t Cx, int64_t Cy, int Kmax, const int32_t* K,
+                                 const double* prm, const double* W, const double* rho_target,
+                                 int64_t n_out, const int64_t* out_off, uint64_t seed, double dx,
+                                 double dy, double q, int order, double* x_out, double* y_out,
+                                 double* v_out, double* alpha_out, uint32_t* status_out,
+                                 double* dA_user, void* ws, cudaStream_t s) {
+  const int64_t C = Cx * Cy;
+  if (C == 0) return cudaSuccess;
+  const int NVm = 9 + D + 1;
+  double* base = (double*)ws;
+  Mesh2dSolve m;
+  m.Cx = Cx;
+  m.Cy = Cy;
+  double* cstat = base;
+  m.cstat = cstat;
+  m.nv = NVm;
+  m.out_off = out_off;
+  m.q = q;
+  m.b = cstat + (size_t)NVm * C;
+  m.dA = m.b + C;
+  m.r = m.dA + C;
+  m.t = m.r + C;
+  double* fx = m.t + C;
+  double* fy = fx + 3 * Cx + 2;
+  m.tx = fx;
+  m.ty = fy;
+  m.norm = (unsigned long long*)(fy + 3 * Cy + 2);
+  m.scale = m.norm + kMesh2dMaxIter + 1;
+  int* converged = (int*)(m.scale + 1);
+  m.tol = kMesh2dTol;
+  if (dA_user) m.dA = dA_user;
+  const double e = order == 1 ? 0.125 : 1.0 / 6.0;
+  const double d0 = order == 1 ? 0.75 : 2.0 / 3.0;
+
+  constexpr int NW = 4;
+  const int g = grid_cap(C, NW, 152 * 16);
+  cudaError_t err = cudaMemsetAsync(m.scale, 0, sizeof(unsigned long long), s);
+  if (err != cudaSuccess) return err;
+  if (D == 1)
+    recon2d_stats_kernel<1, NW><<<g, NW * 32, 0, s>>>(Cx, C, Kmax, K, prm, out_off, seed, order, cstat);
+  else
+    recon2d_stats_kernel<3, NW><<<g, NW * 32, 0, s>>>(Cx, C, Kmax, K, prm, out_off, seed, order, cstat);
+  circ_factor_kernel<<<1, 32, 0, s>>>(Cx, Cy, e, d0, fx, fy);
+  const int ga = grid_cap(C > kMesh2dMaxIter + 1 ? C : kMesh2dMaxIter + 1, 256, 2048);
+  assemble2d_kernel<<<ga, 256, 0, s>>>(m, W, rho_target, dx * dy, kMesh2dMaxIter);
+  // norm[i] for i < C is cleared by the grid-stride loop above; meshes with
+  // fewer cells than iterations clear the rest here
+  if (C <= kMesh2dMaxIter) {
+    err = cudaMemsetAsync(m.norm + C, 0, sizeof(unsigned long long) * (kMesh2dMaxIter + 1 - C), s);
+    if (err != cudaSuccess) return err;
+  }
+  const int gr = grid_cap(C, 256, 152 * 4);
+  for (int it = 0; it < kMesh2dMaxIter; ++it) {
+    mm2d_residual_kernel<<<gr, 256, 0, s>>>(m, it);
+    mm2d_xsweep_kernel<<<grid_cap(Cy, 64, 1024), 64, 0, s>>>(m, it, e, d0);
+    mm2d_ysweep_kernel<<<grid_cap(Cx, 64, 1024), 64, 0, s>>>(m, it, e, d0);
+  }
+  mm2d_residual_kernel<<<gr, 256, 0, s>>>(m, kMesh2dMaxIter);
+  mm2d_finish_kernel<<<grid_cap(C, 256, 1024), 256, 0, s>>>(m, kMesh2dMaxIter, converged);
+  if (D == 1)
+    recon2d_emit_kernel<1, NW><<<g, NW * 32, 0, s>>>(Cx, C, Kmax, K, prm, W, out_off, cstat, m.dA,
+                                                      converged, seed, dx, dy, n_out, x_out, y_out,
+                                                      v_out, alpha_out, status_out);
+  else
+    recon2d_emit_kernel<3, NW><<<g, NW * 32, 0, s>>>(Cx, C, Kmax, K, prm, W, out_off, cstat, m.dA,
+                                                      converged, seed, dx, dy, n_out, x_out, y_out,
+                                                      v_out, alpha_out, status_out);
+  return cudaGetLastError();
+}
+
+}  // namespace gmcr

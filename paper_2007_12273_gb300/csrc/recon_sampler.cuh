@@ -1,0 +1,206 @@
+// recon_sampler.cuh -- the counter-based particle sampler of the
+// reconstruction (Sec. 2.4, eq. mix-dist-1) and the Lemons projection
+// coefficients (Sec. 2.4.2, eqs. alpha, beta), shared by the 1D and 2D
+// meshes.  A particle is regenerated bit-identically from (seed, cell,
+// index); FP64 is kept for the position and for the velocity's offset from
+// the mixture mean, the categorical choice is decided on integers and the
+// Gaussian draw is FP32.
+#pragma once
+
+#include "gm_kernels.cuh"
+
+namespace gmcr {
+
+template <int D>
+struct RecCell {
+  static constexpr int NM = D * (D + 1) / 2;
+  // categorical thresholds: u < cw_k  <=>  2 m + 1 < thr_k, where
+  // u = (m + 1/2) 2^-52 and thr_k = ceil(cw_k 2^53) (cw_k the cumulative
+  // weights summed in component order): the FP64 comparison, decided on
+  // integers
+  long long thr[kMaxK];
+  double dz[kMaxK][D];      // mu_k - u
+  float Lf[kMaxK][NM];      // lower-triangular Cholesky factor (FP32), row-major
+  double u[D];              // mixture mean sum_k w_k mu_k
+  double theta;             // sum_k w_k (tr Sigma_k + |mu_k - u|^2)
+  double a, beta[D], alpha_new;
+  int K;
+  int skip;
+  unsigned int status;
+};
+
+// load cell j's mixture: Cholesky factors (no floor; a non-positive pivot
+// gives a zero column, as for a degenerate stored covariance)
+template <int D>
+__device__ void load_cell(RecCell<D>& rc, int64_t j, int Kmax, const int32_t* K,
+                          const double* prm, int lane) {
+  constexpr int NM = D * (D + 1) / 2;
+  constexpr int P = 1 + D + NM;
+  const int Kj = K[j];
+  const int k = lane;
+  if (k < Kj) {
+    const double* r = prm + ((size_t)j * Kmax + k) * P;
+    if (D == 1) {
+      const double s = r[2];
+      rc.Lf[k][0] = (float)(s > 0.0 ? sqrt(s) : 0.0);
+    } else {
+      // S upper: [s00 s01 s02 s11 s12 s22]
+      const double s00 = r[4], s01 = r[5], s02 = r[6], s11 = r[7], s12 = r[8], s22 = r[9];
+      const double l00 = s00 > 0.0 ? sqrt(s00) : 0.0;
+      const double l10 = l00 > 0.0 ? s01 / l00 : 0.0;
+      const double l20 = l00 > 0.0 ? s02 / l00 : 0.0;
+      const double t11 = s11 - l10 * l10;
+      const double l11 = t11 > 0.0 ? sqrt(t11) : 0.0;
+      const double l21 = l11 > 0.0 ? (s12 - l20 * l10) / l11 : 0.0;
+      const double t22 = s22 - l20 * l20 - l21 * l21;
+      const double l22 = t22 > 0.0 ? sqrt(t22) : 0.0;
+      rc.Lf[k][0] = (float)l00; rc.Lf[k][1] = (float)l10; rc.Lf[k][2] = (float)l11;
+      rc.Lf[k][3] = (float)l20; rc.Lf[k][4] = (float)l21; rc.Lf[k][5] = (float)l22;
+    }
+  }
+  if (lane == 0) {
+    rc.K = Kj;
+    double cum = 0.0, u[D], th = 0.0;
+    for (int d = 0; d < D; ++d) u[d] = 0.0;
+    for (int q = 0; q < Kj; ++q) {
+      const double* r = prm + ((size_t)j * Kmax + q) * P;
+      cum += r[0];
+      const double t = ceil(cum * 9007199254740992.0);  // 2^53
+      rc.thr[q] = t < 4.0e18 ? (long long)t : 4000000000000000000ll;
+      for (int d = 0; d < D; ++d) u[d] += r[0] * r[1 + d];
+    }
+    for (int q = 0; q < Kj; ++q) {
+      const double* r = prm + ((size_t)j * Kmax + q) * P;
+      double tr = 0.0, dd = 0.0;
+      int t = 1 + D;
+      for (int x = 0; x < D; ++x)
+        for (int y = x; y < D; ++y, ++t) {
+          if (x == y) tr += r[t];
+        }
+      for (int d = 0; d < D; ++d) {
+        rc.dz[q][d] = r[1 + d] - u[d];
+        dd += (r[1 + d] - u[d]) * (r[1 + d] - u[d]);
+      }
+      th += r[0] * (tr + dd);
+    }
+    for (int d = 0; d < D; ++d) rc.u[d] = u[d];
+    rc.theta = th;
+  }
+}
+
+// the 52 leading bits of (hi, lo), as uniform52 uses them
+__device__ __forceinline__ uint64_t bits52(uint32_t hi, uint32_t lo) {
+  return ((uint64_t)hi << 20) | (uint64_t)(lo >> 12);
+}
+// (t + 1/2) 2^-52 in FP32 (relative error ~2^-24) for a 52-bit t, without
+// FP64 arithmetic: t = hi26 2^26 + lo26
+__device__ __forceinline__ float half_ulp52_f(uint64_t t) {
+  const float hi = (float)(uint32_t)(t >> 26), lo = (float)(uint32_t)(t & 0x3FFFFFFull);
+  return fmaf(hi, 1.4901161193847656e-08f /* 2^-26 */, (lo + 0.5f) * 2.220446049250313e-16f);
+}
+// Box-Muller radius sqrt(-2 ln u) for u = (m + 1/2) 2^-52, in FP32 from the
+// integer: below 1/2, ln u; above, log1p(-(1 - u)) with 1 - u =
+// (2^52 - 1 - m + 1/2) 2^-52 formed exactly on integers, so the radius
+// keeps FP32 relative accuracy where its derivative is unbounded
+__device__ __forceinline__ float bm_radius(uint64_t m) {
+  const float lnu = m < (1ull << 51) ? logf(half_ulp52_f(m))
+                                     : log1pf(-half_ulp52_f((1ull << 52) - 1ull - m));
+  return sqrtf(-2.0f * lnu);
+}
+
+// particle i of cell j (Sec. 2.4, eq. mix-dist-1): the 52-bit integer m0
+// of its position's uniform u0 = (m0 + 1/2) 2^-52 (x = (j + u0) dx) and
+// w = v - u (u the mixture mean), w = (mu_z - u) + L_z xi with L_z xi in FP32
+template <int D>
+__device__ __forceinline__ void sample_particle(const RecCell<D>& rc, int64_t j, int64_t i,
+                                                uint64_t seed, uint64_t& m0, double (&w)[D]) {
+  const u32x4 r0 = philox_draw(seed, (uint32_t)i, kTagSample | 0u, j);
+  m0 = bits52(r0.x, r0.y);
+  const long long m1x2 = 2 * (long long)bits52(r0.z, r0.w) + 1;
+  const int K = rc.K;
+  int z = K - 1;
+  for (int k = 0; k < K; ++k)
+    if (m1x2 < rc.thr[k]) { z = k; break; }
+  // Box-Muller (Box & Muller 1958) on (u2, u3) [and (u4, u5) for D = 3]
+  float xi[3];
+  {
+    const u32x4 r1 = philox_draw(seed, (uint32_t)i, kTagSample | 1u, j);
+    const float rr = bm_radius(bits52(r1.x, r1.y));
+    float sn, cs;
+    sincospif(2.0f * half_ulp52_f(bits52(r1.z, r1.w)), &sn, &cs);
+    xi[0] = rr * cs;
+    if (D == 3) xi[1] = rr * sn;
+  }
+  if (D == 3) {
+    const u32x4 r2 = philox_draw(seed, (uint32_t)i, kTagSample | 2u, j);
+    const float rr = bm_radius(bits52(r2.x, r2.y));
+    xi[2] = rr * cospif(2.0f * half_ulp52_f(bits52(r2.z, r2.w)));
+  }
+  if (K == 0) {
+    for (int d = 0; d < D; ++d) w[d] = -rc.u[d];
+    return;
+  }
+  const float* L = rc.Lf[z];
+  if (D == 1) {
+    w[0] = rc.dz[z][0] + (double)(L[0] * xi[0]);
+  } else {
+    w[0] = rc.dz[z][0] + (double)(L[0] * xi[0]);
+    w[1] = rc.dz[z][1] + (double)fmaf(L[2], xi[1], L[1] * xi[0]);
+    w[2] = rc.dz[z][2] + (double)fmaf(L[5], xi[2], fmaf(L[4], xi[1], L[3] * xi[0]));
+  }
+}
+
+// the 52 leading bits of the y uniform of particle i of cell j on a 2D mesh
+// (Philox block 3, words 0-1)
+__device__ __forceinline__ uint64_t sample_y_bits(int64_t j, int64_t i, uint64_t seed) {
+  const u32x4 r3 = philox_draw(seed, (uint32_t)i, kTagSample | 3u, j);
+  return bits52(r3.x, r3.y);
+}
+
+// (m + 1/2) 2^-52 - 1/2, the in-cell offset of a position from the cell
+// centre in cell units (exact in FP64)
+__device__ __forceinline__ double centred52(uint64_t m) {
+  return ((double)((long long)m - (1ll << 51)) + 0.5) * 2.220446049250313080847263336181640625e-16;
+}
+
+// Lemons projection of a cell with n resampled particles (lane 0): the
+// corrected weight alpha' = W_j / n + dA_j and, from the sums sw[d] =
+// sum_p w_d and sw[D] = sum_p |w|^2 (w = v - u), the scale a and shift
+// beta of eqs. (alpha), (beta) in the frame of the mixture mean u:
+// 2 E N' - p^2 = W (N' theta + (N' - W) |u|^2),
+// 2 E' N' - p'^2 = alpha'^2 (n sum|w|^2 - |sum w|^2).  Returns the status.
+template <int D>
+__device__ unsigned int projection_coeffs(RecCell<D>& rc, int64_t n, double Wj, double dAj,
+                                          const double* sw) {
+  unsigned int st = 0;
+  if (n == 0) st |= GM_ST_MM_EMPTY_COL;
+  const double an = (n > 0 ? Wj / (double)n : 0.0) + dAj;
+  rc.alpha_new = an;
+  if (n > 0 && !(an > 0.0)) st |= GM_ST_NEG_WEIGHT;
+  rc.skip = 1;
+  rc.a = 1.0;
+  for (int d = 0; d < D; ++d) rc.beta[d] = 0.0;
+  if (n > 0 && rc.K == 0) st |= GM_ST_NO_MIXTURE;
+  if (n > 0 && rc.K > 0) {
+    const double Np = (double)n * an;
+    double u2 = 0.0, sw2 = 0.0;
+    for (int d = 0; d < D; ++d) {
+      u2 += rc.u[d] * rc.u[d];
+      sw2 += sw[d] * sw[d];
+    }
+    const double num = Wj * (Np * rc.theta + (Np - Wj) * u2);
+    const double den = an * an * ((double)n * sw[D] - sw2);
+    if (num > 0.0 && den > 0.0 && Np > 0.0) {
+      const double aa = sqrt(num / den);
+      rc.a = aa;
+      for (int d = 0; d < D; ++d) rc.beta[d] = ((Wj - Np) * rc.u[d] - aa * an * sw[d]) / (aa * Np);
+      rc.skip = 0;
+    } else {
+      st |= GM_ST_PROJ_SKIPPED;
+    }
+  }
+  rc.status = st;
+  return st;
+}
+
+}  // namespace gmcr

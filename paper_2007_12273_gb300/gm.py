@@ -29,11 +29,14 @@ ST_PROJ_SKIPPED = 0x100
 ST_NEG_WEIGHT = 0x200
 ST_MM_EMPTY_COL = 0x400
 ST_NO_MIXTURE = 0x800
+ST_MM_NOT_CONVERGED = 0x1000
 
 EXPORTED = ("gm_compress", "gm_reconstruct", "gm_moments", "gm_mixture_moments",
             "gm_last_error", "gm_shutdown", "gm_reconstruct_noalloc", "gm_gemm_bf16",
             "gm_compress_from", "gm_features", "gm_mlp_targets", "gm_mlp_sync",
-            "gm_mlp_scratch_bytes", "gm_mlp_forward", "gm_mlp_train_step", "gm_mlp_decode")
+            "gm_mlp_scratch_bytes", "gm_mlp_forward", "gm_mlp_train_step", "gm_mlp_decode",
+            "gm_graph_begin", "gm_graph_end", "gm_graph_launch", "gm_graph_destroy", "gm_autotune",
+            "gm_compress_standard", "gm_anderson_affine", "gm_deposit_2d", "gm_reconstruct_2d")
 
 
 class GMMlp(ct.Structure):
@@ -50,6 +53,16 @@ class GMConfig(ct.Structure):
                 ("L", ct.c_double), ("q", ct.c_double), ("threads_per_cell", ct.c_int32),
                 ("smem_particles", ct.c_int32), ("precision", ct.c_int32),
                 ("reserved", ct.c_int32)]
+
+
+class GMMesh2d(ct.Structure):
+    """Mirror of ``gm_mesh2d`` (include/gm.h)."""
+    _fields_ = [("Cx", ct.c_int64), ("Cy", ct.c_int64), ("Lx", ct.c_double), ("Ly", ct.c_double)]
+
+
+def mesh2d(params: dict) -> GMMesh2d:
+    """gm_mesh2d from a method-parameter dict with Cx, Cy, Lx, Ly."""
+    return GMMesh2d(int(params["Cx"]), int(params["Cy"]), float(params["Lx"]), float(params["Ly"]))
 
 
 class GMStdOpts(ct.Structure):
@@ -102,11 +115,14 @@ def load(build_if_missing: bool = False):
         lib.gm_autotune.argtypes = [P, I64, I64, P, P, P, I32, P, I32, ct.POINTER(ct.c_float), P]
         lib.gm_compress_standard.argtypes = [P, P, I64, I64, P, P, P, I32, P] + [P] * 10 + [P]
         lib.gm_anderson_affine.argtypes = [I32, P, P, P, I32, I32, P, P, P]
+        lib.gm_deposit_2d.argtypes = [P] * 8
+        lib.gm_reconstruct_2d.argtypes = [P, P, P, P, P, P, I64] + [P] * 8
         for f in ("gm_compress", "gm_reconstruct", "gm_moments", "gm_mixture_moments", "gm_shutdown",
                   "gm_reconstruct_noalloc", "gm_gemm_bf16", "gm_compress_from", "gm_features",
                   "gm_mlp_targets", "gm_mlp_sync", "gm_mlp_forward", "gm_mlp_train_step",
                   "gm_mlp_decode", "gm_graph_begin", "gm_graph_end", "gm_graph_launch",
-                  "gm_graph_destroy", "gm_autotune", "gm_compress_standard", "gm_anderson_affine"):
+                  "gm_graph_destroy", "gm_autotune", "gm_compress_standard", "gm_anderson_affine",
+                  "gm_deposit_2d", "gm_reconstruct_2d"):
             getattr(lib, f).restype = ct.c_int
         lib.gm_last_error.restype = ct.c_char_p
         _lib = lib
@@ -167,26 +183,28 @@ def gm_compress(cfg: GMConfig, cell_off, x, v, alpha, stream=None, out=None, ini
     (``gm_compress_from``)."""
     lib = load()
     C = cell_off.shape[0] - 1
-    n = x.shape[0]
+    n = alpha.shape[0]
     D = cfg.D
     _check(cell_off, torch.int64, "cell_off")
-    _check(x, torch.float64, "x")
+    if x is not None:
+        _check(x, torch.float64, "x")
     _check(alpha, torch.float64, "alpha")
     if v.dtype not in (torch.float32, torch.float64) or tuple(v.shape) != (D, n):
         raise ValueError("v must be [D, n] float32/float64")
     _check(v, v.dtype, "v")
-    dev = x.device
+    dev = alpha.device
     if out is None:
         out = dict(K=torch.empty(C, dtype=torch.int32, device=dev),
                    params=torch.empty((C, cfg.Kmax, P_of(D)), dtype=torch.float64, device=dev),
                    W=torch.empty(C, dtype=torch.float64, device=dev),
-                   rho_target=torch.empty(C, dtype=torch.float64, device=dev),
+                   rho_target=torch.empty(C, dtype=torch.float64, device=dev) if x is not None else None,
                    lnL=torch.empty(C, dtype=torch.float64, device=dev),
                    sweeps=torch.empty(C, dtype=torch.int32, device=dev),
                    kwork=torch.empty(C, dtype=torch.int32, device=dev),
                    status=torch.empty(C, dtype=torch.int32, device=dev))
     vf = 1 if v.dtype == torch.float64 else 0
-    tail = (_ptr(out["K"]), _ptr(out["params"]), _ptr(out["W"]), _ptr(out["rho_target"]),
+    tail = (_ptr(out["K"]), _ptr(out["params"]), _ptr(out["W"]),
+            _ptr(out["rho_target"]) if x is not None else None,
             _ptr(out["lnL"]), _ptr(out["sweeps"]), _ptr(out["kwork"]), _ptr(out["status"]),
             _stream_ptr(stream))
     if init_K is None:
@@ -565,6 +583,59 @@ def gm_compress_standard(cfg: GMConfig, cell_off, x, v, alpha, init: int = 0, aa
                                   _ptr(out["aa_resets"]), _ptr(out["km_passes"]), _ptr(out["status"]),
                                   _stream_ptr(stream))
     _rc(lib, rc, "gm_compress_standard")
+    return out
+
+
+def gm_deposit_2d(cfg: GMConfig, mesh: GMMesh2d, cell_off, x, y, alpha=None, stream=None, out=None):
+    """Charge density [Cy * Cx] on the 2D mesh (node jy * Cx + jx) of
+    particles sorted by cell; ``alpha`` None = unit weights."""
+    lib = load()
+    C = mesh.Cx * mesh.Cy
+    if cell_off.shape[0] != C + 1:
+        raise ValueError("cell_off must have Cx * Cy + 1 entries")
+    _check(cell_off, torch.int64, "cell_off")
+    _check(x, torch.float64, "x")
+    _check(y, torch.float64, "y")
+    if alpha is not None:
+        _check(alpha, torch.float64, "alpha")
+    if out is None:
+        out = torch.empty(C, dtype=torch.float64, device=x.device)
+    rc = lib.gm_deposit_2d(ct.byref(cfg), ct.byref(mesh), _ptr(cell_off), _ptr(x), _ptr(y), _ptr(alpha),
+                           _ptr(out), _stream_ptr(stream))
+    _rc(lib, rc, "gm_deposit_2d")
+    return out
+
+
+def gm_reconstruct_2d(cfg: GMConfig, mesh: GMMesh2d, K, params, W, rho_target, out_off,
+                      n_out: int | None = None, stream=None, want_dA: bool = False, out=None) -> dict:
+    """Resample every cell of the 2D mesh: x, y [n'], v [D, n'], alpha [n'],
+    status [C] (and dA [C] if asked)."""
+    lib = load()
+    C = mesh.Cx * mesh.Cy
+    D = cfg.D
+    if out_off.shape[0] != C + 1:
+        raise ValueError("out_off must have Cx * Cy + 1 entries")
+    _check(K, torch.int32, "K")
+    _check(params, torch.float64, "params")
+    _check(W, torch.float64, "W")
+    _check(rho_target, torch.float64, "rho_target")
+    _check(out_off, torch.int64, "out_off")
+    if n_out is None:
+        n_out = int(out_off[-1].item())
+    dev = W.device
+    if out is None:
+        out = dict(x=torch.empty(n_out, dtype=torch.float64, device=dev),
+                   y=torch.empty(n_out, dtype=torch.float64, device=dev),
+                   v=torch.empty((D, n_out), dtype=torch.float64, device=dev),
+                   alpha=torch.empty(n_out, dtype=torch.float64, device=dev),
+                   status=torch.empty(C, dtype=torch.int32, device=dev))
+        if want_dA:
+            out["dA"] = torch.empty(C, dtype=torch.float64, device=dev)
+    rc = lib.gm_reconstruct_2d(ct.byref(cfg), ct.byref(mesh), _ptr(K), _ptr(params), _ptr(W),
+                               _ptr(rho_target), n_out, _ptr(out_off), _ptr(out["x"]), _ptr(out["y"]),
+                               _ptr(out["v"]), _ptr(out["alpha"]), _ptr(out["status"]),
+                               _ptr(out.get("dA")), _stream_ptr(stream))
+    _rc(lib, rc, "gm_reconstruct_2d")
     return out
 
 

@@ -100,3 +100,37 @@ def test_binding_argument_counts_match_header(lib):
         assert len(at) == n, (name, len(at), n)
         checked += 1
     assert checked >= 20
+
+
+@pytest.mark.parametrize("py,c", [("GMMesh2d", "gm_mesh2d"), ("GMStdOpts", "gm_std_opts")])
+def test_small_struct_layouts_match_header(tmp_path, py, c):
+    from paper_2007_12273_gb300 import gm
+    cls = getattr(gm, py)
+    fields = [f for f, _ in cls._fields_]
+    src = tmp_path / f"{c}.c"
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "gm.h"\n'
+        f"int main(void){{printf(\"%zu\", sizeof({c}));"
+        + "".join(f'printf(" %zu", offsetof({c}, {f}));' for f in fields)
+        + "return 0;}\n")
+    exe = tmp_path / c
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    vals = [int(t) for t in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    assert vals[0] == ct.sizeof(cls)
+    assert vals[1:] == [getattr(cls, f).offset for f in fields]
+
+
+def test_mesh2d_argument_errors_without_gpu(lib):
+    from paper_2007_12273_gb300 import gm
+    cfg = gm.config(dict(D=3, Kmax=4, shape_order=2, L=1.0))
+    assert lib.gm_deposit_2d(ct.byref(cfg), None, None, None, None, None, None, None) == -1
+    assert b"mesh" in lib.gm_last_error()
+    mesh = gm.GMMesh2d(0, 4, 1.0, 1.0)
+    assert lib.gm_deposit_2d(ct.byref(cfg), ct.byref(mesh), None, None, None, None, None, None) == -1
+    mesh = gm.GMMesh2d(4, 4, 1.0, -1.0)
+    assert lib.gm_deposit_2d(ct.byref(cfg), ct.byref(mesh), None, None, None, None, None, None) == -1
+    mesh = gm.GMMesh2d(4, 4, 1.0, 1.0)
+    cfg0 = gm.config(dict(D=3, Kmax=4, shape_order=2, L=1.0, q=0.0))
+    assert lib.gm_reconstruct_2d(ct.byref(cfg0), ct.byref(mesh), None, None, None, None, 0, None,
+                                 None, None, None, None, None, None, None) == -1
+    assert b"q must be nonzero" in lib.gm_last_error()
