@@ -11,9 +11,15 @@
 // its own node), so M dA = dx dy (rho' - rho) is solved by defect
 // correction with the operator of uniformly filled cells as preconditioner:
 // P = (Tx (x) Ty) diag(q N'_j), T the circulant tridiagonal matrix of the
-// mean shape weights (1/6, 2/3, 1/6; CIC 1/8, 3/4, 1/8), so that P^-1 is a
-// cyclic tridiagonal solve along every row and then along every column.
-// Each iteration is a residual pass, an x sweep and a y sweep (three
+// mean shape weights (e, d0, e) = (1/6, 2/3, 1/6); CIC (1/8, 3/4, 1/8).
+// T^-1 is circulant with entries c_k = (r^k + r^(n-k)) / ((1 - r^n) s),
+// s = sqrt(d0^2 - 4 e^2), r = (s - d0) / (2 e) (r = -(2 - sqrt 3) for the
+// quadratic B-spline: the images of the bi-infinite inverse), so P^-1 is a
+// convolution along every row and then every column: all n entries for
+// lines of at most 33 cells, else the 33 central ones (the first one left
+// out is below 2e-10 of c_0; the residual is always formed with the true M,
+// so the preconditioner's truncation changes the rate, not the solution).
+// Each iteration is a residual pass, an x pass and a y pass (three
 // launches, each a no-op once the residual is below the tolerance).  A cell
 // without resampled particles has a unit column: its unknown appears in its
 // own row only, so it is left out of the iteration and found afterwards
@@ -142,6 +148,9 @@ __device__ __forceinline__ unsigned long long pos_bits(double v) {
   return (unsigned long long)__double_as_longlong(v);
 }
 
+constexpr int kCircTaps = 33;  // entries of T^-1 kept per direction
+constexpr int kCircHalf = 16;  // window half-width for lines of more than kCircTaps cells
+
 struct Mesh2dSolve {
   int64_t Cx, Cy;
   const double* cstat;   // [C][NV]
@@ -154,8 +163,6 @@ struct Mesh2dSolve {
   double* t;             // [C] after the x sweep
   unsigned long long* norm;  // [max_iter + 1] max |r| per iteration (as bits)
   unsigned long long* scale; // [1] max |dx dy rho'| (as bits)
-  const double* tx;      // x-direction factors: [4][Cx] inv_m, cp, z and [2] (fact, vlast)
-  const double* ty;
   double tol;
 };
 
@@ -217,97 +224,75 @@ __global__ void __launch_bounds__(256) mm2d_residual_kernel(Mesh2dSolve m, int i
   }
 }
 
-// x = T^-1 r for the circulant tridiagonal T = (e, d0, e) of length n along
-// a line with stride st: Sherman-Morrison on the Thomas factors of f
-// (inv_m, cp, z: 3 n values, then fact, vlast); n = 1 and 2 in closed form
-__device__ __forceinline__ void circ_solve(int64_t n, const double* f, const double* r, double* x,
-                                           int64_t st, double e, double d0) {
-  if (n == 1) {
-    x[0] = r[0] / (d0 + 2.0 * e);
-    return;
+// entries of T^-1 along one direction (host-computed, passed by value)
+struct CircTaps {
+  int full;        // 1: all n entries c_0 .. c_{n-1}; 0: c_0 .. c_16 (window)
+  double c[kCircTaps];
+};
+
+// (T^-1 line)_i for a line of n values at stride st
+__device__ __forceinline__ double circ_apply(const CircTaps& T, const double* line, int64_t n,
+                                             int64_t i, int64_t st) {
+  double s = 0.0;
+  if (T.full) {
+#pragma unroll
+    for (int k = 0; k < kCircTaps; ++k)
+      if (k < n) {
+        int64_t j = i - k;
+        j = j < 0 ? j + n : j;
+        s = fma(T.c[k], line[j * st], s);
+      }
+    return s;
   }
-  if (n == 2) {
-    const double a = d0, c = 2.0 * e, det = a * a - c * c;
-    const double r0 = r[0], r1 = r[st];
-    x[0] = (a * r0 - c * r1) / det;
-    x[st] = (a * r1 - c * r0) / det;
-    return;
+  s = T.c[0] * line[i * st];
+#pragma unroll
+  for (int k = 1; k <= kCircHalf; ++k) {
+    int64_t jm = i - k, jp = i + k;
+    jm = jm < 0 ? jm + n : jm;
+    jp = jp >= n ? jp - n : jp;
+    s = fma(T.c[k], line[jm * st] + line[jp * st], s);
   }
-  const double* inv_m = f;
-  const double* cp = f + n;
-  const double* z = f + 2 * n;
-  const double fact = f[3 * n], vlast = f[3 * n + 1];
-  double yp = r[0] * inv_m[0];
-  x[0] = yp;
-  for (int64_t i = 1; i < n; ++i) {
-    yp = (r[i * st] - e * yp) * inv_m[i];
-    x[i * st] = yp;
-  }
-  double yn = yp;
-  for (int64_t i = n - 2; i >= 0; --i) {
-    yn = x[i * st] - cp[i] * yn;
-    x[i * st] = yn;
-  }
-  const double g = (x[0] + vlast * x[(n - 1) * st]) * fact;
-  for (int64_t i = 0; i < n; ++i) x[i * st] = fma(-g, z[i], x[i * st]);
+  return s;
 }
 
-// the Thomas factors of T for both directions (thread 0: x, thread 1: y):
-// B = T with B_00 = d0 - gamma, B_nn = d0 - e^2 / gamma (gamma = -d0),
-// u = (gamma, 0, .., 0, e), v = (1, 0, .., 0, e / gamma); z = B^-1 u,
-// fact = 1 / (1 + v.z)
-__global__ void circ_factor_kernel(int64_t nx, int64_t ny, double e, double d0, double* fx,
-                                   double* fy) {
-  const int64_t n = threadIdx.x == 0 ? nx : ny;
-  double* f = threadIdx.x == 0 ? fx : fy;
-  if (threadIdx.x > 1 || n < 3) return;
-  const double gam = -d0;
-  double* inv_m = f;
-  double* cp = f + n;
-  double* z = f + 2 * n;
-  for (int64_t i = 0; i < n; ++i) {
-    double bi = d0;
-    if (i == 0) bi = d0 - gam;
-    if (i == n - 1) bi = d0 - e * e / gam;
-    const double mi = i == 0 ? bi : bi - e * cp[i - 1];
-    inv_m[i] = 1.0 / mi;
-    cp[i] = e * inv_m[i];
-  }
-  double yp = gam * inv_m[0];
-  z[0] = yp;
-  for (int64_t i = 1; i < n; ++i) {
-    yp = ((i == n - 1 ? e : 0.0) - e * yp) * inv_m[i];
-    z[i] = yp;
-  }
-  for (int64_t i = n - 2; i >= 0; --i) z[i] -= cp[i] * z[i + 1];
-  const double vlast = e / gam;
-  f[3 * n] = 1.0 / (1.0 + z[0] + vlast * z[n - 1]);
-  f[3 * n + 1] = vlast;
-}
-
-// x sweep: t = Tx^-1 r along every row (one thread per row)
-__global__ void mm2d_xsweep_kernel(Mesh2dSolve m, int it, double e, double d0) {
+// x pass: t = (Tx^-1 along every row) r, one thread per node
+__global__ void mm2d_xsweep_kernel(Mesh2dSolve m, int it, CircTaps tx) {
   const double thr = m.tol * __longlong_as_double((long long)*m.scale);
   if (__longlong_as_double((long long)m.norm[it]) <= thr) return;
-  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < m.Cy;
-       row += (int64_t)gridDim.x * blockDim.x)
-    circ_solve(m.Cx, m.tx, m.r + row * m.Cx, m.t + row * m.Cx, 1, e, d0);
+  const int64_t C = m.Cx * m.Cy;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < C;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ix = i % m.Cx, row = i - ix;
+    m.t[i] = circ_apply(tx, m.r + row, m.Cx, ix, 1);
+  }
 }
 
-// y sweep: s = Ty^-1 t along every column (in place), dA_j += s_j / (q N'_j)
-// on cells with particles
-__global__ void mm2d_ysweep_kernel(Mesh2dSolve m, int it, double e, double d0) {
+// y pass: dA_j += (Ty^-1 along every column of t)_j / (q N'_j) on cells with
+// particles, one thread per node
+__global__ void mm2d_ysweep_kernel(Mesh2dSolve m, int it, CircTaps ty) {
   const double thr = m.tol * __longlong_as_double((long long)*m.scale);
   if (__longlong_as_double((long long)m.norm[it]) <= thr) return;
-  for (int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; col < m.Cx;
-       col += (int64_t)gridDim.x * blockDim.x) {
-    circ_solve(m.Cy, m.ty, m.t + col, m.t + col, m.Cx, e, d0);
-    for (int64_t iy = 0; iy < m.Cy; ++iy) {
-      const int64_t j = iy * m.Cx + col;
-      const int64_t n = m.out_off[j + 1] - m.out_off[j];
-      if (n > 0) m.dA[j] += m.t[j] / (m.q * (double)n);
-    }
+  const int64_t C = m.Cx * m.Cy;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < C;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = m.out_off[i + 1] - m.out_off[i];
+    if (n == 0) continue;
+    const int64_t ix = i % m.Cx, iy = i / m.Cx;
+    m.dA[i] += circ_apply(ty, m.t + ix, m.Cy, iy, m.Cx) / (m.q * (double)n);
   }
+}
+
+// the entries of T^-1 for a periodic line of n cells (closed form above)
+static CircTaps circ_taps(int64_t n, double e, double d0) {
+  CircTaps T;
+  const double sq = sqrt(d0 * d0 - 4.0 * e * e), r = (sq - d0) / (2.0 * e);
+  const double rn = pow(r, (double)n);
+  T.full = n <= kCircTaps ? 1 : 0;
+  const int cnt = T.full ? (int)n : kCircHalf + 1;
+  for (int k = 0; k < kCircTaps; ++k) T.c[k] = 0.0;
+  for (int k = 0; k < cnt; ++k)
+    T.c[k] = (pow(r, (double)k) + pow(r, (double)(n - k))) / ((1.0 - rn) * sq);
+  return T;
 }
 
 // after the iterations: the unknowns of empty cells from their own rows
@@ -397,8 +382,7 @@ cudaError_t launch_deposit2d(int64_t Cx, int64_t Cy, const int64_t* cell_off, co
 
 size_t reconstruct2d_ws_bytes(int D, int64_t Cx, int64_t Cy) {
   const int64_t C = Cx * Cy;
-  const size_t dbl = (size_t)(9 + D + 1) * C + 4 * (size_t)C + (3 * (size_t)Cx + 2) +
-                     (3 * (size_t)Cy + 2) + (kMesh2dMaxIter + 1) + 1;
+  const size_t dbl = (size_t)(9 + D + 1) * C + 4 * (size_t)C + (kMesh2dMaxIter + 1) + 1;
   return dbl * sizeof(double) + 1024;
 }
 
@@ -424,17 +408,14 @@ cudaError_t launch_reconstruct2d(int D, int64_t Cx, int64_t Cy, int Kmax, const 
   m.dA = m.b + C;
   m.r = m.dA + C;
   m.t = m.r + C;
-  double* fx = m.t + C;
-  double* fy = fx + 3 * Cx + 2;
-  m.tx = fx;
-  m.ty = fy;
-  m.norm = (unsigned long long*)(fy + 3 * Cy + 2);
+  m.norm = (unsigned long long*)(m.t + C);
   m.scale = m.norm + kMesh2dMaxIter + 1;
   int* converged = (int*)(m.scale + 1);
   m.tol = kMesh2dTol;
   if (dA_user) m.dA = dA_user;
   const double e = order == 1 ? 0.125 : 1.0 / 6.0;
   const double d0 = order == 1 ? 0.75 : 2.0 / 3.0;
+  const CircTaps tx = circ_taps(Cx, e, d0), ty = circ_taps(Cy, e, d0);
 
   constexpr int NW = 4;
   const int g = grid_cap(C, NW, 152 * 16);
@@ -444,7 +425,6 @@ cudaError_t launch_reconstruct2d(int D, int64_t Cx, int64_t Cy, int Kmax, const 
     recon2d_stats_kernel<1, NW><<<g, NW * 32, 0, s>>>(Cx, C, Kmax, K, prm, out_off, seed, order, cstat);
   else
     recon2d_stats_kernel<3, NW><<<g, NW * 32, 0, s>>>(Cx, C, Kmax, K, prm, out_off, seed, order, cstat);
-  circ_factor_kernel<<<1, 32, 0, s>>>(Cx, Cy, e, d0, fx, fy);
   const int ga = grid_cap(C > kMesh2dMaxIter + 1 ? C : kMesh2dMaxIter + 1, 256, 2048);
   assemble2d_kernel<<<ga, 256, 0, s>>>(m, W, rho_target, dx * dy, kMesh2dMaxIter);
   // norm[i] for i < C is cleared by the grid-stride loop above; meshes with
@@ -456,8 +436,8 @@ cudaError_t launch_reconstruct2d(int D, int64_t Cx, int64_t Cy, int Kmax, const 
   const int gr = grid_cap(C, 256, 152 * 4);
   for (int it = 0; it < kMesh2dMaxIter; ++it) {
     mm2d_residual_kernel<<<gr, 256, 0, s>>>(m, it);
-    mm2d_xsweep_kernel<<<grid_cap(Cy, 64, 1024), 64, 0, s>>>(m, it, e, d0);
-    mm2d_ysweep_kernel<<<grid_cap(Cx, 64, 1024), 64, 0, s>>>(m, it, e, d0);
+    mm2d_xsweep_kernel<<<gr, 256, 0, s>>>(m, it, tx);
+    mm2d_ysweep_kernel<<<gr, 256, 0, s>>>(m, it, ty);
   }
   mm2d_residual_kernel<<<gr, 256, 0, s>>>(m, kMesh2dMaxIter);
   mm2d_finish_kernel<<<grid_cap(C, 256, 1024), 256, 0, s>>>(m, kMesh2dMaxIter, converged);
