@@ -62,7 +62,7 @@ typedef struct gm_config {
   uint64_t seed;       /* Philox key: initial picks (compress) / sampler (reconstruct) */
   double L;            /* periodic domain length; dx = L / C */
   double q;            /* species charge q_p */
-  int32_t threads_per_cell; /* EM CTA size: 0 = library choice, else 128 or 256 */
+  int32_t threads_per_cell; /* EM CTA size: 0 = library choice, else 64, 128 or 256 */
   int32_t smem_particles;   /* EM shared-memory tile in particles: 0 = library choice;
                                cells with more particles use an L2-resident global tile */
   int32_t precision;        /* penalised sweeps' M-step (covariance, Cholesky factor,
@@ -454,23 +454,26 @@ int gm_graph_destroy(gm_graph* g);
  * has no counterpart (it runs one cell per process on CPUs).
  *
  * Times gm_compress on a sample of the batch (the first cells, about two
- * waves of CTAs) for every candidate shape: threads_per_cell in {128, 256}
- * and shared-tile capacities smem_particles covering the library default
- * and the 90th, 99th and 100th percentiles of the cell sizes (only those
- * that fit in shared memory; larger cells use the L2-resident global
- * tile).  Each trial runs a fixed number of sweeps (tol = 0, max_sweeps =
+ * waves of CTAs) for every candidate shape: threads_per_cell in
+ * {64, 128, 256} and shared-tile capacities smem_particles covering the
+ * library default and the 90th, 99th, 100th and 50th percentiles of the
+ * cell sizes (only those that fit in shared memory; larger cells use the
+ * L2-resident global tile; small CTAs with small tiles put more cells on
+ * an SM at once, which pays where per-cell serial phases dominate).  Each trial runs a fixed number of sweeps (tol = 0, max_sweeps =
  * sweeps_per_trial, 0 = 24) so that every candidate does the same work,
  * and the fastest of two repetitions counts; the library default (256
  * threads, default tile) is kept unless another candidate is more than 3 %
  * faster.  Writes the winner into
  * cfg->threads_per_cell and cfg->smem_particles and, if timings_ms is not
- * NULL, the trial times (host array of at least 8 floats, -1 for skipped
- * candidates, candidate i = (threads 128 : 256 for i even : odd, tile i/2)).
+ * NULL, the trial times (host array of at least GM_TUNE_CANDIDATES floats,
+ * -1 for skipped candidates; candidate i has threads_per_cell
+ * {64, 128, 256}[i % 3] and tile i / 3).
  * Arguments as gm_compress (device arrays); cell_off is copied to the host,
  * so the call synchronises `stream`.  Results of later gm_compress calls do
  * not depend on the tile; the CTA size changes the order of FP32 partial
  * sums only.  Returns GM_OK or an error code; cfg is unchanged on error.
  */
+#define GM_TUNE_CANDIDATES 15
 int gm_autotune(gm_config* cfg, int64_t C, int64_t n_particles, const int64_t* cell_off,
                 const double* x, const void* v, int32_t v_is_f64, const double* alpha,
                 int32_t sweeps_per_trial, float* timings_ms, void* stream);

@@ -58,8 +58,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(r.stdout + r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(compile_one, srcs))
+    # the largest units (the EM kernel instantiations) start first
+    order = sorted(srcs, key=lambda f: (not os.path.basename(f).startswith("gm_em"), f))
+    workers = max(1, min(16, len(srcs), os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        objs = list(ex.map(compile_one, order))
     tmp = LIB + f".tmp{os.getpid()}"
     r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:

@@ -100,6 +100,7 @@ struct EmCtl {
   double mean[D], sc[D], isc[D];
   float meanf[D], scf[D];
   double Nd, W, L, logjac, logN;
+  double cov0[D * (D + 1) / 2];  // the cell's weighted covariance (original coordinates)
   // FP32 convergence test on the centred log-likelihood (natural log, up to
   // the constant Lbase that c0 removes)
   float Lf, Lfprev, Lbase, halfLogNf;
@@ -326,6 +327,59 @@ __device__ __forceinline__ void block_partials(const float (&v)[NV], float (&red
   __syncthreads();
 }
 
+// one component (thread 0): fw, fmu, fS of the final mixture = the sample
+// moments; L = eq. (lnL-GM) in closed form: -(N/2)(D ln 2 pi + ln|Sigma| +
+// D) - (T/2) ln N (d = T parameters, ln omega = 0); the covariance passed
+// the floor in the prologue
+template <int D, int NT, typename R>
+__device__ void k1_closed_form(EmCtl<D, NT / 32, R>& c) {
+  constexpr int NM = D * (D + 1) / 2;
+  constexpr int T = D * (D + 3) / 2;
+  c.K = 1;
+  c.fw[0] = 1.0;
+  for (int d = 0; d < D; ++d) c.fmu[0][d] = 0.0;
+  for (int i = 0; i < NM; ++i) c.fS[0][i] = c.cov0[i];
+  double L2[3][3] = {{0}}, logdet = 0.0;
+  for (int x = 0; x < D; ++x)
+    for (int y = 0; y <= x; ++y) {
+      double sv = c.cov0[tri<D>(y, x)];
+      for (int m = 0; m < y; ++m) sv -= L2[x][m] * L2[y][m];
+      if (x == y) {
+        L2[x][x] = sqrt(sv);
+        logdet += 2.0 * log(L2[x][x]);
+      } else {
+        L2[x][y] = sv / L2[y][y];
+      }
+    }
+  c.L = -0.5 * c.Nd * ((double)D * 1.8378770664093454836 + logdet + (double)D) - 0.5 * (double)T * c.logN;
+  c.final_pd = 1;
+}
+
+// the cell's outputs (thread 0 writes, then a barrier)
+template <int D, int NT, typename R>
+__device__ __forceinline__ void write_cell(const EmParams& a, EmCtl<D, NT / 32, R>& c, int64_t j,
+                                           double* prm_out) {
+  constexpr int NM = D * (D + 1) / 2;
+  constexpr int P = 1 + D + NM;
+  if (threadIdx.x == 0) {
+    const int Kf = c.K;
+    for (int k = 0; k < Kf; ++k) {
+      double* r = prm_out + (size_t)k * P;
+      r[0] = c.fw[k];
+      for (int d = 0; d < D; ++d) r[1 + d] = c.mean[d] + c.fmu[k][d];
+      for (int q = 0; q < NM; ++q) r[1 + D + q] = c.fS[k][q];
+    }
+    for (int i = Kf * P; i < a.Kmax * P; ++i) prm_out[i] = 0.0;
+    a.K_out[j] = Kf;
+    a.W_out[j] = c.W;
+    a.lnL_out[j] = c.final_pd ? c.L : 0.0;
+    if (a.sweeps_out) a.sweeps_out[j] = c.sweep;
+    if (a.kwork_out) a.kwork_out[j] = c.kwork;
+    a.status_out[j] = c.status;
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // one cell, after its moments are known and it is not degenerate.  The
 // particle tile (shared or global) holds N rounded up to even particles (a
@@ -353,33 +407,6 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
   const int P2 = (N + 1) >> 1;  // particle pairs
   const int ys2 = ys >> 1;
 
-  // ---- stage whitened velocities and normalised weights ------------------
-  {
-    const double nw = c.Nd / c.W;
-    double sa[1] = {0.0};
-    for (int p = tid; p < 2 * P2; p += NT) {
-      if (p < N) {
-#pragma unroll
-        for (int d = 0; d < D; ++d)
-          Y[d * ys + p] = (float)(((double)vin[(int64_t)d * a.n + off + p] - c.mean[d]) * c.isc[d]);
-        const float ah = (float)(a.alpha[off + p] * nw);
-        GAT[4 * (p >> 1) + 2 + (p & 1)] = ah;
-        sa[0] += (double)ah;
-      } else {  // zero-weight pad particle
-#pragma unroll
-        for (int d = 0; d < D; ++d) Y[d * ys + p] = 0.0f;
-        GAT[4 * (p >> 1) + 2 + (p & 1)] = 0.0f;
-      }
-    }
-    block_sum_d<D, NT, 1, R>(c, sa);
-    if (tid == 0) {
-      c.sumAH = c.res[0];
-      c.sumAHf = (float)c.res[0];
-      c.c0 = -2.0471975511965976f * D;  // mean log2 density of a standard normal
-      c.NdR = (R)c.Nd;
-      c.halfLogNf = (float)(0.5 * c.logN);
-    }
-  }
   // ---- initialisation --------------------------------------------------
   // A supplied initial mixture (learned initialisation) is used when given:
   // components failing the Cholesky floor are dropped, the count is capped
@@ -471,6 +498,49 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
       c.elc[k] = elc;
       c.eb[k] = lg2((float)c.u[k]) + elc;
       pack_econst<D>(c.emu[k], c.eA[k], c.eb[k], c.ec[k]);
+    }
+  }
+  __syncthreads();
+  // ---- one component: the EM's fixed point in closed form ----------------
+  // With K = 1 every responsibility is the particle's weight, so one EM step
+  // from any start gives the weighted sample mean and covariance (Sec.
+  // 2.3.1), and eq. (lnL-GM) is -(N/2)(D ln 2 pi + ln|Sigma| + D) - (T/2) ln N.
+  // Reported as one sweep without component E-steps (kwork 0).
+  if (c.K == 1) {
+    if (tid == 0) {
+      c.sweep = 1;
+      c.kwork = 0;
+      k1_closed_form<D, NT, R>(c);
+    }
+    __syncthreads();
+    write_cell<D, NT, R>(a, c, j, prm_out);
+    return;
+  }
+  // ---- stage whitened velocities and normalised weights ------------------
+  {
+    const double nw = c.Nd / c.W;
+    double sa[1] = {0.0};
+    for (int p = tid; p < 2 * P2; p += NT) {
+      if (p < N) {
+#pragma unroll
+        for (int d = 0; d < D; ++d)
+          Y[d * ys + p] = (float)(((double)vin[(int64_t)d * a.n + off + p] - c.mean[d]) * c.isc[d]);
+        const float ah = (float)(a.alpha[off + p] * nw);
+        GAT[4 * (p >> 1) + 2 + (p & 1)] = ah;
+        sa[0] += (double)ah;
+      } else {  // zero-weight pad particle
+#pragma unroll
+        for (int d = 0; d < D; ++d) Y[d * ys + p] = 0.0f;
+        GAT[4 * (p >> 1) + 2 + (p & 1)] = 0.0f;
+      }
+    }
+    block_sum_d<D, NT, 1, R>(c, sa);
+    if (tid == 0) {
+      c.sumAH = c.res[0];
+      c.sumAHf = (float)c.res[0];
+      c.c0 = -2.0471975511965976f * D;  // mean log2 density of a standard normal
+      c.NdR = (R)c.Nd;
+      c.halfLogNf = (float)(0.5 * c.logN);
     }
   }
   if (tid == 0) {
@@ -892,6 +962,12 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
   }
 
   // ---- final unpenalised step (Sec. 2.3.1), FP64 ---------------------------
+  if (c.K == 1) {  // the final step of one component: the sample moments
+    if (tid == 0) k1_closed_form<D, NT, R>(c);
+    __syncthreads();
+    write_cell<D, NT, R>(a, c, j, prm_out);
+    return;
+  }
   if (tid == 0) c.Kf = 0;
   __syncthreads();
   {
@@ -996,23 +1072,7 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
     }
     __syncthreads();
   }
-  if (tid == 0) {
-    const int Kf = c.K;
-    for (int k = 0; k < Kf; ++k) {
-      double* r = prm_out + (size_t)k * P;
-      r[0] = c.fw[k];
-      for (int d = 0; d < D; ++d) r[1 + d] = c.mean[d] + c.fmu[k][d];
-      for (int q = 0; q < NM; ++q) r[1 + D + q] = c.fS[k][q];
-    }
-    for (int i = Kf * P; i < a.Kmax * P; ++i) prm_out[i] = 0.0;
-    a.K_out[j] = Kf;
-    a.W_out[j] = c.W;
-    a.lnL_out[j] = c.final_pd ? c.L : 0.0;
-    if (a.sweeps_out) a.sweeps_out[j] = c.sweep;
-    if (a.kwork_out) a.kwork_out[j] = c.kwork;
-    a.status_out[j] = c.status;
-  }
-  __syncthreads();
+  write_cell<D, NT, R>(a, c, j, prm_out);
   (void)NW;
 }
 
@@ -1116,6 +1176,7 @@ __global__ void __launch_bounds__(NT, (D == 1 ? 1024 : 512) / NT) em_kernel(EmPa
         if (c.degenerate) {
           for (int i = 0; i < NM; ++i) c.fS[0][i] = cov[i];
         } else {
+          for (int i = 0; i < NM; ++i) c.cov0[i] = cov[i];
           c.logjac = 0.0;
           c.logN = log(c.Nd);
           for (int d = 0; d < D; ++d) {

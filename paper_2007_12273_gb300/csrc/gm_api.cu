@@ -236,7 +236,8 @@ static int compress_impl(const gm_config* cfg, int64_t C, int64_t n_particles,
   cudaStream_t s = (cudaStream_t)stream;
   const int D = cfg->D;
   int nt = cfg->threads_per_cell > 0 ? cfg->threads_per_cell : 256;
-  if (nt != 128 && nt != 256) return fail(GM_ERR_ARG, "threads_per_cell must be 128 or 256");
+  if (nt != 64 && nt != 128 && nt != 256)
+    return fail(GM_ERR_ARG, "threads_per_cell must be 64, 128 or 256");
   int cap = cfg->smem_particles > 0 ? cfg->smem_particles : (D == 1 ? 2560 : 3072);
   cap &= ~3;  // pair records of 16 bytes behind D arrays of cap floats
   if (cap < 4) cap = 4;

@@ -29,6 +29,13 @@ struct TrialOut {
 
 size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// candidates: CTA sizes x shared tiles; candidate i = (kTuneNT[i % 3], tile i / 3)
+constexpr int kTuneThreads = 3;
+constexpr int kTuneNT[kTuneThreads] = {64, 128, 256};
+constexpr int kTuneCaps = 5;
+constexpr int kTuneCands = kTuneThreads * kTuneCaps;
+static_assert(kTuneCands == GM_TUNE_CANDIDATES, "gm.h states the number of candidates");
+
 }  // namespace
 
 extern "C" int gm_autotune(gm_config* cfg, int64_t C, int64_t n_particles, const int64_t* cell_off,
@@ -77,7 +84,8 @@ extern "C" int gm_autotune(gm_config* cfg, int64_t C, int64_t n_particles, const
   add_cap(quant(0.90));
   add_cap(quant(0.99));
   add_cap(sizes.back());
-  if (caps.size() > 4) caps.resize(4);
+  add_cap(quant(0.50));  // small tiles: more (smaller) CTAs per SM
+  if (caps.size() > (size_t)kTuneCaps) caps.resize(kTuneCaps);
 
   // trial outputs
   TrialOut o;
@@ -98,16 +106,16 @@ extern "C" int gm_autotune(gm_config* cfg, int64_t C, int64_t n_particles, const
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   cudaEventCreate(&t0);
   cudaEventCreate(&t1);
-  float times[8];
-  for (int i = 0; i < 8; ++i) times[i] = -1.0f;
+  float times[kTuneCands];
+  for (int i = 0; i < kTuneCands; ++i) times[i] = -1.0f;
   int best = -1;
   int rc = GM_OK;
   for (size_t ci = 0; ci < caps.size() && rc == GM_OK; ++ci) {
-    for (int ti = 0; ti < 2; ++ti) {
+    for (int ti = 0; ti < kTuneThreads; ++ti) {
       gm_config tr = *cfg;
       tr.tol = 0.0;
       tr.max_sweeps = spt;
-      tr.threads_per_cell = ti == 0 ? 128 : 256;
+      tr.threads_per_cell = kTuneNT[ti];
       tr.smem_particles = caps[ci];
       tr.L = cfg->L * (double)S / (double)C;  // the sample keeps the cell width
       float tmin = -1.0f;
@@ -129,24 +137,25 @@ extern "C" int gm_autotune(gm_config* cfg, int64_t C, int64_t n_particles, const
         cudaEventElapsedTime(&ms, t0, t1);
         if (rep > 0 && (tmin < 0.0f || ms < tmin)) tmin = ms;
       }
-      times[(int)ci * 2 + ti] = tmin;
+      times[(int)ci * kTuneThreads + ti] = tmin;
     }
   }
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
   cudaFree(o.base);
   if (rc != GM_OK) return rc;
-  // the library default (256 threads, default tile: candidate 1) stays
+  // the library default (256 threads, default tile: candidate 2) stays
   // unless another shape is faster by more than 3 %: trials closer than
   // that are within the run-to-run spread
-  for (int i = 0; i < 8; ++i)
+  const int dflt = 2;
+  for (int i = 0; i < kTuneCands; ++i)
     if (times[i] >= 0.0f && (best < 0 || times[i] < times[best])) best = i;
-  if (best >= 0 && times[1] >= 0.0f && times[best] > 0.97f * times[1]) best = 1;
+  if (best >= 0 && times[dflt] >= 0.0f && times[best] > 0.97f * times[dflt]) best = dflt;
   if (best < 0) return tune_fail(GM_ERR_CUDA, "no candidate ran");
   if (timings_ms)
-    for (int i = 0; i < 8; ++i) timings_ms[i] = times[i];
-  cfg->threads_per_cell = (best % 2 == 0) ? 128 : 256;
-  cfg->smem_particles = caps[(size_t)(best / 2)];
+    for (int i = 0; i < kTuneCands; ++i) timings_ms[i] = times[i];
+  cfg->threads_per_cell = kTuneNT[best % kTuneThreads];
+  cfg->smem_particles = caps[(size_t)(best / kTuneThreads)];
   gmcr::record_error(GM_OK, "");
   return GM_OK;
 }

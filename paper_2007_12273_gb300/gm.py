@@ -30,6 +30,7 @@ ST_NEG_WEIGHT = 0x200
 ST_MM_EMPTY_COL = 0x400
 ST_NO_MIXTURE = 0x800
 ST_MM_NOT_CONVERGED = 0x1000
+TUNE_CANDIDATES = 15  # GM_TUNE_CANDIDATES
 
 EXPORTED = ("gm_compress", "gm_reconstruct", "gm_moments", "gm_mixture_moments",
             "gm_last_error", "gm_shutdown", "gm_reconstruct_noalloc", "gm_gemm_bf16",
@@ -485,11 +486,12 @@ class Net:
 def gm_autotune(cfg: GMConfig, cell_off, x, v, alpha, sweeps_per_trial: int = 0, stream=None):
     """Times the EM launch shapes on a sample of the batch and writes the
     fastest into ``cfg`` (threads_per_cell, smem_particles).  Returns the
-    trial times in ms (8 entries, -1 = not run)."""
+    trial times in ms (TUNE_CANDIDATES entries, -1 = not run; candidate i
+    has threads_per_cell (64, 128, 256)[i % 3] and tile i // 3)."""
     lib = load()
     C = cell_off.shape[0] - 1
     n = x.shape[0]
-    t = (ct.c_float * 8)()
+    t = (ct.c_float * TUNE_CANDIDATES)()
     rc = lib.gm_autotune(ct.byref(cfg), C, n, _ptr(cell_off), _ptr(x), _ptr(v),
                          1 if v.dtype == torch.float64 else 0, _ptr(alpha), int(sweeps_per_trial), t,
                          _stream_ptr(stream))

@@ -144,7 +144,7 @@ def test_autotune_picks_a_valid_shape_and_the_fit_stays_on_the_oracle(gm):
     cfg = gm.config(wl.params)
     off, x, v, a = inputs(wl)
     t = gm.gm_autotune(cfg, off, x, v, a, sweeps_per_trial=8)
-    assert cfg.threads_per_cell in (128, 256)
+    assert cfg.threads_per_cell in (64, 128, 256)
     assert cfg.smem_particles > 0 and cfg.smem_particles % 4 == 0
     ran = [z for z in t if z >= 0]
     assert len(ran) >= 2 and min(ran) > 0
@@ -166,3 +166,21 @@ def test_autotune_picks_a_valid_shape_and_the_fit_stays_on_the_oracle(gm):
     lnL = out["lnL"].cpu().numpy()[sub]
     agree = (K == ref["K"]) & (np.abs(lnL - ref["lnL"]) <= 1e-5 * np.abs(ref["lnL"]))
     assert agree.mean() >= 0.6, agree.mean()
+
+
+@pytest.mark.parametrize("nt,cap", [(64, 0), (64, 256), (128, 512)])
+def test_small_ctas_fit_like_the_oracle(gm, nt, cap):
+    """64- and 128-thread CTAs (more cells per SM) with small and default
+    tiles: the fit keeps the oracle's K and lnL under the equal-sweep rule,
+    1V and 3V."""
+    from parity_helpers import agreement
+    for wl in (workloads.mixture_1d1v(C=48, mean_n=700, clip=(100, 2000), seed=36),
+               workloads.with_weights(workloads.bimaxwellian_1d3v(C=24, ppc=600, seed=37))):
+        cfg = gm.config(wl.params, threads_per_cell=nt, smem_particles=cap)
+        out = gm.gm_compress(cfg, *inputs(wl))
+        g = {k: t.cpu().numpy() for k, t in out.items()}
+        ref = oracle.compress(wl.params, wl.cell_off, wl.x, wl.v, wl.alpha, nthreads=8)
+        agree, eq = agreement(g, ref, wl)
+        print(f"nt {nt} cap {cap} D {wl.D}: natural {agree.mean():.3f}, equal sweeps {eq.mean():.3f}")
+        assert eq.mean() >= 0.95 and agree.mean() >= 0.5
+        np.testing.assert_allclose(g["W"], ref["W"], rtol=1e-13)
