@@ -58,38 +58,40 @@ constexpr double kAAStart = 1e-4;      // AA starts when |dL| <= kAAStart |L|
 constexpr double kFix = 1099511627776.0;  // 2^40: fixed point of the K-means sums
 
 // Anderson state (Walker & Ni 2011, type II): the iterate x, G(x), the
-// extrapolation, the previous (f, G) pair and the last h <= m differences
+// extrapolation, the previous (f, G) pair and the last h <= m differences,
+// kept in a ring of m slots (the oldest at slot head) with their Gram
+// matrix, which only gains the newest column's row each step
 template <int MAXN>
 struct AAState {
   double th[MAXN], tg[MAXN], tn[MAXN], fprev[MAXN], gprev[MAXN];
   double dF[kStdMaxM][MAXN], dG[kStdMaxM][MAXN];
   double gram[kStdMaxM][kStdMaxM], rhs[kStdMaxM], gam[kStdMaxM];
-  int h, have;
+  int h, have, head;
 };
 
 // One Anderson step by a whole warp (FP64): f = G(x) - x; the difference
 // with the previous pair joins the history (the oldest dropped beyond m);
 // gamma from (dF^T dF + 1e-12 max diag I) gamma = dF^T f by Cholesky on
-// lane 0; tn = G(x) - dG gamma.  Returns true if the extrapolation was
-// made (tn valid); false with no history or a pivot that is not positive.
-// Reads s.th, s.tg (n values); the caller syncs the warp before and after.
+// lane 0 (columns oldest first); tn = G(x) - dG gamma.  The dot products a
+// step needs (dF^T f, and the new column against every column) are summed
+// per lane in one pass and reduced together.  Returns true if the
+// extrapolation was made (tn valid); false with no history or a pivot that
+// is not positive.  Reads s.th, s.tg (n values); the caller syncs the warp
+// before and after; h = 0 clears the history.
 template <int MAXN>
 __device__ bool aa_warp_step(AAState<MAXN>& s, int n, int m) {
   const int lane = threadIdx.x & 31;
-  int h = s.h;
+  int h = s.h, head = h > 0 ? s.head : 0, nw = -1;
   if (m > 0 && s.have) {
-    if (h == m) {
-      for (int col = 1; col < m; ++col)
-        for (int i = lane; i < n; i += 32) {
-          s.dF[col - 1][i] = s.dF[col][i];
-          s.dG[col - 1][i] = s.dG[col][i];
-        }
+    if (h == m) {  // drop the oldest: its slot takes the new column
+      head = head + 1 == m ? 0 : head + 1;
       --h;
     }
-    __syncwarp();
+    nw = head + h;
+    nw = nw >= m ? nw - m : nw;
     for (int i = lane; i < n; i += 32) {
-      s.dF[h][i] = (s.tg[i] - s.th[i]) - s.fprev[i];
-      s.dG[h][i] = s.tg[i] - s.gprev[i];
+      s.dF[nw][i] = (s.tg[i] - s.th[i]) - s.fprev[i];
+      s.dG[nw][i] = s.tg[i] - s.gprev[i];
     }
     ++h;
   }
@@ -100,34 +102,52 @@ __device__ bool aa_warp_step(AAState<MAXN>& s, int n, int m) {
   __syncwarp();
   if (lane == 0) {
     s.h = h;
+    s.head = head;
     s.have = 1;
   }
   __syncwarp();
   if (h == 0) return false;
-  for (int a0 = 0; a0 < h; ++a0) {
-    for (int c1 = 0; c1 <= a0; ++c1) {
-      double t = 0.0;
-      for (int i = lane; i < n; i += 32) t += s.dF[a0][i] * s.dF[c1][i];
-      t = warp_sum(t);
-      if (lane == 0) s.gram[a0][c1] = s.gram[c1][a0] = t;
-    }
-    double t = 0.0;
-    for (int i = lane; i < n; i += 32) t += s.dF[a0][i] * s.fprev[i];
-    t = warp_sum(t);
-    if (lane == 0) s.rhs[a0] = t;
+  int slot[kStdMaxM];
+#pragma unroll
+  for (int a = 0; a < kStdMaxM; ++a) {
+    const int q = head + a;
+    slot[a] = q >= m ? q - m : q;
   }
+  double part[2 * kStdMaxM];
+#pragma unroll
+  for (int a = 0; a < 2 * kStdMaxM; ++a) part[a] = 0.0;
+  for (int i = lane; i < n; i += 32) {
+    const double fi = s.fprev[i], di = s.dF[nw][i];
+#pragma unroll
+    for (int a = 0; a < kStdMaxM; ++a)
+      if (a < h) {
+        const double v = s.dF[slot[a]][i];
+        part[a] = fma(v, fi, part[a]);
+        part[kStdMaxM + a] = fma(v, di, part[kStdMaxM + a]);
+      }
+  }
+#pragma unroll
+  for (int a = 0; a < 2 * kStdMaxM; ++a)
+    if ((a % kStdMaxM) < h) part[a] = warp_sum(part[a]);
+  if (lane == 0)
+#pragma unroll
+    for (int a = 0; a < kStdMaxM; ++a)
+      if (a < h) {
+        s.rhs[slot[a]] = part[a];
+        s.gram[nw][slot[a]] = part[kStdMaxM + a];
+        s.gram[slot[a]][nw] = part[kStdMaxM + a];
+      }
   __syncwarp();
   int solved = 0;
   if (lane == 0) {
-    double dmax = 0.0;
-    for (int a0 = 0; a0 < h; ++a0) dmax = fmax(dmax, s.gram[a0][a0]);
+    // Cholesky in place (lower triangle of Lm), columns oldest first
+    double Lm[kStdMaxM][kStdMaxM], z[kStdMaxM], dmax = 0.0;
+    for (int a0 = 0; a0 < h; ++a0) dmax = fmax(dmax, s.gram[slot[a0]][slot[a0]]);
     if (dmax > 0.0) {
-      double Lm[kStdMaxM][kStdMaxM], z[kStdMaxM];
       solved = 1;
-      for (int a0 = 0; a0 < h; ++a0) s.gram[a0][a0] += 1e-12 * dmax;
       for (int a0 = 0; a0 < h && solved; ++a0)
         for (int c1 = 0; c1 <= a0 && solved; ++c1) {
-          double t = s.gram[a0][c1];
+          double t = s.gram[slot[a0]][slot[c1]] + (a0 == c1 ? 1e-12 * dmax : 0.0);
           for (int e = 0; e < c1; ++e) t -= Lm[a0][e] * Lm[c1][e];
           if (a0 == c1) {
             if (!(t > 0.0)) solved = 0;
@@ -138,15 +158,16 @@ __device__ bool aa_warp_step(AAState<MAXN>& s, int n, int m) {
         }
       if (solved) {
         for (int a0 = 0; a0 < h; ++a0) {
-          double t = s.rhs[a0];
+          double t = s.rhs[slot[a0]];
           for (int e = 0; e < a0; ++e) t -= Lm[a0][e] * z[e];
           z[a0] = t / Lm[a0][a0];
         }
         for (int a0 = h - 1; a0 >= 0; --a0) {
           double t = z[a0];
-          for (int e = a0 + 1; e < h; ++e) t -= Lm[e][a0] * s.gam[e];
-          s.gam[a0] = t / Lm[a0][a0];
+          for (int e = a0 + 1; e < h; ++e) t -= Lm[e][a0] * z[e];
+          z[a0] = t / Lm[a0][a0];
         }
+        for (int a0 = 0; a0 < h; ++a0) s.gam[slot[a0]] = z[a0];
       }
     }
   }
@@ -155,7 +176,7 @@ __device__ bool aa_warp_step(AAState<MAXN>& s, int n, int m) {
   if (!solved) return false;
   for (int i = lane; i < n; i += 32) {
     double t = s.tg[i];
-    for (int col = 0; col < h; ++col) t -= s.dG[col][i] * s.gam[col];
+    for (int a = 0; a < h; ++a) t -= s.dG[slot[a]][i] * s.gam[slot[a]];
     s.tn[i] = t;
   }
   __syncwarp();
@@ -546,20 +567,30 @@ __global__ void __launch_bounds__(NT, (D == 1 ? 1024 : 512) / NT) std_kernel(Std
     for (;;) {
       const int K = c.K;
       const float c0 = c.c0;
-      // exact pass: m_p = max_k log2(omega_k f_k), s_p, and the log-likelihood
+      // exact pass: m_p = max_k log2(omega_k f_k) and s_p = sum_k 2^(l_k - m_p)
+      // in one evaluation per component (a new maximum rescales the running
+      // sum), R_p = ah_p / s_p for the component passes, and the
+      // log-likelihood
       {
         float accl = 0.0f;
         for (int p = tid; p < N; p += NT) {
           float y[D], dd[D];
 #pragma unroll
           for (int d = 0; d < D; ++d) y[d] = Y[d * ys + p];
-          float m = -3.0e38f;
-          for (int k = 0; k < K; ++k) m = fmaxf(m, lg_eval<D>(c.emu[k], c.eA[k], c.eb[k], y, dd));
-          float s = 0.0f;
-          for (int k = 0; k < K; ++k) s += ex2(lg_eval<D>(c.emu[k], c.eA[k], c.eb[k], y, dd) - m);
-          SS[p] = s;
+          float m = -3.0e38f, s = 0.0f;
+          for (int k = 0; k < K; ++k) {
+            const float l = lg_eval<D>(c.emu[k], c.eA[k], c.eb[k], y, dd);
+            if (l > m) {
+              s = fmaf(s, ex2(m - l), 1.0f);
+              m = l;
+            } else {
+              s += ex2(l - m);
+            }
+          }
+          const float ah = AH[p];
+          SS[p] = ah * rcp_approx(s);
           MM[p] = m;
-          accl = fmaf(AH[p], (m - c0) + lg2(s), accl);
+          accl = fmaf(ah, (m - c0) + lg2(s), accl);
         }
         accl = warp_sum(accl);
         if (lane == 0) c.redl[wid] = accl;
@@ -574,8 +605,7 @@ __global__ void __launch_bounds__(NT, (D == 1 ? 1024 : 512) / NT) std_kernel(Std
           float y[D], dd[D];
 #pragma unroll
           for (int d = 0; d < D; ++d) y[d] = Y[d * ys + p];
-          const float g = ex2(lg_eval<D>(c.emu[k], c.eA[k], c.eb[k], y, dd) - MM[p]);
-          const float gam = AH[p] * g * rcp_approx(SS[p]);
+          const float gam = ex2(lg_eval<D>(c.emu[k], c.eA[k], c.eb[k], y, dd) - MM[p]) * SS[p];
           acc[0] += gam;
           int t = 1 + D;
 #pragma unroll
@@ -856,10 +886,16 @@ __global__ void __launch_bounds__(NT, (D == 1 ? 1024 : 512) / NT) std_kernel(Std
         float y[D], dd[D];
 #pragma unroll
         for (int d = 0; d < D; ++d) y[d] = Y[d * ys + p];
-        float m = -3.0e38f;
-        for (int k = 0; k < K; ++k) m = fmaxf(m, lg_eval<D>(c.emu[k], c.eA[k], c.eb[k], y, dd));
-        float s = 0.0f;
-        for (int k = 0; k < K; ++k) s += ex2(lg_eval<D>(c.emu[k], c.eA[k], c.eb[k], y, dd) - m);
+        float m = -3.0e38f, s = 0.0f;
+        for (int k = 0; k < K; ++k) {
+          const float l = lg_eval<D>(c.emu[k], c.eA[k], c.eb[k], y, dd);
+          if (l > m) {
+            s = fmaf(s, ex2(m - l), 1.0f);
+            m = l;
+          } else {
+            s += ex2(l - m);
+          }
+        }
         accl = fmaf(AH[p], (m - c0) + lg2(s), accl);
       }
       double v1[1] = {(double)accl};

