@@ -158,17 +158,18 @@ __device__ __forceinline__ float rsqrt_nr(float x) {
 
 // Cholesky of the upper-triangle S (precision R); returns false if a pivot
 // is not positive or, measured in the original coordinates (pivots scale by
-// sc_i^2), falls under 1e-13 * sum_d (Sigma_dd + mu_d^2).  Lc[i][i] holds the
-// pivot's square root and ri[i] its reciprocal.
+// sc_i^2), falls under rel * sum_d (Sigma_dd + mu_d^2) (rel = 1e-13: the
+// covariance floor).  Lc[i][i] holds the pivot's square root and ri[i] its
+// reciprocal.
 template <int D, typename R, typename M>
 __device__ bool chol_whitened(const R* S, const R* mu, const M* mean, const M* sc,
-                              R (&Lc)[3][3], R (&ri)[3]) {
+                              R (&Lc)[3][3], R (&ri)[3], double rel = 1e-13) {
   R scale2 = 0;
   for (int d = 0; d < D; ++d) {
     const R m = (R)mean[d] + (R)sc[d] * mu[d];
     scale2 += (R)(sc[d] * sc[d]) * S[tri<D>(d, d)] + m * m;
   }
-  const R fl = (R)1e-13 * scale2;
+  const R fl = (R)rel * scale2;
   for (int i = 0; i < D; ++i)
     for (int j = 0; j <= i; ++j) {
       R s = S[tri<D>(j, i)];

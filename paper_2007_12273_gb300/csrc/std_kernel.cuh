@@ -69,6 +69,22 @@ struct AAState {
   int h, have, head;
 };
 
+// 1/sqrt(t) for t > 0 in FP64: an FP32 estimate (from t's exponent-scaled
+// FP32 value, so that t outside the FP32 range still gets one) refined by
+// two Newton steps y <- y (3 - t y^2) / 2 (each about doubles the correct
+// bits: ~2^-22 -> 2^-44 -> below FP64 rounding)
+__device__ __forceinline__ double rsqrt_nr_seed(double t) {
+  int ex;
+  const double m = frexp(t, &ex);  // t = m 2^ex, m in [1/2, 1)
+  const int e2 = ex & ~1;          // even part of the exponent
+  const double y0 = (double)rsqrt_approx((float)ldexp(m, ex - e2));
+  return ldexp(y0, -e2 / 2);
+}
+__device__ __forceinline__ double rsqrt_nr(double y, double t) {
+  y = y * (1.5 - 0.5 * t * y * y);
+  return y * (1.5 - 0.5 * t * y * y);
+}
+
 // One Anderson step by a whole warp (FP64): f = G(x) - x; the difference
 // with the previous pair joins the history (the oldest dropped beyond m);
 // gamma from (dF^T dF + 1e-12 max diag I) gamma = dF^T f by Cholesky on
@@ -141,7 +157,9 @@ __device__ bool aa_warp_step(AAState<MAXN>& s, int n, int m) {
   int solved = 0;
   if (lane == 0) {
     // Cholesky in place (lower triangle of Lm), columns oldest first
-    double Lm[kStdMaxM][kStdMaxM], z[kStdMaxM], dmax = 0.0;
+    // (the reciprocal of each pivot's square root by two Newton steps from
+    // the FP32 estimate: multiplications instead of FP64 divides)
+    double Lm[kStdMaxM][kStdMaxM], rl[kStdMaxM], z[kStdMaxM], dmax = 0.0;
     for (int a0 = 0; a0 < h; ++a0) dmax = fmax(dmax, s.gram[slot[a0]][slot[a0]]);
     if (dmax > 0.0) {
       solved = 1;
@@ -150,22 +168,27 @@ __device__ bool aa_warp_step(AAState<MAXN>& s, int n, int m) {
           double t = s.gram[slot[a0]][slot[c1]] + (a0 == c1 ? 1e-12 * dmax : 0.0);
           for (int e = 0; e < c1; ++e) t -= Lm[a0][e] * Lm[c1][e];
           if (a0 == c1) {
-            if (!(t > 0.0)) solved = 0;
-            else Lm[a0][a0] = sqrt(t);
+            if (!(t > 0.0) || !(t < 1e300)) {
+              solved = 0;
+            } else {
+              const double r = rsqrt_nr(rsqrt_nr_seed(t), t);
+              rl[a0] = r;
+              Lm[a0][a0] = t * r;
+            }
           } else {
-            Lm[a0][c1] = t / Lm[c1][c1];
+            Lm[a0][c1] = t * rl[c1];
           }
         }
       if (solved) {
         for (int a0 = 0; a0 < h; ++a0) {
           double t = s.rhs[slot[a0]];
           for (int e = 0; e < a0; ++e) t -= Lm[a0][e] * z[e];
-          z[a0] = t / Lm[a0][a0];
+          z[a0] = t * rl[a0];
         }
         for (int a0 = h - 1; a0 >= 0; --a0) {
           double t = z[a0];
           for (int e = a0 + 1; e < h; ++e) t -= Lm[e][a0] * z[e];
-          z[a0] = t / Lm[a0][a0];
+          z[a0] = t * rl[a0];
         }
         for (int a0 = 0; a0 < h; ++a0) s.gam[slot[a0]] = z[a0];
       }
@@ -192,6 +215,7 @@ struct StdCtl {
   static constexpr int NRED = pow2_at_least(NS);
   // the cell
   double mean[D], sc[D], isc[D], S0[NM];
+  float meanf[D], scf[D], rsumAH;  // FP32 copies for the iteration's M-steps
   double W, Nd, sumAH, logjac, L, Lprev;
   float c0;
   int64_t cell;
@@ -239,15 +263,38 @@ __device__ __forceinline__ void std_bsum(StdCtl<D, NW>& c, double (&v)[NV]) {
 
 // E-step constants of component k from its FP64 whitened (w, mu, S);
 // false if the covariance fails the Cholesky floor (original coordinates)
+// The covariance floor test of the iteration (FP64 S, mu in whitened
+// coordinates): FP32 first, accepted only if every pivot clears 1e-6 of the
+// floor's scale (far above FP32 rounding); otherwise FP64 with the floor
+// itself (1e-13), as the oracle has it.  Factors returned in FP32 (the
+// E-step's precision).
+template <int D>
+__device__ bool std_chol(const double* S, const double* mu, const double* mean, const double* sc,
+                         const float* meanf, const float* scf, float (&Lc)[3][3], float (&ri)[3]) {
+  constexpr int NM = D * (D + 1) / 2;
+  float Sf[NM], muf[D];
+  for (int q = 0; q < NM; ++q) Sf[q] = (float)S[q];
+  for (int d = 0; d < D; ++d) muf[d] = (float)mu[d];
+  if (chol_whitened<D, float, float>(Sf, muf, meanf, scf, Lc, ri, 1e-6)) return true;
+  double L64[3][3], r64[3];
+  if (!chol_whitened<D, double, double>(S, mu, mean, sc, L64, r64)) return false;
+  for (int i = 0; i < D; ++i) {
+    ri[i] = (float)r64[i];
+    for (int j = 0; j <= i; ++j) Lc[i][j] = (float)L64[i][j];
+  }
+  return true;
+}
+
 template <int D, int NW>
 __device__ bool std_econst(StdCtl<D, NW>& c, int k) {
   constexpr int NM = D * (D + 1) / 2;
-  double Lc[3][3], ri[3];
-  if (!chol_whitened<D, double, double>(c.S[k], c.mu[k], c.mean, c.sc, Lc, ri)) return false;
+  float Lc[3][3], ri[3], muf[D];
+  for (int d = 0; d < D; ++d) muf[d] = (float)c.mu[k][d];
+  if (!std_chol<D>(c.S[k], c.mu[k], c.mean, c.sc, c.meanf, c.scf, Lc, ri)) return false;
   float eA[NM], elc;
-  make_econst<D, double>(Lc, ri, eA, elc);
+  make_econst<D, float>(Lc, ri, eA, elc);
   for (int q = 0; q < NM; ++q) c.eA[k][q] = eA[q];
-  for (int d = 0; d < D; ++d) c.emu[k][d] = (float)c.mu[k][d];
+  for (int d = 0; d < D; ++d) c.emu[k][d] = muf[d];
   c.eb[k] = lg2((float)c.w[k]) + elc;
   return true;
 }
@@ -364,6 +411,8 @@ __global__ void __launch_bounds__(NT, (D == 1 ? 1024 : 512) / NT) std_kernel(Std
           for (int d = 0; d < D; ++d) {
             c.sc[d] = sqrt(cov[tri<D>(d, d)]);
             c.isc[d] = 1.0 / c.sc[d];
+            c.meanf[d] = (float)c.mean[d];
+            c.scf[d] = (float)c.sc[d];
             c.logjac += log(c.sc[d]);
           }
           for (int x = 0; x < D; ++x)
@@ -420,6 +469,7 @@ __global__ void __launch_bounds__(NT, (D == 1 ? 1024 : 512) / NT) std_kernel(Std
       std_bsum<D, NW, 1>(c, sa);
       if (tid == 0) {
         c.sumAH = c.res[0];
+        c.rsumAH = (float)(1.0 / c.res[0]);
         c.c0 = -2.0471975511965976f * D;
       }
     }
@@ -625,29 +675,48 @@ __global__ void __launch_bounds__(NT, (D == 1 ? 1024 : 512) / NT) std_kernel(Std
       __syncthreads();
       // M-step of every component (one lane each), L, convergence, AA start
       if (tid < 32) {
-        double Nk = 0.0;
+        // FP32 (the statistics are FP32 sums; FP64 here would put ~200
+        // serial FP64 instructions on every iteration's critical path): the
+        // shift of the mean is added to the FP64 iterate, so the mean keeps
+        // its full precision
+        float Nk = 0.0f;
         if (lane < K) {
           const int k = lane;
-          double st[NS];
+          float st[NS];
           for (int q = 0; q < NS; ++q) {
-            double s = 0.0;
-            for (int w = 0; w < NW; ++w) s += (double)c.redk[k][w][q];
-            st[q] = s;
+            float sq = 0.0f;
+            for (int w = 0; w < NW; ++w) sq += c.redk[k][w][q];
+            st[q] = sq;
           }
           Nk = st[0];
-          bool ok = Nk > 0.0;
+          bool ok = Nk > 0.0f;
           if (ok) {
-            double dl[D];
+            const float rN = rcp_nr(Nk);
+            float dl[D], muf[D], Sf[NM];
             for (int x = 0; x < D; ++x) {
-              dl[x] = st[1 + x] / Nk;
-              c.gmu[k][x] = (double)c.emu[k][x] + dl[x];
+              dl[x] = st[1 + x] * rN;
+              muf[x] = c.emu[k][x] + dl[x];
+              c.gmu[k][x] = (double)c.emu[k][x] + (double)dl[x];
             }
             int t = 0;
             for (int x = 0; x < D; ++x)
-              for (int yy = x; yy < D; ++yy, ++t) c.gS[k][t] = st[1 + D + t] / Nk - dl[x] * dl[yy];
-            c.gw[k] = Nk / c.sumAH;
-            double Lc[3][3], ri[3];
-            ok = chol_whitened<D, double, double>(c.gS[k], c.gmu[k], c.mean, c.sc, Lc, ri);
+              for (int yy = x; yy < D; ++yy, ++t) {
+                Sf[t] = fmaf(-dl[x], dl[yy], st[1 + D + t] * rN);
+                c.gS[k][t] = (double)Sf[t];
+              }
+            c.gw[k] = (double)(Nk * c.rsumAH);
+            float Lc[3][3], ri[3];
+            ok = chol_whitened<D, float, float>(Sf, muf, c.meanf, c.scf, Lc, ri, 1e-6);
+            if (!ok) {  // near the floor: the covariance and its test in FP64
+              const double rN64 = 1.0 / (double)Nk;
+              double dl64[D], L64[3][3], r64[3];
+              for (int x = 0; x < D; ++x) dl64[x] = (double)st[1 + x] * rN64;
+              int t2 = 0;
+              for (int x = 0; x < D; ++x)
+                for (int yy = x; yy < D; ++yy, ++t2)
+                  c.gS[k][t2] = (double)st[1 + D + t2] * rN64 - dl64[x] * dl64[yy];
+              ok = chol_whitened<D, double, double>(c.gS[k], c.gmu[k], c.mean, c.sc, L64, r64);
+            }
             if (!ok) atomicOr(&c.status, GM_ST_COV_NOT_PD);
           }
           c.gok[k] = ok ? 1 : 0;
@@ -655,19 +724,19 @@ __global__ void __launch_bounds__(NT, (D == 1 ? 1024 : 512) / NT) std_kernel(Std
         __syncwarp();
         if (a.mml) {
           // eq. (omegak) over the survivors; annihilation of N_k - T/2 <= 0
-          const double hT = 0.5 * (double)T;
+          const float hT = 0.5f * (float)T;
           const bool okk = lane < K && c.gok[lane];
-          const bool alive = okk && Nk - hT > 0.0;
-          const double den = warp_sum(alive ? Nk - hT : 0.0);
+          const bool alive = okk && Nk - hT > 0.0f;
+          const float den = warp_sum(alive ? Nk - hT : 0.0f);
           if (__ballot_sync(0xffffffffu, alive) == 0u) {
             // nothing survives: the component with the largest N_k stays
             // (lowest index on ties), with its old parameters if its new
             // covariance failed the floor
-            double bv = lane < K ? Nk : -1.0;
+            float bv = lane < K ? Nk : -1.0f;
             int bi = lane;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-              const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+              const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
               const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
               if (ov > bv || (ov == bv && oi < bi)) {
                 bv = ov;
@@ -686,7 +755,7 @@ __global__ void __launch_bounds__(NT, (D == 1 ? 1024 : 512) / NT) std_kernel(Std
             }
           } else if (lane < K) {
             c.gok[lane] = alive ? 1 : 0;
-            c.gw[lane] = alive ? (Nk - hT) / den : 0.0;
+            c.gw[lane] = alive ? (double)((Nk - hT) / den) : 0.0;
           }
           __syncwarp();
         }
@@ -754,15 +823,19 @@ __global__ void __launch_bounds__(NT, (D == 1 ? 1024 : 512) / NT) std_kernel(Std
           // M2 - mu mu^T passing the floor (whitened and original)
           bool valid = true;
           if (lane < K) {
+            // M2 - mu mu^T formed in FP64; the floor tested in FP32 and,
+            // near it, in FP64 (whitened and original coordinates)
             const double* t = c.aa.tn + lane * P;
-            double mw[D], Sw[NM], Lc[3][3], ri[3];
+            double mw[D], Sw[NM];
+            float Lc[3][3], ri[3];
             const double zero[3] = {0.0, 0.0, 0.0}, one[3] = {1.0, 1.0, 1.0};
+            const float zf[3] = {0.0f, 0.0f, 0.0f}, of[3] = {1.0f, 1.0f, 1.0f};
             for (int d = 0; d < D; ++d) mw[d] = t[1 + d];
             int q = 0;
             for (int x = 0; x < D; ++x)
-              for (int yy = x; yy < D; ++yy, ++q) Sw[q] = t[1 + D + q] - mw[x] * mw[yy];
-            valid = t[0] > 0.0 && chol_whitened<D, double, double>(Sw, mw, zero, one, Lc, ri) &&
-                    chol_whitened<D, double, double>(Sw, mw, c.mean, c.sc, Lc, ri);
+              for (int yy = x; yy < D; ++yy, ++q) Sw[q] = fma(-t[1 + x], t[1 + yy], t[1 + D + q]);
+            valid = t[0] > 0.0 && std_chol<D>(Sw, mw, zero, one, zf, of, Lc, ri) &&
+                    std_chol<D>(Sw, mw, c.mean, c.sc, c.meanf, c.scf, Lc, ri);
           }
           applied = __all_sync(0xffffffffu, valid);
           if (applied) {
