@@ -66,34 +66,54 @@ struct AAState {
   double th[MAXN], tg[MAXN], tn[MAXN], fprev[MAXN], gprev[MAXN];
   double dF[kStdMaxM][MAXN], dG[kStdMaxM][MAXN];
   double gram[kStdMaxM][kStdMaxM], rhs[kStdMaxM], gam[kStdMaxM];
+  double A[kStdMaxM][kStdMaxM + 1], z[kStdMaxM];  // the small system, logical order
   int h, have, head;
 };
 
-// 1/sqrt(t) for t > 0 in FP64: an FP32 estimate (from t's exponent-scaled
-// FP32 value, so that t outside the FP32 range still gets one) refined by
-// two Newton steps y <- y (3 - t y^2) / 2 (each about doubles the correct
-// bits: ~2^-22 -> 2^-44 -> below FP64 rounding)
-__device__ __forceinline__ double rsqrt_nr_seed(double t) {
+// 1/t for t > 0 in FP64: an FP32 estimate of the mantissa's reciprocal
+// (t = m 2^e, so any t gets one) refined by two Newton steps
+// y <- y (2 - t y) (each doubles the correct bits: ~2^-22 -> 2^-44 -> below
+// FP64 rounding)
+__device__ __forceinline__ double rcp_nr_d(double t) {
   int ex;
-  const double m = frexp(t, &ex);  // t = m 2^ex, m in [1/2, 1)
-  const int e2 = ex & ~1;          // even part of the exponent
-  const double y0 = (double)rsqrt_approx((float)ldexp(m, ex - e2));
-  return ldexp(y0, -e2 / 2);
+  const double m = frexp(t, &ex);
+  double y = ldexp((double)rcp_approx((float)m), -ex);
+  y = y * (2.0 - t * y);
+  return y * (2.0 - t * y);
 }
-__device__ __forceinline__ double rsqrt_nr(double y, double t) {
-  y = y * (1.5 - 0.5 * t * y * y);
-  return y * (1.5 - 0.5 * t * y * y);
+
+// warp sums of NP doubles by recursive halving (the FP64 form of warp_rs):
+// lane l ends with the total of value warp_rs_index<NP>(l) in v[0]
+template <int NP>
+__device__ __forceinline__ void warp_rs_d(double (&v)[NP], int lane) {
+  constexpr int LV = NP == 1 ? 0 : (NP == 2 ? 1 : (NP == 4 ? 2 : (NP == 8 ? 3 : (NP == 16 ? 4 : 5))));
+#pragma unroll
+  for (int lv = 0; lv < LV; ++lv) {
+    const int hh = NP >> (lv + 1), b = 16 >> lv;
+    const bool up = (lane & b) != 0;
+#pragma unroll
+    for (int i = 0; i < hh; ++i) {
+      const double send = up ? v[i] : v[i + hh];
+      const double keep = up ? v[i + hh] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, b);
+    }
+  }
+#pragma unroll
+  for (int b = 16 >> LV; b >= 1; b >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], b);
 }
 
 // One Anderson step by a whole warp (FP64): f = G(x) - x; the difference
 // with the previous pair joins the history (the oldest dropped beyond m);
-// gamma from (dF^T dF + 1e-12 max diag I) gamma = dF^T f by Cholesky on
-// lane 0 (columns oldest first); tn = G(x) - dG gamma.  The dot products a
-// step needs (dF^T f, and the new column against every column) are summed
-// per lane in one pass and reduced together.  Returns true if the
-// extrapolation was made (tn valid); false with no history or a pivot that
-// is not positive.  Reads s.th, s.tg (n values); the caller syncs the warp
-// before and after; h = 0 clears the history.
+// gamma from (dF^T dF + 1e-12 max diag I) gamma = dF^T f; tn = G(x) - dG
+// gamma.  The history is a ring of m slots (the oldest at head) whose Gram
+// matrix gains the newest column's row each step; the step's dot products
+// (dF^T f and the new column against every column) are summed per lane in
+// one pass and reduced together; the h x h system is solved by Gaussian
+// elimination without pivoting (it is symmetric positive definite), one
+// row per lane, columns oldest first.  Returns true if the extrapolation
+// was made (tn valid); false with no history or a pivot that is not
+// positive.  Reads s.th, s.tg (n values); the caller syncs the warp before
+// and after; h = 0 clears the history.
 template <int MAXN>
 __device__ bool aa_warp_step(AAState<MAXN>& s, int n, int m) {
   const int lane = threadIdx.x & 31;
@@ -123,12 +143,10 @@ __device__ bool aa_warp_step(AAState<MAXN>& s, int n, int m) {
   }
   __syncwarp();
   if (h == 0) return false;
-  int slot[kStdMaxM];
-#pragma unroll
-  for (int a = 0; a < kStdMaxM; ++a) {
+  auto slot = [&](int a) {
     const int q = head + a;
-    slot[a] = q >= m ? q - m : q;
-  }
+    return q >= m ? q - m : q;
+  };
   double part[2 * kStdMaxM];
 #pragma unroll
   for (int a = 0; a < 2 * kStdMaxM; ++a) part[a] = 0.0;
@@ -137,69 +155,65 @@ __device__ bool aa_warp_step(AAState<MAXN>& s, int n, int m) {
 #pragma unroll
     for (int a = 0; a < kStdMaxM; ++a)
       if (a < h) {
-        const double v = s.dF[slot[a]][i];
+        const double v = s.dF[slot(a)][i];
         part[a] = fma(v, fi, part[a]);
         part[kStdMaxM + a] = fma(v, di, part[kStdMaxM + a]);
       }
   }
-#pragma unroll
-  for (int a = 0; a < 2 * kStdMaxM; ++a)
-    if ((a % kStdMaxM) < h) part[a] = warp_sum(part[a]);
-  if (lane == 0)
-#pragma unroll
-    for (int a = 0; a < kStdMaxM; ++a)
-      if (a < h) {
-        s.rhs[slot[a]] = part[a];
-        s.gram[nw][slot[a]] = part[kStdMaxM + a];
-        s.gram[slot[a]][nw] = part[kStdMaxM + a];
-      }
-  __syncwarp();
-  int solved = 0;
-  if (lane == 0) {
-    // Cholesky in place (lower triangle of Lm), columns oldest first
-    // (the reciprocal of each pivot's square root by two Newton steps from
-    // the FP32 estimate: multiplications instead of FP64 divides)
-    double Lm[kStdMaxM][kStdMaxM], rl[kStdMaxM], z[kStdMaxM], dmax = 0.0;
-    for (int a0 = 0; a0 < h; ++a0) dmax = fmax(dmax, s.gram[slot[a0]][slot[a0]]);
-    if (dmax > 0.0) {
-      solved = 1;
-      for (int a0 = 0; a0 < h && solved; ++a0)
-        for (int c1 = 0; c1 <= a0 && solved; ++c1) {
-          double t = s.gram[slot[a0]][slot[c1]] + (a0 == c1 ? 1e-12 * dmax : 0.0);
-          for (int e = 0; e < c1; ++e) t -= Lm[a0][e] * Lm[c1][e];
-          if (a0 == c1) {
-            if (!(t > 0.0) || !(t < 1e300)) {
-              solved = 0;
-            } else {
-              const double r = rsqrt_nr(rsqrt_nr_seed(t), t);
-              rl[a0] = r;
-              Lm[a0][a0] = t * r;
-            }
-          } else {
-            Lm[a0][c1] = t * rl[c1];
-          }
-        }
-      if (solved) {
-        for (int a0 = 0; a0 < h; ++a0) {
-          double t = s.rhs[slot[a0]];
-          for (int e = 0; e < a0; ++e) t -= Lm[a0][e] * z[e];
-          z[a0] = t * rl[a0];
-        }
-        for (int a0 = h - 1; a0 >= 0; --a0) {
-          double t = z[a0];
-          for (int e = a0 + 1; e < h; ++e) t -= Lm[e][a0] * z[e];
-          z[a0] = t * rl[a0];
-        }
-        for (int a0 = 0; a0 < h; ++a0) s.gam[slot[a0]] = z[a0];
+  warp_rs_d<2 * kStdMaxM>(part, lane);
+  if ((lane & 1) == 0) {
+    const int q = warp_rs_index<2 * kStdMaxM>(lane);
+    const int a = q < kStdMaxM ? q : q - kStdMaxM;
+    if (a < h) {
+      const int sa = slot(a);
+      if (q < kStdMaxM) {
+        s.rhs[sa] = part[0];
+      } else {
+        s.gram[nw][sa] = part[0];
+        s.gram[sa][nw] = part[0];
       }
     }
   }
-  solved = __shfl_sync(0xffffffffu, solved, 0);
   __syncwarp();
-  if (!solved) return false;
+  double dmax = lane < h ? s.gram[slot(lane)][slot(lane)] : 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+  if (!(dmax > 0.0)) return false;
+  if (lane < h) {
+    const int sl = slot(lane);
+    for (int b = 0; b < h; ++b) s.A[lane][b] = s.gram[sl][slot(b)] + (b == lane ? 1e-12 * dmax : 0.0);
+    s.A[lane][kStdMaxM] = s.rhs[sl];
+  }
+  __syncwarp();
+  double myr = 0.0;
+  for (int j = 0; j < h; ++j) {
+    const double d = s.A[j][j];
+    if (!(d > 0.0) || !(d < 1e300)) return false;  // the same on every lane
+    const double rd = rcp_nr_d(d);
+    if (lane == j) myr = rd;
+    if (lane > j && lane < h) {
+      const double f = s.A[lane][j] * rd;
+      for (int b = j + 1; b < h; ++b) s.A[lane][b] = fma(-f, s.A[j][b], s.A[lane][b]);
+      s.A[lane][kStdMaxM] = fma(-f, s.A[j][kStdMaxM], s.A[lane][kStdMaxM]);
+    }
+    __syncwarp();
+  }
+  for (int j = h - 1; j >= 0; --j) {
+    if (lane == j) {
+      double t = s.A[j][kStdMaxM];
+      for (int b = j + 1; b < h; ++b) t = fma(-s.A[j][b], s.z[b], t);
+      s.z[j] = t * myr;
+    }
+    __syncwarp();
+  }
+  if (lane < h) s.gam[slot(lane)] = s.z[lane];
+  __syncwarp();
   for (int i = lane; i < n; i += 32) {
     double t = s.tg[i];
-    for (int a = 0; a < h; ++a) t -= s.dG[slot[a]][i] * s.gam[slot[a]];
+    for (int a = 0; a < h; ++a) {
+      const int sa = slot(a);
+      t = fma(-s.dG[sa][i], s.gam[sa], t);
+    }
     s.tn[i] = t;
   }
   __syncwarp();
