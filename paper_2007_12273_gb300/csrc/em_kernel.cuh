@@ -1100,26 +1100,95 @@ __global__ void __launch_bounds__(NT, (D == 1 ? 1024 : 512) / NT) em_kernel(EmPa
     const int N = (int)(a.cell_off[j + 1] - off);
     double* prm_out = a.params_out + (size_t)j * a.Kmax * P;
 
-    // ---- total weight and weighted mean (FP64) ---------------------------
+    // ---- total weight, mean and covariance (FP64, one pass) ----------------
+    // sums of alpha, alpha d and alpha d d^T with d = v - s, s the cell's
+    // first particle (d is exact in FP64, and s lies within the cell's
+    // spread, so mean = s + sum(alpha d) / W and cov = sum(alpha d d^T) / W
+    // - (mean - s)(mean - s)^T lose no more than a few ulps to cancellation)
     {
-      double acc[1 + D];
+      double sh[D];
 #pragma unroll
-      for (int i = 0; i <= D; ++i) acc[i] = 0.0;
+      for (int d = 0; d < D; ++d) sh[d] = N > 0 ? (double)vin[(int64_t)d * a.n + off] : 0.0;
+      double acc[1 + D + NM];
+#pragma unroll
+      for (int i = 0; i < 1 + D + NM; ++i) acc[i] = 0.0;
       for (int p = tid; p < N; p += NT) {
         const double al = a.alpha[off + p];
-        acc[0] += al;
+        double dv[D];
 #pragma unroll
-        for (int d = 0; d < D; ++d) acc[1 + d] += al * (double)vin[(int64_t)d * a.n + off + p];
+        for (int d = 0; d < D; ++d) dv[d] = (double)vin[(int64_t)d * a.n + off + p] - sh[d];
+        acc[0] += al;
+        int t = 1 + D;
+#pragma unroll
+        for (int x = 0; x < D; ++x) {
+          const double ad = al * dv[x];
+          acc[1 + x] += ad;
+#pragma unroll
+          for (int y = x; y < D; ++y, ++t) acc[t] = fma(ad, dv[y], acc[t]);
+        }
       }
-      block_sum_d<D, NT, 1 + D, R>(c, acc);
+      block_sum_d<D, NT, 1 + D + NM, R>(c, acc);
       if (tid == 0) {
         c.W = c.res[0];
         c.Nd = (double)N;
-        for (int d = 0; d < D; ++d) c.mean[d] = c.res[1 + d] / c.res[0];
+        c.status = (N <= 10) ? GM_ST_TOO_FEW : 0u;
+        const double rW = 1.0 / c.res[0];
+        double dm[D];
+        for (int d = 0; d < D; ++d) {
+          dm[d] = c.res[1 + d] * rW;
+          c.mean[d] = sh[d] + dm[d];
+        }
+        double cov[NM];
+        int t = 0;
+        for (int x = 0; x < D; ++x)
+          for (int y = x; y < D; ++y, ++t) cov[t] = fma(-dm[x], dm[y], c.res[1 + D + t] * rW);
+        c.degenerate = 0;
+        if (N == 0 || !(c.W > 0.0)) {
+          c.degenerate = 2;  // empty: handled below
+        } else {
+          // degenerate cell: the total covariance fails the Cholesky floor
+          // 1e-13 * sum_d (cov_dd + mean_d^2)
+          double scale2 = 0.0;
+          for (int d = 0; d < D; ++d) scale2 += cov[tri<D>(d, d)] + c.mean[d] * c.mean[d];
+          const double fl = 1e-13 * scale2;
+          bool ok = true;
+          double L2[3][3] = {{0}};
+          for (int x = 0; x < D && ok; ++x)
+            for (int y = 0; y <= x && ok; ++y) {
+              double sv = cov[tri<D>(y, x)];
+              for (int m = 0; m < y; ++m) sv -= L2[x][m] * L2[y][m];
+              if (x == y) {
+                if (!(sv > fl) || !(sv < 1e300)) ok = false;
+                else L2[x][x] = sqrt(sv);
+              } else {
+                L2[x][y] = sv / L2[y][y];
+              }
+            }
+          c.degenerate = ok ? 0 : 1;
+          if (c.degenerate) {
+            for (int i = 0; i < NM; ++i) c.fS[0][i] = cov[i];
+          } else {
+            for (int i = 0; i < NM; ++i) c.cov0[i] = cov[i];
+            c.logN = log(c.Nd);
+            double prod = 1.0;
+            for (int d = 0; d < D; ++d) {
+              c.sc[d] = sqrt(cov[tri<D>(d, d)]);
+              c.isc[d] = 1.0 / c.sc[d];
+              prod *= c.sc[d];
+              c.meanf[d] = (float)c.mean[d];
+              c.scf[d] = (float)c.sc[d];
+            }
+            c.logjac = log(prod);
+            // whitened total covariance (correlation matrix) for the init
+            for (int x = 0; x < D; ++x)
+              for (int y = x; y < D; ++y)
+                c.S0[tri<D>(x, y)] = (x == y) ? 1.0 : cov[tri<D>(x, y)] * c.isc[x] * c.isc[y];
+          }
+        }
       }
       __syncthreads();
     }
-    if (N == 0 || !(c.W > 0.0)) {
+    if (c.degenerate == 2) {
       for (int i = tid; i < a.Kmax * P; i += NT) prm_out[i] = 0.0;
       if (tid == 0) {
         a.K_out[j] = 0;
@@ -1131,69 +1200,6 @@ __global__ void __launch_bounds__(NT, (D == 1 ? 1024 : 512) / NT) em_kernel(EmPa
       }
       __syncthreads();
       continue;
-    }
-    // ---- total covariance (two-pass, FP64) --------------------------------
-    {
-      double acc[NM];
-#pragma unroll
-      for (int i = 0; i < NM; ++i) acc[i] = 0.0;
-      for (int p = tid; p < N; p += NT) {
-        const double al = a.alpha[off + p];
-        double dv[D];
-#pragma unroll
-        for (int d = 0; d < D; ++d) dv[d] = (double)vin[(int64_t)d * a.n + off + p] - c.mean[d];
-        int t = 0;
-#pragma unroll
-        for (int x = 0; x < D; ++x)
-#pragma unroll
-          for (int y = x; y < D; ++y, ++t) acc[t] += al * dv[x] * dv[y];
-      }
-      block_sum_d<D, NT, NM, R>(c, acc);
-      if (tid == 0) {
-        double cov[NM];
-        for (int i = 0; i < NM; ++i) cov[i] = c.res[i] / c.W;
-        c.status = (N <= 10) ? GM_ST_TOO_FEW : 0u;
-        // degenerate cell: the total covariance fails the Cholesky floor
-        // 1e-13 * sum_d (cov_dd + mean_d^2)
-        {
-          double scale2 = 0.0;
-          for (int d = 0; d < D; ++d) scale2 += cov[tri<D>(d, d)] + c.mean[d] * c.mean[d];
-          const double fl = 1e-13 * scale2;
-          bool ok = true;
-          double L2[3][3] = {{0}};
-          for (int x = 0; x < D && ok; ++x)
-            for (int y = 0; y <= x && ok; ++y) {
-              double s = cov[tri<D>(y, x)];
-              for (int m = 0; m < y; ++m) s -= L2[x][m] * L2[y][m];
-              if (x == y) {
-                if (!(s > fl) || !(s < 1e300)) ok = false;
-                else L2[x][x] = sqrt(s);
-              } else {
-                L2[x][y] = s / L2[y][y];
-              }
-            }
-          c.degenerate = ok ? 0 : 1;
-        }
-        if (c.degenerate) {
-          for (int i = 0; i < NM; ++i) c.fS[0][i] = cov[i];
-        } else {
-          for (int i = 0; i < NM; ++i) c.cov0[i] = cov[i];
-          c.logjac = 0.0;
-          c.logN = log(c.Nd);
-          for (int d = 0; d < D; ++d) {
-            c.sc[d] = sqrt(cov[tri<D>(d, d)]);
-            c.isc[d] = 1.0 / c.sc[d];
-            c.logjac += log(c.sc[d]);
-            c.meanf[d] = (float)c.mean[d];
-            c.scf[d] = (float)c.sc[d];
-          }
-          // whitened total covariance (correlation matrix) for the init
-          for (int x = 0; x < D; ++x)
-            for (int y = x; y < D; ++y)
-              c.S0[tri<D>(x, y)] = (x == y) ? 1.0 : cov[tri<D>(x, y)] * c.isc[x] * c.isc[y];
-        }
-      }
-      __syncthreads();
     }
     if (c.degenerate) {
       for (int i = tid; i < a.Kmax * P; i += NT) prm_out[i] = 0.0;
