@@ -348,12 +348,25 @@ def run_gmcr(args):
         o_ = net.forward(f_, stream=stream)
         return gm.gm_mlp_decode(cfg, o_, w_, cell_off, stream=stream, presence_logit=args.presence_logit)
 
+    # the learned path's EM launch shape, tuned from the learned start
+    # (untimed): most of its cells start with one component, a cost balance
+    # unlike the random start's
+    cfg_l, tune_l = cfg, None
+    if use_learned and tune is not None:
+        cfg_l = gm.config(wl.params, **over)
+        K0_, prm0_ = init_learned(None)
+        trial_l = gm.gm_autotune(cfg_l, cell_off, x, v, alpha, stream=stream, init_K=K0_, init_params=prm0_)
+        tune_l = {"threads_per_cell": cfg_l.threads_per_cell, "smem_particles": cfg_l.smem_particles,
+                  "trial_ms": [round(z, 4) for z in trial_l]}
+        del K0_, prm0_
+
     def timed(path: str, steps: int, warmup: int):
         """per-step CUDA events (init, compress, reconstruct), L2 flushed
         between steps; the phases are replayed from CUDA graphs captured
         after the warm-up (unless --no-graph); returns per-phase mean ms and
         the compress outputs"""
         cout = comp_out()
+        ecfg = cfg_l if path == "learned" else cfg
 
         def one(ev=None):
             if ev:
@@ -364,7 +377,7 @@ def run_gmcr(args):
                 kw = dict(init_K=K0, init_params=prm)
             if ev:
                 ev[1].record(stream)
-            gm.gm_compress(cfg, cell_off, x, v, alpha, stream=stream, out=cout, **kw)
+            gm.gm_compress(ecfg, cell_off, x, v, alpha, stream=stream, out=cout, **kw)
             if ev:
                 ev[2].record(stream)
             gm.gm_reconstruct(rcfg, cout["K"], cout["params"], cout["W"], cout["rho_target"],
@@ -396,7 +409,7 @@ def run_gmcr(args):
                 kw = {}
             gc = gm.Graph(stream)
             with gc:
-                gm.gm_compress(cfg, cell_off, x, v, alpha, stream=stream, out=cout, **kw)
+                gm.gm_compress(ecfg, cell_off, x, v, alpha, stream=stream, out=cout, **kw)
             graphs.append(gc)
             gr = gm.Graph(stream)
             with gr:
@@ -471,7 +484,8 @@ def run_gmcr(args):
             K0, prm = gm.gm_mlp_decode(cfg, o_, w_, d_in[0], stream=stream,
                                          presence_logit=args.presence_logit)
             kw = dict(init_K=K0, init_params=prm)
-        gm.gm_compress(cfg, d_in[0], d_in[1], d_in[2], d_in[3], stream=stream, out=cout_e, **kw)
+        gm.gm_compress(cfg_l if head == "learned" else cfg, d_in[0], d_in[1], d_in[2], d_in[3],
+                       stream=stream, out=cout_e, **kw)
         gm.gm_reconstruct(rcfg, cout_e["K"], cout_e["params"], cout_e["W"], cout_e["rho_target"],
                           d_in[0], n_out=n, stream=stream, out=rout)
         for k, h in h_out.items():
@@ -541,6 +555,9 @@ def run_gmcr(args):
                               else "direct calls"),
                    "em_shape": ({"threads_per_cell": cfg.threads_per_cell,
                                  "smem_particles": cfg.smem_particles, "autotune": tune}),
+                   "em_shape_learned": ({"threads_per_cell": cfg_l.threads_per_cell,
+                                         "smem_particles": cfg_l.smem_particles,
+                                         "autotune_from_learned_start": tune_l}),
                    "parallelism": f"replicas x{world} (independent batches)"},
         "ms_init": hs["ms_init"], "ms_compress": hs["ms_compress"],
         "ms_reconstruct": hs["ms_reconstruct"],

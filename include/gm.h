@@ -453,8 +453,8 @@ int gm_graph_destroy(gm_graph* g);
  * gm_autotune -- picks the EM launch shape for a batch of cells.  The paper
  * has no counterpart (it runs one cell per process on CPUs).
  *
- * Times gm_compress on a sample of the batch (the first cells, about two
- * waves of CTAs) for every candidate shape: threads_per_cell in
+ * Times gm_compress on a sample of the batch (the first 128 x #SM cells,
+ * many per CTA) for every candidate shape: threads_per_cell in
  * {64, 128, 256} and shared-tile capacities smem_particles covering the
  * library default and the 90th, 99th, 100th and 50th percentiles of the
  * cell sizes (only those that fit in shared memory; larger cells use the
@@ -477,6 +477,20 @@ int gm_graph_destroy(gm_graph* g);
 int gm_autotune(gm_config* cfg, int64_t C, int64_t n_particles, const int64_t* cell_off,
                 const double* x, const void* v, int32_t v_is_f64, const double* alpha,
                 int32_t sweeps_per_trial, float* timings_ms, void* stream);
+
+/*
+ * gm_autotune_from -- gm_autotune for fits that start from supplied
+ * mixtures (gm_compress_from): the trials run gm_compress_from with the
+ * first cells' init_K / init_params (same layout as gm_compress_from, for
+ * the whole batch) and with cfg->tol (capped at sweeps_per_trial sweeps).  A learned start leaves many cells with one component,
+ * whose fit is the prologue's closed form, so the cost balance (and the
+ * best launch shape) differs from that of the paper's random start.  Both
+ * init pointers are required (GM_ERR_ARG otherwise).
+ */
+int gm_autotune_from(gm_config* cfg, int64_t C, int64_t n_particles, const int64_t* cell_off,
+                     const double* x, const void* v, int32_t v_is_f64, const double* alpha,
+                     const int32_t* init_K, const double* init_params, int32_t sweeps_per_trial,
+                     float* timings_ms, void* stream);
 
 /* Description of the last error on this host thread ("" if none). */
 const char* gm_last_error(void);

@@ -36,11 +36,10 @@ constexpr int kTuneCaps = 5;
 constexpr int kTuneCands = kTuneThreads * kTuneCaps;
 static_assert(kTuneCands == GM_TUNE_CANDIDATES, "gm.h states the number of candidates");
 
-}  // namespace
-
-extern "C" int gm_autotune(gm_config* cfg, int64_t C, int64_t n_particles, const int64_t* cell_off,
-                           const double* x, const void* v, int32_t v_is_f64, const double* alpha,
-                           int32_t sweeps_per_trial, float* timings_ms, void* stream) {
+int tune_impl(gm_config* cfg, int64_t C, int64_t n_particles, const int64_t* cell_off,
+              const double* x, const void* v, int32_t v_is_f64, const double* alpha,
+              const int32_t* init_K, const double* init_params, int32_t sweeps_per_trial,
+              float* timings_ms, void* stream) {
   if (!cfg || !cell_off || !x || !v || !alpha) return tune_fail(GM_ERR_ARG, "a required pointer is NULL");
   if (C < 1) return tune_fail(GM_ERR_ARG, "C must be >= 1");
   if (cfg->D != 1 && cfg->D != 3) return tune_fail(GM_ERR_ARG, "D must be 1 or 3");
@@ -57,8 +56,10 @@ extern "C" int gm_autotune(gm_config* cfg, int64_t C, int64_t n_particles, const
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (sms < 1) sms = 1;
 
-  // cell sizes of the sample: the first cells, about two waves of CTAs
-  const int64_t S = std::min<int64_t>(C, (int64_t)8 * sms);
+  // cell sizes of the sample: the first 128 cells per SM (many cells per
+  // CTA even for the smallest CTAs, so that a trial measures throughput,
+  // not one wave)
+  const int64_t S = std::min<int64_t>(C, (int64_t)128 * sms);
   std::vector<int64_t> off((size_t)S + 1);
   e = cudaMemcpyAsync(off.data(), cell_off, sizeof(int64_t) * (size_t)(S + 1), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -113,7 +114,10 @@ extern "C" int gm_autotune(gm_config* cfg, int64_t C, int64_t n_particles, const
   for (size_t ci = 0; ci < caps.size() && rc == GM_OK; ++ci) {
     for (int ti = 0; ti < kTuneThreads; ++ti) {
       gm_config tr = *cfg;
-      tr.tol = 0.0;
+      // the paper's start: tol = 0, every candidate does the same sweeps; a
+      // supplied start: the caller's tol (capped at the same sweeps), so
+      // that its cells stop about where they will in the fit
+      tr.tol = init_K ? cfg->tol : 0.0;
       tr.max_sweeps = spt;
       tr.threads_per_cell = kTuneNT[ti];
       tr.smem_particles = caps[ci];
@@ -121,8 +125,12 @@ extern "C" int gm_autotune(gm_config* cfg, int64_t C, int64_t n_particles, const
       float tmin = -1.0f;
       for (int rep = 0; rep < 3; ++rep) {  // one warm-up, two timed
         cudaEventRecord(t0, s);
-        const int r = gm_compress(&tr, S, n_particles, cell_off, x, v, v_is_f64, alpha, o.K, o.params,
-                                  o.W, o.rho, o.lnL, o.sweeps, o.kwork, o.status, stream);
+        const int r =
+            init_K ? gm_compress_from(&tr, S, n_particles, cell_off, x, v, v_is_f64, alpha, init_K,
+                                      init_params, o.K, o.params, o.W, o.rho, o.lnL, o.sweeps,
+                                      o.kwork, o.status, stream)
+                   : gm_compress(&tr, S, n_particles, cell_off, x, v, v_is_f64, alpha, o.K, o.params,
+                                 o.W, o.rho, o.lnL, o.sweeps, o.kwork, o.status, stream);
         if (r != GM_OK) {
           tmin = -1.0f;
           break;
@@ -158,4 +166,23 @@ extern "C" int gm_autotune(gm_config* cfg, int64_t C, int64_t n_particles, const
   cfg->smem_particles = caps[(size_t)(best / kTuneThreads)];
   gmcr::record_error(GM_OK, "");
   return GM_OK;
+}
+
+}  // namespace
+
+extern "C" int gm_autotune(gm_config* cfg, int64_t C, int64_t n_particles, const int64_t* cell_off,
+                           const double* x, const void* v, int32_t v_is_f64, const double* alpha,
+                           int32_t sweeps_per_trial, float* timings_ms, void* stream) {
+  return tune_impl(cfg, C, n_particles, cell_off, x, v, v_is_f64, alpha, nullptr, nullptr,
+                   sweeps_per_trial, timings_ms, stream);
+}
+
+extern "C" int gm_autotune_from(gm_config* cfg, int64_t C, int64_t n_particles,
+                                const int64_t* cell_off, const double* x, const void* v,
+                                int32_t v_is_f64, const double* alpha, const int32_t* init_K,
+                                const double* init_params, int32_t sweeps_per_trial,
+                                float* timings_ms, void* stream) {
+  if (!init_K || !init_params) return tune_fail(GM_ERR_ARG, "init_K and init_params are required");
+  return tune_impl(cfg, C, n_particles, cell_off, x, v, v_is_f64, alpha, init_K, init_params,
+                   sweeps_per_trial, timings_ms, stream);
 }

@@ -37,7 +37,8 @@ EXPORTED = ("gm_compress", "gm_reconstruct", "gm_moments", "gm_mixture_moments",
             "gm_compress_from", "gm_features", "gm_mlp_targets", "gm_mlp_sync",
             "gm_mlp_scratch_bytes", "gm_mlp_forward", "gm_mlp_train_step", "gm_mlp_decode",
             "gm_graph_begin", "gm_graph_end", "gm_graph_launch", "gm_graph_destroy", "gm_autotune",
-            "gm_compress_standard", "gm_anderson_affine", "gm_deposit_2d", "gm_reconstruct_2d")
+            "gm_compress_standard", "gm_anderson_affine", "gm_deposit_2d", "gm_reconstruct_2d",
+            "gm_autotune_from")
 
 
 class GMMlp(ct.Structure):
@@ -114,6 +115,7 @@ def load(build_if_missing: bool = False):
         lib.gm_graph_launch.argtypes = [P, P]
         lib.gm_graph_destroy.argtypes = [P]
         lib.gm_autotune.argtypes = [P, I64, I64, P, P, P, I32, P, I32, ct.POINTER(ct.c_float), P]
+        lib.gm_autotune_from.argtypes = [P, I64, I64, P, P, P, I32, P, P, P, I32, ct.POINTER(ct.c_float), P]
         lib.gm_compress_standard.argtypes = [P, P, I64, I64, P, P, P, I32, P] + [P] * 10 + [P]
         lib.gm_anderson_affine.argtypes = [I32, P, P, P, I32, I32, P, P, P]
         lib.gm_deposit_2d.argtypes = [P] * 8
@@ -123,7 +125,7 @@ def load(build_if_missing: bool = False):
                   "gm_mlp_targets", "gm_mlp_sync", "gm_mlp_forward", "gm_mlp_train_step",
                   "gm_mlp_decode", "gm_graph_begin", "gm_graph_end", "gm_graph_launch",
                   "gm_graph_destroy", "gm_autotune", "gm_compress_standard", "gm_anderson_affine",
-                  "gm_deposit_2d", "gm_reconstruct_2d"):
+                  "gm_deposit_2d", "gm_reconstruct_2d", "gm_autotune_from"):
             getattr(lib, f).restype = ct.c_int
         lib.gm_last_error.restype = ct.c_char_p
         _lib = lib
@@ -483,7 +485,8 @@ class Net:
         return loss
 
 
-def gm_autotune(cfg: GMConfig, cell_off, x, v, alpha, sweeps_per_trial: int = 0, stream=None):
+def gm_autotune(cfg: GMConfig, cell_off, x, v, alpha, sweeps_per_trial: int = 0, stream=None,
+                init_K=None, init_params=None):
     """Times the EM launch shapes on a sample of the batch and writes the
     fastest into ``cfg`` (threads_per_cell, smem_particles).  Returns the
     trial times in ms (TUNE_CANDIDATES entries, -1 = not run; candidate i
@@ -492,10 +495,18 @@ def gm_autotune(cfg: GMConfig, cell_off, x, v, alpha, sweeps_per_trial: int = 0,
     C = cell_off.shape[0] - 1
     n = x.shape[0]
     t = (ct.c_float * TUNE_CANDIDATES)()
-    rc = lib.gm_autotune(ct.byref(cfg), C, n, _ptr(cell_off), _ptr(x), _ptr(v),
-                         1 if v.dtype == torch.float64 else 0, _ptr(alpha), int(sweeps_per_trial), t,
-                         _stream_ptr(stream))
-    _rc(lib, rc, "gm_autotune")
+    vf = 1 if v.dtype == torch.float64 else 0
+    if init_K is None:
+        rc = lib.gm_autotune(ct.byref(cfg), C, n, _ptr(cell_off), _ptr(x), _ptr(v), vf, _ptr(alpha),
+                             int(sweeps_per_trial), t, _stream_ptr(stream))
+        _rc(lib, rc, "gm_autotune")
+    else:  # trials from the supplied initial mixtures (gm_autotune_from)
+        _check(init_K, torch.int32, "init_K")
+        _check(init_params, torch.float64, "init_params")
+        rc = lib.gm_autotune_from(ct.byref(cfg), C, n, _ptr(cell_off), _ptr(x), _ptr(v), vf,
+                                  _ptr(alpha), _ptr(init_K), _ptr(init_params), int(sweeps_per_trial),
+                                  t, _stream_ptr(stream))
+        _rc(lib, rc, "gm_autotune_from")
     return list(t)
 
 

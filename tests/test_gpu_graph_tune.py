@@ -184,3 +184,33 @@ def test_small_ctas_fit_like_the_oracle(gm, nt, cap):
         print(f"nt {nt} cap {cap} D {wl.D}: natural {agree.mean():.3f}, equal sweeps {eq.mean():.3f}")
         assert eq.mean() >= 0.95 and agree.mean() >= 0.5
         np.testing.assert_allclose(g["W"], ref["W"], rtol=1e-13)
+
+
+def test_autotune_from_a_supplied_start(gm):
+    """gm_autotune_from: trials from supplied initial mixtures (the oracle's
+    fits of the cells, one component in half of them) pick a valid shape,
+    and the fit from the same start with that shape equals the fit with the
+    same CTA size and the default tile bit for bit."""
+    import ctypes as ct
+    wl = workloads.with_weights(workloads.bimaxwellian_1d3v(C=320, ppc=600, seed=38))
+    off, x, v, a = inputs(wl)
+    ref = oracle.compress(wl.params, wl.cell_off, wl.x, wl.v, wl.alpha, nthreads=8)
+    K0 = ref["K"].copy()
+    K0[::2] = 1
+    prm = ref["params"].copy()
+    prm[::2, 0, 0] = 1.0
+    K0t, prmt = dev(K0.astype(np.int32)), dev(prm)
+    cfg = gm.config(wl.params)
+    t = gm.gm_autotune(cfg, off, x, v, a, sweeps_per_trial=8, init_K=K0t, init_params=prmt)
+    assert cfg.threads_per_cell in (64, 128, 256)
+    assert cfg.smem_particles > 0 and cfg.smem_particles % 4 == 0
+    assert len([z for z in t if z > 0]) >= 2
+    out = gm.gm_compress(cfg, off, x, v, a, init_K=K0t, init_params=prmt)
+    cfg2 = gm.config(wl.params, threads_per_cell=cfg.threads_per_cell)
+    out2 = gm.gm_compress(cfg2, off, x, v, a, init_K=K0t, init_params=prmt)
+    torch.cuda.synchronize()
+    same(out, out2)
+    lib = gm.load()
+    buf = (ct.c_float * gm.TUNE_CANDIDATES)()
+    assert lib.gm_autotune_from(ct.byref(cfg), wl.C, wl.ntot, gm._ptr(off), gm._ptr(x), gm._ptr(v), 0,
+                                gm._ptr(a), None, None, 0, buf, None) == gm.GM_ERR_ARG
