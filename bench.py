@@ -358,6 +358,21 @@ def run_gmcr(args):
         trial_l = gm.gm_autotune(cfg_l, cell_off, x, v, alpha, stream=stream, init_K=K0_, init_params=prm0_)
         tune_l = {"threads_per_cell": cfg_l.threads_per_cell, "smem_particles": cfg_l.smem_particles,
                   "trial_ms": [round(z, 4) for z in trial_l]}
+        # the tuners time samples; where they disagree, one fit of the whole
+        # batch from the learned start per shape decides (untimed)
+        if (cfg_l.threads_per_cell, cfg_l.smem_particles) != (cfg.threads_per_cell, cfg.smem_particles):
+            fit_ms = {}
+            for name, cf in (("plain-tuned", cfg), ("learned-tuned", cfg_l)):
+                gm.gm_compress(cf, cell_off, x, v, alpha, stream=stream, init_K=K0_, init_params=prm0_)
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                gm.gm_compress(cf, cell_off, x, v, alpha, stream=stream, init_K=K0_, init_params=prm0_)
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                fit_ms[name] = ev0.elapsed_time(ev1)
+            tune_l["whole_batch_fit_ms"] = {k: round(z, 3) for k, z in fit_ms.items()}
+            if fit_ms["plain-tuned"] < fit_ms["learned-tuned"]:
+                cfg_l = cfg
         del K0_, prm0_
 
     def timed(path: str, steps: int, warmup: int):

@@ -482,7 +482,8 @@ int gm_autotune(gm_config* cfg, int64_t C, int64_t n_particles, const int64_t* c
  * gm_autotune_from -- gm_autotune for fits that start from supplied
  * mixtures (gm_compress_from): the trials run gm_compress_from with the
  * first cells' init_K / init_params (same layout as gm_compress_from, for
- * the whole batch) and with cfg->tol (capped at sweeps_per_trial sweeps).  A learned start leaves many cells with one component,
+ * the whole batch), each trial the fit on the sample with cfg->tol,
+ * capped at sweeps_per_trial sweeps (0 = 64).  A learned start leaves many cells with one component,
  * whose fit is the prologue's closed form, so the cost balance (and the
  * best launch shape) differs from that of the paper's random start.  Both
  * init pointers are required (GM_ERR_ARG otherwise).

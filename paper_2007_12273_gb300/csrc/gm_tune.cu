@@ -115,10 +115,13 @@ int tune_impl(gm_config* cfg, int64_t C, int64_t n_particles, const int64_t* cel
     for (int ti = 0; ti < kTuneThreads; ++ti) {
       gm_config tr = *cfg;
       // the paper's start: tol = 0, every candidate does the same sweeps; a
-      // supplied start: the caller's tol (capped at the same sweeps), so
-      // that its cells stop about where they will in the fit
+      // supplied start: the caller's tol, capped at sweeps_per_trial (0 =
+      // 64): a start that leaves most cells converged in a few sweeps and
+      // one that needs hundreds weigh per-cell and per-sweep costs very
+      // differently, while without a cap the sample's few slowest cells
+      // decide the trial (in a whole batch they are hidden among the rest)
       tr.tol = init_K ? cfg->tol : 0.0;
-      tr.max_sweeps = spt;
+      tr.max_sweeps = init_K ? (sweeps_per_trial > 0 ? sweeps_per_trial : 64) : spt;
       tr.threads_per_cell = kTuneNT[ti];
       tr.smem_particles = caps[ci];
       tr.L = cfg->L * (double)S / (double)C;  // the sample keeps the cell width
