@@ -13,7 +13,10 @@
 //   * Standard EM iteration: an exact pass gives each particle's normaliser
 //     and the log-likelihood L(theta_i); one pass per component gives its
 //     E-step statistics (no barrier between components); the M-step of all
-//     components runs on one lane each (FP64 masters, eq. omegak-mle).
+//     components runs on one lane each (eq. omegak-mle), in FP32 with the
+//     mean's shift added to the FP64 iterate and the covariance floor
+//     retested in FP64 near the floor: FP64 on warp 0 between barriers
+//     stalls the CTA (GB300's FP64 pipe is narrow and shared by the SM).
 //   * Anderson acceleration (FP64, warp 0) on theta = (omega_k, mu_k,
 //     M2_k = Sigma_k + mu_k mu_k^T) in the cell's whitened coordinates,
 //     started once the relative change of L is at most 1e-4, reset when an
