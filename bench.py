@@ -140,7 +140,7 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# algorithmic work of the EM kernel ("Roofline")
+# algorithmic work of the EM kernel
 # ---------------------------------------------------------------------------
 FLOPS_PER_PK = {1: 30, 3: 90}  # FP32 flops per particle per component step
 
@@ -158,6 +158,46 @@ def em_flops(counts: np.ndarray, kwork: np.ndarray, D: int) -> float:
 
 def fp32_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
     return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# Second rooflines of the EM kernel: the special-function unit and the FP64
+# pipe.  MUFU work per particle and component step: two base-2 exponentials
+# (the replaced term of the previous component and the density of the
+# current one) and one reciprocal (gamma = alpha G / s); per particle and
+# sweep one base-2 logarithm (eq. lnL-GM).  Its peak: 16 results per SM per
+# clock (the documented throughput of exp2 / log2 / reciprocal on compute
+# capability 10.x) x 152 SMs x the clock.  FP64 work per particle: the
+# prologue's moments, 2 (1 + D + D(D+1)/2) flops, and per component of the
+# final step the FP64 responsibility (3), the centred velocity (2 D) and its
+# statistics (1 + 2 D + D(D+1)); its peak is GB300's nominal FP64 rate.
+MUFU_PER_PK = 3
+MUFU_PER_PSWEEP = 1
+MUFU_PER_SM_CLK = 16
+FP64_PEAK_TFLOPS = 1.25
+
+
+def fp64_flops_per_particle(D: int, K: np.ndarray) -> np.ndarray:
+    NM = D * (D + 1) // 2
+    return 2 * (1 + D + NM) + K.astype(np.float64) * (3 + 2 * D + 1 + 2 * D + 2 * NM)
+
+
+def em_secondary_rooflines(counts: np.ndarray, K: np.ndarray, kwork: np.ndarray,
+                           sweeps: np.ndarray, D: int, seconds: float, sm_mhz: float,
+                           sms: int = 152) -> list:
+    n = counts.astype(np.float64)
+    mufu = float(np.sum(n * (MUFU_PER_PK * kwork.astype(np.float64) +
+                             MUFU_PER_PSWEEP * sweeps.astype(np.float64))))
+    mufu_rate = mufu / seconds / 1e12
+    mufu_peak = sms * MUFU_PER_SM_CLK * sm_mhz * 1e6 / 1e12
+    f64 = float(np.sum(n * fp64_flops_per_particle(D, K)))
+    f64_rate = f64 / seconds / 1e12
+    return [{"unit": "MUFU Top/s", "achieved": mufu_rate, "peak": mufu_peak,
+             "frac": mufu_rate / mufu_peak,
+             "note": f"sum_j N_j ({MUFU_PER_PK} kwork_j + {MUFU_PER_PSWEEP} sweeps_j); peak = "
+                     f"{sms} SMs x {MUFU_PER_SM_CLK} / clock x {sm_mhz:.0f} MHz"},
+            {"unit": "FP64 TFLOP/s", "achieved": f64_rate, "peak": FP64_PEAK_TFLOPS,
+             "frac": f64_rate / FP64_PEAK_TFLOPS,
+             "note": "prologue moments + final FP64 step per particle; peak = nominal GB300 FP64"}]
 
 
 def measured_peaks() -> dict:
@@ -188,6 +228,25 @@ def oracle_step(wl, nthreads: int) -> float:
     return time.perf_counter() - t0
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the ISA)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
 def cpu_baseline(wl, budget_s: float = 15.0) -> dict:
     import oracle
     oracle.build()
@@ -201,9 +260,15 @@ def cpu_baseline(wl, budget_s: float = 15.0) -> dict:
         ncells = min(wl.C, ncells * scale)
         sw = sub_workload(wl, ncells)
         t = oracle_step(sw, cores)
+    # one thread on the first cells
+    s1 = sub_workload(wl, 4)
+    t1 = oracle_step(s1, 1)
     return {"value": sw.ntot / t, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"first {sw.C} cells ({sw.ntot} particles) of the workload, "
-                      f"compress+reconstruct, OpenMP over cells, {t:.1f} s"}
+                      f"compress+reconstruct, OpenMP over cells, {t:.1f} s",
+            "cpu_model": cpu_model(),
+            "single_thread": {"value": s1.ntot / t1, "unit": UNIT, "cores": 1,
+                              "sample": f"first {s1.C} cells ({s1.ntot} particles), {t1:.1f} s"}}
 
 
 # ---------------------------------------------------------------------------
@@ -231,7 +296,8 @@ def run_reference(args):
             "config": {"workload": WORKLOAD_DESC if args.workload == "mixture_1d1v" else args.workload,
                        "sample_cells": sw.C, "sample_particles": sw.ntot},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"first {sw.C} cells ({sw.ntot} particles) per step"},
+                             "sample": f"first {sw.C} cells ({sw.ntot} particles) per step",
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -538,7 +604,9 @@ def run_gmcr(args):
                 "maxsweeps_frac": float(np.mean((o["status"] & 1) != 0)),
                 "compression_ratio": float(counts.sum() * numbers_per_particle /
                                            max(1.0, float(np.sum(o["K"])) * P)),
-                "em_tflops": achieved, "em_frac_fp32_peak": achieved / peak}
+                "em_tflops": achieved, "em_frac_fp32_peak": achieved / peak,
+                "em_secondary": em_secondary_rooflines(counts, o["K"], o["kwork"], o["sweeps"], D,
+                                                       res[path]["ms_compress"] * 1e-3, sm_mhz)}
 
     paths = {p_: summary(p_) for p_ in res}
     if "plain" in outs and "learned" in outs:
@@ -586,7 +654,8 @@ def run_gmcr(args):
                      "traffic": (EM_DRAM_BYTES_PER_PARTICLE * n
                                  if D == 1 and wl.v.dtype == np.float32 else None),
                      "note": f"FP32 flops = sum_j N_j * kwork_j * {FLOPS_PER_PK[D]}; peak = 152 SMs "
-                             f"x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (unit counts and max clock)"},
+                             f"x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (unit counts and max clock)",
+                     "secondary": hs["em_secondary"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": (13 if head == "learned" else 7) * args.steps,
@@ -918,7 +987,9 @@ def run_mesh2d(args):
         "roofline": {"kernel": "em_kernel (gm_compress)", "bound": "alu", "achieved": em_tf,
                      "peak": peak, "unit": "TFLOP/s", "frac": em_tf / peak, "traffic": None,
                      "note": f"FP32 flops = sum_j N_j * kwork_j * {FLOPS_PER_PK[D]}; peak = 152 SMs "
-                             f"x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"},
+                             f"x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz",
+                     "secondary": em_secondary_rooflines(counts, K, kwork, sweeps, D, ms[0] * 1e-3,
+                                                         sm_mhz)},
         "e2e": {"value": n / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         # em_kernel; 2 deposit kernels; reconstruct: stats, factors, assemble,

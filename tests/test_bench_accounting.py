@@ -1,0 +1,40 @@
+"""The roofline accounting of bench.py on hand-counted cases (CPU): FP32
+flops, the special-function (MUFU) operations and the FP64 flops of the EM
+kernel, from per-cell particle counts, component steps (kwork), sweeps and
+final component counts."""
+import numpy as np
+import pytest
+
+import bench
+
+
+def test_fp32_flops_and_peak():
+    counts = np.array([10, 20])
+    kwork = np.array([4, 9])
+    assert bench.em_flops(counts, kwork, 1) == (10 * 4 + 20 * 9) * 30
+    assert bench.em_flops(counts, kwork, 3) == (10 * 4 + 20 * 9) * 90
+    # 152 SMs x 128 lanes x 2 flops x 2 GHz
+    assert bench.fp32_peak_tflops(2000.0) == pytest.approx(77.824)
+
+
+def test_fp64_flops_per_particle():
+    # D = 1: moments 2 (1 + 1 + 1); per component 3 + 2 + 1 + 2 + 2
+    assert list(bench.fp64_flops_per_particle(1, np.array([0, 1, 4]))) == [6, 16, 46]
+    # D = 3: moments 2 (1 + 3 + 6); per component 3 + 6 + 1 + 6 + 12
+    assert list(bench.fp64_flops_per_particle(3, np.array([0, 2]))) == [20, 76]
+
+
+def test_secondary_rooflines():
+    counts = np.array([10, 20])
+    K = np.array([2, 3])
+    kwork = np.array([4, 9])
+    sweeps = np.array([2, 3])
+    mufu, f64 = bench.em_secondary_rooflines(counts, K, kwork, sweeps, 1, 1e-3, 2000.0)
+    # 10 (3 * 4 + 2) + 20 (3 * 9 + 3) MUFU operations in 1 ms
+    assert mufu["achieved"] == pytest.approx(740 / 1e-3 / 1e12)
+    assert mufu["peak"] == pytest.approx(152 * 16 * 2000e6 / 1e12)
+    assert mufu["frac"] == pytest.approx(mufu["achieved"] / mufu["peak"])
+    # 10 (6 + 2 * 10) + 20 (6 + 3 * 10) FP64 flops in 1 ms
+    assert f64["achieved"] == pytest.approx(980 / 1e-3 / 1e12)
+    assert f64["peak"] == bench.FP64_PEAK_TFLOPS
+    assert f64["frac"] == pytest.approx(f64["achieved"] / f64["peak"])
