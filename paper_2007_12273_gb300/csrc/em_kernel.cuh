@@ -974,6 +974,29 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
   {
     const int K = c.K;
     const double nw = c.Nd / c.W;
+    // Normaliser pass: per particle the shift m_p = max_j log2(u_j f_j) and
+    // r_p = alpha_p (N / W) / S_p with S_p = sum_j 2^(log2(u_j f_j) - m_p)
+    // summed in FP64.  r_p goes to the tile's s_p / m_p records (8 bytes per
+    // particle there) and m_p to the first word of each particle's term
+    // record; the weights in the second word stay for the last exact pass.
+    // Every thread keeps its particles p = tid + i NT in all passes below, so
+    // it reads back only what it wrote.  The component passes recompute
+    // 2^(log2(u_k f_k) - m_p) with the same instructions on the same operands,
+    // so sum_k gamma_pk = alpha_p N / W to FP64 rounding.
+    double* Rd = reinterpret_cast<double*>(SMT);
+    float* Mf = GAT;  // particle p at 4 (p >> 1) + (p & 1)
+    for (int p = tid; p < N; p += NT) {
+      float y[D], d[D];
+#pragma unroll
+      for (int q = 0; q < D; ++q) y[q] = Y[q * ys + p];
+      float m = -3.0e38f;
+      for (int jj = 0; jj < K; ++jj) m = fmaxf(m, lg_eval<D>(c.emu[jj], c.eA[jj], c.eb[jj], y, d));
+      double Ssum = 0.0;
+      for (int jj = 0; jj < K; ++jj)
+        Ssum += (double)ex2(lg_eval<D>(c.emu[jj], c.eA[jj], c.eb[jj], y, d) - m);
+      Rd[p] = a.alpha[off + p] * nw / Ssum;
+      Mf[4 * (p >> 1) + (p & 1)] = m;
+    }
     for (int k = 0; k < K; ++k) {
       double ck[D];
 #pragma unroll
@@ -985,15 +1008,9 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
         float y[D], d[D];
 #pragma unroll
         for (int q = 0; q < D; ++q) y[q] = Y[q * ys + p];
-        float m = -3.0e38f;
-        for (int jj = 0; jj < K; ++jj) m = fmaxf(m, lg_eval<D>(c.emu[jj], c.eA[jj], c.eb[jj], y, d));
-        double Ssum = 0.0, gk = 0.0;
-        for (int jj = 0; jj < K; ++jj) {
-          const double g = (double)ex2(lg_eval<D>(c.emu[jj], c.eA[jj], c.eb[jj], y, d) - m);
-          Ssum += g;
-          if (jj == k) gk = g;
-        }
-        const double gam = a.alpha[off + p] * nw * gk / Ssum;
+        const float m = Mf[4 * (p >> 1) + (p & 1)];
+        const double gk = (double)ex2(lg_eval<D>(c.emu[k], c.eA[k], c.eb[k], y, d) - m);
+        const double gam = Rd[p] * gk;
         double dv[D];
 #pragma unroll
         for (int q = 0; q < D; ++q) dv[q] = ((double)vin[(int64_t)q * a.n + off + p] - c.mean[q]) - ck[q];
