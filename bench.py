@@ -146,10 +146,10 @@ FLOPS_PER_PK = {1: 30, 3: 90}  # FP32 flops per particle per component step
 
 
 # DRAM bytes (read + write) of one em_kernel launch per particle, from an
-# ncu capture of 1216 cells of the 1D-1V batch (FP32 v): 29.94 MB for
+# ncu capture of 1216 cells of the 1D-1V batch (FP32 v): 30.30 MB for
 # 2434617 particles, i.e. the inputs read once (4 B v + 8 B alpha).  The
 # traffic grows with the particles, so a full launch is this times n.
-EM_DRAM_BYTES_PER_PARTICLE = 29.938688e6 / 2434617
+EM_DRAM_BYTES_PER_PARTICLE = 30.302464e6 / 2434617
 
 
 def em_flops(counts: np.ndarray, kwork: np.ndarray, D: int) -> float:
