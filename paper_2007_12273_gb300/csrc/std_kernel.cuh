@@ -895,6 +895,29 @@ __global__ void __launch_bounds__(NT, (D == 1 ? 1024 : 512) / NT) std_kernel(Std
     {
       const int K = c.K;
       const double nw = c.Nd / c.W;
+      // Normaliser pass: per particle r_p = alpha_p (N / W) / S_p with
+      // S_p = sum_j 2^(log2(w_j f_j) - m_p) summed in FP64 (m_p the largest
+      // term), kept exactly as its two 32-bit halves in the particle's SS
+      // and MM words (free after the iterations).  Each thread keeps its
+      // particles p = tid + i NT in every pass, so it reads back only what it
+      // wrote; the component passes recompute m_p and the term of component k
+      // with the same instructions on the same operands, so
+      // sum_k gamma_pk = alpha_p N / W to FP64 rounding.
+      int* Rlo = reinterpret_cast<int*>(SS);
+      int* Rhi = reinterpret_cast<int*>(MM);
+      for (int p = tid; p < N; p += NT) {
+        float y[D], d[D];
+#pragma unroll
+        for (int q = 0; q < D; ++q) y[q] = Y[q * ys + p];
+        float m = -3.0e38f;
+        for (int jj = 0; jj < K; ++jj) m = fmaxf(m, lg_eval<D>(c.emu[jj], c.eA[jj], c.eb[jj], y, d));
+        double Ssum = 0.0;
+        for (int jj = 0; jj < K; ++jj)
+          Ssum += (double)ex2(lg_eval<D>(c.emu[jj], c.eA[jj], c.eb[jj], y, d) - m);
+        const double r = a.alpha[off + p] * nw / Ssum;
+        Rlo[p] = __double2loint(r);
+        Rhi[p] = __double2hiint(r);
+      }
       for (int k = 0; k < K; ++k) {
         double ck[D];
 #pragma unroll
@@ -908,13 +931,8 @@ __global__ void __launch_bounds__(NT, (D == 1 ? 1024 : 512) / NT) std_kernel(Std
           for (int q = 0; q < D; ++q) y[q] = Y[q * ys + p];
           float m = -3.0e38f;
           for (int jj = 0; jj < K; ++jj) m = fmaxf(m, lg_eval<D>(c.emu[jj], c.eA[jj], c.eb[jj], y, d));
-          double Ssum = 0.0, gk = 0.0;
-          for (int jj = 0; jj < K; ++jj) {
-            const double g = (double)ex2(lg_eval<D>(c.emu[jj], c.eA[jj], c.eb[jj], y, d) - m);
-            Ssum += g;
-            if (jj == k) gk = g;
-          }
-          const double gam = a.alpha[off + p] * nw * gk / Ssum;
+          const double gk = (double)ex2(lg_eval<D>(c.emu[k], c.eA[k], c.eb[k], y, d) - m);
+          const double gam = __hiloint2double(Rhi[p], Rlo[p]) * gk;
           double dv[D];
 #pragma unroll
           for (int q = 0; q < D; ++q) dv[q] = ((double)vin[(int64_t)q * a.n + off + p] - c.mean[q]) - ck[q];
