@@ -680,10 +680,11 @@ def run_gmcr(args):
 # whitening, sum of squares), the normaliser and the responsibility, and the
 # moment sums (1 + D + D(D+1)/2 fused multiply-adds).
 STD_FLOPS_PER_PKI = {1: 14, 3: 46}
-# DRAM bytes of one std_kernel launch (K-means + AA5) per particle, from an
-# ncu capture of 1216 cells of the 1D-1V batch: 29.38 MB for 2434617
-# particles (the inputs read once); a full launch is this times n
-STD_DRAM_BYTES_PER_PARTICLE = 29.381376e6 / 2434617
+# DRAM bytes of one std_kernel launch (K-means + AA5) per particle: None,
+# because the kernel's output step changed after its last ncu capture (1216
+# cells of the 1D-1V batch: 29.38 MB for 2434617 particles, the inputs read
+# once); a new capture sets it again (a full launch is it times n)
+STD_DRAM_BYTES_PER_PARTICLE = None
 STD_MODES = (("random", 0, 0, False), ("kmeans", 1, 0, False), ("random+aa5", 0, 5, False),
              ("kmeans+aa5", 1, 5, False), ("penalised", 0, 0, True))
 
@@ -825,7 +826,8 @@ def run_standard(args):
                      "achieved": hm["tflops"], "peak": peak, "unit": "TFLOP/s",
                      "frac": hm["frac_fp32_peak"],
                      "traffic": (STD_DRAM_BYTES_PER_PARTICLE * n
-                                 if D == 1 and wl.v.dtype == np.float32 else None),
+                                 if STD_DRAM_BYTES_PER_PARTICLE is not None and D == 1
+                                 and wl.v.dtype == np.float32 else None),
                      "note": f"FP32 flops = sum_j N_j * K_j * iters_j * {STD_FLOPS_PER_PKI[D]}; peak = "
                              f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"},
         "e2e": {"value": n / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
