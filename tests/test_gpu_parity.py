@@ -152,6 +152,25 @@ def test_compress_variable_weights_and_edge_cells(gm):
     check_compress_parity(g, ref, min_agree=0.75, wl=wl, min_equal_sweeps=1.0)
 
 
+@pytest.mark.parametrize("D", [1, 3])
+def test_compress_and_reconstruct_at_the_largest_kmax(gm, D):
+    """Kmax = 16, the largest the library accepts: every per-component array
+    of the EM kernel at full size (16 initial components); the fits and the
+    reconstruction of the oracle's fits against the oracle."""
+    if D == 1:
+        wl = workloads.mixture_1d1v(C=24, mean_n=1200, clip=(100, 3000), seed=91, Kmax=16)
+    else:
+        wl = workloads.bimaxwellian_1d3v(C=20, ppc=800, seed=92, Kmax=16)
+    g, gd = run_gpu_compress(gm, wl)
+    ref = oracle.compress(wl.params, wl.cell_off, wl.x, wl.v, wl.alpha, nthreads=NTHREADS)
+    check_compress_parity(g, ref, min_agree=0.5, wl=wl, min_equal_sweeps=0.9)
+    check_fit_moments(gm, wl, gd)
+    gr, o = recon_both(gm, wl, ref)
+    np.testing.assert_array_equal(gr["x"], o["x"])
+    np.testing.assert_allclose(gr["alpha"], o["alpha"], rtol=1e-12)
+    np.testing.assert_array_equal(gr["status"], o["status"])
+
+
 def test_compress_kmax1_is_sample_moments(gm):
     wl = workloads.bimaxwellian_1d3v(C=6, ppc=700)
     wl.params["Kmax"] = 1
