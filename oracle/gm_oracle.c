@@ -19,6 +19,7 @@
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
@@ -39,6 +40,26 @@
 #define ST_NEG_WEIGHT     0x200u
 #define ST_MM_EMPTY_COL   0x400u
 #define ST_NO_MIXTURE     0x800u
+
+/* Allocation that fails loudly: this library is test infrastructure, so an
+ * allocation failure ends the process with a message (instead of a NULL
+ * dereference inside a parallel loop). */
+static void *or_malloc(size_t bytes) {
+  void *p = malloc(bytes > 0 ? bytes : 1);
+  if (!p) {
+    fprintf(stderr, "gm_oracle: out of memory (%zu bytes)\n", bytes);
+    abort();
+  }
+  return p;
+}
+static void *or_calloc(size_t n, size_t size) {
+  void *p = calloc(n > 0 ? n : 1, size > 0 ? size : 1);
+  if (!p) {
+    fprintf(stderr, "gm_oracle: out of memory (%zu x %zu bytes)\n", n, size);
+    abort();
+  }
+  return p;
+}
 
 typedef struct oracle_cfg {
   int D;            /* velocity dimensions, 1 or 3 */
@@ -241,8 +262,8 @@ static void em_cell(const oracle_cfg *cfg, int64_t cell, int64_t N, const double
   o->W = W;
   if (!(W > 0.0)) { o->status = ST_EMPTY | ST_DEGENERATE; return; }
   const double Nd = (double)N;
-  double *ah = (double *)malloc(sizeof(double) * (size_t)N);
-  double *gam = (double *)malloc(sizeof(double) * (size_t)N * OR_MAXK);
+  double *ah = (double *)or_malloc(sizeof(double) * (size_t)N);
+  double *gam = (double *)or_malloc(sizeof(double) * (size_t)N * OR_MAXK);
   for (int64_t p = 0; p < N; ++p) ah[p] = alpha[p] * Nd / W;
   if (N <= 10) o->status |= ST_TOO_FEW; /* Sec. 1: "more than 10" per cell */
 
@@ -503,7 +524,7 @@ int oracle_compress(const oracle_cfg *cfg, int64_t C, const int64_t *cell_off,
 #endif
   for (int64_t j = 0; j < C; ++j) {
     int64_t n = cell_off[j + 1] - cell_off[j];
-    double *vv = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * D);
+    double *vv = (double *)or_malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * D);
     for (int64_t p = 0; p < n; ++p)
       for (int d = 0; d < D; ++d) vv[p * D + d] = v[(int64_t)d * Ntot + cell_off[j] + p];
     cell_out o;
@@ -574,12 +595,12 @@ static void thomas(int64_t n, const double *a, const double *b, const double *c,
 int oracle_cyclic_tridiag(int64_t n, const double *a, const double *b, const double *c,
                           const double *d, double *x) {
   if (n < 3) return -1;
-  double *bb = (double *)malloc(sizeof(double) * n);
-  double *u = (double *)malloc(sizeof(double) * n);
-  double *y = (double *)malloc(sizeof(double) * n);
-  double *z = (double *)malloc(sizeof(double) * n);
-  double *cp = (double *)malloc(sizeof(double) * n);
-  double *dp = (double *)malloc(sizeof(double) * n);
+  double *bb = (double *)or_malloc(sizeof(double) * n);
+  double *u = (double *)or_malloc(sizeof(double) * n);
+  double *y = (double *)or_malloc(sizeof(double) * n);
+  double *z = (double *)or_malloc(sizeof(double) * n);
+  double *cp = (double *)or_malloc(sizeof(double) * n);
+  double *dp = (double *)or_malloc(sizeof(double) * n);
   /* A = T + u v^T, u = (g, 0..0, c_{n-1}), v = (1, 0..0, a_0/g), g = -b_0 */
   double g = -b[0];
   for (int64_t i = 0; i < n; ++i) { bb[i] = b[i]; u[i] = 0.0; }
@@ -785,15 +806,15 @@ int oracle_reconstruct(const oracle_cfg *cfg, int64_t C, const int32_t *K, const
   /* 2. Gauss' law (Sec. 2.4.1): rho from the sampled particles, the mass
    *    matrix M_ij = sum_p q S0(x_j - x_p) S(x_i - x_p) (column j collects
    *    the particles of cell j), and the solve M dA = dx (rho' - rho). */
-  double *rho = (double *)malloc(sizeof(double) * C);
-  double *rhs = (double *)malloc(sizeof(double) * C);
-  double *dA = (double *)malloc(sizeof(double) * C);
+  double *rho = (double *)or_malloc(sizeof(double) * C);
+  double *rhs = (double *)or_malloc(sizeof(double) * C);
+  double *dA = (double *)or_malloc(sizeof(double) * C);
   deposit(cfg, C, out_off, x_out, alpha_out, rho);
   for (int64_t i = 0; i < C; ++i) rhs[i] = dx * (rho_target[i] - rho[i]);
   if (C >= 3) {
-    double *a = (double *)calloc(C, sizeof(double)); /* M(i, i-1) */
-    double *b = (double *)calloc(C, sizeof(double)); /* M(i, i)   */
-    double *c = (double *)calloc(C, sizeof(double)); /* M(i, i+1) */
+    double *a = (double *)or_calloc(C, sizeof(double)); /* M(i, i-1) */
+    double *b = (double *)or_calloc(C, sizeof(double)); /* M(i, i)   */
+    double *c = (double *)or_calloc(C, sizeof(double)); /* M(i, i+1) */
     for (int64_t j = 0; j < C; ++j)
       for (int64_t p = out_off[j]; p < out_off[j + 1]; ++p)
         for (int64_t i = j - 1; i <= j + 1; ++i) {
@@ -939,10 +960,10 @@ int oracle_reconstruct2d(const oracle_cfg *cfg, const oracle_mesh2d *m, const in
   }
 
   /* 2. Gauss' law */
-  double *rho = (double *)malloc(sizeof(double) * C);
-  double *rhs = (double *)malloc(sizeof(double) * C);
-  double *dA = (double *)malloc(sizeof(double) * C);
-  double *A = (double *)calloc((size_t)C * C, sizeof(double));
+  double *rho = (double *)or_malloc(sizeof(double) * C);
+  double *rhs = (double *)or_malloc(sizeof(double) * C);
+  double *dA = (double *)or_malloc(sizeof(double) * C);
+  double *A = (double *)or_calloc((size_t)C * C, sizeof(double));
   deposit2d(cfg, m, out_off, x_out, y_out, alpha_out, rho);
   for (int64_t i = 0; i < C; ++i) rhs[i] = dx * dy * (rho_target[i] - rho[i]);
   for (int64_t j = 0; j < C; ++j) {
@@ -1337,8 +1358,8 @@ static int kmeans_init(int D, int K, int64_t N, const double *vv, const double *
                        const int64_t *picks, int iters, comp *cs, int *passes) {
   double isd[OR_MAXD];
   for (int d = 0; d < D; ++d) isd[d] = 1.0 / sd[d];
-  float *y = (float *)malloc(sizeof(float) * (size_t)N * D);
-  int *as = (int *)malloc(sizeof(int) * (size_t)N);
+  float *y = (float *)or_malloc(sizeof(float) * (size_t)N * D);
+  int *as = (int *)or_malloc(sizeof(int) * (size_t)N);
   for (int64_t p = 0; p < N; ++p)
     for (int d = 0; d < D; ++d) y[p * D + d] = (float)((vv[p * D + d] - mean[d]) * isd[d]);
   float c[OR_MAXK][OR_MAXD];
@@ -1443,8 +1464,8 @@ static void std_cell(const oracle_cfg *cfg, int64_t cell, int64_t N, const doubl
   o->W = W;
   if (!(W > 0.0)) { o->status = ST_EMPTY | ST_DEGENERATE; return; }
   const double Nd = (double)N;
-  double *ah = (double *)malloc(sizeof(double) * (size_t)N);
-  double *gam = (double *)malloc(sizeof(double) * (size_t)N * OR_MAXK);
+  double *ah = (double *)or_malloc(sizeof(double) * (size_t)N);
+  double *gam = (double *)or_malloc(sizeof(double) * (size_t)N * OR_MAXK);
   for (int64_t p = 0; p < N; ++p) ah[p] = alpha[p] * Nd / W;
   if (N <= 10) o->status |= ST_TOO_FEW;
   double mean[OR_MAXD] = {0}, cov[OR_MAXD][OR_MAXD] = {{0}}, sd[OR_MAXD];
@@ -1518,7 +1539,7 @@ static void std_cell(const oracle_cfg *cfg, int64_t cell, int64_t N, const doubl
       chol_floor(D, cs[k].S, cs[k].mu, cs[k].Lc, &cs[k].logdet);
     }
   }
-  aa_state *aa = (aa_state *)malloc(sizeof(aa_state));
+  aa_state *aa = (aa_state *)or_malloc(sizeof(aa_state));
   aa_init(aa, K * P, aa_m);
   double th[AA_MAXN], tg[AA_MAXN], tn[AA_MAXN];
   double Lprev = 0.0;
@@ -1603,7 +1624,7 @@ int oracle_standard(const oracle_cfg *cfg, int64_t C, const int64_t *cell_off, c
 #endif
   for (int64_t j = 0; j < C; ++j) {
     int64_t n = cell_off[j + 1] - cell_off[j];
-    double *vv = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * D);
+    double *vv = (double *)or_malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * D);
     for (int64_t p = 0; p < n; ++p)
       for (int d = 0; d < D; ++d) vv[p * D + d] = v[(int64_t)d * Ntot + cell_off[j] + p];
     std_out o;
@@ -1644,7 +1665,7 @@ int oracle_std_cell(const oracle_cfg *cfg, int64_t cell, int64_t N, const double
 int oracle_aa_affine(int n, const double *A, const double *b, const double *x0, int m, int iters,
                      double *x_out, double *res_trace) {
   if (n < 1 || n > AA_MAXN) return -1;
-  aa_state *s = (aa_state *)malloc(sizeof(aa_state));
+  aa_state *s = (aa_state *)or_malloc(sizeof(aa_state));
   aa_init(s, n, m);
   double x[AA_MAXN], g[AA_MAXN], xn[AA_MAXN];
   memcpy(x, x0, sizeof(double) * (size_t)n);
