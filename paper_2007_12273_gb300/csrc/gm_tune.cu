@@ -105,8 +105,13 @@ int tune_impl(gm_config* cfg, int64_t C, int64_t n_particles, const int64_t* cel
   o.lnL = (double*)(b + 4 * bK + bP + 2 * bD);
 
   cudaEvent_t t0 = nullptr, t1 = nullptr;
-  cudaEventCreate(&t0);
-  cudaEventCreate(&t1);
+  e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  if (e != cudaSuccess) {
+    if (t0) cudaEventDestroy(t0);
+    cudaFree(o.base);
+    return tune_fail(GM_ERR_CUDA, "timing events", e);
+  }
   float times[kTuneCands];
   for (int i = 0; i < kTuneCands; ++i) times[i] = -1.0f;
   int best = -1;
