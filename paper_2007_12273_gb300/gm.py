@@ -163,13 +163,49 @@ def _stream_ptr(stream):
     return ct.c_void_p(s.cuda_stream)
 
 
-def _check(t, dtype, name):
+# per-cell status words: int32 or uint32 tensors
+_STATUS = (torch.int32,) + ((torch.uint32,) if hasattr(torch, "uint32") else ())
+
+
+def _check(t, dtype, name, numel: int | None = None):
+    """A contiguous CUDA tensor of ``dtype`` (or of one of a tuple of dtypes)
+    with at least ``numel`` elements: the C call reads or writes that many
+    through its pointer, so a shorter tensor is refused here."""
+    if t is None:
+        raise ValueError(f"{name} is required")
     if not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
-    if t.dtype != dtype:
-        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    dts = dtype if isinstance(dtype, tuple) else (dtype,)
+    if t.dtype not in dts:
+        raise ValueError(f"{name} must be {' or '.join(map(str, dts))}, got {t.dtype}")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} has {t.numel()} elements; the call needs at least {numel}")
+
+
+def _check_out(out: dict, required: dict, optional: dict | None = None):
+    """Caller-supplied outputs: every ``required`` key (name -> (dtype,
+    numel)) present and valid, every ``optional`` key valid if present."""
+    for k, (dt, ne) in required.items():
+        if k not in out:
+            raise ValueError(f"out is missing {k!r}")
+        _check(out[k], dt, f"out[{k!r}]", ne)
+    for k, (dt, ne) in (optional or {}).items():
+        if out.get(k) is not None:
+            _check(out[k], dt, f"out[{k!r}]", ne)
+
+
+def _check_particles(cfg: GMConfig, cell_off, x, v, alpha, n: int):
+    """Particles in CSR order: cell_off [C+1] int64, x [n] f64 (optional),
+    v [D, n] f32 / f64, alpha [n] f64."""
+    _check(cell_off, torch.int64, "cell_off")
+    if x is not None:
+        _check(x, torch.float64, "x", n)
+    _check(alpha, torch.float64, "alpha", n)
+    if v is None or v.dtype not in (torch.float32, torch.float64) or tuple(v.shape) != (cfg.D, n):
+        raise ValueError("v must be [D, n] float32/float64")
+    _check(v, v.dtype, "v")
 
 
 def _rc(lib, rc, what):
@@ -188,14 +224,16 @@ def gm_compress(cfg: GMConfig, cell_off, x, v, alpha, stream=None, out=None, ini
     C = cell_off.shape[0] - 1
     n = alpha.shape[0]
     D = cfg.D
-    _check(cell_off, torch.int64, "cell_off")
-    if x is not None:
-        _check(x, torch.float64, "x")
-    _check(alpha, torch.float64, "alpha")
-    if v.dtype not in (torch.float32, torch.float64) or tuple(v.shape) != (D, n):
-        raise ValueError("v must be [D, n] float32/float64")
-    _check(v, v.dtype, "v")
+    KP = C * cfg.Kmax * P_of(D)
+    _check_particles(cfg, cell_off, x, v, alpha, n)
     dev = alpha.device
+    if out is not None:
+        req = dict(K=(torch.int32, C), params=(torch.float64, KP), W=(torch.float64, C),
+                   lnL=(torch.float64, C), sweeps=(torch.int32, C), kwork=(torch.int32, C),
+                   status=(_STATUS, C))
+        if x is not None:
+            req["rho_target"] = (torch.float64, C)
+        _check_out(out, req)
     if out is None:
         out = dict(K=torch.empty(C, dtype=torch.int32, device=dev),
                    params=torch.empty((C, cfg.Kmax, P_of(D)), dtype=torch.float64, device=dev),
@@ -215,12 +253,31 @@ def gm_compress(cfg: GMConfig, cell_off, x, v, alpha, stream=None, out=None, ini
                              _ptr(alpha), *tail)
         _rc(lib, rc, "gm_compress")
     else:
-        _check(init_K, torch.int32, "init_K")
-        _check(init_params, torch.float64, "init_params")
+        _check(init_K, torch.int32, "init_K", C)
+        _check(init_params, torch.float64, "init_params", KP)
         rc = lib.gm_compress_from(ct.byref(cfg), C, n, _ptr(cell_off), _ptr(x), _ptr(v), vf,
                                   _ptr(alpha), _ptr(init_K), _ptr(init_params), *tail)
         _rc(lib, rc, "gm_compress_from")
     return out
+
+
+def _check_mixtures(cfg: GMConfig, C: int, K, params, W, rho_target=None):
+    """Per-cell mixtures as gm_compress writes them: K [C] int32, params
+    [C][Kmax][P] f64, W [C] f64 (and rho_target [C] f64)."""
+    _check(K, torch.int32, "K", C)
+    _check(params, torch.float64, "params", C * cfg.Kmax * P_of(cfg.D))
+    _check(W, torch.float64, "W", C)
+    if rho_target is not None:
+        _check(rho_target, torch.float64, "rho_target", C)
+
+
+def _check_recon_out(out: dict, D: int, C: int, n_out: int, two_d: bool = False):
+    """Caller-supplied reconstruction outputs (dA optional)."""
+    req = dict(x=(torch.float64, n_out), v=(torch.float64, D * n_out),
+               alpha=(torch.float64, n_out), status=(_STATUS, C))
+    if two_d:
+        req["y"] = (torch.float64, n_out)
+    _check_out(out, req, dict(dA=(torch.float64, C)))
 
 
 def gm_reconstruct(cfg: GMConfig, K, params, W, rho_target, out_off, n_out: int | None = None,
@@ -231,14 +288,13 @@ def gm_reconstruct(cfg: GMConfig, K, params, W, rho_target, out_off, n_out: int 
     lib = load()
     C = out_off.shape[0] - 1
     D = cfg.D
-    _check(K, torch.int32, "K")
-    _check(params, torch.float64, "params")
-    _check(W, torch.float64, "W")
-    _check(rho_target, torch.float64, "rho_target")
+    _check_mixtures(cfg, C, K, params, W, rho_target)
     _check(out_off, torch.int64, "out_off")
     if n_out is None:
         n_out = int(out_off[-1].item())
     dev = W.device
+    if out is not None:
+        _check_recon_out(out, D, C, n_out)
     if out is None:
         out = dict(x=torch.empty(n_out, dtype=torch.float64, device=dev),
                    v=torch.empty((D, n_out), dtype=torch.float64, device=dev),
@@ -262,10 +318,9 @@ def gm_reconstruct_noalloc(cfg: GMConfig, K, params, W, rho_target, out_off, out
     (keys x, v, alpha, status, optionally dA)."""
     lib = load()
     C = out_off.shape[0] - 1
-    for nm_, t_, dt in (("K", K, torch.int32), ("params", params, torch.float64),
-                        ("W", W, torch.float64), ("rho_target", rho_target, torch.float64),
-                        ("out_off", out_off, torch.int64)):
-        _check(t_, dt, nm_)
+    _check_mixtures(cfg, C, K, params, W, rho_target)
+    _check(out_off, torch.int64, "out_off")
+    _check_recon_out(out, cfg.D, C, int(n_out))
     rc = lib.gm_reconstruct_noalloc(ct.byref(cfg), C, _ptr(K), _ptr(params), _ptr(W),
                                     _ptr(rho_target), int(n_out), _ptr(out_off), _ptr(out["x"]),
                                     _ptr(out["v"]), _ptr(out["alpha"]), _ptr(out["status"]),
@@ -281,6 +336,7 @@ def gm_moments(cfg: GMConfig, cell_off, x, v, alpha, stream=None) -> dict:
     D = cfg.D
     dev = alpha.device
     nm = D * (D + 1) // 2
+    _check_particles(cfg, cell_off, x, v, alpha, n)
     out = dict(W=torch.empty(C, dtype=torch.float64, device=dev),
                p=torch.empty((C, D), dtype=torch.float64, device=dev),
                M2=torch.empty((C, nm), dtype=torch.float64, device=dev),
@@ -300,6 +356,7 @@ def gm_mixture_moments(cfg: GMConfig, K, params, W, stream=None) -> dict:
     D = cfg.D
     dev = W.device
     nm = D * (D + 1) // 2
+    _check_mixtures(cfg, C, K, params, W)
     out = dict(W=torch.empty(C, dtype=torch.float64, device=dev),
                p=torch.empty((C, D), dtype=torch.float64, device=dev),
                M2=torch.empty((C, nm), dtype=torch.float64, device=dev),
@@ -494,6 +551,7 @@ def gm_autotune(cfg: GMConfig, cell_off, x, v, alpha, sweeps_per_trial: int = 0,
     lib = load()
     C = cell_off.shape[0] - 1
     n = x.shape[0]
+    _check_particles(cfg, cell_off, x, v, alpha, n)
     t = (ct.c_float * TUNE_CANDIDATES)()
     vf = 1 if v.dtype == torch.float64 else 0
     if init_K is None:
@@ -501,8 +559,8 @@ def gm_autotune(cfg: GMConfig, cell_off, x, v, alpha, sweeps_per_trial: int = 0,
                              int(sweeps_per_trial), t, _stream_ptr(stream))
         _rc(lib, rc, "gm_autotune")
     else:  # trials from the supplied initial mixtures (gm_autotune_from)
-        _check(init_K, torch.int32, "init_K")
-        _check(init_params, torch.float64, "init_params")
+        _check(init_K, torch.int32, "init_K", C)
+        _check(init_params, torch.float64, "init_params", C * cfg.Kmax * P_of(cfg.D))
         rc = lib.gm_autotune_from(ct.byref(cfg), C, n, _ptr(cell_off), _ptr(x), _ptr(v), vf,
                                   _ptr(alpha), _ptr(init_K), _ptr(init_params), int(sweeps_per_trial),
                                   t, _stream_ptr(stream))
@@ -574,13 +632,14 @@ def gm_compress_standard(cfg: GMConfig, cell_off, x, v, alpha, init: int = 0, aa
     C = cell_off.shape[0] - 1
     n = x.shape[0]
     D = cfg.D
-    _check(cell_off, torch.int64, "cell_off")
-    _check(x, torch.float64, "x")
-    _check(alpha, torch.float64, "alpha")
-    if v.dtype not in (torch.float32, torch.float64) or tuple(v.shape) != (D, n):
-        raise ValueError("v must be [D, n] float32/float64")
-    _check(v, v.dtype, "v")
+    _check_particles(cfg, cell_off, x, v, alpha, n)
     dev = x.device
+    if out is not None:
+        _check_out(out, dict(K=(torch.int32, C), params=(torch.float64, C * cfg.Kmax * P_of(D)),
+                             W=(torch.float64, C), rho_target=(torch.float64, C),
+                             lnL=(torch.float64, C), iters=(torch.int32, C),
+                             aa_steps=(torch.int32, C), aa_resets=(torch.int32, C),
+                             km_passes=(torch.int32, C), status=(_STATUS, C)))
     if out is None:
         i32 = lambda: torch.empty(C, dtype=torch.int32, device=dev)
         out = dict(K=i32(), params=torch.empty((C, cfg.Kmax, P_of(D)), dtype=torch.float64, device=dev),
@@ -613,6 +672,8 @@ def gm_deposit_2d(cfg: GMConfig, mesh: GMMesh2d, cell_off, x, y, alpha=None, str
         _check(alpha, torch.float64, "alpha")
     if out is None:
         out = torch.empty(C, dtype=torch.float64, device=x.device)
+    else:
+        _check(out, torch.float64, "out", C)
     rc = lib.gm_deposit_2d(ct.byref(cfg), ct.byref(mesh), _ptr(cell_off), _ptr(x), _ptr(y), _ptr(alpha),
                            _ptr(out), _stream_ptr(stream))
     _rc(lib, rc, "gm_deposit_2d")
@@ -628,14 +689,13 @@ def gm_reconstruct_2d(cfg: GMConfig, mesh: GMMesh2d, K, params, W, rho_target, o
     D = cfg.D
     if out_off.shape[0] != C + 1:
         raise ValueError("out_off must have Cx * Cy + 1 entries")
-    _check(K, torch.int32, "K")
-    _check(params, torch.float64, "params")
-    _check(W, torch.float64, "W")
-    _check(rho_target, torch.float64, "rho_target")
+    _check_mixtures(cfg, C, K, params, W, rho_target)
     _check(out_off, torch.int64, "out_off")
     if n_out is None:
         n_out = int(out_off[-1].item())
     dev = W.device
+    if out is not None:
+        _check_recon_out(out, D, C, n_out, two_d=True)
     if out is None:
         out = dict(x=torch.empty(n_out, dtype=torch.float64, device=dev),
                    y=torch.empty(n_out, dtype=torch.float64, device=dev),
