@@ -411,11 +411,14 @@ def gm_features(cfg: GMConfig, cell_off, v, alpha, stream=None, out=None):
     C = cell_off.shape[0] - 1
     n = alpha.shape[0]
     D = cfg.D
+    _check_particles(cfg, cell_off, None, v, alpha, n)
     if out is None:
         feat = torch.empty((C, feat_width(D)), dtype=torch.bfloat16, device=alpha.device)
         wstat = torch.empty((C, 2 * D), dtype=torch.float64, device=alpha.device)
     else:
         feat, wstat = out
+        _check(feat, torch.bfloat16, "feat", C * feat_width(D))
+        _check(wstat, torch.float64, "wstat", C * 2 * D)
     rc = lib.gm_features(ct.byref(cfg), C, n, _ptr(cell_off), _ptr(v),
                          1 if v.dtype == torch.float64 else 0, _ptr(alpha), _ptr(feat),
                          _ptr(wstat), _stream_ptr(stream))
@@ -427,6 +430,9 @@ def gm_mlp_targets(cfg: GMConfig, K, params, wstat, stream=None):
     lib = load()
     C = K.shape[0]
     O = out_width(cfg.D, cfg.Kmax)
+    _check(K, torch.int32, "K", C)
+    _check(params, torch.float64, "params", C * cfg.Kmax * P_of(cfg.D))
+    _check(wstat, torch.float64, "wstat", C * 2 * cfg.D)
     T = torch.empty((C, O), dtype=torch.float32, device=K.device)
     Mk = torch.empty((C, O), dtype=torch.float32, device=K.device)
     rc = lib.gm_mlp_targets(ct.byref(cfg), C, _ptr(K), _ptr(params), _ptr(wstat), O, _ptr(T),
@@ -442,11 +448,18 @@ def gm_mlp_decode(cfg: GMConfig, out, wstat, cell_off, stream=None, dest=None,
     ``dest`` = (K0, params) may supply them."""
     lib = load()
     C = cell_off.shape[0] - 1
+    _check(cell_off, torch.int64, "cell_off")
+    _check(out, torch.float32, "out")
+    if out.dim() != 2 or out.shape[0] < C or out.shape[1] < cfg.Kmax * slot_size(cfg.D):
+        raise ValueError(f"out must be [C, >= {cfg.Kmax * slot_size(cfg.D)}] float32")
+    _check(wstat, torch.float64, "wstat", C * 2 * cfg.D)
     if dest is None:
         K0 = torch.empty(C, dtype=torch.int32, device=out.device)
         prm = torch.empty((C, cfg.Kmax, P_of(cfg.D)), dtype=torch.float64, device=out.device)
     else:
         K0, prm = dest
+        _check(K0, torch.int32, "K0", C)
+        _check(prm, torch.float64, "params", C * cfg.Kmax * P_of(cfg.D))
     rc = lib.gm_mlp_decode(ct.byref(cfg), C, _ptr(out), out.shape[1], _ptr(wstat), _ptr(cell_off),
                            float(presence_logit), _ptr(K0), _ptr(prm), _stream_ptr(stream))
     _rc(lib, rc, "gm_mlp_decode")
@@ -512,11 +525,18 @@ class Net:
             self._scratch = torch.empty(need, dtype=torch.uint8, device=self.device)
         return self._scratch
 
+    def _check_rows(self, X):
+        _check(X, torch.bfloat16, "X")
+        if X.dim() != 2 or X.shape[1] != self.F:
+            raise ValueError(f"X must be [M, {self.F}] bfloat16")
+        return X.shape[0]
+
     def forward(self, X, out=None, stream=None):
         lib = load()
-        M = X.shape[0]
+        M = self._check_rows(X)
         if out is None:
             out = torch.empty((M, self.O), dtype=torch.float32, device=self.device)
+        _check(out, torch.float32, "out", M * self.O)
         sc = self.scratch(M)
         rc = lib.gm_mlp_forward(ct.byref(self.s), M, _ptr(X), _ptr(sc), sc.numel(), _ptr(out),
                                 _ptr(self.err), _stream_ptr(stream))
@@ -527,11 +547,15 @@ class Net:
         """One step; returns the device loss accumulator.  lr <= 0 computes
         gradients only."""
         lib = load()
-        M = X.shape[0]
+        M = self._check_rows(X)
+        _check(T, torch.float32, "T", M * self.O)
+        _check(Mk, torch.float32, "Mk", M * self.O)
         if out is None:
             out = torch.empty((M, self.O), dtype=torch.float32, device=self.device)
         if loss is None:
             loss = torch.zeros(1, dtype=torch.float64, device=self.device)
+        _check(out, torch.float32, "out", M * self.O)
+        _check(loss, torch.float64, "loss", 1)
         if lr > 0:
             self.step += 1
         sc = self.scratch(M)

@@ -77,3 +77,22 @@ def test_particles():
         gm._check_particles(cfg, T(4, torch.int64), T(n), V((1, n)), T(n - 1), n)
     with pytest.raises(ValueError, match="cell_off"):
         gm._check_particles(cfg, T(4, torch.int32), T(n), V((1, n)), T(n), n)
+
+
+def test_network_rows():
+    import types
+
+    class X(T):
+        def __init__(self, shape, dtype=torch.bfloat16):
+            super().__init__(shape[0] * shape[1], dtype)
+            self.shape = shape
+
+        def dim(self):
+            return len(self.shape)
+
+    net = types.SimpleNamespace(F=gm.feat_width(1))
+    assert gm.Net._check_rows(net, X((32, 128))) == 32
+    with pytest.raises(ValueError, match=r"\[M, 128\]"):
+        gm.Net._check_rows(net, X((32, 576)))
+    with pytest.raises(ValueError, match="bfloat16"):
+        gm.Net._check_rows(net, X((32, 128), torch.float32))
