@@ -69,7 +69,9 @@ typedef struct gm_config {
                                inverse, weight): 0 = FP32 (default), 1 = FP64.  Either
                                way the component means are accumulated to about 48
                                bits (FP64, or a pair of FP32 numbers) and the final
-                               unpenalised step is entirely FP64 */
+                               unpenalised step is entirely FP64.  Another value,
+                               like a threads_per_cell or smem_particles out of
+                               range, is GM_ERR_ARG (before any device call) */
   int32_t reserved;         /* must be 0 */
 } gm_config;
 

@@ -231,9 +231,6 @@ static int compress_impl(const gm_config* cfg, int64_t C, int64_t n_particles,
   if (!cell_off || !v || !alpha || !K_out || !params_out || !W_out || !lnL_out || !status_out)
     return fail(GM_ERR_ARG, "a required pointer is NULL");
   if (!x != !rho_target_out) return fail(GM_ERR_ARG, "x and rho_target_out must be both set or both NULL");
-  int sms = 0;
-  if ((rc = check_device(&sms))) return rc;
-  cudaStream_t s = (cudaStream_t)stream;
   const int D = cfg->D;
   int nt = cfg->threads_per_cell > 0 ? cfg->threads_per_cell : 256;
   if (nt != 64 && nt != 128 && nt != 256)
@@ -243,7 +240,12 @@ static int compress_impl(const gm_config* cfg, int64_t C, int64_t n_particles,
   if (cap < 4) cap = 4;
   const size_t smem = (size_t)cap * (D + 4) * sizeof(float);
   if (smem > 200 * 1024) return fail(GM_ERR_ARG, "smem_particles too large (%d)", cap);
-  const int fp64_mstep = (cfg->precision == 1) ? 1 : 0;
+  if (cfg->precision != 0 && cfg->precision != 1)
+    return fail(GM_ERR_ARG, "precision must be 0 (FP32 M-step) or 1 (FP64) (got %d)", cfg->precision);
+  const int fp64_mstep = cfg->precision;
+  int sms = 0;
+  if ((rc = check_device(&sms))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
 
   const size_t q_bytes = 256, part_bytes = align256((size_t)3 * C * sizeof(double));
   const int64_t sstride = gmcr::scratch_stride(n_particles, C);

@@ -64,6 +64,18 @@ def test_argument_errors_without_gpu(lib):
     cfg = gm.config(dict(D=1, Kmax=4, shape_order=3, L=1.0))
     assert lib.gm_moments(ct.byref(cfg), 1, 1, None, None, None, 0, None, None, None, None,
                           None, None, None) == -1
+    # launch options are checked before any device call
+    cfg = gm.config(dict(D=1, Kmax=4, shape_order=2, L=1.0), precision=2)
+    ptr = ct.c_void_p(16)  # never dereferenced: the call fails on the option
+    args = (1, 1, ptr, None, ptr, 0, ptr, ptr, ptr, ptr, None, ptr, ptr, ptr, ptr, None)
+    assert lib.gm_compress(ct.byref(cfg), *args) == -1
+    assert b"precision" in lib.gm_last_error()
+    cfg = gm.config(dict(D=1, Kmax=4, shape_order=2, L=1.0), threads_per_cell=96)
+    assert lib.gm_compress(ct.byref(cfg), *args) == -1
+    assert b"threads_per_cell" in lib.gm_last_error()
+    cfg = gm.config(dict(D=1, Kmax=4, shape_order=2, L=1.0), smem_particles=1 << 20)
+    assert lib.gm_compress(ct.byref(cfg), *args) == -1
+    assert b"smem_particles" in lib.gm_last_error()
     # empty problems are valid no-ops
     cfg = gm.config(dict(D=1, Kmax=4, shape_order=2, L=1.0))
     assert lib.gm_mixture_moments(ct.byref(cfg), 0, None, None, None, None, None, None, None,
