@@ -375,6 +375,34 @@ def test_reconstruction_conserves_charge_momentum_energy(which):
     assert np.all(rec["x"] >= cell * dx) and np.all(rec["x"] < (cell + 1) * dx)
 
 
+def test_projection_is_one_scalar_affine_map_per_cell():
+    # Sec. 2.4.2, eqs. (alpha), (beta): a projected cell's velocities are
+    # v' = a (v + beta) with ONE scalar a > 0 for all D axes and a vector
+    # beta.  With the conservation of momentum and energy (tested above),
+    # that form fixes a and beta uniquely; a per-axis scaling would also
+    # conserve both and is excluded here.
+    wl = workloads.with_weights(workloads.bimaxwellian_1d3v(C=6, ppc=300))
+    out, rec = _roundtrip(wl)
+    done = 0
+    for j in range(wl.C):
+        if rec["status"][j] & oracle.ST_PROJ_SKIPPED:
+            continue
+        sl = slice(wl.cell_off[j], wl.cell_off[j + 1])
+        u, w = rec["v_raw"][:, sl], rec["v"][:, sl]
+        slopes = []
+        for d in range(wl.D):
+            A = np.stack([u[d], np.ones(u.shape[1])], axis=1)
+            coef, *_ = np.linalg.lstsq(A, w[d], rcond=None)
+            resid = w[d] - A @ coef
+            assert np.abs(resid).max() <= 1e-12 * np.abs(w[d]).max(), (j, d)
+            slopes.append(coef[0])
+        slopes = np.array(slopes)
+        assert slopes.min() > 0
+        np.testing.assert_allclose(slopes, slopes[0], rtol=1e-12)
+        done += 1
+    assert done >= 4
+
+
 def test_sampling_matches_mixture_distribution():
     # ancestral sampling, eq. (mix-dist-1): the raw samples of one cell follow
     # the mixture CDF (KS test) and positions are uniform in the cell
