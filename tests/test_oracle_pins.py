@@ -375,6 +375,41 @@ def test_reconstruction_conserves_charge_momentum_energy(which):
     assert np.all(rec["x"] >= cell * dx) and np.all(rec["x"] < (cell + 1) * dx)
 
 
+@pytest.mark.parametrize("order", [1, 2])
+def test_gauss_correction_is_the_mass_matrix_equation(order):
+    # Sec. 2.4.1, eqs. (p-weight-correction), (new-p-weight): every resampled
+    # particle of cell j gets the same dA_j, and dA solves M dA = dx (rho' -
+    # rho) with M_ij = q sum_{p in j} S(x_i - x_p).  M, rho and the residual
+    # are built here from scipy's B-spline basis and a dense product.
+    wl = workloads.mixture_1d1v(C=12, mean_n=300, clip=(50, 600), seed=23, shape_order=order)
+    p = dict(wl.params, q=-0.8)
+    out = oracle.compress(p, wl.cell_off, wl.x, wl.v, wl.alpha, nthreads=4)
+    rec = oracle.reconstruct(p, out["K"], out["params"], out["W"], out["rho_target"], wl.cell_off,
+                             nthreads=4)
+    C, L, q = wl.C, p["L"], p["q"]
+    dx = L / C
+    knots = [-1.0, 0.0, 1.0] if order == 1 else [-1.5, -0.5, 0.5, 1.5]
+    S = interpolate.BSpline.basis_element(knots, extrapolate=False)
+    M = np.zeros((C, C))
+    for j in range(C):
+        a, b = wl.cell_off[j], wl.cell_off[j + 1]
+        base = out["W"][j] / (b - a)
+        # one shift per cell
+        np.testing.assert_allclose(rec["alpha"][a:b] - base, rec["dA"][j], rtol=0,
+                                   atol=1e-13 * base)
+        for i in range(C):
+            d = ((i + 0.5) * dx - rec["x"][a:b] + L / 2) % L - L / 2
+            M[i, j] = q * np.nan_to_num(S(d / dx)).sum()
+        # partition of unity: a column sums to q N'_j
+        assert M[:, j].sum() == pytest.approx(q * (b - a), rel=1e-13)
+    n_out = np.diff(wl.cell_off)
+    rho_raw = M @ (out["W"] / n_out) / dx
+    rhs = dx * (out["rho_target"] - rho_raw)
+    res = M @ rec["dA"] - rhs
+    assert np.abs(res).max() <= 1e-12 * dx * np.abs(out["rho_target"]).max()
+    assert np.abs(rhs).max() > 1e-6 * dx * np.abs(out["rho_target"]).max()  # not trivial
+
+
 def test_projection_is_one_scalar_affine_map_per_cell():
     # Sec. 2.4.2, eqs. (alpha), (beta): a projected cell's velocities are
     # v' = a (v + beta) with ONE scalar a > 0 for all D axes and a vector
