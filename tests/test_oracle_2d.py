@@ -92,6 +92,40 @@ def test_reconstruction_matches_charge_momentum_and_energy():
     assert np.all(np.floor(r["y"] / dy) == cell // Cx)
 
 
+@pytest.mark.parametrize("order", [1, 2])
+def test_gauss_correction_is_the_9_point_mass_matrix_equation(order):
+    """Sec. 2.4.1 on the 2D mesh: every resampled particle of cell j gets the
+    same dA_j, and dA solves M dA = dx dy (rho' - rho) with the 9-point
+    M_ij = q sum_{p in j} S(x_i - x_p) S(y_i - y_p), built here from scipy's
+    B-spline basis; its column sums are q N'_j."""
+    wl = workloads.with_weights(workloads.weibel_2d3v(Cx=5, Cy=4, ppc=60, shape_order=order, seed=64))
+    p = dict(wl.params, q=-1.2)
+    fit = _fit(wl)
+    rho_t = deposit_ref(p, wl.cell_off, wl.x, wl.y, wl.alpha)
+    out_off = workloads.resample_offsets(wl.cell_off)
+    r = oracle.reconstruct2d(p, fit["K"], fit["params"], fit["W"], rho_t, out_off, nthreads=4)
+    Cx, Cy = p["Cx"], p["Cy"]
+    dx, dy = p["Lx"] / Cx, p["Ly"] / Cy
+    C = Cx * Cy
+    M = np.zeros((C, C))
+    for j in range(C):
+        a, b = out_off[j], out_off[j + 1]
+        base = fit["W"][j] / (b - a)
+        np.testing.assert_allclose(r["alpha"][a:b] - base, r["dA"][j], rtol=0, atol=1e-13 * base)
+        for i in range(C):
+            ix, iy = i % Cx, i // Cx
+            ddx = ((ix + 0.5) * dx - r["x"][a:b] + p["Lx"] / 2) % p["Lx"] - p["Lx"] / 2
+            ddy = ((iy + 0.5) * dy - r["y"][a:b] + p["Ly"] / 2) % p["Ly"] - p["Ly"] / 2
+            M[i, j] = p["q"] * (shape(order, ddx / dx) * shape(order, ddy / dy)).sum()
+        assert M[:, j].sum() == pytest.approx(p["q"] * (b - a), rel=1e-13)
+    raw = np.repeat(fit["W"] / np.diff(out_off), np.diff(out_off))
+    rho_raw = deposit_ref(p, out_off, r["x"], r["y"], raw)
+    rhs = dx * dy * (rho_t - rho_raw)
+    res = M @ r["dA"] - rhs
+    assert np.abs(res).max() <= 1e-12 * dx * dy * np.abs(rho_t).max()
+    assert np.abs(rhs).max() > 1e-6 * dx * dy * np.abs(rho_t).max()
+
+
 def test_one_row_mesh_is_the_1d_oracle():
     """Cy = 1: every particle's y weights wrap onto the one row and sum to
     one, so M and the right-hand side are the 1D ones: dA equals the 1D
