@@ -103,6 +103,39 @@ def test_two_steps_recomputed_with_scipy(D):
     assert r["lnL"] == pytest.approx(lnL, rel=1e-11)
 
 
+@pytest.mark.parametrize("D", [1, 3])
+def test_standard_two_iterations_recomputed_with_scipy(D):
+    """The plain standard EM of Sec. 4 (no penalty, no annihilation): with
+    max_sweeps = 2 from a supplied mixture, the trace holds the unpenalised
+    eq. (lnL-GM) at the start and after one EM step (eqs. responsibility,
+    muk, sigmak, omegak-mle), and the output is one more EM step; all
+    recomputed here with scipy densities.  A light far component stays."""
+    rng = np.random.default_rng(50 + D)
+    N = 300
+    vv = np.concatenate([rng.normal(-1.0, 0.4, (N // 2, D)), rng.normal(1.0, 0.6, (N - N // 2, D))])
+    alpha = rng.uniform(0.5, 1.5, N)
+    ah = alpha * N / alpha.sum()
+    I = np.eye(D)
+    init = [(0.45, -0.8 * np.ones(D), 0.3 * I), (0.45, 0.9 * np.ones(D), 0.5 * I),
+            (0.10, 1.5 * np.ones(D), 0.2 * I)]
+    prm0 = np.stack([_pack(D, *c) for c in init])
+    p = dict(D=D, Kmax=4, shape_order=2, tol=0.0, max_sweeps=2, seed=1, L=1.0, q=1.0)
+    r = oracle.std_cell(p, vv, alpha, init=2, init_params=prm0, trace_cap=4)
+    _, L0 = _resp(D, init, vv, ah)
+    th1 = _final_step(D, init, vv, ah)
+    _, L1 = _resp(D, th1, vv, ah)
+    out = _final_step(D, th1, vv, ah)
+    assert r["K"] == 3 and r["iters"] == 2
+    np.testing.assert_allclose(r["Ltrace"], [L0, L1], rtol=1e-11)
+    for k in range(3):
+        w, mu, S = _unpack(D, r["params"][k])
+        np.testing.assert_allclose(w, out[k][0], rtol=1e-11)
+        np.testing.assert_allclose(mu, out[k][1], rtol=1e-10, atol=1e-12)
+        np.testing.assert_allclose(S, out[k][2], rtol=1e-10, atol=1e-12)
+    _, lnL = _resp(D, out, vv, ah)
+    assert r["lnL"] == pytest.approx(lnL, rel=1e-11)
+
+
 def test_penalised_objective_never_decreases_without_annihilation():
     """Two well-separated beams fitted with Kmax = 2: no component is ever
     annihilated (every N_k >> T/2), so K is constant and the penalised L,
