@@ -52,6 +52,49 @@ def test_uniform52_range_and_resolution():
     assert oracle.uniform52(7, 0xFFF) == oracle.uniform52(7, 0)
 
 
+def _curand():
+    import ctypes as ct
+    import ctypes.util
+    cands = [ctypes.util.find_library("curand")]
+    for root in (os.environ.get("CUDA_HOME"), "/usr/local/cuda"):
+        if root:
+            cands += [os.path.join(root, "lib64", "libcurand.so"),
+                      os.path.join(root, "lib", "libcurand.so")]
+    for c in cands:
+        if not c:
+            continue
+        try:
+            return ct.CDLL(c)
+        except OSError:
+            continue
+    return None
+
+
+def test_philox_matches_curand_host_generator():
+    # The oracle's Philox4x32-10 (Salmon et al., SC'11) against cuRAND's host
+    # generator of the same name, called through its public API on the CPU:
+    # with a 64-bit seed its output block t (4 words) is the bijection at
+    # counter (0, 0, t, 0) under the key (low, high) words of the seed.
+    import ctypes as ct
+    lib = _curand()
+    if lib is None:
+        pytest.skip("libcurand not found")
+    philox_rng = 161  # CURAND_RNG_PSEUDO_PHILOX4_32_10
+    nb = 4096
+    for seed in (0x0123456789ABCDEF, 1, 20071227, 0xFFFFFFFF00000001):
+        gen = ct.c_void_p()
+        assert lib.curandCreateGeneratorHost(ct.byref(gen), philox_rng) == 0
+        try:
+            assert lib.curandSetPseudoRandomGeneratorSeed(gen, ct.c_ulonglong(seed)) == 0
+            buf = np.zeros(4 * nb, dtype=np.uint32)
+            assert lib.curandGenerate(gen, buf.ctypes.data_as(ct.c_void_p), ct.c_size_t(buf.size)) == 0
+        finally:
+            lib.curandDestroyGenerator(gen)
+        key = (seed & 0xFFFFFFFF, seed >> 32)
+        for t, block in enumerate(buf.reshape(nb, 4)):
+            np.testing.assert_array_equal(oracle.philox((0, 0, t, 0), key), block)
+
+
 def test_philox_statistics():
     key = np.array([0x12345678, 0x9ABCDEF0], np.uint32)
     words = np.array([oracle.philox([i, 3, 5, 0], key) for i in range(20000)])
