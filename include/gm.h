@@ -61,7 +61,7 @@ typedef struct gm_config {
   double tol;          /* EM stops when |L - L_prev| <= tol |L_prev| (e.g. 1e-6) */
   uint64_t seed;       /* Philox key: initial picks (compress) / sampler (reconstruct) */
   double L;            /* periodic domain length; dx = L / C */
-  double q;            /* species charge q_p */
+  double q;            /* species charge q_p; nonzero for the reconstructions (GM_ERR_ARG) */
   int32_t threads_per_cell; /* EM CTA size: 0 = library choice, else 64, 128 or 256 */
   int32_t smem_particles;   /* EM shared-memory tile in particles: 0 = library choice;
                                cells with more particles use an L2-resident global tile */

@@ -429,6 +429,7 @@ int gm_reconstruct(const gm_config* cfg, int64_t C, const int32_t* K, const doub
   g_err.clear();
   int rc = check_cfg(cfg);
   if (rc) return rc;
+  if (!(cfg->q != 0.0)) return fail(GM_ERR_ARG, "q must be nonzero (the mass matrix is q times the shape sums)");
   if (C < 0) return fail(GM_ERR_ARG, "C < 0");
   if (n_out < 0 || n_out >= (int64_t)1 << 40) return fail(GM_ERR_ARG, "n_out out of range");
   if (C == 0) return GM_OK;

@@ -64,6 +64,7 @@ int gm_reconstruct_noalloc(const gm_config* cfg, int64_t C, const int32_t* K, co
   if (cfg->shape_order != 1 && cfg->shape_order != 2)
     return fail2(GM_ERR_ARG, "shape_order must be 1 or 2");
   if (!(cfg->L > 0.0)) return fail2(GM_ERR_ARG, "L must be positive");
+  if (!(cfg->q != 0.0)) return fail2(GM_ERR_ARG, "q must be nonzero (the mass matrix is q times the shape sums)");
   if (C < 0 || n_out < 0) return fail2(GM_ERR_ARG, "negative size");
   if (C > kMaxCells)
     return fail2(GM_ERR_ARG, "gm_reconstruct_noalloc handles at most 32768 cells per call (got " +

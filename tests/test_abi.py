@@ -76,6 +76,13 @@ def test_argument_errors_without_gpu(lib):
     cfg = gm.config(dict(D=1, Kmax=4, shape_order=2, L=1.0), smem_particles=1 << 20)
     assert lib.gm_compress(ct.byref(cfg), *args) == -1
     assert b"smem_particles" in lib.gm_last_error()
+    # a zero charge makes the mass matrix zero: refused by both reconstructions
+    cfg = gm.config(dict(D=1, Kmax=4, shape_order=2, L=1.0, q=0.0))
+    rargs = (1, ptr, ptr, ptr, ptr, 1, ptr, ptr, ptr, ptr, ptr, None, None)
+    assert lib.gm_reconstruct(ct.byref(cfg), *rargs) == -1
+    assert b"q must be nonzero" in lib.gm_last_error()
+    assert lib.gm_reconstruct_noalloc(ct.byref(cfg), *rargs) == -1
+    assert b"q must be nonzero" in lib.gm_last_error()
     # empty problems are valid no-ops
     cfg = gm.config(dict(D=1, Kmax=4, shape_order=2, L=1.0))
     assert lib.gm_mixture_moments(ct.byref(cfg), 0, None, None, None, None, None, None, None,
