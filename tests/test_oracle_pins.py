@@ -334,6 +334,27 @@ def test_single_3v_maxwellian_collapses_to_one_component():
     assert kbar[1] >= kbar[0]
 
 
+def test_stopping_rule_is_the_first_quiet_sweep():
+    # Sec. 2.3 step 4 with readings 2 and 5: after each sweep, stop when the
+    # relative change of the penalised L is within tol AND the sweep removed
+    # no component; the trace (L and K after initialisation and after each
+    # sweep, K negative for a removing sweep) must stop at the first such
+    # sweep, K must never grow, and K0 = Kmax for these cells (N >> Kmax).
+    wl = workloads.with_weights(workloads.mixture_1d1v(C=10, mean_n=400, clip=(100, 800), seed=71))
+    tol = wl.params["tol"]
+    for j in range(wl.C):
+        sl = slice(wl.cell_off[j], wl.cell_off[j + 1])
+        r = oracle.em_cell(dict(wl.params), wl.v[:, sl].T, wl.alpha[sl], cell=j, trace_cap=2000)
+        L, Kt = r["Ltrace"], r["Ktrace"]
+        S = r["sweeps"]
+        assert r["status"] & oracle.ST_EM_MAXSWEEPS == 0
+        assert L.shape[0] == S + 1 and Kt[0] == wl.params["Kmax"]
+        quiet = [Kt[s] > 0 and abs(L[s] - L[s - 1]) <= tol * abs(L[s - 1]) for s in range(1, S + 1)]
+        assert quiet[-1] and not any(quiet[:-1]), j
+        assert np.all(np.diff(np.abs(Kt)) <= 0)
+        assert abs(r["K"]) == abs(Kt[-1]) or r["status"] & oracle.ST_COV_NOT_PD
+
+
 def test_L_nondecreasing_between_removals():
     # the component-wise EM is a generalised EM for eq. (lnL-GM): L does not
     # decrease over a sweep that removes nothing
