@@ -368,6 +368,25 @@ def test_L_nondecreasing_between_removals():
         assert (d >= -1e-9 * np.abs(L[1:][clean])).all()
 
 
+@pytest.mark.parametrize("D,Kmax,N,K0", [
+    # hand-computed: T = D (D + 3) / 2; K0 = the largest K <= min(Kmax, N)
+    # with N - T K / 2 > 0 (a component must be able to survive eq. omegak),
+    # at least 1
+    (1, 8, 3, 2),    # T = 2: 3 - K > 0 -> K <= 2
+    (1, 8, 8, 7),    # 8 - K > 0 -> K <= 7
+    (1, 8, 12, 8),   # Kmax binds
+    (3, 10, 4, 1),   # T = 9: 4 - 4.5 K > 0 fails for K = 1: floor of 1
+    (3, 10, 9, 1),   # 9 - 4.5 K > 0 -> K < 2 (a tie removes)
+    (3, 10, 10, 2),  # K < 2.22
+    (3, 10, 14, 3),  # K < 3.11
+])
+def test_initial_component_count_for_small_cells(D, Kmax, N, K0):
+    rng = np.random.default_rng(N + 10 * D)
+    vv = rng.standard_normal((N, D))
+    r = oracle.em_cell(_params(D, Kmax), vv, np.ones(N), trace_cap=8)
+    assert r["Ktrace"][0] == K0
+
+
 def test_degenerate_cell():
     vv = np.full((20, 1), 0.25)
     r = oracle.em_cell(_params(1, 4), vv, np.ones(20))
