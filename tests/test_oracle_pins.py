@@ -387,6 +387,31 @@ def test_initial_component_count_for_small_cells(D, Kmax, N, K0):
     assert r["Ktrace"][0] == K0
 
 
+def test_collapsed_component_is_removed_at_the_covariance_floor():
+    # Reading 11: no regularisation; a component whose covariance fails the
+    # Cholesky floor in a sweep is removed and COV_NOT_PD is set.  30
+    # particles share one velocity far from a normal bulk; a supplied
+    # component sitting on them (covariance 1e-4 I) gets responsibility
+    # exactly 0 from the bulk, so its M-step covariance is exactly 0.
+    D = 3
+    rng = np.random.default_rng(81)
+    vv = np.concatenate([rng.standard_normal((200, D)), np.tile([0.0, 0.0, 5.0], (30, 1))])
+    al = np.ones(vv.shape[0])
+    iu = np.triu_indices(D)
+    init = np.stack([np.concatenate([[0.87], np.zeros(D), np.eye(D)[iu]]),
+                     np.concatenate([[0.13], [0.0, 0.0, 5.0], 1e-4 * np.eye(D)[iu]])])
+    p = _params(D, 4)
+    r1 = oracle.em_cell(p, vv, al, init_params=init, only_sweeps=1, trace_cap=8)
+    assert r1["K"] == 1 and r1["status"] & oracle.ST_COV_NOT_PD
+    assert list(r1["Ktrace"]) == [2, -1]
+    r = oracle.em_cell(p, vv, al, init_params=init)
+    assert r["K"] == 1 and r["status"] & oracle.ST_COV_NOT_PD
+    w, mu, S = r["params"][0][0], r["params"][0][1:1 + D], r["params"][0][1 + D:]
+    assert w == pytest.approx(1.0, rel=1e-14)
+    np.testing.assert_allclose(mu, vv.mean(0), rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(S, np.cov(vv.T, bias=True)[iu], rtol=1e-11, atol=1e-14)
+
+
 def test_degenerate_cell():
     vv = np.full((20, 1), 0.25)
     r = oracle.em_cell(_params(1, 4), vv, np.ones(20))
