@@ -410,6 +410,13 @@ def test_collapsed_component_is_removed_at_the_covariance_floor():
     assert w == pytest.approx(1.0, rel=1e-14)
     np.testing.assert_allclose(mu, vv.mean(0), rtol=1e-12, atol=1e-14)
     np.testing.assert_allclose(S, np.cov(vv.T, bias=True)[iu], rtol=1e-11, atol=1e-14)
+    # the standard EM of Sec. 4 and its simultaneous penalised variant drop
+    # the component the same way
+    for penalised in (False, True):
+        rs = oracle.std_cell(dict(p, max_sweeps=50), vv, al, init=2, init_params=init,
+                             penalised=penalised)
+        assert rs["K"] == 1 and rs["status"] & oracle.ST_COV_NOT_PD, penalised
+        np.testing.assert_allclose(rs["params"][0][1:1 + D], vv.mean(0), rtol=1e-12, atol=1e-14)
 
 
 def test_degenerate_cell():
