@@ -158,6 +158,55 @@ def test_deposit_single_particle_by_hand(order, xi, expect):
     assert np.abs(rho[2:4]).max() < 1e-15
 
 
+@pytest.mark.parametrize("D", [1, 3])
+def test_moments_of_particles_and_of_mixtures_match_numpy(D):
+    # the moments the conservation checks compare (Sec. 2.3.1, 2.4.2):
+    # W = sum alpha, p = sum alpha v, M2 = sum alpha v v^T (upper triangle,
+    # row-major), E = sum alpha |v|^2 / 2; of a mixture with total weight W:
+    # p = W sum w_k mu_k, M2 = W sum w_k (Sigma_k + mu_k mu_k^T), E = tr M2 / 2
+    rng = np.random.default_rng(90 + D)
+    counts = np.array([0, 1, 17, 250, 40])
+    C = counts.shape[0]
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    n = int(off[-1])
+    v = rng.standard_normal((D, n)) * 0.3 + 0.1
+    a = rng.uniform(0.5, 1.5, n)
+    x = (np.repeat(np.arange(C), counts) + rng.random(n)) * 1.0
+    p = workloads.method_params(D, 3, 2, float(C))
+    m = oracle.moments(p, off, x, v, a)
+    iu = np.triu_indices(D)
+    for j in range(C):
+        sl = slice(off[j], off[j + 1])
+        vj, aj = v[:, sl], a[sl]
+        assert m["W"][j] == pytest.approx(aj.sum(), rel=1e-14, abs=1e-300)
+        np.testing.assert_allclose(m["p"][j], (aj * vj).sum(1), rtol=1e-13, atol=1e-15)
+        np.testing.assert_allclose(m["M2"][j], ((aj * vj) @ vj.T)[iu], rtol=1e-13, atol=1e-15)
+        assert m["E"][j] == pytest.approx(0.5 * (aj * vj ** 2).sum(), rel=1e-13, abs=1e-300)
+    # mixtures
+    K = np.array([0, 1, 2, 3, 3], dtype=np.int32)
+    prm = np.zeros((C, 3, 1 + D + len(iu[0])))
+    W = rng.uniform(1.0, 5.0, C)
+    comps = {}
+    for j in range(C):
+        w = rng.dirichlet(np.ones(K[j])) if K[j] else np.zeros(0)
+        for k in range(K[j]):
+            mu = rng.standard_normal(D)
+            A = rng.standard_normal((D, D))
+            S = A @ A.T + 0.1 * np.eye(D)
+            prm[j, k] = np.concatenate([[w[k]], mu, S[iu]])
+            comps.setdefault(j, []).append((w[k], mu, S))
+    mm = oracle.mixture_moments(p, K, prm, W)
+    for j in range(C):
+        if not K[j]:
+            continue
+        pe = W[j] * sum(w * mu for w, mu, _ in comps[j])
+        M2 = W[j] * sum(w * (S + np.outer(mu, mu)) for w, mu, S in comps[j])
+        assert mm["W"][j] == pytest.approx(W[j], rel=1e-15)
+        np.testing.assert_allclose(mm["p"][j], pe, rtol=1e-13, atol=1e-15)
+        np.testing.assert_allclose(mm["M2"][j], M2[iu], rtol=1e-13, atol=1e-15)
+        assert mm["E"][j] == pytest.approx(0.5 * np.trace(M2), rel=1e-13)
+
+
 def test_deposit_conserves_total_charge():
     wl = workloads.with_weights(workloads.mixture_1d1v(C=16, mean_n=50, clip=(5, 100)))
     m = oracle.moments(wl.params, wl.cell_off, wl.x, wl.v, wl.alpha)
