@@ -207,6 +207,30 @@ def test_moments_of_particles_and_of_mixtures_match_numpy(D):
         assert mm["E"][j] == pytest.approx(0.5 * np.trace(M2), rel=1e-13)
 
 
+@pytest.mark.parametrize("D,K", [(1, 1), (1, 4), (3, 2), (3, 5)])
+def test_penalised_L_against_scipy(D, K):
+    # eq. (lnL-GM): sum_p ah_p ln sum_k w_k f_k(v_p) - (d/2) ln N
+    # - (T/2) sum_k ln w_k with T = D (D + 3) / 2, d = K (T + 1) - 1, the
+    # densities from scipy
+    rng = np.random.default_rng(7 * D + K)
+    N = 120
+    vv = rng.standard_normal((N, D))
+    ah = rng.uniform(0.5, 1.5, N)
+    ah *= N / ah.sum()
+    iu = np.triu_indices(D)
+    w = rng.dirichlet(np.ones(K))
+    rows, dens = [], np.zeros(N)
+    for k in range(K):
+        mu = rng.standard_normal(D) * 0.5
+        A = rng.standard_normal((D, D))
+        S = A @ A.T + 0.3 * np.eye(D)
+        rows.append(np.concatenate([[w[k]], mu, S[iu]]))
+        dens += w[k] * stats.multivariate_normal(mean=mu, cov=S).pdf(vv).reshape(-1)
+    T = D * (D + 3) / 2
+    ref = np.sum(ah * np.log(dens)) - (K * (T + 1) - 1) / 2 * math.log(N) - T / 2 * np.log(w).sum()
+    assert oracle.penalised_L(D, np.stack(rows), vv, ah) == pytest.approx(ref, rel=1e-12)
+
+
 def test_deposit_conserves_total_charge():
     wl = workloads.with_weights(workloads.mixture_1d1v(C=16, mean_n=50, clip=(5, 100)))
     m = oracle.moments(wl.params, wl.cell_off, wl.x, wl.v, wl.alpha)
