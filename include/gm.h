@@ -305,31 +305,41 @@ typedef struct gm_mlp {
   float* vb[4];
 } gm_mlp;
 
-/* Features (see above) of every cell; wstat [C][2D] gets mean and sd. */
+/* Features (see above) of every cell (learned initialisation, not in the
+ * paper); wstat [C][2D] gets mean and sd.  Device arrays as gm_compress;
+ * feat BF16 [C][F] and wstat caller-owned.  GM_ERR_ARG for a bad cfg,
+ * negative sizes or a NULL required pointer. */
 int gm_features(const gm_config* cfg, int64_t C, int64_t n_particles, const int64_t* cell_off,
                 const void* v, int32_t v_is_f64, const double* alpha, void* feat, double* wstat,
                 void* stream);
 
-/* Training targets from fits (K, params: gm_compress outputs) and the
+/* Training targets (learned initialisation, not in the paper) from the
+ * paper's fits (K, params: gm_compress outputs, Sec. 2.2-2.3) and the
  * cells' wstat: components sorted by whitened mu_0; slot s < K gets
  * presence 1 and [ln w, mu, ln diag L, L10, L20, L21] of the whitened
- * component, slots s >= K presence 0.  T, Mk: FP32 [C][O]; Mk marks the
- * entries that enter the loss. */
+ * component, slots s >= K presence 0.  T, Mk: FP32 [C][O], caller-owned;
+ * Mk marks the entries that enter the loss.  GM_ERR_ARG for a bad cfg,
+ * O < Kmax SP or a NULL pointer. */
 int gm_mlp_targets(const gm_config* cfg, int64_t C, const int32_t* K, const double* params,
                    const double* wstat, int32_t O, float* T, float* Mk, void* stream);
 
 /* BF16 copies and transposes of the FP32 master weights (after the caller
- * sets or loads W). */
+ * sets or loads W).  Not in the paper.  GM_ERR_ARG for a malformed net. */
 int gm_mlp_sync(const gm_mlp* net, void* stream);
 
 /* Device scratch that gm_mlp_forward / gm_mlp_train_step need for M rows. */
 size_t gm_mlp_scratch_bytes(const gm_mlp* net, int32_t M);
 
-/* out [M][O] = network(X [M][F] BF16).  M any. */
+/* out [M][O] = network(X [M][F] BF16), FP32 (learned initialisation, not
+ * in the paper).  M any; scratch of at least gm_mlp_scratch_bytes(net, M)
+ * bytes, caller-owned.  GM_ERR_ARG for a malformed net, M < 0, a NULL
+ * pointer or short scratch; *err (device, may be NULL) as gm_gemm_bf16. */
 int gm_mlp_forward(const gm_mlp* net, int32_t M, const void* X, void* scratch,
                    size_t scratch_bytes, float* out, uint32_t* err, void* stream);
 
-/* One training step on a batch of M rows (M a multiple of 64): forward,
+/* One training step (learned initialisation, not in the paper) on a batch
+ * of M rows (M a multiple of 64, else GM_ERR_ARG; so are NULL pointers,
+ * short scratch and step < 1 with lr > 0): forward,
  * loss (mean over rows: sum over slots of softplus(p) - t p on presence
  * logits plus squared errors on the entries Mk marks) added to *loss
  * (device FP64), backward into net->gW / net->gb, and, if lr > 0, an Adam
@@ -346,7 +356,11 @@ int gm_mlp_train_step(const gm_mlp* net, int32_t M, const void* X, const float* 
  * which the annihilation may remove again), capped so that N - T K0 / 2 > 0
  * by dropping the smallest log weights; weights by softmax of the log
  * weights; mu = mean + sd * mu_w, Sigma = diag(sd) L L^T diag(sd) with
- * ln diag L clamped to [-10, 5].  K0 [C], init_params [C][Kmax][P]. */
+ * ln diag L clamped to [-10, 5].  K0 [C], init_params [C][Kmax][P]
+ * (caller-owned, the layout gm_compress_from takes).  Learned
+ * initialisation, not in the paper; the cap is eq. (omegak)'s survival
+ * condition (Sec. 2.2).  GM_ERR_ARG for a bad cfg, O < Kmax SP, a NULL
+ * pointer or a NaN presence_logit. */
 int gm_mlp_decode(const gm_config* cfg, int64_t C, const float* out, int32_t O,
                   const double* wstat, const int64_t* cell_off, float presence_logit, int32_t* K0,
                   double* init_params, void* stream);
@@ -485,20 +499,24 @@ int gm_autotune(gm_config* cfg, int64_t C, int64_t n_particles, const int64_t* c
  * mixtures (gm_compress_from): the trials run gm_compress_from with the
  * first cells' init_K / init_params (same layout as gm_compress_from, for
  * the whole batch), each trial the fit on the sample with cfg->tol,
- * capped at sweeps_per_trial sweeps (0 = 64).  A learned start leaves many cells with one component,
- * whose fit is the prologue's closed form, so the cost balance (and the
- * best launch shape) differs from that of the paper's random start.  Both
- * init pointers are required (GM_ERR_ARG otherwise).
+ * capped at sweeps_per_trial sweeps (0 = 64).  No counterpart in the
+ * paper.  A learned start leaves many cells with one component, whose fit
+ * is the prologue's closed form, so the cost balance (and the best launch
+ * shape) differs from that of the paper's random start.  Both init
+ * pointers are required (GM_ERR_ARG otherwise); other errors and the
+ * outputs as gm_autotune.
  */
 int gm_autotune_from(gm_config* cfg, int64_t C, int64_t n_particles, const int64_t* cell_off,
                      const double* x, const void* v, int32_t v_is_f64, const double* alpha,
                      const int32_t* init_K, const double* init_params, int32_t sweeps_per_trial,
                      float* timings_ms, void* stream);
 
-/* Description of the last error on this host thread ("" if none). */
+/* Description of the last error on this host thread ("" if none); library
+ * bookkeeping with no counterpart in the paper. */
 const char* gm_last_error(void);
 
-/* Frees the internal workspace.  The library stays usable. */
+/* Frees the internal workspace (no counterpart in the paper).  The library
+ * stays usable; returns GM_OK. */
 int gm_shutdown(void);
 
 #ifdef __cplusplus
