@@ -128,6 +128,9 @@ int gm_compress(const gm_config* cfg, int64_t C, int64_t n_particles, const int6
  * Out: x_out [n_out] f64; v_out [D][n_out] f64; alpha_out [n_out] f64;
  *      status_out [C] uint32; dA_out [C] f64 (may be NULL).
  * Box-Muller normals are FP32; everything else is FP64.
+ * Errors: GM_ERR_ARG (bad cfg, q = 0, negative sizes, NULL required
+ * pointers), GM_ERR_UNSUPPORTED (no sm_103 device), GM_ERR_NOMEM
+ * (workspace), GM_ERR_CUDA (launch); per-cell outcomes in status bits.
  */
 int gm_reconstruct(const gm_config* cfg, int64_t C, const int32_t* K, const double* params,
                    const double* W, const double* rho_target, int64_t n_out,
@@ -153,7 +156,9 @@ typedef struct gm_mesh2d {
  * In: cell_off [Cx Cy + 1] int64; x, y [n] f64 (each particle inside its
  * cell); alpha [n] f64 or NULL (unit weights).  Out: rho_out [Cy][Cx] f64
  * (node jy * Cx + jx).  This is the target rho' of the 2D reconstruction
- * when called on the particles before compression.
+ * when called on the particles before compression.  Errors: GM_ERR_ARG (bad
+ * cfg or mesh, NULL required pointers), GM_ERR_UNSUPPORTED, GM_ERR_NOMEM,
+ * GM_ERR_CUDA.
  */
 int gm_deposit_2d(const gm_config* cfg, const gm_mesh2d* mesh, const int64_t* cell_off,
                   const double* x, const double* y, const double* alpha, double* rho_out,
@@ -178,7 +183,8 @@ int gm_deposit_2d(const gm_config* cfg, const gm_mesh2d* mesh, const int64_t* ce
  * In: as gm_reconstruct with rho_target [Cy][Cx] and out_off [Cx Cy + 1]
  * (cfg->q must be nonzero).  Out: x_out, y_out [n_out] f64, v_out
  * [D][n_out] f64, alpha_out [n_out] f64, status_out [Cx Cy] uint32, dA_out
- * [Cx Cy] f64 (may be NULL).
+ * [Cx Cy] f64 (may be NULL).  Errors as gm_reconstruct (and a bad mesh);
+ * a solve that stops at its iteration cap sets GM_ST_MM_NOT_CONVERGED.
  */
 int gm_reconstruct_2d(const gm_config* cfg, const gm_mesh2d* mesh, const int32_t* K,
                       const double* params, const double* W, const double* rho_target,
@@ -191,7 +197,9 @@ int gm_reconstruct_2d(const gm_config* cfg, const gm_mesh2d* mesh, const int32_t
  * 2.4.2): W = sum alpha, p = sum alpha v [C][D], M2 = sum alpha v v^T upper
  * triangle row-major [C][D(D+1)/2], E = (1/2) sum alpha |v|^2, and the
  * charge density rho [C] with the shape function of cfg (Sec. 2.4.1).
- * Any output pointer may be NULL.  FP64 accumulation.
+ * Any output pointer may be NULL.  FP64 accumulation.  Errors: GM_ERR_ARG
+ * (bad cfg, negative sizes, NULL inputs), GM_ERR_UNSUPPORTED, GM_ERR_NOMEM,
+ * GM_ERR_CUDA; C = 0 is a no-op.
  */
 int gm_moments(const gm_config* cfg, int64_t C, int64_t n_particles, const int64_t* cell_off,
                const double* x, const void* v, int32_t v_is_f64, const double* alpha, double* W,
@@ -201,6 +209,8 @@ int gm_moments(const gm_config* cfg, int64_t C, int64_t n_particles, const int64
  * gm_mixture_moments -- the same moments of each cell's mixture (W given):
  * p = W sum_k w_k mu_k, M2 = W sum_k w_k (Sigma_k + mu_k mu_k^T),
  * E = tr(M2)/2 (eq. equal-mean and the variance identity of Sec. 2.3.1).
+ * In: K [C] int32, params [C][Kmax][P] f64, Wc [C] f64; out as
+ * gm_moments.  Errors as gm_moments; C = 0 is a no-op.
  */
 int gm_mixture_moments(const gm_config* cfg, int64_t C, const int32_t* K, const double* params,
                        const double* Wc, double* W, double* p, double* M2, double* E,
@@ -245,7 +255,9 @@ int gm_reconstruct_noalloc(const gm_config* cfg, int64_t C, const int32_t* K, co
  * (multiples of 8, >= K), 16-byte aligned; bias: FP32 [N] or NULL; mask:
  * BF16 [M][ldm] or NULL; outputs C_f32 (FP32) and/or C_bf16 (BF16), row
  * stride ldc.  err (device, may be NULL) gets bit 0 set if a tensor-core
- * completion wait timed out (results then undefined).
+ * completion wait timed out (results then undefined).  Errors: GM_ERR_ARG
+ * (negative sizes, NULL operands, leading dimensions or alignment as
+ * above), GM_ERR_UNSUPPORTED (no sm_103 device), GM_ERR_CUDA (launch).
  */
 int gm_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, int32_t lda, const void* B,
                  int32_t ldb, const float* bias, int32_t relu, const void* mask, int32_t ldm,
@@ -259,7 +271,8 @@ int gm_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, int32_t lda, co
  * whose covariance fails the Cholesky floor are dropped, the count is
  * capped so that N - T K / 2 > 0, and a cell left with none falls back to
  * the random initialisation.  Everything after the initialisation is the
- * paper's method, as in gm_compress.
+ * paper's method, as in gm_compress; so are the errors (and GM_ERR_ARG
+ * when init_K or init_params is NULL).
  */
 int gm_compress_from(const gm_config* cfg, int64_t C, int64_t n_particles,
                      const int64_t* cell_off, const double* x, const void* v, int32_t v_is_f64,
@@ -327,7 +340,8 @@ int gm_mlp_targets(const gm_config* cfg, int64_t C, const int32_t* K, const doub
  * sets or loads W).  Not in the paper.  GM_ERR_ARG for a malformed net. */
 int gm_mlp_sync(const gm_mlp* net, void* stream);
 
-/* Device scratch that gm_mlp_forward / gm_mlp_train_step need for M rows. */
+/* Device scratch that gm_mlp_forward / gm_mlp_train_step need for M rows
+ * (not in the paper); 0 for a NULL net or M <= 0 (no error code). */
 size_t gm_mlp_scratch_bytes(const gm_mlp* net, int32_t M);
 
 /* out [M][O] = network(X [M][F] BF16), FP32 (learned initialisation, not
@@ -410,6 +424,8 @@ int gm_mlp_decode(const gm_config* cfg, int64_t C, const float* out, int32_t O,
  * not used; cfg->smem_particles sets the shared tile); iters_out [C]: EM
  * steps evaluated; aa_steps_out, aa_resets_out: extrapolations taken and
  * history resets; km_passes_out: Lloyd passes (each of these may be NULL).
+ * Errors as gm_compress, and GM_ERR_ARG for options out of range (init not
+ * 0 or 1, aa_memory outside 0..8, Anderson with the penalised variant).
  */
 typedef struct gm_std_opts {
   int32_t init;         /* 0 = random particles (Sec. 2.3), 1 = K-means */

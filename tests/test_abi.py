@@ -153,3 +153,24 @@ def test_mesh2d_argument_errors_without_gpu(lib):
     assert lib.gm_reconstruct_2d(ct.byref(cfg0), ct.byref(mesh), None, None, None, None, 0, None,
                                  None, None, None, None, None, None, None) == -1
     assert b"q must be nonzero" in lib.gm_last_error()
+
+
+def test_every_declaration_cites_the_paper_and_its_errors():
+    """Each entry point of include/gm.h is documented (its own comment, or
+    the comment of the group it is declared in) with the passage of the
+    paper it implements or the statement that the paper has none, and with
+    its error behaviour."""
+    txt = open(HEADER).read()
+    decl = list(re.finditer(r"^(?:int|size_t|const char\*)\s+(gm_\w+)\s*\(", txt, re.M))
+    cite = re.compile(r"Sec\.|eqs?\.|not in the paper|no counterpart|not part of the paper",
+                      re.I)
+    errs = re.compile(r"GM_ERR|GM_OK|error|Returns", re.I)
+    prev_end, prev_doc = 0, ""
+    for m in decl:
+        chunk = txt[prev_end:m.start()]
+        doc = " ".join(re.findall(r"/\*.*?\*/", chunk, re.S)) or prev_doc
+        doc = re.sub(r"\s+", " ", re.sub(r"\n\s*\*(?!/)", " ", doc))  # join wrapped lines
+        assert cite.search(doc), m.group(1)
+        assert errs.search(doc), m.group(1)
+        prev_end = txt.index(";", m.end()) + 1
+        prev_doc = doc
