@@ -38,3 +38,18 @@ def test_secondary_rooflines():
     assert f64["achieved"] == pytest.approx(980 / 1e-3 / 1e12)
     assert f64["peak"] == bench.FP64_PEAK_TFLOPS
     assert f64["frac"] == pytest.approx(f64["achieved"] / f64["peak"])
+
+
+def test_oracle_sample_keeps_the_mesh_spacing():
+    # the CPU baseline times the oracle on the first cells of the workload:
+    # the sample keeps each cell's particles and the cell width dx
+    import workloads
+    wl = workloads.mixture_1d1v(C=64, mean_n=300, clip=(50, 600))
+    sw = bench.sub_workload(wl, 10)
+    n = int(wl.cell_off[10])
+    assert sw.C == 10 and sw.ntot == n
+    assert (sw.cell_off == wl.cell_off[:11]).all()
+    assert (sw.x == wl.x[:n]).all() and (sw.v == wl.v[:, :n]).all() and (sw.alpha == wl.alpha[:n]).all()
+    assert sw.params["L"] / sw.C == pytest.approx(wl.params["L"] / wl.C)
+    assert sw.v.flags.c_contiguous
+    assert bench.sub_workload(wl, 1000).C == wl.C  # capped at the workload
