@@ -28,6 +28,7 @@
 #ifndef GMCR_GM_H
 #define GMCR_GM_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus

@@ -174,3 +174,15 @@ def test_every_declaration_cites_the_paper_and_its_errors():
         assert errs.search(doc), m.group(1)
         prev_end = txt.index(";", m.end()) + 1
         prev_doc = doc
+
+
+@pytest.mark.parametrize("lang,std,comp", [("c", "c99", "gcc"), ("c++", "c++17", "g++")])
+def test_header_is_self_contained(tmp_path, lang, std, comp):
+    """include/gm.h compiles on its own (first include, no other headers)
+    as strict C99 and as C++17, warnings as errors."""
+    src = tmp_path / ("h.c" if lang == "c" else "h.cpp")
+    src.write_text('#include "gm.h"\nint main(void) { return 0; }\n')
+    r = subprocess.run([comp, f"-std={std}", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-fsyntax-only", "-I", os.path.join(ROOT, "include"), str(src)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
