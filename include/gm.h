@@ -53,6 +53,8 @@ extern "C" {
 #define GM_ST_MM_EMPTY_COL 0x400u /* no resampled particle: unit mass-matrix column */
 #define GM_ST_NO_MIXTURE 0x800u   /* K[j] = 0 but particles were requested */
 #define GM_ST_MM_NOT_CONVERGED 0x1000u /* 2D mass-matrix solve stopped at its iteration cap */
+#define GM_ST_BAD_RANGE 0x2000u   /* out_off[j] .. out_off[j+1] not inside [0, n_out): the
+                                     cell gets no particles and nothing is written for it */
 
 typedef struct gm_config {
   int32_t D;           /* velocity dimensions: 1 or 3 */
@@ -66,8 +68,13 @@ typedef struct gm_config {
   int32_t threads_per_cell; /* EM CTA size: 0 = library choice, else 64, 128 or 256 */
   int32_t smem_particles;   /* EM shared-memory tile in particles: 0 = library choice;
                                cells with more particles use an L2-resident global tile */
-  int32_t precision;        /* penalised sweeps' M-step (covariance, Cholesky factor,
-                               inverse, weight): 0 = FP32 (default), 1 = FP64.  Either
+  int32_t precision;        /* penalised sweeps' M-step: 0 (default) = FP64 -- the
+                               cross-warp statistic sums, covariance, its factor and
+                               inverse, the weight -- with the convergence test's
+                               log-likelihood corrected to first order for the
+                               rounding of the FP32 E-step constants; 1 = FP32
+                               M-step and uncorrected test (faster; its stopping
+                               sweep follows the FP64 method less closely).  Either
                                way the component means are accumulated to about 48
                                bits (FP64, or a pair of FP32 numbers) and the final
                                unpenalised step is entirely FP64.  Another value,
@@ -102,7 +109,8 @@ typedef struct gm_config {
  * E-step densities and responsibilities are FP32; the per-component
  * statistics are FP32 per thread and warp and summed across warps in the
  * M-step's precision (cfg->precision); component means are accumulated in
- * FP64; the whole final step (which makes the moments exact) is FP64.
+ * FP64; the log-likelihood of the convergence test is summed in FP64; the
+ * whole final step (which makes the moments exact) is FP64.
  */
 int gm_compress(const gm_config* cfg, int64_t C, int64_t n_particles, const int64_t* cell_off,
                 const double* x, const void* v, int32_t v_is_f64, const double* alpha,
@@ -232,14 +240,26 @@ int gm_mixture_moments(const gm_config* cfg, int64_t C, const int32_t* K, const 
  * Limits and rules:
  *  - at most 32768 cells per call (C > 32768 returns GM_ERR_ARG);
  *  - the first call on a device looks up the array's device address (once
- *    per device, with that device current); make that first call before any
- *    stream capture;
+ *    per device, with that device current).  Under CUDA's lazy module
+ *    loading that first use of the library's device module on a device is
+ *    also when the CUDA runtime loads the module and reserves the array,
+ *    which may allocate device memory and synchronise.  A call with C = 0
+ *    does only this set-up (device check, address lookup; nothing is
+ *    launched): make such a call, or the first real call, before any
+ *    stream capture and before the point where no allocation may happen;
+ *  - out_off is read on the device: a cell whose range out_off[j] ..
+ *    out_off[j+1] does not lie inside [0, n_out) gets no particles and
+ *    GM_ST_BAD_RANGE, and nothing is written for it;
  *  - every call shares the one array: calls that overlap on the GPU (other
  *    streams, other host threads) race and must be serialised by the
  *    caller; the array keeps the last call's contents, and nothing in it has
  *    to start at zero (each call writes every entry before reading it);
  *  - no cudaMalloc, cudaFree or allocating library routine is called.
  */
+/* 1 if the scratch a call of kMaxCells = 32768 cells needs (D = 1 and
+ * D = 3) fits the 5 MiB array, else 0: a host-side self-check of the limit
+ * above, no device access. */
+int gm_noalloc_limits_ok(void);
 int gm_reconstruct_noalloc(const gm_config* cfg, int64_t C, const int32_t* K, const double* params,
                            const double* W, const double* rho_target, int64_t n_out,
                            const int64_t* out_off, double* x_out, double* v_out,

@@ -53,9 +53,10 @@ int check_device(int* sm_count) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   int major = 0, minor = 0, sms = 0;
-  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
-  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if ((e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return cuda_fail(e, "cudaDeviceGetAttribute");
   if (major != 10 || minor != 3)
     return fail(GM_ERR_UNSUPPORTED, "device %d has compute capability %d.%d; this library is built for sm_103a",
                 dev, major, minor);
@@ -113,7 +114,37 @@ int check_cfg(const gm_config* cfg) {
   return GM_OK;
 }
 
+// the argument checks of gm_reconstruct (and of gm_reconstruct_noalloc),
+// up to the device check; nothing is launched
+int check_reconstruct(const gm_config* cfg, int64_t C, const int32_t* K, const double* params,
+                      const double* W, const double* rho_target, int64_t n_out,
+                      const int64_t* out_off, const double* x_out, const double* v_out,
+                      const double* alpha_out, const uint32_t* status_out) {
+  int rc = check_cfg(cfg);
+  if (rc) return rc;
+  if (!(cfg->q != 0.0)) return fail(GM_ERR_ARG, "q must be nonzero (the mass matrix is q times the shape sums)");
+  if (C < 0) return fail(GM_ERR_ARG, "C < 0");
+  if (n_out < 0 || n_out >= (int64_t)1 << 40) return fail(GM_ERR_ARG, "n_out out of range");
+  if (C == 0) return GM_OK;
+  if (!K || !params || !W || !rho_target || !out_off || !status_out)
+    return fail(GM_ERR_ARG, "a required pointer is NULL");
+  if (n_out > 0 && (!x_out || !v_out || !alpha_out))
+    return fail(GM_ERR_ARG, "an output particle pointer is NULL");
+  return GM_OK;
+}
+
 }  // namespace
+
+int gmcr::api_check_reconstruct(const gm_config* cfg, int64_t C, const int32_t* K,
+                                const double* params, const double* W, const double* rho_target,
+                                int64_t n_out, const int64_t* out_off, const double* x_out,
+                                const double* v_out, const double* alpha_out,
+                                const uint32_t* status_out) {
+  return check_reconstruct(cfg, C, K, params, W, rho_target, n_out, out_off, x_out, v_out,
+                           alpha_out, status_out);
+}
+
+int gmcr::api_check_device() { return check_device(nullptr); }
 
 int gmcr::record_error(int code, const char* msg) {
   g_err = msg;
@@ -241,25 +272,28 @@ static int compress_impl(const gm_config* cfg, int64_t C, int64_t n_particles,
   const size_t smem = (size_t)cap * (D + 4) * sizeof(float);
   if (smem > 200 * 1024) return fail(GM_ERR_ARG, "smem_particles too large (%d)", cap);
   if (cfg->precision != 0 && cfg->precision != 1)
-    return fail(GM_ERR_ARG, "precision must be 0 (FP32 M-step) or 1 (FP64) (got %d)", cfg->precision);
-  const int fp64_mstep = cfg->precision;
+    return fail(GM_ERR_ARG, "precision must be 0 (FP64 M-step) or 1 (FP32) (got %d)", cfg->precision);
+  const int fp64_mstep = cfg->precision == 0;
   int sms = 0;
   if ((rc = check_device(&sms))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
 
   const size_t q_bytes = 256, part_bytes = align256((size_t)3 * C * sizeof(double));
+  const size_t list_bytes = init_K ? align256((size_t)C * sizeof(unsigned int)) : 0;
   const int64_t sstride = gmcr::scratch_stride(n_particles, C);
   if ((int64_t)(D + 4) * sstride >= ((int64_t)1 << 31))
     return fail(GM_ERR_ARG, "too many particles for one call (%lld)", (long long)n_particles);
   const size_t scr_bytes = align256((size_t)sstride * (D + 4) * sizeof(float));
   void* ws = nullptr;
-  if ((rc = ws_get(q_bytes + part_bytes + scr_bytes, &ws))) return rc;
+  if ((rc = ws_get(q_bytes + part_bytes + list_bytes + scr_bytes, &ws))) return rc;
   char* wb = (char*)ws;
   unsigned int* queue = (unsigned int*)wb;
+  unsigned int* list_count = queue + 1;
   double* part = (double*)(wb + q_bytes);
-  float* scratch = (float*)(wb + q_bytes + part_bytes);
+  unsigned int* list = init_K ? (unsigned int*)(wb + q_bytes + part_bytes) : nullptr;
+  float* scratch = (float*)(wb + q_bytes + part_bytes + list_bytes);
 
-  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), s);
+  cudaError_t e = cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned int), s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   gmcr::EmParams p;
   p.C = C;
@@ -279,6 +313,8 @@ static int compress_impl(const gm_config* cfg, int64_t C, int64_t n_particles,
   p.scratch = scratch;
   p.scratch_stride = sstride;
   p.queue = queue;
+  p.list = list;
+  p.list_count = list_count;
   p.Kmax = cfg->Kmax;
   p.max_sweeps = cfg->max_sweeps;
   p.cap = cap;
@@ -289,6 +325,30 @@ static int compress_impl(const gm_config* cfg, int64_t C, int64_t n_particles,
   if (per_sm < 1) return fail(GM_ERR_CUDA, "EM kernel does not fit on an SM (smem %zu)", smem);
   int64_t grid = (int64_t)per_sm * sms;
   if (grid > C) grid = C;
+  if (init_K) {
+    // supplied starts: the closed-form cells (one valid component, empty,
+    // degenerate) one warp each; the EM kernel takes the list of the rest
+    gmcr::K1Params kp;
+    kp.C = C;
+    kp.n = n_particles;
+    kp.cell_off = cell_off;
+    kp.v = v;
+    kp.alpha = alpha;
+    kp.init_K = init_K;
+    kp.init_prm = init_params;
+    kp.K_out = K_out;
+    kp.params_out = params_out;
+    kp.W_out = W_out;
+    kp.lnL_out = lnL_out;
+    kp.sweeps_out = sweeps_out;
+    kp.kwork_out = kwork_out;
+    kp.status_out = status_out;
+    kp.list = list;
+    kp.list_count = list_count;
+    kp.Kmax = cfg->Kmax;
+    e = gmcr::launch_em_k1(D, v_is_f64, kp, sms, s);
+    if (e != cudaSuccess) return cuda_fail(e, "closed-form pre-pass launch");
+  }
   e = D == 1 ? gmcr::launch_em1(p, nt, fp64_mstep, v_is_f64, smem, (int)grid, s)
              : gmcr::launch_em3(p, nt, fp64_mstep, v_is_f64, smem, (int)grid, s);
   if (e != cudaSuccess) return cuda_fail(e, "EM kernel launch");
@@ -427,16 +487,10 @@ int gm_reconstruct(const gm_config* cfg, int64_t C, const int32_t* K, const doub
                    const int64_t* out_off, double* x_out, double* v_out, double* alpha_out,
                    uint32_t* status_out, double* dA_out, void* stream) {
   g_err.clear();
-  int rc = check_cfg(cfg);
+  int rc = check_reconstruct(cfg, C, K, params, W, rho_target, n_out, out_off, x_out, v_out,
+                             alpha_out, status_out);
   if (rc) return rc;
-  if (!(cfg->q != 0.0)) return fail(GM_ERR_ARG, "q must be nonzero (the mass matrix is q times the shape sums)");
-  if (C < 0) return fail(GM_ERR_ARG, "C < 0");
-  if (n_out < 0 || n_out >= (int64_t)1 << 40) return fail(GM_ERR_ARG, "n_out out of range");
   if (C == 0) return GM_OK;
-  if (!K || !params || !W || !rho_target || !out_off || !status_out)
-    return fail(GM_ERR_ARG, "a required pointer is NULL");
-  if (n_out > 0 && (!x_out || !v_out || !alpha_out))
-    return fail(GM_ERR_ARG, "an output particle pointer is NULL");
   if ((rc = check_device(nullptr))) return rc;
   void* ws = nullptr;
   if ((rc = ws_get(gmcr::reconstruct_ws_bytes(cfg->D, C), &ws))) return rc;

@@ -4,12 +4,14 @@
 
 #include "gm_common.cuh"
 #include "em_kernel.cuh"
+#include "em_k1.cuh"
 
 namespace gmcr {
 
 // EM (compression); returns the launch error
 cudaError_t launch_em1(const EmParams& p, int nt, int fp64_mstep, int v_f64, size_t smem, int grid,
                        cudaStream_t s);
+cudaError_t launch_em_k1(int D, int v_f64, const K1Params& p, int sms, cudaStream_t s);
 cudaError_t launch_em3(const EmParams& p, int nt, int fp64_mstep, int v_f64, size_t smem, int grid,
                        cudaStream_t s);
 // CTAs of an EM kernel that fit on one SM with `smem` dynamic bytes
@@ -35,6 +37,13 @@ cudaError_t launch_aa_affine(int n, const double* A, const double* b, const doub
                              int iters, double* x_out, double* res_out, cudaStream_t s);
 // sets the calling thread's gm_last_error() text; returns code
 int record_error(int code, const char* msg);
+// the C ABI's own argument and device checks (gm_api.cu), shared by the
+// entry points defined in other translation units
+int api_check_reconstruct(const gm_config* cfg, int64_t C, const int32_t* K, const double* params,
+                          const double* W, const double* rho_target, int64_t n_out,
+                          const int64_t* out_off, const double* x_out, const double* v_out,
+                          const double* alpha_out, const uint32_t* status_out);
+int api_check_device();
 size_t reconstruct_ws_bytes(int D, int64_t C);
 cudaError_t launch_reconstruct(int D, int64_t C, int Kmax, const int32_t* K, const double* prm,
                                const double* W, const double* rho_target, int64_t n_out,

@@ -30,6 +30,7 @@ ST_NEG_WEIGHT = 0x200
 ST_MM_EMPTY_COL = 0x400
 ST_NO_MIXTURE = 0x800
 ST_MM_NOT_CONVERGED = 0x1000
+ST_BAD_RANGE = 0x2000
 TUNE_CANDIDATES = 15  # GM_TUNE_CANDIDATES
 
 EXPORTED = ("gm_compress", "gm_reconstruct", "gm_moments", "gm_mixture_moments",
@@ -38,7 +39,7 @@ EXPORTED = ("gm_compress", "gm_reconstruct", "gm_moments", "gm_mixture_moments",
             "gm_mlp_scratch_bytes", "gm_mlp_forward", "gm_mlp_train_step", "gm_mlp_decode",
             "gm_graph_begin", "gm_graph_end", "gm_graph_launch", "gm_graph_destroy", "gm_autotune",
             "gm_compress_standard", "gm_anderson_affine", "gm_deposit_2d", "gm_reconstruct_2d",
-            "gm_autotune_from")
+            "gm_autotune_from", "gm_noalloc_limits_ok")
 
 
 class GMMlp(ct.Structure):
@@ -120,12 +121,13 @@ def load(build_if_missing: bool = False):
         lib.gm_anderson_affine.argtypes = [I32, P, P, P, I32, I32, P, P, P]
         lib.gm_deposit_2d.argtypes = [P] * 8
         lib.gm_reconstruct_2d.argtypes = [P, P, P, P, P, P, I64] + [P] * 8
+        lib.gm_noalloc_limits_ok.argtypes = []
         for f in ("gm_compress", "gm_reconstruct", "gm_moments", "gm_mixture_moments", "gm_shutdown",
                   "gm_reconstruct_noalloc", "gm_gemm_bf16", "gm_compress_from", "gm_features",
                   "gm_mlp_targets", "gm_mlp_sync", "gm_mlp_forward", "gm_mlp_train_step",
                   "gm_mlp_decode", "gm_graph_begin", "gm_graph_end", "gm_graph_launch",
                   "gm_graph_destroy", "gm_autotune", "gm_compress_standard", "gm_anderson_affine",
-                  "gm_deposit_2d", "gm_reconstruct_2d", "gm_autotune_from"):
+                  "gm_deposit_2d", "gm_reconstruct_2d", "gm_autotune_from", "gm_noalloc_limits_ok"):
             getattr(lib, f).restype = ct.c_int
         lib.gm_last_error.restype = ct.c_char_p
         _lib = lib
@@ -311,15 +313,19 @@ def gm_reconstruct(cfg: GMConfig, K, params, W, rho_target, out_off, n_out: int 
 
 
 def gm_reconstruct_noalloc(cfg: GMConfig, K, params, W, rho_target, out_off, out: dict,
-                           n_out: int, stream=None) -> dict:
+                           n_out: int | None = None, stream=None) -> dict:
     """``gm_reconstruct`` without device allocation inside the library: the
     scratch is the library's fixed static array (at most 32768 cells per
     call) and every output tensor is supplied by the caller in ``out``
-    (keys x, v, alpha, status, optionally dA)."""
+    (keys x, v, alpha, status, optionally dA).  ``n_out`` = out_off[-1]
+    (read from the device if not given); a cell whose out_off range does
+    not fit n_out is skipped on the device with GM_ST_BAD_RANGE."""
     lib = load()
     C = out_off.shape[0] - 1
     _check_mixtures(cfg, C, K, params, W, rho_target)
     _check(out_off, torch.int64, "out_off")
+    if n_out is None:
+        n_out = int(out_off[-1].item()) if C > 0 else 0
     _check_recon_out(out, cfg.D, C, int(n_out))
     rc = lib.gm_reconstruct_noalloc(ct.byref(cfg), C, _ptr(K), _ptr(params), _ptr(W),
                                     _ptr(rho_target), int(n_out), _ptr(out_off), _ptr(out["x"]),
