@@ -106,7 +106,7 @@ __global__ void deposit2d_combine_kernel(int64_t Cx, int64_t Cy, const double* p
 template <int D, int NW>
 __global__ void __launch_bounds__(NW * 32) recon2d_stats_kernel(
     int64_t Cx, int64_t C, int Kmax, const int32_t* K, const double* prm, const int64_t* out_off,
-    uint64_t seed, int order, double* cstat) {
+    int64_t n_out, uint64_t seed, int order, double* cstat) {
   constexpr int NV = 9 + D + 1;
   __shared__ RecCell<D> rcs[NW];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -114,7 +114,8 @@ __global__ void __launch_bounds__(NW * 32) recon2d_stats_kernel(
   for (int64_t j = (int64_t)blockIdx.x * NW + wid; j < C; j += (int64_t)gridDim.x * NW) {
     load_cell<D>(rc, j, Kmax, K, prm, lane);
     __syncwarp();
-    const int64_t o = out_off[j], n = out_off[j + 1] - o;
+    int64_t o, n;
+    out_range(out_off, j, n_out, o, n);
     double acc[NV];
 #pragma unroll
     for (int t = 0; t < NV; ++t) acc[t] = 0.0;
@@ -156,6 +157,7 @@ struct Mesh2dSolve {
   const double* cstat;   // [C][NV]
   int nv;                // 9 + D + 1
   const int64_t* out_off;
+  int64_t n_out;
   double q;
   double* b;             // [C] right-hand side dx dy (rho' - rho)
   double* dA;            // [C]
@@ -177,7 +179,7 @@ __global__ void assemble2d_kernel(Mesh2dSolve m, const double* W, const double* 
     for (int b = -1; b <= 1; ++b)
       for (int a = -1; a <= 1; ++a) {
         const int64_t src = src_cell(ix, iy, a, b, m.Cx, m.Cy);
-        const int64_t ns = m.out_off[src + 1] - m.out_off[src];
+        const int64_t ns = out_count(m.out_off, src, m.n_out);
         if (ns > 0) s += (W[src] / (double)ns) * m.cstat[(size_t)src * m.nv + 3 * (b + 1) + (a + 1)];
       }
     const double tgt = dv * rho_target[i];
@@ -201,12 +203,12 @@ __global__ void __launch_bounds__(256) mm2d_residual_kernel(Mesh2dSolve m, int i
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t ix = i % m.Cx, iy = i / m.Cx;
     double ri = 0.0;
-    if (m.out_off[i + 1] > m.out_off[i]) {
+    if (out_count(m.out_off, i, m.n_out) > 0) {
       double s = 0.0;
       for (int b = -1; b <= 1; ++b)
         for (int a = -1; a <= 1; ++a) {
           const int64_t src = src_cell(ix, iy, a, b, m.Cx, m.Cy);
-          if (m.out_off[src + 1] > m.out_off[src])
+          if (out_count(m.out_off, src, m.n_out) > 0)
             s = fma(m.cstat[(size_t)src * m.nv + 3 * (b + 1) + (a + 1)], m.dA[src], s);
         }
       ri = m.b[i] - m.q * s;
@@ -275,7 +277,7 @@ __global__ void mm2d_ysweep_kernel(Mesh2dSolve m, int it, CircTaps ty) {
   const int64_t C = m.Cx * m.Cy;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < C;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t n = m.out_off[i + 1] - m.out_off[i];
+    const int64_t n = out_count(m.out_off, i, m.n_out);
     if (n == 0) continue;
     const int64_t ix = i % m.Cx, iy = i / m.Cx;
     m.dA[i] += circ_apply(ty, m.t + ix, m.Cy, iy, m.Cx) / (m.q * (double)n);
@@ -308,13 +310,13 @@ __global__ void mm2d_finish_kernel(Mesh2dSolve m, int max_iter, int* converged) 
         if (__longlong_as_double((long long)m.norm[k]) <= thr) conv = 1;
       *converged = conv;
     }
-    if (m.out_off[i + 1] > m.out_off[i]) continue;
+    if (out_count(m.out_off, i, m.n_out) > 0) continue;
     const int64_t ix = i % m.Cx, iy = i / m.Cx;
     double s = 0.0;
     for (int b = -1; b <= 1; ++b)
       for (int a = -1; a <= 1; ++a) {
         const int64_t src = src_cell(ix, iy, a, b, m.Cx, m.Cy);
-        if (m.out_off[src + 1] > m.out_off[src])
+        if (out_count(m.out_off, src, m.n_out) > 0)
           s = fma(m.cstat[(size_t)src * m.nv + 3 * (b + 1) + (a + 1)], m.dA[src], s);
       }
     m.dA[i] = m.b[i] - m.q * s;
@@ -336,10 +338,11 @@ __global__ void __launch_bounds__(NW * 32) recon2d_emit_kernel(
     const int64_t jx = j % Cx, jy = j / Cx;
     load_cell<D>(rc, j, Kmax, K, prm, lane);
     __syncwarp();
-    const int64_t o = out_off[j], n = out_off[j + 1] - o;
+    int64_t o, n;
+    const bool in_range = out_range(out_off, j, n_out, o, n);
     if (lane == 0)
       status_out[j] = projection_coeffs<D>(rc, n, W[j], dA[j], cstat + (size_t)j * NV + 9) |
-                      (*converged ? 0u : GM_ST_MM_NOT_CONVERGED);
+                      (*converged ? 0u : GM_ST_MM_NOT_CONVERGED) | (in_range ? 0u : GM_ST_BAD_RANGE);
     __syncwarp();
     const double aa = rc.a, an = rc.alpha_new;
     const int skip = rc.skip;
@@ -403,6 +406,7 @@ cudaError_t launch_reconstruct2d(int D, int64_t Cx, int64_t Cy, int Kmax, const 
   m.cstat = cstat;
   m.nv = NVm;
   m.out_off = out_off;
+  m.n_out = n_out;
   m.q = q;
   m.b = cstat + (size_t)NVm * C;
   m.dA = m.b + C;
@@ -422,9 +426,11 @@ cudaError_t launch_reconstruct2d(int D, int64_t Cx, int64_t Cy, int Kmax, const 
   cudaError_t err = cudaMemsetAsync(m.scale, 0, sizeof(unsigned long long), s);
   if (err != cudaSuccess) return err;
   if (D == 1)
-    recon2d_stats_kernel<1, NW><<<g, NW * 32, 0, s>>>(Cx, C, Kmax, K, prm, out_off, seed, order, cstat);
+    recon2d_stats_kernel<1, NW><<<g, NW * 32, 0, s>>>(Cx, C, Kmax, K, prm, out_off, n_out, seed, order,
+                                                      cstat);
   else
-    recon2d_stats_kernel<3, NW><<<g, NW * 32, 0, s>>>(Cx, C, Kmax, K, prm, out_off, seed, order, cstat);
+    recon2d_stats_kernel<3, NW><<<g, NW * 32, 0, s>>>(Cx, C, Kmax, K, prm, out_off, n_out, seed, order,
+                                                      cstat);
   const int ga = grid_cap(C > kMesh2dMaxIter + 1 ? C : kMesh2dMaxIter + 1, 256, 2048);
   assemble2d_kernel<<<ga, 256, 0, s>>>(m, W, rho_target, dx * dy, kMesh2dMaxIter);
   // norm[i] for i < C is cleared by the grid-stride loop above; meshes with

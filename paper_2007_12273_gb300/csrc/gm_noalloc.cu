@@ -5,10 +5,15 @@
 // For callers that cannot allocate device memory while they run: a host
 // code whose device memory is owned by its own allocator or by a fixed
 // budget, or one that must not pay the device-wide synchronisation of
-// cudaFree/cudaMalloc (gm_reconstruct grows its workspace that way).  This
-// entry point performs no allocation at all; the array below is created
-// when the library is loaded and lives on every GPU that loads the library
-// until the process exits.
+// cudaFree/cudaMalloc (gm_reconstruct grows its workspace that way).  The
+// library itself calls no allocating routine here.  The array below is part
+// of the library's device module: under CUDA's lazy module loading the
+// runtime loads that module, and with it reserves the array, on the first
+// use of the module on each device -- the first address lookup or launch --
+// and that step may allocate device memory and synchronise.  A call with
+// C = 0 performs exactly that step (the device check and the address
+// lookup) and launches nothing, so a caller can do it ahead of time.  The
+// array then lives on that GPU until the process exits.
 #include <mutex>
 #include <string>
 
@@ -58,33 +63,18 @@ int gm_reconstruct_noalloc(const gm_config* cfg, int64_t C, const int32_t* K, co
                            double* alpha_out, uint32_t* status_out, double* dA_out,
                            void* stream) {
   gmcr::record_error(GM_OK, "");
-  if (!cfg) return fail2(GM_ERR_ARG, "cfg is NULL");
-  if (cfg->D != 1 && cfg->D != 3) return fail2(GM_ERR_ARG, "D must be 1 or 3");
-  if (cfg->Kmax < 1 || cfg->Kmax > gmcr::kMaxK) return fail2(GM_ERR_ARG, "Kmax must be in 1..16");
-  if (cfg->shape_order != 1 && cfg->shape_order != 2)
-    return fail2(GM_ERR_ARG, "shape_order must be 1 or 2");
-  if (!(cfg->L > 0.0)) return fail2(GM_ERR_ARG, "L must be positive");
-  if (!(cfg->q != 0.0)) return fail2(GM_ERR_ARG, "q must be nonzero (the mass matrix is q times the shape sums)");
-  if (C < 0 || n_out < 0) return fail2(GM_ERR_ARG, "negative size");
+  int rc = gmcr::api_check_reconstruct(cfg, C, K, params, W, rho_target, n_out, out_off, x_out,
+                                       v_out, alpha_out, status_out);
+  if (rc) return rc;
   if (C > kMaxCells)
     return fail2(GM_ERR_ARG, "gm_reconstruct_noalloc handles at most 32768 cells per call (got " +
                                  std::to_string((long long)C) + "); use gm_reconstruct");
   if (gmcr::reconstruct_ws_bytes(cfg->D, C) > kScratchBytes)
     return fail2(GM_ERR_ARG, "scratch of gm_reconstruct_noalloc too small for this call");
-  if (C == 0) return GM_OK;
-  if (!K || !params || !W || !rho_target || !out_off || !status_out)
-    return fail2(GM_ERR_ARG, "a required pointer is NULL");
-  if (n_out > 0 && (!x_out || !v_out || !alpha_out))
-    return fail2(GM_ERR_ARG, "an output particle pointer is NULL");
-  int dev = 0, major = 0, minor = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
-  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
-  if (major != 10 || minor != 3)
-    return fail2(GM_ERR_UNSUPPORTED, "this library is built for sm_103a");
+  if ((rc = gmcr::api_check_device())) return rc;
   void* ws = nullptr;
-  int rc = scratch_address(&ws);
-  if (rc) return rc;
+  if ((rc = scratch_address(&ws))) return rc;  // also the whole of a C = 0 call
+  if (C == 0) return GM_OK;
   // every scratch entry a call reads is written earlier in the same call,
   // so nothing has to be cleared between calls
   cudaError_t e = gmcr::launch_reconstruct(cfg->D, C, cfg->Kmax, K, params, W, rho_target, n_out,
@@ -93,6 +83,12 @@ int gm_reconstruct_noalloc(const gm_config* cfg, int64_t C, const int32_t* K, co
                                            dA_out, ws, (cudaStream_t)stream);
   if (e != cudaSuccess) return fail2(GM_ERR_CUDA, std::string("reconstruct launch: ") + cudaGetErrorString(e));
   return GM_OK;
+}
+
+// the largest scratch a call may need (D = 3, kMaxCells cells) fits the array
+int gm_noalloc_limits_ok() {
+  return gmcr::reconstruct_ws_bytes(1, kMaxCells) <= kScratchBytes &&
+         gmcr::reconstruct_ws_bytes(3, kMaxCells) <= kScratchBytes;
 }
 
 }  // extern "C"

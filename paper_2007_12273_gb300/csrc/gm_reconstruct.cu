@@ -29,8 +29,8 @@ namespace gmcr {
 template <int D, int NW>
 __global__ void __launch_bounds__(NW * 32) recon_stats_kernel(int64_t C, int Kmax, const int32_t* K,
                                                               const double* prm,
-                                                              const int64_t* out_off, uint64_t seed,
-                                                              int order, double* cstat) {
+                                                              const int64_t* out_off, int64_t n_out,
+                                                              uint64_t seed, int order, double* cstat) {
   constexpr int NV = 3 + D + 1;
   constexpr int NA = 2 + D + 1;
   __shared__ RecCell<D> rcs[NW];
@@ -39,7 +39,8 @@ __global__ void __launch_bounds__(NW * 32) recon_stats_kernel(int64_t C, int Kma
   for (int64_t j = (int64_t)blockIdx.x * NW + wid; j < C; j += (int64_t)gridDim.x * NW) {
     load_cell<D>(rc, j, Kmax, K, prm, lane);
     __syncwarp();
-    const int64_t o = out_off[j], n = out_off[j + 1] - o;
+    int64_t o, n;
+    out_range(out_off, j, n_out, o, n);
     double acc[NA];
 #pragma unroll
     for (int i = 0; i < NA; ++i) acc[i] = 0.0;
@@ -86,16 +87,16 @@ __global__ void __launch_bounds__(NW * 32) recon_stats_kernel(int64_t C, int Kma
 // rhs_i = dx (rho'_i - rho_i), rho_i dx = q sum_j alpha_j (shape sum).
 template <int D>
 __global__ void assemble_kernel(int64_t C, const double* cstat, const double* W,
-                                const int64_t* out_off, const double* rho_target, double dx,
-                                double q, double* A, double* B, double* Cc, double* Dd) {
+                                const int64_t* out_off, int64_t n_out, const double* rho_target,
+                                double dx, double q, double* A, double* B, double* Cc, double* Dd) {
   constexpr int NV = 3 + D + 1;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < C;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t im = (i == 0) ? C - 1 : i - 1;
     const int64_t ip = (i == C - 1) ? 0 : i + 1;
-    const int64_t nm = out_off[im + 1] - out_off[im];
-    const int64_t n0 = out_off[i + 1] - out_off[i];
-    const int64_t np = out_off[ip + 1] - out_off[ip];
+    const int64_t nm = out_count(out_off, im, n_out);
+    const int64_t n0 = out_count(out_off, i, n_out);
+    const int64_t np = out_count(out_off, ip, n_out);
     const double am = nm > 0 ? W[im] / (double)nm : 0.0;
     const double a0 = n0 > 0 ? W[i] / (double)n0 : 0.0;
     const double ap = np > 0 ? W[ip] / (double)np : 0.0;
@@ -261,8 +262,11 @@ __global__ void __launch_bounds__(NW * 32) recon_emit_kernel(
   for (int64_t j = (int64_t)blockIdx.x * NW + wid; j < C; j += (int64_t)gridDim.x * NW) {
     load_cell<D>(rc, j, Kmax, K, prm, lane);
     __syncwarp();
-    const int64_t o = out_off[j], n = out_off[j + 1] - o;
-    if (lane == 0) status_out[j] = projection_coeffs<D>(rc, n, W[j], dA[j], cstat + (size_t)j * NV + 3);
+    int64_t o, n;
+    const bool in_range = out_range(out_off, j, n_out, o, n);
+    if (lane == 0)
+      status_out[j] = projection_coeffs<D>(rc, n, W[j], dA[j], cstat + (size_t)j * NV + 3) |
+                      (in_range ? 0u : GM_ST_BAD_RANGE);
     __syncwarp();
     const double aa = rc.a, an = rc.alpha_new;
     const int skip = rc.skip;
@@ -359,14 +363,18 @@ cudaError_t launch_reconstruct(int D, int64_t C, int Kmax, const int32_t* K, con
   const int64_t ncta = (C + NW - 1) / NW;
   const int g = (int)(ncta < 152 * 16 ? ncta : 152 * 16);
   if (D == 1)
-    recon_stats_kernel<1, NW><<<g, NW * 32, 0, s>>>(C, Kmax, K, prm, out_off, seed, order, cstat);
+    recon_stats_kernel<1, NW><<<g, NW * 32, 0, s>>>(C, Kmax, K, prm, out_off, n_out, seed, order,
+                                                    cstat);
   else
-    recon_stats_kernel<3, NW><<<g, NW * 32, 0, s>>>(C, Kmax, K, prm, out_off, seed, order, cstat);
+    recon_stats_kernel<3, NW><<<g, NW * 32, 0, s>>>(C, Kmax, K, prm, out_off, n_out, seed, order,
+                                                    cstat);
   const int ga = (int)((C + 255) / 256 < 4096 ? (C + 255) / 256 : 4096);
   if (D == 1)
-    assemble_kernel<1><<<ga, 256, 0, s>>>(C, cstat, W, out_off, rho_target, dx, q, A, B, Cc, Dd);
+    assemble_kernel<1><<<ga, 256, 0, s>>>(C, cstat, W, out_off, n_out, rho_target, dx, q, A, B, Cc,
+                                          Dd);
   else
-    assemble_kernel<3><<<ga, 256, 0, s>>>(C, cstat, W, out_off, rho_target, dx, q, A, B, Cc, Dd);
+    assemble_kernel<3><<<ga, 256, 0, s>>>(C, cstat, W, out_off, n_out, rho_target, dx, q, A, B, Cc,
+                                          Dd);
   if (pl.multi) {
     mm_eliminate_kernel<<<(P + 127) / 128, 128, 0, s>>>(C, A, B, Cc, Dd, sw, P);
     const int P2 = pl.P2;

@@ -11,6 +11,29 @@
 
 namespace gmcr {
 
+// Cell j's output range [o, o + n) of the caller's particle arrays (n_out
+// particles).  A range that does not lie inside [0, n_out) -- a negative
+// count, or a start or an end outside the arrays -- is replaced by the empty
+// range, and the function returns false: the cell is then treated as a cell
+// without resampled particles and flagged GM_ST_BAD_RANGE, so that no kernel
+// writes outside the caller's buffers.
+__device__ __forceinline__ bool out_range(const int64_t* out_off, int64_t j, int64_t n_out,
+                                          int64_t& o, int64_t& n) {
+  o = out_off[j];
+  n = out_off[j + 1] - o;
+  if (o < 0 || n < 0 || o > n_out - n) {
+    o = 0;
+    n = 0;
+    return false;
+  }
+  return true;
+}
+__device__ __forceinline__ int64_t out_count(const int64_t* out_off, int64_t j, int64_t n_out) {
+  int64_t o, n;
+  out_range(out_off, j, n_out, o, n);
+  return n;
+}
+
 template <int D>
 struct RecCell {
   static constexpr int NM = D * (D + 1) / 2;

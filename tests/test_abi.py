@@ -89,6 +89,13 @@ def test_argument_errors_without_gpu(lib):
                                   None) == 0
 
 
+def test_noalloc_scratch_holds_its_cell_limit(lib):
+    """The static scratch of gm_reconstruct_noalloc (5 MiB) holds the
+    workspace of its advertised 32768-cell limit for D = 1 and D = 3
+    (host-side layout arithmetic, no device access)."""
+    assert lib.gm_noalloc_limits_ok() == 1
+
+
 def test_mlp_struct_layout_matches_header(tmp_path):
     from paper_2007_12273_gb300.gm import GMMlp
     src = tmp_path / "lay2.c"

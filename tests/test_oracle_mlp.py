@@ -135,3 +135,93 @@ def test_bf16_rounding():
     x = np.random.default_rng(0).standard_normal(10000) * 10.0 ** np.random.default_rng(1).uniform(-5, 5, 10000)
     ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).double().numpy()
     np.testing.assert_array_equal(mlp.bf16(x), ref)
+
+
+def _slot_out(D, Kmax, slots):
+    """A network output vector from per-slot tuples (presence logit, log
+    weight, mu (D), log diag (D), off-diagonals (D(D-1)/2))."""
+    SP = mlp.slot_size(D)
+    o, opad = mlp.out_dims(D, Kmax)
+    out = np.zeros(opad)
+    for s, vals in enumerate(slots):
+        flat = [vals[0], vals[1], *vals[2], *vals[3], *vals[4]]
+        assert len(flat) == SP
+        out[s * SP:(s + 1) * SP] = flat
+    for s in range(len(slots), Kmax):
+        out[s * SP] = -9.0
+    return out
+
+
+def test_decode_caps_K0_so_that_the_penalised_weights_stay_positive():
+    # 3V: T = 9, so N - T K0 / 2 > 0 allows K0 <= 4 at N = 20 and K0 = 1 at
+    # N = 9.  Six slots are present; the cap drops the smallest log weights
+    # one at a time (hand table: log weights 0.1, -2, 0.5, -1, 0.3, 0.2 ->
+    # slots 0, 2, 4, 5 at N = 20; slot 2 alone at N = 9).
+    D, Kmax = 3, 10
+    lw = [0.1, -2.0, 0.5, -1.0, 0.3, 0.2]
+    slots = [(1.0, lw[s], [0.1 * s, 0.0, 0.0], [0.0, 0.0, 0.0], [0.0, 0.0, 0.0]) for s in range(6)]
+    out = _slot_out(D, Kmax, slots)
+    mean, sd = np.zeros(3), np.ones(3)
+    K0, prm = mlp.decode(out, mean, sd, 20, D, Kmax)
+    assert K0 == 4
+    np.testing.assert_allclose(prm[:, 1], [0.0, 0.2, 0.4, 0.5])  # slots 0, 2, 4, 5 in slot order
+    e = np.exp([0.1, 0.5, 0.3, 0.2])
+    np.testing.assert_allclose(prm[:, 0], e / e.sum(), rtol=1e-14)
+    K0, prm = mlp.decode(out, mean, sd, 9, D, Kmax)
+    assert K0 == 1
+    assert prm[0, 1] == pytest.approx(0.2) and prm[0, 0] == 1.0
+    # 1V: T = 2, N = 3 allows K0 <= 2
+    slots1 = [(2.0, w_, [0.5 * s], [0.0], []) for s, w_ in enumerate([0.0, 1.0, -1.0])]
+    K0, prm = mlp.decode(_slot_out(1, 8, slots1), np.zeros(1), np.ones(1), 3, 1, 8)
+    assert K0 == 2
+    np.testing.assert_allclose(prm[:, 1], [0.0, 0.5])
+
+
+def test_decode_keeps_at_least_the_most_likely_slot():
+    # every presence logit below the threshold: the slot of the largest
+    # logit alone, with weight 1, its mean and covariance
+    D, Kmax = 1, 8
+    slots = [(-3.0, 0.0, [1.0], [0.0], []), (-0.5, 0.7, [-2.0], [np.log(0.5)], []),
+             (-1.0, 0.0, [3.0], [0.0], [])]
+    mean, sd = np.array([10.0]), np.array([2.0])
+    K0, prm = mlp.decode(_slot_out(D, Kmax, slots), mean, sd, 1000, D, Kmax)
+    assert K0 == 1
+    # mu = mean + sd * (-2) = 6; Sigma = (sd * 0.5)^2 = 1
+    np.testing.assert_allclose(prm[0], [1.0, 6.0, 1.0], rtol=1e-14)
+    # a higher threshold does the same even when some logits are positive
+    K0, prm = mlp.decode(_slot_out(D, Kmax, [(0.5, 0.0, [1.0], [0.0], [])]), mean, sd, 1000, D,
+                         Kmax, presence_logit=1.0)
+    assert K0 == 1 and prm[0, 1] == pytest.approx(12.0)
+
+
+def test_decode_clamps_the_log_diagonal():
+    # log diag of the whitened Cholesky factor clamped to [-10, 5]: 20 -> 5,
+    # -30 -> -10, 1 kept; 3V with zero off-diagonals gives a diagonal
+    # covariance sd_d^2 exp(2 clamp(ld_d))
+    D, Kmax = 3, 10
+    slots = [(4.0, 0.0, [0.0, 0.0, 0.0], [20.0, -30.0, 1.0], [0.0, 0.0, 0.0])]
+    sd = np.array([1.0, 2.0, 3.0])
+    K0, prm = mlp.decode(_slot_out(D, Kmax, slots), np.zeros(3), sd, 1000, D, Kmax)
+    assert K0 == 1
+    # upper-triangle order: 00, 01, 02, 11, 12, 22
+    S = prm[0, 4:]
+    np.testing.assert_allclose(S, [np.exp(10.0), 0.0, 0.0, 4.0 * np.exp(-20.0), 0.0, 9.0 * np.exp(2.0)],
+                               rtol=1e-14)
+    # the off-diagonal entries of L enter unclamped: L10 = 3 gives
+    # Sigma_01 = sd0 sd1 * L00 * L10
+    slots = [(4.0, 0.0, [0.0, 0.0, 0.0], [0.0, 0.0, 0.0], [3.0, 0.0, 0.0])]
+    K0, prm = mlp.decode(_slot_out(D, Kmax, slots), np.zeros(3), sd, 1000, D, Kmax)
+    np.testing.assert_allclose(prm[0, 4:], [1.0, 2.0 * 3.0, 0.0, 4.0 * (9.0 + 1.0), 0.0, 9.0], rtol=1e-14)
+
+
+@pytest.mark.parametrize("D", [1, 3])
+def test_features_of_a_zero_variance_cell_are_zero(D):
+    # a cell whose velocities are all equal (in one dimension for 3V) cannot
+    # be whitened: its feature vector is all zero and its sd is returned as 0
+    rng = np.random.default_rng(3)
+    v = rng.standard_normal((50, D))
+    v[:, D - 1] = 0.25
+    f, mean, sd = mlp.cell_features(v, rng.uniform(0.5, 1.5, 50))
+    assert f.shape == (mlp.feat_dims(D)[2],)
+    assert np.all(f == 0.0)
+    assert sd[D - 1] == 0.0 and mean[D - 1] == pytest.approx(0.25)
