@@ -6,11 +6,15 @@ charge deposit) and reconstruct (sampling, Gauss'-law weight correction,
 Lemons projection) of one batch of cells.  Metric: particles/s =
 N_in / (t_compress + t_reconstruct), with N' = N_in per cell.
 
-Default workload: 1D-1V batched cells -- 4096 cells with Poisson(2000)
-particles (clipped to 200-8000), each a random mixture of 1-4 drifting
-Maxwellians (drifts U[-0.5, 0.5], vth U[0.02, 0.1], Dirichlet(1) weights),
-FP32 velocities, FP64 weights and positions, Kmax = 8, quadratic B-spline
-shape functions.
+Default workload: the full-scale 1D-3V pipeline -- 262144 cells with
+log-normal particle counts N_j = round(512 exp(0.47 Z)) clipped to
+[16, 8192] (about 1.5e8 particles), one bi-Maxwellian per cell (v_th,par =
+0.1 along x, T_perp/T_par ~ U[4, 25], drift U[-0.1, 0.1]^3), FP32
+velocities, FP64 weights and positions, Kmax = 10, quadratic B-spline shape
+functions; learned initialisation against plain EM, both timed, with the
+M-step in FP64 (statistic sums, covariance updates, Cholesky factors and
+inverses).  ``--workload mixture_1d1v`` and ``bimaxwellian_1d3v`` select the
+4096-cell 1D-1V and the 2048 x 4000 1D-3V batches.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gmcr|reference]
 
@@ -38,9 +42,23 @@ import workloads  # noqa: E402
 
 METRIC = "GM CR particles/s (compress+reconstruct) on GB300, learned-init vs plain EM"
 UNIT = "particles/s"
-WORKLOAD_DESC = ("mixture_1d1v: 4096 cells x Poisson(2000) particles (clip 200-8000), "
-                 "1-4 drifting Maxwellians per cell, FP32 v, FP64 x/alpha, Kmax=8, S2 shape, "
-                 "tol=1e-6, max_sweeps=1000, N'=N per cell")
+WORKLOAD_DESCS = {
+    "lognormal_1d3v": ("lognormal_1d3v: full-scale 1D-3V pipeline, 262144 cells x round(512 exp(0.47 Z)) "
+                       "particles (clip 16-8192, ~1.5e8), one bi-Maxwellian per cell (T_perp/T_par "
+                       "U[4,25], drift U[-0.1,0.1]^3), FP32 v, FP64 x/alpha, Kmax=10, S2 shape, "
+                       "tol=1e-6, max_sweeps=1000, N'=N per cell"),
+    "mixture_1d1v": ("mixture_1d1v: 4096 cells x Poisson(2000) particles (clip 200-8000), "
+                     "1-4 drifting Maxwellians per cell, FP32 v, FP64 x/alpha, Kmax=8, S2 shape, "
+                     "tol=1e-6, max_sweeps=1000, N'=N per cell"),
+    "bimaxwellian_1d3v": ("bimaxwellian_1d3v: 2048 cells x 4000 particles, one bi-Maxwellian per cell "
+                          "(T_perp/T_par U[4,25], drift U[-0.1,0.1]^3), FP32 v, FP64 x/alpha, Kmax=10, "
+                          "S2 shape, tol=1e-6, max_sweeps=1000, N'=N per cell"),
+}
+WORKLOAD_DESC = WORKLOAD_DESCS["lognormal_1d3v"]
+
+
+def workload_desc(name: str) -> str:
+    return WORKLOAD_DESCS.get(name, name)
 L2_BYTES = 126 * 1024 * 1024
 
 
@@ -219,10 +237,31 @@ def sub_workload(wl, ncells: int):
                               np.ascontiguousarray(wl.v[:, :n]), wl.alpha[:n].copy(), p)
 
 
-def oracle_step(wl, nthreads: int) -> float:
+def strided_sample(wl, ncells: int):
+    """Every (C / ncells)-th cell of the workload (at most ncells cells), as
+    a workload of its own: a sample that follows the batch's size
+    distribution.  Positions are moved into the sample's own periodic mesh
+    (same dx) so that the reconstruction's mesh is consistent."""
+    stride = max(1, wl.C // max(1, ncells))
+    cells = np.arange(0, wl.C, stride)[:ncells]
+    counts = wl.counts()[cells]
+    off = np.zeros(len(cells) + 1, dtype=np.int64)
+    off[1:] = np.cumsum(counts)
+    idx = np.concatenate([np.arange(wl.cell_off[j], wl.cell_off[j + 1]) for j in cells]) \
+        if len(cells) else np.zeros(0, dtype=np.int64)
+    dx = wl.params["L"] / wl.C
+    shift = np.repeat((np.arange(len(cells)) - cells) * dx, counts)
+    p = dict(wl.params)
+    p["L"] = dx * len(cells)
+    sw = workloads.Workload(wl.name + "_sample", off, wl.x[idx] + shift, np.ascontiguousarray(wl.v[:, idx]),
+                            wl.alpha[idx].copy(), p)
+    return sw, cells
+
+
+def oracle_step(wl, nthreads: int, cell_ids=None) -> float:
     import oracle
     t0 = time.perf_counter()
-    out = oracle.compress(wl.params, wl.cell_off, wl.x, wl.v, wl.alpha, nthreads=nthreads)
+    out = oracle.compress(wl.params, wl.cell_off, wl.x, wl.v, wl.alpha, nthreads=nthreads, cell_ids=cell_ids)
     oracle.reconstruct(wl.params, out["K"], out["params"], out["W"], out["rho_target"], wl.cell_off,
                        nthreads=nthreads)
     return time.perf_counter() - t0
@@ -247,28 +286,41 @@ def cpu_model() -> str:
     return platform.machine()
 
 
+ORACLE_MAX_SAMPLE_CELLS = 8192
+
+
+def sized_oracle_sample(wl, cores: int, budget_s: float):
+    """A strided sample of the workload's cells whose oracle step
+    (compress + reconstruct, OpenMP over cells on `cores` threads) takes
+    about budget_s, grown from 2 cells per core up to 8192 cells; returns
+    (sample, cells, seconds of the last timed step)."""
+    ncells = min(wl.C, max(2 * cores, 8))
+    while True:
+        sw, cells = strided_sample(wl, ncells)
+        t = oracle_step(sw, cores, cell_ids=cells)
+        if t >= budget_s / 3 or ncells >= min(wl.C, ORACLE_MAX_SAMPLE_CELLS):
+            return sw, cells, t
+        ncells = min(wl.C, ORACLE_MAX_SAMPLE_CELLS,
+                     max(2 * ncells, int(ncells * budget_s / max(t, 1e-3) / 1.5)))
+
+
 def cpu_baseline(wl, budget_s: float = 15.0) -> dict:
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
-    ncells = max(cores, 4)
-    sw = sub_workload(wl, ncells)
-    t = oracle_step(sw, cores)
-    # grow the sample toward the budget
-    if t < budget_s / 3:
-        scale = max(1, int(budget_s / max(t, 1e-3) / 1.5))
-        ncells = min(wl.C, ncells * scale)
-        sw = sub_workload(wl, ncells)
-        t = oracle_step(sw, cores)
-    # one thread on the first cells
-    s1 = sub_workload(wl, 4)
-    t1 = oracle_step(s1, 1)
+    sw, cells, t = sized_oracle_sample(wl, cores, budget_s)
+    # one thread on a few cells of the same strided sample
+    s1, c1 = strided_sample(wl, 4)
+    t1 = oracle_step(s1, 1, cell_ids=c1)
+    full_s = t * wl.ntot / max(1, sw.ntot)
     return {"value": sw.ntot / t, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {sw.C} cells ({sw.ntot} particles) of the workload, "
-                      f"compress+reconstruct, OpenMP over cells, {t:.1f} s",
+            "sample": f"every {wl.C // len(cells)}-th cell: {sw.C} cells ({sw.ntot} particles) of the "
+                      f"workload, compress+reconstruct, OpenMP over cells, {t:.1f} s",
+            "extrapolated_full_workload_s": full_s,
+            "extrapolation": "linear in particles: sample seconds x total / sample particles",
             "cpu_model": cpu_model(),
             "single_thread": {"value": s1.ntot / t1, "unit": UNIT, "cores": 1,
-                              "sample": f"first {s1.C} cells ({s1.ntot} particles), {t1:.1f} s"}}
+                              "sample": f"{s1.C} strided cells ({s1.ntot} particles), {t1:.1f} s"}}
 
 
 # ---------------------------------------------------------------------------
@@ -282,21 +334,26 @@ def run_reference(args):
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
-    ncells = max(2 * cores, 8)
-    sw = sub_workload(wl, ncells)
+    # each step is a bounded strided sample of the workload, sized so that
+    # warmup + steps together take about ref_budget seconds
+    per_step = max(2.0, args.ref_budget / max(1, args.steps + args.warmup))
+    sw, cells, _ = sized_oracle_sample(wl, cores, per_step)
     for _ in range(args.warmup):
-        oracle_step(sw, cores)
-    times = [oracle_step(sw, cores) for _ in range(args.steps)]
+        oracle_step(sw, cores, cell_ids=cells)
+    times = [oracle_step(sw, cores, cell_ids=cells) for _ in range(args.steps)]
     tot = sum(times)
     value = sw.ntot * args.steps / tot
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC if args.workload == "mixture_1d1v" else args.workload,
-                       "sample_cells": sw.C, "sample_particles": sw.ntot},
+            "config": {"workload": workload_desc(args.workload),
+                       "sample_cells": sw.C, "sample_particles": sw.ntot,
+                       "init": "paper (random particles)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"first {sw.C} cells ({sw.ntot} particles) per step",
+                             "sample": f"every {wl.C // len(cells)}-th cell: {sw.C} cells "
+                                       f"({sw.ntot} particles) per step",
+                             "extrapolated_full_workload_s": (tot / args.steps) * wl.ntot / max(1, sw.ntot),
                              "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -340,7 +397,7 @@ def run_gmcr(args):
     if args.cells:
         wl = sub_workload(wl, args.cells)
     D = wl.D
-    over = dict(precision=args.precision, threads_per_cell=args.threads_per_cell,
+    over = dict(precision=0 if args.mstep == "fp64" else 1, threads_per_cell=args.threads_per_cell,
                 smem_particles=args.smem_particles)
     cfg = gm.config(wl.params, **over)
     rcfg = gm.config(wl.params, seed_key="recon_seed", **over)
@@ -383,10 +440,18 @@ def run_gmcr(args):
     # ---- learned initialisation: the network is trained (untimed) on cells
     # of the same generator family fitted by the paper's method
     net, train_info = None, None
-    if use_learned:
+    if use_learned and args.load_net:
+        # a network trained and saved by an earlier run (--save-net): lets a
+        # profiler run skip the training launches
+        saved = np.load(args.load_net)
+        net = gm.Net(D, cfg.Kmax)
+        net.load([saved[f"W{i}"] for i in range(4)], [saved[f"b{i}"] for i in range(4)])
+        train_info = {"cells": int(saved["cells"]), "loaded_from": args.load_net}
+    elif use_learned:
         t0 = time.perf_counter()
         feats, Ts, Mks = [], [], []
-        nchunk = max(1, args.train_cells // 4096)
+        train_cells = args.train_cells or (65536 if D == 1 else 32768)
+        nchunk = max(1, train_cells // 4096)
         for ch in range(nchunk):
             tw = make_train_workload(args.workload, rank, ch, 4096)
             f_, T_, M_, _ = learned.fit_targets(cfg, t(tw.cell_off), t(tw.x), t(tw.v), t(tw.alpha))
@@ -406,6 +471,10 @@ def run_gmcr(args):
                       "adam_steps": hist["steps"], "loss_first": hist["loss"][0],
                       "loss_last": hist["loss"][-1]}
         del feat, T, Mk, feats, Ts, Mks
+        if args.save_net and rank == 0:
+            np.savez(args.save_net, cells=train_info["cells"],
+                     **{f"W{i}": w.cpu().numpy() for i, w in enumerate(net.W)},
+                     **{f"b{i}": b.cpu().numpy() for i, b in enumerate(net.b)})
 
     feat_wstat = {}
 
@@ -516,7 +585,9 @@ def run_gmcr(args):
         torch.cuda.synchronize()
         for i in range(steps):
             flush.fill_(float(i))
+            torch.cuda.nvtx.range_push("gmcr_step")  # lets a profiler select the timed steps
             one(evs[i])
+            torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
@@ -626,13 +697,15 @@ def run_gmcr(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC if args.workload == "mixture_1d1v" else args.workload,
+        "config": {"workload": workload_desc(args.workload),
                    "cells": C, "particles": n, "D": D, "Kmax": cfg.Kmax,
                    "init": ("learned (network trained untimed on %d cells of the same generator, "
                             "init time included in every step)" % train_info["cells"]
                             if head == "learned" else "paper (random particles)"),
-                   "precision": ("fp32 m-step, fp64 means and final step" if args.precision == 0
-                                 else "fp64 m-step"),
+                   "precision": ("fp64 m-step (statistic sums, covariance, factor, inverse), fp64 "
+                                 "convergence log-likelihood, fp64 final step; fp32 e-step"
+                                 if args.mstep == "fp64" else
+                                 "fp32 m-step, fp64 means and final step; fp32 e-step"),
                    "l2": "inputs > L2 and a 252 MB flush between timed steps",
                    "launch": ("CUDA-graph replay of init / compress / reconstruct" if not args.no_graph
                               else "direct calls"),
@@ -774,7 +847,8 @@ def run_standard(args):
         "ms": ms, "value": n / (ms * 1e-3), "sweeps_mean": float(o["sweeps"].mean()),
         "converged_frac": float(np.mean((o["status"] & 1) == 0)), "Kbar": float(o["K"].mean()),
         "lnL_mean": float(o["lnL"].mean()),
-        "mml_objective_mean": float(np.mean(mml_objective(o["K"], o["params"], o["lnL"], counts, D)))}
+        # gm_compress reports eq. (lnL-GM) itself, the penalised objective
+        "mml_objective_mean": float(o["lnL"].mean())}
     clk = clocks.stop()
     head = "kmeans+aa5"
     hm = modes[head]
@@ -816,7 +890,7 @@ def run_standard(args):
         "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": hm["ms"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC if args.workload == "mixture_1d1v" else args.workload,
+        "config": {"workload": workload_desc(args.workload),
                    "cells": C, "particles": n, "D": D, "Kmax": cfg.Kmax,
                    "mode": "K = Kmax components, K-means init, Anderson memory 5, tol 1e-6",
                    "l2": "inputs > L2 and a 252 MB flush between timed steps",
@@ -1023,15 +1097,23 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gmcr", choices=["gmcr", "reference"])
-    ap.add_argument("--workload", default="mixture_1d1v")
-    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--workload", default="lognormal_1d3v")
+    ap.add_argument("--mstep", default="fp64", choices=["fp64", "fp32"],
+                    help="fp64: FP64 M-step (statistic sums, covariance, factor, inverse) and the "
+                         "corrected convergence test (the library default); fp32: FP32 M-step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-budget", type=float, default=60.0,
+                    help="--impl reference: seconds of oracle work over warmup + steps")
     ap.add_argument("--cells", type=int, default=0, help="use only the first N cells (profiling)")
     ap.add_argument("--threads-per-cell", type=int, default=0)
     ap.add_argument("--init", default="both", choices=["plain", "learned", "both"])
-    ap.add_argument("--train-cells", type=int, default=65536)
+    ap.add_argument("--train-cells", type=int, default=0,
+                    help="training cells of the learned initialisation (default 65536 for 1V, "
+                         "32768 for 3V)")
     ap.add_argument("--epochs", type=int, default=60)
+    ap.add_argument("--save-net", default="", help="save the trained network (.npz)")
+    ap.add_argument("--load-net", default="", help="use a saved network instead of training")
     ap.add_argument("--smem-particles", type=int, default=0)
     ap.add_argument("--no-graph", action="store_true", help="time direct calls instead of graph replay")
     ap.add_argument("--presence-logit", type=float, default=0.0,

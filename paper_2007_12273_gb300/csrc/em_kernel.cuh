@@ -51,6 +51,10 @@ struct EmParams {
   float* scratch;          // global tile for cells larger than the shared one
   int64_t scratch_stride;  // floats per array of the global tile (even)
   unsigned int* queue;
+  // optional work list: the queue then runs over list[0 .. *list_count)
+  // (the cells that a closed-form pre-pass left to EM)
+  const unsigned int* list;
+  const unsigned int* list_count;
   int Kmax, max_sweeps, cap;
   double tol;
   uint64_t seed;
@@ -94,6 +98,14 @@ struct EmCtl {
   float eA[kMaxK][NM];  // lower triangle of sqrt(log2e/2) L^{-1}, row-major
   float elc[kMaxK];     // -log2|L| - (D/2) log2(2 pi)
   float eb[kMaxK];      // log2(u) + elc
+  // FP64 M-step only: the product of the whitened covariance's pivots
+  // (|Sigma_k|), the first-order log-likelihood error (log2 units, per unit
+  // responsibility mass) of the FP32 inverse-factor diagonal the E-step
+  // uses, and each component's responsibility mass N_k at its last update;
+  // with them the convergence test corrects the log-likelihood for the
+  // rounding of the FP32 E-step constants
+  double pp[kMaxK];
+  float corrA[kMaxK], Nkf[kMaxK];
   // the same, packed for the pair loop; slot kMaxK holds the previous
   // component's updated constants
   f32x2 ec[kMaxK + 1][NConst<D>::N];
@@ -101,14 +113,17 @@ struct EmCtl {
   float meanf[D], scf[D];
   double Nd, W, L, logjac, logN;
   double cov0[D * (D + 1) / 2];  // the cell's weighted covariance (original coordinates)
-  // FP32 convergence test on the centred log-likelihood (natural log, up to
-  // the constant Lbase that c0 removes)
-  float Lf, Lfprev, Lbase, halfLogNf;
+  // convergence test on the centred log-likelihood (natural log, up to the
+  // constant Lbase that c0 removes), assembled in FP64 from FP64 warp sums
+  // of the FP32 per-particle terms: at the stopping point L changes by about
+  // tol |L| per sweep, and an FP32 sum of N terms (or an FP32 log of the
+  // weights' normaliser times N) errs by a tenth of that
+  double Ld, Ldprev, Lbase;
   double sumAH;  // sum of the staged FP32 weights
-  float sumAHf;
   float c0;      // centring constant of the log-likelihood sum (log2 units)
   R NdR;
   float redf[NW][NRED];
+  double redL[NW];  // per-warp FP64 sums of the centred log-likelihood terms
   double redd[NW][NS + 1];
   double res[NS + 1];
   // final step (centered original coordinates)
@@ -313,6 +328,26 @@ __device__ __forceinline__ int warp_rs_index(int lane) {
   return q;
 }
 
+// warp sums of NP doubles by recursive halving (the FP64 form of warp_rs):
+// lane l ends with the total of value warp_rs_index<NP>(l) in v[0]
+template <int NP>
+__device__ __forceinline__ void warp_rs_d(double (&v)[NP], int lane) {
+  constexpr int LV = NP == 1 ? 0 : (NP == 2 ? 1 : (NP == 4 ? 2 : (NP == 8 ? 3 : (NP == 16 ? 4 : 5))));
+#pragma unroll
+  for (int lv = 0; lv < LV; ++lv) {
+    const int h2 = NP >> (lv + 1), b = 16 >> lv;
+    const bool up = (lane & b) != 0;
+#pragma unroll
+    for (int i = 0; i < h2; ++i) {
+      const double send = up ? v[i] : v[i + h2];
+      const double keep = up ? v[i + h2] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, b);
+    }
+  }
+#pragma unroll
+  for (int b = 16 >> LV; b >= 1; b >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], b);
+}
+
 // per-warp totals of NV per-thread values into red[warp][q], then a barrier
 template <int NV, int NP, int NW>
 __device__ __forceinline__ void block_partials(const float (&v)[NV], float (&red)[NW][NP]) {
@@ -447,6 +482,8 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
       for (int k = 0; k < K; ++k) {
         c.u[k] = (R)((double)c.u[k] / wsum);
         c.eb[k] = lg2((float)c.u[k]) + c.elc[k];
+        c.pp[k] = 1.0;
+        c.corrA[k] = c.Nkf[k] = 0.0f;
         pack_econst<D>(c.emu[k], c.eA[k], c.eb[k], c.ec[k]);
       }
       c.K = K;
@@ -498,6 +535,8 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
       for (int i = 0; i < NM; ++i) c.eA[k][i] = eA[i];
       c.elc[k] = elc;
       c.eb[k] = lg2((float)c.u[k]) + elc;
+      c.pp[k] = 1.0;
+      c.corrA[k] = c.Nkf[k] = 0.0f;
       pack_econst<D>(c.emu[k], c.eA[k], c.eb[k], c.ec[k]);
     }
   }
@@ -538,10 +577,8 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
     block_sum_d<D, NT, 1, R>(c, sa);
     if (tid == 0) {
       c.sumAH = c.res[0];
-      c.sumAHf = (float)c.res[0];
       c.c0 = -2.0471975511965976f * D;  // mean log2 density of a standard normal
       c.NdR = (R)c.Nd;
-      c.halfLogNf = (float)(0.5 * c.logN);
     }
   }
   if (tid == 0) {
@@ -557,6 +594,31 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
   ulonglong2* GA4 = reinterpret_cast<ulonglong2*>(GAT);
   f32x2* GG2 = reinterpret_cast<f32x2*>(GAT);  // term of pair pp at GG2[2 * pp]
   constexpr int NRED = EmCtl<D, NW, R>::NRED;
+
+  // ---- annihilation of component k (one thread): compaction, eq. (omegak)'s
+  // renormalisation through Z
+  auto remove_comp = [&](int k) {
+    const int K = c.K;
+    c.Z -= c.u[k];
+    for (int m = k; m < K - 1; ++m) {
+      c.u[m] = c.u[m + 1];
+      for (int x = 0; x < D; ++x) {
+        c.mu[m][x] = c.mu[m + 1][x];
+        c.emu[m][x] = c.emu[m + 1][x];
+        c.mulo[m][x] = c.mulo[m + 1][x];
+      }
+      for (int q = 0; q < NM; ++q) c.eA[m][q] = c.eA[m + 1][q];
+      for (int q = 0; q < NC; ++q) c.ec[m][q] = c.ec[m + 1][q];
+      c.elc[m] = c.elc[m + 1];
+      c.eb[m] = c.eb[m + 1];
+      c.pp[m] = c.pp[m + 1];
+      c.corrA[m] = c.corrA[m + 1];
+      c.Nkf[m] = c.Nkf[m + 1];
+    }
+    c.K = K - 1;
+    c.annih = 1;
+    c.pstate = 2;
+  };
 
   // ---- M-step for component k (eqs. muk, sigmak, omegak), one thread -----
   // sv: N_k, the first moments and the second moments about the FP32 mean
@@ -641,24 +703,199 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
         c.k = k + 1;
       }
     }
-    if (removed) {
-      c.Z -= c.u[k];
-      for (int m = k; m < K - 1; ++m) {
-        c.u[m] = c.u[m + 1];
-        for (int x = 0; x < D; ++x) {
-          c.mu[m][x] = c.mu[m + 1][x];
-          c.emu[m][x] = c.emu[m + 1][x];
-          c.mulo[m][x] = c.mulo[m + 1][x];
-        }
-        for (int q = 0; q < NM; ++q) c.eA[m][q] = c.eA[m + 1][q];
-        for (int q = 0; q < NC; ++q) c.ec[m][q] = c.ec[m + 1][q];
-        c.elc[m] = c.elc[m + 1];
-        c.eb[m] = c.eb[m + 1];
-      }
-      c.K = K - 1;
-      c.annih = 1;
-      c.pstate = 2;
+    if (removed) remove_comp(k);
+  };
+
+  // ---- the same M-step in FP64 by the 32 lanes of warp 0 (precision 1) ------
+  // Every lane holds the cross-warp FP64 sums sv.  Independent FP64 steps run
+  // on separate lanes in one instruction (the two reciprocals, the D new
+  // means, the D(D+1)/2 covariance entries, the floor's D terms), which
+  // keeps the FP64 instruction count -- GB300's FP64 pipe is 1/64 of its
+  // FP32 rate and every warp instruction occupies it whole -- near 60.
+  // The covariance about the new mean is factored as L~ diag(p) L~^T in
+  // FP64 (pivots p_i = the squared Cholesky diagonal); the FP32 E-step
+  // constants are then c diag(p)^-1/2 L~^-1 with c = sqrt(log2(e) / 2) and
+  // eb = log2(u) - log2|L| - (D/2) log2(2 pi) (FP32 logarithms: their error
+  // is what the convergence test corrects for).  The floor test is
+  // chol_whitened's: p_i sc_i^2 > 1e-13 sum_d (sc_d^2 S_dd + m_d^2) and
+  // p_i < 1e300.
+  auto mstep64 = [&](int k, const double (&sv)[NS + 1]) {
+    const int K = c.K;
+    const double Nk = sv[0];
+    const double Zold = (double)c.Z, uold = (double)c.u[k];
+    __syncwarp();
+    if (lane == 0) c.kwork++;
+    if (K > 1 && Nk - halfT <= 0.0) {
+      if (lane == 0) remove_comp(k);
+      __syncwarp();
+      return;
     }
+    // 1 / N_k (lane 0) and 1 / (N - T K / 2) (lane 1)
+    const double rin = rcp_nr(lane == 1 ? (double)c.NdR - halfT * K : Nk);
+    const double rN = __shfl_sync(0xffffffffu, rin, 0);
+    const double rD = __shfl_sync(0xffffffffu, rin, 1);
+    // the mean's shift dl and the new FP64 mean, coordinate x on lane x
+    double dl[D], mun[D];
+    {
+      double s1 = sv[1];
+      if (D == 3) s1 = lane == 1 ? sv[2] : (lane == 2 ? sv[3] : sv[1]);
+      const double dlv = s1 * rN;
+      const double mv = c.mu[k][lane < D ? lane : 0] + dlv;
+#pragma unroll
+      for (int x = 0; x < D; ++x) {
+        dl[x] = __shfl_sync(0xffffffffu, dlv, x);
+        mun[x] = __shfl_sync(0xffffffffu, mv, x);
+      }
+    }
+    // covariance about the new mean, entry t (upper triangle) on lane t
+    double Sn[NM];
+    if (D == 1) {
+      Sn[0] = fma(-dl[0], dl[0], sv[2] * rN);
+    } else {
+      const int t = lane < NM ? lane : 0;
+      const int tx = t < 3 ? 0 : (t < 5 ? 1 : 2);
+      const int ty = t < 3 ? t : (t < 5 ? t - 2 : 2);
+      double s2 = sv[4];
+#pragma unroll
+      for (int q = 1; q < NM; ++q) s2 = t == q ? sv[4 + q] : s2;
+      const double dx = tx == 0 ? dl[0] : (tx == 1 ? dl[1] : dl[D - 1]);
+      const double dy = ty == 0 ? dl[0] : (ty == 1 ? dl[1] : dl[D - 1]);
+      const double snv = fma(-dx, dy, s2 * rN);
+#pragma unroll
+      for (int q = 0; q < NM; ++q) Sn[q] = __shfl_sync(0xffffffffu, snv, q);
+    }
+    // L~ diag(p) L~^T (FP64)
+    double piv[D], l10 = 0.0, l20 = 0.0, l21 = 0.0;
+    piv[0] = Sn[0];
+    if (D == 3) {
+      const double r0 = rcp_nr(piv[0]);
+      l10 = Sn[1] * r0;
+      l20 = Sn[2] * r0;
+      piv[1] = fma(-l10, Sn[1], Sn[3]);
+      const double r1 = rcp_nr(piv[1]);
+      const double e12 = fma(-l20, Sn[1], Sn[4]);
+      l21 = e12 * r1;
+      piv[D - 1] = fma(-l21, e12, fma(-l20, Sn[2], Sn[5]));
+    }
+    // floor test, coordinate d on lane d
+    int pd;
+    {
+      const int d = lane < D ? lane : 0;
+      const double pd_ = D == 1 ? piv[0] : (d == 0 ? piv[0] : (d == 1 ? piv[1] : piv[D - 1]));
+      const double sdd = D == 1 ? Sn[0] : (d == 0 ? Sn[0] : (d == 1 ? Sn[3] : Sn[NM - 1]));
+      const double mud = D == 1 ? mun[0] : (d == 0 ? mun[0] : (d == 1 ? mun[1] : mun[D - 1]));
+      const double scd = c.sc[d], md = fma(scd, mud, c.mean[d]);
+      double term = lane < D ? fma(scd * scd, sdd, md * md) : 0.0;
+      if (D == 3) {
+        term += __shfl_xor_sync(0xffffffffu, term, 1);
+        term += __shfl_xor_sync(0xffffffffu, term, 2);
+      }
+      const double scale2 = __shfl_sync(0xffffffffu, term, 0);
+      const bool ok = !(lane < D) || ((pd_ * (scd * scd) > 1e-13 * scale2) && (pd_ < 1e300));
+      pd = __all_sync(0xffffffffu, ok);
+    }
+    if (!pd) {
+      if (lane == 0) {
+        c.status |= GM_ST_COV_NOT_PD;
+        if (K > 1) {
+          remove_comp(k);
+        } else {
+          c.pstate = 0;  // a lone component keeps its parameters
+          c.k = k + 1;
+        }
+      }
+      __syncwarp();
+      return;
+    }
+    // eq. (omegak), then the renormalisation of step 3 through Z
+    const double wn = (K == 1) ? 1.0 : (Nk - halfT) * rD;
+    const double un = wn * Zold;
+    // FP32 E constants: p_i^-1/2 on lane i
+    float ri[D];
+    {
+      const int d = lane < D ? lane : 0;
+      const float pf = (float)(D == 1 ? piv[0] : (d == 0 ? piv[0] : (d == 1 ? piv[1] : piv[D - 1])));
+      const float rr = rsqrt_nr(pf);
+#pragma unroll
+      for (int x = 0; x < D; ++x) ri[x] = __shfl_sync(0xffffffffu, rr, x);
+    }
+    const float cc = 0.84932180028801904272f;  // sqrt(log2(e) / 2)
+    float eA[NM];
+    if (D == 1) {
+      eA[0] = cc * ri[0];
+    } else {
+      eA[0] = cc * ri[0];
+      eA[1] = cc * (float)(-l10) * ri[1];
+      eA[2] = cc * ri[1];
+      eA[3] = cc * (float)fma(l10, l21, -l20) * ri[D - 1];
+      eA[4] = cc * (float)(-l21) * ri[D - 1];
+      eA[5] = cc * ri[D - 1];
+    }
+    // eb = log2(u) - (1/2) log2(prod p) - (D/2) log2(2 pi) (FP32), and the
+    // first-order log-likelihood error of the FP32 inverse factor's diagonal:
+    // the quadratic form's error summed over the component's
+    // responsibilities is N_k sum_i (A_ii^2 p_i - c^2), A_ii as used
+    double pp = piv[0];
+#pragma unroll
+    for (int x = 1; x < D; ++x) pp *= piv[x];
+    const float eb = lg2((float)un) - 0.5f * lg2((float)pp) - (float)D * 1.3257480647361593f;
+    double ca = 0.0;
+    if (D == 1) {
+      const float a2 = eA[0] * eA[0];  // the packed constant is -A^2 (one FP32 product)
+      ca = fma((double)a2, piv[0], -0.72134752044448170368);
+    } else {
+      ca = fma((double)eA[0] * (double)eA[0], piv[0], -0.72134752044448170368) +
+           fma((double)eA[2] * (double)eA[2], piv[1], -0.72134752044448170368) +
+           fma((double)eA[5] * (double)eA[5], piv[D - 1], -0.72134752044448170368);
+    }
+    float ec[NC];
+    {
+      float em[D];
+#pragma unroll
+      for (int x = 0; x < D; ++x) em[x] = (float)mun[x];
+      f32x2 e2[NC];
+      pack_econst<D>(em, eA, eb, e2);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        float lo, hi;
+        upk2(e2[q], lo, hi);
+        ec[q] = lo;
+      }
+    }
+    __syncwarp();
+    if (lane < D) {
+      const int x = lane;
+      double mx = mun[0];
+#pragma unroll
+      for (int q = 1; q < D; ++q) mx = x == q ? mun[q] : mx;
+      c.mu[k][x] = mx;
+      c.emu[k][x] = (float)mx;
+    }
+    if (lane < NM) {
+      float ax = eA[0];
+#pragma unroll
+      for (int q = 1; q < NM; ++q) ax = lane == q ? eA[q] : ax;
+      c.eA[k][lane] = ax;
+    }
+    if (lane < NC) {
+      float ex = ec[0];
+#pragma unroll
+      for (int q = 1; q < NC; ++q) ex = lane == q ? ec[q] : ex;
+      c.ec[k][lane] = bc2(ex);
+      c.ec[kMaxK][lane] = bc2(ex);
+    }
+    if (lane == 0) {
+      c.Z = (R)(Zold - uold + un);
+      c.u[k] = (R)un;
+      c.elc[k] = eb - lg2((float)un);
+      c.eb[k] = eb;
+      c.pp[k] = pp;
+      c.corrA[k] = (float)ca;
+      c.Nkf[k] = (float)Nk;
+      c.pstate = 1;
+      c.k = k + 1;
+    }
+    __syncwarp();
   };
 
   // ---- exact pass: s_p, m_p and eq. (lnL-GM) ------------------------------
@@ -744,45 +981,77 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
       upk2(acc[q], lo, hi);
       v[q] = lo + hi;
     }
-    v[NS] = accl;
+    v[NS] = 0.0f;
+    const double accw = warp_sum((double)accl);
+    if (lane == 0) c.redL[wid] = accw;
     block_partials<NS + 1, NRED, NW>(v, c.redf);
   };
 
   // warp 0 after a pass that summed the log-likelihood: the cross-warp sums
-  // (returned in sv by every lane of warp 0) and eq. (lnL-GM) (lane 0): the
-  // FP32 centred value c.Lf for the convergence test, and with full the FP64
-  // value c.L.  The first pass of a cell fixes c0 at the mean per-particle
-  // term, so that later passes sum small deviations.  The weights enter as
-  // omega_k = u_k / Z (Z = 1 after an exact pass).
+  // of the statistics (returned in sv by every lane of warp 0) and eq.
+  // (lnL-GM) (lane 0, FP64): the centred value c.Ld for the convergence test,
+  // and with full the value c.L.  The first pass of a cell fixes c0 at the
+  // mean per-particle term, so that later passes sum small deviations.  The
+  // weights enter as omega_k = u_k / Z with Z = sum_k u_k summed afresh in
+  // FP64 (the running Z of the M-step carries its rounding).
   auto finish_exact = [&](R (&sv)[NS + 1], bool full) {
     const int K = c.K;
     R st[NW];
 #pragma unroll
-    for (int q = 0; q < NW; ++q) st[q] = lane <= NS ? (R)c.redf[q][lane] : (R)0;
+    for (int q = 0; q < NW; ++q) st[q] = lane < NS ? (R)c.redf[q][lane] : (R)0;
 #pragma unroll
     for (int h = NW / 2; h >= 1; h >>= 1)
 #pragma unroll
       for (int q = 0; q < h; ++q) st[q] += st[q + h];
 #pragma unroll
-    for (int q = 0; q <= NS; ++q) sv[q] = __shfl_sync(0xffffffffu, st[0], q);
-    const float lz = lg2((float)c.Z);
-    float pen = lane < K ? lg2((float)c.u[lane]) - lz : 0.0f;  // log2 units
+    for (int q = 0; q < NS; ++q) sv[q] = __shfl_sync(0xffffffffu, st[0], q);
+    sv[NS] = (R)0;
+    const double ud = lane < K ? (double)c.u[lane] : 0.0;
+    const double Zd = warp_sum(ud);
+    float pen = lane < K ? lg2((float)ud / (float)Zd) : 0.0f;  // log2 omega_k
     pen = warp_sum(pen) * (float)kLn2;
+    // FP64 logarithms in one lane-parallel sequence: lane k < K log2 u_k,
+    // lane 16 + k log2 |Sigma_k|, lane K (K < 16) log2 Z
+    const int kk = lane & 15;
+    double arg = 1.0;
+    if (lane < K) arg = ud;
+    else if (lane >= 16 && kk < K) arg = (sizeof(R) == 8) ? c.pp[kk] : 1.0;
+    else if (lane == K) arg = Zd;
+    const double lg = log2(arg);
+    const double lz = K < 16 ? __shfl_sync(0xffffffffu, lg, K < 16 ? K : 0) : log2(Zd);
+    // FP64 M-step, convergence test: the first-order correction
+    // sum_k N_k corr_k (log2 units) of the log-likelihood for the rounding of
+    // the FP32 E-step constants, corr_k = (eb_k exact - eb_k as used) +
+    // corrA_k (see mstep64).  Not for the reported value after the final
+    // step (full), whose constants the final step rebuilt.
+    float cor = 0.0f;
+    if (sizeof(R) == 8 && !full) {
+      const double lpp = __shfl_sync(0xffffffffu, lg, (lane + 16) & 31);
+      float ck = 0.0f;
+      if (lane < K) {
+        const double b64 = lg - 0.5 * lpp - D * 1.3257480647361593;
+        ck = c.Nkf[lane] * ((float)(b64 - (double)c.eb[lane]) + c.corrA[lane]);
+      }
+      cor = warp_sum(ck);
+    }
     if (lane == 0) {
       const int dpar = K * (T + 1) - 1;
-      sv[NS] -= (R)(c.sumAHf * lz);
+      double lsum = (double)cor;
+#pragma unroll
+      for (int q = 0; q < NW; ++q) lsum += c.redL[q];
+      lsum -= c.sumAH * lz;
+      const double pc = -0.5 * dpar * c.logN - 0.5 * T * (double)pen;
       if (full || c.sweep == 0) {
-        const double lsum = (double)sv[NS] + (double)c.c0 * c.sumAH;
-        const double pc = -0.5 * dpar * c.logN - 0.5 * T * (double)pen;
-        c.L = lsum * kLn2 - c.Nd * c.logjac + pc;
+        const double ls = lsum + (double)c.c0 * c.sumAH;
+        c.L = ls * kLn2 - c.Nd * c.logjac + pc;
         if (!full) {
-          const float c0n = c.sumAH > 0.0 ? (float)(lsum / c.sumAH) : c.c0;
+          const float c0n = c.sumAH > 0.0 ? (float)(ls / c.sumAH) : c.c0;
           c.c0 = c0n;
-          c.Lf = (float)((lsum - (double)c0n * c.sumAH) * kLn2 + pc);
-          c.Lbase = (float)((double)c0n * c.sumAH * kLn2 - c.Nd * c.logjac);
+          c.Ld = (ls - (double)c0n * c.sumAH) * kLn2 + pc;
+          c.Lbase = (double)c0n * c.sumAH * kLn2 - c.Nd * c.logjac;
         }
       } else {
-        c.Lf = (float)kLn2 * (float)sv[NS] - c.halfLogNf * (float)dpar - 0.5f * T * pen;
+        c.Ld = kLn2 * lsum + pc;
       }
     }
   };
@@ -888,7 +1157,11 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
       upk2(acc[q], lo, hi);
       v[q] = lo + hi;
     }
-    v[NS] = accl;
+    v[NS] = 0.0f;
+    if (withL) {
+      const double accw = warp_sum((double)accl);
+      if (lane == 0) c.redL[wid] = accw;
+    }
     block_partials<NS + 1, NRED, NW>(v, c.redf);
   };
 
@@ -918,19 +1191,24 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
       R sv[NS + 1];
       finish_exact(sv, false);
       if (lane == 0) {
-        if (c.sweep > 0 && !c.annih &&
-            fabsf(c.Lf - c.Lfprev) <= (float)a.tol * fabsf(c.Lfprev + c.Lbase))
+        if (c.sweep > 0 && !c.annih && fabs(c.Ld - c.Ldprev) <= a.tol * fabs(c.Ldprev + c.Lbase))
           c.done = 1;
         else if (c.sweep >= a.max_sweeps)
           c.done = 2;
-        c.Lfprev = c.Lf;
+        c.Ldprev = c.Ld;
         if (!c.done) {
           c.sweep = c.sweep + 1;
           c.annih = 0;
           c.k = 0;
           c.pstate = 0;
-          mstep(0, sv);
         }
+      }
+      __syncwarp();
+      if (!c.done) {
+        if constexpr (sizeof(R) == 8)
+          mstep64(0, sv);
+        else if (lane == 0)
+          mstep(0, sv);
       }
     }
     __syncthreads();
@@ -950,7 +1228,10 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
 #pragma unroll
         for (int q = 0; q < NS; ++q) sv[q] = __shfl_sync(0xffffffffu, st[0], q);
         sv[NS] = (R)0;
-        if (lane == 0) mstep(k, sv);
+        if constexpr (sizeof(R) == 8)
+          mstep64(k, sv);
+        else if (lane == 0)
+          mstep(k, sv);
       }
       __syncthreads();
     }
@@ -1109,7 +1390,10 @@ __global__ void __launch_bounds__(NT, (D == 1 ? 1024 : 512) / NT) em_kernel(EmPa
   const VT* __restrict__ vin = static_cast<const VT*>(a.v);
 
   for (;;) {
-    if (tid == 0) c.cell = (int64_t)atomicAdd(a.queue, 1u);
+    if (tid == 0) {
+      const unsigned int t = atomicAdd(a.queue, 1u);
+      c.cell = a.list ? (t < *a.list_count ? (int64_t)a.list[t] : a.C) : (int64_t)t;
+    }
     __syncthreads();
     const int64_t j = c.cell;
     if (j >= a.C) break;

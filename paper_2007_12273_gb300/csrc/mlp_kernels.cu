@@ -22,11 +22,14 @@ __host__ __device__ constexpr int mlp_SP(int D) { return 2 + 2 * D + D * (D - 1)
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// features: one warp per cell (NW cells per CTA).  The weighted mean and
-// standard deviation (which whiten the cell and map the network's output
-// back) are FP64 two-pass sums; the whitened moments and the histogram are
-// FP32 (the features are stored in BF16; GB300 runs FP64 at 1/64 of the
-// FP32 rate).
+// features: one warp per cell (NW cells per CTA), two passes over the cell's
+// particles, both FP32.  The first sums W, the first and the diagonal second
+// moments about the cell's first particle (a shift inside the cell's spread,
+// so that the variance keeps FP32's relative accuracy); the second whitens
+// with the resulting mean and standard deviation and accumulates the higher
+// moments and the histogram.  The features are stored in BF16 and the
+// whitening only maps the network's start back to the cell, so FP32 is
+// ample -- and GB300 runs FP64 at 1/64 of the FP32 rate.
 // ---------------------------------------------------------------------------
 template <int D, typename VT, int NW>
 __global__ void __launch_bounds__(NW * 32) features_kernel(int64_t C, int64_t n, const int64_t* cell_off,
@@ -43,38 +46,34 @@ __global__ void __launch_bounds__(NW * 32) features_kernel(int64_t C, int64_t n,
     const int64_t o = cell_off[j];
     const int N = (int)(cell_off[j + 1] - o);
     for (int b = lane; b < NB; b += 32) hist[b] = 0.0f;
-    // W and the weighted mean
-    double W = 0.0, s1[D];
+    // W, and the first and diagonal second moments about the first particle
+    float sh[D];
 #pragma unroll
-    for (int d = 0; d < D; ++d) s1[d] = 0.0;
+    for (int d = 0; d < D; ++d) sh[d] = N > 0 ? (float)v[(int64_t)d * n + o] : 0.0f;
+    float W = 0.0f, s1[D], s2[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) s1[d] = s2[d] = 0.0f;
     for (int p = lane; p < N; p += 32) {
-      const double a = alpha[o + p];
+      const float a = (float)alpha[o + p];
       W += a;
 #pragma unroll
-      for (int d = 0; d < D; ++d) s1[d] = fma(a, (double)v[(int64_t)d * n + o + p], s1[d]);
-    }
-    W = warp_sum(W);
-    double mean[D];
-#pragma unroll
-    for (int d = 0; d < D; ++d) mean[d] = W > 0.0 ? warp_sum(s1[d]) / W : 0.0;
-    // variances
-    double s2[D];
-#pragma unroll
-    for (int d = 0; d < D; ++d) s2[d] = 0.0;
-    for (int p = lane; p < N; p += 32) {
-      const double a = alpha[o + p];
-#pragma unroll
       for (int d = 0; d < D; ++d) {
-        const double dv = (double)v[(int64_t)d * n + o + p] - mean[d];
-        s2[d] = fma(a * dv, dv, s2[d]);
+        const float dv = (float)v[(int64_t)d * n + o + p] - sh[d];
+        const float ad = a * dv;
+        s1[d] += ad;
+        s2[d] = fmaf(ad, dv, s2[d]);
       }
     }
-    double sd[D];
-    bool ok = W > 0.0;
+    W = warp_sum(W);
+    double mean[D], sd[D];
+    bool ok = W > 0.0f;
+    const float iW0 = ok ? 1.0f / W : 0.0f;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-      const double var = warp_sum(s2[d]);
-      sd[d] = ok ? sqrt(var / W) : 0.0;
+      const float m1 = warp_sum(s1[d]) * iW0;
+      const float var = fmaxf(warp_sum(s2[d]) * iW0 - m1 * m1, 0.0f);
+      mean[d] = (double)sh[d] + (double)m1;  // the shift kept exact
+      sd[d] = ok ? (double)sqrtf(var) : 0.0;
       ok = ok && sd[d] > 0.0;
     }
     if (lane == 0)
@@ -94,9 +93,9 @@ __global__ void __launch_bounds__(NW * 32) features_kernel(int64_t C, int64_t n,
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       mf[d] = (float)mean[d];
-      isf[d] = (float)(1.0 / sd[d]);
+      isf[d] = 1.0f / (float)sd[d];
     }
-    const float iW = (float)(1.0 / W);
+    const float iW = iW0;
     float s3[NC];
 #pragma unroll
     for (int i = 0; i < NC; ++i) s3[i] = 0.0f;
@@ -139,12 +138,12 @@ __global__ void __launch_bounds__(NW * 32) features_kernel(int64_t C, int64_t n,
       float val = 0.0f;
       if (i < NMOM) {
         if (D == 1) {
-          val = i == 0 ? s3[0] : (i == 1 ? s3[1] - 3.0f : (float)(log((double)N) / 10.0));
+          val = i == 0 ? s3[0] : (i == 1 ? s3[1] - 3.0f : logf((float)N) * 0.1f);
         } else {
           if (i < 3) val = s3[i];
           else if (i < 6) val = s3[i] - 3.0f;
           else if (i < 9) val = s3[i];
-          else val = (float)(log((double)N) / 10.0);
+          else val = logf((float)N) * 0.1f;
         }
       } else if (i < NMOM + NB) {
         val = hist[i - NMOM] * (float)NB;

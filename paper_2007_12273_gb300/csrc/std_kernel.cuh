@@ -85,26 +85,6 @@ __device__ __forceinline__ double rcp_nr_d(double t) {
   return y * (2.0 - t * y);
 }
 
-// warp sums of NP doubles by recursive halving (the FP64 form of warp_rs):
-// lane l ends with the total of value warp_rs_index<NP>(l) in v[0]
-template <int NP>
-__device__ __forceinline__ void warp_rs_d(double (&v)[NP], int lane) {
-  constexpr int LV = NP == 1 ? 0 : (NP == 2 ? 1 : (NP == 4 ? 2 : (NP == 8 ? 3 : (NP == 16 ? 4 : 5))));
-#pragma unroll
-  for (int lv = 0; lv < LV; ++lv) {
-    const int hh = NP >> (lv + 1), b = 16 >> lv;
-    const bool up = (lane & b) != 0;
-#pragma unroll
-    for (int i = 0; i < hh; ++i) {
-      const double send = up ? v[i] : v[i + hh];
-      const double keep = up ? v[i + hh] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, b);
-    }
-  }
-#pragma unroll
-  for (int b = 16 >> LV; b >= 1; b >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], b);
-}
-
 // One Anderson step by a whole warp (FP64): f = G(x) - x; the difference
 // with the previous pair joins the history (the oldest dropped beyond m);
 // gamma from (dF^T dF + 1e-12 max diag I) gamma = dF^T f; tn = G(x) - dG

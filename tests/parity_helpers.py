@@ -1,11 +1,14 @@
-"""Shared parity rule for EM fits (GPU against the FP64 oracle).
+"""Shared parity measures for EM fits (GPU against the FP64 oracle).
 
 A cell agrees naturally when it selects the same K and its penalised
-log-likelihood is within 1e-5 (relative) of the oracle's.  The stopping
-rule (relative change of L at most tol over a sweep) is knife-edge for
-cells whose EM creeps at a rate close to tol: rounding differences of order
-1e-8 in L decide whether a sweep stops, and the two sides can end many
-sweeps apart.  For such a cell the oracle is rerun for exactly the GPU's
+log-likelihood is within 1e-5 (relative) of the oracle's; the tests assert
+the natural rates (K alone, and K with lnL).  With the default FP64 M-step
+the GPU's convergence test follows the oracle's stopping sweep (its
+log-likelihood is summed in FP64 and corrected for the rounding of the
+FP32 E-step constants), so the natural rates are the gate.
+
+As a diagnostic (printed, not asserted) a disagreeing cell is also
+compared at equal sweep counts: the oracle is rerun for exactly the GPU's
 number of sweeps (tol = 0):
   * a cell the GPU stopped by the convergence test must then agree (same
     K, lnL within 1e-5);
@@ -37,6 +40,11 @@ def equal_sweep_agreement(params, v_cell, alpha_cell, cell, K_gpu, lnL_gpu, swee
         dL = abs(tr[-1] - tr[-2]) if len(tr) >= 2 else 0.0
         return bool(diff <= lag_sweeps * dL), rel
     return False, rel
+
+
+def same_k(g, ref):
+    """per-cell flags: the same selected component count"""
+    return np.asarray(g["K"]) == np.asarray(ref["K"])
 
 
 def agreement(g, ref, wl, cells=None):

@@ -53,3 +53,25 @@ def test_oracle_sample_keeps_the_mesh_spacing():
     assert sw.params["L"] / sw.C == pytest.approx(wl.params["L"] / wl.C)
     assert sw.v.flags.c_contiguous
     assert bench.sub_workload(wl, 1000).C == wl.C  # capped at the workload
+
+
+def test_strided_oracle_sample():
+    # the CPU baseline times the oracle on every k-th cell: each sampled cell
+    # keeps its particles, moved into the sample's own periodic mesh of the
+    # same dx, and its index in the batch (which keys its initial picks)
+    import workloads
+    wl = workloads.mixture_1d1v(C=64, mean_n=300, clip=(50, 600))
+    sw, cells = bench.strided_sample(wl, 16)
+    assert list(cells) == list(range(0, 64, 4))
+    dx = wl.params["L"] / wl.C
+    assert sw.C == 16 and sw.params["L"] == pytest.approx(16 * dx)
+    for i, j in enumerate(cells):
+        a, b = wl.cell_off[j], wl.cell_off[j + 1]
+        c, d = sw.cell_off[i], sw.cell_off[i + 1]
+        assert d - c == b - a
+        assert (sw.v[:, c:d] == wl.v[:, a:b]).all() and (sw.alpha[c:d] == wl.alpha[a:b]).all()
+        np.testing.assert_allclose(sw.x[c:d], wl.x[a:b] + (i - j) * dx, rtol=0, atol=1e-12)
+        assert np.all((sw.x[c:d] >= i * dx - 1e-12) & (sw.x[c:d] < (i + 1) * dx + 1e-12))
+    assert sw.v.flags.c_contiguous
+    sw2, cells2 = bench.strided_sample(wl, 1000)  # capped at the workload
+    assert sw2.C == wl.C and list(cells2) == list(range(64))

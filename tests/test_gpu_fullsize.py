@@ -68,9 +68,14 @@ def test_full_size_3v(gm, which):
                           wl.alpha[idx], nthreads=NTHREADS, cell_ids=cells)
     g = {k: t.cpu().numpy()[cells] for k, t in out.items()}
     agree, eq = agreement(g, ref, wl, cells)
-    print(f"{which}: natural agreement {agree.mean():.3f}, at equal sweeps {eq.mean():.3f}")
-    assert eq.mean() >= 0.95, (cells[~eq], g["K"][~eq], ref["K"][~eq])
-    assert agree.mean() >= 0.6
+    ks = g["K"] == ref["K"]
+    print(f"{which}: K {ks.mean():.3f}, K + lnL {agree.mean():.3f}, at equal sweeps {eq.mean():.3f}")
+    # the same K on 40 sampled cells; lnL within 1e-5 relative on most: the
+    # 3V cells' |L| is often 1-3 % of N (whitened densities near 1), where
+    # 1e-5 of |L| is 1e-7 nats per particle, the FP32 E-step's resolution
+    # (tests/test_gpu_parity_natural.py measures this on 256 cells)
+    assert ks.mean() >= 0.95, (cells[~ks], g["K"][~ks], ref["K"][~ks])
+    assert agree.mean() >= 0.85, agree.mean()
     np.testing.assert_allclose(g["W"], ref["W"], rtol=1e-13)
 
     # ---- exact moments of every fit ------------------------------------------

@@ -165,7 +165,7 @@ def test_autotune_picks_a_valid_shape_and_the_fit_stays_on_the_oracle(gm):
     K = out["K"].cpu().numpy()[sub]
     lnL = out["lnL"].cpu().numpy()[sub]
     agree = (K == ref["K"]) & (np.abs(lnL - ref["lnL"]) <= 1e-5 * np.abs(ref["lnL"]))
-    assert agree.mean() >= 0.6, agree.mean()
+    assert (K == ref["K"]).mean() >= 0.95 and agree.mean() >= 0.9, agree.mean()
 
 
 @pytest.mark.parametrize("nt,cap", [(64, 0), (64, 256), (128, 512)])
@@ -181,8 +181,10 @@ def test_small_ctas_fit_like_the_oracle(gm, nt, cap):
         g = {k: t.cpu().numpy() for k, t in out.items()}
         ref = oracle.compress(wl.params, wl.cell_off, wl.x, wl.v, wl.alpha, nthreads=8)
         agree, eq = agreement(g, ref, wl)
-        print(f"nt {nt} cap {cap} D {wl.D}: natural {agree.mean():.3f}, equal sweeps {eq.mean():.3f}")
-        assert eq.mean() >= 0.95 and agree.mean() >= 0.5
+        ks = g["K"] == ref["K"]
+        print(f"nt {nt} cap {cap} D {wl.D}: K {ks.mean():.3f}, K + lnL {agree.mean():.3f}, "
+              f"equal sweeps {eq.mean():.3f}")
+        assert ks.mean() >= 0.95 and agree.mean() >= 0.85, (ks.mean(), agree.mean())
         np.testing.assert_allclose(g["W"], ref["W"], rtol=1e-13)
 
 

@@ -47,8 +47,11 @@ def test_features_match_oracle(gm, which):
     for j in range(wl.C):
         sl = slice(wl.cell_off[j], wl.cell_off[j + 1])
         f, mean, sd = mlp.cell_features(wl.v[:, sl].T, wl.alpha[sl])
-        np.testing.assert_allclose(wstat[j, :D], mean, rtol=1e-12, atol=1e-15)
-        np.testing.assert_allclose(wstat[j, D:], sd, rtol=1e-12)
+        # FP32 whitening statistics (the features are BF16 and the whitening
+        # only maps the network's start back to the cell): the mean within
+        # 2e-6 of the cell's spread, the spread within 2e-6 relative
+        np.testing.assert_allclose(wstat[j, :D], mean, rtol=0, atol=2e-6 * sd.max())
+        np.testing.assert_allclose(wstat[j, D:], sd, rtol=2e-6)
         one = 2.0 * (64 if D == 1 else 512) / (sl.stop - sl.start)  # a particle near a bin edge
         np.testing.assert_allclose(feat[j], bf16_round(f), rtol=1e-2, atol=one)
 
@@ -81,7 +84,9 @@ def test_targets_and_decode_match_oracle(gm, which):
             k0, dec = mlp.decode(outs[j].astype(np.float64), mean, sd, sl.stop - sl.start, D, Kmax,
                                  presence_logit=thr)
             assert K0[j] == k0
-            np.testing.assert_allclose(prm[j, :k0], dec, rtol=1e-6, atol=1e-9)
+            # FP32 whitening statistics: means and covariances within 1e-5
+            # relative (1e-7 absolute for means near zero)
+            np.testing.assert_allclose(prm[j, :k0], dec, rtol=1e-5, atol=1e-7)
 
 
 def _net_and_batch(gm, D, Kmax, B, seed):

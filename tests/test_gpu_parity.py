@@ -54,18 +54,22 @@ def run_gpu_compress(gm, wl, **over):
     return {k: host(v) for k, v in out.items()}, out
 
 
-def check_compress_parity(g, ref, min_agree=0.99, wl=None, cells=None, min_equal_sweeps=0.99):
-    """Natural agreement (same K, lnL within 1e-5) and agreement after the
-    equal-sweep rule of parity_helpers (knife-edge stopping, unconverged
-    cells); both rates are asserted.  Returns (natural, equal-sweep)."""
+def check_compress_parity(g, ref, min_k=0.95, min_agree=0.85, wl=None, cells=None):
+    """Asserts the natural rates: the same K in at least min_k of the cells,
+    the same K and lnL within 1e-5 in at least min_agree.  Prints the rate
+    after the equal-sweep rule of parity_helpers as a diagnostic.  Returns
+    (K rate, natural rate)."""
+    from parity_helpers import same_k
+    ks = same_k(g, ref)
     if wl is not None:
         agree, eq = agreement(g, ref, wl, cells)
     else:
         rel = np.abs(g["lnL"] - ref["lnL"]) / np.maximum(np.abs(ref["lnL"]), 1e-300)
-        agree = (g["K"] == ref["K"]) & (rel <= 1e-5)
+        agree = ks & (rel <= 1e-5)
         eq = agree.copy()
+    print(f"parity: K {ks.mean():.3f}, K + lnL {agree.mean():.3f} (at equal sweeps {eq.mean():.3f})")
     bad = np.flatnonzero(~agree)
-    assert eq.mean() >= min_equal_sweeps, (np.flatnonzero(~eq), g["K"][~eq], ref["K"][~eq])
+    assert ks.mean() >= min_k, (np.flatnonzero(~ks), g["K"][~ks], ref["K"][~ks])
     assert agree.mean() >= min_agree, (bad, g["K"][bad], ref["K"][bad])
     np.testing.assert_allclose(g["W"], ref["W"], rtol=1e-13)
     if cells is None:
@@ -74,7 +78,7 @@ def check_compress_parity(g, ref, min_agree=0.99, wl=None, cells=None, min_equal
     # status bits that do not depend on the FP32 trajectory
     mask = oracle.ST_EMPTY | oracle.ST_DEGENERATE | oracle.ST_TOO_FEW
     np.testing.assert_array_equal(g["status"] & mask, ref["status"] & mask)
-    return agree.mean(), eq.mean()
+    return ks.mean(), agree.mean()
 
 
 def check_fit_moments(gm, wl, out_dev):
@@ -106,7 +110,7 @@ def test_compress_two_stream_full(gm):
     wl = workloads.two_stream_1d1v()  # 32 cells x 1024, FP64 v, CIC
     g, gd = run_gpu_compress(gm, wl)
     ref = oracle.compress(wl.params, wl.cell_off, wl.x, wl.v, wl.alpha, nthreads=NTHREADS)
-    check_compress_parity(g, ref, min_agree=0.9, wl=wl)
+    check_compress_parity(g, ref, min_k=0.96, min_agree=0.96, wl=wl)
     check_fit_moments(gm, wl, gd)
 
 
@@ -123,7 +127,12 @@ def test_compress_mixture_ragged(gm, precision):
     wl = workloads.mixture_1d1v(C=40, counts=counts, seed=77)
     g, gd = run_gpu_compress(gm, wl, precision=precision)
     ref = oracle.compress(wl.params, wl.cell_off, wl.x, wl.v, wl.alpha, nthreads=NTHREADS)
-    check_compress_parity(g, ref, min_agree=0.6, wl=wl, min_equal_sweeps=0.97)
+    # the FP64 M-step and corrected convergence test (precision 0, the
+    # default) follow the oracle's stopping sweep; the FP32 option stops
+    # within a few sweeps of it on most cells but not on the cells that creep
+    # at a rate near tol (measured 78-90 % natural agreement)
+    check_compress_parity(g, ref, min_k=0.95 if precision == 0 else 0.8,
+                          min_agree=0.95 if precision == 0 else 0.6, wl=wl)
     check_fit_moments(gm, wl, gd)
 
 
@@ -132,7 +141,7 @@ def test_compress_3v(gm, smem_particles):
     wl = workloads.bimaxwellian_1d3v(C=24, ppc=1500)
     g, gd = run_gpu_compress(gm, wl, smem_particles=smem_particles)
     ref = oracle.compress(wl.params, wl.cell_off, wl.x, wl.v, wl.alpha, nthreads=NTHREADS)
-    check_compress_parity(g, ref, min_agree=0.6, wl=wl, min_equal_sweeps=0.95)
+    check_compress_parity(g, ref, min_k=0.95, min_agree=0.85, wl=wl)
     check_fit_moments(gm, wl, gd)
 
 
@@ -149,7 +158,7 @@ def test_compress_variable_weights_and_edge_cells(gm):
     np.testing.assert_array_equal(g["status"] & (oracle.ST_EMPTY | oracle.ST_DEGENERATE),
                                   ref["status"] & (oracle.ST_EMPTY | oracle.ST_DEGENERATE))
     assert g["K"][0] == 0 and g["K"][5] == 0 and g["K"][7] == 1
-    check_compress_parity(g, ref, min_agree=0.75, wl=wl, min_equal_sweeps=1.0)
+    check_compress_parity(g, ref, min_k=1.0, min_agree=1.0, wl=wl)
 
 
 @pytest.mark.parametrize("D", [1, 3])
@@ -163,7 +172,7 @@ def test_compress_and_reconstruct_at_the_largest_kmax(gm, D):
         wl = workloads.bimaxwellian_1d3v(C=20, ppc=800, seed=92, Kmax=16)
     g, gd = run_gpu_compress(gm, wl)
     ref = oracle.compress(wl.params, wl.cell_off, wl.x, wl.v, wl.alpha, nthreads=NTHREADS)
-    check_compress_parity(g, ref, min_agree=0.5, wl=wl, min_equal_sweeps=0.9)
+    check_compress_parity(g, ref, min_k=0.9, min_agree=0.85, wl=wl)
     check_fit_moments(gm, wl, gd)
     gr, o = recon_both(gm, wl, ref)
     np.testing.assert_array_equal(gr["x"], o["x"])
@@ -288,8 +297,7 @@ def test_full_size_batched_sampled_cells(gm):
     ref = oracle.compress(wl.params, off, wl.x[idx], wl.v[:, idx], wl.alpha[idx],
                           nthreads=NTHREADS, cell_ids=cells)
     gs = {k: v[cells] for k, v in g.items()}
-    nat, eqs = check_compress_parity(gs, ref, min_agree=0.7, wl=wl, cells=cells, min_equal_sweeps=0.96)
-    print(f"full-size sampled cells: natural agreement {nat:.3f}, at equal sweeps {eqs:.3f}")
+    check_compress_parity(gs, ref, min_k=0.95, min_agree=0.95, wl=wl, cells=cells)
     # exact moments on every cell
     check_fit_moments(gm, wl, gd)
     # reconstruction invariants on every cell
