@@ -218,6 +218,95 @@ def em_secondary_rooflines(counts: np.ndarray, K: np.ndarray, kwork: np.ndarray,
              "note": "prologue moments + final FP64 step per particle; peak = nominal GB300 FP64"}]
 
 
+def fp64_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
+    """152 SMs x 2 FP64 FMA lanes per clock x 2 flops x the clock (at
+    2070 MHz 1.26 TFLOP/s, GB300's nominal 1.25)"""
+    return sms * 2 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# Algorithmic work of the kernels of one step, per particle of the cells a
+# kernel handles (FMA = 2 flops), D = 1 or 3, NM = D (D + 1) / 2:
+#  em_k1_kernel      FP64: the moments about the first particle -- D
+#                    differences, the weight sum, D products alpha dv, D
+#                    first-moment sums, NM second-moment FMAs: 1 + 3 D + 2 NM;
+#                    bytes: v (FP32) and alpha read once, 4 D + 8
+#  recon_stats_kernel FP64: w = dz + L xi (D adds), the shape sums of s and
+#                    s^2 (3), sum w (D), sum |w|^2 (2 D): 3 + 4 D
+#  recon_emit_kernel FP64: x = (j + u0) dx (2), w (D), v = u + a (w + beta)
+#                    (3 D): 2 + 4 D; bytes written: x, v, alpha = 16 + 8 D
+#  deposit           FP64: cell fraction (2), sum alpha, alpha s, alpha s^2
+#                    (5): 7; bytes read: x and alpha, 16
+#  features_kernel   bytes read: v (FP32) and alpha once, 4 D + 8
+#  mlp_forward       BF16 tensor flops 2 (F H + 2 H^2 + H O) per cell
+#  em_kernel         FP32 flops FLOPS_PER_PK per particle and component step
+K1_FP64_PER_P = {1: 1 + 3 + 2, 3: 1 + 9 + 12}
+STATS_FP64_PER_P = {1: 7, 3: 15}
+EMIT_FP64_PER_P = {1: 6, 3: 14}
+DEPOSIT_FP64_PER_P = 7
+
+
+def kernel_roofline(kernels: dict, ctx: dict) -> dict:
+    """Roofline of the step's dominant kernel (largest traced device time):
+    algorithmic work per launch / the kernel's traced time per step against
+    the bounding unit's peak (FP64 and FP32 from unit counts and the clock,
+    HBM and BF16 measured)."""
+    if not kernels:
+        return None
+    name, kt = max(kernels.items(), key=lambda kv: kv[1]["ms"])
+    sec = kt["ms"] * 1e-3
+    n = ctx["counts"].astype(np.float64)
+    D = ctx["D"]
+    f64_peak = fp64_peak_tflops(ctx["sm_mhz"])
+    f32_peak = fp32_peak_tflops(ctx["sm_mhz"])
+
+    def line(bound, achieved, peak, unit, note, secondary=None):
+        return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": None, "ms_per_launch": kt["ms"] / max(1, kt["launches_per_step"]),
+                "note": note, "secondary": secondary or []}
+
+    if name == "em_k1_kernel":
+        sel = ctx["K0"] == 1 if ctx["K0"] is not None else np.ones_like(n, dtype=bool)
+        np_ = float(n[sel].sum())
+        f = np_ * K1_FP64_PER_P[D] / sec / 1e12
+        b = np_ * (4 * D + 8) / sec / 1e9
+        return line("alu", f, f64_peak, "TFLOP/s",
+                    f"FP64 flops = {K1_FP64_PER_P[D]} per particle of the one-component cells "
+                    f"({int(sel.sum())} cells, {np_:.0f} particles); peak = 152 SMs x 2 FP64 FMA/clock x 2 "
+                    f"x {ctx['sm_mhz']:.0f} MHz",
+                    [{"unit": "GB/s", "achieved": b, "peak": ctx["hbm_gbs"], "frac": b / ctx["hbm_gbs"],
+                      "note": f"{4 * D + 8} B read per particle; peak measured (copy)"}])
+    if name == "recon_stats_kernel" or name == "recon_emit_kernel":
+        per = STATS_FP64_PER_P[D] if name == "recon_stats_kernel" else EMIT_FP64_PER_P[D]
+        f = float(n.sum()) * per / sec / 1e12
+        sec_l = []
+        if name == "recon_emit_kernel":
+            b = float(n.sum()) * (16 + 8 * D) / sec / 1e9
+            sec_l.append({"unit": "GB/s", "achieved": b, "peak": ctx["hbm_gbs"], "frac": b / ctx["hbm_gbs"],
+                          "note": f"{16 + 8 * D} B written per particle (x, v, alpha); peak measured (copy)"})
+        return line("alu", f, f64_peak, "TFLOP/s",
+                    f"FP64 flops = {per} per resampled particle; peak = 152 SMs x 2 FP64 FMA/clock x 2 x "
+                    f"{ctx['sm_mhz']:.0f} MHz", sec_l)
+    if name.startswith("deposit"):
+        f = float(n.sum()) * DEPOSIT_FP64_PER_P / sec / 1e12
+        return line("alu", f, f64_peak, "TFLOP/s", f"FP64 flops = {DEPOSIT_FP64_PER_P} per particle")
+    if name == "features_kernel":
+        b = float(n.sum()) * (4 * D + 8) / sec / 1e9
+        return line("hbm", b, ctx["hbm_gbs"], "GB/s", f"{4 * D + 8} B read per particle; peak measured (copy)")
+    if name.startswith("mlp_forward"):
+        H = 256
+        f = 2.0 * len(n) * (ctx["F"] * H + 2 * H * H + H * ctx["O"]) / sec / 1e12
+        return line("tensor", f, ctx["bf16_tflops"], "TFLOP/s", "BF16 dense flops of the 4 layers; peak measured (cuBLAS burst)")
+    if name == "em_kernel":
+        f = em_flops(ctx["counts"], ctx["kwork"], D) / sec / 1e12
+        return line("alu", f, f32_peak, "TFLOP/s",
+                    f"FP32 flops = sum_j N_j * kwork_j * {FLOPS_PER_PK[D]}; peak = 152 SMs x 128 FP32 lanes x 2 "
+                    f"x {ctx['sm_mhz']:.0f} MHz",
+                    em_secondary_rooflines(ctx["counts"], ctx["K"], ctx["kwork"], ctx["sweeps"], D, sec,
+                                           ctx["sm_mhz"]))
+    b = float(len(n)) * 64 / sec / 1e9
+    return line("hbm", b, ctx["hbm_gbs"], "GB/s", "per-cell records, ~64 B per cell")
+
+
 def measured_peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -447,6 +536,8 @@ def run_gmcr(args):
         net = gm.Net(D, cfg.Kmax)
         net.load([saved[f"W{i}"] for i in range(4)], [saved[f"b{i}"] for i in range(4)])
         train_info = {"cells": int(saved["cells"]), "loaded_from": args.load_net}
+        if args.presence_logit is None:
+            args.presence_logit = float(saved["presence_logit"])
     elif use_learned:
         t0 = time.perf_counter()
         feats, Ts, Mks = [], [], []
@@ -454,10 +545,11 @@ def run_gmcr(args):
         nchunk = max(1, train_cells // 4096)
         for ch in range(nchunk):
             tw = make_train_workload(args.workload, rank, ch, 4096)
-            f_, T_, M_, _ = learned.fit_targets(cfg, t(tw.cell_off), t(tw.x), t(tw.v), t(tw.alpha))
+            f_, T_, M_, fit_ = learned.fit_targets(cfg, t(tw.cell_off), t(tw.x), t(tw.v), t(tw.alpha))
             feats.append(f_)
             Ts.append(T_)
             Mks.append(M_)
+        calib = (tw, fit_["lnL"].clone())  # the last training chunk and its plain-EM objective
         feat = torch.cat(feats)
         T = torch.cat(Ts)
         Mk = torch.cat(Mks)
@@ -471,8 +563,16 @@ def run_gmcr(args):
                       "adam_steps": hist["steps"], "loss_first": hist["loss"][0],
                       "loss_last": hist["loss"][-1]}
         del feat, T, Mk, feats, Ts, Mks
+        # the decode's presence threshold, chosen on that training chunk
+        # (untimed): the fastest threshold whose start reaches plain EM's
+        # objective (eq. lnL-GM within 1e-4) as often as the best one, less
+        # half a percent
+        if args.presence_logit is None:
+            args.presence_logit, train_info["presence_calibration"] = learned.calibrate_presence(
+                net, cfg, *(t(a) for a in (calib[0].cell_off, calib[0].x, calib[0].v, calib[0].alpha)),
+                calib[1])
         if args.save_net and rank == 0:
-            np.savez(args.save_net, cells=train_info["cells"],
+            np.savez(args.save_net, cells=train_info["cells"], presence_logit=args.presence_logit,
                      **{f"W{i}": w.cpu().numpy() for i, w in enumerate(net.W)},
                      **{f"b{i}": b.cpu().numpy() for i, b in enumerate(net.b)})
 
@@ -538,6 +638,7 @@ def run_gmcr(args):
         for _ in range(warmup):
             one()
         torch.cuda.synchronize()
+        one_direct = one
         graphs = None
         if not args.no_graph:
             graphs = []
@@ -596,7 +697,17 @@ def run_gmcr(args):
             for g_ in graphs:
                 if g_ is not None:
                     g_.close()
-        return {"ms_init": ms[0], "ms_compress": ms[1], "ms_reconstruct": ms[2]}, cout
+        # per-kernel device times: the same steps as direct calls, with the
+        # library's event trace (CUDA events on the launching stream after
+        # each kernel), the L2 flushed between steps as above
+        tsteps = min(steps, 3)
+        with gm.Trace() as tr:
+            for i in range(tsteps):
+                flush.fill_(float(i))
+                one_direct()
+            torch.cuda.synchronize()
+        kern = {k: {"ms": v[0] / tsteps, "launches_per_step": v[1] / tsteps} for k, v in tr.times.items()}
+        return {"ms_init": ms[0], "ms_compress": ms[1], "ms_reconstruct": ms[2], "kernels": kern}, cout
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -693,6 +804,17 @@ def run_gmcr(args):
         paths["plain"]["other_seed_reaches_plain_L_1e-4"] = float(np.mean(L2 >= Lp - 1e-4 * np.abs(Lp)))
         paths["plain"]["other_seed_mean_lnL_minus_plain"] = float(np.mean(L2 - Lp))
     hs = paths[head]
+    K0_head = None
+    if head == "learned":
+        K0_head = init_learned(None)[0].cpu().numpy()
+
+    def head_ctx(path):
+        o = outs[path]
+        return dict(counts=counts, D=D, K=o["K"], kwork=o["kwork"], sweeps=o["sweeps"], K0=K0_head,
+                    sm_mhz=sm_mhz, hbm_gbs=float(peaks.get("hbm_gbs", 6800.0)),
+                    bf16_tflops=float(peaks.get("bf16_tflops", 1900.0)), F=gm.feat_width(D),
+                    O=gm.out_width(D, cfg.Kmax), ms_compress=res[path]["ms_compress"])
+
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
@@ -700,7 +822,8 @@ def run_gmcr(args):
         "config": {"workload": workload_desc(args.workload),
                    "cells": C, "particles": n, "D": D, "Kmax": cfg.Kmax,
                    "init": ("learned (network trained untimed on %d cells of the same generator, "
-                            "init time included in every step)" % train_info["cells"]
+                            "init time included in every step; decode presence threshold %g)"
+                            % (train_info["cells"], args.presence_logit)
                             if head == "learned" else "paper (random particles)"),
                    "precision": ("fp64 m-step (statistic sums, covariance, factor, inverse), fp64 "
                                  "convergence log-likelihood, fp64 final step; fp32 e-step"
@@ -722,16 +845,13 @@ def run_gmcr(args):
         "fit": {"Kbar": hs["Kbar"], "sweeps_mean": hs["sweeps_mean"],
                 "maxsweeps_frac": hs["maxsweeps_frac"], "compression_ratio": hs["compression_ratio"],
                 "proj_skipped_frac": float(np.mean((rst & 0x100) != 0))},
-        "roofline": {"kernel": "em_kernel (gm_compress)", "bound": "alu", "achieved": hs["em_tflops"],
-                     "peak": peak, "unit": "TFLOP/s", "frac": hs["em_tflops"] / peak,
-                     "traffic": (EM_DRAM_BYTES_PER_PARTICLE * n
-                                 if D == 1 and wl.v.dtype == np.float32 else None),
-                     "note": f"FP32 flops = sum_j N_j * kwork_j * {FLOPS_PER_PK[D]}; peak = 152 SMs "
-                             f"x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (unit counts and max clock)",
-                     "secondary": hs["em_secondary"]},
+        "roofline": kernel_roofline(res[head]["kernels"], head_ctx(head)),
+        "kernels": {k: dict(v, share=v["ms"] / max(1e-9, sum(z["ms"] for z in res[head]["kernels"].values())))
+                    for k, v in sorted(res[head]["kernels"].items(), key=lambda kv: -kv[1]["ms"])},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": (13 if head == "learned" else 7) * args.steps,
+        "gpu_launches": int(round(sum(v["launches_per_step"] for v in res[head]["kernels"].values())
+                                  + (4 if head == "learned" else 0) + 2)) * args.steps,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1116,8 +1236,9 @@ def main(argv=None):
     ap.add_argument("--load-net", default="", help="use a saved network instead of training")
     ap.add_argument("--smem-particles", type=int, default=0)
     ap.add_argument("--no-graph", action="store_true", help="time direct calls instead of graph replay")
-    ap.add_argument("--presence-logit", type=float, default=0.0,
-                    help="learned init: decode slots whose presence logit exceeds this")
+    ap.add_argument("--presence-logit", type=float, default=None,
+                    help="learned init: decode slots whose presence logit exceeds this "
+                         "(default: calibrated on a training chunk)")
     ap.add_argument("--mesh2d", action="store_true",
                     help="the 2D-mesh pipeline (compress, target deposit, 2D reconstruct; one GPU)")
     ap.add_argument("--standard", action="store_true",

@@ -256,9 +256,26 @@ int gm_mixture_moments(const gm_config* cfg, int64_t C, const int32_t* K, const 
  *    to start at zero (each call writes every entry before reading it);
  *  - no cudaMalloc, cudaFree or allocating library routine is called.
  */
-/* 1 if the scratch a call of kMaxCells = 32768 cells needs (D = 1 and
- * D = 3) fits the 5 MiB array, else 0: a host-side self-check of the limit
- * above, no device access. */
+/*
+ * Per-kernel device times (the library's stage timer; the paper has no
+ * counterpart).  gm_trace_begin starts a trace: from then on, outside CUDA
+ * graph capture, the library records a CUDA event on the launching stream
+ * after each of its main kernels and at the start of each call; the time
+ * between consecutive events is the kernel's.  gm_trace_end synchronises
+ * the events, stops the trace and returns the number of distinct kernel
+ * names (or a negative GM_ERR_*); gm_trace_get(i, ...) returns name i
+ * (NUL-terminated, truncated to name_len - 1), its total milliseconds and
+ * its number of launches.  Host-side only besides the events; one trace
+ * per process at a time.
+ */
+int gm_trace_begin(void);
+int gm_trace_end(void);
+int gm_trace_get(int32_t i, char* name, int32_t name_len, double* ms, int32_t* launches);
+
+/* gm_noalloc_limits_ok -- 1 if the scratch a call of 32768 cells needs
+ * (D = 1 and D = 3) fits the 5 MiB array of gm_reconstruct_noalloc, else 0:
+ * a host-side self-check of that limit (no counterpart in the paper); it
+ * touches no device and returns no error code. */
 int gm_noalloc_limits_ok(void);
 int gm_reconstruct_noalloc(const gm_config* cfg, int64_t C, const int32_t* K, const double* params,
                            const double* W, const double* rho_target, int64_t n_out,

@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(NW * 32) em_k1_kernel(K1Params a) {
     // ---- moments about the first particle (FP64) -------------------------
     double sh[D];
 #pragma unroll
-    for (int d = 0; d < D; ++d) sh[d] = N > 0 ? (double)vin[(int64_t)d * a.n + off] : 0.0;
+    for (int d = 0; d < D; ++d) sh[d] = N > 0 ? to_f64(vin[(int64_t)d * a.n + off]) : 0.0;
     double acc[NP];
 #pragma unroll
     for (int i = 0; i < NP; ++i) acc[i] = 0.0;
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(NW * 32) em_k1_kernel(K1Params a) {
       const double al = a.alpha[off + p];
       double dv[D];
 #pragma unroll
-      for (int d = 0; d < D; ++d) dv[d] = (double)vin[(int64_t)d * a.n + off + p] - sh[d];
+      for (int d = 0; d < D; ++d) dv[d] = to_f64(vin[(int64_t)d * a.n + off + p]) - sh[d];
       acc[0] += al;
       int t = 1 + D;
 #pragma unroll

@@ -1294,7 +1294,7 @@ __device__ __forceinline__ void em_cell_body(const EmParams& a, EmCtl<D, NT / 32
         const double gam = Rd[p] * gk;
         double dv[D];
 #pragma unroll
-        for (int q = 0; q < D; ++q) dv[q] = ((double)vin[(int64_t)q * a.n + off + p] - c.mean[q]) - ck[q];
+        for (int q = 0; q < D; ++q) dv[q] = (to_f64(vin[(int64_t)q * a.n + off + p]) - c.mean[q]) - ck[q];
         acc[0] += gam;
         int t = 1 + D;
 #pragma unroll
@@ -1409,7 +1409,7 @@ __global__ void __launch_bounds__(NT, (D == 1 ? 1024 : 512) / NT) em_kernel(EmPa
     {
       double sh[D];
 #pragma unroll
-      for (int d = 0; d < D; ++d) sh[d] = N > 0 ? (double)vin[(int64_t)d * a.n + off] : 0.0;
+      for (int d = 0; d < D; ++d) sh[d] = N > 0 ? to_f64(vin[(int64_t)d * a.n + off]) : 0.0;
       double acc[1 + D + NM];
 #pragma unroll
       for (int i = 0; i < 1 + D + NM; ++i) acc[i] = 0.0;
@@ -1417,7 +1417,7 @@ __global__ void __launch_bounds__(NT, (D == 1 ? 1024 : 512) / NT) em_kernel(EmPa
         const double al = a.alpha[off + p];
         double dv[D];
 #pragma unroll
-        for (int d = 0; d < D; ++d) dv[d] = (double)vin[(int64_t)d * a.n + off + p] - sh[d];
+        for (int d = 0; d < D; ++d) dv[d] = to_f64(vin[(int64_t)d * a.n + off + p]) - sh[d];
         acc[0] += al;
         int t = 1 + D;
 #pragma unroll

@@ -295,6 +295,7 @@ static int compress_impl(const gm_config* cfg, int64_t C, int64_t n_particles,
 
   cudaError_t e = cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned int), s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  gmcr::trace_mark(nullptr, s);
   gmcr::EmParams p;
   p.C = C;
   p.n = n_particles;
@@ -348,14 +349,17 @@ static int compress_impl(const gm_config* cfg, int64_t C, int64_t n_particles,
     kp.Kmax = cfg->Kmax;
     e = gmcr::launch_em_k1(D, v_is_f64, kp, sms, s);
     if (e != cudaSuccess) return cuda_fail(e, "closed-form pre-pass launch");
+    gmcr::trace_mark("em_k1_kernel", s);
   }
   e = D == 1 ? gmcr::launch_em1(p, nt, fp64_mstep, v_is_f64, smem, (int)grid, s)
              : gmcr::launch_em3(p, nt, fp64_mstep, v_is_f64, smem, (int)grid, s);
   if (e != cudaSuccess) return cuda_fail(e, "EM kernel launch");
+  gmcr::trace_mark("em_kernel", s);
   if (x) {
     e = gmcr::launch_deposit(C, cell_off, x, alpha, cfg->L / (double)C, cfg->q, cfg->shape_order,
                              part, rho_target_out, s);
     if (e != cudaSuccess) return cuda_fail(e, "deposit launch");
+    gmcr::trace_mark("deposit (deposit_partials_kernel, deposit_combine_kernel)", s);
   }
   return GM_OK;
 }

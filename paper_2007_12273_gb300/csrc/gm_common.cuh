@@ -60,6 +60,41 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Conversions on the integer pipe.  GB300's FP64 pipe runs at 1/64 of the
+// FP32 rate and a conversion to or from FP64 occupies it like an FP64
+// operation; these produce the same values from the bit patterns.
+// f2d_exact: FP32 -> FP64, exact (zero, subnormals, infinities and NaN take
+// the hardware conversion).
+__device__ __forceinline__ double f2d_exact(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) return (double)f;
+  return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3)),
+                          (int)(u << 29));
+}
+template <typename VT>
+__device__ __forceinline__ double to_f64(VT v) {
+  if constexpr (sizeof(VT) == 4) return f2d_exact(v);
+  else return (double)v;
+}
+// d2f_trunc: FP64 -> FP32 with the mantissa truncated (relative error below
+// 2^-23), for values in FP32's normal range (others: hardware conversion)
+__device__ __forceinline__ float d2f_trunc(double d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const int e = (int)((u >> 52) & 0x7FFull) - 896;
+  if (e <= 0 || e >= 255) return (float)d;
+  return __uint_as_float((uint32_t)((u >> 32) & 0x80000000ull) | ((uint32_t)e << 23) |
+                         (uint32_t)((u >> 29) & 0x7FFFFFull));
+}
+// k 2^-53 for an odd integer 1 <= k < 2^53 (exact), negated if neg: the
+// double built from k's leading bit position and the bits below it
+__device__ __forceinline__ double odd_2m53(unsigned long long k, bool neg) {
+  const int b = 63 - __clzll((long long)k);  // leading bit, 0 .. 52
+  const unsigned long long mant = (k << (52 - b)) & ((1ull << 52) - 1ull);
+  const unsigned long long ex = (unsigned long long)(970 + b) << 52;  // 1023 + b - 53
+  return __longlong_as_double((long long)(ex | mant | (neg ? (1ull << 63) : 0ull)));
+}
+
 __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));

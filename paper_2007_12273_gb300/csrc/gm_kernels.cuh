@@ -44,6 +44,10 @@ int api_check_reconstruct(const gm_config* cfg, int64_t C, const int32_t* K, con
                           const int64_t* out_off, const double* x_out, const double* v_out,
                           const double* alpha_out, const uint32_t* status_out);
 int api_check_device();
+// per-kernel device times (gm_trace.cu): an event after each traced kernel
+// on its stream (name = the kernel), or a boundary (name = nullptr) at the
+// start of an API call; a no-op unless a trace is on
+void trace_mark(const char* name, cudaStream_t s);
 size_t reconstruct_ws_bytes(int D, int64_t C);
 cudaError_t launch_reconstruct(int D, int64_t C, int Kmax, const int32_t* K, const double* prm,
                                const double* W, const double* rho_target, int64_t n_out,

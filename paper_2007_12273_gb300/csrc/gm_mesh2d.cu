@@ -350,9 +350,9 @@ __global__ void __launch_bounds__(NW * 32) recon2d_emit_kernel(
       uint64_t m0;
       double w[D];
       sample_particle<D>(rc, j, i, seed, m0, w);
-      const double u0 = __dmul_rn(__dadd_rn((double)m0, 0.5), 2.220446049250313080847263336181640625e-16);
+      const double u0 = uniform_pos52(m0);
       const double uy =
-          __dmul_rn(__dadd_rn((double)sample_y_bits(j, i, seed), 0.5), 2.220446049250313080847263336181640625e-16);
+          uniform_pos52(sample_y_bits(j, i, seed));
       x_out[o + i] = __dmul_rn(__dadd_rn((double)jx, u0), dx);
       y_out[o + i] = __dmul_rn(__dadd_rn((double)jy, uy), dy);
       alpha_out[o + i] = an;

@@ -139,8 +139,10 @@ int gm_features(const gm_config* cfg, int64_t C, int64_t n_particles, const int6
     return gmcr::record_error(GM_ERR_ARG, "a required pointer is NULL");
   int rc = check_sm103();
   if (rc) return rc;
+  gmcr::trace_mark(nullptr, (cudaStream_t)stream);
   cudaError_t e = gmcr::launch_features(cfg->D, C, n_particles, cell_off, v, v_is_f64, alpha, feat,
                                         wstat, (cudaStream_t)stream);
+  gmcr::trace_mark("features_kernel", (cudaStream_t)stream);
   return e == cudaSuccess ? GM_OK : cuda_err(e, "features launch");
 }
 
@@ -194,7 +196,10 @@ int gm_mlp_forward(const gm_mlp* net, int32_t M, const void* X, void* scratch,
   if ((rc = check_sm103())) return rc;
   MlpScratch sc;
   scratch_layout(net, M, (char*)scratch, &sc);
-  return forward_impl(net, M, X, sc, out, err, (cudaStream_t)stream);
+  gmcr::trace_mark(nullptr, (cudaStream_t)stream);
+  rc = forward_impl(net, M, X, sc, out, err, (cudaStream_t)stream);
+  gmcr::trace_mark("mlp_forward (tc_gemm_kernel x4)", (cudaStream_t)stream);
+  return rc;
 }
 
 int gm_mlp_train_step(const gm_mlp* net, int32_t M, const void* X, const float* T,
@@ -280,8 +285,10 @@ int gm_mlp_decode(const gm_config* cfg, int64_t C, const float* out, int32_t O,
   int rc = check_sm103();
   if (rc) return rc;
   if (!(presence_logit == presence_logit)) return gmcr::record_error(GM_ERR_ARG, "presence_logit is NaN");
+  gmcr::trace_mark(nullptr, (cudaStream_t)stream);
   cudaError_t e = gmcr::launch_decode(cfg->D, C, cfg->Kmax, O, out, wstat, cell_off, presence_logit,
                                       K0, init_params, (cudaStream_t)stream);
+  gmcr::trace_mark("decode_kernel", (cudaStream_t)stream);
   return e == cudaSuccess ? GM_OK : cuda_err(e, "decode launch");
 }
 

@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(NW * 32) recon_emit_kernel(
       uint64_t m0;
       double w[D];
       sample_particle<D>(rc, j, i, seed, m0, w);
-      const double u0 = __dmul_rn(__dadd_rn((double)m0, 0.5), 2.220446049250313080847263336181640625e-16);
+      const double u0 = uniform_pos52(m0);
       x_out[o + i] = __dmul_rn(__dadd_rn((double)j, u0), dx);
       alpha_out[o + i] = an;
 #pragma unroll
@@ -358,6 +358,7 @@ cudaError_t launch_reconstruct(int D, int64_t C, int Kmax, const int32_t* K, con
   }
   if (dA_user) dA = dA_user;
 
+  trace_mark(nullptr, s);
   // one warp per cell, 4 cells per CTA, at most 16 CTAs per SM resident
   constexpr int NW = 4;
   const int64_t ncta = (C + NW - 1) / NW;
@@ -368,6 +369,7 @@ cudaError_t launch_reconstruct(int D, int64_t C, int Kmax, const int32_t* K, con
   else
     recon_stats_kernel<3, NW><<<g, NW * 32, 0, s>>>(C, Kmax, K, prm, out_off, n_out, seed, order,
                                                     cstat);
+  trace_mark("recon_stats_kernel", s);
   const int ga = (int)((C + 255) / 256 < 4096 ? (C + 255) / 256 : 4096);
   if (D == 1)
     assemble_kernel<1><<<ga, 256, 0, s>>>(C, cstat, W, out_off, n_out, rho_target, dx, q, A, B, Cc,
@@ -375,6 +377,7 @@ cudaError_t launch_reconstruct(int D, int64_t C, int Kmax, const int32_t* K, con
   else
     assemble_kernel<3><<<ga, 256, 0, s>>>(C, cstat, W, out_off, n_out, rho_target, dx, q, A, B, Cc,
                                           Dd);
+  trace_mark("assemble_kernel", s);
   if (pl.multi) {
     mm_eliminate_kernel<<<(P + 127) / 128, 128, 0, s>>>(C, A, B, Cc, Dd, sw, P);
     const int P2 = pl.P2;
@@ -384,12 +387,14 @@ cudaError_t launch_reconstruct(int D, int64_t C, int Kmax, const int32_t* K, con
   } else {
     mass_solve_kernel<<<1, P < 32 ? 32 : ((P + 31) / 32) * 32, 0, s>>>(C, A, B, Cc, Dd, dA, sw, P);
   }
+  trace_mark("mass-matrix solve (mass_solve_kernel and the blocked kernels)", s);
   if (D == 1)
     recon_emit_kernel<1, NW><<<g, NW * 32, 0, s>>>(C, Kmax, K, prm, W, out_off, cstat, dA, seed, dx,
                                                     n_out, x_out, v_out, alpha_out, status_out);
   else
     recon_emit_kernel<3, NW><<<g, NW * 32, 0, s>>>(C, Kmax, K, prm, W, out_off, cstat, dA, seed, dx,
                                                     n_out, x_out, v_out, alpha_out, status_out);
+  trace_mark("recon_emit_kernel", s);
   return cudaGetLastError();
 }
 

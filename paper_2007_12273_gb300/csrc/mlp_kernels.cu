@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(NW * 32) features_kernel(int64_t C, int64_t n,
 #pragma unroll
     for (int d = 0; d < D; ++d) s1[d] = s2[d] = 0.0f;
     for (int p = lane; p < N; p += 32) {
-      const float a = (float)alpha[o + p];
+      const float a = d2f_trunc(alpha[o + p]);
       W += a;
 #pragma unroll
       for (int d = 0; d < D; ++d) {
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(NW * 32) features_kernel(int64_t C, int64_t n,
 #pragma unroll
     for (int i = 0; i < NC; ++i) s3[i] = 0.0f;
     for (int p = lane; p < N; p += 32) {
-      const float w = (float)alpha[o + p] * iW;
+      const float w = d2f_trunc(alpha[o + p]) * iW;
       float y[D];
 #pragma unroll
       for (int d = 0; d < D; ++d) y[d] = ((float)v[(int64_t)d * n + o + p] - mf[d]) * isf[d];

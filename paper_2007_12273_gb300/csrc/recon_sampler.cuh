@@ -165,11 +165,11 @@ __device__ __forceinline__ void sample_particle(const RecCell<D>& rc, int64_t j,
   }
   const float* L = rc.Lf[z];
   if (D == 1) {
-    w[0] = rc.dz[z][0] + (double)(L[0] * xi[0]);
+    w[0] = rc.dz[z][0] + f2d_exact(L[0] * xi[0]);
   } else {
-    w[0] = rc.dz[z][0] + (double)(L[0] * xi[0]);
-    w[1] = rc.dz[z][1] + (double)fmaf(L[2], xi[1], L[1] * xi[0]);
-    w[2] = rc.dz[z][2] + (double)fmaf(L[5], xi[2], fmaf(L[4], xi[1], L[3] * xi[0]));
+    w[0] = rc.dz[z][0] + f2d_exact(L[0] * xi[0]);
+    w[1] = rc.dz[z][1] + f2d_exact(fmaf(L[2], xi[1], L[1] * xi[0]));
+    w[2] = rc.dz[z][2] + f2d_exact(fmaf(L[5], xi[2], fmaf(L[4], xi[1], L[3] * xi[0])));
   }
 }
 
@@ -183,8 +183,12 @@ __device__ __forceinline__ uint64_t sample_y_bits(int64_t j, int64_t i, uint64_t
 // (m + 1/2) 2^-52 - 1/2, the in-cell offset of a position from the cell
 // centre in cell units (exact in FP64)
 __device__ __forceinline__ double centred52(uint64_t m) {
-  return ((double)((long long)m - (1ll << 51)) + 0.5) * 2.220446049250313080847263336181640625e-16;
+  // ((m - 2^51) + 1/2) 2^-52 = (2 m - 2^52 + 1) 2^-53, built on the integer pipe
+  return m >= (1ull << 51) ? odd_2m53(2ull * m - (1ull << 52) + 1ull, false)
+                           : odd_2m53((1ull << 52) - 2ull * m - 1ull, true);
 }
+// the position uniform u0 = (m + 1/2) 2^-52 = (2 m + 1) 2^-53 of a 52-bit m
+__device__ __forceinline__ double uniform_pos52(uint64_t m) { return odd_2m53(2ull * m + 1ull, false); }
 
 // Lemons projection of a cell with n resampled particles (lane 0): the
 // corrected weight alpha' = W_j / n + dA_j and, from the sums sw[d] =

@@ -39,7 +39,8 @@ EXPORTED = ("gm_compress", "gm_reconstruct", "gm_moments", "gm_mixture_moments",
             "gm_mlp_scratch_bytes", "gm_mlp_forward", "gm_mlp_train_step", "gm_mlp_decode",
             "gm_graph_begin", "gm_graph_end", "gm_graph_launch", "gm_graph_destroy", "gm_autotune",
             "gm_compress_standard", "gm_anderson_affine", "gm_deposit_2d", "gm_reconstruct_2d",
-            "gm_autotune_from", "gm_noalloc_limits_ok")
+            "gm_autotune_from", "gm_noalloc_limits_ok", "gm_trace_begin", "gm_trace_end",
+            "gm_trace_get")
 
 
 class GMMlp(ct.Structure):
@@ -122,12 +123,16 @@ def load(build_if_missing: bool = False):
         lib.gm_deposit_2d.argtypes = [P] * 8
         lib.gm_reconstruct_2d.argtypes = [P, P, P, P, P, P, I64] + [P] * 8
         lib.gm_noalloc_limits_ok.argtypes = []
+        lib.gm_trace_begin.argtypes = []
+        lib.gm_trace_end.argtypes = []
+        lib.gm_trace_get.argtypes = [I32, ct.c_char_p, I32, ct.POINTER(ct.c_double), ct.POINTER(I32)]
         for f in ("gm_compress", "gm_reconstruct", "gm_moments", "gm_mixture_moments", "gm_shutdown",
                   "gm_reconstruct_noalloc", "gm_gemm_bf16", "gm_compress_from", "gm_features",
                   "gm_mlp_targets", "gm_mlp_sync", "gm_mlp_forward", "gm_mlp_train_step",
                   "gm_mlp_decode", "gm_graph_begin", "gm_graph_end", "gm_graph_launch",
                   "gm_graph_destroy", "gm_autotune", "gm_compress_standard", "gm_anderson_affine",
-                  "gm_deposit_2d", "gm_reconstruct_2d", "gm_autotune_from", "gm_noalloc_limits_ok"):
+                  "gm_deposit_2d", "gm_reconstruct_2d", "gm_autotune_from", "gm_noalloc_limits_ok",
+                  "gm_trace_begin", "gm_trace_end", "gm_trace_get"):
             getattr(lib, f).restype = ct.c_int
         lib.gm_last_error.restype = ct.c_char_p
         _lib = lib
@@ -755,3 +760,28 @@ def gm_anderson_affine(A, b, x0, memory: int, iters: int, stream=None):
                                 _stream_ptr(stream))
     _rc(lib, rc, "gm_anderson_affine")
     return x, res[:iters]
+
+
+class Trace:
+    """Per-kernel device times of the library's calls inside a ``with``
+    block (``gm_trace_begin`` / ``gm_trace_end``): ``.times`` maps kernel
+    name -> (milliseconds, launches) after the block."""
+
+    def __enter__(self):
+        lib = load()
+        _rc(lib, lib.gm_trace_begin(), "gm_trace_begin")
+        self.times = {}
+        return self
+
+    def __exit__(self, exc_type, exc, tb):
+        lib = load()
+        n = lib.gm_trace_end()
+        if n < 0:
+            _rc(lib, n, "gm_trace_end")
+        buf = ct.create_string_buffer(128)
+        ms = ct.c_double()
+        cnt = ct.c_int32()
+        for i in range(n):
+            _rc(lib, lib.gm_trace_get(i, buf, 128, ct.byref(ms), ct.byref(cnt)), "gm_trace_get")
+            self.times[buf.value.decode()] = (ms.value, cnt.value)
+        return False

@@ -54,3 +54,32 @@ def compress_learned(net: gm.Net, cfg, cell_off, x, v, alpha, out=None, presence
     """gm_compress started from the network's mixtures."""
     K0, prm = init_from_net(net, cfg, cell_off, v, alpha, presence_logit)
     return gm.gm_compress(cfg, cell_off, x, v, alpha, out=out, init_K=K0, init_params=prm)
+
+
+def calibrate_presence(net: gm.Net, cfg, cell_off, x, v, alpha, lnL_plain,
+                       candidates=(0.0, 0.5, 1.0, 2.0, 4.0), slack: float = 0.005):
+    """The decode's presence-logit threshold for a batch of training cells
+    whose plain-EM objective (eq. lnL-GM, ``lnL_plain``) is known: for each
+    candidate, EM from the decoded start is timed once and its rate of
+    reaching plain EM's objective (within 1e-4 relative) measured; the
+    fastest candidate whose rate is within ``slack`` of the best is
+    returned, with the table."""
+    feat, wstat = gm.gm_features(cfg, cell_off, v, alpha)
+    out = net.forward(feat)
+    table = {}
+    Lp = lnL_plain
+    for thr in candidates:
+        K0, prm = gm.gm_mlp_decode(cfg, out, wstat, cell_off, presence_logit=thr)
+        fit = gm.gm_compress(cfg, cell_off, x, v, alpha, init_K=K0, init_params=prm)  # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        gm.gm_compress(cfg, cell_off, x, v, alpha, init_K=K0, init_params=prm, out=fit)
+        e1.record()
+        torch.cuda.synchronize()
+        reach = float(((fit["lnL"] >= Lp - 1e-4 * Lp.abs())).double().mean())
+        table[thr] = {"ms": e0.elapsed_time(e1), "reach": reach,
+                      "sweeps": float(fit["sweeps"].double().mean())}
+    best = max(r["reach"] for r in table.values())
+    ok = [thr for thr, r in table.items() if r["reach"] >= best - slack]
+    pick = min(ok, key=lambda thr: table[thr]["ms"])
+    return pick, {"picked": pick, "table": {str(k): v for k, v in table.items()}}

@@ -216,3 +216,32 @@ def test_autotune_from_a_supplied_start(gm):
     buf = (ct.c_float * gm.TUNE_CANDIDATES)()
     assert lib.gm_autotune_from(ct.byref(cfg), wl.C, wl.ntot, gm._ptr(off), gm._ptr(x), gm._ptr(v), 0,
                                 gm._ptr(a), None, None, 0, buf, None) == gm.GM_ERR_ARG
+
+
+def test_kernel_trace_times_each_kernel(gm):
+    """gm_trace_begin / gm_trace_end: per-kernel device times (CUDA events on
+    the launching stream) of a learned-start compress and a reconstruct;
+    nothing is recorded inside a graph capture."""
+    wl = workloads.mixture_1d1v(C=64, mean_n=400, clip=(50, 900), seed=5)
+    cfg = gm.config(wl.params)
+    off, x, v, a = inputs(wl)
+    fit = gm.gm_compress(cfg, off, x, v, a)
+    K0 = torch.ones(wl.C, dtype=torch.int32, device="cuda")
+    K0[::2] = 2  # half the cells start with two components: both kernels run
+    torch.cuda.synchronize()
+    with gm.Trace() as tr:
+        out = gm.gm_compress(cfg, off, x, v, a, init_K=K0, init_params=fit["params"])
+        gm.gm_reconstruct(cfg, out["K"], out["params"], out["W"], out["rho_target"], off, n_out=wl.ntot)
+    t = tr.times
+    for k in ("em_k1_kernel", "em_kernel", "recon_stats_kernel", "recon_emit_kernel", "assemble_kernel"):
+        assert k in t and t[k][0] > 0.0 and t[k][1] == 1, (k, t)
+    assert any(k.startswith("deposit") for k in t)
+    # captured launches are not traced
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        g = gm.Graph(stream)
+        with gm.Trace() as tr2:
+            with g:
+                gm.gm_compress(cfg, off, x, v, a, stream=stream, out=out)
+        g.close()
+    assert tr2.times == {}
