@@ -1211,6 +1211,139 @@ def run_mesh2d(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# the learned initialisation's own evaluation: train on cells of the 1D-1V
+# batch's generator lifted to 3V and of the 1D-3V generator, evaluate on
+# held-out 1D-3V cells against plain EM
+# ---------------------------------------------------------------------------
+C4_DESC = ("learned init, 1D-3V: network trained on cells fitted by plain EM, half from the 1D-1V "
+           "mixture generator lifted to 3V (isotropic y, z), half from the 2048 x 4000 bi-Maxwellian "
+           "generator; inference + EM on held-out bi-Maxwellian cells (4000 particles each, seed + 1000) "
+           "against plain EM on the eq. (lnL-GM) objective and the sweep count")
+
+
+def run_c4(args):
+    """The learned initialisation evaluated as its own configuration:
+    training cells from two generator families, evaluation cells held out;
+    reports per-cell objective and sweeps of the learned start against
+    plain EM, and both paths' compress throughput."""
+    import torch
+    torch.cuda.set_device(0)
+    device = torch.device("cuda", 0)
+    from paper_2007_12273_gb300 import build as gbuild
+    from paper_2007_12273_gb300 import gm, learned
+    gbuild.build()
+    gm.load()
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    train_cells = args.train_cells or 200704
+    eval_cells = args.cells or 65536
+    # ---- training set (untimed) -------------------------------------------
+    t0 = time.perf_counter()
+    feats, Ts, Mks = [], [], []
+    nchunk = max(2, train_cells // 4096)
+    calib = None
+    cfg = None
+    for ch in range(nchunk):
+        seed = workloads.GEN_SEED_BASE + 50000 + ch
+        if ch % 2 == 0:
+            tw = workloads.mixture_lifted_3v(C=4096, seed=seed)
+        else:
+            tw = workloads.bimaxwellian_1d3v(C=4096, ppc=4000, seed=seed)
+        if cfg is None:
+            cfg = gm.config(tw.params)
+        dev_tw = (t(tw.cell_off), t(tw.x), t(tw.v), t(tw.alpha))
+        f_, T_, M_, fit_ = learned.fit_targets(cfg, *dev_tw)
+        feats.append(f_)
+        Ts.append(T_)
+        Mks.append(M_)
+        if ch % 2 == 1:
+            calib = (dev_tw, fit_["lnL"].clone())
+        del dev_tw
+    feat, T, Mk = torch.cat(feats), torch.cat(Ts), torch.cat(Mks)
+    torch.cuda.synchronize()
+    t_fit = time.perf_counter() - t0
+    net = gm.Net(3, cfg.Kmax)
+    net.init_weights(seed=1)
+    hist = learned.train(net, feat, T, Mk, epochs=args.epochs, batch=1024, lr=1e-3)
+    thr, calib_info = learned.calibrate_presence(net, cfg, *calib[0], calib[1])
+    if args.presence_logit is not None:
+        thr = args.presence_logit
+    del feat, T, Mk, feats, Ts, Mks, calib
+    # ---- held-out evaluation cells -------------------------------------------
+    ew = workloads.bimaxwellian_1d3v(C=eval_cells, ppc=4000, seed=workloads.GEN_SEED_BASE + 2 + 1000)
+    off, x, v, a = t(ew.cell_off), t(ew.x), t(ew.v), t(ew.alpha)
+    ecfg = gm.config(ew.params)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=device)
+
+    def timed(fn, steps):
+        out = fn(None)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            fn(out)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        return out, sum(e0.elapsed_time(e1) for e0, e1 in evs) / steps
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    plain, ms_plain = timed(lambda o: gm.gm_compress(ecfg, off, x, v, a, stream=stream, out=o), args.steps)
+    bufs = {}
+
+    def learned_step(o):
+        f_, w_ = gm.gm_features(ecfg, off, v, a, stream=stream, out=bufs.get("f"))
+        bufs["f"] = (f_, w_)
+        y_ = net.forward(f_, out=bufs.get("y"), stream=stream)
+        bufs["y"] = y_
+        K0, prm = gm.gm_mlp_decode(ecfg, y_, w_, off, stream=stream, presence_logit=thr, dest=bufs.get("d"))
+        bufs["d"] = (K0, prm)
+        return gm.gm_compress(ecfg, off, x, v, a, stream=stream, out=o, init_K=K0, init_params=prm)
+
+    lrn, ms_learned = timed(learned_step, args.steps)
+    clk = clocks.stop()
+    n = ew.ntot
+    Lp, Ll = plain["lnL"].cpu().numpy(), lrn["lnL"].cpu().numpy()
+    Kp, Kl = plain["K"].cpu().numpy(), lrn["K"].cpu().numpy()
+    K0 = bufs["d"][0].cpu().numpy()
+    sp, sl = plain["sweeps"].cpu().numpy(), lrn["sweeps"].cpu().numpy()
+    reach = Ll >= Lp - 1e-4 * np.abs(Lp)
+    cfg2 = gm.config(dict(ew.params, seed=int(ew.params.get("seed", 1)) + 1000))
+    L2 = gm.gm_compress(cfg2, off, x, v, a, stream=stream)["lnL"].cpu().numpy()
+    short = ~reach
+    result = {
+        "metric": "c4: learned-init vs plain EM, compress particles/s on held-out 1D-3V cells",
+        "value": n / (ms_learned * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": 1, "ms_per_step": ms_learned, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+        "config": {"workload": C4_DESC, "train_cells": int(nchunk * 4096), "eval_cells": eval_cells,
+                   "eval_particles": n, "presence_threshold": thr,
+                   "l2": "inputs > L2 and a 252 MB flush between timed steps", "launch": "direct calls"},
+        "training": {"fit_seconds": t_fit, "train_seconds": hist["seconds"], "epochs": args.epochs,
+                     "adam_steps": hist["steps"], "loss_first": hist["loss"][0], "loss_last": hist["loss"][-1],
+                     "presence_calibration": calib_info},
+        "plain": {"value": n / (ms_plain * 1e-3), "ms": ms_plain, "sweeps_mean": float(sp.mean()),
+                  "Kbar": float(Kp.mean()), "maxsweeps_frac": float(np.mean((plain["status"].cpu().numpy() & 1) != 0))},
+        "learned": {"value": n / (ms_learned * 1e-3), "ms": ms_learned, "sweeps_mean": float(sl.mean()),
+                    "Kbar": float(Kl.mean()), "K0bar": float(K0.mean()),
+                    "maxsweeps_frac": float(np.mean((lrn["status"].cpu().numpy() & 1) != 0))},
+        "objective": {"reaches_plain_L_1e-4": float(reach.mean()),
+                      "mean_lnL_minus_plain": float(np.mean(Ll - Lp)),
+                      "median_rel_shortfall": float(np.median(((Lp - Ll) / np.abs(Lp))[short])) if short.any() else 0.0,
+                      "short_cells_with_K_below_plain": float(np.mean(Kl[short] < Kp[short])) if short.any() else 0.0,
+                      "short_cells_with_K0_below_plain": float(np.mean(K0[short] < Kp[short])) if short.any() else 0.0,
+                      "other_seed_reaches_plain_L_1e-4": float(np.mean(L2 >= Lp - 1e-4 * np.abs(Lp)))},
+        "gpu_launches": 8 * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(result), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1244,7 +1377,14 @@ def main(argv=None):
     ap.add_argument("--standard", action="store_true",
                     help="the acceleration study: standard EM with random or K-means start, "
                          "with or without Anderson acceleration (one GPU)")
+    ap.add_argument("--c4", action="store_true",
+                    help="the learned initialisation's evaluation: train on 200704 cells of two "
+                         "generator families, evaluate on 65536 held-out 1D-3V cells (one GPU)")
     args = ap.parse_args(argv)
+    if args.c4 and args.impl != "reference":
+        if args.epochs == 60 and not any(a.startswith("--epochs") for a in (argv or sys.argv[1:])):
+            args.epochs = 20
+        return run_c4(args)
     if args.standard and args.impl != "reference":
         return run_standard(args)
     if args.mesh2d and args.impl != "reference":

@@ -33,6 +33,32 @@ __device__ __forceinline__ int warp_rs_lane(int q) {
   return l;
 }
 
+// The Cholesky floor test of a symmetric D x D matrix (upper triangle S),
+// by its L~ diag(p) L~^T pivots p_i (the squared Cholesky diagonal, FP64,
+// two reciprocals and no square root): every p_i sc2_i > fl and p_i <
+// 1e300; on success det = prod p_i.  (sc2 = 1 for a matrix in original
+// coordinates; the coordinate scales squared for a whitened one, as in
+// chol_whitened.)
+template <int D>
+__device__ __forceinline__ bool ldl_floor(const double* S, const double* sc2, double fl, double& det) {
+  const double p0 = S[0];
+  if (!(p0 * sc2[0] > fl) || !(p0 < 1e300)) return false;
+  if (D == 1) {
+    det = p0;
+    return true;
+  }
+  const double r0 = rcp_nr(p0);
+  const double l10 = S[1] * r0, l20 = S[2] * r0;
+  const double p1 = fma(-l10, S[1], S[3]);
+  if (!(p1 * sc2[1] > fl) || !(p1 < 1e300)) return false;
+  const double r1 = rcp_nr(p1);
+  const double e12 = fma(-l20, S[1], S[4]);
+  const double p2 = fma(-(e12 * r1), e12, fma(-l20, S[2], S[5]));
+  if (!(p2 * sc2[D - 1] > fl) || !(p2 < 1e300)) return false;
+  det = p0 * p1 * p2;
+  return true;
+}
+
 struct K1Params {
   int64_t C, n;
   const int64_t* cell_off;
@@ -112,7 +138,7 @@ __global__ void __launch_bounds__(NW * 32) em_k1_kernel(K1Params a) {
       continue;
     }
     // mean and covariance (every lane: the values are warp-uniform)
-    const double rW = 1.0 / W;
+    const double rW = rcp_nr(W);
     double mean[D], dm[D], cov[NM];
 #pragma unroll
     for (int d = 0; d < D; ++d) {
@@ -127,33 +153,17 @@ __global__ void __launch_bounds__(NW * 32) em_k1_kernel(K1Params a) {
         for (int y = x; y < D; ++y, ++t) cov[t] = fma(-dm[x], dm[y], res[1 + D + t] * rW);
     }
     // the covariance floor 1e-13 sum_d (cov_dd + mean_d^2) (degenerate cell)
-    // and, on success, ln|Sigma| = sum of the pivots' logs
+    // and, on success, |Sigma| = the product of the pivots
     int ok = 1;
-    double logdet = 0.0;
+    double det = 1.0;
     if (lane == 0) {
       double scale2 = 0.0;
       for (int d = 0; d < D; ++d) scale2 += cov[tri<D>(d, d)] + mean[d] * mean[d];
-      const double fl = 1e-13 * scale2;
-      double L2[3][3] = {{0}};
-      double piv = 1.0;
-      for (int x = 0; x < D && ok; ++x)
-        for (int y = 0; y <= x && ok; ++y) {
-          double sv = cov[tri<D>(y, x)];
-          for (int m = 0; m < y; ++m) sv -= L2[x][m] * L2[y][m];
-          if (x == y) {
-            if (!(sv > fl) || !(sv < 1e300)) {
-              ok = 0;
-            } else {
-              L2[x][x] = sqrt(sv);
-              piv *= sv;
-            }
-          } else {
-            L2[x][y] = sv / L2[y][y];
-          }
-        }
-      if (ok) logdet = log(piv);
+      const double one[3] = {1.0, 1.0, 1.0};
+      ok = ldl_floor<D>(cov, one, 1e-13 * scale2, det);
     }
     ok = __shfl_sync(0xffffffffu, ok, 0);
+    det = __shfl_sync(0xffffffffu, det, 0);
     if (!ok) {  // degenerate: the cell's moments, flagged
       for (int i = lane; i < a.Kmax * P; i += 32) {
         double val = 0.0;
@@ -173,14 +183,15 @@ __global__ void __launch_bounds__(NW * 32) em_k1_kernel(K1Params a) {
       continue;
     }
     // ---- the supplied component: valid (weight > 0, Cholesky floor in
-    // whitened coordinates) and not capped away by N - T K / 2 > 0 --------
+    // whitened coordinates, as chol_whitened) and not capped away by
+    // N - T K / 2 > 0 ------------------------------------------------------
     double sc[D], isc[D];
     {
-      // lane d < D takes coordinate d's scale (one sqrt and one division
+      // lane d < D takes coordinate d's scale (one sqrt and one reciprocal
       // for all D)
       double cdd = cov[0];
       if (D == 3) cdd = lane == 1 ? cov[tri<D>(1, 1)] : (lane == 2 ? cov[tri<D>(2, 2)] : cov[0]);
-      const double s1 = sqrt(cdd), i1 = 1.0 / s1;
+      const double s1 = sqrt(cdd), i1 = rcp_nr(s1);
 #pragma unroll
       for (int d = 0; d < D; ++d) {
         sc[d] = __shfl_sync(0xffffffffu, s1, d);
@@ -190,18 +201,25 @@ __global__ void __launch_bounds__(NW * 32) em_k1_kernel(K1Params a) {
     int valid = 0;
     if (lane == 0) {
       const double* r = a.init_prm + (size_t)j * a.Kmax * P;
-      double mw[D], Sw[NM], Lw[3][3], rw[3];
-      for (int d = 0; d < D; ++d) mw[d] = (r[1 + d] - mean[d]) * isc[d];
+      double Sw[NM], sc2[3], scale2 = 0.0, dw;
+      for (int d = 0; d < D; ++d) {
+        const double m = mean[d] + sc[d] * ((r[1 + d] - mean[d]) * isc[d]);
+        sc2[d] = sc[d] * sc[d];
+        scale2 += sc2[d] * (r[1 + D + tri<D>(d, d)] * isc[d] * isc[d]) + m * m;
+      }
       int q = 0;
       for (int x = 0; x < D; ++x)
         for (int yy = x; yy < D; ++yy, ++q) Sw[q] = r[1 + D + q] * isc[x] * isc[yy];
-      valid = (r[0] > 0.0) && chol_whitened<D, double, double>(Sw, mw, mean, sc, Lw, rw);
+      valid = (r[0] > 0.0) && ldl_floor<D>(Sw, sc2, 1e-13 * scale2, dw);
     }
     valid = __shfl_sync(0xffffffffu, valid, 0);
     if (!valid) {  // no component left: the paper's initialisation, by EM
       if (lane == 0) a.list[atomicAdd(a.list_count, 1u)] = (unsigned int)j;
       continue;
     }
+    // ln|Sigma| (lane 0) and ln N (lane 1) in one logarithm
+    const double lg = log(lane == 1 ? (double)N : det);
+    const double logdet = __shfl_sync(0xffffffffu, lg, 0), logN = __shfl_sync(0xffffffffu, lg, 1);
     // ---- closed form ---------------------------------------------------------
     for (int i = lane; i < a.Kmax * P; i += 32) {
       double val = 0.0;
@@ -215,7 +233,7 @@ __global__ void __launch_bounds__(NW * 32) em_k1_kernel(K1Params a) {
       a.K_out[j] = 1;
       a.W_out[j] = W;
       a.lnL_out[j] = -0.5 * Nd * ((double)D * 1.8378770664093454836 + logdet + (double)D) -
-                     0.5 * (double)T * log(Nd);
+                     0.5 * (double)T * logN;
       if (a.sweeps_out) a.sweeps_out[j] = 1;
       if (a.kwork_out) a.kwork_out[j] = 0;
       a.status_out[j] = too_few;

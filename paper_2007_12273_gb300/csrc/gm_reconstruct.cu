@@ -44,26 +44,64 @@ __global__ void __launch_bounds__(NW * 32) recon_stats_kernel(int64_t C, int Kma
     double acc[NA];
 #pragma unroll
     for (int i = 0; i < NA; ++i) acc[i] = 0.0;
-    for (int64_t i = lane; i < n; i += 32) {
-      uint64_t m0;
-      double w[D];
-      sample_particle<D>(rc, j, i, seed, m0, w);
-      const double sx = centred52(m0);
-      if (order == 1) {
-        acc[0] += sx < 0.0 ? -sx : 0.0;
-        acc[1] += sx > 0.0 ? sx : 0.0;
-      } else {
-        acc[0] += sx;
-        acc[1] = fma(sx, sx, acc[1]);
+    if (rc.K == 1) {
+      // one component: w = dz + f with one dz for the cell, so the sums of
+      // w and |w|^2 follow from those of f (FP64 sums of the FP32 f):
+      // sum w = n dz + sum f, sum |w|^2 = n |dz|^2 + 2 dz . sum f + sum |f|^2
+      for (int64_t i = lane; i < n; i += 32) {
+        uint64_t m0;
+        int z;
+        float f[D];
+        sample_f<D>(rc, j, i, seed, m0, z, f);
+        const double sx = centred52(m0);
+        if (order == 1) {
+          acc[0] += sx < 0.0 ? -sx : 0.0;
+          acc[1] += sx > 0.0 ? sx : 0.0;
+        } else {
+          acc[0] += sx;
+          acc[1] = fma(sx, sx, acc[1]);
+        }
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          const double fd = f2d_exact(f[d]);
+          acc[2 + d] += fd;
+          acc[2 + D] = fma(fd, fd, acc[2 + D]);
+        }
       }
+#pragma unroll
+      for (int i = 0; i < NA; ++i) acc[i] = warp_sum(acc[i]);
+      const double nd = (double)n;
+      double dzf = 0.0, dz2 = 0.0;
 #pragma unroll
       for (int d = 0; d < D; ++d) {
-        acc[2 + d] += w[d];
-        acc[2 + D] = fma(w[d], w[d], acc[2 + D]);
+        const double dz = rc.dz[0][d];
+        dzf = fma(dz, acc[2 + d], dzf);
+        dz2 = fma(dz, dz, dz2);
+        acc[2 + d] = fma(nd, dz, acc[2 + d]);
       }
-    }
+      acc[2 + D] = fma(nd, dz2, fma(2.0, dzf, acc[2 + D]));
+    } else {
+      for (int64_t i = lane; i < n; i += 32) {
+        uint64_t m0;
+        double w[D];
+        sample_particle<D>(rc, j, i, seed, m0, w);
+        const double sx = centred52(m0);
+        if (order == 1) {
+          acc[0] += sx < 0.0 ? -sx : 0.0;
+          acc[1] += sx > 0.0 ? sx : 0.0;
+        } else {
+          acc[0] += sx;
+          acc[1] = fma(sx, sx, acc[1]);
+        }
 #pragma unroll
-    for (int i = 0; i < NA; ++i) acc[i] = warp_sum(acc[i]);
+        for (int d = 0; d < D; ++d) {
+          acc[2 + d] += w[d];
+          acc[2 + D] = fma(w[d], w[d], acc[2 + D]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NA; ++i) acc[i] = warp_sum(acc[i]);
+    }
     if (lane == 0) {
       double* cs = cstat + (size_t)j * NV;
       const double nd = (double)n;
@@ -270,18 +308,37 @@ __global__ void __launch_bounds__(NW * 32) recon_emit_kernel(
     __syncwarp();
     const double aa = rc.a, an = rc.alpha_new;
     const int skip = rc.skip;
-    for (int64_t i = lane; i < n; i += 32) {
-      uint64_t m0;
-      double w[D];
-      sample_particle<D>(rc, j, i, seed, m0, w);
-      const double u0 = uniform_pos52(m0);
-      x_out[o + i] = __dmul_rn(__dadd_rn((double)j, u0), dx);
-      alpha_out[o + i] = an;
+    if (rc.K == 1) {
+      // one component: v = u + a (dz + f + beta) = c + a f with one
+      // c = u + a (dz + beta) for the cell (a = 1, beta = 0 when skipped)
+      double cv[D];
 #pragma unroll
-      for (int d = 0; d < D; ++d) {
-        // v = u + w; projected: u + a (w + beta) (eqs. alpha, beta)
-        const double vp = skip ? rc.u[d] + w[d] : fma(aa, w[d] + rc.beta[d], rc.u[d]);
-        v_out[(int64_t)d * n_out + o + i] = vp;
+      for (int d = 0; d < D; ++d) cv[d] = fma(aa, rc.dz[0][d] + rc.beta[d], rc.u[d]);
+      for (int64_t i = lane; i < n; i += 32) {
+        uint64_t m0;
+        int z;
+        float f[D];
+        sample_f<D>(rc, j, i, seed, m0, z, f);
+        const double u0 = uniform_pos52(m0);
+        x_out[o + i] = __dmul_rn(__dadd_rn((double)j, u0), dx);
+        alpha_out[o + i] = an;
+#pragma unroll
+        for (int d = 0; d < D; ++d) v_out[(int64_t)d * n_out + o + i] = fma(aa, f2d_exact(f[d]), cv[d]);
+      }
+    } else {
+      for (int64_t i = lane; i < n; i += 32) {
+        uint64_t m0;
+        double w[D];
+        sample_particle<D>(rc, j, i, seed, m0, w);
+        const double u0 = uniform_pos52(m0);
+        x_out[o + i] = __dmul_rn(__dadd_rn((double)j, u0), dx);
+        alpha_out[o + i] = an;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          // v = u + w; projected: u + a (w + beta) (eqs. alpha, beta)
+          const double vp = skip ? rc.u[d] + w[d] : fma(aa, w[d] + rc.beta[d], rc.u[d]);
+          v_out[(int64_t)d * n_out + o + i] = vp;
+        }
       }
     }
     __syncwarp();

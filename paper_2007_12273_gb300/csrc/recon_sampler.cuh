@@ -132,16 +132,17 @@ __device__ __forceinline__ float bm_radius(uint64_t m) {
 }
 
 // particle i of cell j (Sec. 2.4, eq. mix-dist-1): the 52-bit integer m0
-// of its position's uniform u0 = (m0 + 1/2) 2^-52 (x = (j + u0) dx) and
-// w = v - u (u the mixture mean), w = (mu_z - u) + L_z xi with L_z xi in FP32
+// of its position's uniform u0 = (m0 + 1/2) 2^-52 (x = (j + u0) dx), its
+// component z (the categorical draw) and f = L_z xi (FP32), so that
+// w = v - u = (mu_z - u) + f
 template <int D>
-__device__ __forceinline__ void sample_particle(const RecCell<D>& rc, int64_t j, int64_t i,
-                                                uint64_t seed, uint64_t& m0, double (&w)[D]) {
+__device__ __forceinline__ void sample_f(const RecCell<D>& rc, int64_t j, int64_t i, uint64_t seed,
+                                         uint64_t& m0, int& z, float (&f)[D]) {
   const u32x4 r0 = philox_draw(seed, (uint32_t)i, kTagSample | 0u, j);
   m0 = bits52(r0.x, r0.y);
   const long long m1x2 = 2 * (long long)bits52(r0.z, r0.w) + 1;
   const int K = rc.K;
-  int z = K - 1;
+  z = K - 1;
   for (int k = 0; k < K; ++k)
     if (m1x2 < rc.thr[k]) { z = k; break; }
   // Box-Muller (Box & Muller 1958) on (u2, u3) [and (u4, u5) for D = 3]
@@ -160,17 +161,33 @@ __device__ __forceinline__ void sample_particle(const RecCell<D>& rc, int64_t j,
     xi[2] = rr * cospif(2.0f * half_ulp52_f(bits52(r2.z, r2.w)));
   }
   if (K == 0) {
-    for (int d = 0; d < D; ++d) w[d] = -rc.u[d];
+    for (int d = 0; d < D; ++d) f[d] = 0.0f;
     return;
   }
   const float* L = rc.Lf[z];
   if (D == 1) {
-    w[0] = rc.dz[z][0] + f2d_exact(L[0] * xi[0]);
+    f[0] = L[0] * xi[0];
   } else {
-    w[0] = rc.dz[z][0] + f2d_exact(L[0] * xi[0]);
-    w[1] = rc.dz[z][1] + f2d_exact(fmaf(L[2], xi[1], L[1] * xi[0]));
-    w[2] = rc.dz[z][2] + f2d_exact(fmaf(L[5], xi[2], fmaf(L[4], xi[1], L[3] * xi[0])));
+    f[0] = L[0] * xi[0];
+    f[1] = fmaf(L[2], xi[1], L[1] * xi[0]);
+    f[2] = fmaf(L[5], xi[2], fmaf(L[4], xi[1], L[3] * xi[0]));
   }
+}
+
+// the same particle with w = v - u in FP64: (mu_z - u) + f (w = -u for a
+// cell without a mixture)
+template <int D>
+__device__ __forceinline__ void sample_particle(const RecCell<D>& rc, int64_t j, int64_t i,
+                                                uint64_t seed, uint64_t& m0, double (&w)[D]) {
+  int z;
+  float f[D];
+  sample_f<D>(rc, j, i, seed, m0, z, f);
+  if (rc.K == 0) {
+    for (int d = 0; d < D; ++d) w[d] = -rc.u[d];
+    return;
+  }
+#pragma unroll
+  for (int d = 0; d < D; ++d) w[d] = rc.dz[z][d] + f2d_exact(f[d]);
 }
 
 // the 52 leading bits of the y uniform of particle i of cell j on a 2D mesh

@@ -4,19 +4,30 @@
 //   C[M,N] = A[M,K] . B[N,K]^T   (+ bias[N]) (ReLU) (* (mask > 0))
 //
 // A and B are BF16, "K-major" (row-major with K contiguous); accumulation is
-// FP32 in tensor memory (TMEM).  One CTA (4 warps) computes a 128 x BN tile:
-// the K dimension is walked in chunks of 64; each chunk of A (128 x 64) and
-// B (BN x 64) is staged in shared memory in the canonical no-swizzle
-// core-matrix layout (8 rows x 16 bytes per core matrix), one thread issues
-// four tcgen05.mma (K = 16 each) and commits them to an mbarrier; the
-// epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM lanes
-// 32w..32w+31 = tile rows) and applies bias / ReLU / mask.
+// FP32 in tensor memory (TMEM).  One CTA (4 warps) computes a 128 x BN tile,
+// walking K in chunks of 64 through an S-stage shared-memory ring:
+//   * thread 0 (warp 0) is the producer: per chunk one TMA tiled load
+//     (cp.async.bulk.tensor) of A (64 x 128) and one of B (64 x BN) with the
+//     128-byte swizzle, completing on the stage's "full" mbarrier;
+//   * thread 32 (warp 1) issues the four tcgen05.mma (K = 16 each) of a
+//     chunk once it has landed and commits them to the stage's "empty"
+//     mbarrier, which the producer waits on before refilling the stage;
+//   * the epilogue (all 4 warps) reads the accumulator with tcgen05.ld (warp
+//     w owns TMEM lanes 32w..32w+31 = tile rows) and applies bias / ReLU /
+//     mask.
+// Loads of later chunks overlap the MMAs of earlier ones.  The TMA fills
+// rows and K columns outside the matrices with zeros.
 //
-// Every wait on the mbarrier is bounded; on time-out the kernel records an
-// error flag, releases its TMEM and returns.
+// Every wait on an mbarrier is bounded; on time-out the kernel records an
+// error flag, waits (bounded) for its copies in flight, releases its TMEM
+// and returns.
 #include "gm_kernels.cuh"
 
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
 
 namespace gmcr {
 
@@ -30,16 +41,20 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// shared-memory matrix descriptor, no swizzle: start address, leading-
-// dimension byte offset (between core matrices adjacent along K) and stride
-// byte offset (between core matrices adjacent along M/N), all >> 4;
-// descriptor version 1 (bits 46-47)
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+// shared-memory matrix descriptor of a K-major operand in the 128-byte
+// swizzled layout the TMA writes (rows of 64 BF16 = 128 bytes, 8-row groups
+// of 1024 bytes): start address >> 4 (bits 0-13), leading-dimension offset
+// field 1 (unused by this layout), stride byte offset 1024 >> 4 between
+// 8-row groups (bits 32-45), descriptor version 1 (bit 46), layout type
+// "128-byte swizzle" (2, bits 61-63).  The K = 16 slice s of a chunk starts
+// 32 s bytes into each row; the stage buffers are 1024-byte aligned.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
   d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
   return d;
 }
 
@@ -64,6 +79,21 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   return false;
 }
 
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes)
+               : "memory");
+}
+
+// 2D tiled TMA load of the box at (x, y) (x the K coordinate: a multiple of
+// 64 elements, so 128-byte aligned) into shared memory, completing on mbar
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+
 template <int N>
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[N]) {
   static_assert(N == 16, "16 columns per load");
@@ -81,12 +111,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[N]) {
 
 }  // namespace
 
-// BN: tile columns (16..256, multiple of 16); TMEM columns = BN rounded up
-// to a power of two >= 32.
-template <int BN>
-__global__ void __launch_bounds__(128) tc_gemm_kernel(const __nv_bfloat16* __restrict__ A,
-                                                      const __nv_bfloat16* __restrict__ B, int M,
-                                                      int N, int K, int lda, int ldb,
+// BN: tile columns (32..256, a power of two); TMEM columns = BN rounded up
+// to a power of two >= 32; S: pipeline stages
+template <int BN, int S>
+__global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                      const __grid_constant__ CUtensorMap mapB,
+                                                      int M, int N, int K,
                                                       const float* __restrict__ bias, int relu,
                                                       const __nv_bfloat16* __restrict__ mask,
                                                       int ldm, float* __restrict__ Cf,
@@ -94,16 +124,18 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __nv_bfloat16* __res
                                                       int accumulate, unsigned int* err) {
   constexpr int TCOLS = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
   constexpr uint32_t IDESC = idesc_bf16(kBM, BN);
-  extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* sA = smem;                    // 128 x 64 bf16 = 16 KB
-  unsigned char* sB = smem + kBM * kBK * 2;    // BN x 64 bf16
-  __shared__ __align__(8) uint64_t mbar;
+  constexpr uint32_t A_BYTES = kBM * kBK * 2, B_BYTES = BN * kBK * 2;
+  constexpr uint32_t STAGE = A_BYTES + B_BYTES;  // a multiple of 1024
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // the stages start at the first 1024-byte boundary of the dynamic buffer
+  unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  __shared__ __align__(8) uint64_t full[S], empty[S], done;
   __shared__ uint32_t tmem_slot;
   __shared__ int failed;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
-  const uint32_t mbar_a = smem_u32(&mbar);
+  const int nk = (K + kBK - 1) / kBK;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
@@ -113,7 +145,11 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __nv_bfloat16* __res
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar_a));
+    for (int q = 0; q < S; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&full[q])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty[q])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&done)));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     failed = 0;
   }
@@ -122,40 +158,44 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __nv_bfloat16* __res
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = tmem_slot;
 
-  uint32_t phase = 0;
-  const int nk = (K + kBK - 1) / kBK;
-  for (int kc = 0; kc < nk; ++kc) {
-    const int k0 = kc * kBK;
-    // stage A (128 x 64) and B (BN x 64): 16-byte chunks; core matrix (i, j)
-    // (rows 8i.., K columns 8j..) at byte (i * 8 + j) * 128, row r % 8 at +16
-    for (int c = tid; c < (kBM + BN) * 8; c += 128) {
-      const bool isA = c < kBM * 8;
-      const int cc = isA ? c : c - kBM * 8;
-      const int r = cc >> 3, j = cc & 7;
-      const int gr = (isA ? m0 : n0) + r, gk = k0 + 8 * j;
-      uint4 val = make_uint4(0u, 0u, 0u, 0u);
-      const int rows = isA ? M : N;
-      if (gr < rows && gk + 8 <= K) {
-        const __nv_bfloat16* src = isA ? A + (size_t)gr * lda + gk : B + (size_t)gr * ldb + gk;
-        val = *reinterpret_cast<const uint4*>(src);
-      } else if (gr < rows && gk < K) {
-        __nv_bfloat16 t[8];
-        const __nv_bfloat16* src = isA ? A + (size_t)gr * lda : B + (size_t)gr * ldb;
-        for (int e = 0; e < 8; ++e) t[e] = (gk + e < K) ? src[gk + e] : __float2bfloat16(0.0f);
-        val = *reinterpret_cast<uint4*>(t);
+  if (tid == 0) {
+    // producer: chunk kc into stage kc % S, once the MMAs of chunk kc - S
+    // (the stage's previous content) have completed
+    int issued = 0;
+    for (int kc = 0; kc < nk; ++kc) {
+      const int st = kc % S;
+      if (kc >= S && !mbar_wait(smem_u32(&empty[st]), (uint32_t)((kc / S - 1) & 1))) {
+        failed = 1;
+        if (err) atomicOr(err, 1u);
+        break;
       }
-      unsigned char* dst = (isA ? sA : sB) + ((r >> 3) * 8 + j) * 128 + (r & 7) * 16;
-      *reinterpret_cast<uint4*>(dst) = val;
+      const uint32_t fb = smem_u32(&full[st]);
+      const uint32_t sa = smem_u32(smem + (size_t)st * STAGE);
+      mbar_expect_tx(fb, STAGE);
+      tma_load_2d(sa, &mapA, kc * kBK, m0, fb);
+      tma_load_2d(sa + A_BYTES, &mapB, kc * kBK, n0, fb);
+      issued = kc + 1;
     }
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
+    // on a time-out, wait (bounded) for the copies still in flight
+    if (failed)
+      for (int kc = (issued > S ? issued - S : 0); kc < issued; ++kc)
+        mbar_wait(smem_u32(&full[kc % S]), (uint32_t)((kc / S) & 1));
+  } else if (tid == 32) {
+    // MMA issuer: the four K = 16 MMAs of each landed chunk, committed to the
+    // stage's empty barrier; the last commit also signals the epilogue
+    for (int kc = 0; kc < nk; ++kc) {
+      const int st = kc % S;
+      if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((kc / S) & 1))) {
+        failed = 1;
+        if (err) atomicOr(err, 1u);
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+      const uint32_t a0 = smem_u32(smem + (size_t)st * STAGE), b0 = a0 + A_BYTES;
 #pragma unroll
       for (int s = 0; s < kBK / 16; ++s) {
-        const uint64_t ad = smem_desc(a0 + s * 256, 128, 1024);
-        const uint64_t bd = smem_desc(b0 + s * 256, 128, 1024);
+        const uint64_t ad = smem_desc_sw128(a0 + 32 * s);
+        const uint64_t bd = smem_desc_sw128(b0 + 32 * s);
         const uint32_t acc = (kc > 0 || s > 0) ? 1u : 0u;
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
@@ -164,18 +204,21 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __nv_bfloat16* __res
       }
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-              mbar_a)
+              smem_u32(&empty[st]))
           : "memory");
     }
-    // the MMAs of this chunk must finish before its tiles are overwritten
-    if (!mbar_wait(mbar_a, phase)) {
-      failed = 1;
-      if (err) atomicOr(err, 1u);
-    }
-    phase ^= 1u;
-    __syncthreads();
-    if (failed) break;
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+            smem_u32(&done))
+        : "memory");
   }
+  // the accumulator is complete once the last commit arrives (the commit
+  // tracks every earlier MMA of this thread)
+  if (!mbar_wait(smem_u32(&done), 0u)) {
+    failed = 1;
+    if (err) atomicOr(err, 1u);
+  }
+  __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 
   if (!failed) {
@@ -208,13 +251,52 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __nv_bfloat16* __res
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TCOLS));
 }
 
-size_t tc_gemm_smem(int bn) { return (size_t)(kBM + bn) * kBK * 2 + 1024; }
+template <int BN>
+constexpr int gemm_stages() { return BN >= 256 ? 3 : 4; }
+
+size_t tc_gemm_smem(int bn) {
+  const int S = bn >= 256 ? 3 : 4;
+  return (size_t)(kBM + bn) * kBK * 2 * S + 1024;
+}
+
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+// tensor map of a K-major BF16 matrix [rows][ld] (K valid columns): boxes
+// of 64 K x box_rows, 128-byte swizzle, zero fill outside
+bool make_map(CUtensorMap* map, const void* base, int rows, int K, int ld, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+}  // namespace
 
 cudaError_t launch_tc_gemm(const void* A, const void* B, int M, int N, int K, int lda, int ldb,
                            const float* bias, int relu, const void* mask, int ldm, float* Cf,
                            void* Cb, int ldc, unsigned int* err, cudaStream_t s, int accumulate) {
   if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
   int bn = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+  CUtensorMap mapA, mapB;
+  if (!make_map(&mapA, A, M, K, lda, kBM) || !make_map(&mapB, B, N, K, ldb, bn))
+    return cudaErrorInvalidValue;
   // at least 80 KB of shared memory per CTA keeps two CTAs (2 x 256 TMEM
   // columns) per SM at most, so a TMEM allocation never waits
   size_t smem = tc_gemm_smem(bn);
@@ -222,13 +304,12 @@ cudaError_t launch_tc_gemm(const void* A, const void* B, int M, int N, int K, in
   dim3 grid((M + kBM - 1) / kBM, (N + bn - 1) / bn);
 #define GM_TC_LAUNCH(BNV)                                                                        \
   {                                                                                              \
-    auto k = tc_gemm_kernel<BNV>;                                                                \
+    auto k = tc_gemm_kernel<BNV, gemm_stages<BNV>()>;                                             \
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
                                          (int)smem);                                             \
     if (e != cudaSuccess) return e;                                                              \
-    k<<<grid, 128, smem, s>>>((const __nv_bfloat16*)A, (const __nv_bfloat16*)B, M, N, K, lda,    \
-                              ldb, bias, relu, (const __nv_bfloat16*)mask, ldm, Cf,              \
-                              (__nv_bfloat16*)Cb, ldc, accumulate, err);                         \
+    k<<<grid, 128, smem, s>>>(mapA, mapB, M, N, K, bias, relu, (const __nv_bfloat16*)mask, ldm, \
+                              Cf, (__nv_bfloat16*)Cb, ldc, accumulate, err);                     \
   }
   if (bn == 32) GM_TC_LAUNCH(32)
   else if (bn == 64) GM_TC_LAUNCH(64)

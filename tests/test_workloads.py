@@ -34,6 +34,7 @@ def _check_layout(wl, D, v_dtype, dx):
     ("mixture_1d1v_uniform", dict(C=64), 1, np.float32, 1.0),
     ("bimaxwellian_1d3v", dict(C=16, ppc=500), 3, np.float32, 1.0),
     ("lognormal_1d3v", dict(C=256), 3, np.float32, 1.0),
+    ("mixture_lifted_3v", dict(C=32, mean_n=300), 3, np.float32, 1.0),
     ("weibel_2d3v", dict(Cx=4, Cy=3, ppc=100), 3, np.float32, None),
 ])
 def test_layout_determinism_and_seeds(name, kw, D, dt, dx):
@@ -153,3 +154,19 @@ def test_with_weights_and_resample_offsets():
     off = workloads.resample_offsets(base.cell_off)
     np.testing.assert_array_equal(off, base.cell_off)
     assert off is not base.cell_off and off.dtype == np.int64
+
+
+def test_lifted_mixture_is_isotropic_across_y_z_and_drifts_along_x():
+    # the 1D-1V batch lifted to 3V: drifts along x only; in y and z every
+    # cell is centred (a mixture of zero-mean Maxwellians), with the same
+    # spread in y and z, and no correlation between y and z
+    wl = workloads.mixture_lifted_3v(C=128, mean_n=2000)
+    for j in range(wl.C):
+        v = wl.v[:, wl.cell_off[j]:wl.cell_off[j + 1]].astype(np.float64)
+        n = v.shape[1]
+        sy, sz = v[1].std(), v[2].std()
+        assert abs(v[1].mean()) < 6 * sy / math.sqrt(n) and abs(v[2].mean()) < 6 * sz / math.sqrt(n)
+        assert 0.02 * 0.85 < sy < 0.1 * 1.15 and abs(sy / sz - 1.0) < 0.25
+        assert abs(np.corrcoef(v[1], v[2])[0, 1]) < 6 / math.sqrt(n)
+        assert -0.5 - 0.1 < v[0].mean() < 0.5 + 0.1
+    assert wl.params["Kmax"] == 10 and wl.params["D"] == 3

@@ -254,6 +254,35 @@ def with_weights(wl: Workload, seed=7, lo=0.5, hi=1.5) -> Workload:
 
 # Named workloads: the first is small enough for the oracle to fit in
 # seconds; the others are the batched / 3V / full-scale cases.
+def mixture_lifted_3v(C=4096, mean_n=2000, clip=(200, 8000), seed=GEN_SEED_BASE + 6,
+                      v_dtype=np.float32, Kmax=10, shape_order=2):
+    """The 1D-1V batch's cells lifted to 3V: each cell a random mixture of 1-4
+    Maxwellians drifting along x (drifts U[-0.5, 0.5], Dirichlet(1) weights)
+    with isotropic thermal speed vth U[0.02, 0.1] in x, y and z; counts
+    Poisson(mean_n) clipped to ``clip``.  Mesh: dx = 1, L = C."""
+    rng = np.random.default_rng(seed)
+    n = np.clip(rng.poisson(mean_n, C), clip[0], clip[1]).astype(np.int64)
+    m = rng.integers(1, 5, C)
+    drift = rng.uniform(-0.5, 0.5, (C, 4))
+    vth = rng.uniform(0.02, 0.1, (C, 4))
+    w = rng.exponential(1.0, (C, 4)) * (np.arange(4)[None, :] < m[:, None])
+    w /= w.sum(axis=1, keepdims=True)
+    cw = np.cumsum(w, axis=1)
+    cw[:, -1] = 1.0 + 1e-12
+    cell = np.repeat(np.arange(C), n)
+    u = rng.random(cell.shape[0])
+    comp = np.minimum((u[:, None] >= cw[cell]).sum(axis=1), m[cell] - 1)
+    th = vth[cell, comp]
+    z = rng.standard_normal((3, cell.shape[0]))
+    v = np.empty((3, cell.shape[0]))
+    v[0] = drift[cell, comp] + th * z[0]
+    v[1] = th * z[1]
+    v[2] = th * z[2]
+    x = _uniform_positions(rng, n, 1.0)
+    return Workload("mixture_lifted_3v", _offsets(n), x, np.ascontiguousarray(v.astype(v_dtype)),
+                    np.ones(cell.shape[0]), method_params(3, Kmax, shape_order, float(C)))
+
+
 def get(name: str, **kw) -> Workload:
     if name == "two_stream_1d1v":
         return two_stream_1d1v(**kw)
@@ -267,6 +296,8 @@ def get(name: str, **kw) -> Workload:
         return lognormal_1d3v(**kw)
     if name == "weibel_2d3v":
         return weibel_2d3v(**kw)
+    if name == "mixture_lifted_3v":
+        return mixture_lifted_3v(**kw)
     raise KeyError(name)
 
 
