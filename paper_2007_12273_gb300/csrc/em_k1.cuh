@@ -59,6 +59,84 @@ __device__ __forceinline__ bool ldl_floor(const double* S, const double* sc2, do
   return true;
 }
 
+// ---------------------------------------------------------------------------
+// Moments of an equal-weight cell on the integer pipe (fixq and the 128-bit
+// helpers are in gm_common.cuh).  With every weight
+// equal to alpha_0 the sums are alpha_0 times sums of d = v - s (s the
+// first particle), and the FP32 velocities are integers times a power of
+// two: each is taken as v / 2^eq rounded to an integer with eq = (the
+// cell's largest exponent in that dimension) + 1 - 54, which is exact for
+// every velocity within 2^-30 of the largest and within 2^-55 of it
+// otherwise.  The sums of d and of d_x d_y are then exact 128-bit integer
+// sums (|d| < 2^55, d^2 < 2^110, at most 2^14 particles), converted to FP64
+// once per cell -- no FP64 arithmetic per particle, where GB300's FP64 pipe
+// (1/64 of the FP32 rate) bounds the FP64 sums.
+// ---------------------------------------------------------------------------
+// the FP64 sums [sum alpha, sum alpha d (D), sum alpha d d^T (upper, NM)] of
+// an equal-weight cell (weight a0, n particles, velocities v[d * ldv + p],
+// shift sh = v[., 0]) on the integer pipe, lane-parallel over particles;
+// every lane returns them.  Returns false (nothing written) when a velocity
+// is not finite.
+template <int D>
+__device__ bool fixed_moments(const float* __restrict__ v, int64_t ldv, int n, double a0, int lane,
+                              double* res) {
+  constexpr int NM = D * (D + 1) / 2;
+  // the largest biased exponent per dimension
+  int emax[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) emax[d] = 0;
+  for (int p = lane; p < n; p += 32)
+#pragma unroll
+    for (int d = 0; d < D; ++d) emax[d] = max(emax[d], (int)((__float_as_uint(v[d * ldv + p]) >> 23) & 0xFFu));
+  int eq[D];
+  bool ok = true;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) emax[d] = max(emax[d], __shfl_xor_sync(0xffffffffu, emax[d], o));
+    ok = ok && emax[d] < 255;
+    eq[d] = (emax[d] ? emax[d] - 127 : -126) + 1 - kFixBits;
+  }
+  if (!ok) return false;
+  long long s0[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) s0[d] = fixq(v[d * ldv], eq[d]);
+  __int128 s1[D], s2[NM];
+#pragma unroll
+  for (int d = 0; d < D; ++d) s1[d] = 0;
+#pragma unroll
+  for (int t = 0; t < NM; ++t) s2[t] = 0;
+  for (int p = lane; p < n; p += 32) {
+    long long dq[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      dq[d] = fixq(v[d * ldv + p], eq[d]) - s0[d];
+      s1[d] += (__int128)dq[d];
+    }
+    int t = 0;
+#pragma unroll
+    for (int x = 0; x < D; ++x)
+#pragma unroll
+      for (int y = x; y < D; ++y, ++t) s2[t] += (__int128)dq[x] * (__int128)dq[y];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) s1[d] += shfl_xor_i128(s1[d], o);
+#pragma unroll
+    for (int t = 0; t < NM; ++t) s2[t] += shfl_xor_i128(s2[t], o);
+  }
+  res[0] = (double)n * a0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) res[1 + d] = a0 * i128_to_f64(s1[d], eq[d]);
+  int t = 0;
+#pragma unroll
+  for (int x = 0; x < D; ++x)
+#pragma unroll
+    for (int y = x; y < D; ++y, ++t) res[1 + D + t] = a0 * i128_to_f64(s2[t], eq[x] + eq[y]);
+  return true;
+}
+
 struct K1Params {
   int64_t C, n;
   const int64_t* cell_off;
@@ -96,32 +174,47 @@ __global__ void __launch_bounds__(NW * 32) em_k1_kernel(K1Params a) {
       if (lane == 0) a.list[atomicAdd(a.list_count, 1u)] = (unsigned int)j;
       continue;
     }
-    // ---- moments about the first particle (FP64) -------------------------
+    // ---- moments about the first particle ------------------------------
     double sh[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) sh[d] = N > 0 ? to_f64(vin[(int64_t)d * a.n + off]) : 0.0;
-    double acc[NP];
-#pragma unroll
-    for (int i = 0; i < NP; ++i) acc[i] = 0.0;
-    for (int p = lane; p < N; p += 32) {
-      const double al = a.alpha[off + p];
-      double dv[D];
-#pragma unroll
-      for (int d = 0; d < D; ++d) dv[d] = to_f64(vin[(int64_t)d * a.n + off + p]) - sh[d];
-      acc[0] += al;
-      int t = 1 + D;
-#pragma unroll
-      for (int x = 0; x < D; ++x) {
-        const double ad = al * dv[x];
-        acc[1 + x] += ad;
-#pragma unroll
-        for (int y = x; y < D; ++y, ++t) acc[t] = fma(ad, dv[y], acc[t]);
+    double res[NS];
+    bool fixed = false;
+    if constexpr (sizeof(VT) == 4) {
+      // equal weights (bit for bit) and at most 2^14 particles: exact sums
+      // on the integer pipe
+      if (N > 0 && N <= kFixMaxN) {
+        const long long a0b = __double_as_longlong(a.alpha[off]);
+        bool same = true;
+        for (int p = lane; p < N; p += 32) same = same && (__double_as_longlong(a.alpha[off + p]) == a0b);
+        if (__all_sync(0xffffffffu, same) && __longlong_as_double(a0b) > 0.0)
+          fixed = fixed_moments<D>(reinterpret_cast<const float*>(vin) + off, a.n, N,
+                                   __longlong_as_double(a0b), lane, res);
       }
     }
-    warp_rs_d<NP>(acc, lane);
-    double res[NS];
+    if (!fixed) {  // FP64 sums
+      double acc[NP];
 #pragma unroll
-    for (int q = 0; q < NS; ++q) res[q] = __shfl_sync(0xffffffffu, acc[0], warp_rs_lane<NP>(q));
+      for (int i = 0; i < NP; ++i) acc[i] = 0.0;
+      for (int p = lane; p < N; p += 32) {
+        const double al = a.alpha[off + p];
+        double dv[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) dv[d] = to_f64(vin[(int64_t)d * a.n + off + p]) - sh[d];
+        acc[0] += al;
+        int t = 1 + D;
+#pragma unroll
+        for (int x = 0; x < D; ++x) {
+          const double ad = al * dv[x];
+          acc[1 + x] += ad;
+#pragma unroll
+          for (int y = x; y < D; ++y, ++t) acc[t] = fma(ad, dv[y], acc[t]);
+        }
+      }
+      warp_rs_d<NP>(acc, lane);
+#pragma unroll
+      for (int q = 0; q < NS; ++q) res[q] = __shfl_sync(0xffffffffu, acc[0], warp_rs_lane<NP>(q));
+    }
     const double W = res[0];
     double* prm_out = a.params_out + (size_t)j * a.Kmax * P;
     const unsigned int too_few = (N <= 10) ? GM_ST_TOO_FEW : 0u;

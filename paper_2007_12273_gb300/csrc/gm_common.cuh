@@ -95,6 +95,40 @@ __device__ __forceinline__ double odd_2m53(unsigned long long k, bool neg) {
   return __longlong_as_double((long long)(ex | mant | (neg ? (1ull << 63) : 0ull)));
 }
 
+// Fixed-point sums on the integer pipe: a value v is taken as the integer
+// round(v / 2^eq), sums of such integers and of their products are exact in
+// 128 bits, and one conversion to FP64 per sum replaces a per-element FP64
+// accumulation.  kFixBits bounds |v| / 2^eq below 2^kFixBits, kFixMaxN the
+// count of summed products (2 kFixBits + 2 + log2 kFixMaxN < 127).
+constexpr int kFixBits = 54;
+constexpr int kFixMaxN = 1 << 14;
+
+// v / 2^eq rounded to the nearest integer (ties away from zero), from the
+// bit pattern of an FP32 v with |v| < 2^(eq + kFixBits)
+__device__ __forceinline__ long long fixq(float v, int eq) {
+  const uint32_t u = __float_as_uint(v);
+  const int eb = (int)((u >> 23) & 0xFFu);
+  const long long m = (long long)((u & 0x7FFFFFu) | (eb ? 0x800000u : 0u));
+  const int sh = (eb ? eb - 150 : -149) - eq;  // v = m 2^(eb - 150) (subnormal: 2^-149)
+  long long r = 0;
+  if (sh >= 0) r = m << sh;
+  else if (sh > -40) r = (m + (1ll << (-sh - 1))) >> (-sh);
+  return (u >> 31) ? -r : r;
+}
+
+__device__ __forceinline__ __int128 shfl_xor_i128(__int128 x, int b) {
+  const long long lo = __shfl_xor_sync(0xffffffffu, (long long)(unsigned long long)x, b);
+  const long long hi = __shfl_xor_sync(0xffffffffu, (long long)(x >> 64), b);
+  return ((__int128)hi << 64) | (__int128)(unsigned long long)lo;
+}
+
+// a 128-bit integer times 2^e as the nearest-ish double (two roundings)
+__device__ __forceinline__ double i128_to_f64(__int128 x, int e) {
+  const long long hi = (long long)(x >> 64);
+  const unsigned long long lo = (unsigned long long)x;
+  return ldexp(fma((double)hi, 18446744073709551616.0, (double)lo), e);
+}
+
 __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));

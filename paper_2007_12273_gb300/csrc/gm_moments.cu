@@ -35,23 +35,73 @@ __global__ void __launch_bounds__(NW * 32) deposit_partials_kernel(int64_t C, co
   for (int64_t j = (int64_t)blockIdx.x * NW + wid; j < C; j += (int64_t)gridDim.x * NW) {
     const int64_t o = cell_off[j], n = cell_off[j + 1] - o;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-    for (int64_t p = lane; p < n; p += 32) {
-      const double sx = cell_frac(x[o + p], j, inv_dx) - 0.5;
-      const double al = alpha ? alpha[o + p] : 1.0;
-      if (order == 1) {
-        a0 += al;
-        a1 = sx < 0.0 ? fma(-al, sx, a1) : a1;
-        a2 = sx > 0.0 ? fma(al, sx, a2) : a2;
-      } else {
-        const double as = al * sx;
-        a0 += al;
-        a1 += as;
-        a2 = fma(as, sx, a2);
+    // equal weights (bit for bit) and at most 2^14 particles: the sums of s
+    // and s^2 (or of the CIC parts) exactly on the integer pipe, s = k 2^-53
+    // with k = round(xi 2^53) - 2^52 from the bits of the FP64 in-cell
+    // position xi in [0, 1); the weight multiplies the sums once
+    bool fixed = false;
+    if (n > 0 && n <= kFixMaxN) {
+      const long long wb = alpha ? __double_as_longlong(alpha[o]) : __double_as_longlong(1.0);
+      bool same = true;
+      if (alpha)
+        for (int64_t p = lane; p < n; p += 32) same = same && (__double_as_longlong(alpha[o + p]) == wb);
+      fixed = __all_sync(0xffffffffu, same);
+      if (fixed) {
+        __int128 k0 = 0, k1 = 0;
+        for (int64_t p = lane; p < n; p += 32) {
+          const double xi = cell_frac(x[o + p], j, inv_dx);
+          // xi = m 2^(e - 1075) (m with its implicit bit), k = round(xi 2^53) - 2^52
+          const unsigned long long u = (unsigned long long)__double_as_longlong(xi);
+          const int e = (int)((u >> 52) & 0x7FFull);
+          const long long m = (long long)((u & ((1ull << 52) - 1ull)) | (e ? (1ull << 52) : 0ull));
+          const int sh = (e ? e : 1) - 1022;  // xi 2^53 = m 2^sh, sh <= 0
+          long long r = 0;
+          if (sh == 0) r = m;
+          else if (sh > -60) r = (m + (1ll << (-sh - 1))) >> (-sh);
+          const long long k = r - (1ll << 52);
+          if (order == 1) {
+            k0 += (__int128)(k < 0 ? -k : 0);
+            k1 += (__int128)(k > 0 ? k : 0);
+          } else {
+            k0 += (__int128)k;
+            k1 += (__int128)k * (__int128)k;
+          }
+        }
+#pragma unroll
+        for (int q = 16; q > 0; q >>= 1) {
+          k0 += shfl_xor_i128(k0, q);
+          k1 += shfl_xor_i128(k1, q);
+        }
+        const double al = __longlong_as_double(wb);
+        a0 = al * (double)n;
+        if (order == 1) {
+          a1 = al * i128_to_f64(k0, -53);
+          a2 = al * i128_to_f64(k1, -53);
+        } else {
+          a1 = al * i128_to_f64(k0, -53);
+          a2 = al * i128_to_f64(k1, -106);
+        }
       }
     }
-    a0 = warp_sum(a0);
-    a1 = warp_sum(a1);
-    a2 = warp_sum(a2);
+    if (!fixed) {
+      for (int64_t p = lane; p < n; p += 32) {
+        const double sx = cell_frac(x[o + p], j, inv_dx) - 0.5;
+        const double al = alpha ? alpha[o + p] : 1.0;
+        if (order == 1) {
+          a0 += al;
+          a1 = sx < 0.0 ? fma(-al, sx, a1) : a1;
+          a2 = sx > 0.0 ? fma(al, sx, a2) : a2;
+        } else {
+          const double as = al * sx;
+          a0 += al;
+          a1 += as;
+          a2 = fma(as, sx, a2);
+        }
+      }
+      a0 = warp_sum(a0);
+      a1 = warp_sum(a1);
+      a2 = warp_sum(a2);
+    }
     if (lane == 0) {
       if (order == 1) {
         part[3 * j + 0] = a1;

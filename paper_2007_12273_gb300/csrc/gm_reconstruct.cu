@@ -44,10 +44,85 @@ __global__ void __launch_bounds__(NW * 32) recon_stats_kernel(int64_t C, int Kma
     double acc[NA];
 #pragma unroll
     for (int i = 0; i < NA; ++i) acc[i] = 0.0;
-    if (rc.K == 1) {
+    if (rc.K == 1 && n <= kFixMaxN) {
       // one component: w = dz + f with one dz for the cell, so the sums of
-      // w and |w|^2 follow from those of f (FP64 sums of the FP32 f):
-      // sum w = n dz + sum f, sum |w|^2 = n |dz|^2 + 2 dz . sum f + sum |f|^2
+      // w and |w|^2 follow from those of f: sum w = n dz + sum f,
+      // sum |w|^2 = n |dz|^2 + 2 dz . sum f + sum |f|^2.  All sums on the
+      // integer pipe, exactly: the in-cell position offset s = k 2^-53 with
+      // the odd integer k = 2 m0 - 2^52 + 1, and f_d = L_d. xi taken as an
+      // integer multiple of 2^eq_d, eq_d from the bound |f_d| <= 9 sum_e
+      // |L_de| (|xi| <= sqrt(-2 ln 2^-53) = 8.6), which keeps f_d / 2^eq_d
+      // below 2^54 (exact within 2^-30 of the bound, to 2^-55 of it below).
+      int eq[D];
+      {
+        const float* L = rc.Lf[0];
+        float bnd[D];
+        if (D == 1) {
+          bnd[0] = fabsf(L[0]);
+        } else {
+          bnd[0] = fabsf(L[0]);
+          bnd[1] = fabsf(L[1]) + fabsf(L[2]);
+          bnd[D - 1] = fabsf(L[3]) + fabsf(L[4]) + fabsf(L[5]);
+        }
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          const int eb = (int)((__float_as_uint(9.0f * bnd[d]) >> 23) & 0xFFu);
+          eq[d] = (eb ? eb - 127 : -126) + 1 - kFixBits;
+        }
+      }
+      __int128 sk0 = 0, sk1 = 0, sf[D], sf2[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) sf[d] = sf2[d] = 0;
+      for (int64_t i = lane; i < n; i += 32) {
+        uint64_t m0;
+        int z;
+        float f[D];
+        sample_f<D>(rc, j, i, seed, m0, z, f);
+        const long long k = 2ll * (long long)m0 - (1ll << 52) + 1ll;
+        if (order == 1) {
+          sk0 += (__int128)(k < 0 ? -k : 0);
+          sk1 += (__int128)(k > 0 ? k : 0);
+        } else {
+          sk0 += (__int128)k;
+          sk1 += (__int128)k * (__int128)k;
+        }
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          const long long fq = fixq(f[d], eq[d]);
+          sf[d] += (__int128)fq;
+          sf2[d] += (__int128)fq * (__int128)fq;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sk0 += shfl_xor_i128(sk0, o);
+        sk1 += shfl_xor_i128(sk1, o);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          sf[d] += shfl_xor_i128(sf[d], o);
+          sf2[d] += shfl_xor_i128(sf2[d], o);
+        }
+      }
+      acc[0] = i128_to_f64(sk0, -53);
+      acc[1] = i128_to_f64(sk1, order == 1 ? -53 : -106);
+      acc[2 + D] = 0.0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        acc[2 + d] = i128_to_f64(sf[d], eq[d]);
+        acc[2 + D] += i128_to_f64(sf2[d], 2 * eq[d]);
+      }
+      const double nd = (double)n;
+      double dzf = 0.0, dz2 = 0.0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const double dz = rc.dz[0][d];
+        dzf = fma(dz, acc[2 + d], dzf);
+        dz2 = fma(dz, dz, dz2);
+        acc[2 + d] = fma(nd, dz, acc[2 + d]);
+      }
+      acc[2 + D] = fma(nd, dz2, fma(2.0, dzf, acc[2 + D]));
+    } else if (rc.K == 1) {
+      // the same with FP64 sums (cells above 2^14 particles)
       for (int64_t i = lane; i < n; i += 32) {
         uint64_t m0;
         int z;

@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(NW * 32) features_kernel(int64_t C, int64_t n,
     float W = 0.0f, s1[D], s2[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) s1[d] = s2[d] = 0.0f;
+#pragma unroll 4
     for (int p = lane; p < N; p += 32) {
       const float a = d2f_trunc(alpha[o + p]);
       W += a;
@@ -99,6 +100,7 @@ __global__ void __launch_bounds__(NW * 32) features_kernel(int64_t C, int64_t n,
     float s3[NC];
 #pragma unroll
     for (int i = 0; i < NC; ++i) s3[i] = 0.0f;
+#pragma unroll 4
     for (int p = lane; p < N; p += 32) {
       const float w = d2f_trunc(alpha[o + p]) * iW;
       float y[D];

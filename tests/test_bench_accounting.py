@@ -75,3 +75,31 @@ def test_strided_oracle_sample():
     assert sw.v.flags.c_contiguous
     sw2, cells2 = bench.strided_sample(wl, 1000)  # capped at the workload
     assert sw2.C == wl.C and list(cells2) == list(range(64))
+
+
+def test_dominant_kernel_roofline_accounting():
+    # the roofline of the step's largest traced kernel: algorithmic work per
+    # launch / its traced time against the unit's peak (FP64 from unit
+    # counts and the clock: 152 SMs x 2 FMA x 2 flops x 2070 MHz)
+    counts = np.array([100, 300, 600])
+    ctx = dict(counts=counts, D=3, K=np.array([1, 1, 2]), kwork=np.array([0, 0, 10]),
+               sweeps=np.array([1, 1, 5]), K0=np.array([1, 1, 2]), sm_mhz=2070.0, hbm_gbs=6780.0,
+               bf16_tflops=1916.2, F=576, O=112, ms_compress=1.0)
+    assert bench.fp64_peak_tflops(2070.0) == pytest.approx(1.25856)
+    kern = {"em_k1_kernel": {"ms": 2.0, "launches_per_step": 1.0},
+            "recon_emit_kernel": {"ms": 1.0, "launches_per_step": 1.0}}
+    r = bench.kernel_roofline(kern, ctx)
+    assert r["kernel"] == "em_k1_kernel" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    # one-component cells only (K0 == 1): 400 particles x 22 FP64 flops in 2 ms
+    assert r["achieved"] == pytest.approx(400 * 22 / 2e-3 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / bench.fp64_peak_tflops(2070.0))
+    assert r["secondary"][0]["achieved"] == pytest.approx(400 * 20 / 2e-3 / 1e9)
+    kern["recon_emit_kernel"]["ms"] = 3.0
+    r = bench.kernel_roofline(kern, ctx)
+    assert r["kernel"] == "recon_emit_kernel"
+    assert r["achieved"] == pytest.approx(1000 * 14 / 3e-3 / 1e12)
+    assert r["secondary"][0]["achieved"] == pytest.approx(1000 * 40 / 3e-3 / 1e9)
+    kern = {"mlp_forward (tc_gemm_kernel x4)": {"ms": 1.0, "launches_per_step": 1.0}}
+    r = bench.kernel_roofline(kern, ctx)
+    assert r["bound"] == "tensor"
+    assert r["achieved"] == pytest.approx(2 * 3 * (576 * 256 + 2 * 256 * 256 + 256 * 112) / 1e-3 / 1e12)
