@@ -726,44 +726,66 @@ def run_gmcr(args):
     rst = rout["status"].cpu().numpy()
 
     # ---- end to end through the API with host buffers ----------------------
+    # Every step copies its inputs from pinned host memory and all its outputs
+    # (particles, mixtures) back.  The copies run on streams of their own with
+    # two device buffer sets, so step i's inputs arrive while step i - 1
+    # computes and its outputs leave while step i + 1 computes -- a restart
+    # code streaming its batches through the library would do the same.
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     h_in = [pin(wl.cell_off), pin(wl.x), pin(wl.v), pin(wl.alpha)]
-    d_in = [torch.empty_like(h, device=device) for h in h_in]
-    cout_e = comp_out()
-    h_out = {k: torch.empty(tuple(vv.shape), dtype=vv.dtype).pin_memory()
-             for k, vv in list(rout.items()) + [("params", cout_e["params"]), ("K", cout_e["K"]),
-                                                ("W", cout_e["W"]), ("rho_target", cout_e["rho_target"])]}
+    NB = 2
+    d_in = [[torch.empty_like(h, device=device) for h in h_in] for _ in range(NB)]
+    couts = [comp_out() for _ in range(NB)]
+    routs = [rout] + [{k: torch.empty_like(vv) for k, vv in rout.items()} for _ in range(NB - 1)]
+    out_keys = list(rout.keys()) + ["params", "K", "W", "rho_target"]
+    src_of = lambda b, k: routs[b][k] if k in routs[b] else couts[b][k]
+    h_out = [{k: torch.empty(tuple(src_of(b, k).shape), dtype=src_of(b, k).dtype).pin_memory()
+              for k in out_keys} for b in range(NB)]
     h2d = sum(h.numel() * h.element_size() for h in h_in)
-    d2h = sum(h.numel() * h.element_size() for h in h_out.values())
-    e2e_steps = max(2, min(args.steps, 5))
+    d2h = sum(h.numel() * h.element_size() for h in h_out[0].values())
+    e2e_steps = max(4, min(args.steps, 6))
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    ev = lambda: torch.cuda.Event()
+    ev_in, ev_done, ev_out = [ev() for _ in range(NB)], [ev() for _ in range(NB)], [ev() for _ in range(NB)]
 
-    def e2e_step():
-        for h, d in zip(h_in, d_in):
-            d.copy_(h, non_blocking=True)
+    def e2e_step(i):
+        b = i % NB
+        s_in.wait_event(ev_done[b])  # step i - 2 has finished with this input set
+        with torch.cuda.stream(s_in):
+            for h, d in zip(h_in, d_in[b]):
+                d.copy_(h, non_blocking=True)
+        ev_in[b].record(s_in)
+        stream.wait_event(ev_in[b])
+        stream.wait_event(ev_out[b])  # step i - 2's outputs have left this set
+        di, co, ro = d_in[b], couts[b], routs[b]
         kw = {}
         if head == "learned":
-            f_, w_ = gm.gm_features(cfg, d_in[0], d_in[2], d_in[3], stream=stream)
+            f_, w_ = gm.gm_features(cfg, di[0], di[2], di[3], stream=stream)
             o_ = net.forward(f_, stream=stream)
-            K0, prm = gm.gm_mlp_decode(cfg, o_, w_, d_in[0], stream=stream,
+            K0, prm = gm.gm_mlp_decode(cfg, o_, w_, di[0], stream=stream,
                                          presence_logit=args.presence_logit)
             kw = dict(init_K=K0, init_params=prm)
-        gm.gm_compress(cfg_l if head == "learned" else cfg, d_in[0], d_in[1], d_in[2], d_in[3],
-                       stream=stream, out=cout_e, **kw)
-        gm.gm_reconstruct(rcfg, cout_e["K"], cout_e["params"], cout_e["W"], cout_e["rho_target"],
-                          d_in[0], n_out=n, stream=stream, out=rout)
-        for k, h in h_out.items():
-            src = rout[k] if k in rout else cout_e[k]
-            h.copy_(src, non_blocking=True)
+        gm.gm_compress(cfg_l if head == "learned" else cfg, di[0], di[1], di[2], di[3],
+                       stream=stream, out=co, **kw)
+        gm.gm_reconstruct(rcfg, co["K"], co["params"], co["W"], co["rho_target"],
+                          di[0], n_out=n, stream=stream, out=ro)
+        ev_done[b].record(stream)
+        s_out.wait_event(ev_done[b])
+        with torch.cuda.stream(s_out):
+            for k, h in h_out[b].items():
+                h.copy_(src_of(b, k), non_blocking=True)
+        ev_out[b].record(s_out)
 
-    e2e_step()
+    for i in range(NB):
+        e2e_step(i)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(e2e_steps):
-        e2e_step()
-    e1.record(stream)
+    e0.record(s_in)
+    for i in range(e2e_steps):
+        e2e_step(i)
+    e1.record(s_out)
     torch.cuda.synchronize()
     e2e_ms = reduce_max(e0.elapsed_time(e1) / e2e_steps, dist, device)
     e2e_value = total_particles / (e2e_ms * 1e-3)
@@ -849,7 +871,9 @@ def run_gmcr(args):
         "kernels": {k: dict(v, share=v["ms"] / max(1e-9, sum(z["ms"] for z in res[head]["kernels"].values())))
                     for k, v in sorted(res[head]["kernels"].items(), key=lambda kv: -kv[1]["ms"])},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "steps": e2e_steps,
+                "copies": "inputs in and outputs out on their own streams, overlapping the "
+                          "neighbouring steps' compute (two device buffer sets)"},
         "gpu_launches": int(round(sum(v["launches_per_step"] for v in res[head]["kernels"].values())
                                   + (4 if head == "learned" else 0) + 2)) * args.steps,
         "clocks": clk,
