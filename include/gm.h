@@ -234,7 +234,7 @@ int gm_mixture_moments(const gm_config* cfg, int64_t C, const int32_t* K, const 
  * that must not pay the device-wide synchronisation that cudaFree/cudaMalloc
  * imply (gm_reconstruct grows its workspace that way).  This entry point
  * computes exactly what gm_reconstruct computes, with the same arguments,
- * but takes its scratch from a fixed 5 MiB array that the library reserves
+ * but takes its scratch from a fixed 40 MiB array that the library reserves
  * statically on every GPU that loads it, held until the process exits.
  *
  * Limits and rules:
@@ -273,7 +273,7 @@ int gm_trace_end(void);
 int gm_trace_get(int32_t i, char* name, int32_t name_len, double* ms, int32_t* launches);
 
 /* gm_noalloc_limits_ok -- 1 if the scratch a call of 32768 cells needs
- * (D = 1 and D = 3) fits the 5 MiB array of gm_reconstruct_noalloc, else 0:
+ * (D = 1 and D = 3, Kmax = 16) fits the 40 MiB array of gm_reconstruct_noalloc, else 0:
  * a host-side self-check of that limit (no counterpart in the paper); it
  * touches no device and returns no error code. */
 int gm_noalloc_limits_ok(void);

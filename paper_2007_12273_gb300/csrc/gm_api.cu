@@ -497,7 +497,7 @@ int gm_reconstruct(const gm_config* cfg, int64_t C, const int32_t* K, const doub
   if (C == 0) return GM_OK;
   if ((rc = check_device(nullptr))) return rc;
   void* ws = nullptr;
-  if ((rc = ws_get(gmcr::reconstruct_ws_bytes(cfg->D, C), &ws))) return rc;
+  if ((rc = ws_get(gmcr::reconstruct_ws_bytes(cfg->D, C, cfg->Kmax), &ws))) return rc;
   cudaError_t e = gmcr::launch_reconstruct(cfg->D, C, cfg->Kmax, K, params, W, rho_target, n_out,
                                            out_off, cfg->seed, cfg->L / (double)C, cfg->q,
                                            cfg->shape_order, x_out, v_out, alpha_out, status_out,

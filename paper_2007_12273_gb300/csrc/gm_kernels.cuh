@@ -11,6 +11,7 @@ namespace gmcr {
 // EM (compression); returns the launch error
 cudaError_t launch_em1(const EmParams& p, int nt, int fp64_mstep, int v_f64, size_t smem, int grid,
                        cudaStream_t s);
+size_t em_k1_raw_bytes(int D, int64_t C);
 cudaError_t launch_em_k1(int D, int v_f64, const K1Params& p, int sms, cudaStream_t s);
 cudaError_t launch_em3(const EmParams& p, int nt, int fp64_mstep, int v_f64, size_t smem, int grid,
                        cudaStream_t s);
@@ -48,7 +49,7 @@ int api_check_device();
 // on its stream (name = the kernel), or a boundary (name = nullptr) at the
 // start of an API call; a no-op unless a trace is on
 void trace_mark(const char* name, cudaStream_t s);
-size_t reconstruct_ws_bytes(int D, int64_t C);
+size_t reconstruct_ws_bytes(int D, int64_t C, int Kmax);
 cudaError_t launch_reconstruct(int D, int64_t C, int Kmax, const int32_t* K, const double* prm,
                                const double* W, const double* rho_target, int64_t n_out,
                                const int64_t* out_off, uint64_t seed, double dx, double q,

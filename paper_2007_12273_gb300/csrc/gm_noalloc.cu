@@ -21,9 +21,10 @@
 
 namespace {
 
-// 5 MiB: the per-cell sums, the mass-matrix rows and the solver's
-// temporaries of up to kMaxCells cells (D = 1 or 3).
-constexpr size_t kScratchBytes = (size_t)5 << 20;
+// 40 MiB: the per-cell sums, mixture records and projection coefficients,
+// the mass-matrix rows and the solver's temporaries of up to kMaxCells cells
+// (D = 1 or 3, up to 16 components per cell).
+constexpr size_t kScratchBytes = (size_t)40 << 20;
 constexpr int64_t kMaxCells = 32768;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -69,7 +70,7 @@ int gm_reconstruct_noalloc(const gm_config* cfg, int64_t C, const int32_t* K, co
   if (C > kMaxCells)
     return fail2(GM_ERR_ARG, "gm_reconstruct_noalloc handles at most 32768 cells per call (got " +
                                  std::to_string((long long)C) + "); use gm_reconstruct");
-  if (gmcr::reconstruct_ws_bytes(cfg->D, C) > kScratchBytes)
+  if (gmcr::reconstruct_ws_bytes(cfg->D, C, cfg->Kmax) > kScratchBytes)
     return fail2(GM_ERR_ARG, "scratch of gm_reconstruct_noalloc too small for this call");
   if ((rc = gmcr::api_check_device())) return rc;
   void* ws = nullptr;
@@ -85,10 +86,11 @@ int gm_reconstruct_noalloc(const gm_config* cfg, int64_t C, const int32_t* K, co
   return GM_OK;
 }
 
-// the largest scratch a call may need (D = 3, kMaxCells cells) fits the array
+// the largest scratch a call may need (kMaxCells cells, 16 components) fits
+// the array
 int gm_noalloc_limits_ok() {
-  return gmcr::reconstruct_ws_bytes(1, kMaxCells) <= kScratchBytes &&
-         gmcr::reconstruct_ws_bytes(3, kMaxCells) <= kScratchBytes;
+  return gmcr::reconstruct_ws_bytes(1, kMaxCells, gmcr::kMaxK) <= kScratchBytes &&
+         gmcr::reconstruct_ws_bytes(3, kMaxCells, gmcr::kMaxK) <= kScratchBytes;
 }
 
 }  // extern "C"

@@ -18,61 +18,139 @@
 
 namespace gmcr {
 
-// Pass 1, one warp per cell: per cell, the unit-weight shape sums of the
-// resampled particles on nodes j-1, j, j+1 (column j of M / q) and sum w,
-// sum |w|^2 with w = v - u.  cstat[j] = [c-, c0, c+, sum w (D), sum |w|^2].
-// The shape sums come from the moments of s = xi - 1/2 (xi = u0, the
-// particle's position inside its cell): for the quadratic B-spline
-// c- = (n/4 - S1 + S2) / 2, c+ = (n/4 + S1 + S2) / 2, c0 = 3n/4 - S2 with
-// S1 = sum s, S2 = sum s^2; for CIC c- = sum max(-s, 0), c+ = sum max(s, 0),
-// c0 = n - c- - c+.
+// Per-cell sums of the resampled particles, written by pass 1 (raw_words
+// doubles per cell).  A one-component cell with at most kFixMaxN particles
+// keeps exact 128-bit integer sums (see below), every other cell FP64 sums:
+//   integer: words (2t, 2t+1) hold sum t as (low, high) 64-bit halves, t =
+//            0, 1 the position sums, 2 .. 1+D the sums of f_d, 2+D .. 1+2D
+//            those of f_d^2;
+//   FP64:    words 0, 1 the position sums, 2 .. 1+D the sums of f_d (one
+//            component) or w_d (otherwise), 2+D the sum of |f|^2 or |w|^2.
+// The position sums are S1 = sum s, S2 = sum s^2 (quadratic B-spline) or
+// sum max(-s, 0), sum max(s, 0) (CIC), s = xi - 1/2 the particle's offset
+// from the cell centre; w = v - u = dz + f with f = L_z xi.
+template <int D>
+__host__ __device__ constexpr int raw_words() { return 2 * (2 + 2 * D); }
+__device__ __forceinline__ bool fixed_sums(int Kj, int64_t n) { return Kj == 1 && n <= kFixMaxN; }
+__device__ __forceinline__ __int128 load_i128(const double* p) {
+  const longlong2 v = *reinterpret_cast<const longlong2*>(p);
+  return ((__int128)v.y << 64) | (__int128)(unsigned long long)v.x;
+}
+// the exponents eq_d of the fixed-point f_d: |f_d| <= 9 sum_e |L_de|
+// (|xi| <= sqrt(-2 ln 2^-53) = 8.6) keeps f_d / 2^eq_d below 2^kFixBits
+template <int D>
+__device__ __forceinline__ void fix_exponents(const float* L, int (&eq)[D]) {
+  float bnd[D];
+  if (D == 1) {
+    bnd[0] = fabsf(L[0]);
+  } else {
+    bnd[0] = fabsf(L[0]);
+    bnd[1] = fabsf(L[1]) + fabsf(L[2]);
+    bnd[D - 1] = fabsf(L[3]) + fabsf(L[4]) + fabsf(L[5]);
+  }
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const int eb = (int)((__float_as_uint(9.0f * bnd[d]) >> 23) & 0xFFu);
+    eq[d] = (eb ? eb - 127 : -126) + 1 - kFixBits;
+  }
+}
+// the unit-weight shape sums of a cell's n particles on nodes j-1, j, j+1
+// (cs[0], cs[1], cs[2]): c- = (n/4 - S1 + S2) / 2, c+ = (n/4 + S1 + S2) / 2,
+// c0 = 3n/4 - S2 for the quadratic B-spline; c- = sum max(-s, 0),
+// c+ = sum max(s, 0), c0 = n - c- - c+ for CIC
+__device__ __forceinline__ void shape_sums(const double* rw, bool fixed, int order, int64_t n,
+                                           double (&cs)[3]) {
+  double a0, a1;
+  if (fixed) {
+    a0 = i128_to_f64(load_i128(rw), -53);
+    a1 = i128_to_f64(load_i128(rw + 2), order == 1 ? -53 : -106);
+  } else {
+    a0 = rw[0];
+    a1 = rw[1];
+  }
+  const double nd = (double)n;
+  if (order == 1) {
+    cs[0] = a0;
+    cs[2] = a1;
+    cs[1] = nd - a0 - a1;
+  } else {
+    cs[0] = 0.5 * (0.25 * nd - a0 + a1);
+    cs[2] = 0.5 * (0.25 * nd + a0 + a1);
+    cs[1] = 0.75 * nd - a1;
+  }
+}
+// sum w (sw[0 .. D-1]) and sum |w|^2 (sw[D]) of a cell; for one component
+// w = dz + f with one dz, so sum w = n dz + sum f and
+// sum |w|^2 = n |dz|^2 + 2 dz . sum f + sum |f|^2
+template <int D>
+__device__ __forceinline__ void velocity_sums(const double* rw, bool fixed, int Kj,
+                                              const RecComp<D>& c0, int64_t n, double (&sw)[D + 1]) {
+  if (fixed) {
+    int eq[D];
+    fix_exponents<D>(c0.Lf, eq);
+    sw[D] = 0.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      sw[d] = i128_to_f64(load_i128(rw + 4 + 2 * d), eq[d]);
+      sw[D] += i128_to_f64(load_i128(rw + 4 + 2 * (D + d)), 2 * eq[d]);
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t <= D; ++t) sw[t] = rw[2 + t];
+  }
+  if (Kj == 1) {
+    const double nd = (double)n;
+    double dzf = 0.0, dz2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const double dz = c0.dz[d];
+      dzf = fma(dz, sw[d], dzf);
+      dz2 = fma(dz, dz, dz2);
+      sw[d] = fma(nd, dz, sw[d]);
+    }
+    sw[D] = fma(nd, dz2, fma(2.0, dzf, sw[D]));
+  }
+}
+
+// Pass 0, one thread per cell: each cell's mixture data for the two particle
+// passes (prep_cell).
+template <int D>
+__global__ void recon_prep_kernel(int64_t C, int Kmax, const int32_t* K, const double* prm,
+                                  RecHead<D>* head, RecComp<D>* comp) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < C;
+       j += (int64_t)gridDim.x * blockDim.x)
+    prep_cell<D>(j, Kmax, K, prm, head, comp);
+}
+
+// Pass 1, one warp per cell: the position and velocity sums of the cell's
+// resampled particles (raw_words layout above).
 template <int D, int NW>
-__global__ void __launch_bounds__(NW * 32) recon_stats_kernel(int64_t C, int Kmax, const int32_t* K,
-                                                              const double* prm,
+__global__ void __launch_bounds__(NW * 32) recon_stats_kernel(int64_t C, int Kmax,
+                                                              const RecHead<D>* head,
+                                                              const RecComp<D>* comp,
                                                               const int64_t* out_off, int64_t n_out,
-                                                              uint64_t seed, int order, double* cstat) {
-  constexpr int NV = 3 + D + 1;
+                                                              uint64_t seed, int order, double* raw) {
   constexpr int NA = 2 + D + 1;
+  constexpr int NS = 2 + 2 * D;
   __shared__ RecCell<D> rcs[NW];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   RecCell<D>& rc = rcs[wid];
   for (int64_t j = (int64_t)blockIdx.x * NW + wid; j < C; j += (int64_t)gridDim.x * NW) {
-    load_cell<D>(rc, j, Kmax, K, prm, lane);
+    load_prepped<D>(rc, j, Kmax, head, comp, lane);
     __syncwarp();
     int64_t o, n;
     out_range(out_off, j, n_out, o, n);
-    double acc[NA];
-#pragma unroll
-    for (int i = 0; i < NA; ++i) acc[i] = 0.0;
-    if (rc.K == 1 && n <= kFixMaxN) {
-      // one component: w = dz + f with one dz for the cell, so the sums of
-      // w and |w|^2 follow from those of f: sum w = n dz + sum f,
-      // sum |w|^2 = n |dz|^2 + 2 dz . sum f + sum |f|^2.  All sums on the
-      // integer pipe, exactly: the in-cell position offset s = k 2^-53 with
-      // the odd integer k = 2 m0 - 2^52 + 1, and f_d = L_d. xi taken as an
-      // integer multiple of 2^eq_d, eq_d from the bound |f_d| <= 9 sum_e
-      // |L_de| (|xi| <= sqrt(-2 ln 2^-53) = 8.6), which keeps f_d / 2^eq_d
-      // below 2^54 (exact within 2^-30 of the bound, to 2^-55 of it below).
+    double* rw = raw + (size_t)j * raw_words<D>();
+    if (fixed_sums(rc.K, n)) {
+      // one component: all sums on the integer pipe, exactly: the in-cell
+      // position offset s = k 2^-53 with the odd integer
+      // k = 2 m0 - 2^52 + 1, and f_d taken as an integer multiple of 2^eq_d
+      // (exact within 2^-30 of the bound, to 2^-55 of it below)
       int eq[D];
-      {
-        const float* L = rc.Lf[0];
-        float bnd[D];
-        if (D == 1) {
-          bnd[0] = fabsf(L[0]);
-        } else {
-          bnd[0] = fabsf(L[0]);
-          bnd[1] = fabsf(L[1]) + fabsf(L[2]);
-          bnd[D - 1] = fabsf(L[3]) + fabsf(L[4]) + fabsf(L[5]);
-        }
+      fix_exponents<D>(rc.Lf[0], eq);
+      __int128 sm[NS];
 #pragma unroll
-        for (int d = 0; d < D; ++d) {
-          const int eb = (int)((__float_as_uint(9.0f * bnd[d]) >> 23) & 0xFFu);
-          eq[d] = (eb ? eb - 127 : -126) + 1 - kFixBits;
-        }
-      }
-      __int128 sk0 = 0, sk1 = 0, sf[D], sf2[D];
-#pragma unroll
-      for (int d = 0; d < D; ++d) sf[d] = sf2[d] = 0;
+      for (int t = 0; t < NS; ++t) sm[t] = 0;
       for (int64_t i = lane; i < n; i += 32) {
         uint64_t m0;
         int z;
@@ -80,86 +158,46 @@ __global__ void __launch_bounds__(NW * 32) recon_stats_kernel(int64_t C, int Kma
         sample_f<D>(rc, j, i, seed, m0, z, f);
         const long long k = 2ll * (long long)m0 - (1ll << 52) + 1ll;
         if (order == 1) {
-          sk0 += (__int128)(k < 0 ? -k : 0);
-          sk1 += (__int128)(k > 0 ? k : 0);
+          sm[0] += (__int128)(k < 0 ? -k : 0);
+          sm[1] += (__int128)(k > 0 ? k : 0);
         } else {
-          sk0 += (__int128)k;
-          sk1 += (__int128)k * (__int128)k;
+          sm[0] += (__int128)k;
+          sm[1] += (__int128)k * (__int128)k;
         }
 #pragma unroll
         for (int d = 0; d < D; ++d) {
           const long long fq = fixq(f[d], eq[d]);
-          sf[d] += (__int128)fq;
-          sf2[d] += (__int128)fq * (__int128)fq;
+          sm[2 + d] += (__int128)fq;
+          sm[2 + D + d] += (__int128)fq * (__int128)fq;
         }
       }
+      __int128 mine = 0;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        sk0 += shfl_xor_i128(sk0, o);
-        sk1 += shfl_xor_i128(sk1, o);
+      for (int t = 0; t < NS; ++t) {
 #pragma unroll
-        for (int d = 0; d < D; ++d) {
-          sf[d] += shfl_xor_i128(sf[d], o);
-          sf2[d] += shfl_xor_i128(sf2[d], o);
-        }
+        for (int o2 = 16; o2 > 0; o2 >>= 1) sm[t] += shfl_xor_i128(sm[t], o2);
+        if (lane == t) mine = sm[t];
       }
-      acc[0] = i128_to_f64(sk0, -53);
-      acc[1] = i128_to_f64(sk1, order == 1 ? -53 : -106);
-      acc[2 + D] = 0.0;
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        acc[2 + d] = i128_to_f64(sf[d], eq[d]);
-        acc[2 + D] += i128_to_f64(sf2[d], 2 * eq[d]);
-      }
-      const double nd = (double)n;
-      double dzf = 0.0, dz2 = 0.0;
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        const double dz = rc.dz[0][d];
-        dzf = fma(dz, acc[2 + d], dzf);
-        dz2 = fma(dz, dz, dz2);
-        acc[2 + d] = fma(nd, dz, acc[2 + d]);
-      }
-      acc[2 + D] = fma(nd, dz2, fma(2.0, dzf, acc[2 + D]));
-    } else if (rc.K == 1) {
-      // the same with FP64 sums (cells above 2^14 particles)
-      for (int64_t i = lane; i < n; i += 32) {
-        uint64_t m0;
-        int z;
-        float f[D];
-        sample_f<D>(rc, j, i, seed, m0, z, f);
-        const double sx = centred52(m0);
-        if (order == 1) {
-          acc[0] += sx < 0.0 ? -sx : 0.0;
-          acc[1] += sx > 0.0 ? sx : 0.0;
-        } else {
-          acc[0] += sx;
-          acc[1] = fma(sx, sx, acc[1]);
-        }
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-          const double fd = f2d_exact(f[d]);
-          acc[2 + d] += fd;
-          acc[2 + D] = fma(fd, fd, acc[2 + D]);
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < NA; ++i) acc[i] = warp_sum(acc[i]);
-      const double nd = (double)n;
-      double dzf = 0.0, dz2 = 0.0;
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        const double dz = rc.dz[0][d];
-        dzf = fma(dz, acc[2 + d], dzf);
-        dz2 = fma(dz, dz, dz2);
-        acc[2 + d] = fma(nd, dz, acc[2 + d]);
-      }
-      acc[2 + D] = fma(nd, dz2, fma(2.0, dzf, acc[2 + D]));
+      if (lane < NS)
+        *reinterpret_cast<longlong2*>(rw + 2 * lane) =
+            make_longlong2((long long)(unsigned long long)mine, (long long)(mine >> 64));
     } else {
+      double acc[NA];
+#pragma unroll
+      for (int t = 0; t < NA; ++t) acc[t] = 0.0;
       for (int64_t i = lane; i < n; i += 32) {
         uint64_t m0;
         double w[D];
-        sample_particle<D>(rc, j, i, seed, m0, w);
+        if (rc.K == 1) {
+          // the f sums (above 2^14 particles)
+          int z;
+          float f[D];
+          sample_f<D>(rc, j, i, seed, m0, z, f);
+#pragma unroll
+          for (int d = 0; d < D; ++d) w[d] = f2d_exact(f[d]);
+        } else {
+          sample_particle<D>(rc, j, i, seed, m0, w);
+        }
         const double sx = centred52(m0);
         if (order == 1) {
           acc[0] += sx < 0.0 ? -sx : 0.0;
@@ -175,21 +213,9 @@ __global__ void __launch_bounds__(NW * 32) recon_stats_kernel(int64_t C, int Kma
         }
       }
 #pragma unroll
-      for (int i = 0; i < NA; ++i) acc[i] = warp_sum(acc[i]);
-    }
-    if (lane == 0) {
-      double* cs = cstat + (size_t)j * NV;
-      const double nd = (double)n;
-      if (order == 1) {
-        cs[0] = acc[0];
-        cs[2] = acc[1];
-        cs[1] = nd - acc[0] - acc[1];
-      } else {
-        cs[0] = 0.5 * (0.25 * nd - acc[0] + acc[1]);
-        cs[2] = 0.5 * (0.25 * nd + acc[0] + acc[1]);
-        cs[1] = 0.75 * nd - acc[1];
-      }
-      for (int d = 0; d <= D; ++d) cs[3 + d] = acc[2 + d];
+      for (int t = 0; t < NA; ++t) acc[t] = warp_sum(acc[t]);
+      if (lane == 0)
+        for (int t = 0; t < NA; ++t) rw[t] = acc[t];
     }
     __syncwarp();
   }
@@ -199,10 +225,11 @@ __global__ void __launch_bounds__(NW * 32) recon_stats_kernel(int64_t C, int Kma
 // dA_{i+1}; M(i,j) = q * (shape sum of cell j's particles on node i).
 // rhs_i = dx (rho'_i - rho_i), rho_i dx = q sum_j alpha_j (shape sum).
 template <int D>
-__global__ void assemble_kernel(int64_t C, const double* cstat, const double* W,
-                                const int64_t* out_off, int64_t n_out, const double* rho_target,
-                                double dx, double q, double* A, double* B, double* Cc, double* Dd) {
-  constexpr int NV = 3 + D + 1;
+__global__ void assemble_kernel(int64_t C, const RecHead<D>* head, const double* raw,
+                                const double* W, const int64_t* out_off, int64_t n_out,
+                                const double* rho_target, double dx, double q, int order, double* A,
+                                double* B, double* Cc, double* Dd) {
+  constexpr int RW = raw_words<D>();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < C;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t im = (i == 0) ? C - 1 : i - 1;
@@ -213,9 +240,13 @@ __global__ void assemble_kernel(int64_t C, const double* cstat, const double* W,
     const double am = nm > 0 ? W[im] / (double)nm : 0.0;
     const double a0 = n0 > 0 ? W[i] / (double)n0 : 0.0;
     const double ap = np > 0 ? W[ip] / (double)np : 0.0;
-    const double cm = cstat[(size_t)im * NV + 2];  // cell i-1 on node i
-    const double c0 = cstat[(size_t)i * NV + 1];
-    const double cp = cstat[(size_t)ip * NV + 0];  // cell i+1 on node i
+    double sm[3], s0[3], sp[3];
+    shape_sums(raw + (size_t)im * RW, fixed_sums(head[im].K, nm), order, nm, sm);
+    shape_sums(raw + (size_t)i * RW, fixed_sums(head[i].K, n0), order, n0, s0);
+    shape_sums(raw + (size_t)ip * RW, fixed_sums(head[ip].K, np), order, np, sp);
+    const double cm = sm[2];  // cell i-1 on node i
+    const double c0 = s0[1];
+    const double cp = sp[0];  // cell i+1 on node i
     A[i] = q * cm;
     B[i] = n0 > 0 ? q * c0 : 1.0;  // empty column: unit diagonal
     Cc[i] = q * cp;
@@ -361,44 +392,75 @@ __global__ void mm_reconstruct_kernel(int64_t n, SolveWs ws, int P, double* x) {
   if (t < P) block_reconstruct(n, ws, P, t, x);
 }
 
-// Pass 2, one warp per cell: Lemons projection coefficients and the final
-// particles.
+// After the mass-matrix solve, one thread per cell: the Lemons projection
+// coefficients (proj_coeffs) from the cell's velocity sums and dA, and the
+// cell's status.  For one component also cv = u + a (dz + beta), so that
+// the particle pass writes v = cv + a f.
+template <int D>
+struct RecCoef {
+  double a, beta[D], alpha_new, cv[D];
+  int skip;
+  int pad;
+};
+template <int D>
+__global__ void recon_coeffs_kernel(int64_t C, int Kmax, const RecHead<D>* head,
+                                    const RecComp<D>* comp, const double* raw,
+                                    const int64_t* out_off, int64_t n_out, const double* W,
+                                    const double* dA, RecCoef<D>* coef, uint32_t* status_out) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < C;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    int64_t o, n;
+    const bool in_range = out_range(out_off, j, n_out, o, n);
+    const RecHead<D> h = head[j];
+    const RecComp<D>& c0 = comp[(size_t)j * Kmax];
+    double sw[D + 1];
+    velocity_sums<D>(raw + (size_t)j * raw_words<D>(), fixed_sums(h.K, n), h.K, c0, n, sw);
+    const ProjCoef<D> pc = proj_coeffs<D>(h.K, h.u, h.theta, n, W[j], dA[j], sw);
+    RecCoef<D> cf;
+    cf.a = pc.a;
+    cf.alpha_new = pc.alpha_new;
+    cf.skip = pc.skip;
+    cf.pad = 0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      cf.beta[d] = pc.beta[d];
+      // one component: v = u + a (dz + f + beta) = cv + a f (a = 1, beta = 0
+      // when skipped)
+      cf.cv[d] = h.K == 1 ? fma(pc.a, c0.dz[d] + pc.beta[d], h.u[d]) : 0.0;
+    }
+    coef[j] = cf;
+    status_out[j] = pc.status | (in_range ? 0u : GM_ST_BAD_RANGE);
+  }
+}
+
+// Pass 2, one warp per cell: the final particles (positions, projected
+// velocities, corrected weights).
 template <int D, int NW>
 __global__ void __launch_bounds__(NW * 32) recon_emit_kernel(
-    int64_t C, int Kmax, const int32_t* K, const double* prm, const double* W,
-    const int64_t* out_off, const double* cstat, const double* dA, uint64_t seed, double dx,
-    int64_t n_out, double* x_out, double* v_out, double* alpha_out, uint32_t* status_out) {
-  constexpr int NV = 3 + D + 1;
+    int64_t C, int Kmax, const RecHead<D>* head, const RecComp<D>* comp, const RecCoef<D>* coef,
+    const int64_t* out_off, uint64_t seed, double dx, int64_t n_out, double* x_out, double* v_out,
+    double* alpha_out) {
   __shared__ RecCell<D> rcs[NW];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   RecCell<D>& rc = rcs[wid];
   for (int64_t j = (int64_t)blockIdx.x * NW + wid; j < C; j += (int64_t)gridDim.x * NW) {
-    load_cell<D>(rc, j, Kmax, K, prm, lane);
+    load_prepped<D>(rc, j, Kmax, head, comp, lane);
+    const RecCoef<D> cf = coef[j];
     __syncwarp();
     int64_t o, n;
-    const bool in_range = out_range(out_off, j, n_out, o, n);
-    if (lane == 0)
-      status_out[j] = projection_coeffs<D>(rc, n, W[j], dA[j], cstat + (size_t)j * NV + 3) |
-                      (in_range ? 0u : GM_ST_BAD_RANGE);
-    __syncwarp();
-    const double aa = rc.a, an = rc.alpha_new;
-    const int skip = rc.skip;
+    out_range(out_off, j, n_out, o, n);
+    const double aa = cf.a, an = cf.alpha_new, jd = (double)j;
     if (rc.K == 1) {
-      // one component: v = u + a (dz + f + beta) = c + a f with one
-      // c = u + a (dz + beta) for the cell (a = 1, beta = 0 when skipped)
-      double cv[D];
-#pragma unroll
-      for (int d = 0; d < D; ++d) cv[d] = fma(aa, rc.dz[0][d] + rc.beta[d], rc.u[d]);
       for (int64_t i = lane; i < n; i += 32) {
         uint64_t m0;
         int z;
         float f[D];
         sample_f<D>(rc, j, i, seed, m0, z, f);
         const double u0 = uniform_pos52(m0);
-        x_out[o + i] = __dmul_rn(__dadd_rn((double)j, u0), dx);
+        x_out[o + i] = __dmul_rn(__dadd_rn(jd, u0), dx);
         alpha_out[o + i] = an;
 #pragma unroll
-        for (int d = 0; d < D; ++d) v_out[(int64_t)d * n_out + o + i] = fma(aa, f2d_exact(f[d]), cv[d]);
+        for (int d = 0; d < D; ++d) v_out[(int64_t)d * n_out + o + i] = fma(aa, f2d_exact(f[d]), cf.cv[d]);
       }
     } else {
       for (int64_t i = lane; i < n; i += 32) {
@@ -406,12 +468,12 @@ __global__ void __launch_bounds__(NW * 32) recon_emit_kernel(
         double w[D];
         sample_particle<D>(rc, j, i, seed, m0, w);
         const double u0 = uniform_pos52(m0);
-        x_out[o + i] = __dmul_rn(__dadd_rn((double)j, u0), dx);
+        x_out[o + i] = __dmul_rn(__dadd_rn(jd, u0), dx);
         alpha_out[o + i] = an;
 #pragma unroll
         for (int d = 0; d < D; ++d) {
           // v = u + w; projected: u + a (w + beta) (eqs. alpha, beta)
-          const double vp = skip ? rc.u[d] + w[d] : fma(aa, w[d] + rc.beta[d], rc.u[d]);
+          const double vp = cf.skip ? rc.u[d] + w[d] : fma(aa, w[d] + cf.beta[d], rc.u[d]);
           v_out[(int64_t)d * n_out + o + i] = vp;
         }
       }
@@ -446,12 +508,74 @@ static SolvePlan plan_solve(int64_t C) {
   return pl;
 }
 
-size_t reconstruct_ws_bytes(int D, int64_t C) {
+// workspace: the raw sums, the mixture heads and component records, the
+// projection coefficients, then the FP64 arrays of the mass-matrix solve
+static size_t rec_bytes(int D, int64_t C, int Kmax, size_t* off_head, size_t* off_coef,
+                        size_t* off_comp) {
+  const size_t raw = (size_t)C * (D == 1 ? raw_words<1>() : raw_words<3>()) * sizeof(double);
+  const size_t hd = (size_t)C * (D == 1 ? sizeof(RecHead<1>) : sizeof(RecHead<3>));
+  const size_t cf = (size_t)C * (D == 1 ? sizeof(RecCoef<1>) : sizeof(RecCoef<3>));
+  const size_t cp = (size_t)C * Kmax * (D == 1 ? sizeof(RecComp<1>) : sizeof(RecComp<3>));
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  if (off_head) *off_head = up(raw);
+  if (off_coef) *off_coef = up(raw) + up(hd);
+  if (off_comp) *off_comp = up(raw) + up(hd) + up(cf);
+  return up(raw) + up(hd) + up(cf) + up(cp);
+}
+
+size_t reconstruct_ws_bytes(int D, int64_t C, int Kmax) {
   const SolvePlan pl = plan_solve(C);
-  const size_t per_cell = (size_t)(3 + D + 1) + 4 /*a b c d*/ + 1 /*dA*/ + 4 /*y v w cp*/;
+  const size_t per_cell = 4 /*a b c d*/ + 1 /*dA*/ + 4 /*y v w cp*/;
   size_t dbl = per_cell * (size_t)C + 8 * (size_t)(2 * pl.P + 2);
   if (pl.multi) dbl += 4 * (size_t)(2 * pl.P) + 8 * (size_t)(2 * pl.P2 + 2);
-  return dbl * sizeof(double) + 1024;
+  return rec_bytes(D, C, Kmax, nullptr, nullptr, nullptr) + dbl * sizeof(double) + 1024;
+}
+
+template <int D>
+static void launch_passes(int64_t C, int Kmax, const int32_t* K, const double* prm, const double* W,
+                          const double* rho_target, int64_t n_out, const int64_t* out_off,
+                          uint64_t seed, double dx, double q, int order, double* x_out,
+                          double* v_out, double* alpha_out, uint32_t* status_out, double* dA,
+                          unsigned char* recs, double* A, double* B, double* Cc, double* Dd,
+                          const SolvePlan& pl, const SolveWs& sw, const SolveWs& sw2,
+                          cudaStream_t s) {
+  size_t oh, oc, op;
+  rec_bytes(D, C, Kmax, &oh, &oc, &op);
+  double* raw = (double*)recs;
+  RecHead<D>* head = (RecHead<D>*)(recs + oh);
+  RecCoef<D>* coef = (RecCoef<D>*)(recs + oc);
+  RecComp<D>* comp = (RecComp<D>*)(recs + op);
+  const int P = pl.P;
+  trace_mark(nullptr, s);
+  const int ga = (int)((C + 255) / 256 < 4096 ? (C + 255) / 256 : 4096);
+  recon_prep_kernel<D><<<ga, 256, 0, s>>>(C, Kmax, K, prm, head, comp);
+  trace_mark("recon_prep_kernel", s);
+  // one warp per cell, 4 cells per CTA, at most 16 CTAs per SM resident
+  constexpr int NW = 4;
+  const int64_t ncta = (C + NW - 1) / NW;
+  const int g = (int)(ncta < 152 * 16 ? ncta : 152 * 16);
+  recon_stats_kernel<D, NW><<<g, NW * 32, 0, s>>>(C, Kmax, head, comp, out_off, n_out, seed, order,
+                                                  raw);
+  trace_mark("recon_stats_kernel", s);
+  assemble_kernel<D><<<ga, 256, 0, s>>>(C, head, raw, W, out_off, n_out, rho_target, dx, q, order,
+                                        A, B, Cc, Dd);
+  trace_mark("assemble_kernel", s);
+  if (pl.multi) {
+    mm_eliminate_kernel<<<(P + 127) / 128, 128, 0, s>>>(C, A, B, Cc, Dd, sw, P);
+    const int P2 = pl.P2;
+    mass_solve_kernel<<<1, P2 < 32 ? 32 : ((P2 + 31) / 32) * 32, 0, s>>>(
+        2 * (int64_t)P, sw.ra, sw.rb, sw.rc, sw.rd, sw.rz, sw2, P2);
+    mm_reconstruct_kernel<<<(P + 127) / 128, 128, 0, s>>>(C, sw, P, dA);
+  } else {
+    mass_solve_kernel<<<1, P < 32 ? 32 : ((P + 31) / 32) * 32, 0, s>>>(C, A, B, Cc, Dd, dA, sw, P);
+  }
+  trace_mark("mass-matrix solve (mass_solve_kernel and the blocked kernels)", s);
+  recon_coeffs_kernel<D><<<ga, 256, 0, s>>>(C, Kmax, head, comp, raw, out_off, n_out, W, dA, coef,
+                                            status_out);
+  trace_mark("recon_coeffs_kernel", s);
+  recon_emit_kernel<D, NW><<<g, NW * 32, 0, s>>>(C, Kmax, head, comp, coef, out_off, seed, dx,
+                                                 n_out, x_out, v_out, alpha_out);
+  trace_mark("recon_emit_kernel", s);
 }
 
 cudaError_t launch_reconstruct(int D, int64_t C, int Kmax, const int32_t* K, const double* prm,
@@ -460,12 +584,10 @@ cudaError_t launch_reconstruct(int D, int64_t C, int Kmax, const int32_t* K, con
                                int order, double* x_out, double* v_out, double* alpha_out,
                                uint32_t* status_out, double* dA_user, void* ws, cudaStream_t s) {
   if (C == 0) return cudaSuccess;
-  const int NVm = 3 + D + 1;
   const SolvePlan pl = plan_solve(C);
   const int P = pl.P;
-  double* base = (double*)ws;
-  double* cstat = base;
-  double* A = cstat + (size_t)NVm * C;
+  unsigned char* recs = (unsigned char*)ws;
+  double* A = (double*)(recs + rec_bytes(D, C, Kmax, nullptr, nullptr, nullptr));
   double* B = A + C;
   double* Cc = B + C;
   double* Dd = Cc + C;
@@ -489,44 +611,12 @@ cudaError_t launch_reconstruct(int D, int64_t C, int Kmax, const int32_t* K, con
     sw2.rz = q2 + 4 * R22; sw2.rcp = q2 + 5 * R22; sw2.ry = q2 + 6 * R22; sw2.rzz = q2 + 7 * R22;
   }
   if (dA_user) dA = dA_user;
-
-  trace_mark(nullptr, s);
-  // one warp per cell, 4 cells per CTA, at most 16 CTAs per SM resident
-  constexpr int NW = 4;
-  const int64_t ncta = (C + NW - 1) / NW;
-  const int g = (int)(ncta < 152 * 16 ? ncta : 152 * 16);
   if (D == 1)
-    recon_stats_kernel<1, NW><<<g, NW * 32, 0, s>>>(C, Kmax, K, prm, out_off, n_out, seed, order,
-                                                    cstat);
+    launch_passes<1>(C, Kmax, K, prm, W, rho_target, n_out, out_off, seed, dx, q, order, x_out,
+                     v_out, alpha_out, status_out, dA, recs, A, B, Cc, Dd, pl, sw, sw2, s);
   else
-    recon_stats_kernel<3, NW><<<g, NW * 32, 0, s>>>(C, Kmax, K, prm, out_off, n_out, seed, order,
-                                                    cstat);
-  trace_mark("recon_stats_kernel", s);
-  const int ga = (int)((C + 255) / 256 < 4096 ? (C + 255) / 256 : 4096);
-  if (D == 1)
-    assemble_kernel<1><<<ga, 256, 0, s>>>(C, cstat, W, out_off, n_out, rho_target, dx, q, A, B, Cc,
-                                          Dd);
-  else
-    assemble_kernel<3><<<ga, 256, 0, s>>>(C, cstat, W, out_off, n_out, rho_target, dx, q, A, B, Cc,
-                                          Dd);
-  trace_mark("assemble_kernel", s);
-  if (pl.multi) {
-    mm_eliminate_kernel<<<(P + 127) / 128, 128, 0, s>>>(C, A, B, Cc, Dd, sw, P);
-    const int P2 = pl.P2;
-    mass_solve_kernel<<<1, P2 < 32 ? 32 : ((P2 + 31) / 32) * 32, 0, s>>>(
-        2 * (int64_t)P, sw.ra, sw.rb, sw.rc, sw.rd, sw.rz, sw2, P2);
-    mm_reconstruct_kernel<<<(P + 127) / 128, 128, 0, s>>>(C, sw, P, dA);
-  } else {
-    mass_solve_kernel<<<1, P < 32 ? 32 : ((P + 31) / 32) * 32, 0, s>>>(C, A, B, Cc, Dd, dA, sw, P);
-  }
-  trace_mark("mass-matrix solve (mass_solve_kernel and the blocked kernels)", s);
-  if (D == 1)
-    recon_emit_kernel<1, NW><<<g, NW * 32, 0, s>>>(C, Kmax, K, prm, W, out_off, cstat, dA, seed, dx,
-                                                    n_out, x_out, v_out, alpha_out, status_out);
-  else
-    recon_emit_kernel<3, NW><<<g, NW * 32, 0, s>>>(C, Kmax, K, prm, W, out_off, cstat, dA, seed, dx,
-                                                    n_out, x_out, v_out, alpha_out, status_out);
-  trace_mark("recon_emit_kernel", s);
+    launch_passes<3>(C, Kmax, K, prm, W, rho_target, n_out, out_off, seed, dx, q, order, x_out,
+                     v_out, alpha_out, status_out, dA, recs, A, B, Cc, Dd, pl, sw, sw2, s);
   return cudaGetLastError();
 }
 

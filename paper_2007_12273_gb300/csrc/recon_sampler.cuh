@@ -52,62 +52,141 @@ struct RecCell {
   unsigned int status;
 };
 
-// load cell j's mixture: Cholesky factors (no floor; a non-positive pivot
-// gives a zero column, as for a degenerate stored covariance)
+// FP32 lower-triangular Cholesky factor (row-major) of a component's
+// covariance r[1 + D ..] (upper triangle), factored in FP64 with no floor: a
+// non-positive pivot gives a zero column, as for a degenerate stored
+// covariance
+template <int D>
+__device__ __forceinline__ void chol_f(const double* r, float* Lf) {
+  if (D == 1) {
+    const double s = r[2];
+    Lf[0] = (float)(s > 0.0 ? sqrt(s) : 0.0);
+  } else {
+    // S upper: [s00 s01 s02 s11 s12 s22]
+    const double s00 = r[4], s01 = r[5], s02 = r[6], s11 = r[7], s12 = r[8], s22 = r[9];
+    const double l00 = s00 > 0.0 ? sqrt(s00) : 0.0;
+    const double l10 = l00 > 0.0 ? s01 / l00 : 0.0;
+    const double l20 = l00 > 0.0 ? s02 / l00 : 0.0;
+    const double t11 = s11 - l10 * l10;
+    const double l11 = t11 > 0.0 ? sqrt(t11) : 0.0;
+    const double l21 = l11 > 0.0 ? (s12 - l20 * l10) / l11 : 0.0;
+    const double t22 = s22 - l20 * l20 - l21 * l21;
+    const double l22 = t22 > 0.0 ? sqrt(t22) : 0.0;
+    Lf[0] = (float)l00; Lf[1] = (float)l10; Lf[2] = (float)l11;
+    Lf[3] = (float)l20; Lf[4] = (float)l21; Lf[5] = (float)l22;
+  }
+}
+
+// the mixture-wide quantities of a cell's Kj components rj (records of P
+// values): the categorical thresholds (put_thr(k, t)), dz_k = mu_k - u
+// (put_dz(k, d, value)), the mean u and the spread theta
+template <int D, class PutThr, class PutDz>
+__device__ __forceinline__ void mix_head(const double* rj, int Kj, PutThr put_thr, PutDz put_dz,
+                                         double* u_out, double& theta) {
+  constexpr int P = 1 + D + D * (D + 1) / 2;
+  double cum = 0.0, u[D], th = 0.0;
+  for (int d = 0; d < D; ++d) u[d] = 0.0;
+  for (int q = 0; q < Kj; ++q) {
+    const double* r = rj + (size_t)q * P;
+    cum += r[0];
+    const double t = ceil(cum * 9007199254740992.0);  // 2^53
+    put_thr(q, t < 4.0e18 ? (long long)t : 4000000000000000000ll);
+    for (int d = 0; d < D; ++d) u[d] += r[0] * r[1 + d];
+  }
+  for (int q = 0; q < Kj; ++q) {
+    const double* r = rj + (size_t)q * P;
+    double tr = 0.0, dd = 0.0;
+    int t = 1 + D;
+    for (int x = 0; x < D; ++x)
+      for (int y = x; y < D; ++y, ++t) {
+        if (x == y) tr += r[t];
+      }
+    for (int d = 0; d < D; ++d) {
+      put_dz(q, d, r[1 + d] - u[d]);
+      dd += (r[1 + d] - u[d]) * (r[1 + d] - u[d]);
+    }
+    th += r[0] * (tr + dd);
+  }
+  for (int d = 0; d < D; ++d) u_out[d] = u[d];
+  theta = th;
+}
+
+// load cell j's mixture into the warp's RecCell: Cholesky factors on lanes
+// k < K, the rest on lane 0
 template <int D>
 __device__ void load_cell(RecCell<D>& rc, int64_t j, int Kmax, const int32_t* K,
                           const double* prm, int lane) {
-  constexpr int NM = D * (D + 1) / 2;
-  constexpr int P = 1 + D + NM;
+  constexpr int P = 1 + D + D * (D + 1) / 2;
   const int Kj = K[j];
-  const int k = lane;
-  if (k < Kj) {
-    const double* r = prm + ((size_t)j * Kmax + k) * P;
-    if (D == 1) {
-      const double s = r[2];
-      rc.Lf[k][0] = (float)(s > 0.0 ? sqrt(s) : 0.0);
-    } else {
-      // S upper: [s00 s01 s02 s11 s12 s22]
-      const double s00 = r[4], s01 = r[5], s02 = r[6], s11 = r[7], s12 = r[8], s22 = r[9];
-      const double l00 = s00 > 0.0 ? sqrt(s00) : 0.0;
-      const double l10 = l00 > 0.0 ? s01 / l00 : 0.0;
-      const double l20 = l00 > 0.0 ? s02 / l00 : 0.0;
-      const double t11 = s11 - l10 * l10;
-      const double l11 = t11 > 0.0 ? sqrt(t11) : 0.0;
-      const double l21 = l11 > 0.0 ? (s12 - l20 * l10) / l11 : 0.0;
-      const double t22 = s22 - l20 * l20 - l21 * l21;
-      const double l22 = t22 > 0.0 ? sqrt(t22) : 0.0;
-      rc.Lf[k][0] = (float)l00; rc.Lf[k][1] = (float)l10; rc.Lf[k][2] = (float)l11;
-      rc.Lf[k][3] = (float)l20; rc.Lf[k][4] = (float)l21; rc.Lf[k][5] = (float)l22;
-    }
-  }
+  const double* rj = prm + (size_t)j * Kmax * P;
+  if (lane < Kj) chol_f<D>(rj + (size_t)lane * P, rc.Lf[lane]);
   if (lane == 0) {
     rc.K = Kj;
-    double cum = 0.0, u[D], th = 0.0;
-    for (int d = 0; d < D; ++d) u[d] = 0.0;
-    for (int q = 0; q < Kj; ++q) {
-      const double* r = prm + ((size_t)j * Kmax + q) * P;
-      cum += r[0];
-      const double t = ceil(cum * 9007199254740992.0);  // 2^53
-      rc.thr[q] = t < 4.0e18 ? (long long)t : 4000000000000000000ll;
-      for (int d = 0; d < D; ++d) u[d] += r[0] * r[1 + d];
-    }
-    for (int q = 0; q < Kj; ++q) {
-      const double* r = prm + ((size_t)j * Kmax + q) * P;
-      double tr = 0.0, dd = 0.0;
-      int t = 1 + D;
-      for (int x = 0; x < D; ++x)
-        for (int y = x; y < D; ++y, ++t) {
-          if (x == y) tr += r[t];
-        }
-      for (int d = 0; d < D; ++d) {
-        rc.dz[q][d] = r[1 + d] - u[d];
-        dd += (r[1 + d] - u[d]) * (r[1 + d] - u[d]);
-      }
-      th += r[0] * (tr + dd);
-    }
-    for (int d = 0; d < D; ++d) rc.u[d] = u[d];
-    rc.theta = th;
+    mix_head<D>(
+        rj, Kj, [&](int q, long long t) { rc.thr[q] = t; },
+        [&](int q, int d, double x) { rc.dz[q][d] = x; }, rc.u, rc.theta);
+  }
+}
+
+// The same mixture data computed once per cell, by one thread per cell (the
+// FP64 square roots and divisions then run 32 cells to a warp instruction),
+// and kept in the workspace for the two particle passes: per cell a head
+// (u, theta, K) and Kmax component records (threshold, dz, FP32 factor).
+template <int D>
+struct RecHead {
+  double u[D];
+  double theta;
+  int K;
+  int pad;
+};
+template <int D>
+struct RecComp {
+  long long thr;
+  double dz[D];
+  float Lf[D * (D + 1) / 2];
+};
+template <int D>
+__device__ __forceinline__ void prep_cell(int64_t j, int Kmax, const int32_t* K, const double* prm,
+                                          RecHead<D>* head, RecComp<D>* comp) {
+  constexpr int P = 1 + D + D * (D + 1) / 2;
+  const int Kj = K[j];
+  const double* rj = prm + (size_t)j * Kmax * P;
+  RecComp<D>* cj = comp + (size_t)j * Kmax;
+  RecHead<D> h;
+  mix_head<D>(
+      rj, Kj, [&](int q, long long t) { cj[q].thr = t; },
+      [&](int q, int d, double x) { cj[q].dz[d] = x; }, h.u, h.theta);
+  h.K = Kj;
+  h.pad = 0;
+  head[j] = h;
+  for (int q = 0; q < Kj; ++q) {
+    float Lf[D * (D + 1) / 2];
+    chol_f<D>(rj + (size_t)q * P, Lf);
+    for (int m = 0; m < D * (D + 1) / 2; ++m) cj[q].Lf[m] = Lf[m];
+  }
+}
+// copy cell j's prepared mixture into the warp's RecCell (lanes k < K copy
+// component k, lane 0 the head)
+template <int D>
+__device__ __forceinline__ void load_prepped(RecCell<D>& rc, int64_t j, int Kmax,
+                                             const RecHead<D>* head, const RecComp<D>* comp,
+                                             int lane) {
+  constexpr int NM = D * (D + 1) / 2;
+  const int Kj = head[j].K;
+  if (lane < Kj) {
+    const RecComp<D>& c = comp[(size_t)j * Kmax + lane];
+    rc.thr[lane] = c.thr;
+#pragma unroll
+    for (int d = 0; d < D; ++d) rc.dz[lane][d] = c.dz[d];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) rc.Lf[lane][m] = c.Lf[m];
+  }
+  if (lane == 0) {
+    const RecHead<D>& h = head[j];
+    rc.K = Kj;
+#pragma unroll
+    for (int d = 0; d < D; ++d) rc.u[d] = h.u[d];
+    rc.theta = h.theta;
   }
 }
 
@@ -207,44 +286,63 @@ __device__ __forceinline__ double centred52(uint64_t m) {
 // the position uniform u0 = (m + 1/2) 2^-52 = (2 m + 1) 2^-53 of a 52-bit m
 __device__ __forceinline__ double uniform_pos52(uint64_t m) { return odd_2m53(2ull * m + 1ull, false); }
 
-// Lemons projection of a cell with n resampled particles (lane 0): the
-// corrected weight alpha' = W_j / n + dA_j and, from the sums sw[d] =
-// sum_p w_d and sw[D] = sum_p |w|^2 (w = v - u), the scale a and shift
-// beta of eqs. (alpha), (beta) in the frame of the mixture mean u:
+// Lemons projection of a cell with n resampled particles: the corrected
+// weight alpha' = W_j / n + dA_j and, from the sums sw[d] = sum_p w_d and
+// sw[D] = sum_p |w|^2 (w = v - u), the scale a and shift beta of eqs.
+// (alpha), (beta) in the frame of the mixture mean u:
 // 2 E N' - p^2 = W (N' theta + (N' - W) |u|^2),
-// 2 E' N' - p'^2 = alpha'^2 (n sum|w|^2 - |sum w|^2).  Returns the status.
+// 2 E' N' - p'^2 = alpha'^2 (n sum|w|^2 - |sum w|^2).
 template <int D>
-__device__ unsigned int projection_coeffs(RecCell<D>& rc, int64_t n, double Wj, double dAj,
-                                          const double* sw) {
+struct ProjCoef {
+  double a, beta[D], alpha_new;
+  int skip;
+  unsigned int status;
+};
+template <int D>
+__device__ __forceinline__ ProjCoef<D> proj_coeffs(int K, const double* u, double theta, int64_t n,
+                                                   double Wj, double dAj, const double* sw) {
+  ProjCoef<D> pc;
   unsigned int st = 0;
   if (n == 0) st |= GM_ST_MM_EMPTY_COL;
   const double an = (n > 0 ? Wj / (double)n : 0.0) + dAj;
-  rc.alpha_new = an;
+  pc.alpha_new = an;
   if (n > 0 && !(an > 0.0)) st |= GM_ST_NEG_WEIGHT;
-  rc.skip = 1;
-  rc.a = 1.0;
-  for (int d = 0; d < D; ++d) rc.beta[d] = 0.0;
-  if (n > 0 && rc.K == 0) st |= GM_ST_NO_MIXTURE;
-  if (n > 0 && rc.K > 0) {
+  pc.skip = 1;
+  pc.a = 1.0;
+  for (int d = 0; d < D; ++d) pc.beta[d] = 0.0;
+  if (n > 0 && K == 0) st |= GM_ST_NO_MIXTURE;
+  if (n > 0 && K > 0) {
     const double Np = (double)n * an;
     double u2 = 0.0, sw2 = 0.0;
     for (int d = 0; d < D; ++d) {
-      u2 += rc.u[d] * rc.u[d];
+      u2 += u[d] * u[d];
       sw2 += sw[d] * sw[d];
     }
-    const double num = Wj * (Np * rc.theta + (Np - Wj) * u2);
+    const double num = Wj * (Np * theta + (Np - Wj) * u2);
     const double den = an * an * ((double)n * sw[D] - sw2);
     if (num > 0.0 && den > 0.0 && Np > 0.0) {
       const double aa = sqrt(num / den);
-      rc.a = aa;
-      for (int d = 0; d < D; ++d) rc.beta[d] = ((Wj - Np) * rc.u[d] - aa * an * sw[d]) / (aa * Np);
-      rc.skip = 0;
+      pc.a = aa;
+      for (int d = 0; d < D; ++d) pc.beta[d] = ((Wj - Np) * u[d] - aa * an * sw[d]) / (aa * Np);
+      pc.skip = 0;
     } else {
       st |= GM_ST_PROJ_SKIPPED;
     }
   }
-  rc.status = st;
-  return st;
+  pc.status = st;
+  return pc;
+}
+// the same on the warp's RecCell (lane 0); returns the status
+template <int D>
+__device__ unsigned int projection_coeffs(RecCell<D>& rc, int64_t n, double Wj, double dAj,
+                                          const double* sw) {
+  const ProjCoef<D> pc = proj_coeffs<D>(rc.K, rc.u, rc.theta, n, Wj, dAj, sw);
+  rc.alpha_new = pc.alpha_new;
+  rc.a = pc.a;
+  for (int d = 0; d < D; ++d) rc.beta[d] = pc.beta[d];
+  rc.skip = pc.skip;
+  rc.status = pc.status;
+  return pc.status;
 }
 
 }  // namespace gmcr

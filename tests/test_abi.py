@@ -90,7 +90,7 @@ def test_argument_errors_without_gpu(lib):
 
 
 def test_noalloc_scratch_holds_its_cell_limit(lib):
-    """The static scratch of gm_reconstruct_noalloc (5 MiB) holds the
+    """The static scratch of gm_reconstruct_noalloc (40 MiB) holds the
     workspace of its advertised 32768-cell limit for D = 1 and D = 3
     (host-side layout arithmetic, no device access)."""
     assert lib.gm_noalloc_limits_ok() == 1
