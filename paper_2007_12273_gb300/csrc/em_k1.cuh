@@ -1,10 +1,10 @@
-// em_k1.cuh -- one warp per cell for the cells whose fit is known in closed
-// form before any EM sweep: empty and degenerate cells, and cells started
-// from a supplied mixture (gm_compress_from) with exactly one valid
-// component.  With K = 1 every responsibility is the particle's weight, so
-// one EM step from any start gives the weighted sample mean and covariance
-// and the final unpenalised step (Sec. 2.3.1) returns them unchanged; eq.
-// (lnL-GM) is then -(N/2)(D ln 2 pi + ln|Sigma| + D) - (T/2) ln N.
+// em_k1.cuh -- the cells whose fit is known in closed form before any EM
+// sweep: empty and degenerate cells, and cells started from a supplied
+// mixture (gm_compress_from) with exactly one valid component.  With K = 1
+// every responsibility is the particle's weight, so one EM step from any
+// start gives the weighted sample mean and covariance and the final
+// unpenalised step (Sec. 2.3.1) returns them unchanged; eq. (lnL-GM) is then
+// -(N/2)(D ln 2 pi + ln|Sigma| + D) - (T/2) ln N.
 //
 // Every other cell is appended to a work list that the persistent EM kernel
 // takes its cells from.  The decisions and outputs are those of the EM
@@ -13,10 +13,14 @@
 // supplied component), so a cell's result does not depend on which kernel
 // fitted it beyond the summation order of its FP64 moments.
 //
-// A warp per cell instead of a CTA: no CTA barriers, and the per-cell FP64
-// work (GB300 runs FP64 at 1/64 of the FP32 rate) spread over the lanes --
-// the particle sums lane-parallel, the moments reduced by recursive halving
-// (one FP64 add per shuffle), the three coordinate scales on three lanes.
+// Two kernels.  em_k1_kernel, one warp per cell, reads the particles and
+// writes the cell's moment sums to a per-cell record (exact 128-bit integer
+// sums for an equal-weight cell, FP64 sums otherwise); em_k1_finish_kernel,
+// one thread per cell, turns them into the mean, the covariance, the floor
+// and validity tests and eq. (lnL-GM).  The per-cell FP64 work (a square
+// root, reciprocals, logarithms, the pivots) thus runs 32 cells to a warp
+// instruction: GB300 runs FP64 at 1/64 of the FP32 rate, and a warp-uniform
+// FP64 instruction costs the pipe as much as a full one.
 #pragma once
 
 #include "em_kernel.cuh"
@@ -72,14 +76,14 @@ __device__ __forceinline__ bool ldl_floor(const double* S, const double* sc2, do
 // once per cell -- no FP64 arithmetic per particle, where GB300's FP64 pipe
 // (1/64 of the FP32 rate) bounds the FP64 sums.
 // ---------------------------------------------------------------------------
-// the FP64 sums [sum alpha, sum alpha d (D), sum alpha d d^T (upper, NM)] of
-// an equal-weight cell (weight a0, n particles, velocities v[d * ldv + p],
-// shift sh = v[., 0]) on the integer pipe, lane-parallel over particles;
-// every lane returns them.  Returns false (nothing written) when a velocity
-// is not finite.
+// the 128-bit sums [sum d (D), sum d d^T (upper, NM)] of an equal-weight
+// cell (n particles, velocities v[d * ldv + p], shift = the first particle)
+// in units of 2^eq_d (2^(eq_x + eq_y) for the products), on the integer
+// pipe, lane-parallel over particles; every lane returns them.  Returns
+// false (nothing written) when a velocity is not finite.
 template <int D>
-__device__ bool fixed_moments(const float* __restrict__ v, int64_t ldv, int n, double a0, int lane,
-                              double* res) {
+__device__ bool fixed_sums(const float* __restrict__ v, int64_t ldv, int n, int lane,
+                           __int128 (&s1)[D], __int128 (&s2)[D * (D + 1) / 2], int (&eq)[D]) {
   constexpr int NM = D * (D + 1) / 2;
   // the largest biased exponent per dimension
   int emax[D];
@@ -88,7 +92,6 @@ __device__ bool fixed_moments(const float* __restrict__ v, int64_t ldv, int n, d
   for (int p = lane; p < n; p += 32)
 #pragma unroll
     for (int d = 0; d < D; ++d) emax[d] = max(emax[d], (int)((__float_as_uint(v[d * ldv + p]) >> 23) & 0xFFu));
-  int eq[D];
   bool ok = true;
 #pragma unroll
   for (int d = 0; d < D; ++d) {
@@ -101,7 +104,6 @@ __device__ bool fixed_moments(const float* __restrict__ v, int64_t ldv, int n, d
   long long s0[D];
 #pragma unroll
   for (int d = 0; d < D; ++d) s0[d] = fixq(v[d * ldv], eq[d]);
-  __int128 s1[D], s2[NM];
 #pragma unroll
   for (int d = 0; d < D; ++d) s1[d] = 0;
 #pragma unroll
@@ -126,16 +128,21 @@ __device__ bool fixed_moments(const float* __restrict__ v, int64_t ldv, int n, d
 #pragma unroll
     for (int t = 0; t < NM; ++t) s2[t] += shfl_xor_i128(s2[t], o);
   }
-  res[0] = (double)n * a0;
-#pragma unroll
-  for (int d = 0; d < D; ++d) res[1 + d] = a0 * i128_to_f64(s1[d], eq[d]);
-  int t = 0;
-#pragma unroll
-  for (int x = 0; x < D; ++x)
-#pragma unroll
-    for (int y = x; y < D; ++y, ++t) res[1 + D + t] = a0 * i128_to_f64(s2[t], eq[x] + eq[y]);
   return true;
 }
+
+// Per-cell record between the two kernels.  fixed = 1: the integer sums
+// (sum t as (low, high) halves in words 2t, 2t+1; t < D the first moments,
+// then the NM second moments), their exponents eq and the common weight a0;
+// fixed = 0: the FP64 sums [sum alpha, sum alpha d (D), sum alpha d d^T] in
+// words 0 .. NS-1.
+template <int D>
+struct alignas(16) K1Raw {
+  double w[2 * (D + D * (D + 1) / 2)];
+  double a0;
+  int eq[D];
+  int fixed;
+};
 
 struct K1Params {
   int64_t C, n;
@@ -153,18 +160,23 @@ struct K1Params {
   uint32_t* status_out;
   unsigned int* list;        // cells left to the EM kernel
   unsigned int* list_count;  // their number (zeroed before the launch)
+  void* raw;                 // K1Raw<D> [C]
   int Kmax;
 };
 
+// Pass 1, one warp per cell: cells with several (or no) supplied components
+// go to the EM kernel's list; for the others the moment sums about the first
+// particle go to the cell's K1Raw record, and the parameter slots past the
+// first are cleared.
 template <int D, typename VT, int NW>
 __global__ void __launch_bounds__(NW * 32) em_k1_kernel(K1Params a) {
   constexpr int NM = D * (D + 1) / 2;
   constexpr int NS = 1 + D + NM;
   constexpr int NP = NS <= 4 ? 4 : 16;
   constexpr int P = 1 + D + NM;
-  constexpr int T = D * (D + 3) / 2;
   const int lane = threadIdx.x & 31;
   const VT* __restrict__ vin = static_cast<const VT*>(a.v);
+  K1Raw<D>* raw = static_cast<K1Raw<D>*>(a.raw);
   for (int64_t j = ((int64_t)blockIdx.x * NW + (threadIdx.x >> 5)); j < a.C;
        j += (int64_t)gridDim.x * NW) {
     const int64_t off = a.cell_off[j];
@@ -174,25 +186,50 @@ __global__ void __launch_bounds__(NW * 32) em_k1_kernel(K1Params a) {
       if (lane == 0) a.list[atomicAdd(a.list_count, 1u)] = (unsigned int)j;
       continue;
     }
-    // ---- moments about the first particle ------------------------------
-    double sh[D];
-#pragma unroll
-    for (int d = 0; d < D; ++d) sh[d] = N > 0 ? to_f64(vin[(int64_t)d * a.n + off]) : 0.0;
-    double res[NS];
+    // slots 1 .. Kmax-1 are zero in every closed-form result (a cell that
+    // the finishing pass hands to EM is rewritten whole by the EM kernel)
+    double* prm_out = a.params_out + (size_t)j * a.Kmax * P;
+    for (int i = P + lane; i < a.Kmax * P; i += 32) prm_out[i] = 0.0;
+    if (N == 0) continue;
+    K1Raw<D>& r = raw[j];
     bool fixed = false;
     if constexpr (sizeof(VT) == 4) {
-      // equal weights (bit for bit) and at most 2^14 particles: exact sums
-      // on the integer pipe
-      if (N > 0 && N <= kFixMaxN) {
+      // equal weights (bit for bit, positive) and at most 2^14 particles:
+      // exact sums on the integer pipe
+      if (N <= kFixMaxN) {
         const long long a0b = __double_as_longlong(a.alpha[off]);
         bool same = true;
         for (int p = lane; p < N; p += 32) same = same && (__double_as_longlong(a.alpha[off + p]) == a0b);
-        if (__all_sync(0xffffffffu, same) && __longlong_as_double(a0b) > 0.0)
-          fixed = fixed_moments<D>(reinterpret_cast<const float*>(vin) + off, a.n, N,
-                                   __longlong_as_double(a0b), lane, res);
+        // a0 > 0 on the bits: positive sign, not a NaN
+        if (__all_sync(0xffffffffu, same) && a0b > 0 && a0b <= 0x7FF0000000000000ll) {
+          __int128 s1[D], s2[NM];
+          int eq[D];
+          fixed = fixed_sums<D>(reinterpret_cast<const float*>(vin) + off, a.n, N, lane, s1, s2, eq);
+          if (fixed) {
+            __int128 mine = 0;
+#pragma unroll
+            for (int t = 0; t < D; ++t)
+              if (lane == t) mine = s1[t];
+#pragma unroll
+            for (int t = 0; t < NM; ++t)
+              if (lane == D + t) mine = s2[t];
+            if (lane < D + NM)
+              *reinterpret_cast<longlong2*>(&r.w[2 * lane]) =
+                  make_longlong2((long long)(unsigned long long)mine, (long long)(mine >> 64));
+            if (lane == 0) {
+              r.a0 = __longlong_as_double(a0b);
+#pragma unroll
+              for (int d = 0; d < D; ++d) r.eq[d] = eq[d];
+              r.fixed = 1;
+            }
+          }
+        }
       }
     }
     if (!fixed) {  // FP64 sums
+      double sh[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) sh[d] = to_f64(vin[(int64_t)d * a.n + off]);
       double acc[NP];
 #pragma unroll
       for (int i = 0; i < NP; ++i) acc[i] = 0.0;
@@ -212,25 +249,78 @@ __global__ void __launch_bounds__(NW * 32) em_k1_kernel(K1Params a) {
         }
       }
       warp_rs_d<NP>(acc, lane);
+      double mine = 0.0;
 #pragma unroll
-      for (int q = 0; q < NS; ++q) res[q] = __shfl_sync(0xffffffffu, acc[0], warp_rs_lane<NP>(q));
+      for (int q = 0; q < NS; ++q) {
+        const double t = __shfl_sync(0xffffffffu, acc[0], warp_rs_lane<NP>(q));
+        if (lane == q) mine = t;
+      }
+      if (lane < NS) r.w[lane] = mine;
+      if (lane == 0) r.fixed = 0;
+    }
+  }
+}
+
+// Pass 2, one thread per cell: the closed-form result of every cell that
+// pass 1 did not list, or its hand-over to the EM kernel's list.
+template <int D, typename VT>
+__global__ void em_k1_finish_kernel(K1Params a) {
+  constexpr int NM = D * (D + 1) / 2;
+  constexpr int NS = 1 + D + NM;
+  constexpr int P = 1 + D + NM;
+  constexpr int T = D * (D + 3) / 2;
+  const VT* __restrict__ vin = static_cast<const VT*>(a.v);
+  const K1Raw<D>* raw = static_cast<const K1Raw<D>*>(a.raw);
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < a.C;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t off = a.cell_off[j];
+    const int N = (int)(a.cell_off[j + 1] - off);
+    const int K0 = a.init_K[j] < a.Kmax ? a.init_K[j] : a.Kmax;
+    if (K0 != 1 && N > 0) continue;  // listed by pass 1
+    // ---- moments about the first particle ------------------------------
+    double sh[D], res[NS];
+#pragma unroll
+    for (int d = 0; d < D; ++d) sh[d] = N > 0 ? to_f64(vin[(int64_t)d * a.n + off]) : 0.0;
+#pragma unroll
+    for (int q = 0; q < NS; ++q) res[q] = 0.0;
+    if (N > 0) {
+      const K1Raw<D>& r = raw[j];
+      if (r.fixed) {
+        const double a0 = r.a0;
+        res[0] = (double)N * a0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          const longlong2 h = *reinterpret_cast<const longlong2*>(&r.w[2 * d]);
+          res[1 + d] = a0 * i128_to_f64(((__int128)h.y << 64) | (__int128)(unsigned long long)h.x, r.eq[d]);
+        }
+        int t = 0;
+#pragma unroll
+        for (int x = 0; x < D; ++x)
+#pragma unroll
+          for (int y = x; y < D; ++y, ++t) {
+            const longlong2 h = *reinterpret_cast<const longlong2*>(&r.w[2 * (D + t)]);
+            res[1 + D + t] =
+                a0 * i128_to_f64(((__int128)h.y << 64) | (__int128)(unsigned long long)h.x, r.eq[x] + r.eq[y]);
+          }
+      } else {
+#pragma unroll
+        for (int q = 0; q < NS; ++q) res[q] = r.w[q];
+      }
     }
     const double W = res[0];
     double* prm_out = a.params_out + (size_t)j * a.Kmax * P;
     const unsigned int too_few = (N <= 10) ? GM_ST_TOO_FEW : 0u;
     if (N == 0 || !(W > 0.0)) {  // empty cell
-      for (int i = lane; i < a.Kmax * P; i += 32) prm_out[i] = 0.0;
-      if (lane == 0) {
-        a.K_out[j] = 0;
-        a.W_out[j] = N == 0 ? 0.0 : W;
-        a.lnL_out[j] = 0.0;
-        if (a.sweeps_out) a.sweeps_out[j] = 0;
-        if (a.kwork_out) a.kwork_out[j] = 0;
-        a.status_out[j] = N == 0 ? GM_ST_EMPTY : (GM_ST_EMPTY | GM_ST_DEGENERATE);
-      }
+      for (int i = 0; i < P; ++i) prm_out[i] = 0.0;
+      a.K_out[j] = 0;
+      a.W_out[j] = N == 0 ? 0.0 : W;
+      a.lnL_out[j] = 0.0;
+      if (a.sweeps_out) a.sweeps_out[j] = 0;
+      if (a.kwork_out) a.kwork_out[j] = 0;
+      a.status_out[j] = N == 0 ? GM_ST_EMPTY : (GM_ST_EMPTY | GM_ST_DEGENERATE);
       continue;
     }
-    // mean and covariance (every lane: the values are warp-uniform)
+    // mean and covariance
     const double rW = rcp_nr(W);
     double mean[D], dm[D], cov[NM];
 #pragma unroll
@@ -247,52 +337,37 @@ __global__ void __launch_bounds__(NW * 32) em_k1_kernel(K1Params a) {
     }
     // the covariance floor 1e-13 sum_d (cov_dd + mean_d^2) (degenerate cell)
     // and, on success, |Sigma| = the product of the pivots
-    int ok = 1;
     double det = 1.0;
-    if (lane == 0) {
+    bool ok;
+    {
       double scale2 = 0.0;
       for (int d = 0; d < D; ++d) scale2 += cov[tri<D>(d, d)] + mean[d] * mean[d];
       const double one[3] = {1.0, 1.0, 1.0};
       ok = ldl_floor<D>(cov, one, 1e-13 * scale2, det);
     }
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    det = __shfl_sync(0xffffffffu, det, 0);
     if (!ok) {  // degenerate: the cell's moments, flagged
-      for (int i = lane; i < a.Kmax * P; i += 32) {
-        double val = 0.0;
-        if (i == 0) val = 1.0;
-        else if (i < 1 + D) val = mean[i - 1];
-        else if (i < P) val = cov[i - 1 - D];
-        prm_out[i] = val;
-      }
-      if (lane == 0) {
-        a.K_out[j] = 1;
-        a.W_out[j] = W;
-        a.lnL_out[j] = 0.0;
-        if (a.sweeps_out) a.sweeps_out[j] = 0;
-        if (a.kwork_out) a.kwork_out[j] = 0;
-        a.status_out[j] = too_few | GM_ST_DEGENERATE | GM_ST_COV_NOT_PD;
-      }
+      prm_out[0] = 1.0;
+      for (int d = 0; d < D; ++d) prm_out[1 + d] = mean[d];
+      for (int t = 0; t < NM; ++t) prm_out[1 + D + t] = cov[t];
+      a.K_out[j] = 1;
+      a.W_out[j] = W;
+      a.lnL_out[j] = 0.0;
+      if (a.sweeps_out) a.sweeps_out[j] = 0;
+      if (a.kwork_out) a.kwork_out[j] = 0;
+      a.status_out[j] = too_few | GM_ST_DEGENERATE | GM_ST_COV_NOT_PD;
       continue;
     }
     // ---- the supplied component: valid (weight > 0, Cholesky floor in
     // whitened coordinates, as chol_whitened) and not capped away by
     // N - T K / 2 > 0 ------------------------------------------------------
     double sc[D], isc[D];
-    {
-      // lane d < D takes coordinate d's scale (one sqrt and one reciprocal
-      // for all D)
-      double cdd = cov[0];
-      if (D == 3) cdd = lane == 1 ? cov[tri<D>(1, 1)] : (lane == 2 ? cov[tri<D>(2, 2)] : cov[0]);
-      const double s1 = sqrt(cdd), i1 = rcp_nr(s1);
 #pragma unroll
-      for (int d = 0; d < D; ++d) {
-        sc[d] = __shfl_sync(0xffffffffu, s1, d);
-        isc[d] = __shfl_sync(0xffffffffu, i1, d);
-      }
+    for (int d = 0; d < D; ++d) {
+      sc[d] = sqrt(cov[tri<D>(d, d)]);
+      isc[d] = rcp_nr(sc[d]);
     }
-    int valid = 0;
-    if (lane == 0) {
+    bool valid;
+    {
       const double* r = a.init_prm + (size_t)j * a.Kmax * P;
       double Sw[NM], sc2[3], scale2 = 0.0, dw;
       for (int d = 0; d < D; ++d) {
@@ -305,32 +380,23 @@ __global__ void __launch_bounds__(NW * 32) em_k1_kernel(K1Params a) {
         for (int yy = x; yy < D; ++yy, ++q) Sw[q] = r[1 + D + q] * isc[x] * isc[yy];
       valid = (r[0] > 0.0) && ldl_floor<D>(Sw, sc2, 1e-13 * scale2, dw);
     }
-    valid = __shfl_sync(0xffffffffu, valid, 0);
     if (!valid) {  // no component left: the paper's initialisation, by EM
-      if (lane == 0) a.list[atomicAdd(a.list_count, 1u)] = (unsigned int)j;
+      a.list[atomicAdd(a.list_count, 1u)] = (unsigned int)j;
       continue;
     }
-    // ln|Sigma| (lane 0) and ln N (lane 1) in one logarithm
-    const double lg = log(lane == 1 ? (double)N : det);
-    const double logdet = __shfl_sync(0xffffffffu, lg, 0), logN = __shfl_sync(0xffffffffu, lg, 1);
     // ---- closed form ---------------------------------------------------------
-    for (int i = lane; i < a.Kmax * P; i += 32) {
-      double val = 0.0;
-      if (i == 0) val = 1.0;
-      else if (i < 1 + D) val = mean[i - 1];
-      else if (i < P) val = cov[i - 1 - D];
-      prm_out[i] = val;
-    }
-    if (lane == 0) {
-      const double Nd = (double)N;
-      a.K_out[j] = 1;
-      a.W_out[j] = W;
-      a.lnL_out[j] = -0.5 * Nd * ((double)D * 1.8378770664093454836 + logdet + (double)D) -
-                     0.5 * (double)T * logN;
-      if (a.sweeps_out) a.sweeps_out[j] = 1;
-      if (a.kwork_out) a.kwork_out[j] = 0;
-      a.status_out[j] = too_few;
-    }
+    const double logdet = log(det), logN = log((double)N);
+    prm_out[0] = 1.0;
+    for (int d = 0; d < D; ++d) prm_out[1 + d] = mean[d];
+    for (int t = 0; t < NM; ++t) prm_out[1 + D + t] = cov[t];
+    const double Nd = (double)N;
+    a.K_out[j] = 1;
+    a.W_out[j] = W;
+    a.lnL_out[j] = -0.5 * Nd * ((double)D * 1.8378770664093454836 + logdet + (double)D) -
+                   0.5 * (double)T * logN;
+    if (a.sweeps_out) a.sweeps_out[j] = 1;
+    if (a.kwork_out) a.kwork_out[j] = 0;
+    a.status_out[j] = too_few;
   }
 }
 

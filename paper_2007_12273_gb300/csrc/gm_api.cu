@@ -284,14 +284,16 @@ static int compress_impl(const gm_config* cfg, int64_t C, int64_t n_particles,
   if ((int64_t)(D + 4) * sstride >= ((int64_t)1 << 31))
     return fail(GM_ERR_ARG, "too many particles for one call (%lld)", (long long)n_particles);
   const size_t scr_bytes = align256((size_t)sstride * (D + 4) * sizeof(float));
+  const size_t k1_bytes = init_K ? align256(gmcr::em_k1_raw_bytes(D, C)) : 0;
   void* ws = nullptr;
-  if ((rc = ws_get(q_bytes + part_bytes + list_bytes + scr_bytes, &ws))) return rc;
+  if ((rc = ws_get(q_bytes + part_bytes + list_bytes + scr_bytes + k1_bytes, &ws))) return rc;
   char* wb = (char*)ws;
   unsigned int* queue = (unsigned int*)wb;
   unsigned int* list_count = queue + 1;
   double* part = (double*)(wb + q_bytes);
   unsigned int* list = init_K ? (unsigned int*)(wb + q_bytes + part_bytes) : nullptr;
   float* scratch = (float*)(wb + q_bytes + part_bytes + list_bytes);
+  void* k1_raw = init_K ? (void*)(wb + q_bytes + part_bytes + list_bytes + scr_bytes) : nullptr;
 
   cudaError_t e = cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned int), s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
@@ -346,10 +348,10 @@ static int compress_impl(const gm_config* cfg, int64_t C, int64_t n_particles,
     kp.status_out = status_out;
     kp.list = list;
     kp.list_count = list_count;
+    kp.raw = k1_raw;
     kp.Kmax = cfg->Kmax;
     e = gmcr::launch_em_k1(D, v_is_f64, kp, sms, s);
     if (e != cudaSuccess) return cuda_fail(e, "closed-form pre-pass launch");
-    gmcr::trace_mark("em_k1_kernel", s);
   }
   e = D == 1 ? gmcr::launch_em1(p, nt, fp64_mstep, v_is_f64, smem, (int)grid, s)
              : gmcr::launch_em3(p, nt, fp64_mstep, v_is_f64, smem, (int)grid, s);

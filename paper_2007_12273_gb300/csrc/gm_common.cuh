@@ -165,11 +165,16 @@ __device__ __forceinline__ void shape3(int order, double xi, double& wm, double&
   }
 }
 
-// fractional position of x inside cell j (clamped to [0,1))
+// fractional position of x inside cell j, clamped to [0, 1): below 0 (and
+// -inf) to 0, from 1 up (+inf, NaN) to 1 - 2^-53.  One FP64 operation; the
+// clamp compares the bit pattern on the integer pipe (the sign bit, then
+// the magnitude against those of 1.0 and of the infinities).
 __device__ __forceinline__ double cell_frac(double x, int64_t j, double inv_dx) {
-  double xi = x * inv_dx - (double)j;
-  xi = xi < 0.0 ? 0.0 : xi;
-  return xi < 1.0 ? xi : 0.99999999999999989;
+  const double xi = x * inv_dx - (double)j;
+  const long long b = __double_as_longlong(xi);
+  const unsigned long long mag = (unsigned long long)b & 0x7FFFFFFFFFFFFFFFull;
+  if (mag > 0x7FF0000000000000ull || (b >= 0 && mag >= 0x3FF0000000000000ull)) return 0.99999999999999989;
+  return b < 0 ? 0.0 : xi;
 }
 
 }  // namespace gmcr

@@ -7,13 +7,18 @@
 // and to the velocity's offset from the mixture mean (so that both passes
 // see the same w = v - u, which is what makes the projected moments exact);
 // the categorical choice is decided on integers and the Gaussian draw is
-// FP32 (GB300 runs FP64 at 1/64 of the FP32 rate).  The pipeline therefore never
-// writes unprojected particles: pass 1 regenerates every particle to
-// accumulate the per-cell mass-matrix column and the velocity sums, a small
-// FP64 solve gives dA, and pass 2 regenerates the particles once more and
-// writes the final positions, projected velocities and corrected weights.
-// HBM traffic is the output alone: 8 (x) + 8 D (v) + 8 (alpha) bytes per
-// particle.
+// FP32 (GB300 runs FP64 at 1/64 of the FP32 rate).  The pipeline never
+// writes unprojected particles:
+//   pass 0 (one thread per cell) prepares each cell's mixture data;
+//   pass 1 (one warp per cell) draws every particle, accumulates the
+//     per-cell mass-matrix column and the velocity sums, and stages the
+//     draw (20 bytes) in the particle's own output slots;
+//   a small FP64 solve gives dA, and one thread per cell the projection
+//     coefficients;
+//   pass 2 (one warp per cell) reads each staged draw back and writes the
+//     final position, projected velocity and corrected weight over it.
+// HBM traffic: the staged draws (written once, read once) and the output,
+// 8 (x) + 8 D (v) + 8 (alpha) bytes per particle.
 #include "recon_sampler.cuh"
 
 namespace gmcr {
@@ -54,6 +59,36 @@ __device__ __forceinline__ void fix_exponents(const float* L, int (&eq)[D]) {
     eq[d] = (eb ? eb - 127 : -126) + 1 - kFixBits;
   }
 }
+// Pass 1 stages each particle's draw in the caller's output slots of that
+// same particle, and pass 2 reads it back before it overwrites them with
+// the final values (one thread reads, then writes, each particle's slots,
+// so no other particle's staging is ever touched): x_out[p] holds the
+// position integer m0 (52 bits) and the component z (bits 56-63),
+// alpha_out[p] the FP32 pair (f_0, f_1), v_out[0][p] (D = 3) the FP32 f_2.
+// The second pass then needs neither the Philox draws nor the Box-Muller
+// transform of the first.
+template <int D>
+__device__ __forceinline__ void stage_draw(double* x_out, double* v_out, double* alpha_out,
+                                           int64_t p, uint64_t m0, int z, const float (&f)[D]) {
+  reinterpret_cast<unsigned long long*>(x_out)[p] = m0 | ((unsigned long long)(z & 0xFF) << 56);
+  reinterpret_cast<float2*>(alpha_out)[p] = make_float2(f[0], D == 3 ? f[1] : 0.0f);
+  if (D == 3) reinterpret_cast<float2*>(v_out)[p] = make_float2(f[D - 1], 0.0f);
+}
+template <int D>
+__device__ __forceinline__ void load_draw(const double* x_out, const double* v_out,
+                                          const double* alpha_out, int64_t p, uint64_t& m0, int& z,
+                                          float (&f)[D]) {
+  const unsigned long long t = reinterpret_cast<const unsigned long long*>(x_out)[p];
+  m0 = t & ((1ull << 52) - 1ull);
+  z = (int)(t >> 56);
+  const float2 a = reinterpret_cast<const float2*>(alpha_out)[p];
+  f[0] = a.x;
+  if (D == 3) {
+    f[1] = a.y;
+    f[D - 1] = reinterpret_cast<const float2*>(v_out)[p].x;
+  }
+}
+
 // the unit-weight shape sums of a cell's n particles on nodes j-1, j, j+1
 // (cs[0], cs[1], cs[2]): c- = (n/4 - S1 + S2) / 2, c+ = (n/4 + S1 + S2) / 2,
 // c0 = 3n/4 - S2 for the quadratic B-spline; c- = sum max(-s, 0),
@@ -125,11 +160,13 @@ __global__ void recon_prep_kernel(int64_t C, int Kmax, const int32_t* K, const d
 // Pass 1, one warp per cell: the position and velocity sums of the cell's
 // resampled particles (raw_words layout above).
 template <int D, int NW>
-__global__ void __launch_bounds__(NW * 32) recon_stats_kernel(int64_t C, int Kmax,
+__global__ void __launch_bounds__(NW * 32, 6) recon_stats_kernel(int64_t C, int Kmax,
                                                               const RecHead<D>* head,
                                                               const RecComp<D>* comp,
                                                               const int64_t* out_off, int64_t n_out,
-                                                              uint64_t seed, int order, double* raw) {
+                                                              uint64_t seed, int order, double* raw,
+                                                              double* x_out, double* v_out,
+                                                              double* alpha_out) {
   constexpr int NA = 2 + D + 1;
   constexpr int NS = 2 + 2 * D;
   __shared__ RecCell<D> rcs[NW];
@@ -156,6 +193,7 @@ __global__ void __launch_bounds__(NW * 32) recon_stats_kernel(int64_t C, int Kma
         int z;
         float f[D];
         sample_f<D>(rc, j, i, seed, m0, z, f);
+        stage_draw<D>(x_out, v_out, alpha_out, o + i, m0, z, f);
         const long long k = 2ll * (long long)m0 - (1ll << 52) + 1ll;
         if (order == 1) {
           sm[0] += (__int128)(k < 0 ? -k : 0);
@@ -187,16 +225,17 @@ __global__ void __launch_bounds__(NW * 32) recon_stats_kernel(int64_t C, int Kma
       for (int t = 0; t < NA; ++t) acc[t] = 0.0;
       for (int64_t i = lane; i < n; i += 32) {
         uint64_t m0;
+        int z;
+        float f[D];
         double w[D];
+        sample_f<D>(rc, j, i, seed, m0, z, f);
+        stage_draw<D>(x_out, v_out, alpha_out, o + i, m0, z, f);
         if (rc.K == 1) {
           // the f sums (above 2^14 particles)
-          int z;
-          float f[D];
-          sample_f<D>(rc, j, i, seed, m0, z, f);
 #pragma unroll
           for (int d = 0; d < D; ++d) w[d] = f2d_exact(f[d]);
         } else {
-          sample_particle<D>(rc, j, i, seed, m0, w);
+          draw_offset<D>(rc, z, f, w);
         }
         const double sx = centred52(m0);
         if (order == 1) {
@@ -434,11 +473,11 @@ __global__ void recon_coeffs_kernel(int64_t C, int Kmax, const RecHead<D>* head,
 }
 
 // Pass 2, one warp per cell: the final particles (positions, projected
-// velocities, corrected weights).
+// velocities, corrected weights) from the draws that pass 1 staged.
 template <int D, int NW>
 __global__ void __launch_bounds__(NW * 32) recon_emit_kernel(
     int64_t C, int Kmax, const RecHead<D>* head, const RecComp<D>* comp, const RecCoef<D>* coef,
-    const int64_t* out_off, uint64_t seed, double dx, int64_t n_out, double* x_out, double* v_out,
+    const int64_t* out_off, double dx, int64_t n_out, double* x_out, double* v_out,
     double* alpha_out) {
   __shared__ RecCell<D> rcs[NW];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -455,7 +494,7 @@ __global__ void __launch_bounds__(NW * 32) recon_emit_kernel(
         uint64_t m0;
         int z;
         float f[D];
-        sample_f<D>(rc, j, i, seed, m0, z, f);
+        load_draw<D>(x_out, v_out, alpha_out, o + i, m0, z, f);
         const double u0 = uniform_pos52(m0);
         x_out[o + i] = __dmul_rn(__dadd_rn(jd, u0), dx);
         alpha_out[o + i] = an;
@@ -465,8 +504,11 @@ __global__ void __launch_bounds__(NW * 32) recon_emit_kernel(
     } else {
       for (int64_t i = lane; i < n; i += 32) {
         uint64_t m0;
+        int z;
+        float f[D];
         double w[D];
-        sample_particle<D>(rc, j, i, seed, m0, w);
+        load_draw<D>(x_out, v_out, alpha_out, o + i, m0, z, f);
+        draw_offset<D>(rc, z, f, w);
         const double u0 = uniform_pos52(m0);
         x_out[o + i] = __dmul_rn(__dadd_rn(jd, u0), dx);
         alpha_out[o + i] = an;
@@ -555,7 +597,7 @@ static void launch_passes(int64_t C, int Kmax, const int32_t* K, const double* p
   const int64_t ncta = (C + NW - 1) / NW;
   const int g = (int)(ncta < 152 * 16 ? ncta : 152 * 16);
   recon_stats_kernel<D, NW><<<g, NW * 32, 0, s>>>(C, Kmax, head, comp, out_off, n_out, seed, order,
-                                                  raw);
+                                                  raw, x_out, v_out, alpha_out);
   trace_mark("recon_stats_kernel", s);
   assemble_kernel<D><<<ga, 256, 0, s>>>(C, head, raw, W, out_off, n_out, rho_target, dx, q, order,
                                         A, B, Cc, Dd);
@@ -573,8 +615,8 @@ static void launch_passes(int64_t C, int Kmax, const int32_t* K, const double* p
   recon_coeffs_kernel<D><<<ga, 256, 0, s>>>(C, Kmax, head, comp, raw, out_off, n_out, W, dA, coef,
                                             status_out);
   trace_mark("recon_coeffs_kernel", s);
-  recon_emit_kernel<D, NW><<<g, NW * 32, 0, s>>>(C, Kmax, head, comp, coef, out_off, seed, dx,
-                                                 n_out, x_out, v_out, alpha_out);
+  recon_emit_kernel<D, NW><<<g, NW * 32, 0, s>>>(C, Kmax, head, comp, coef, out_off, dx, n_out,
+                                                 x_out, v_out, alpha_out);
   trace_mark("recon_emit_kernel", s);
 }
 

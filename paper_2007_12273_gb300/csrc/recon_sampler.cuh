@@ -253,20 +253,26 @@ __device__ __forceinline__ void sample_f(const RecCell<D>& rc, int64_t j, int64_
   }
 }
 
-// the same particle with w = v - u in FP64: (mu_z - u) + f (w = -u for a
-// cell without a mixture)
+// the particle's w = v - u in FP64 from its draw (z, f): (mu_z - u) + f
+// (w = -u for a cell without a mixture)
 template <int D>
-__device__ __forceinline__ void sample_particle(const RecCell<D>& rc, int64_t j, int64_t i,
-                                                uint64_t seed, uint64_t& m0, double (&w)[D]) {
-  int z;
-  float f[D];
-  sample_f<D>(rc, j, i, seed, m0, z, f);
+__device__ __forceinline__ void draw_offset(const RecCell<D>& rc, int z, const float (&f)[D],
+                                            double (&w)[D]) {
   if (rc.K == 0) {
     for (int d = 0; d < D; ++d) w[d] = -rc.u[d];
     return;
   }
 #pragma unroll
   for (int d = 0; d < D; ++d) w[d] = rc.dz[z][d] + f2d_exact(f[d]);
+}
+// the same, drawing the particle
+template <int D>
+__device__ __forceinline__ void sample_particle(const RecCell<D>& rc, int64_t j, int64_t i,
+                                                uint64_t seed, uint64_t& m0, double (&w)[D]) {
+  int z;
+  float f[D];
+  sample_f<D>(rc, j, i, seed, m0, z, f);
+  draw_offset<D>(rc, z, f, w);
 }
 
 // the 52 leading bits of the y uniform of particle i of cell j on a 2D mesh

@@ -222,26 +222,75 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ CU
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 
   if (!failed) {
-    // epilogue: thread (warp w, lane l) owns tile row 32 w + l
+    // epilogue: thread (warp w, lane l) owns tile row 32 w + l and handles
+    // 16 columns at a time; a full 16-column chunk of an aligned matrix is
+    // moved with 16-byte vector accesses (32 B of BF16, 64 B of FP32 per
+    // row), a ragged or unaligned one element by element
     const int row = m0 + warp * 32 + lane;
+    const bool vf = !Cf || (((ldc & 3) == 0) && (((uintptr_t)Cf & 15) == 0));
+    const bool vb = !Cb || (((ldc & 7) == 0) && (((uintptr_t)Cb & 15) == 0));
+    const bool vm = !mask || (((ldm & 7) == 0) && (((uintptr_t)mask & 15) == 0));
     for (int c0 = 0; c0 < BN; c0 += 16) {
       float v[16];
       tmem_ld16<16>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      if (row < M) {
+      if (row >= M || n0 + c0 >= N) continue;
+      const int cb = n0 + c0;
+      if (cb + 16 <= N && vf && vb && vm) {
+        float x[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
-          const int col = n0 + c0 + e;
-          if (col >= N) continue;
-          float x = v[e];
-          if (bias) x += bias[col];
-          if (relu) x = fmaxf(x, 0.0f);
-          if (mask && !(__bfloat162float(mask[(size_t)row * ldm + col]) > 0.0f)) x = 0.0f;
-          if (Cf) {
-            float* cp = Cf + (size_t)row * ldc + col;
-            *cp = accumulate ? *cp + x : x;
-          }
-          if (Cb) Cb[(size_t)row * ldc + col] = __float2bfloat16(x);
+          x[e] = v[e];
+          if (bias) x[e] += bias[cb + e];
+          if (relu) x[e] = fmaxf(x[e], 0.0f);
         }
+        if (mask) {
+          const uint4* mp = reinterpret_cast<const uint4*>(mask + (size_t)row * ldm + cb);
+          const uint4 q0 = mp[0], q1 = mp[1];
+          const uint32_t mw[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const float mv = __uint_as_float((e & 1) ? (mw[e >> 1] & 0xFFFF0000u) : (mw[e >> 1] << 16));
+            if (!(mv > 0.0f)) x[e] = 0.0f;
+          }
+        }
+        if (Cf) {
+          float4* cp = reinterpret_cast<float4*>(Cf + (size_t)row * ldc + cb);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            float4 o = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+            if (accumulate) {
+              const float4 a = cp[q];
+              o.x += a.x; o.y += a.y; o.z += a.z; o.w += a.w;
+            }
+            cp[q] = o;
+          }
+        }
+        if (Cb) {
+          uint32_t pk[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(x[2 * q], x[2 * q + 1]);
+            pk[q] = *reinterpret_cast<const uint32_t*>(&h);
+          }
+          uint4* bp = reinterpret_cast<uint4*>(Cb + (size_t)row * ldc + cb);
+          bp[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          bp[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        }
+        continue;
+      }
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int col = cb + e;
+        if (col >= N) continue;
+        float x = v[e];
+        if (bias) x += bias[col];
+        if (relu) x = fmaxf(x, 0.0f);
+        if (mask && !(__bfloat162float(mask[(size_t)row * ldm + col]) > 0.0f)) x = 0.0f;
+        if (Cf) {
+          float* cp = Cf + (size_t)row * ldc + col;
+          *cp = accumulate ? *cp + x : x;
+        }
+        if (Cb) Cb[(size_t)row * ldc + col] = __float2bfloat16(x);
       }
     }
   }
