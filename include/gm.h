@@ -272,6 +272,25 @@ int gm_trace_begin(void);
 int gm_trace_end(void);
 int gm_trace_get(int32_t i, char* name, int32_t name_len, double* ms, int32_t* launches);
 
+/*
+ * gm_convert -- the library's FP32 <-> FP64 conversions (no counterpart in
+ * the paper).  GB300 runs FP64, and conversions to and from it, at 1/64 of
+ * the FP32 rate, so the kernels convert on the integer pipe instead; this
+ * entry point applies those conversions to an array so that they can be
+ * checked against the hardware's.
+ *   dir 0: in [n] FP32 -> out [n] FP64, exact for every finite value
+ *          (subnormals and signed zeros included); infinities stay
+ *          infinities, a NaN becomes a quiet NaN;
+ *   dir 1: in [n] FP64 -> out [n] FP32 with the mantissa truncated toward
+ *          zero; below FP32's normal range the value truncates to a
+ *          subnormal or a signed zero, from 2^128 up (and infinities) it
+ *          becomes a signed infinity, a NaN a quiet NaN.
+ * in and out are caller-owned device arrays; asynchronous on stream.
+ * Returns GM_ERR_ARG for n < 0, dir not 0 or 1, or a null array with n > 0;
+ * GM_ERR_CUDA if the launch fails.
+ */
+int gm_convert(int32_t dir, int64_t n, const void* in, void* out, void* stream);
+
 /* gm_noalloc_limits_ok -- 1 if the scratch a call of 32768 cells needs
  * (D = 1 and D = 3, Kmax = 16) fits the 40 MiB array of gm_reconstruct_noalloc, else 0:
  * a host-side self-check of that limit (no counterpart in the paper); it

@@ -62,29 +62,52 @@ __device__ __forceinline__ T warp_sum(T v) {
 
 // Conversions on the integer pipe.  GB300's FP64 pipe runs at 1/64 of the
 // FP32 rate and a conversion to or from FP64 occupies it like an FP64
-// operation; these produce the same values from the bit patterns.
-// f2d_exact: FP32 -> FP64, exact (zero, subnormals, infinities and NaN take
-// the hardware conversion).
+// operation; these build the result from the bit patterns with integer
+// operations and selects only (no hardware conversion on any path).
+// f2d_exact: FP32 -> FP64, exact for every finite input (normal, subnormal,
+// signed zero); infinities map to infinities, a NaN to a quiet NaN.
 __device__ __forceinline__ double f2d_exact(float f) {
   const uint32_t u = __float_as_uint(f);
-  const uint32_t e = (u >> 23) & 0xFFu;
-  if (e == 0u || e == 0xFFu) return (double)f;
-  return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3)),
-                          (int)(u << 29));
+  const uint32_t e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  const unsigned long long sgn = (unsigned long long)(u >> 31) << 63;
+  // normal: rebias the exponent, widen the mantissa
+  unsigned long long r = sgn | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+  // subnormal m 2^-149 (m != 0): leading bit b of m, value 2^(b - 149) (m / 2^b)
+  const int b = 31 - __clz((int)m);
+  const unsigned long long rs = sgn | ((unsigned long long)(b + 874) << 52) |
+                                (((unsigned long long)m << (52 - b)) & ((1ull << 52) - 1ull));
+  // infinity / NaN (the quiet bit set)
+  const unsigned long long ri = sgn | (0x7FFull << 52) | ((unsigned long long)m << 29) |
+                                (m ? (1ull << 51) : 0ull);
+  r = e == 0xFFu ? ri : r;
+  r = e == 0u ? (m ? rs : sgn) : r;
+  return __longlong_as_double((long long)r);
 }
 template <typename VT>
 __device__ __forceinline__ double to_f64(VT v) {
   if constexpr (sizeof(VT) == 4) return f2d_exact(v);
   else return (double)v;
 }
-// d2f_trunc: FP64 -> FP32 with the mantissa truncated (relative error below
-// 2^-23), for values in FP32's normal range (others: hardware conversion)
+// d2f_trunc: FP64 -> FP32 with the mantissa truncated (toward zero,
+// relative error below 2^-23 in FP32's normal range); below it the value
+// truncates to an FP32 subnormal or a signed zero, from 2^128 up (and
+// infinities) to a signed infinity, a NaN to a quiet NaN
 __device__ __forceinline__ float d2f_trunc(double d) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(d);
-  const int e = (int)((u >> 52) & 0x7FFull) - 896;
-  if (e <= 0 || e >= 255) return (float)d;
-  return __uint_as_float((uint32_t)((u >> 32) & 0x80000000ull) | ((uint32_t)e << 23) |
-                         (uint32_t)((u >> 29) & 0x7FFFFFull));
+  const uint32_t sgn = (uint32_t)(u >> 32) & 0x80000000u;
+  const int ed = (int)((u >> 52) & 0x7FFull);
+  const int e = ed - 896;
+  const unsigned long long mant = u & ((1ull << 52) - 1ull);
+  uint32_t r = sgn | ((uint32_t)(e > 0 ? e : 0) << 23) | (uint32_t)(mant >> 29);
+  // below the normal range: |d| = (2^52 + mant) 2^(ed - 1075), as a multiple
+  // of 2^-149 truncated (zero for ed <= 873 and for double subnormals)
+  const int sh = 926 - ed < 30 ? 30 : 926 - ed;  // 926 - ed >= 30 wherever sub is used
+  const uint32_t sub = (ed > 0 && sh < 64) ? (uint32_t)(((1ull << 52) | mant) >> sh) : 0u;
+  r = e <= 0 ? (sgn | sub) : r;
+  // overflow, infinity, NaN
+  const uint32_t big = sgn | 0x7F800000u | ((ed == 0x7FF && mant) ? 0x400000u : 0u);
+  r = e >= 255 ? big : r;
+  return __uint_as_float(r);
 }
 // k 2^-53 for an odd integer 1 <= k < 2^53 (exact), negated if neg: the
 // double built from k's leading bit position and the bits below it

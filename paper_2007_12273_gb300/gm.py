@@ -40,7 +40,7 @@ EXPORTED = ("gm_compress", "gm_reconstruct", "gm_moments", "gm_mixture_moments",
             "gm_graph_begin", "gm_graph_end", "gm_graph_launch", "gm_graph_destroy", "gm_autotune",
             "gm_compress_standard", "gm_anderson_affine", "gm_deposit_2d", "gm_reconstruct_2d",
             "gm_autotune_from", "gm_noalloc_limits_ok", "gm_trace_begin", "gm_trace_end",
-            "gm_trace_get")
+            "gm_trace_get", "gm_convert")
 
 
 class GMMlp(ct.Structure):
@@ -126,13 +126,14 @@ def load(build_if_missing: bool = False):
         lib.gm_trace_begin.argtypes = []
         lib.gm_trace_end.argtypes = []
         lib.gm_trace_get.argtypes = [I32, ct.c_char_p, I32, ct.POINTER(ct.c_double), ct.POINTER(I32)]
+        lib.gm_convert.argtypes = [I32, I64, P, P, P]
         for f in ("gm_compress", "gm_reconstruct", "gm_moments", "gm_mixture_moments", "gm_shutdown",
                   "gm_reconstruct_noalloc", "gm_gemm_bf16", "gm_compress_from", "gm_features",
                   "gm_mlp_targets", "gm_mlp_sync", "gm_mlp_forward", "gm_mlp_train_step",
                   "gm_mlp_decode", "gm_graph_begin", "gm_graph_end", "gm_graph_launch",
                   "gm_graph_destroy", "gm_autotune", "gm_compress_standard", "gm_anderson_affine",
                   "gm_deposit_2d", "gm_reconstruct_2d", "gm_autotune_from", "gm_noalloc_limits_ok",
-                  "gm_trace_begin", "gm_trace_end", "gm_trace_get"):
+                  "gm_trace_begin", "gm_trace_end", "gm_trace_get", "gm_convert"):
             getattr(lib, f).restype = ct.c_int
         lib.gm_last_error.restype = ct.c_char_p
         _lib = lib
@@ -760,6 +761,18 @@ def gm_anderson_affine(A, b, x0, memory: int, iters: int, stream=None):
                                 _stream_ptr(stream))
     _rc(lib, rc, "gm_anderson_affine")
     return x, res[:iters]
+
+
+def gm_convert(x, stream=None):
+    """The library's integer-pipe conversions: an FP32 CUDA tensor to FP64
+    (exact), an FP64 one to FP32 (mantissa truncated toward zero)."""
+    lib = load()
+    if not x.is_cuda or not x.is_contiguous() or x.dtype not in (torch.float32, torch.float64):
+        raise ValueError("x must be a contiguous CUDA float32 or float64 tensor")
+    d = 0 if x.dtype == torch.float32 else 1
+    out = torch.empty(x.shape, dtype=torch.float64 if d == 0 else torch.float32, device=x.device)
+    _rc(lib, lib.gm_convert(d, x.numel(), _ptr(x), _ptr(out), _stream_ptr(stream)), "gm_convert")
+    return out
 
 
 class Trace:
