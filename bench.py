@@ -225,73 +225,101 @@ def fp64_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
 
 
 # Algorithmic work of the kernels of one step, per particle of the cells a
-# kernel handles (FMA = 2 flops), D = 1 or 3, NM = D (D + 1) / 2:
-#  em_k1_kernel      FP64: the moments about the first particle -- D
-#                    differences, the weight sum, D products alpha dv, D
-#                    first-moment sums, NM second-moment FMAs: 1 + 3 D + 2 NM;
-#                    bytes: v (FP32) and alpha read once, 4 D + 8
-#  recon_stats_kernel FP64: w = dz + L xi (D adds), the shape sums of s and
-#                    s^2 (3), sum w (D), sum |w|^2 (2 D): 3 + 4 D
-#  recon_emit_kernel FP64: x = (j + u0) dx (2), w (D), v = u + a (w + beta)
-#                    (3 D): 2 + 4 D; bytes written: x, v, alpha = 16 + 8 D
-#  deposit           FP64: cell fraction (2), sum alpha, alpha s, alpha s^2
-#                    (5): 7; bytes read: x and alpha, 16
-#  features_kernel   bytes read: v (FP32) and alpha once, 4 D + 8
+# kernel handles, D = 1 or 3, NM = D (D + 1) / 2, and the bound each is
+# reported against:
+#  em_k1_kernel      HBM: v (FP32) and alpha read once, 4 D + 8 bytes.  (The
+#                    method's FP64 moments, 1 + 3 D + 2 NM flops, run as
+#                    exact integer sums: a secondary line.)
+#  recon_stats_kernel ALU: the sampler's 32-bit integer / FP32 operations,
+#                    counted from the definitions: Philox4x32-10 blocks
+#                    (10 rounds of two 32x32->64 multiplies and two
+#                    three-input XORs, 40 ops; 2 blocks for 1V, 3 for 3V),
+#                    two operations per 52-bit uniform (4 or 6 uniforms),
+#                    Box-Muller (ln 10 + sqrt 1 + scale 1 per radius, 8 per
+#                    sine or cosine, 1 per product; 1V one radius and one
+#                    cosine, 3V two radii, three trig values), f = L xi
+#                    (1 or 6), and the exact sums (position 8, each velocity
+#                    dimension 14): 132 (1V), 239 (3V) ops; peak = 152 SMs x
+#                    128 lanes x the clock.  Secondary: the staged draws
+#                    written, 20 bytes (12 for 1V).
+#  recon_emit_kernel HBM: the staged draw read (20 / 12 bytes) and x, v,
+#                    alpha written (16 + 8 D); secondary FP64: x = (j + u0)
+#                    dx (2 flops) and v = c + a f (2 D).
+#  deposit           HBM: x and alpha read, 16 bytes; secondary FP64: the
+#                    cell fraction x / dx - j (2 flops)
+#  features_kernel   HBM: v (FP32) and alpha read once, 4 D + 8
 #  mlp_forward       BF16 tensor flops 2 (F H + 2 H^2 + H O) per cell
 #  em_kernel         FP32 flops FLOPS_PER_PK per particle and component step
 K1_FP64_PER_P = {1: 1 + 3 + 2, 3: 1 + 9 + 12}
-STATS_FP64_PER_P = {1: 7, 3: 15}
-EMIT_FP64_PER_P = {1: 6, 3: 14}
-DEPOSIT_FP64_PER_P = 7
+STATS_OPS_PER_P = {1: 2 * 40 + 2 * 4 + (12 + 8 + 1) + 1 + (8 + 14),
+                   3: 3 * 40 + 2 * 6 + (2 * 12 + 3 * 8 + 3) + 6 + (8 + 3 * 14)}
+STAGED_BYTES_PER_P = {1: 12, 3: 20}
+EMIT_FP64_PER_P = {1: 2 + 2, 3: 2 + 6}
+DEPOSIT_FP64_PER_P = 2
+
+
+def alu_peak_tops(sm_mhz: float, sms: int = 152) -> float:
+    """152 SMs x 128 32-bit lanes (FP32 / INT32) x the clock, in T ops/s"""
+    return sms * 128 * sm_mhz * 1e6 / 1e12
 
 
 def kernel_roofline(kernels: dict, ctx: dict) -> dict:
     """Roofline of the step's dominant kernel (largest traced device time):
     algorithmic work per launch / the kernel's traced time per step against
-    the bounding unit's peak (FP64 and FP32 from unit counts and the clock,
-    HBM and BF16 measured)."""
+    the bounding unit's peak (FP64, FP32 and the 32-bit lanes from unit
+    counts and the clock, HBM and BF16 measured)."""
     if not kernels:
         return None
     name, kt = max(kernels.items(), key=lambda kv: kv[1]["ms"])
     sec = kt["ms"] * 1e-3
     n = ctx["counts"].astype(np.float64)
     D = ctx["D"]
+    hbm = ctx["hbm_gbs"]
     f64_peak = fp64_peak_tflops(ctx["sm_mhz"])
     f32_peak = fp32_peak_tflops(ctx["sm_mhz"])
+    f64_note = f"peak = 152 SMs x 2 FP64 FMA/clock x 2 x {ctx['sm_mhz']:.0f} MHz"
 
     def line(bound, achieved, peak, unit, note, secondary=None):
         return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak, "traffic": None, "ms_per_launch": kt["ms"] / max(1, kt["launches_per_step"]),
                 "note": note, "secondary": secondary or []}
 
+    def sec_line(unit, achieved, peak, note):
+        return {"unit": unit, "achieved": achieved, "peak": peak, "frac": achieved / peak, "note": note}
+
     if name == "em_k1_kernel":
         sel = ctx["K0"] == 1 if ctx["K0"] is not None else np.ones_like(n, dtype=bool)
         np_ = float(n[sel].sum())
-        f = np_ * K1_FP64_PER_P[D] / sec / 1e12
         b = np_ * (4 * D + 8) / sec / 1e9
-        return line("alu", f, f64_peak, "TFLOP/s",
-                    f"FP64 flops = {K1_FP64_PER_P[D]} per particle of the one-component cells "
-                    f"({int(sel.sum())} cells, {np_:.0f} particles); peak = 152 SMs x 2 FP64 FMA/clock x 2 "
-                    f"x {ctx['sm_mhz']:.0f} MHz",
-                    [{"unit": "GB/s", "achieved": b, "peak": ctx["hbm_gbs"], "frac": b / ctx["hbm_gbs"],
-                      "note": f"{4 * D + 8} B read per particle; peak measured (copy)"}])
-    if name == "recon_stats_kernel" or name == "recon_emit_kernel":
-        per = STATS_FP64_PER_P[D] if name == "recon_stats_kernel" else EMIT_FP64_PER_P[D]
-        f = float(n.sum()) * per / sec / 1e12
-        sec_l = []
-        if name == "recon_emit_kernel":
-            b = float(n.sum()) * (16 + 8 * D) / sec / 1e9
-            sec_l.append({"unit": "GB/s", "achieved": b, "peak": ctx["hbm_gbs"], "frac": b / ctx["hbm_gbs"],
-                          "note": f"{16 + 8 * D} B written per particle (x, v, alpha); peak measured (copy)"})
-        return line("alu", f, f64_peak, "TFLOP/s",
-                    f"FP64 flops = {per} per resampled particle; peak = 152 SMs x 2 FP64 FMA/clock x 2 x "
-                    f"{ctx['sm_mhz']:.0f} MHz", sec_l)
+        f = np_ * K1_FP64_PER_P[D] / sec / 1e12
+        return line("hbm", b, hbm, "GB/s",
+                    f"{4 * D + 8} B read per particle of the one-component cells ({int(sel.sum())} cells, "
+                    f"{np_:.0f} particles); peak measured (copy)",
+                    [sec_line("TFLOP/s", f, f64_peak, f"the method's FP64 moment flops ({K1_FP64_PER_P[D]} per "
+                              f"particle), run as exact integer sums; {f64_note}")])
+    if name == "recon_stats_kernel":
+        o = float(n.sum()) * STATS_OPS_PER_P[D] / sec / 1e12
+        b = float(n.sum()) * STAGED_BYTES_PER_P[D] / sec / 1e9
+        return line("alu", o, alu_peak_tops(ctx["sm_mhz"]), "Tops/s",
+                    f"the sampler's 32-bit operations, {STATS_OPS_PER_P[D]} per resampled particle (Philox, "
+                    f"Box-Muller, f = L xi, exact sums); peak = 152 SMs x 128 lanes x {ctx['sm_mhz']:.0f} MHz",
+                    [sec_line("GB/s", b, hbm, f"{STAGED_BYTES_PER_P[D]} B of staged draws written per particle; "
+                              "peak measured (copy)")])
+    if name == "recon_emit_kernel":
+        by = STAGED_BYTES_PER_P[D] + 16 + 8 * D
+        b = float(n.sum()) * by / sec / 1e9
+        f = float(n.sum()) * EMIT_FP64_PER_P[D] / sec / 1e12
+        return line("hbm", b, hbm, "GB/s",
+                    f"{by} B per particle: the staged draw read, x, v, alpha written; peak measured (copy)",
+                    [sec_line("TFLOP/s", f, f64_peak, f"FP64 flops = {EMIT_FP64_PER_P[D]} per particle; {f64_note}")])
     if name.startswith("deposit"):
+        b = float(n.sum()) * 16 / sec / 1e9
         f = float(n.sum()) * DEPOSIT_FP64_PER_P / sec / 1e12
-        return line("alu", f, f64_peak, "TFLOP/s", f"FP64 flops = {DEPOSIT_FP64_PER_P} per particle")
+        return line("hbm", b, hbm, "GB/s", "16 B (x, alpha) read per particle; peak measured (copy)",
+                    [sec_line("TFLOP/s", f, f64_peak, f"FP64 flops = {DEPOSIT_FP64_PER_P} per particle; {f64_note}")])
     if name == "features_kernel":
         b = float(n.sum()) * (4 * D + 8) / sec / 1e9
-        return line("hbm", b, ctx["hbm_gbs"], "GB/s", f"{4 * D + 8} B read per particle; peak measured (copy)")
+        return line("hbm", b, hbm, "GB/s", f"{4 * D + 8} B read per particle; peak measured (copy)")
     if name.startswith("mlp_forward"):
         H = 256
         f = 2.0 * len(n) * (ctx["F"] * H + 2 * H * H + H * ctx["O"]) / sec / 1e12
@@ -304,7 +332,7 @@ def kernel_roofline(kernels: dict, ctx: dict) -> dict:
                     em_secondary_rooflines(ctx["counts"], ctx["K"], ctx["kwork"], ctx["sweeps"], D, sec,
                                            ctx["sm_mhz"]))
     b = float(len(n)) * 64 / sec / 1e9
-    return line("hbm", b, ctx["hbm_gbs"], "GB/s", "per-cell records, ~64 B per cell")
+    return line("hbm", b, hbm, "GB/s", "per-cell records, ~64 B per cell")
 
 
 def measured_peaks() -> dict:

@@ -89,6 +89,7 @@ __device__ bool fixed_sums(const float* __restrict__ v, int64_t ldv, int n, int 
   int emax[D];
 #pragma unroll
   for (int d = 0; d < D; ++d) emax[d] = 0;
+#pragma unroll 4
   for (int p = lane; p < n; p += 32)
 #pragma unroll
     for (int d = 0; d < D; ++d) emax[d] = max(emax[d], (int)((__float_as_uint(v[d * ldv + p]) >> 23) & 0xFFu));
@@ -108,6 +109,7 @@ __device__ bool fixed_sums(const float* __restrict__ v, int64_t ldv, int n, int 
   for (int d = 0; d < D; ++d) s1[d] = 0;
 #pragma unroll
   for (int t = 0; t < NM; ++t) s2[t] = 0;
+#pragma unroll 2
   for (int p = lane; p < n; p += 32) {
     long long dq[D];
 #pragma unroll
@@ -199,7 +201,8 @@ __global__ void __launch_bounds__(NW * 32) em_k1_kernel(K1Params a) {
       if (N <= kFixMaxN) {
         const long long a0b = __double_as_longlong(a.alpha[off]);
         bool same = true;
-        for (int p = lane; p < N; p += 32) same = same && (__double_as_longlong(a.alpha[off + p]) == a0b);
+#pragma unroll 4
+        for (int p = lane; p < N; p += 32) same &= (__double_as_longlong(a.alpha[off + p]) == a0b);
         // a0 > 0 on the bits: positive sign, not a NaN
         if (__all_sync(0xffffffffu, same) && a0b > 0 && a0b <= 0x7FF0000000000000ll) {
           __int128 s1[D], s2[NM];

@@ -278,7 +278,7 @@ static int compress_impl(const gm_config* cfg, int64_t C, int64_t n_particles,
   if ((rc = check_device(&sms))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
 
-  const size_t q_bytes = 256, part_bytes = align256((size_t)3 * C * sizeof(double));
+  const size_t q_bytes = 256, part_bytes = align256(gmcr::deposit_ws_bytes(C));
   const size_t list_bytes = init_K ? align256((size_t)C * sizeof(unsigned int)) : 0;
   const int64_t sstride = gmcr::scratch_stride(n_particles, C);
   if ((int64_t)(D + 4) * sstride >= ((int64_t)1 << 31))
@@ -412,7 +412,7 @@ int gm_compress_standard(const gm_config* cfg, const gm_std_opts* opts, int64_t 
   const size_t smem = (size_t)cap * (D + 3) * sizeof(float);
   if (smem > 160 * 1024) return fail(GM_ERR_ARG, "smem_particles too large (%d)", cap);
 
-  const size_t q_bytes = 256, part_bytes = align256((size_t)3 * C * sizeof(double));
+  const size_t q_bytes = 256, part_bytes = align256(gmcr::deposit_ws_bytes(C));
   const int64_t sstride = gmcr::scratch_stride(n_particles, C);
   if ((int64_t)(D + 3) * sstride >= ((int64_t)1 << 31))
     return fail(GM_ERR_ARG, "too many particles for one call (%lld)", (long long)n_particles);
@@ -583,9 +583,9 @@ int gm_moments(const gm_config* cfg, int64_t C, int64_t n_particles, const int64
   }
   if (rho) {
     void* ws = nullptr;
-    if ((rc = ws_get(align256((size_t)3 * C * sizeof(double)), &ws))) return rc;
+    if ((rc = ws_get(align256(gmcr::deposit_ws_bytes(C)), &ws))) return rc;
     e = gmcr::launch_deposit(C, cell_off, x, alpha, cfg->L / (double)C, cfg->q, cfg->shape_order,
-                             (double*)ws, rho, s);
+                             ws, rho, s);
     if (e != cudaSuccess) return cuda_fail(e, "deposit launch");
   }
   return GM_OK;

@@ -18,8 +18,9 @@ cudaError_t launch_em3(const EmParams& p, int nt, int fp64_mstep, int v_f64, siz
 // CTAs of an EM kernel that fit on one SM with `smem` dynamic bytes
 int em_blocks_per_sm(int D, int nt, int fp64_mstep, int v_f64, size_t smem);
 
+size_t deposit_ws_bytes(int64_t C);
 cudaError_t launch_deposit(int64_t C, const int64_t* cell_off, const double* x,
-                           const double* alpha, double dx, double q, int order, double* part,
+                           const double* alpha, double dx, double q, int order, void* ws,
                            double* rho, cudaStream_t s);
 cudaError_t launch_moments(int D, int64_t C, int64_t n, const int64_t* cell_off, const void* v,
                            int v_f64, const double* alpha, double* W, double* p, double* M2,

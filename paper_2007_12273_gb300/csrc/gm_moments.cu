@@ -20,21 +20,32 @@ __device__ __forceinline__ void block_sum_to0(double (&v)[NV], double (*red)[NV]
 }
 
 // Per-cell partial deposits: part[j] = sum_{p in j} alpha_p S(x_i - x_p)
-// for i = j-1, j, j+1 (alpha = NULL means unit weights).  One warp per
-// cell.  With s = xi - 1/2 (xi the position inside the cell) the quadratic
-// B-spline weights are (1/2 - s)^2 / 2, 3/4 - s^2, (1/2 + s)^2 / 2, so the
-// three sums follow from A0 = sum alpha, A1 = sum alpha s, A2 = sum alpha
-// s^2; for CIC they are sum alpha max(-s, 0), A0 - (the other two),
-// sum alpha max(s, 0).
+// for i = j-1, j, j+1 (alpha = NULL means unit weights).  With s = xi - 1/2
+// (xi the position inside the cell) the quadratic B-spline weights are
+// (1/2 - s)^2 / 2, 3/4 - s^2, (1/2 + s)^2 / 2, so the three sums follow
+// from A0 = sum alpha, A1 = sum alpha s, A2 = sum alpha s^2; for CIC they
+// are sum alpha max(-s, 0), A0 - (the other two), sum alpha max(s, 0).
+//
+// deposit_partials_kernel, one warp per cell, writes each cell's sums to a
+// record of kDepWords 64-bit words; deposit_combine_kernel, one thread per
+// node, turns the records of the node's three cells into the charge, so the
+// per-cell FP64 work runs 32 cells to a warp instruction.  Record:
+//   equal weights: [k0 (low, high), k1 (low, high), alpha bits, n], the
+//     exact 128-bit sums of k and k^2 (or of the CIC parts) with
+//     s = k 2^-53;
+//   otherwise: [A0, A1, A2 (FP64 bits), -, -, -1].
+constexpr int kDepWords = 6;
+size_t deposit_ws_bytes(int64_t C) { return (size_t)kDepWords * 8 * (size_t)(C > 0 ? C : 0) + 256; }
+
 template <int NW>
 __global__ void __launch_bounds__(NW * 32) deposit_partials_kernel(int64_t C, const int64_t* cell_off,
                                                                    const double* x, const double* alpha,
                                                                    double inv_dx, int order,
-                                                                   double* part /*[C][3]*/) {
+                                                                   long long* rec) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int64_t j = (int64_t)blockIdx.x * NW + wid; j < C; j += (int64_t)gridDim.x * NW) {
     const int64_t o = cell_off[j], n = cell_off[j + 1] - o;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    long long* r = rec + (size_t)j * kDepWords;
     // equal weights (bit for bit) and at most 2^14 particles: the sums of s
     // and s^2 (or of the CIC parts) exactly on the integer pipe, s = k 2^-53
     // with k = round(xi 2^53) - 2^52 from the bits of the FP64 in-cell
@@ -43,11 +54,14 @@ __global__ void __launch_bounds__(NW * 32) deposit_partials_kernel(int64_t C, co
     if (n > 0 && n <= kFixMaxN) {
       const long long wb = alpha ? __double_as_longlong(alpha[o]) : __double_as_longlong(1.0);
       bool same = true;
-      if (alpha)
-        for (int64_t p = lane; p < n; p += 32) same = same && (__double_as_longlong(alpha[o + p]) == wb);
+      if (alpha) {
+#pragma unroll 4
+        for (int64_t p = lane; p < n; p += 32) same &= (__double_as_longlong(alpha[o + p]) == wb);
+      }
       fixed = __all_sync(0xffffffffu, same);
       if (fixed) {
         __int128 k0 = 0, k1 = 0;
+#pragma unroll 2
         for (int64_t p = lane; p < n; p += 32) {
           const double xi = cell_frac(x[o + p], j, inv_dx);
           // xi = m 2^(e - 1075) (m with its implicit bit), k = round(xi 2^53) - 2^52
@@ -55,10 +69,10 @@ __global__ void __launch_bounds__(NW * 32) deposit_partials_kernel(int64_t C, co
           const int e = (int)((u >> 52) & 0x7FFull);
           const long long m = (long long)((u & ((1ull << 52) - 1ull)) | (e ? (1ull << 52) : 0ull));
           const int sh = (e ? e : 1) - 1022;  // xi 2^53 = m 2^sh, sh <= 0
-          long long r = 0;
-          if (sh == 0) r = m;
-          else if (sh > -60) r = (m + (1ll << (-sh - 1))) >> (-sh);
-          const long long k = r - (1ll << 52);
+          long long rr = 0;
+          if (sh == 0) rr = m;
+          else if (sh > -60) rr = (m + (1ll << (-sh - 1))) >> (-sh);
+          const long long k = rr - (1ll << 52);
           if (order == 1) {
             k0 += (__int128)(k < 0 ? -k : 0);
             k1 += (__int128)(k > 0 ? k : 0);
@@ -72,18 +86,18 @@ __global__ void __launch_bounds__(NW * 32) deposit_partials_kernel(int64_t C, co
           k0 += shfl_xor_i128(k0, q);
           k1 += shfl_xor_i128(k1, q);
         }
-        const double al = __longlong_as_double(wb);
-        a0 = al * (double)n;
-        if (order == 1) {
-          a1 = al * i128_to_f64(k0, -53);
-          a2 = al * i128_to_f64(k1, -53);
-        } else {
-          a1 = al * i128_to_f64(k0, -53);
-          a2 = al * i128_to_f64(k1, -106);
-        }
+        // lanes 0-5 write the record's words
+        long long wv = (long long)(unsigned long long)k0;
+        wv = lane == 1 ? (long long)(k0 >> 64) : wv;
+        wv = lane == 2 ? (long long)(unsigned long long)k1 : wv;
+        wv = lane == 3 ? (long long)(k1 >> 64) : wv;
+        wv = lane == 4 ? wb : wv;
+        wv = lane == 5 ? (long long)n : wv;
+        if (lane < kDepWords) r[lane] = wv;
       }
     }
     if (!fixed) {
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0;
       for (int64_t p = lane; p < n; p += 32) {
         const double sx = cell_frac(x[o + p], j, inv_dx) - 0.5;
         const double al = alpha ? alpha[o + p] : 1.0;
@@ -101,29 +115,54 @@ __global__ void __launch_bounds__(NW * 32) deposit_partials_kernel(int64_t C, co
       a0 = warp_sum(a0);
       a1 = warp_sum(a1);
       a2 = warp_sum(a2);
-    }
-    if (lane == 0) {
-      if (order == 1) {
-        part[3 * j + 0] = a1;
-        part[3 * j + 1] = a0 - a1 - a2;
-        part[3 * j + 2] = a2;
-      } else {
-        part[3 * j + 0] = 0.5 * (0.25 * a0 - a1 + a2);
-        part[3 * j + 1] = 0.75 * a0 - a2;
-        part[3 * j + 2] = 0.5 * (0.25 * a0 + a1 + a2);
-      }
+      long long wv = __double_as_longlong(a0);
+      wv = lane == 1 ? __double_as_longlong(a1) : wv;
+      wv = lane == 2 ? __double_as_longlong(a2) : wv;
+      wv = lane == 5 ? -1ll : wv;
+      if (lane < kDepWords) r[lane] = wv;
     }
   }
 }
 
+// the three partial deposits of a cell (on its nodes j-1, j, j+1) from its
+// record
+__device__ __forceinline__ void dep_parts(const long long* r, int order, double (&pt)[3]) {
+  double a0, a1, a2;
+  if (r[5] >= 0) {
+    const double al = __longlong_as_double(r[4]);
+    const __int128 k0 = ((__int128)r[1] << 64) | (__int128)(unsigned long long)r[0];
+    const __int128 k1 = ((__int128)r[3] << 64) | (__int128)(unsigned long long)r[2];
+    a0 = al * (double)r[5];
+    a1 = al * i128_to_f64(k0, -53);
+    a2 = al * i128_to_f64(k1, order == 1 ? -53 : -106);
+  } else {
+    a0 = __longlong_as_double(r[0]);
+    a1 = __longlong_as_double(r[1]);
+    a2 = __longlong_as_double(r[2]);
+  }
+  if (order == 1) {
+    pt[0] = a1;
+    pt[1] = a0 - a1 - a2;
+    pt[2] = a2;
+  } else {
+    pt[0] = 0.5 * (0.25 * a0 - a1 + a2);
+    pt[1] = 0.75 * a0 - a2;
+    pt[2] = 0.5 * (0.25 * a0 + a1 + a2);
+  }
+}
+
 // rho_i = (q/dx) (part[i-1][+] + part[i][0] + part[i+1][-]), periodic
-__global__ void deposit_combine_kernel(int64_t C, const double* part, double q_over_dx,
+__global__ void deposit_combine_kernel(int64_t C, const long long* rec, int order, double q_over_dx,
                                        double* rho) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < C;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t im = (i == 0) ? C - 1 : i - 1;
     const int64_t ip = (i == C - 1) ? 0 : i + 1;
-    rho[i] = q_over_dx * (part[3 * im + 2] + part[3 * i + 1] + part[3 * ip + 0]);
+    double pm[3], p0[3], pp[3];
+    dep_parts(rec + (size_t)im * kDepWords, order, pm);
+    dep_parts(rec + (size_t)i * kDepWords, order, p0);
+    dep_parts(rec + (size_t)ip * kDepWords, order, pp);
+    rho[i] = q_over_dx * (pm[2] + p0[1] + pp[0]);
   }
 }
 
@@ -209,12 +248,13 @@ __global__ void mixture_moments_kernel(int64_t C, int Kmax, const int32_t* K, co
 static int grid_for(int64_t C, int cap) { return (int)(C < cap ? (C > 0 ? C : 1) : cap); }
 
 cudaError_t launch_deposit(int64_t C, const int64_t* cell_off, const double* x,
-                           const double* alpha, double dx, double q, int order, double* part,
+                           const double* alpha, double dx, double q, int order, void* ws,
                            double* rho, cudaStream_t s) {
   if (C == 0) return cudaSuccess;
+  long long* rec = (long long*)ws;
   deposit_partials_kernel<4><<<grid_for((C + 3) / 4, 152 * 16), 128, 0, s>>>(C, cell_off, x, alpha,
-                                                                              1.0 / dx, order, part);
-  deposit_combine_kernel<<<grid_for((C + 255) / 256, 1024), 256, 0, s>>>(C, part, q / dx, rho);
+                                                                              1.0 / dx, order, rec);
+  deposit_combine_kernel<<<grid_for((C + 255) / 256, 1024), 256, 0, s>>>(C, rec, order, q / dx, rho);
   return cudaGetLastError();
 }
 

@@ -488,15 +488,34 @@ __global__ void __launch_bounds__(NW * 32) recon_emit_kernel(
     __syncwarp();
     int64_t o, n;
     out_range(out_off, j, n_out, o, n);
-    const double aa = cf.a, an = cf.alpha_new, jd = (double)j;
+    const double aa = cf.a, an = cf.alpha_new;
     if (rc.K == 1) {
-      for (int64_t i = lane; i < n; i += 32) {
+      // four particles per lane per step: their staged draws are all loaded
+      // before any of their slots is overwritten, so the loads of a step
+      // are in flight together
+      constexpr int U = 4;
+      int64_t i = lane;
+      for (; i + 32 * (U - 1) < n; i += 32 * U) {
+        uint64_t m0[U];
+        int z[U];
+        float f[U][D];
+#pragma unroll
+        for (int u = 0; u < U; ++u) load_draw<D>(x_out, v_out, alpha_out, o + i + 32 * u, m0[u], z[u], f[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t p = o + i + 32 * u;
+          x_out[p] = __dmul_rn(cell_plus_u0((uint64_t)j, m0[u]), dx);
+          alpha_out[p] = an;
+#pragma unroll
+          for (int d = 0; d < D; ++d) v_out[(int64_t)d * n_out + p] = fma(aa, f2d_exact(f[u][d]), cf.cv[d]);
+        }
+      }
+      for (; i < n; i += 32) {
         uint64_t m0;
         int z;
         float f[D];
         load_draw<D>(x_out, v_out, alpha_out, o + i, m0, z, f);
-        const double u0 = uniform_pos52(m0);
-        x_out[o + i] = __dmul_rn(__dadd_rn(jd, u0), dx);
+        x_out[o + i] = __dmul_rn(cell_plus_u0((uint64_t)j, m0), dx);
         alpha_out[o + i] = an;
 #pragma unroll
         for (int d = 0; d < D; ++d) v_out[(int64_t)d * n_out + o + i] = fma(aa, f2d_exact(f[d]), cf.cv[d]);
@@ -509,8 +528,7 @@ __global__ void __launch_bounds__(NW * 32) recon_emit_kernel(
         double w[D];
         load_draw<D>(x_out, v_out, alpha_out, o + i, m0, z, f);
         draw_offset<D>(rc, z, f, w);
-        const double u0 = uniform_pos52(m0);
-        x_out[o + i] = __dmul_rn(__dadd_rn(jd, u0), dx);
+        x_out[o + i] = __dmul_rn(cell_plus_u0((uint64_t)j, m0), dx);
         alpha_out[o + i] = an;
 #pragma unroll
         for (int d = 0; d < D; ++d) {
@@ -533,21 +551,53 @@ int solve_blocks(int64_t C) {
   return P;
 }
 
-// mass-matrix solve plan: meshes of at least kMultiRows cells are
-// eliminated in blocks of ~64 rows across the GPU (P blocks; interface
-// system of 2P rows solved on one CTA with P2 blocks); smaller ones on one
-// CTA (P = solve_blocks(C))
+// Mass-matrix solve plan.  A mesh below kMultiRows cells is solved on one
+// CTA (mass_solve_kernel, solve_blocks(n) blocks).  A larger one by the same
+// partition method applied level by level across the GPU: level l splits
+// its n_l rows into P_l blocks of about kLevelRows rows, one thread each
+// (mm_eliminate_kernel), and the blocks' 2 P_l interface rows are level
+// l + 1's cyclic tridiagonal system; the first level below kMultiRows rows
+// goes to one CTA, and the levels are then reconstructed in reverse order
+// (mm_reconstruct_kernel).  Short blocks keep each thread's sequential
+// FP64 elimination short; 262144 cells take three levels (16384, 2048 and
+// 256 blocks) and a 512-row system on one CTA.
 constexpr int64_t kMultiRows = 2048;
+constexpr int64_t kLevelRows = 16;
+constexpr int kMaxLevels = 12;
 struct SolvePlan {
-  bool multi;
-  int P, P2;
+  int L;                      // multi-CTA levels (0: the whole system on one CTA)
+  int64_t n[kMaxLevels + 1];  // rows of level l; n[L] the one-CTA system
+  int P[kMaxLevels];          // blocks of the multi-CTA levels
+  int Pf;                     // blocks of the one-CTA system
 };
 static SolvePlan plan_solve(int64_t C) {
   SolvePlan pl;
-  pl.multi = C >= kMultiRows;
-  pl.P = pl.multi ? (int)(C / 64) : solve_blocks(C);
-  pl.P2 = pl.multi ? solve_blocks(2 * (int64_t)pl.P) : 1;
+  pl.L = 0;
+  pl.n[0] = C;
+  while (pl.n[pl.L] >= kMultiRows && pl.L < kMaxLevels) {
+    pl.P[pl.L] = (int)(pl.n[pl.L] / kLevelRows);
+    pl.n[pl.L + 1] = 2 * (int64_t)pl.P[pl.L];
+    ++pl.L;
+  }
+  pl.Pf = solve_blocks(pl.n[pl.L]);
   return pl;
+}
+// doubles of one level's SolveWs: y, v, w, cp over its n rows and the eight
+// interface arrays over 2 P + 2
+static size_t level_doubles(int64_t n, int P) { return 4 * (size_t)n + 8 * (size_t)(2 * (int64_t)P + 2); }
+static SolveWs level_ws(double* base, int64_t n, int P) {
+  SolveWs w;
+  w.y = base; w.v = base + n; w.w = base + 2 * n; w.cp = base + 3 * n;
+  double* r = base + 4 * n;
+  const int64_t R2 = 2 * (int64_t)P + 2;
+  w.ra = r; w.rb = r + R2; w.rc = r + 2 * R2; w.rd = r + 3 * R2;
+  w.rz = r + 4 * R2; w.rcp = r + 5 * R2; w.ry = r + 6 * R2; w.rzz = r + 7 * R2;
+  return w;
+}
+static size_t solve_doubles(const SolvePlan& pl) {
+  size_t d = 0;
+  for (int l = 0; l < pl.L; ++l) d += level_doubles(pl.n[l], pl.P[l]);
+  return d + level_doubles(pl.n[pl.L], pl.Pf);
 }
 
 // workspace: the raw sums, the mixture heads and component records, the
@@ -567,9 +617,7 @@ static size_t rec_bytes(int D, int64_t C, int Kmax, size_t* off_head, size_t* of
 
 size_t reconstruct_ws_bytes(int D, int64_t C, int Kmax) {
   const SolvePlan pl = plan_solve(C);
-  const size_t per_cell = 4 /*a b c d*/ + 1 /*dA*/ + 4 /*y v w cp*/;
-  size_t dbl = per_cell * (size_t)C + 8 * (size_t)(2 * pl.P + 2);
-  if (pl.multi) dbl += 4 * (size_t)(2 * pl.P) + 8 * (size_t)(2 * pl.P2 + 2);
+  const size_t dbl = 5 * (size_t)C /*a b c d, dA*/ + solve_doubles(pl);
   return rec_bytes(D, C, Kmax, nullptr, nullptr, nullptr) + dbl * sizeof(double) + 1024;
 }
 
@@ -579,15 +627,13 @@ static void launch_passes(int64_t C, int Kmax, const int32_t* K, const double* p
                           uint64_t seed, double dx, double q, int order, double* x_out,
                           double* v_out, double* alpha_out, uint32_t* status_out, double* dA,
                           unsigned char* recs, double* A, double* B, double* Cc, double* Dd,
-                          const SolvePlan& pl, const SolveWs& sw, const SolveWs& sw2,
-                          cudaStream_t s) {
+                          const SolvePlan& pl, const SolveWs* lws, cudaStream_t s) {
   size_t oh, oc, op;
   rec_bytes(D, C, Kmax, &oh, &oc, &op);
   double* raw = (double*)recs;
   RecHead<D>* head = (RecHead<D>*)(recs + oh);
   RecCoef<D>* coef = (RecCoef<D>*)(recs + oc);
   RecComp<D>* comp = (RecComp<D>*)(recs + op);
-  const int P = pl.P;
   trace_mark(nullptr, s);
   const int ga = (int)((C + 255) / 256 < 4096 ? (C + 255) / 256 : 4096);
   recon_prep_kernel<D><<<ga, 256, 0, s>>>(C, Kmax, K, prm, head, comp);
@@ -602,14 +648,21 @@ static void launch_passes(int64_t C, int Kmax, const int32_t* K, const double* p
   assemble_kernel<D><<<ga, 256, 0, s>>>(C, head, raw, W, out_off, n_out, rho_target, dx, q, order,
                                         A, B, Cc, Dd);
   trace_mark("assemble_kernel", s);
-  if (pl.multi) {
-    mm_eliminate_kernel<<<(P + 127) / 128, 128, 0, s>>>(C, A, B, Cc, Dd, sw, P);
-    const int P2 = pl.P2;
-    mass_solve_kernel<<<1, P2 < 32 ? 32 : ((P2 + 31) / 32) * 32, 0, s>>>(
-        2 * (int64_t)P, sw.ra, sw.rb, sw.rc, sw.rd, sw.rz, sw2, P2);
-    mm_reconstruct_kernel<<<(P + 127) / 128, 128, 0, s>>>(C, sw, P, dA);
-  } else {
-    mass_solve_kernel<<<1, P < 32 ? 32 : ((P + 31) / 32) * 32, 0, s>>>(C, A, B, Cc, Dd, dA, sw, P);
+  {
+    // level l's system: (A, B, Cc, Dd) for l = 0, else level l - 1's
+    // interface rows; its solution: dA for l = 0, else level l - 1's rz
+    const double *sa = A, *sb = B, *sc = Cc, *sd = Dd;
+    for (int l = 0; l < pl.L; ++l) {
+      mm_eliminate_kernel<<<(pl.P[l] + 127) / 128, 128, 0, s>>>(pl.n[l], sa, sb, sc, sd, lws[l], pl.P[l]);
+      sa = lws[l].ra; sb = lws[l].rb; sc = lws[l].rc; sd = lws[l].rd;
+    }
+    const int Pf = pl.Pf;
+    double* xf = pl.L > 0 ? lws[pl.L - 1].rz : dA;
+    mass_solve_kernel<<<1, Pf < 32 ? 32 : ((Pf + 31) / 32) * 32, 0, s>>>(pl.n[pl.L], sa, sb, sc, sd, xf,
+                                                                         lws[pl.L], Pf);
+    for (int l = pl.L - 1; l >= 0; --l)
+      mm_reconstruct_kernel<<<(pl.P[l] + 127) / 128, 128, 0, s>>>(pl.n[l], lws[l], pl.P[l],
+                                                                  l > 0 ? lws[l - 1].rz : dA);
   }
   trace_mark("mass-matrix solve (mass_solve_kernel and the blocked kernels)", s);
   recon_coeffs_kernel<D><<<ga, 256, 0, s>>>(C, Kmax, head, comp, raw, out_off, n_out, W, dA, coef,
@@ -627,38 +680,26 @@ cudaError_t launch_reconstruct(int D, int64_t C, int Kmax, const int32_t* K, con
                                uint32_t* status_out, double* dA_user, void* ws, cudaStream_t s) {
   if (C == 0) return cudaSuccess;
   const SolvePlan pl = plan_solve(C);
-  const int P = pl.P;
   unsigned char* recs = (unsigned char*)ws;
   double* A = (double*)(recs + rec_bytes(D, C, Kmax, nullptr, nullptr, nullptr));
   double* B = A + C;
   double* Cc = B + C;
   double* Dd = Cc + C;
   double* dA = Dd + C;
-  SolveWs sw;
-  sw.y = dA + C;
-  sw.v = sw.y + C;
-  sw.w = sw.v + C;
-  sw.cp = sw.w + C;
-  double* r = sw.cp + C;
-  const int64_t R2 = 2 * (int64_t)P + 2;
-  sw.ra = r; sw.rb = r + R2; sw.rc = r + 2 * R2; sw.rd = r + 3 * R2;
-  sw.rz = r + 4 * R2; sw.rcp = r + 5 * R2; sw.ry = r + 6 * R2; sw.rzz = r + 7 * R2;
-  SolveWs sw2;  // the interface system's own workspace (multi-CTA plan)
-  if (pl.multi) {
-    const int64_t n2 = 2 * (int64_t)P, R22 = 2 * (int64_t)pl.P2 + 2;
-    double* r2 = r + 8 * R2;
-    sw2.y = r2; sw2.v = r2 + n2; sw2.w = r2 + 2 * n2; sw2.cp = r2 + 3 * n2;
-    double* q2 = r2 + 4 * n2;
-    sw2.ra = q2; sw2.rb = q2 + R22; sw2.rc = q2 + 2 * R22; sw2.rd = q2 + 3 * R22;
-    sw2.rz = q2 + 4 * R22; sw2.rcp = q2 + 5 * R22; sw2.ry = q2 + 6 * R22; sw2.rzz = q2 + 7 * R22;
+  SolveWs lws[kMaxLevels + 1];
+  double* base = dA + C;
+  for (int l = 0; l < pl.L; ++l) {
+    lws[l] = level_ws(base, pl.n[l], pl.P[l]);
+    base += level_doubles(pl.n[l], pl.P[l]);
   }
+  lws[pl.L] = level_ws(base, pl.n[pl.L], pl.Pf);
   if (dA_user) dA = dA_user;
   if (D == 1)
     launch_passes<1>(C, Kmax, K, prm, W, rho_target, n_out, out_off, seed, dx, q, order, x_out,
-                     v_out, alpha_out, status_out, dA, recs, A, B, Cc, Dd, pl, sw, sw2, s);
+                     v_out, alpha_out, status_out, dA, recs, A, B, Cc, Dd, pl, lws, s);
   else
     launch_passes<3>(C, Kmax, K, prm, W, rho_target, n_out, out_off, seed, dx, q, order, x_out,
-                     v_out, alpha_out, status_out, dA, recs, A, B, Cc, Dd, pl, sw, sw2, s);
+                     v_out, alpha_out, status_out, dA, recs, A, B, Cc, Dd, pl, lws, s);
   return cudaGetLastError();
 }
 

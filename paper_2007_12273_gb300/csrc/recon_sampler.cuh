@@ -219,11 +219,13 @@ __device__ __forceinline__ void sample_f(const RecCell<D>& rc, int64_t j, int64_
                                          uint64_t& m0, int& z, float (&f)[D]) {
   const u32x4 r0 = philox_draw(seed, (uint32_t)i, kTagSample | 0u, j);
   m0 = bits52(r0.x, r0.y);
-  const long long m1x2 = 2 * (long long)bits52(r0.z, r0.w) + 1;
   const int K = rc.K;
-  z = K - 1;
-  for (int k = 0; k < K; ++k)
-    if (m1x2 < rc.thr[k]) { z = k; break; }
+  z = K - 1;  // the only choice when K <= 1
+  if (K > 1) {
+    const long long m1x2 = 2 * (long long)bits52(r0.z, r0.w) + 1;
+    for (int k = 0; k < K; ++k)
+      if (m1x2 < rc.thr[k]) { z = k; break; }
+  }
   // Box-Muller (Box & Muller 1958) on (u2, u3) [and (u4, u5) for D = 3]
   float xi[3];
   {
@@ -291,6 +293,22 @@ __device__ __forceinline__ double centred52(uint64_t m) {
 }
 // the position uniform u0 = (m + 1/2) 2^-52 = (2 m + 1) 2^-53 of a 52-bit m
 __device__ __forceinline__ double uniform_pos52(uint64_t m) { return odd_2m53(2ull * m + 1ull, false); }
+// j + u0 rounded to the nearest double (ties to even), as the FP64 addition
+// (double)j + u0 gives it, on the integer pipe, for 0 <= j < 2^52: with L
+// the leading bit of j the sum's 53-bit significand in units of 2^(L - 52)
+// is j 2^(52 - L) + t / 2^(L + 1), t = 2 m + 1; the fraction t mod 2^(L+1)
+// decides the rounding, and a carry to 2^53 moves the exponent up by one
+__device__ __forceinline__ double cell_plus_u0(uint64_t j, uint64_t m) {
+  const unsigned long long t = 2ull * m + 1ull;
+  if (j == 0) return odd_2m53(t, false);
+  const int L = 63 - __clzll((long long)j);
+  unsigned long long M = (j << (52 - L)) + (t >> (L + 1));
+  const unsigned long long rem = t & ((2ull << L) - 1ull), half = 1ull << L;
+  M += (rem > half || (rem == half && (M & 1ull))) ? 1ull : 0ull;
+  const int e = M >> 53 ? L + 1 : L;
+  M = M >> 53 ? (1ull << 52) : M;
+  return __longlong_as_double((long long)(((unsigned long long)(1023 + e) << 52) | (M & ((1ull << 52) - 1ull))));
+}
 
 // Lemons projection of a cell with n resampled particles: the corrected
 // weight alpha' = W_j / n + dA_j and, from the sums sw[d] = sum_p w_d and

@@ -79,26 +79,36 @@ def test_strided_oracle_sample():
 
 def test_dominant_kernel_roofline_accounting():
     # the roofline of the step's largest traced kernel: algorithmic work per
-    # launch / its traced time against the unit's peak (FP64 from unit
-    # counts and the clock: 152 SMs x 2 FMA x 2 flops x 2070 MHz)
+    # launch / its traced time against the unit's peak (FP64 and the 32-bit
+    # lanes from unit counts and the clock, HBM measured)
     counts = np.array([100, 300, 600])
     ctx = dict(counts=counts, D=3, K=np.array([1, 1, 2]), kwork=np.array([0, 0, 10]),
                sweeps=np.array([1, 1, 5]), K0=np.array([1, 1, 2]), sm_mhz=2070.0, hbm_gbs=6780.0,
                bf16_tflops=1916.2, F=576, O=112, ms_compress=1.0)
     assert bench.fp64_peak_tflops(2070.0) == pytest.approx(1.25856)
+    assert bench.alu_peak_tops(2070.0) == pytest.approx(152 * 128 * 2.07e9 / 1e12)
     kern = {"em_k1_kernel": {"ms": 2.0, "launches_per_step": 1.0},
             "recon_emit_kernel": {"ms": 1.0, "launches_per_step": 1.0}}
     r = bench.kernel_roofline(kern, ctx)
-    assert r["kernel"] == "em_k1_kernel" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
-    # one-component cells only (K0 == 1): 400 particles x 22 FP64 flops in 2 ms
-    assert r["achieved"] == pytest.approx(400 * 22 / 2e-3 / 1e12)
-    assert r["frac"] == pytest.approx(r["achieved"] / bench.fp64_peak_tflops(2070.0))
-    assert r["secondary"][0]["achieved"] == pytest.approx(400 * 20 / 2e-3 / 1e9)
+    # one-component cells only (K0 == 1): 400 particles x 20 bytes in 2 ms
+    assert r["kernel"] == "em_k1_kernel" and r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["achieved"] == pytest.approx(400 * 20 / 2e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6780.0)
+    assert r["secondary"][0]["achieved"] == pytest.approx(400 * 22 / 2e-3 / 1e12)
     kern["recon_emit_kernel"]["ms"] = 3.0
     r = bench.kernel_roofline(kern, ctx)
-    assert r["kernel"] == "recon_emit_kernel"
-    assert r["achieved"] == pytest.approx(1000 * 14 / 3e-3 / 1e12)
-    assert r["secondary"][0]["achieved"] == pytest.approx(1000 * 40 / 3e-3 / 1e9)
+    # emit: 20 staged + 40 written bytes, 8 FP64 flops per particle
+    assert r["kernel"] == "recon_emit_kernel" and r["bound"] == "hbm"
+    assert r["achieved"] == pytest.approx(1000 * 60 / 3e-3 / 1e9)
+    assert r["secondary"][0]["achieved"] == pytest.approx(1000 * 8 / 3e-3 / 1e12)
+    kern["recon_stats_kernel"] = {"ms": 4.0, "launches_per_step": 1.0}
+    r = bench.kernel_roofline(kern, ctx)
+    assert r["kernel"] == "recon_stats_kernel" and r["bound"] == "alu" and r["unit"] == "Tops/s"
+    # 3 Philox blocks x 40 + 6 uniforms x 2 + Box-Muller 51 + L xi 6 + sums 8 + 3 x 14
+    assert bench.STATS_OPS_PER_P[3] == 120 + 12 + 51 + 6 + 8 + 42
+    assert r["achieved"] == pytest.approx(1000 * 239 / 4e-3 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / bench.alu_peak_tops(2070.0))
+    assert r["secondary"][0]["achieved"] == pytest.approx(1000 * 20 / 4e-3 / 1e9)
     kern = {"mlp_forward (tc_gemm_kernel x4)": {"ms": 1.0, "launches_per_step": 1.0}}
     r = bench.kernel_roofline(kern, ctx)
     assert r["bound"] == "tensor"
