@@ -227,21 +227,24 @@ def fp64_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
 # Algorithmic work of the kernels of one step, per particle of the cells a
 # kernel handles, D = 1 or 3, NM = D (D + 1) / 2, and the bound each is
 # reported against:
-#  em_k1_kernel      HBM: v (FP32) and alpha read once, 4 D + 8 bytes.  (The
-#                    method's FP64 moments, 1 + 3 D + 2 NM flops, run as
-#                    exact integer sums: a secondary line.)
+#  em_k1_kernel      HBM: x and alpha read once for every cell (the charge
+#                    deposit is fused in), v (FP32) once for the cells whose
+#                    start has one component: 16 + 4 D bytes for those, 16
+#                    for the others.  (The method's FP64 moments, 1 + 3 D +
+#                    2 NM flops, run as exact integer sums: a secondary line.)
 #  recon_stats_kernel ALU: the sampler's 32-bit integer / FP32 operations,
-#                    counted from the definitions: Philox4x32-10 blocks
+#                    counted from the definitions: two Philox4x32-10 blocks
 #                    (10 rounds of two 32x32->64 multiplies and two
-#                    three-input XORs, 40 ops; 2 blocks for 1V, 3 for 3V),
-#                    two operations per 52-bit uniform (4 or 6 uniforms),
-#                    Box-Muller (ln 10 + sqrt 1 + scale 1 per radius, 8 per
-#                    sine or cosine, 1 per product; 1V one radius and one
-#                    cosine, 3V two radii, three trig values), f = L xi
-#                    (1 or 6), and the exact sums (position 8, each velocity
-#                    dimension 14): 132 (1V), 239 (3V) ops; peak = 152 SMs x
-#                    128 lanes x the clock.  Secondary: the staged draws
-#                    written, 20 bytes (12 for 1V).
+#                    three-input XORs, 40 ops each), two operations per
+#                    52-bit uniform and one per 32-bit uniform (1V: four
+#                    52-bit; 3V: two 52-bit, four 32-bit), Box-Muller (ln 10
+#                    + sqrt 1 + scale 1 per radius, 8 per sine or cosine, 1
+#                    per product; 1V one radius and one cosine, 3V two
+#                    radii, three trig values), f = L xi (1 or 6), and the
+#                    exact sums (position 8, each velocity dimension 14):
+#                    132 (1V), 195 (3V) ops; peak = 152 SMs x 128 lanes x the
+#                    clock.  Secondary: the staged draws written, 20 bytes
+#                    (12 for 1V).
 #  recon_emit_kernel HBM: the staged draw read (20 / 12 bytes) and x, v,
 #                    alpha written (16 + 8 D); secondary FP64: x = (j + u0)
 #                    dx (2 flops) and v = c + a f (2 D).
@@ -252,7 +255,7 @@ def fp64_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
 #  em_kernel         FP32 flops FLOPS_PER_PK per particle and component step
 K1_FP64_PER_P = {1: 1 + 3 + 2, 3: 1 + 9 + 12}
 STATS_OPS_PER_P = {1: 2 * 40 + 2 * 4 + (12 + 8 + 1) + 1 + (8 + 14),
-                   3: 3 * 40 + 2 * 6 + (2 * 12 + 3 * 8 + 3) + 6 + (8 + 3 * 14)}
+                   3: 2 * 40 + (2 * 2 + 4) + (2 * 12 + 3 * 8 + 3) + 6 + (8 + 3 * 14)}
 STAGED_BYTES_PER_P = {1: 12, 3: 20}
 EMIT_FP64_PER_P = {1: 2 + 2, 3: 2 + 6}
 DEPOSIT_FP64_PER_P = 2
@@ -290,11 +293,11 @@ def kernel_roofline(kernels: dict, ctx: dict) -> dict:
     if name == "em_k1_kernel":
         sel = ctx["K0"] == 1 if ctx["K0"] is not None else np.ones_like(n, dtype=bool)
         np_ = float(n[sel].sum())
-        b = np_ * (4 * D + 8) / sec / 1e9
+        b = (float(n.sum()) * 16 + np_ * 4 * D) / sec / 1e9
         f = np_ * K1_FP64_PER_P[D] / sec / 1e12
         return line("hbm", b, hbm, "GB/s",
-                    f"{4 * D + 8} B read per particle of the one-component cells ({int(sel.sum())} cells, "
-                    f"{np_:.0f} particles); peak measured (copy)",
+                    f"x and alpha (16 B) read per particle, and v ({4 * D} B) per particle of the one-component "
+                    f"cells ({int(sel.sum())} cells, {np_:.0f} particles); peak measured (copy)",
                     [sec_line("TFLOP/s", f, f64_peak, f"the method's FP64 moment flops ({K1_FP64_PER_P[D]} per "
                               f"particle), run as exact integer sums; {f64_note}")])
     if name == "recon_stats_kernel":

@@ -100,6 +100,9 @@ double oracle_uniform52(uint32_t hi, uint32_t lo) {
   return ((double)m + 0.5) * (1.0 / 4503599627370496.0);
 }
 
+/* uniform in (0,1) from one 32-bit word w: u = (w + 1/2) 2^-32 (exact) */
+static double oracle_uniform32(uint32_t w) { return ((double)w + 0.5) * (1.0 / 4294967296.0); }
+
 #define TAG_INIT 0x494E4954u   /* counter word 1 of the initial picks */
 #define TAG_SAMPLE 0x53000000u /* counter word 1 of the sampler (| block) */
 
@@ -667,10 +670,13 @@ static void load_sampling_cell(int D, int Kj, const double *prm, comp *cs) {
  * position inside the cell and its velocity: a component z with
  * probability omega_z (the smallest k with u1 < sum_{m <= k} omega_m), then
  * v = mu_z + Lc_z xi with xi from Box-Muller (Box & Muller 1958) on pairs
- * of uniforms.  Philox counter (i, TAG_SAMPLE | block, j). */
+ * of uniforms.  Philox counter (i, TAG_SAMPLE | block, j): block 0 gives
+ * u0 and u1 (52 bits each); block 1 one (radius, angle) pair of 52-bit
+ * uniforms for D = 1, two pairs of 32-bit uniforms (one per word) for
+ * D = 3. */
 static double sample_one(const oracle_cfg *cfg, int D, const comp *cs, int Kj, int64_t j,
                          int64_t i, double *v) {
-  uint32_t r0[4], r1[4], r2[4];
+  uint32_t r0[4], r1[4];
   philox_draw(cfg->seed, (uint32_t)i, TAG_SAMPLE | 0u, j, r0);
   philox_draw(cfg->seed, (uint32_t)i, TAG_SAMPLE | 1u, j, r1);
   const double u0 = oracle_uniform52(r0[0], r0[1]);
@@ -682,18 +688,18 @@ static double sample_one(const oracle_cfg *cfg, int D, const comp *cs, int Kj, i
     if (u1 < cum) { z = k; break; }
   }
   double xi[4];
-  {
+  if (D == 1) {
     double ua = oracle_uniform52(r1[0], r1[1]), ub = oracle_uniform52(r1[2], r1[3]);
     double rr = sqrt(-2.0 * log(ua));
     xi[0] = rr * cos(2.0 * OR_PI * ub);
     xi[1] = rr * sin(2.0 * OR_PI * ub);
-  }
-  if (D == 3) {
-    philox_draw(cfg->seed, (uint32_t)i, TAG_SAMPLE | 2u, j, r2);
-    double ua = oracle_uniform52(r2[0], r2[1]), ub = oracle_uniform52(r2[2], r2[3]);
-    double rr = sqrt(-2.0 * log(ua));
-    xi[2] = rr * cos(2.0 * OR_PI * ub);
-    xi[3] = rr * sin(2.0 * OR_PI * ub);
+  } else {
+    for (int q = 0; q < 2; ++q) {
+      double ua = oracle_uniform32(r1[2 * q]), ub = oracle_uniform32(r1[2 * q + 1]);
+      double rr = sqrt(-2.0 * log(ua));
+      xi[2 * q] = rr * cos(2.0 * OR_PI * ub);
+      xi[2 * q + 1] = rr * sin(2.0 * OR_PI * ub);
+    }
   }
   for (int a = 0; a < D; ++a) {
     double sv = 0.0;

@@ -23,6 +23,7 @@
 // FP64 instruction costs the pipe as much as a full one.
 #pragma once
 
+#include "deposit_cell.cuh"
 #include "em_kernel.cuh"
 
 namespace gmcr {
@@ -163,6 +164,12 @@ struct K1Params {
   unsigned int* list;        // cells left to the EM kernel
   unsigned int* list_count;  // their number (zeroed before the launch)
   void* raw;                 // K1Raw<D> [C]
+  // the charge deposit fused in (dep_rec = NULL: not done here): positions,
+  // 1 / dx, shape order, per-cell records (deposit_cell.cuh)
+  const double* x;
+  double inv_dx;
+  int order;
+  long long* dep_rec;
   int Kmax;
 };
 
@@ -184,6 +191,10 @@ __global__ void __launch_bounds__(NW * 32) em_k1_kernel(K1Params a) {
     const int64_t off = a.cell_off[j];
     const int N = (int)(a.cell_off[j + 1] - off);
     const int K0 = a.init_K[j] < a.Kmax ? a.init_K[j] : a.Kmax;
+    // the weights' bit-for-bit equality, shared by the deposit and the sums
+    const bool same = N > 0 && N <= kFixMaxN && equal_weights(a.alpha, off, N, lane);
+    if (a.dep_rec) deposit_cell(j, off, N, a.x, a.alpha, a.inv_dx, a.order, a.dep_rec + (size_t)j * kDepWords,
+                                lane, same);
     if (K0 != 1 && N > 0) {  // several (or no) supplied components: EM
       if (lane == 0) a.list[atomicAdd(a.list_count, 1u)] = (unsigned int)j;
       continue;
@@ -198,13 +209,10 @@ __global__ void __launch_bounds__(NW * 32) em_k1_kernel(K1Params a) {
     if constexpr (sizeof(VT) == 4) {
       // equal weights (bit for bit, positive) and at most 2^14 particles:
       // exact sums on the integer pipe
-      if (N <= kFixMaxN) {
+      if (same) {
         const long long a0b = __double_as_longlong(a.alpha[off]);
-        bool same = true;
-#pragma unroll 4
-        for (int p = lane; p < N; p += 32) same &= (__double_as_longlong(a.alpha[off + p]) == a0b);
         // a0 > 0 on the bits: positive sign, not a NaN
-        if (__all_sync(0xffffffffu, same) && a0b > 0 && a0b <= 0x7FF0000000000000ll) {
+        if (a0b > 0 && a0b <= 0x7FF0000000000000ll) {
           __int128 s1[D], s2[NM];
           int eq[D];
           fixed = fixed_sums<D>(reinterpret_cast<const float*>(vin) + off, a.n, N, lane, s1, s2, eq);

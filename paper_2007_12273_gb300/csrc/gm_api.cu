@@ -349,6 +349,11 @@ static int compress_impl(const gm_config* cfg, int64_t C, int64_t n_particles,
     kp.list = list;
     kp.list_count = list_count;
     kp.raw = k1_raw;
+    // the charge deposit rides along (one read of the weights)
+    kp.x = x;
+    kp.inv_dx = 1.0 / (cfg->L / (double)C);
+    kp.order = cfg->shape_order;
+    kp.dep_rec = x ? (long long*)part : nullptr;
     kp.Kmax = cfg->Kmax;
     e = gmcr::launch_em_k1(D, v_is_f64, kp, sms, s);
     if (e != cudaSuccess) return cuda_fail(e, "closed-form pre-pass launch");
@@ -357,7 +362,12 @@ static int compress_impl(const gm_config* cfg, int64_t C, int64_t n_particles,
              : gmcr::launch_em3(p, nt, fp64_mstep, v_is_f64, smem, (int)grid, s);
   if (e != cudaSuccess) return cuda_fail(e, "EM kernel launch");
   gmcr::trace_mark("em_kernel", s);
-  if (x) {
+  if (x && init_K) {  // the records came from em_k1_kernel
+    e = gmcr::launch_deposit_combine(C, cfg->L / (double)C, cfg->q, cfg->shape_order, part,
+                                     rho_target_out, s);
+    if (e != cudaSuccess) return cuda_fail(e, "deposit launch");
+    gmcr::trace_mark("deposit_combine_kernel", s);
+  } else if (x) {
     e = gmcr::launch_deposit(C, cell_off, x, alpha, cfg->L / (double)C, cfg->q, cfg->shape_order,
                              part, rho_target_out, s);
     if (e != cudaSuccess) return cuda_fail(e, "deposit launch");

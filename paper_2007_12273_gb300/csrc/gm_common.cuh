@@ -192,8 +192,8 @@ __device__ __forceinline__ void shape3(int order, double xi, double& wm, double&
 // -inf) to 0, from 1 up (+inf, NaN) to 1 - 2^-53.  One FP64 operation; the
 // clamp compares the bit pattern on the integer pipe (the sign bit, then
 // the magnitude against those of 1.0 and of the infinities).
-__device__ __forceinline__ double cell_frac(double x, int64_t j, double inv_dx) {
-  const double xi = x * inv_dx - (double)j;
+__device__ __forceinline__ double cell_frac(double x, double jd, double inv_dx) {
+  const double xi = x * inv_dx - jd;  // jd = (double)j, converted once per cell by the caller
   const long long b = __double_as_longlong(xi);
   const unsigned long long mag = (unsigned long long)b & 0x7FFFFFFFFFFFFFFFull;
   if (mag > 0x7FF0000000000000ull || (b >= 0 && mag >= 0x3FF0000000000000ull)) return 0.99999999999999989;

@@ -19,6 +19,10 @@ cudaError_t launch_em3(const EmParams& p, int nt, int fp64_mstep, int v_f64, siz
 int em_blocks_per_sm(int D, int nt, int fp64_mstep, int v_f64, size_t smem);
 
 size_t deposit_ws_bytes(int64_t C);
+// rho from records that em_k1_kernel wrote (the deposit fused with the
+// closed-form pre-pass)
+cudaError_t launch_deposit_combine(int64_t C, double dx, double q, int order, const void* ws,
+                                   double* rho, cudaStream_t s);
 cudaError_t launch_deposit(int64_t C, const int64_t* cell_off, const double* x,
                            const double* alpha, double dx, double q, int order, void* ws,
                            double* rho, cudaStream_t s);

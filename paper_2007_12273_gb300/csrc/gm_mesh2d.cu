@@ -60,8 +60,8 @@ __global__ void __launch_bounds__(NW * 32) deposit2d_partials_kernel(
     for (int t = 0; t < 9; ++t) acc[t] = 0.0;
     for (int64_t p = lane; p < n; p += 32) {
       double wx[3], wy[3];
-      shape3(order, cell_frac(x[o + p], jx, inv_dx) - 0.5, wx);
-      shape3(order, cell_frac(y[o + p], jy, inv_dy) - 0.5, wy);
+      shape3(order, cell_frac(x[o + p], (double)jx, inv_dx) - 0.5, wx);
+      shape3(order, cell_frac(y[o + p], (double)jy, inv_dy) - 0.5, wy);
       const double al = alpha ? alpha[o + p] : 1.0;
 #pragma unroll
       for (int b = 0; b < 3; ++b) {

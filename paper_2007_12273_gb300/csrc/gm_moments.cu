@@ -1,4 +1,5 @@
 // gm_moments.cu -- charge deposition (Sec. 2.4.1) and per-cell moments.
+#include "deposit_cell.cuh"
 #include "gm_kernels.cuh"
 
 namespace gmcr {
@@ -27,14 +28,9 @@ __device__ __forceinline__ void block_sum_to0(double (&v)[NV], double (*red)[NV]
 // are sum alpha max(-s, 0), A0 - (the other two), sum alpha max(s, 0).
 //
 // deposit_partials_kernel, one warp per cell, writes each cell's sums to a
-// record of kDepWords 64-bit words; deposit_combine_kernel, one thread per
-// node, turns the records of the node's three cells into the charge, so the
-// per-cell FP64 work runs 32 cells to a warp instruction.  Record:
-//   equal weights: [k0 (low, high), k1 (low, high), alpha bits, n], the
-//     exact 128-bit sums of k and k^2 (or of the CIC parts) with
-//     s = k 2^-53;
-//   otherwise: [A0, A1, A2 (FP64 bits), -, -, -1].
-constexpr int kDepWords = 6;
+// record (deposit_cell.cuh); deposit_combine_kernel, one thread per node,
+// turns the records of the node's three cells into the charge, so the
+// per-cell FP64 work runs 32 cells to a warp instruction.
 size_t deposit_ws_bytes(int64_t C) { return (size_t)kDepWords * 8 * (size_t)(C > 0 ? C : 0) + 256; }
 
 template <int NW>
@@ -45,82 +41,8 @@ __global__ void __launch_bounds__(NW * 32) deposit_partials_kernel(int64_t C, co
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int64_t j = (int64_t)blockIdx.x * NW + wid; j < C; j += (int64_t)gridDim.x * NW) {
     const int64_t o = cell_off[j], n = cell_off[j + 1] - o;
-    long long* r = rec + (size_t)j * kDepWords;
-    // equal weights (bit for bit) and at most 2^14 particles: the sums of s
-    // and s^2 (or of the CIC parts) exactly on the integer pipe, s = k 2^-53
-    // with k = round(xi 2^53) - 2^52 from the bits of the FP64 in-cell
-    // position xi in [0, 1); the weight multiplies the sums once
-    bool fixed = false;
-    if (n > 0 && n <= kFixMaxN) {
-      const long long wb = alpha ? __double_as_longlong(alpha[o]) : __double_as_longlong(1.0);
-      bool same = true;
-      if (alpha) {
-#pragma unroll 4
-        for (int64_t p = lane; p < n; p += 32) same &= (__double_as_longlong(alpha[o + p]) == wb);
-      }
-      fixed = __all_sync(0xffffffffu, same);
-      if (fixed) {
-        __int128 k0 = 0, k1 = 0;
-#pragma unroll 2
-        for (int64_t p = lane; p < n; p += 32) {
-          const double xi = cell_frac(x[o + p], j, inv_dx);
-          // xi = m 2^(e - 1075) (m with its implicit bit), k = round(xi 2^53) - 2^52
-          const unsigned long long u = (unsigned long long)__double_as_longlong(xi);
-          const int e = (int)((u >> 52) & 0x7FFull);
-          const long long m = (long long)((u & ((1ull << 52) - 1ull)) | (e ? (1ull << 52) : 0ull));
-          const int sh = (e ? e : 1) - 1022;  // xi 2^53 = m 2^sh, sh <= 0
-          long long rr = 0;
-          if (sh == 0) rr = m;
-          else if (sh > -60) rr = (m + (1ll << (-sh - 1))) >> (-sh);
-          const long long k = rr - (1ll << 52);
-          if (order == 1) {
-            k0 += (__int128)(k < 0 ? -k : 0);
-            k1 += (__int128)(k > 0 ? k : 0);
-          } else {
-            k0 += (__int128)k;
-            k1 += (__int128)k * (__int128)k;
-          }
-        }
-#pragma unroll
-        for (int q = 16; q > 0; q >>= 1) {
-          k0 += shfl_xor_i128(k0, q);
-          k1 += shfl_xor_i128(k1, q);
-        }
-        // lanes 0-5 write the record's words
-        long long wv = (long long)(unsigned long long)k0;
-        wv = lane == 1 ? (long long)(k0 >> 64) : wv;
-        wv = lane == 2 ? (long long)(unsigned long long)k1 : wv;
-        wv = lane == 3 ? (long long)(k1 >> 64) : wv;
-        wv = lane == 4 ? wb : wv;
-        wv = lane == 5 ? (long long)n : wv;
-        if (lane < kDepWords) r[lane] = wv;
-      }
-    }
-    if (!fixed) {
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-      for (int64_t p = lane; p < n; p += 32) {
-        const double sx = cell_frac(x[o + p], j, inv_dx) - 0.5;
-        const double al = alpha ? alpha[o + p] : 1.0;
-        if (order == 1) {
-          a0 += al;
-          a1 = sx < 0.0 ? fma(-al, sx, a1) : a1;
-          a2 = sx > 0.0 ? fma(al, sx, a2) : a2;
-        } else {
-          const double as = al * sx;
-          a0 += al;
-          a1 += as;
-          a2 = fma(as, sx, a2);
-        }
-      }
-      a0 = warp_sum(a0);
-      a1 = warp_sum(a1);
-      a2 = warp_sum(a2);
-      long long wv = __double_as_longlong(a0);
-      wv = lane == 1 ? __double_as_longlong(a1) : wv;
-      wv = lane == 2 ? __double_as_longlong(a2) : wv;
-      wv = lane == 5 ? -1ll : wv;
-      if (lane < kDepWords) r[lane] = wv;
-    }
+    const bool same = n > 0 && n <= kFixMaxN && equal_weights(alpha, o, n, lane);
+    deposit_cell(j, o, n, x, alpha, inv_dx, order, rec + (size_t)j * kDepWords, lane, same);
   }
 }
 
@@ -255,6 +177,14 @@ cudaError_t launch_deposit(int64_t C, const int64_t* cell_off, const double* x,
   deposit_partials_kernel<4><<<grid_for((C + 3) / 4, 152 * 16), 128, 0, s>>>(C, cell_off, x, alpha,
                                                                               1.0 / dx, order, rec);
   deposit_combine_kernel<<<grid_for((C + 255) / 256, 1024), 256, 0, s>>>(C, rec, order, q / dx, rho);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_deposit_combine(int64_t C, double dx, double q, int order, const void* ws,
+                                   double* rho, cudaStream_t s) {
+  if (C == 0) return cudaSuccess;
+  deposit_combine_kernel<<<grid_for((C + 255) / 256, 1024), 256, 0, s>>>(C, (const long long*)ws, order,
+                                                                          q / dx, rho);
   return cudaGetLastError();
 }
 

@@ -343,8 +343,10 @@ struct SolveWs {
 // block t of P (rows r0 .. r1-1): forward elimination of the local
 // tridiagonal system (no outer couplings) with three right-hand sides, back
 // substitution, and the block's two interface rows
-__device__ __forceinline__ void block_eliminate(int64_t n, const double* a, const double* b,
-                                                const double* c, const double* d, const SolveWs& ws,
+__device__ __forceinline__ void block_eliminate(int64_t n, const double* __restrict__ a,
+                                                const double* __restrict__ b,
+                                                const double* __restrict__ c,
+                                                const double* __restrict__ d, const SolveWs& ws,
                                                 int P, int t) {
   const int64_t r0 = (int64_t)t * n / P, r1 = (int64_t)(t + 1) * n / P;
   double r = 1.0 / b[r0];
@@ -653,7 +655,9 @@ static void launch_passes(int64_t C, int Kmax, const int32_t* K, const double* p
     // interface rows; its solution: dA for l = 0, else level l - 1's rz
     const double *sa = A, *sb = B, *sc = Cc, *sd = Dd;
     for (int l = 0; l < pl.L; ++l) {
-      mm_eliminate_kernel<<<(pl.P[l] + 127) / 128, 128, 0, s>>>(pl.n[l], sa, sb, sc, sd, lws[l], pl.P[l]);
+      // 32-thread CTAs spread a level's blocks over the SMs (each thread's
+      // elimination is a latency-bound FP64 chain)
+      mm_eliminate_kernel<<<(pl.P[l] + 31) / 32, 32, 0, s>>>(pl.n[l], sa, sb, sc, sd, lws[l], pl.P[l]);
       sa = lws[l].ra; sb = lws[l].rb; sc = lws[l].rc; sd = lws[l].rd;
     }
     const int Pf = pl.Pf;
@@ -661,7 +665,7 @@ static void launch_passes(int64_t C, int Kmax, const int32_t* K, const double* p
     mass_solve_kernel<<<1, Pf < 32 ? 32 : ((Pf + 31) / 32) * 32, 0, s>>>(pl.n[pl.L], sa, sb, sc, sd, xf,
                                                                          lws[pl.L], Pf);
     for (int l = pl.L - 1; l >= 0; --l)
-      mm_reconstruct_kernel<<<(pl.P[l] + 127) / 128, 128, 0, s>>>(pl.n[l], lws[l], pl.P[l],
+      mm_reconstruct_kernel<<<(pl.P[l] + 31) / 32, 32, 0, s>>>(pl.n[l], lws[l], pl.P[l],
                                                                   l > 0 ? lws[l - 1].rz : dA);
   }
   trace_mark("mass-matrix solve (mass_solve_kernel and the blocked kernels)", s);

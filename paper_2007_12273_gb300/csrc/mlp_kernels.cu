@@ -39,13 +39,16 @@ __global__ void __launch_bounds__(NW * 32) features_kernel(int64_t C, int64_t n,
   constexpr int NB = D == 1 ? 64 : 512;
   constexpr int NMOM = D == 1 ? 3 : 10;
   constexpr int NC = D == 1 ? 2 : 9;  // higher moments accumulated
-  __shared__ float hists[NW][NB];
+  // the histogram in fixed point (units of 2^-30 of the cell's weight):
+  // integer shared-memory atomics add in any order to the same sum, so the
+  // features -- and a network trained on them -- are deterministic
+  __shared__ unsigned int hists[NW][NB];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  float* hist = hists[wid];
+  unsigned int* hist = hists[wid];
   for (int64_t j = (int64_t)blockIdx.x * NW + wid; j < C; j += (int64_t)gridDim.x * NW) {
     const int64_t o = cell_off[j];
     const int N = (int)(cell_off[j + 1] - o);
-    for (int b = lane; b < NB; b += 32) hist[b] = 0.0f;
+    for (int b = lane; b < NB; b += 32) hist[b] = 0u;
     // W, and the first and diagonal second moments about the first particle
     float sh[D];
 #pragma unroll
@@ -66,22 +69,24 @@ __global__ void __launch_bounds__(NW * 32) features_kernel(int64_t C, int64_t n,
       }
     }
     W = warp_sum(W);
-    double mean[D], sd[D];
+    // mean = sh + m1 (FP64, the shift kept exact) and sd = sqrt(var) are
+    // stored; the FP32 pass below uses mf = fl32(sh + m1), the FP32 sum
+    // (the same value as the FP64 sum rounded to FP32), and 1 / sd
+    float mf[D], sdf[D];
     bool ok = W > 0.0f;
     const float iW0 = ok ? 1.0f / W : 0.0f;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
       const float m1 = warp_sum(s1[d]) * iW0;
       const float var = fmaxf(warp_sum(s2[d]) * iW0 - m1 * m1, 0.0f);
-      mean[d] = (double)sh[d] + (double)m1;  // the shift kept exact
-      sd[d] = ok ? (double)sqrtf(var) : 0.0;
-      ok = ok && sd[d] > 0.0;
-    }
-    if (lane == 0)
-      for (int d = 0; d < D; ++d) {
-        wstat[j * 2 * D + d] = mean[d];
-        wstat[j * 2 * D + D + d] = sd[d];
+      mf[d] = __fadd_rn(sh[d], m1);  // no contraction with the product m1
+      sdf[d] = ok ? sqrtf(var) : 0.0f;
+      ok = ok && sdf[d] > 0.0f;
+      if (lane == d) {  // one FP64 addition per dimension, on lane d
+        wstat[j * 2 * D + d] = f2d_exact(sh[d]) + f2d_exact(m1);
+        wstat[j * 2 * D + D + d] = f2d_exact(sdf[d]);
       }
+    }
     __nv_bfloat16* fj = feat + (size_t)j * F;
     if (!ok) {
       for (int i = lane; i < F; i += 32) fj[i] = __float2bfloat16(0.0f);
@@ -90,12 +95,9 @@ __global__ void __launch_bounds__(NW * 32) features_kernel(int64_t C, int64_t n,
     }
     __syncwarp();  // histogram zeroed
     // higher moments and the histogram (FP32)
-    float mf[D], isf[D];
+    float isf[D];
 #pragma unroll
-    for (int d = 0; d < D; ++d) {
-      mf[d] = (float)mean[d];
-      isf[d] = 1.0f / (float)sd[d];
-    }
+    for (int d = 0; d < D; ++d) isf[d] = 1.0f / sdf[d];
     const float iW = iW0;
     float s3[NC];
 #pragma unroll
@@ -112,7 +114,7 @@ __global__ void __launch_bounds__(NW * 32) features_kernel(int64_t C, int64_t n,
         s3[1] = fmaf(wy2, y[0] * y[0], s3[1]);
         int b = (int)floorf((y[0] + 4.0f) * 8.0f);
         b = b < 0 ? 0 : (b > 63 ? 63 : b);
-        atomicAdd(&hist[b], w);
+        atomicAdd(&hist[b], __float2uint_rn(w * 1073741824.0f));
       } else {
 #pragma unroll
         for (int d = 0; d < D; ++d) {
@@ -129,7 +131,7 @@ __global__ void __launch_bounds__(NW * 32) features_kernel(int64_t C, int64_t n,
           b[d] = (int)floorf((y[d] + 2.5f) * 1.6f);
           b[d] = b[d] < 0 ? 0 : (b[d] > 7 ? 7 : b[d]);
         }
-        atomicAdd(&hist[b[0] * 64 + b[1] * 8 + b[2]], w);
+        atomicAdd(&hist[b[0] * 64 + b[1] * 8 + b[2]], __float2uint_rn(w * 1073741824.0f));
       }
     }
 #pragma unroll
@@ -148,7 +150,7 @@ __global__ void __launch_bounds__(NW * 32) features_kernel(int64_t C, int64_t n,
           else val = logf((float)N) * 0.1f;
         }
       } else if (i < NMOM + NB) {
-        val = hist[i - NMOM] * (float)NB;
+        val = (float)hist[i - NMOM] * (9.3132257461547852e-10f /* 2^-30 */ * (float)NB);
       }
       fj[i] = __float2bfloat16(val);
     }

@@ -210,6 +210,16 @@ __device__ __forceinline__ float bm_radius(uint64_t m) {
   return sqrtf(-2.0f * lnu);
 }
 
+// (w + 1/2) 2^-32 in FP32 (relative error ~2^-24) for a 32-bit w
+__device__ __forceinline__ float half_ulp32_f(uint32_t w) {
+  return fmaf((float)w, 2.3283064365386963e-10f /* 2^-32 */, 1.1641532182693481e-10f /* 2^-33 */);
+}
+// the same radius for a 32-bit uniform (w + 1/2) 2^-32
+__device__ __forceinline__ float bm_radius32(uint32_t w) {
+  const float lnu = w < 0x80000000u ? logf(half_ulp32_f(w)) : log1pf(-half_ulp32_f(0xFFFFFFFFu - w));
+  return sqrtf(-2.0f * lnu);
+}
+
 // particle i of cell j (Sec. 2.4, eq. mix-dist-1): the 52-bit integer m0
 // of its position's uniform u0 = (m0 + 1/2) 2^-52 (x = (j + u0) dx), its
 // component z (the categorical draw) and f = L_z xi (FP32), so that
@@ -226,20 +236,21 @@ __device__ __forceinline__ void sample_f(const RecCell<D>& rc, int64_t j, int64_
     for (int k = 0; k < K; ++k)
       if (m1x2 < rc.thr[k]) { z = k; break; }
   }
-  // Box-Muller (Box & Muller 1958) on (u2, u3) [and (u4, u5) for D = 3]
+  // Box-Muller (Box & Muller 1958) on block 1: for D = 1 one (radius,
+  // angle) pair of 52-bit uniforms, for D = 3 two pairs of 32-bit uniforms
+  // (words x, y and z, w), so that a 3V particle takes two Philox blocks
   float xi[3];
-  {
-    const u32x4 r1 = philox_draw(seed, (uint32_t)i, kTagSample | 1u, j);
+  const u32x4 r1 = philox_draw(seed, (uint32_t)i, kTagSample | 1u, j);
+  if (D == 1) {
     const float rr = bm_radius(bits52(r1.x, r1.y));
+    xi[0] = rr * cospif(2.0f * half_ulp52_f(bits52(r1.z, r1.w)));
+  } else {
+    const float rr = bm_radius32(r1.x);
     float sn, cs;
-    sincospif(2.0f * half_ulp52_f(bits52(r1.z, r1.w)), &sn, &cs);
+    sincospif(2.0f * half_ulp32_f(r1.y), &sn, &cs);
     xi[0] = rr * cs;
-    if (D == 3) xi[1] = rr * sn;
-  }
-  if (D == 3) {
-    const u32x4 r2 = philox_draw(seed, (uint32_t)i, kTagSample | 2u, j);
-    const float rr = bm_radius(bits52(r2.x, r2.y));
-    xi[2] = rr * cospif(2.0f * half_ulp52_f(bits52(r2.z, r2.w)));
+    xi[1] = rr * sn;
+    xi[2] = bm_radius32(r1.z) * cospif(2.0f * half_ulp32_f(r1.w));
   }
   if (K == 0) {
     for (int d = 0; d < D; ++d) f[d] = 0.0f;

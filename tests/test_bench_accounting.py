@@ -90,9 +90,10 @@ def test_dominant_kernel_roofline_accounting():
     kern = {"em_k1_kernel": {"ms": 2.0, "launches_per_step": 1.0},
             "recon_emit_kernel": {"ms": 1.0, "launches_per_step": 1.0}}
     r = bench.kernel_roofline(kern, ctx)
-    # one-component cells only (K0 == 1): 400 particles x 20 bytes in 2 ms
+    # x and alpha of every particle (1000 x 16 bytes), v of the one-component
+    # cells (K0 == 1: 400 x 12 bytes), in 2 ms
     assert r["kernel"] == "em_k1_kernel" and r["bound"] == "hbm" and r["unit"] == "GB/s"
-    assert r["achieved"] == pytest.approx(400 * 20 / 2e-3 / 1e9)
+    assert r["achieved"] == pytest.approx((1000 * 16 + 400 * 12) / 2e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / 6780.0)
     assert r["secondary"][0]["achieved"] == pytest.approx(400 * 22 / 2e-3 / 1e12)
     kern["recon_emit_kernel"]["ms"] = 3.0
@@ -104,9 +105,9 @@ def test_dominant_kernel_roofline_accounting():
     kern["recon_stats_kernel"] = {"ms": 4.0, "launches_per_step": 1.0}
     r = bench.kernel_roofline(kern, ctx)
     assert r["kernel"] == "recon_stats_kernel" and r["bound"] == "alu" and r["unit"] == "Tops/s"
-    # 3 Philox blocks x 40 + 6 uniforms x 2 + Box-Muller 51 + L xi 6 + sums 8 + 3 x 14
-    assert bench.STATS_OPS_PER_P[3] == 120 + 12 + 51 + 6 + 8 + 42
-    assert r["achieved"] == pytest.approx(1000 * 239 / 4e-3 / 1e12)
+    # 2 Philox blocks x 40 + uniforms (2 x 2 + 4 x 1) + Box-Muller 51 + L xi 6 + sums 8 + 3 x 14
+    assert bench.STATS_OPS_PER_P[3] == 80 + 8 + 51 + 6 + 8 + 42
+    assert r["achieved"] == pytest.approx(1000 * 195 / 4e-3 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / bench.alu_peak_tops(2070.0))
     assert r["secondary"][0]["achieved"] == pytest.approx(1000 * 20 / 4e-3 / 1e9)
     kern = {"mlp_forward (tc_gemm_kernel x4)": {"ms": 1.0, "launches_per_step": 1.0}}

@@ -674,6 +674,27 @@ def test_sampling_3v_covariance():
         assert np.abs(np.cov(v, bias=True) - cov).max() < 6 * np.sqrt(2.0 / n) * np.abs(cov).max()
 
 
+def test_sampling_3v_marginals_are_independent_normals():
+    # the 3V Box-Muller draws (two pairs of 32-bit uniforms from one Philox
+    # block): with one component of covariance diag(1, 4, 9) each coordinate
+    # divided by its standard deviation is N(0, 1) (KS test) and the three
+    # are uncorrelated
+    p = workloads.method_params(3, 1, 2, 2.0, recon_seed=11)
+    C, n = 2, 50000
+    prm = np.zeros((C, 1, 10))
+    prm[:, 0] = [1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.0, 4.0, 0.0, 9.0]
+    out_off = np.arange(C + 1, dtype=np.int64) * n
+    rec = oracle.reconstruct(p, np.full(C, 1, np.int32), prm, np.full(C, float(n)),
+                             np.full(C, float(n)), out_off, want_raw=True)
+    sd = np.array([1.0, 2.0, 3.0])
+    for j in range(C):
+        y = rec["v_raw"][:, j * n:(j + 1) * n] / sd[:, None]
+        for d in range(3):
+            assert stats.kstest(y[d], "norm").pvalue > 1e-3, (j, d)
+        r = np.corrcoef(y)
+        assert np.abs(r - np.eye(3)).max() < 5.0 / math.sqrt(n)
+
+
 def test_projection_failure_is_skipped_and_flagged():
     # Sec. 2.4.2: a negative numerator 2 E N' - p^2 (a cold drifting cell
     # whose weights the Gauss step lowers) skips the projection
