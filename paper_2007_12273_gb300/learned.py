@@ -57,7 +57,7 @@ def compress_learned(net: gm.Net, cfg, cell_off, x, v, alpha, out=None, presence
 
 
 def calibrate_presence(net: gm.Net, cfg, cell_off, x, v, alpha, lnL_plain,
-                       candidates=(0.0, 0.5, 1.0, 2.0, 4.0, 8.0), slack: float = 0.005):
+                       candidates=(0.0, 0.5, 1.0, 2.0, 4.0, 8.0, 16.0), slack: float = 0.005):
     """The decode's presence-logit threshold for a batch of training cells
     whose plain-EM objective (eq. lnL-GM, ``lnL_plain``) is known: for each
     candidate, EM from the decoded start is timed once and its rate of
