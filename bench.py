@@ -261,6 +261,21 @@ EMIT_FP64_PER_P = {1: 2 + 2, 3: 2 + 6}
 DEPOSIT_FP64_PER_P = 2
 
 
+# DRAM traffic (read + write) per particle of the learned step's largest
+# kernels, from one ncu capture (--set full, one launch each) of the
+# first 16384 cells of the 262144-cell lognormal_1d3v batch (9324406
+# particles), the learned step run with a saved network under
+# ncu --set full --clock-control none -k regex:<kernel> -c 1.  The traffic
+# grows with the particles, so a full launch is this times n.
+# An entry must be removed when its kernel changes.
+DRAM_BYTES_PER_PARTICLE = {
+    ("lognormal_1d3v", "em_k1_kernel"): (262.097664e6 + 13.601536e6) / 9324406,
+    ("lognormal_1d3v", "recon_stats_kernel"): (3.957760e6 + 165.344000e6) / 9324406,
+    ("lognormal_1d3v", "recon_emit_kernel"): (230.330880e6 + 315.433472e6) / 9324406,
+    ("lognormal_1d3v", "features_kernel"): (214.720768e6 + 20.601088e6) / 9324406,
+}
+
+
 def alu_peak_tops(sm_mhz: float, sms: int = 152) -> float:
     """152 SMs x 128 32-bit lanes (FP32 / INT32) x the clock, in T ops/s"""
     return sms * 128 * sm_mhz * 1e6 / 1e12
@@ -282,9 +297,12 @@ def kernel_roofline(kernels: dict, ctx: dict) -> dict:
     f32_peak = fp32_peak_tflops(ctx["sm_mhz"])
     f64_note = f"peak = 152 SMs x 2 FP64 FMA/clock x 2 x {ctx['sm_mhz']:.0f} MHz"
 
+    bpp = DRAM_BYTES_PER_PARTICLE.get((ctx.get("workload"), name))
+    traffic = None if bpp is None else bpp * float(n.sum()) / max(1, kt["launches_per_step"])
+
     def line(bound, achieved, peak, unit, note, secondary=None):
         return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None, "ms_per_launch": kt["ms"] / max(1, kt["launches_per_step"]),
+                "frac": achieved / peak, "traffic": traffic, "ms_per_launch": kt["ms"] / max(1, kt["launches_per_step"]),
                 "note": note, "secondary": secondary or []}
 
     def sec_line(unit, achieved, peak, note):
@@ -866,7 +884,8 @@ def run_gmcr(args):
         return dict(counts=counts, D=D, K=o["K"], kwork=o["kwork"], sweeps=o["sweeps"], K0=K0_head,
                     sm_mhz=sm_mhz, hbm_gbs=float(peaks.get("hbm_gbs", 6800.0)),
                     bf16_tflops=float(peaks.get("bf16_tflops", 1900.0)), F=gm.feat_width(D),
-                    O=gm.out_width(D, cfg.Kmax), ms_compress=res[path]["ms_compress"])
+                    O=gm.out_width(D, cfg.Kmax), ms_compress=res[path]["ms_compress"],
+                    workload=args.workload if not args.cells else None)
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -1399,6 +1418,65 @@ def run_c4(args):
     return 0
 
 
+def run_gemm(args):
+    """The tcgen05 BF16 GEMM on its own: C = relu(A B^T + bias) with A
+    [M, K], B [N, K], BF16 output, at the network's first-layer shape
+    (K = 576, N = 256) and M = 65536 rows, and the four layers of the
+    forward pass on M = 262144 rows.  CUDA events per launch, L2 flushed
+    between launches."""
+    from paper_2007_12273_gb300 import gm
+    torch.manual_seed(0)
+    dev_ = torch.device("cuda")
+    peaks = measured_peaks()
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    flush = torch.empty(252 << 20 >> 2, dtype=torch.float32, device=dev_)
+    stream = torch.cuda.current_stream()
+
+    def time_gemm(M, N, K):
+        A = torch.randn(M, K, device=dev_).to(torch.bfloat16)
+        B = torch.randn(N, K, device=dev_).to(torch.bfloat16)
+        bias = torch.randn(N, device=dev_)
+        out = torch.empty(M, N, dtype=torch.bfloat16, device=dev_)
+        for _ in range(max(3, args.warmup)):
+            gm.gm_gemm_bf16(A, B, bias=bias, relu=True, out_bf16=out)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            gm.gm_gemm_bf16(A, B, bias=bias, relu=True, out_bf16=out)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in evs) / args.steps
+        return ms, 2.0 * M * N * K / (ms * 1e-3) / 1e12
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms, tf = time_gemm(65536, 256, 576)
+    layers = [time_gemm(262144, n, k) for n, k in ((256, 576), (256, 256), (256, 256), (112, 256))]
+    clk = clocks.stop()
+    fwd_ms = sum(l[0] for l in layers)
+    fwd_flops = 2.0 * 262144 * (576 * 256 + 2 * 256 * 256 + 256 * 112)
+    result = {
+        "metric": "tcgen05 BF16 GEMM TFLOP/s (M = 65536, N = 256, K = 576, bias + ReLU, BF16 out)",
+        "value": tf, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "one GEMM launch of the network's first-layer shape; the four layers of the "
+                               "forward pass on 262144 rows",
+                   "l2": "a 252 MB flush between timed launches", "launch": "direct calls"},
+        "roofline": {"kernel": "tc_gemm_kernel", "bound": "tensor", "achieved": tf, "peak": bf16,
+                     "unit": "TFLOP/s", "frac": tf / bf16, "traffic": None,
+                     "note": "dense BF16 flops 2 M N K; peak = measured cuBLAS BF16 burst"},
+        "forward_262144_rows": {"ms": fwd_ms, "tflops": fwd_flops / (fwd_ms * 1e-3) / 1e12,
+                                "layers_ms": [l[0] for l in layers]},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(result), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1435,7 +1513,12 @@ def main(argv=None):
     ap.add_argument("--c4", action="store_true",
                     help="the learned initialisation's evaluation: train on 200704 cells of two "
                          "generator families, evaluate on 65536 held-out 1D-3V cells (one GPU)")
+    ap.add_argument("--gemm", action="store_true",
+                    help="the tcgen05 BF16 GEMM on its own (M = 65536, N = 256, K = 576) and the "
+                         "network's four layers on 262144 rows")
     args = ap.parse_args(argv)
+    if args.gemm and args.impl != "reference":
+        return run_gemm(args)
     if args.c4 and args.impl != "reference":
         if args.epochs == 60 and not any(a.startswith("--epochs") for a in (argv or sys.argv[1:])):
             args.epochs = 20

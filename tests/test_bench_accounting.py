@@ -110,6 +110,11 @@ def test_dominant_kernel_roofline_accounting():
     assert r["achieved"] == pytest.approx(1000 * 195 / 4e-3 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / bench.alu_peak_tops(2070.0))
     assert r["secondary"][0]["achieved"] == pytest.approx(1000 * 20 / 4e-3 / 1e9)
+    # traffic: the captured DRAM bytes per particle of the workload, times
+    # the particles of a launch (null for workloads without a capture)
+    assert r["traffic"] is None
+    r = bench.kernel_roofline(kern, dict(ctx, workload="lognormal_1d3v"))
+    assert r["traffic"] == pytest.approx(1000 * (3.957760e6 + 165.344000e6) / 9324406)
     kern = {"mlp_forward (tc_gemm_kernel x4)": {"ms": 1.0, "launches_per_step": 1.0}}
     r = bench.kernel_roofline(kern, ctx)
     assert r["bound"] == "tensor"
