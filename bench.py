@@ -1424,6 +1424,7 @@ def run_gemm(args):
     (K = 576, N = 256) and M = 65536 rows, and the four layers of the
     forward pass on M = 262144 rows.  CUDA events per launch, L2 flushed
     between launches."""
+    import torch
     from paper_2007_12273_gb300 import gm
     torch.manual_seed(0)
     dev_ = torch.device("cuda")
