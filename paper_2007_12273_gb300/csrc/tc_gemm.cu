@@ -300,13 +300,13 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ CU
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TCOLS));
 }
 
+// ring depth: two stages (48 KB each for 128 x 256 tiles), so that two CTAs
+// share an SM (2 x 97 KB of shared memory, at most 2 x 256 TMEM columns)
+// and one's ring fill and epilogue overlap the other's MMAs
 template <int BN>
-constexpr int gemm_stages() { return BN >= 256 ? 3 : 4; }
+constexpr int gemm_stages() { return 2; }
 
-size_t tc_gemm_smem(int bn) {
-  const int S = bn >= 256 ? 3 : 4;
-  return (size_t)(kBM + bn) * kBK * 2 * S + 1024;
-}
+size_t tc_gemm_smem(int bn) { return (size_t)(kBM + bn) * kBK * 2 * 2 + 1024; }
 
 namespace {
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
