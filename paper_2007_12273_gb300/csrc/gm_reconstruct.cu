@@ -185,9 +185,16 @@ __global__ void __launch_bounds__(NW * 32, 6) recon_stats_kernel(int64_t C, int 
       // (exact within 2^-30 of the bound, to 2^-55 of it below)
       int eq[D];
       fix_exponents<D>(rc.Lf[0], eq);
+      // a lane sums at most kFixMaxN / 32 = 512 terms, so its sums of
+      // k (|k| < 2^52) and of f_d / 2^eq_d (below 0.96 x 2^54: |xi| <= 8.6
+      // against the bound's 9) stay below 2^63 and fit in 64 bits; the
+      // squares take 128
       __int128 sm[NS];
+      long long s0 = 0, sf[D];
 #pragma unroll
       for (int t = 0; t < NS; ++t) sm[t] = 0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) sf[d] = 0;
       for (int64_t i = lane; i < n; i += 32) {
         uint64_t m0;
         int z;
@@ -196,19 +203,22 @@ __global__ void __launch_bounds__(NW * 32, 6) recon_stats_kernel(int64_t C, int 
         stage_draw<D>(x_out, v_out, alpha_out, o + i, m0, z, f);
         const long long k = 2ll * (long long)m0 - (1ll << 52) + 1ll;
         if (order == 1) {
-          sm[0] += (__int128)(k < 0 ? -k : 0);
+          s0 += k < 0 ? -k : 0;
           sm[1] += (__int128)(k > 0 ? k : 0);
         } else {
-          sm[0] += (__int128)k;
+          s0 += k;
           sm[1] += (__int128)k * (__int128)k;
         }
 #pragma unroll
         for (int d = 0; d < D; ++d) {
           const long long fq = fixq(f[d], eq[d]);
-          sm[2 + d] += (__int128)fq;
+          sf[d] += fq;
           sm[2 + D + d] += (__int128)fq * (__int128)fq;
         }
       }
+      sm[0] = (__int128)s0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) sm[2 + d] = (__int128)sf[d];
       __int128 mine = 0;
 #pragma unroll
       for (int t = 0; t < NS; ++t) {
