@@ -42,7 +42,10 @@ __device__ __forceinline__ void deposit_cell(int64_t j, int64_t o, int64_t n, co
   // position xi in [0, 1); the weight multiplies the sums once
   if (n > 0 && n <= kFixMaxN && same) {
     const long long wb = alpha ? __double_as_longlong(alpha[o]) : __double_as_longlong(1.0);
-    __int128 k0 = 0, k1 = 0;
+    // a lane sums at most kFixMaxN / 32 = 512 values of |k| <= 2^52: the
+    // linear sum fits in 64 bits, the squares take 128
+    long long k0l = 0;
+    __int128 k1 = 0;
 #pragma unroll 2
     for (int64_t p = lane; p < n; p += 32) {
       const double xi = cell_frac(x[o + p], jd, inv_dx);
@@ -56,13 +59,14 @@ __device__ __forceinline__ void deposit_cell(int64_t j, int64_t o, int64_t n, co
       else if (sh > -60) rr = (m + (1ll << (-sh - 1))) >> (-sh);
       const long long k = rr - (1ll << 52);
       if (order == 1) {
-        k0 += (__int128)(k < 0 ? -k : 0);
+        k0l += k < 0 ? -k : 0;
         k1 += (__int128)(k > 0 ? k : 0);
       } else {
-        k0 += (__int128)k;
+        k0l += k;
         k1 += (__int128)k * (__int128)k;
       }
     }
+    __int128 k0 = (__int128)k0l;
 #pragma unroll
     for (int q = 16; q > 0; q >>= 1) {
       k0 += shfl_xor_i128(k0, q);
