@@ -114,7 +114,7 @@ def test_dominant_kernel_roofline_accounting():
     # the particles of a launch (null for workloads without a capture)
     assert r["traffic"] is None
     r = bench.kernel_roofline(kern, dict(ctx, workload="lognormal_1d3v"))
-    assert r["traffic"] == pytest.approx(1000 * (3.957760e6 + 165.344000e6) / 9324406)
+    assert r["traffic"] == pytest.approx(1000 * (3.977728e6 + 165.554688e6) / 9324406)
     kern = {"mlp_forward (tc_gemm_kernel x4)": {"ms": 1.0, "launches_per_step": 1.0}}
     r = bench.kernel_roofline(kern, ctx)
     assert r["bound"] == "tensor"
