@@ -269,7 +269,6 @@ DEPOSIT_FP64_PER_P = 2
 # grows with the particles, so a full launch is this times n.
 # An entry must be removed when its kernel changes.
 DRAM_BYTES_PER_PARTICLE = {
-    ("lognormal_1d3v", "em_k1_kernel"): (262.102784e6 + 13.659648e6) / 9324406,
     ("lognormal_1d3v", "recon_stats_kernel"): (3.977728e6 + 165.554688e6) / 9324406,
     ("lognormal_1d3v", "recon_emit_kernel"): (230.330880e6 + 315.433472e6) / 9324406,
     ("lognormal_1d3v", "features_kernel"): (214.720768e6 + 20.601088e6) / 9324406,

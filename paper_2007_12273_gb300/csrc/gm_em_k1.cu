@@ -11,9 +11,9 @@ size_t em_k1_raw_bytes(int D, int64_t C) {
 }
 
 cudaError_t launch_em_k1(int D, int v_f64, const K1Params& p, int sms, cudaStream_t s) {
-  constexpr int NW = 8;  // cells (warps) per CTA
+  constexpr int NW = 4;  // cells (warps) per CTA
   const int64_t ncta = (p.C + NW - 1) / NW;
-  const int g = (int)(ncta < (int64_t)sms * 8 ? ncta : (int64_t)sms * 8);
+  const int g = (int)(ncta < (int64_t)sms * 16 ? ncta : (int64_t)sms * 16);
   if (g == 0) return cudaSuccess;
   const int64_t nf = (p.C + 255) / 256;
   const int gf = (int)(nf < 4096 ? nf : 4096);
