@@ -136,7 +136,12 @@ int gm_compress(const gm_config* cfg, int64_t C, int64_t n_particles, const int6
  *      out_off [C+1] int64, n_out = out_off[C].
  * Out: x_out [n_out] f64; v_out [D][n_out] f64; alpha_out [n_out] f64;
  *      status_out [C] uint32; dA_out [C] f64 (may be NULL).
- * Box-Muller normals are FP32; everything else is FP64.
+ * Box-Muller normals are FP32; everything else is FP64.  For D = 3 the
+ * counter's block 1 gives two (radius, angle) pairs of 32-bit uniforms;
+ * for D = 1 one pair of 52-bit uniforms.  The three output arrays
+ * also hold each particle's draw between the call's two particle passes:
+ * until the call completes on the stream their contents are not the
+ * result, and they must not alias each other or the inputs.
  * Errors: GM_ERR_ARG (bad cfg, q = 0, negative sizes, NULL required
  * pointers), GM_ERR_UNSUPPORTED (no sm_103 device), GM_ERR_NOMEM
  * (workspace), GM_ERR_CUDA (launch); per-cell outcomes in status bits.
